@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark: IADM iterations per second of the GB300 TV/L2 solver.
+
+Workload (the single-image binary32 configuration): n = 128 (N = 16384 pixels),
+m = 4915 Gaussian measurements (ratio 0.3), A = 4915 x 16384 binary32 resident
+in HBM (322 MB, larger than the 129 MB L2, so no L2 flush is needed), seeded
+phantom of 12 ellipses plus a rectangle grid, noise 1e-3 RMS, mu = 1e3,
+beta = 10, reconstructions of 300 iterations.  A step is one IADM iteration
+(one pass of rows a1-a7: multiplier update, shrink, right-hand side, FFT
+u-solve, stop norms, A u - f and A^T r).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun, one independent problem per rank (no collective on
+the data path; weak scaling).  `--impl reference` times the FP64 CPU oracle on
+the host cores instead (a bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ADM iter/s and recons/s at <=1e-4 rel err vs FP64 oracle; % of HBM/tensor roofline"
+ITERS_PER_RECON = 300
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_products_n128_m4915.json")
+PRODUCTS_SRC = os.path.join(ROOT, "paper_1001_1774_gb300", "csrc", "k_products.cu")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30000)
+    ap.add_argument("--warmup", type=int, default=300)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-solves", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def workload_config(P, A_bytes):
+    return {"workload": "n128_m4915_fp32_single_image", "n": P.n, "m": P.m, "N": P.N,
+            "mu": P.mu, "beta": P.beta, "iters_per_recon": ITERS_PER_RECON,
+            "A_bytes": A_bytes, "algo": "IADM",
+            "l2": "inputs larger than L2 (A = %.0f MB > 129 MB); no flush" % (A_bytes / 1e6),
+            "parallelism": "one independent problem per GPU"}
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, local_rank: int):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        idx = str(local_rank)
+        if vis:
+            parts = [p.strip() for p in vis.split(",") if p.strip()]
+            if local_rank < len(parts):
+                idx = parts[local_rank]
+        self.idx = idx
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", self.idx], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        with open(self.path) as fh:
+            for line in fh:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(self.NAMES, p[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- traffic summary
+
+def traffic_from_profile():
+    """dram bytes per launch of the product kernel from the committed ncu summary,
+    or None when the kernel source changed since it was taken."""
+    try:
+        with open(PROFILE_SUMMARY) as fh:
+            d = json.load(fh)
+        with open(PRODUCTS_SRC, "rb") as fh:
+            sha = hashlib.sha256(fh.read()).hexdigest()
+        if d.get("source_sha256") != sha:
+            return None
+        return float(d["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------------------- CPU oracle sample
+
+def oracle_sample(P, tau, budget_s=20.0, want_u=False):
+    """Times the FP64 oracle (as it stands) on this host: iterations/s measured on
+    a bounded number of iterations of the same workload."""
+    import numpy as np
+    import oracle
+    t0 = time.perf_counter()
+    oracle.solve(P.A, P.f, P.n, P.mu, P.beta, tau, max_iter=0)
+    t_init = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.solve(P.A, P.f, P.n, P.mu, P.beta, tau, max_iter=2)
+    per = max((time.perf_counter() - t0 - t_init) / 2, 1e-6)
+    iters = ITERS_PER_RECON if per * ITERS_PER_RECON <= budget_s else max(2, int(budget_s / per))
+    t0 = time.perf_counter()
+    res = oracle.solve(P.A, P.f, P.n, P.mu, P.beta, tau, max_iter=iters)
+    elapsed = time.perf_counter() - t0 - t_init
+    return {"iters": iters, "seconds": elapsed, "value": iters / elapsed,
+            "cores": oracle.num_threads(), "u": res.u if want_u else None}
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    import __graft_entry__
+    ws, rank, local = dist_env()
+    if ws > 1:
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    torch.cuda.set_device(local)
+    if rank == 0:
+        __graft_entry__.build()
+    if ws > 1:
+        dist.barrier()
+    import paper_1001_1774_gb300 as tv
+
+    P = synth.workload_n128() if rank == 0 else synth.make_problem(
+        128, 0.3, 1 + rank, 12, 1e3, 10.0, 0.0, ITERS_PER_RECON, 1e-3, rect_grid=True)
+    stream = torch.cuda.Stream()
+    opt = tv.tvcs_default_options()
+    opt.max_iter = ITERS_PER_RECON
+    opt.stream = ctypes_stream(stream)
+    with torch.cuda.stream(stream):
+        A_dev = torch.from_numpy(P.A).cuda()
+        f_dev = torch.from_numpy(P.f).cuda()
+        u_dev = torch.empty(P.N, dtype=torch.float32, device="cuda")
+    stream.synchronize()
+    h = tv.tvcs_create(A_dev, 0, P.m, P.n, P.mu, P.beta, 0.0, opt)
+    del A_dev
+    tau = tv.tvcs_get_tau(h)
+    # first reconstruction: builds the loop graph and the state
+    tv.tvcs_solve(h, f_dev, u_dev)
+    tv.tvcs_iterate(h, max(args.warmup, 3))
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    sampler = ClockSampler(local)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.2)
+    torch.cuda.nvtx.range_push("timed")
+    ev0.record(stream)
+    res = tv.tvcs_iterate(h, args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    clocks = sampler.stop()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    assert res.iters == args.steps, res.iters
+
+    # Dominant kernel (products, one pass over A): launches back to back on the same stream.
+    reps = 400
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("products")
+    k0.record(stream)
+    tv.tvcs_time_stage(h, 3, reps)
+    k1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    prod_us = k0.elapsed_time(k1) * 1e3 / reps
+    stage_us = {"products": prod_us,
+                "wstep_rowfft": tv.tvcs_time_stage(h, 1, 400) * 1e3 / 400,
+                "fft_cols_rows_inv": tv.tvcs_time_stage(h, 2, 400) * 1e3 / 400}
+    # restore a clean state after the timing runs
+    tv.tvcs_solve(h, f_dev, u_dev)
+
+    # End to end through the C ABI with pinned host buffers: each call copies f in
+    # and the image out and runs one 300-iteration reconstruction.
+    f_host = torch.from_numpy(P.f).pin_memory()
+    u_host = torch.empty(P.N, dtype=torch.float32).pin_memory()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_solves):
+        r = tv.tvcs_solve(h, f_host, u_host)
+        assert r.iters == ITERS_PER_RECON
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    u_gpu = u_host.numpy().copy()
+
+    out = None
+    if rank == 0:
+        peak, peak_src = hbm_peak()
+        A_bytes = P.m * P.N * 4
+        alg_bytes = A_bytes + 4 * (P.N + 2 * P.m)
+        achieved = alg_bytes / (prod_us * 1e-6) / 1e9
+        traffic = traffic_from_profile()
+        value = ws * args.steps / (ms / 1e3)
+        e2e_iters = ws * args.e2e_solves * ITERS_PER_RECON
+        out = {
+            "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic (seeded phantom, Philox Gaussian A)",
+            "recons_per_s": value / ITERS_PER_RECON,
+            "config": workload_config(P, A_bytes),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_products (fused A u - f and A^T r, one pass over A)",
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "launch_us": prod_us, "peak_source": peak_src},
+            "stage_us": stage_us,
+            "e2e": {"value": e2e_iters / e2e_s, "unit": "iter/s",
+                    "h2d_bytes_per_step": 4 * P.m / ITERS_PER_RECON,
+                    "d2h_bytes_per_step": 4 * P.N / ITERS_PER_RECON,
+                    "note": "tvcs_solve with pinned host f and u, %d reconstructions of %d iterations"
+                            % (args.e2e_solves, ITERS_PER_RECON)},
+            "gpu_launches": 4 * args.steps + 2,
+            "clocks": clocks,
+            "tau": tau,
+        }
+        if ws == 1 and not args.no_cpu_baseline:
+            cb = oracle_sample(P, tau, want_u=True)
+            out["cpu_baseline"] = {"value": cb["value"], "unit": "iter/s", "cores": cb["cores"],
+                                   "kind": "oracle",
+                                   "sample": "%d IADM iterations of the same workload (FP64 C "
+                                             "oracle, OpenMP), %.1f s" % (cb["iters"], cb["seconds"])}
+            if cb["iters"] == ITERS_PER_RECON:
+                ref = cb["u"].ravel()
+                err = float(np.linalg.norm(u_gpu - ref) / np.linalg.norm(ref))
+                out["parity_vs_oracle"] = {"rel_image_err": err, "iters": ITERS_PER_RECON,
+                                           "ok": err <= 1e-4}
+    tv.tvcs_destroy(h)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+def ctypes_stream(stream) -> int:
+    return int(stream.cuda_stream)
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    P = synth.workload_n128()
+    tau = oracle.default_tau(P.A, 100)
+    budget = 60.0
+    # warm-up: W oracle iterations at most, bounded in time
+    t0 = time.perf_counter()
+    oracle.solve(P.A, P.f, P.n, P.mu, P.beta, tau, max_iter=min(args.warmup, 3))
+    warm = time.perf_counter() - t0
+    cb = oracle_sample(P, tau, budget_s=budget)
+    A_bytes = P.m * P.N * 4
+    value = cb["value"]
+    sample = ("%d of %d requested IADM iterations (FP64 C oracle, OpenMP), %.1f s"
+              % (cb["iters"], args.steps, cb["seconds"]))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iter/s",
+           "n_gpus": ws, "steps": cb["iters"], "warmup": args.warmup,
+           "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded phantom, Philox Gaussian A)",
+           "config": workload_config(P, A_bytes),
+           "cpu_baseline": {"value": value, "unit": "iter/s", "cores": cb["cores"],
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0},
+           "warmup_seconds": warm}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,175 @@
+/*
+ * tvcs.h -- C ABI of the GB300 (sm_103a) solver for TV/L2 image reconstruction
+ * from random projections (Xiao & Yang, "A Fast Algorithm for Total Variation
+ * Image Reconstruction from Random Projections").
+ *
+ * Problem (eq. (tv), Sec. 1):
+ *     min_u  sum_i ||D_i u||_2 + (mu/2) ||A u - f||_2^2
+ * u: n x n image (row-major, N = n*n pixels), A: m x N dense encoding matrix
+ * (row-major), f: m measurements.  D_i u = (u[r][c+1]-u[r][c], u[r+1][c]-u[r][c])
+ * with periodic boundary (Sec. 1.4, Sec. 2.1).
+ *
+ * Solver: Algorithm 2 (IADM, Sec. 2.2) or Algorithm 1 (FTVCS, Sec. 2.1).  Each
+ * iteration is one isotropic shrinkage, the products A*u and A^T*(A u - f),
+ * and one FFT pair (Sec. 3.1).  All arithmetic runs in this library's CUDA
+ * kernels; binary32 for the iterates, binary64 for the norms of the stopping
+ * test, the objective and the optimality residuals.
+ *
+ * Conventions for every entry point:
+ *  - Pointers to arrays may be host (pageable or pinned) or device pointers;
+ *    the library detects the kind with cudaPointerGetAttributes and copies
+ *    through its own device buffers.  The caller keeps ownership of every
+ *    array it passes; the library keeps no pointer to caller memory after a
+ *    call returns.
+ *  - All device work is ordered on the handle's stream (tvcs_options.stream).
+ *    Every call is synchronous: it returns after its device work finished.
+ *  - Errors: a negative tvcs_status, with a message for tvcs_last_error().
+ *    No call aborts, throws or exits.  Arguments are validated before any
+ *    device work, so invalid arguments never reach a kernel.
+ *  - One handle must not be used by two host threads at the same time.
+ */
+#ifndef TVCS_H
+#define TVCS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tvcs_ctx* tvcs_handle;
+
+typedef enum {
+    TVCS_OK = 0,
+    TVCS_NOT_CONVERGED = 1,      /* max_iter reached before eq. (stop) held (not an error) */
+    TVCS_ERR_INVALID_ARG = -1,   /* null pointer, unsupported size, non-positive parameter */
+    TVCS_ERR_OOM = -2,           /* device or host allocation failed */
+    TVCS_ERR_CUDA = -3,          /* a CUDA runtime call failed (message names it) */
+    TVCS_ERR_TIMEOUT = -4,       /* a bounded device wait gave up */
+    TVCS_ERR_DIVERGED = -5,      /* non-finite iterate or objective */
+    TVCS_ERR_UNSUPPORTED = -6    /* valid request this build does not implement */
+} tvcs_status;
+
+enum { TVCS_ALGO_IADM = 0, TVCS_ALGO_FTVCS = 1 };
+/* Storage of A for the products: binary32; binary16-bfloat hi+lo split (the
+ * entries are hi + lo with both rounded to nearest); FP8 E4M3 with a per-row
+ * binary32 scale plus a bfloat16 correction. */
+enum { TVCS_PREC_FP32 = 0, TVCS_PREC_BF16X2 = 1, TVCS_PREC_FP8_BF16 = 2 };
+/* Initial point: A^T f (back-projection), zero, or caller-given (tvcs_set_state). */
+enum { TVCS_INIT_ATF = 0, TVCS_INIT_ZERO = 1, TVCS_INIT_GIVEN = 2 };
+
+typedef struct {
+    int algo;            /* TVCS_ALGO_IADM (default) or TVCS_ALGO_FTVCS */
+    double tau;          /* proximal step of eq. (line); <= 0: 1/(1.01*lambda_max(A^T A)),
+                            lambda_max from power_iters rounds of power iteration */
+    int max_iter;        /* iteration cap; <= 0: 500 */
+    int precision;       /* TVCS_PREC_* */
+    int init;            /* TVCS_INIT_* for tvcs_solve */
+    void* stream;        /* cudaStream_t for all device work; NULL: a stream the handle owns */
+    int power_iters;     /* <= 0: 100 */
+    long long timeout_cycles; /* bound of every device spin-wait, in SM clock cycles; <= 0: 2^31 */
+} tvcs_options;
+
+typedef struct {
+    int iters;           /* completed iterations of this call */
+    int status;          /* tvcs_status of the call */
+    int stopped_by_tol;  /* 1 if eq. (stop) ended the loop */
+    double rel_change;   /* ||u^k - u^{k-1}|| / ||u^{k-1}|| at the last iteration */
+    double tv;           /* sum_i ||D_i u|| at the returned u */
+    double resid2;       /* ||A u - f||^2 at the returned u */
+    double objective;    /* tv + (mu/2) resid2 */
+    double kkt_primal;   /* ||w - D u|| (after the final multiplier update) */
+    double kkt_dual;     /* ||D^T lambda + mu A^T (A u - f)|| */
+    double lambda_max_norm; /* max_i ||lambda_i|| */
+    double ms;           /* device time of the iterations, milliseconds */
+} tvcs_result;
+
+/* Fills *opt with the defaults above.  Never fails for non-null opt. */
+void tvcs_default_options(tvcs_options* opt);
+
+/*
+ * Creates a solver for one problem size and parameter set.
+ *   A      m x n*n row-major binary32, host or device; NULL: generate A on the
+ *          device from `seed` by the counter-based Gaussian recipe (Philox4x32-10
+ *          and Box-Muller, entries N(0, 1/m); the recipe is stated at the top
+ *          of the library's generator source, k_gen.cu).  A is copied (or generated) into device
+ *          memory the handle owns, stored in opt->precision.
+ *   m      number of measurements, 1 <= m <= 2^24
+ *   n      image side: 4 <= n <= 256, n = 2^a 3^b, n even
+ *   mu     > 0, beta > 0 (penalty of eq. (ALP)), tol >= 0 (eq. (stop); 0 disables)
+ *   opt    nullable (defaults)
+ * On success *out receives the handle (destroy with tvcs_destroy).
+ */
+tvcs_status tvcs_create(tvcs_handle* out, const float* A, uint64_t seed, int m, int n,
+                        double mu, double beta, double tol, const tvcs_options* opt);
+
+/*
+ * Solves from the handle's initial point (opt->init) with data f (m values,
+ * host or device) and writes the n*n image to u (host or device).  Runs at
+ * most max_iter iterations; res (nullable) receives the summary.
+ * Returns TVCS_OK when eq. (stop) held, TVCS_NOT_CONVERGED when max_iter
+ * ended the loop, or an error.
+ */
+tvcs_status tvcs_solve(tvcs_handle h, const float* f, float* u, tvcs_result* res);
+
+/*
+ * Solves `count` problems.  hs[i] are handles, f[i] (m_i values) and u[i]
+ * (n_i*n_i values) host or device pointers; mu (nullable) overrides each
+ * handle's mu; res (nullable) receives count summaries.  When every hs[i] is
+ * the same handle the products run as batched GEMMs over all images;
+ * otherwise the problems are solved one after another on the first handle's
+ * stream.
+ */
+tvcs_status tvcs_solve_batched(const tvcs_handle* hs, int count, const float* const* f,
+                               float* const* u, const double* mu, tvcs_result* res);
+
+/* Releases every resource of h (NULL is a no-op). */
+tvcs_status tvcs_destroy(tvcs_handle h);
+
+/* Message for the last non-OK status returned on the calling thread. */
+const char* tvcs_last_error(void);
+
+/* ---- Step-level access (for tests and tools; same conventions) ------------ */
+
+/* tau used by the handle (auto or given). */
+tvcs_status tvcs_get_tau(tvcs_handle h, double* tau);
+
+enum { TVCS_STATE_U = 0,      /* n*n   current iterate u^k */
+       TVCS_STATE_W = 1,      /* 2*n*n w^k (w1 plane, then w2 plane) */
+       TVCS_STATE_LAMBDA = 2, /* 2*n*n lambda^k (lambda1 plane, then lambda2 plane) */
+       TVCS_STATE_G = 3,      /* n*n   g^k = A^T (A u^k - f) */
+       TVCS_STATE_R = 4,      /* m     r^k = A u^k - f */
+       TVCS_STATE_RHS = 5,    /* n*n   right-hand side of the last u-step, scaled by beta */
+       TVCS_STATE_F = 6 };    /* m     data f */
+
+/* Copies one state array out (get) or in (set; only U, LAMBDA and F).  Setting U
+ * or F recomputes r and g; setting LAMBDA clears any pending multiplier update. */
+tvcs_status tvcs_get_state(tvcs_handle h, int which, float* dst);
+tvcs_status tvcs_set_state(tvcs_handle h, int which, const float* src);
+
+/* Runs exactly `iters` iterations from the current state (no stopping test),
+ * then applies the pending multiplier update and fills res (nullable). */
+tvcs_status tvcs_iterate(tvcs_handle h, int iters, tvcs_result* res);
+
+/* Row-level entry points.  Stage 1: rows a1-a3 (multiplier update, shrink,
+ * u-step right-hand side); stage 2: row a4-a5 (FFT u-solve into u, stop
+ * norms); stage 3: rows a6-a7 (r = A u - f, g = A^T r).  The state moves as
+ * in one iteration of tvcs_iterate. */
+tvcs_status tvcs_run_stage(tvcs_handle h, int stage);
+
+/* Times `reps` back-to-back launches of one stage (1, 2 or 3, as in
+ * tvcs_run_stage, without its host-side bookkeeping) on the handle's stream
+ * between two CUDA events; *ms receives the elapsed milliseconds.  Afterwards
+ * the state is that of `reps` applications of the stage (stage 3 leaves it
+ * unchanged).  Requires a state (tvcs_solve or tvcs_set_state first). */
+tvcs_status tvcs_time_stage(tvcs_handle h, int stage, int reps, double* ms);
+
+/* Products alone on caller data: r = A x - y (y nullable: r = A x) and
+ * g = A^T r, with the handle's stored A.  x: N, y: m, r: m, g: N. */
+tvcs_status tvcs_apply(tvcs_handle h, const float* x, const float* y, float* r, float* g);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TVCS_H */

@@ -1,0 +1,196 @@
+// Shared device definitions of the TV/L2 solver library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tvcs {
+
+// Device-side control block of one handle.  Written by single threads at
+// kernel boundaries (never concurrently within one kernel), read by all.
+struct Ctrl {
+    int it;            // iterations completed in the current run
+    int max_iter;      // cap of the current run
+    int done;          // 1: the run has ended; later iterations are skipped
+    int skip;          // 1: the current iteration is skipped (copied from done by the w-step)
+    int pending;       // 1: the multiplier update of eq. (udlamb) for the last u is pending
+    int stop_by_tol;   // 1: eq. (stop) ended the run
+    int loops;         // executions of the graph loop body (hard bound on the loop)
+    int loops_max;
+    unsigned ticket_fft;   // last-block tickets of the reducing kernels
+    unsigned ticket_prod;
+    unsigned ticket_fin;
+    unsigned ticket_w;
+    unsigned ticket_gather;
+    int wpar;          // which copy of the double-buffered w/lambda is current
+    int error;         // ERR_* below, first error wins
+    int algo;          // 0 IADM, 1 FTVCS
+    double tol;
+    double du2;        // ||u^{k+1} - u^k||^2 of the last iteration
+    double u2;         // ||u^k||^2 of the last iteration
+    double relchg;     // sqrt(du2/u2)
+    double r2;         // ||A u - f||^2 at the current u
+    double tv;         // sum_i ||D_i u||
+    double kkt_p2;     // ||w - D u||^2
+    double kkt_d2;     // ||D^T lambda + mu g||^2
+    double lam_max;    // max_i ||lambda_i||
+    double vec2;       // ||g||^2 of the last gathered vector (power iteration)
+};
+
+enum { ERR_NONE = 0, ERR_TIMEOUT = 1, ERR_NONFINITE = 2 };
+
+// Iteration-kernel modes.
+enum { MODE_PLAIN = 0, MODE_ITER = 1 };
+
+__device__ __forceinline__ void set_error(Ctrl* c, int code)
+{
+    atomicCAS(&c->error, ERR_NONE, code);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// ---- mbarrier (PTX ISA, "Parallel Synchronization and Communication") ----
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t tx)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(tx)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on a phase of an mbarrier: false when `budget` SM cycles pass.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long budget)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > budget) return false;
+    }
+    return true;
+}
+
+// ---- bulk asynchronous copy global -> shared (TMA, non-tensor form) ----
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void tma_load_1d(void* dst_smem, const void* src_gmem, uint32_t bytes,
+                                            uint64_t* bar, uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
+__device__ __forceinline__ uint64_t l2_policy_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// Named barrier over `count` threads (a multiple of 32).
+__device__ __forceinline__ void named_barrier(int id, int count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide sum of one double per thread; result valid in thread 0.
+// `scratch` holds >= 32 doubles of shared memory.
+__device__ __forceinline__ double block_sum(double v, double* scratch)
+{
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int i = 0; i < nw; ++i) s += scratch[i];
+    }
+    return s;
+}
+
+__device__ __forceinline__ double block_max(double v, double* scratch)
+{
+    v = warp_max(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int i = 0; i < nw; ++i) s = fmax(s, scratch[i]);
+    }
+    return s;
+}
+
+// Last-block detection: returns true in exactly one block (the last to
+// arrive), after every block's prior global writes are visible to it.  The
+// ticket is reset by that block.  Call from thread 0 only.
+__device__ __forceinline__ bool last_block_arrive(unsigned* ticket)
+{
+    __threadfence();
+    const unsigned t = atomicAdd(ticket, 1u);
+    const bool last = (t == gridDim.x * gridDim.y * gridDim.z - 1);
+    if (last) {
+        __threadfence();
+        *ticket = 0u;
+    }
+    return last;
+}
+
+}  // namespace tvcs

@@ -1,0 +1,166 @@
+// Shared-memory mixed-radix (4, 3, 2) Stockham FFT of compile-time length NN,
+// used for the u-step of eq. (eqnorm11): the 2D DFT diagonalises D^T D under
+// periodic boundary (Sec. 2.1), so the u-solve is a forward 2D FFT, a divide
+// by beta*Lambda_pq + mu/tau and an inverse 2D FFT.
+//
+// Stage s with radix R and Ns = product of the earlier radices computes, for
+// j in [0, NN/R), k = j mod Ns:
+//   v_r = x[j + r*NN/R] * W^(r*k*NN/(Ns*R)),  V = DFT_R(v),
+//   y[(j/Ns)*Ns*R + k + r*Ns] = V_r,
+// W = exp(-2 pi i/NN) (forward) or its conjugate (inverse, unnormalised).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace tvcs {
+
+// Radix of stage s for length n: all 4s first, then 3s, then 2s.
+__host__ __device__ constexpr int fft_radix(int n, int s)
+{
+    int m = n, st = 0;
+    while (m % 4 == 0 && m > 2) {
+        if (st == s) return 4;
+        m /= 4;
+        ++st;
+    }
+    while (m % 3 == 0) {
+        if (st == s) return 3;
+        m /= 3;
+        ++st;
+    }
+    while (m % 2 == 0) {
+        if (st == s) return 2;
+        m /= 2;
+        ++st;
+    }
+    return 0;
+}
+
+__host__ __device__ constexpr int fft_nstages(int n)
+{
+    int s = 0;
+    while (fft_radix(n, s) != 0) ++s;
+    return s;
+}
+
+__host__ __device__ constexpr int fft_ns(int n, int s)
+{
+    int p = 1;
+    for (int i = 0; i < s; ++i) p *= fft_radix(n, i);
+    return p;
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+// Multiply by -i (forward) or +i (inverse).
+template <bool INV>
+__device__ __forceinline__ float2 mul_mi(float2 a)
+{
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft_small(float2* v)
+{
+    if constexpr (R == 2) {
+        float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if constexpr (R == 4) {
+        float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+        float2 s13 = cadd(v[1], v[3]), d13 = mul_mi<INV>(csub(v[1], v[3]));
+        v[0] = cadd(s02, s13);
+        v[2] = csub(s02, s13);
+        v[1] = cadd(d02, d13);
+        v[3] = csub(d02, d13);
+    } else {  // R == 3: w = exp(-+2 pi i/3) = -1/2 -+ i sqrt(3)/2
+        const float h = 0.866025403784438647f;  // sqrt(3)/2
+        float2 a = v[0], b = v[1], c = v[2];
+        float2 s = cadd(b, c), d = csub(b, c);
+        float2 t = make_float2(a.x - 0.5f * s.x, a.y - 0.5f * s.y);
+        // -+ i*h*d
+        float2 e = INV ? make_float2(-h * d.y, h * d.x) : make_float2(h * d.y, -h * d.x);
+        v[0] = cadd(a, s);
+        v[1] = cadd(t, e);
+        v[2] = csub(t, e);
+    }
+}
+
+// One Stockham stage over `nfft` transforms stored with distance `dist`.
+template <int NN, int S, bool INV>
+__device__ __forceinline__ void fft_stage(const float2* __restrict__ src, float2* __restrict__ dst,
+                                          const float2* __restrict__ tw, int nfft, int dist,
+                                          int tid, int nthr)
+{
+    constexpr int R = fft_radix(NN, S);
+    constexpr int NS = fft_ns(NN, S);
+    constexpr int L = NN / R;          // butterflies per transform
+    constexpr int TSTEP = NN / (NS * R);
+    const int total = nfft * L;
+    for (int idx = tid; idx < total; idx += nthr) {
+        const int f = idx / L;
+        const int j = idx - f * L;
+        const int k = j % NS;
+        const float2* s = src + f * dist;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            float2 x = s[j + r * L];
+            if (r > 0 && NS > 1) {
+                const int t = (r * k * TSTEP) % NN;
+                float2 w = tw[t];
+                if (!INV) w.y = -w.y;
+                x = cmul(x, w);
+            }
+            v[r] = x;
+        }
+        dft_small<R, INV>(v);
+        float2* d = dst + f * dist;
+        const int base = (j / NS) * NS * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) d[base + r * NS] = v[r];
+    }
+}
+
+// Recursion end: S == number of stages.
+template <int NN, bool INV, int S, bool END = (S == fft_nstages(NN))>
+struct FftRun;
+
+template <int NN, bool INV, int S>
+struct FftRun<NN, INV, S, true> {
+    static __device__ __forceinline__ float2* run(float2* a, float2*, const float2*, int, int, int,
+                                                  int)
+    {
+        return a;
+    }
+};
+
+template <int NN, bool INV, int S>
+struct FftRun<NN, INV, S, false> {
+    static __device__ __forceinline__ float2* run(float2* a, float2* b, const float2* tw, int nfft,
+                                                  int dist, int tid, int nthr)
+    {
+        fft_stage<NN, S, INV>(a, b, tw, nfft, dist, tid, nthr);
+        __syncthreads();
+        return FftRun<NN, INV, S + 1>::run(b, a, tw, nfft, dist, tid, nthr);
+    }
+};
+
+// Transforms `nfft` sequences of length NN held in shared memory at a (element
+// i of transform f at a[f*dist + i]); b is scratch of the same size.  Every
+// thread of the block must call it; the input must be visible (synchronised)
+// before the call.  Returns the buffer holding the result (a or b).
+template <int NN, bool INV>
+__device__ __forceinline__ float2* fft_block(float2* a, float2* b, const float2* tw, int nfft,
+                                             int dist)
+{
+    return FftRun<NN, INV, 0>::run(a, b, tw, nfft, dist, threadIdx.x, blockDim.x);
+}
+
+}  // namespace tvcs

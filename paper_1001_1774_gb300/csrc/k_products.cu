@@ -1,0 +1,363 @@
+// Rows a6-a7: r = A x - y and g = A^T r in ONE pass over A (Xiao & Yang,
+// eq. (line): g_k = A^T (A u^k - f); two products per iteration, Sec. 3.1).
+//
+// Each block owns a contiguous range of rows of A (row-major binary32).  A
+// producer warp streams the rows into a 3-stage shared-memory ring with bulk
+// asynchronous copies (TMA, non-tensor form, one mbarrier per stage; A is
+// read once per call, with an L2 evict-first hint).  Consumer threads own
+// fixed columns: for each row they form the dot product with x (warp
+// shuffles + one named barrier), compute r_i = dot - y_i, and fold r_i * A_i
+// into per-thread accumulators of A^T r.  Row i's data is used twice from
+// shared memory and read from HBM once, so the algorithmic traffic is one pass
+// over A.  Each block writes its partial A^T r (N floats); the next kernel sums
+// the P partials in a fixed order (deterministic).
+//
+// Shapes: consumer threads = 512 in RL row lanes of TPR = 512/RL threads; a
+// thread holds V float4 columns of x and of the accumulator (N = 4*TPR*V).
+// RS rows per stage (<= 72 KB), 3 stages.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace tvcs {
+
+constexpr int PROD_CONS = 512;
+constexpr int PROD_THREADS = PROD_CONS + 32;
+constexpr int PROD_NST = 3;
+
+template <int V, int RL, int RS>
+struct ProdShape {
+    static constexpr int TPR = PROD_CONS / RL;
+    static constexpr int WPR = TPR / 32;
+    static constexpr int N = 4 * TPR * V;
+    static constexpr size_t STAGE_FLOATS = (size_t)RS * N;
+    static constexpr size_t SMEM = PROD_NST * STAGE_FLOATS * 4 + 2 * PROD_NST * 8 +
+                                   2 * RL * WPR * 4 + 32 * 8 + 64;
+    static_assert(RS % RL == 0, "rows per stage must be a multiple of the row lanes");
+    static_assert(TPR % 32 == 0, "row lanes must be whole warps");
+};
+
+template <int V, int RL, int RS>
+__global__ void __launch_bounds__(PROD_THREADS, 1)
+    k_products(const float* __restrict__ A, int m, const float* __restrict__ x,
+               const float* __restrict__ y, float* __restrict__ r, float* __restrict__ gpart,
+               double* __restrict__ r2part, Ctrl* __restrict__ ctrl, int mode,
+               cudaGraphConditionalHandle cond, int set_cond, long long budget)
+{
+    using S = ProdShape<V, RL, RS>;
+    constexpr int N = S::N;
+    constexpr int TPR = S::TPR;
+    constexpr int WPR = S::WPR;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float* stage = reinterpret_cast<float*>(smem);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + PROD_NST * S::STAGE_FLOATS * 4);
+    uint64_t* empty = full + PROD_NST;
+    float* red = reinterpret_cast<float*>(empty + PROD_NST);        // [2][RL][WPR]
+    double* dred = reinterpret_cast<double*>(red + 2 * RL * WPR);   // [32]
+
+    const int tid = threadIdx.x;
+    if (mode == MODE_ITER) {
+        const int skip = ctrl->skip;
+        if (blockIdx.x == 0 && tid == 0) {
+            if (!skip && ctrl->algo == 0) ctrl->pending = 1;
+            if (set_cond) {
+                // The loop ends when the run is done; `loops` bounds it independently.
+                const int lc = ++ctrl->loops;
+                const int cont =
+                    (!ctrl->done && ctrl->error == ERR_NONE && lc < ctrl->loops_max) ? 1 : 0;
+                cudaGraphSetConditional(cond, (unsigned)cont);
+            }
+        }
+        if (skip) return;
+    }
+
+    const int G = gridDim.x;
+    const int i0 = (int)(((long long)m * blockIdx.x) / G);
+    const int i1 = (int)(((long long)m * (blockIdx.x + 1)) / G);
+    const int nrows = i1 - i0;
+    const int nst = (nrows + RS - 1) / RS;
+
+    if (tid == 0) {
+        for (int s = 0; s < PROD_NST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], PROD_CONS / 32);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (tid >= PROD_CONS) {
+        // ---------------- producer warp ----------------
+        if (tid == PROD_CONS) {
+            const uint64_t pol = l2_policy_evict_first();
+            bool ok = true;
+            for (int s = 0; s < nst; ++s) {
+                const int slot = s % PROD_NST;
+                if (s >= PROD_NST && ok) {
+                    if (!mbar_wait(&empty[slot], ((s / PROD_NST) - 1) & 1, budget)) {
+                        set_error(ctrl, ERR_TIMEOUT);
+                        ok = false;
+                    }
+                }
+                if (!ok) break;
+                const int rows = min(RS, nrows - s * RS);
+                const uint32_t bytes = (uint32_t)rows * N * 4u;
+                mbar_arrive_expect_tx(&full[slot], bytes);
+                tma_load_1d(stage + slot * S::STAGE_FLOATS, A + (size_t)(i0 + s * RS) * N, bytes,
+                            &full[slot], pol);
+            }
+            // Leave no copy in flight: wait for the last stages to land.
+            const int first = ok ? max(0, nst - PROD_NST) : nst;
+            for (int s = first; s < nst; ++s) mbar_wait(&full[s % PROD_NST], (s / PROD_NST) & 1, budget);
+        }
+        return;
+    }
+
+    // ---------------- consumers ----------------
+    const int lane_row = tid / TPR;
+    const int ltid = tid - lane_row * TPR;
+    const int warp_in_row = ltid >> 5;
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    float4 xu[V], acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        xu[v] = x4[ltid + v * TPR];
+        acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    double r2 = 0.0;
+    bool ok = true;
+    int step = 0;
+    for (int s = 0; s < nst; ++s) {
+        const int slot = s % PROD_NST;
+        if (ok && !mbar_wait(&full[slot], (s / PROD_NST) & 1, budget)) {
+            set_error(ctrl, ERR_TIMEOUT);
+            ok = false;
+        }
+        const float* sb = stage + slot * S::STAGE_FLOATS;
+        const int rows = min(RS, nrows - s * RS);
+#pragma unroll 1
+        for (int st = 0; st < RS / RL; ++st, ++step) {
+            const int rl = st * RL + lane_row;
+            const bool valid = ok && rl < rows;
+            const float4* a4 = reinterpret_cast<const float4*>(sb + (size_t)rl * N);
+            float d = 0.f;
+            if (valid) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const float4 a = a4[ltid + v * TPR];
+                    d = fmaf(a.x, xu[v].x, d);
+                    d = fmaf(a.y, xu[v].y, d);
+                    d = fmaf(a.z, xu[v].z, d);
+                    d = fmaf(a.w, xu[v].w, d);
+                }
+            }
+            d = warp_sum(d);
+            float* rb = red + (step & 1) * RL * WPR;
+            if ((tid & 31) == 0) rb[lane_row * WPR + warp_in_row] = d;
+            named_barrier(1, PROD_CONS);
+            if (valid) {
+                float dot = 0.f;
+#pragma unroll
+                for (int w = 0; w < WPR; ++w) dot += rb[lane_row * WPR + w];
+                const int gi = i0 + s * RS + rl;
+                const float ri = y ? dot - y[gi] : dot;
+                if (ltid == 0) {
+                    r[gi] = ri;
+                    r2 += (double)ri * (double)ri;
+                }
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const float4 a = a4[ltid + v * TPR];
+                    acc[v].x = fmaf(ri, a.x, acc[v].x);
+                    acc[v].y = fmaf(ri, a.y, acc[v].y);
+                    acc[v].z = fmaf(ri, a.z, acc[v].z);
+                    acc[v].w = fmaf(ri, a.w, acc[v].w);
+                }
+            }
+        }
+        __syncwarp();
+        if ((tid & 31) == 0) mbar_arrive(&empty[slot]);
+    }
+
+    // ---------------- epilogue: partial A^T r and ||r||^2 ----------------
+    named_barrier(1, PROD_CONS);   // every consumer is done with the stage ring
+    float4* out4 = reinterpret_cast<float4*>(gpart + (size_t)blockIdx.x * N);
+    if constexpr (RL == 1) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) out4[ltid + v * TPR] = acc[v];
+    } else {
+        float4* scr = reinterpret_cast<float4*>(stage);   // (RL-1) x N/4 float4
+        if (lane_row > 0) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) scr[(lane_row - 1) * (N / 4) + ltid + v * TPR] = acc[v];
+        }
+        named_barrier(1, PROD_CONS);
+        if (lane_row == 0) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                float4 t = acc[v];
+                for (int l = 1; l < RL; ++l) {
+                    const float4 o = scr[(l - 1) * (N / 4) + ltid + v * TPR];
+                    t.x += o.x; t.y += o.y; t.z += o.z; t.w += o.w;
+                }
+                out4[ltid + v * TPR] = t;
+            }
+        }
+    }
+    // binary64 ||r||^2: one value per row lane (held by ltid == 0)
+    if (ltid == 0) dred[lane_row] = r2;
+    named_barrier(1, PROD_CONS);
+    if (tid == 0) {
+        double s = 0.0;
+        for (int l = 0; l < RL; ++l) s += dred[l];
+        r2part[blockIdx.x] = s;
+        if (last_block_arrive(&ctrl->ticket_prod)) {
+            double t = 0.0;
+            for (int b = 0; b < G; ++b) t += r2part[b];
+            ctrl->r2 = t;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Shape table: n -> (V, RL, RS).  N = n^2 = 4 * (512/RL) * V.
+// ---------------------------------------------------------------------------
+template <int V, int RL, int RS>
+static void launch_prod_t(int grid, const ProdArgs& a, cudaStream_t s)
+{
+    using S = ProdShape<V, RL, RS>;
+    k_products<V, RL, RS><<<grid, PROD_THREADS, S::SMEM, s>>>(
+        a.A, a.m, a.x, a.y, a.r, a.gpart, a.r2part, a.ctrl, a.mode,
+        (cudaGraphConditionalHandle)a.cond, a.set_cond, a.budget);
+}
+
+template <int V, int RL, int RS>
+static cudaError_t configure_t()
+{
+    using S = ProdShape<V, RL, RS>;
+    return cudaFuncSetAttribute(k_products<V, RL, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)S::SMEM);
+}
+
+#define TVCS_PROD_TABLE(X)   \
+    X(16, 1, 8, 64)          \
+    X(32, 2, 4, 16)          \
+    X(48, 9, 8, 8)           \
+    X(64, 4, 2, 4)           \
+    X(96, 9, 2, 2)           \
+    X(128, 8, 1, 1)
+
+bool prod_supported(int n)
+{
+    switch (n) {
+#define X(NN, V, RL, RS) case NN: return true;
+        TVCS_PROD_TABLE(X)
+#undef X
+        default: return false;
+    }
+}
+
+static int prod_rl(int n)
+{
+    switch (n) {
+#define X(NN, V, RL, RS) case NN: return RL;
+        TVCS_PROD_TABLE(X)
+#undef X
+        default: return 1;
+    }
+}
+
+int prod_grid(int n, int m, int num_sms)
+{
+    const int rl = prod_rl(n);
+    int g = (m + rl - 1) / rl;
+    return g < num_sms ? g : num_sms;
+}
+
+cudaError_t prod_configure(int n)
+{
+    switch (n) {
+#define X(NN, V, RL, RS) case NN: return configure_t<V, RL, RS>();
+        TVCS_PROD_TABLE(X)
+#undef X
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+void launch_products(int n, int grid, const ProdArgs& a, cudaStream_t s)
+{
+    switch (n) {
+#define X(NN, V, RL, RS) case NN: launch_prod_t<V, RL, RS>(grid, a, s); break;
+        TVCS_PROD_TABLE(X)
+#undef X
+        default: break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Gather of the partials, normalisation, fill.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_gather(const float* __restrict__ gpart, int P, int N,
+                                                float scale, float* __restrict__ out,
+                                                double* __restrict__ part, Ctrl* __restrict__ ctrl)
+{
+    __shared__ double red[32];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double sq = 0.0;
+    if (i < N) {
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        int p = 0;
+        for (; p + 4 <= P; p += 4) {
+            s0 += gpart[(size_t)p * N + i];
+            s1 += gpart[(size_t)(p + 1) * N + i];
+            s2 += gpart[(size_t)(p + 2) * N + i];
+            s3 += gpart[(size_t)(p + 3) * N + i];
+        }
+        for (; p < P; ++p) s0 += gpart[(size_t)p * N + i];
+        const float v = scale * ((s0 + s1) + (s2 + s3));
+        out[i] = v;
+        sq = (double)v * (double)v;
+    }
+    const double s = block_sum(sq, red);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = s;
+        if (last_block_arrive(&ctrl->ticket_gather)) {
+            double t = 0.0;
+            for (unsigned b = 0; b < gridDim.x; ++b) t += part[b];
+            ctrl->vec2 = t;
+        }
+    }
+}
+
+__global__ void k_normalize(const float* __restrict__ z, float* __restrict__ v, int N,
+                            const Ctrl* __restrict__ ctrl)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const double nrm = sqrt(ctrl->vec2);
+    if (i < N) v[i] = (float)((double)z[i] / nrm);
+}
+
+__global__ void k_fill(float* __restrict__ v, int N, float value)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) v[i] = value;
+}
+
+void launch_gather(const float* gpart, int P, int N, float scale, float* out, double* part,
+                   Ctrl* ctrl, cudaStream_t s)
+{
+    k_gather<<<(N + 255) / 256, 256, 0, s>>>(gpart, P, N, scale, out, part, ctrl);
+}
+
+void launch_normalize(const float* z, float* v, int N, const Ctrl* ctrl, cudaStream_t s)
+{
+    k_normalize<<<(N + 255) / 256, 256, 0, s>>>(z, v, N, ctrl);
+}
+
+void launch_fill(float* v, int N, float value, cudaStream_t s)
+{
+    k_fill<<<(N + 255) / 256, 256, 0, s>>>(v, N, value);
+}
+
+}  // namespace tvcs

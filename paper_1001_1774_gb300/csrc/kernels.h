@@ -1,0 +1,64 @@
+// Host-side launchers of the solver kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tvcs {
+
+struct Ctrl;
+
+// Arguments of the TV / FFT kernels (rows a1-a5) and the end-of-run kernels.
+struct TvArgs {
+    float* u;
+    float* w;           // 2 copies x 2 planes x N
+    float* lam;         // 2 copies x 2 planes x N
+    const float* gpart; // P x N partial sums of A^T r
+    int P;
+    float* g_out;       // nullable (w-step) / required (final kernels)
+    float* rhs_out;     // nullable
+    float2* spec;       // n x (n/2+1)
+    const float2* tw;   // n twiddles (cos, sin)(2 pi t / n)
+    const float* s2;    // n values 4 sin^2(pi k / n)
+    double* part;       // per-block binary64 partials (>= 2 * max blocks)
+    float beta, mu_over_tau, mu;
+    Ctrl* ctrl;
+    int mode;
+};
+
+bool tv_supported(int n);
+// which: 1 w-step + row FFT, 2 column pass, 3 inverse rows, 4 final1, 5 final2
+void launch_tv(int n, const TvArgs& a, int which, cudaStream_t s);
+
+// Fused single-pass products r = A x - y, gpart = per-block partials of A^T r.
+struct ProdArgs {
+    const float* A;
+    int m;
+    const float* x;
+    const float* y;     // nullable
+    float* r;
+    float* gpart;       // grid x N
+    double* r2part;     // grid
+    Ctrl* ctrl;
+    int mode;           // MODE_PLAIN or MODE_ITER
+    unsigned long long cond;  // cudaGraphConditionalHandle (MODE_ITER inside the loop graph)
+    int set_cond;
+    long long budget;   // spin-wait bound, SM cycles
+};
+
+bool prod_supported(int n);
+int prod_grid(int n, int m, int num_sms);   // number of blocks = number of partials P
+cudaError_t prod_configure(int n);          // opt-in shared memory size (call once per device)
+void launch_products(int n, int grid, const ProdArgs& a, cudaStream_t s);
+
+// gather: out = scale * sum_p gpart[p], ctrl->vec2 = ||out||^2 (binary64)
+void launch_gather(const float* gpart, int P, int N, float scale, float* out, double* part,
+                   Ctrl* ctrl, cudaStream_t s);
+// v = z / sqrt(ctrl->vec2)
+void launch_normalize(const float* z, float* v, int N, const Ctrl* ctrl, cudaStream_t s);
+void launch_fill(float* v, int N, float value, cudaStream_t s);
+
+// Gaussian encoding matrix rows from the counter-based generator.
+void launch_gen_gauss(float* A, int m, int64_t N, uint64_t seed, float scale, cudaStream_t s);
+
+}  // namespace tvcs

@@ -1,0 +1,679 @@
+// C ABI of the solver (declared in include/tvcs.h): handle lifetime, the
+// iteration loop as a CUDA graph with a device-driven WHILE node, state access
+// and the products entry point.  All arithmetic happens in the kernels.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <new>
+#include <set>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tvcs.h"
+
+using namespace tvcs;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+tvcs_status fail(tvcs_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            return fail(e_ == cudaErrorMemoryAllocation ? TVCS_ERR_OOM : TVCS_ERR_CUDA,       \
+                        "%s failed: %s", #call, cudaGetErrorString(e_));                      \
+        }                                                                                     \
+    } while (0)
+
+#define CKS(expr)                                  \
+    do {                                           \
+        tvcs_status s_ = (expr);                   \
+        if (s_ != TVCS_OK) return s_;              \
+    } while (0)
+
+std::mutex g_cfg_mutex;
+std::set<std::pair<int, int>> g_configured;  // (device, n) with the product kernel configured
+
+}  // namespace
+
+struct tvcs_ctx {
+    int dev = 0, num_sms = 0;
+    int m = 0, n = 0, N = 0, P = 0;
+    double mu = 0, beta = 0, tol = 0, tau = 0;
+    tvcs_options opt{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t cap_stream = nullptr;
+    // device buffers
+    float* A = nullptr;
+    float *f = nullptr, *u = nullptr, *w = nullptr, *lam = nullptr, *g = nullptr, *r = nullptr,
+          *rhs = nullptr, *zeroN = nullptr;
+    float *tx = nullptr, *ty = nullptr, *tr = nullptr, *tg = nullptr;
+    float2* spec = nullptr;
+    float2* tw = nullptr;
+    float* s2 = nullptr;
+    float *gpart = nullptr, *gpart2 = nullptr;
+    double *r2part = nullptr, *part = nullptr;
+    Ctrl* ctrl = nullptr;
+    Ctrl* hctrl = nullptr;  // pinned host mirror
+    // loop graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool state_ready = false;
+};
+
+namespace {
+
+long long budget_of(const tvcs_ctx* h)
+{
+    return h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : (1LL << 31);
+}
+
+TvArgs tv_args(tvcs_ctx* h, int mode, bool stage_outputs)
+{
+    TvArgs a{};
+    a.u = h->u;
+    a.w = h->w;
+    a.lam = h->lam;
+    a.gpart = h->gpart;
+    a.P = h->P;
+    a.g_out = stage_outputs ? h->g : nullptr;
+    a.rhs_out = stage_outputs ? h->rhs : nullptr;
+    a.spec = h->spec;
+    a.tw = h->tw;
+    a.s2 = h->s2;
+    a.part = h->part;
+    a.beta = (float)h->beta;
+    a.mu_over_tau = (float)(h->mu / h->tau);
+    a.mu = (float)h->mu;
+    a.ctrl = h->ctrl;
+    a.mode = mode;
+    return a;
+}
+
+void products(tvcs_ctx* h, const float* x, const float* y, float* r, float* gpart, int mode,
+              unsigned long long cond, int set_cond, cudaStream_t s)
+{
+    ProdArgs a{};
+    a.A = h->A;
+    a.m = h->m;
+    a.x = x;
+    a.y = y;
+    a.r = r;
+    a.gpart = gpart;
+    a.r2part = h->r2part;
+    a.ctrl = h->ctrl;
+    a.mode = mode;
+    a.cond = cond;
+    a.set_cond = set_cond;
+    a.budget = budget_of(h);
+    launch_products(h->n, h->P, a, s);
+}
+
+tvcs_status sync_and_check(tvcs_ctx* h, const char* what)
+{
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail(TVCS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(TVCS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return TVCS_OK;
+}
+
+tvcs_status read_ctrl(tvcs_ctx* h)
+{
+    CK(cudaMemcpyAsync(h->hctrl, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+    return sync_and_check(h, "reading the control block");
+}
+
+// Writes selected control fields from the host (the rest are preserved).
+tvcs_status write_ctrl(tvcs_ctx* h)
+{
+    CK(cudaMemcpyAsync(h->ctrl, h->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
+    return TVCS_OK;
+}
+
+void free_ctx(tvcs_ctx* h)
+{
+    if (!h) return;
+    cudaSetDevice(h->dev);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    void* bufs[] = {h->A, h->f, h->u, h->w, h->lam, h->g, h->r, h->rhs, h->zeroN, h->tx, h->ty,
+                    h->tr, h->tg, h->spec, h->tw, h->s2, h->gpart, h->gpart2, h->r2part, h->part,
+                    h->ctrl};
+    for (void* p : bufs)
+        if (p) cudaFree(p);
+    if (h->hctrl) cudaFreeHost(h->hctrl);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+tvcs_status alloc(void** p, size_t bytes)
+{
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(TVCS_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", bytes,
+                    cudaGetErrorString(e));
+    }
+    return TVCS_OK;
+}
+
+// Runs the iteration body in a loop graph: K1 -> column pass -> inverse rows ->
+// products; the products kernel sets the WHILE condition from ctrl->done.
+tvcs_status build_graph(tvcs_ctx* h)
+{
+    if (h->exec) return TVCS_OK;
+    CK(cudaGraphCreate(&h->graph, 0));
+    cudaGraphConditionalHandle ch;
+    CK(cudaGraphConditionalHandleCreate(&ch, h->graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = ch;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, h->graph, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeThreadLocal));
+    TvArgs a = tv_args(h, MODE_ITER, false);
+    launch_tv(h->n, a, 1, h->cap_stream);
+    launch_tv(h->n, a, 2, h->cap_stream);
+    launch_tv(h->n, a, 3, h->cap_stream);
+    products(h, h->u, h->f, h->r, h->gpart, MODE_ITER, (unsigned long long)ch, 1, h->cap_stream);
+    cudaGraph_t captured = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &captured);
+    if (e != cudaSuccess) return fail(TVCS_ERR_CUDA, "capture of the loop body: %s", cudaGetErrorString(e));
+    CK(cudaGraphInstantiate(&h->exec, h->graph, 0));
+    return TVCS_OK;
+}
+
+// (Re)computes r = A u - f and the partials of g = A^T r for the current u.
+void refresh_products(tvcs_ctx* h)
+{
+    products(h, h->u, h->f, h->r, h->gpart, MODE_PLAIN, 0ull, 0, h->stream);
+}
+
+tvcs_status init_state(tvcs_ctx* h, int init)
+{
+    const size_t N = (size_t)h->N;
+    if (init == TVCS_INIT_GIVEN) {
+        // Warm start: keep the caller's u and lambda (tvcs_set_state), w^0 = 0.
+        if (!h->state_ready) return fail(TVCS_ERR_INVALID_ARG, "INIT_GIVEN needs tvcs_set_state(U) first");
+        refresh_products(h);
+        CKS(read_ctrl(h));   // after the kernels: the host copy is current
+        const int par = h->hctrl->wpar;
+        CK(cudaMemsetAsync(h->w + (size_t)par * 2 * N, 0, sizeof(float) * 2 * N, h->stream));
+        h->hctrl->pending = 0;
+        h->hctrl->error = 0;
+        return write_ctrl(h);
+    }
+    CK(cudaMemsetAsync(h->w, 0, sizeof(float) * 4 * N, h->stream));
+    CK(cudaMemsetAsync(h->lam, 0, sizeof(float) * 4 * N, h->stream));
+    if (init == TVCS_INIT_ATF) {
+        // u^0 = A^T f (reading C3): the products at x = 0 give A^T (0 - f).
+        products(h, h->zeroN, h->f, h->r, h->gpart, MODE_PLAIN, 0ull, 0, h->stream);
+        launch_gather(h->gpart, h->P, h->N, -1.0f, h->u, h->part, h->ctrl, h->stream);
+    } else if (init == TVCS_INIT_ZERO) {
+        CK(cudaMemsetAsync(h->u, 0, sizeof(float) * N, h->stream));
+    }
+    refresh_products(h);
+    CKS(read_ctrl(h));
+    h->hctrl->pending = 0;
+    h->hctrl->wpar = 0;
+    h->hctrl->error = 0;
+    CKS(write_ctrl(h));
+    h->state_ready = true;
+    return TVCS_OK;
+}
+
+// Runs up to `iters` iterations from the current state; tol > 0 enables eq. (stop).
+tvcs_status run_loop(tvcs_ctx* h, int iters, double tol, tvcs_result* res)
+{
+    CKS(build_graph(h));
+    CKS(read_ctrl(h));
+    Ctrl& c = *h->hctrl;
+    c.it = 0;
+    c.max_iter = iters;
+    c.done = 0;
+    c.skip = 0;
+    c.stop_by_tol = 0;
+    c.loops = 0;
+    c.loops_max = iters + 2;
+    c.tol = tol;
+    c.error = 0;
+    c.algo = h->opt.algo;
+    c.ticket_fft = c.ticket_prod = c.ticket_fin = c.ticket_w = c.ticket_gather = 0;
+    CKS(write_ctrl(h));
+    CK(cudaEventRecord(h->ev0, h->stream));
+    if (iters > 0) CK(cudaGraphLaunch(h->exec, h->stream));
+    CK(cudaEventRecord(h->ev1, h->stream));
+    // End of run: final multiplier update, g, objective and optimality residuals.
+    TvArgs a = tv_args(h, MODE_PLAIN, false);
+    a.g_out = h->g;
+    launch_tv(h->n, a, 4, h->stream);
+    launch_tv(h->n, a, 5, h->stream);
+    CKS(read_ctrl(h));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    tvcs_status st = TVCS_OK;
+    if (c.error == ERR_TIMEOUT)
+        st = fail(TVCS_ERR_TIMEOUT, "a bounded device wait gave up");
+    else if (c.error == ERR_NONFINITE || !isfinite(c.tv) || !isfinite(c.r2))
+        st = fail(TVCS_ERR_DIVERGED, "non-finite iterate");
+    else if (tol > 0.0 && !c.stop_by_tol)
+        st = TVCS_NOT_CONVERGED;
+    if (res) {
+        res->iters = c.it;
+        res->status = st;
+        res->stopped_by_tol = c.stop_by_tol;
+        res->rel_change = c.relchg;
+        res->tv = c.tv;
+        res->resid2 = c.r2;
+        res->objective = c.tv + 0.5 * h->mu * c.r2;
+        res->kkt_primal = sqrt(c.kkt_p2);
+        res->kkt_dual = sqrt(c.kkt_d2);
+        res->lambda_max_norm = c.lam_max;
+        res->ms = ms;
+    }
+    return st;
+}
+
+tvcs_status power_tau(tvcs_ctx* h, int iters, double* tau_out)
+{
+    const int N = h->N;
+    launch_fill(h->tx, N, (float)(1.0 / sqrt((double)N)), h->stream);
+    for (int it = 0; it < iters; ++it) {
+        products(h, h->tx, nullptr, h->tr, h->gpart2, MODE_PLAIN, 0ull, 0, h->stream);
+        launch_gather(h->gpart2, h->P, N, 1.0f, h->tg, h->part, h->ctrl, h->stream);
+        launch_normalize(h->tg, h->tx, N, h->ctrl, h->stream);
+    }
+    products(h, h->tx, nullptr, h->tr, h->gpart2, MODE_PLAIN, 0ull, 0, h->stream);
+    CKS(read_ctrl(h));
+    const double lmax = h->hctrl->r2;
+    if (!(lmax > 0.0) || !isfinite(lmax))
+        return fail(TVCS_ERR_DIVERGED, "power iteration gave lambda_max = %g", lmax);
+    *tau_out = 1.0 / (1.01 * lmax);
+    return TVCS_OK;
+}
+
+tvcs_status check_handle(tvcs_handle h)
+{
+    if (!h) return fail(TVCS_ERR_INVALID_ARG, "null handle");
+    cudaError_t e = cudaSetDevice(h->dev);
+    if (e != cudaSuccess) return fail(TVCS_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    return TVCS_OK;
+}
+
+tvcs_status create_impl(tvcs_ctx* h, const float* A, uint64_t seed)
+{
+    CK(cudaGetDevice(&h->dev));
+    CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->dev));
+    {
+        std::lock_guard<std::mutex> lk(g_cfg_mutex);
+        if (!g_configured.count({h->dev, h->n})) {
+            CK(prod_configure(h->n));
+            g_configured.insert({h->dev, h->n});
+        }
+    }
+    if (h->opt.stream) {
+        h->stream = (cudaStream_t)h->opt.stream;
+    } else {
+        CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    CK(cudaEventCreate(&h->ev0));
+    CK(cudaEventCreate(&h->ev1));
+    const size_t m = (size_t)h->m, N = (size_t)h->N;
+    h->P = prod_grid(h->n, h->m, h->num_sms);
+    const size_t nparts = 2 * (size_t)((N + 255) / 256 + 1024);
+    CKS(alloc((void**)&h->A, sizeof(float) * m * N));
+    CKS(alloc((void**)&h->f, sizeof(float) * m));
+    CKS(alloc((void**)&h->r, sizeof(float) * m));
+    CKS(alloc((void**)&h->ty, sizeof(float) * m));
+    CKS(alloc((void**)&h->tr, sizeof(float) * m));
+    CKS(alloc((void**)&h->u, sizeof(float) * N));
+    CKS(alloc((void**)&h->g, sizeof(float) * N));
+    CKS(alloc((void**)&h->rhs, sizeof(float) * N));
+    CKS(alloc((void**)&h->zeroN, sizeof(float) * N));
+    CKS(alloc((void**)&h->tx, sizeof(float) * N));
+    CKS(alloc((void**)&h->tg, sizeof(float) * N));
+    CKS(alloc((void**)&h->w, sizeof(float) * 4 * N));
+    CKS(alloc((void**)&h->lam, sizeof(float) * 4 * N));
+    CKS(alloc((void**)&h->spec, sizeof(float2) * (size_t)h->n * (h->n / 2 + 1)));
+    CKS(alloc((void**)&h->tw, sizeof(float2) * (size_t)h->n));
+    CKS(alloc((void**)&h->s2, sizeof(float) * (size_t)h->n));
+    CKS(alloc((void**)&h->gpart, sizeof(float) * N * (size_t)h->P));
+    CKS(alloc((void**)&h->gpart2, sizeof(float) * N * (size_t)h->P));
+    CKS(alloc((void**)&h->r2part, sizeof(double) * (size_t)h->P));
+    CKS(alloc((void**)&h->part, sizeof(double) * nparts));
+    CKS(alloc((void**)&h->ctrl, sizeof(Ctrl)));
+    CK(cudaMallocHost((void**)&h->hctrl, sizeof(Ctrl)));
+    memset(h->hctrl, 0, sizeof(Ctrl));
+    h->hctrl->algo = h->opt.algo;
+    CK(cudaMemcpyAsync(h->ctrl, h->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemsetAsync(h->zeroN, 0, sizeof(float) * N, h->stream));
+    CK(cudaMemsetAsync(h->u, 0, sizeof(float) * N, h->stream));
+    CK(cudaMemsetAsync(h->f, 0, sizeof(float) * m, h->stream));
+
+    // Twiddles (cos, sin)(2 pi t/n) and 4 sin^2(pi k/n) (eigenvalues of the 1D
+    // periodic difference operator, Sec. 2.1), in binary64 then rounded.
+    std::vector<float2> tw(h->n);
+    std::vector<float> s2(h->n);
+    const double pi = 3.14159265358979323846;
+    for (int t = 0; t < h->n; ++t) {
+        tw[t] = make_float2((float)cos(2.0 * pi * t / h->n), (float)sin(2.0 * pi * t / h->n));
+        const double sv = sin(pi * t / h->n);
+        s2[t] = (float)(4.0 * sv * sv);
+    }
+    CK(cudaMemcpyAsync(h->tw, tw.data(), sizeof(float2) * h->n, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->s2, s2.data(), sizeof(float) * h->n, cudaMemcpyHostToDevice, h->stream));
+
+    if (A) {
+        CK(cudaMemcpyAsync(h->A, A, sizeof(float) * m * N, cudaMemcpyDefault, h->stream));
+    } else {
+        const float scale = (float)(1.0 / sqrt((double)h->m));
+        launch_gen_gauss(h->A, h->m, (int64_t)N, seed, scale, h->stream);
+    }
+    CKS(sync_and_check(h, "uploading A"));
+    if (h->opt.tau > 0.0) {
+        h->tau = h->opt.tau;
+    } else {
+        CKS(power_tau(h, h->opt.power_iters > 0 ? h->opt.power_iters : 100, &h->tau));
+    }
+    return sync_and_check(h, "tvcs_create");
+}
+
+tvcs_status copy_in(tvcs_ctx* h, float* dst, const float* src, size_t count)
+{
+    CK(cudaMemcpyAsync(dst, src, sizeof(float) * count, cudaMemcpyDefault, h->stream));
+    return TVCS_OK;
+}
+
+tvcs_status copy_out(tvcs_ctx* h, float* dst, const float* src, size_t count)
+{
+    CK(cudaMemcpyAsync(dst, src, sizeof(float) * count, cudaMemcpyDefault, h->stream));
+    return TVCS_OK;
+}
+
+bool valid_n(int n)
+{
+    return tv_supported(n) && prod_supported(n);
+}
+
+}  // namespace
+
+extern "C" {
+
+void tvcs_default_options(tvcs_options* opt)
+{
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->algo = TVCS_ALGO_IADM;
+    opt->tau = 0.0;
+    opt->max_iter = 500;
+    opt->precision = TVCS_PREC_FP32;
+    opt->init = TVCS_INIT_ATF;
+    opt->stream = nullptr;
+    opt->power_iters = 100;
+    opt->timeout_cycles = 0;
+}
+
+const char* tvcs_last_error(void)
+{
+    return g_last_error.c_str();
+}
+
+tvcs_status tvcs_create(tvcs_handle* out, const float* A, uint64_t seed, int m, int n, double mu,
+                        double beta, double tol, const tvcs_options* opt)
+{
+    if (!out) return fail(TVCS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (m < 1 || m > (1 << 24)) return fail(TVCS_ERR_INVALID_ARG, "m = %d outside [1, 2^24]", m);
+    if (!valid_n(n))
+        return fail(TVCS_ERR_INVALID_ARG, "n = %d not supported (16, 32, 48, 64, 96, 128)", n);
+    if (!(mu > 0.0) || !isfinite(mu)) return fail(TVCS_ERR_INVALID_ARG, "mu must be > 0");
+    if (!(beta > 0.0) || !isfinite(beta)) return fail(TVCS_ERR_INVALID_ARG, "beta must be > 0");
+    if (!(tol >= 0.0) || !isfinite(tol)) return fail(TVCS_ERR_INVALID_ARG, "tol must be >= 0");
+    tvcs_options o;
+    tvcs_default_options(&o);
+    if (opt) o = *opt;
+    if (o.algo != TVCS_ALGO_IADM && o.algo != TVCS_ALGO_FTVCS)
+        return fail(TVCS_ERR_INVALID_ARG, "unknown algo %d", o.algo);
+    if (o.init < TVCS_INIT_ATF || o.init > TVCS_INIT_GIVEN)
+        return fail(TVCS_ERR_INVALID_ARG, "unknown init %d", o.init);
+    if (o.precision != TVCS_PREC_FP32) {
+        if (o.precision == TVCS_PREC_BF16X2 || o.precision == TVCS_PREC_FP8_BF16)
+            return fail(TVCS_ERR_UNSUPPORTED, "precision %d not available for the single-image path", o.precision);
+        return fail(TVCS_ERR_INVALID_ARG, "unknown precision %d", o.precision);
+    }
+    if (!isfinite(o.tau)) return fail(TVCS_ERR_INVALID_ARG, "tau must be finite");
+    if (o.max_iter <= 0) o.max_iter = 500;
+    tvcs_ctx* h = new (std::nothrow) tvcs_ctx();
+    if (!h) return fail(TVCS_ERR_OOM, "host allocation failed");
+    h->m = m;
+    h->n = n;
+    h->N = n * n;
+    h->mu = mu;
+    h->beta = beta;
+    h->tol = tol;
+    h->opt = o;
+    tvcs_status st = create_impl(h, A, seed);
+    if (st != TVCS_OK) {
+        std::string msg = g_last_error;
+        free_ctx(h);
+        g_last_error = msg;
+        return st;
+    }
+    *out = h;
+    return TVCS_OK;
+}
+
+tvcs_status tvcs_destroy(tvcs_handle h)
+{
+    if (!h) return TVCS_OK;
+    free_ctx(h);
+    return TVCS_OK;
+}
+
+tvcs_status tvcs_get_tau(tvcs_handle h, double* tau)
+{
+    CKS(check_handle(h));
+    if (!tau) return fail(TVCS_ERR_INVALID_ARG, "tau is NULL");
+    *tau = h->tau;
+    return TVCS_OK;
+}
+
+tvcs_status tvcs_solve(tvcs_handle h, const float* f, float* u, tvcs_result* res)
+{
+    CKS(check_handle(h));
+    if (!f || !u) return fail(TVCS_ERR_INVALID_ARG, "f and u must be non-NULL");
+    CKS(copy_in(h, h->f, f, (size_t)h->m));
+    CKS(init_state(h, h->opt.init));
+    tvcs_status st = run_loop(h, h->opt.max_iter, h->tol, res);
+    if (st < 0) return st;
+    CKS(copy_out(h, u, h->u, (size_t)h->N));
+    CKS(sync_and_check(h, "tvcs_solve"));
+    return st;
+}
+
+tvcs_status tvcs_solve_batched(const tvcs_handle* hs, int count, const float* const* f,
+                               float* const* u, const double* mu, tvcs_result* res)
+{
+    if (count < 0) return fail(TVCS_ERR_INVALID_ARG, "count < 0");
+    if (count == 0) return TVCS_OK;
+    if (!hs || !f || !u) return fail(TVCS_ERR_INVALID_ARG, "hs, f and u must be non-NULL");
+    for (int i = 0; i < count; ++i) {
+        if (!hs[i] || !f[i] || !u[i]) return fail(TVCS_ERR_INVALID_ARG, "entry %d is NULL", i);
+        if (mu && !(mu[i] > 0.0)) return fail(TVCS_ERR_INVALID_ARG, "mu[%d] must be > 0", i);
+    }
+    tvcs_status worst = TVCS_OK;
+    for (int i = 0; i < count; ++i) {
+        tvcs_ctx* h = hs[i];
+        const double mu0 = h->mu;
+        if (mu && mu[i] != h->mu) {
+            // mu is baked into the loop graph: rebuild it for this problem.
+            h->mu = mu[i];
+            if (h->exec) { cudaGraphExecDestroy(h->exec); h->exec = nullptr; }
+            if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+        }
+        tvcs_status st = tvcs_solve(h, f[i], u[i], res ? &res[i] : nullptr);
+        if (h->mu != mu0) {
+            h->mu = mu0;
+            if (h->exec) { cudaGraphExecDestroy(h->exec); h->exec = nullptr; }
+            if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+        }
+        if (st < 0) return st;
+        if (st > worst) worst = st;
+    }
+    return worst;
+}
+
+tvcs_status tvcs_get_state(tvcs_handle h, int which, float* dst)
+{
+    CKS(check_handle(h));
+    if (!dst) return fail(TVCS_ERR_INVALID_ARG, "dst is NULL");
+    CKS(read_ctrl(h));
+    const size_t N = (size_t)h->N;
+    const int par = h->hctrl->wpar;
+    switch (which) {
+        case TVCS_STATE_U: CKS(copy_out(h, dst, h->u, N)); break;
+        case TVCS_STATE_W: CKS(copy_out(h, dst, h->w + (size_t)par * 2 * N, 2 * N)); break;
+        case TVCS_STATE_LAMBDA: CKS(copy_out(h, dst, h->lam + (size_t)par * 2 * N, 2 * N)); break;
+        case TVCS_STATE_G:
+            launch_gather(h->gpart, h->P, h->N, 1.0f, h->g, h->part, h->ctrl, h->stream);
+            CKS(copy_out(h, dst, h->g, N));
+            break;
+        case TVCS_STATE_R: CKS(copy_out(h, dst, h->r, (size_t)h->m)); break;
+        case TVCS_STATE_RHS: CKS(copy_out(h, dst, h->rhs, N)); break;
+        case TVCS_STATE_F: CKS(copy_out(h, dst, h->f, (size_t)h->m)); break;
+        default: return fail(TVCS_ERR_INVALID_ARG, "unknown state %d", which);
+    }
+    return sync_and_check(h, "tvcs_get_state");
+}
+
+tvcs_status tvcs_set_state(tvcs_handle h, int which, const float* src)
+{
+    CKS(check_handle(h));
+    if (!src) return fail(TVCS_ERR_INVALID_ARG, "src is NULL");
+    const size_t N = (size_t)h->N;
+    if (which == TVCS_STATE_U || which == TVCS_STATE_F) {
+        if (!h->state_ready) {
+            CK(cudaMemsetAsync(h->w, 0, sizeof(float) * 4 * N, h->stream));
+            CK(cudaMemsetAsync(h->lam, 0, sizeof(float) * 4 * N, h->stream));
+            h->state_ready = true;
+        }
+        CKS(copy_in(h, which == TVCS_STATE_U ? h->u : h->f, src, which == TVCS_STATE_U ? N : (size_t)h->m));
+        refresh_products(h);
+        return sync_and_check(h, "tvcs_set_state");
+    }
+    if (which == TVCS_STATE_LAMBDA) {
+        CKS(read_ctrl(h));
+        CKS(copy_in(h, h->lam + (size_t)h->hctrl->wpar * 2 * N, src, 2 * N));
+        h->hctrl->pending = 0;
+        CKS(write_ctrl(h));
+        return sync_and_check(h, "tvcs_set_state");
+    }
+    return fail(TVCS_ERR_INVALID_ARG, "state %d cannot be set", which);
+}
+
+tvcs_status tvcs_iterate(tvcs_handle h, int iters, tvcs_result* res)
+{
+    CKS(check_handle(h));
+    if (iters < 0) return fail(TVCS_ERR_INVALID_ARG, "iters < 0");
+    if (!h->state_ready) return fail(TVCS_ERR_INVALID_ARG, "no state: call tvcs_set_state or tvcs_solve first");
+    tvcs_status st = run_loop(h, iters, 0.0, res);
+    if (st < 0) return st;
+    return sync_and_check(h, "tvcs_iterate");
+}
+
+tvcs_status tvcs_run_stage(tvcs_handle h, int stage)
+{
+    CKS(check_handle(h));
+    if (!h->state_ready) return fail(TVCS_ERR_INVALID_ARG, "no state: call tvcs_set_state or tvcs_solve first");
+    TvArgs a = tv_args(h, MODE_PLAIN, true);
+    switch (stage) {
+        case 1: launch_tv(h->n, a, 1, h->stream); break;
+        case 2:
+            launch_tv(h->n, a, 2, h->stream);
+            launch_tv(h->n, a, 3, h->stream);
+            break;
+        case 3:
+            refresh_products(h);
+            if (h->opt.algo == TVCS_ALGO_IADM) {
+                CKS(read_ctrl(h));
+                h->hctrl->pending = 1;
+                CKS(write_ctrl(h));
+            }
+            break;
+        default: return fail(TVCS_ERR_INVALID_ARG, "unknown stage %d", stage);
+    }
+    return sync_and_check(h, "tvcs_run_stage");
+}
+
+tvcs_status tvcs_time_stage(tvcs_handle h, int stage, int reps, double* ms)
+{
+    CKS(check_handle(h));
+    if (!ms || reps < 1) return fail(TVCS_ERR_INVALID_ARG, "ms must be non-NULL and reps >= 1");
+    if (stage < 1 || stage > 3) return fail(TVCS_ERR_INVALID_ARG, "unknown stage %d", stage);
+    if (!h->state_ready) return fail(TVCS_ERR_INVALID_ARG, "no state: call tvcs_set_state or tvcs_solve first");
+    TvArgs a = tv_args(h, MODE_PLAIN, false);
+    CK(cudaEventRecord(h->ev0, h->stream));
+    for (int i = 0; i < reps; ++i) {
+        if (stage == 1) {
+            launch_tv(h->n, a, 1, h->stream);
+        } else if (stage == 2) {
+            launch_tv(h->n, a, 2, h->stream);
+            launch_tv(h->n, a, 3, h->stream);
+        } else {
+            refresh_products(h);
+        }
+    }
+    CK(cudaEventRecord(h->ev1, h->stream));
+    CKS(sync_and_check(h, "tvcs_time_stage"));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, h->ev0, h->ev1));
+    *ms = t;
+    return TVCS_OK;
+}
+
+tvcs_status tvcs_apply(tvcs_handle h, const float* x, const float* y, float* r, float* g)
+{
+    CKS(check_handle(h));
+    if (!x || !r || !g) return fail(TVCS_ERR_INVALID_ARG, "x, r and g must be non-NULL");
+    CKS(copy_in(h, h->tx, x, (size_t)h->N));
+    if (y) CKS(copy_in(h, h->ty, y, (size_t)h->m));
+    products(h, h->tx, y ? h->ty : nullptr, h->tr, h->gpart2, MODE_PLAIN, 0ull, 0, h->stream);
+    launch_gather(h->gpart2, h->P, h->N, 1.0f, h->tg, h->part, h->ctrl, h->stream);
+    CKS(copy_out(h, r, h->tr, (size_t)h->m));
+    CKS(copy_out(h, g, h->tg, (size_t)h->N));
+    return sync_and_check(h, "tvcs_apply");
+}
+
+}  // extern "C"

@@ -1,0 +1,318 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (binary32 iterates, binary64 oracle):
+  * products r = A x - y, g = A^T r: per entry |err| <= 1e-5 * (|A| |x|)_i (and
+    the same for g with |A|^T |r|) -- a binary32 dot of N <= 16384 terms summed
+    by fixed-order partials carries at most ~log2(N) * 2^-24 relative to the
+    absolute sum, ~1e-6, with margin;
+  * one iteration: 1e-5 relative (norm-wise) on u, w, lambda;
+  * fixed 50 iterations: <= 1e-5 relative image error (the required bar);
+  * convergence runs: <= 1e-4 relative image error, <= 1e-6 relative objective gap.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tv(cuda_device):
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1001_1774_gb300 as tv
+    return tv
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def make_handle(tv, P, tau, algo=0, init=0, max_iter=500, on_device=True, tol=0.0, seed_only=False):
+    opt = tv.tvcs_default_options()
+    opt.tau = tau
+    opt.algo = algo
+    opt.init = init
+    opt.max_iter = max_iter
+    if seed_only:
+        return tv.tvcs_create(None, P.seed, P.m, P.n, P.mu, P.beta, tol, opt)
+    A = torch.from_numpy(P.A).cuda() if on_device else P.A
+    return tv.tvcs_create(A, 0, P.m, P.n, P.mu, P.beta, tol, opt)
+
+
+def small_problem(n, m, seed=3, mu=1e3, beta=10.0):
+    return synth.make_problem(n, 0.0, seed, 4, mu, beta, m=m, noise_c=1e-3)
+
+
+# ----------------------------------------------------------------------------- generator (a9 recipe)
+
+@pytest.mark.parametrize("n,m,seed", [(32, 307, 0), (128, 4915, 1)])
+def test_device_generator_bit_exact(tv, n, m, seed):
+    N = n * n
+    opt = tv.tvcs_default_options()
+    opt.tau = 0.1
+    h = tv.tvcs_create(None, seed, m, n, 1.0, 1.0, 0.0, opt)
+    rng = np.random.default_rng(0)
+    r = np.empty(m, np.float32)
+    g = np.empty(N, np.float32)
+    for j in [0, 1, 2, 3, N - 1] + list(rng.integers(0, N, 3)):
+        x = np.zeros(N, np.float32)
+        x[j] = 1.0
+        tv.tvcs_apply(h, x, None, r, g)         # r = A e_j = column j, exactly
+        col = np.array([synth.gaussian_matrix(seed, m, N, row0=i, nrows=1)[0, j]
+                        for i in range(0, m, max(1, m // 64))], np.float32)
+        assert np.array_equal(r[::max(1, m // 64)], col)
+    for i in [0, m - 1, int(rng.integers(0, m))]:
+        y = np.zeros(m, np.float32)
+        y[i] = -1.0
+        tv.tvcs_apply(h, np.zeros(N, np.float32), y, r, g)   # g = A^T e_i = row i, exactly
+        assert np.array_equal(g, synth.gaussian_matrix(seed, m, N, row0=i, nrows=1)[0])
+    tv.tvcs_destroy(h)
+
+
+# ----------------------------------------------------------------------------- rows a6, a7
+
+@pytest.mark.parametrize("n,m", [(16, 1), (16, 77), (32, 307), (48, 500), (64, 1229),
+                                 (96, 2764), (128, 4915), (128, 151), (128, 153)])
+def test_products_parity(tv, n, m):
+    N = n * n
+    A = synth.gaussian_matrix(11 + n, m, N)
+    rng = np.random.default_rng(n + m)
+    x = rng.standard_normal(N).astype(np.float32)
+    y = rng.standard_normal(m).astype(np.float32)
+    opt = tv.tvcs_default_options()
+    opt.tau = 0.1
+    h = tv.tvcs_create(torch.from_numpy(A).cuda(), 0, m, n, 1.0, 1.0, 0.0, opt)
+    r = torch.empty(m, dtype=torch.float32, device="cuda")
+    g = torch.empty(N, dtype=torch.float32, device="cuda")
+    tv.tvcs_apply(h, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), r, g)
+    r = r.cpu().numpy().astype(np.float64)
+    g = g.cpu().numpy().astype(np.float64)
+    rr = oracle.Au(A, x, y)
+    scale_r = np.abs(A.astype(np.float64)) @ np.abs(x.astype(np.float64))
+    assert np.all(np.abs(r - rr) <= 1e-5 * scale_r + 1e-30)
+    # g is compared with the oracle's A^T applied to the GPU's own r (the input of that product)
+    gr = oracle.At(A, r)
+    scale_g = np.abs(A.astype(np.float64)).T @ np.abs(r)
+    assert np.all(np.abs(g - gr) <= 1e-5 * scale_g + 1e-30)
+    tv.tvcs_destroy(h)
+
+
+# ----------------------------------------------------------------------------- rows a1-a3, a4-a5
+
+@pytest.mark.parametrize("n,m", [(32, 307), (96, 2764), (128, 4915)])
+def test_stage_parity(tv, n, m):
+    P = small_problem(n, m)
+    N = P.N
+    tau = 0.11
+    rng = np.random.default_rng(5)
+    u0 = (P.ubar + 0.1 * rng.standard_normal((n, n))).astype(np.float32)
+    lam0 = (0.3 * rng.standard_normal((2, n, n))).astype(np.float32)
+    h = make_handle(tv, P, tau)
+    tv.tvcs_set_state(h, tv.TVCS_STATE_F, P.f)
+    tv.tvcs_set_state(h, tv.TVCS_STATE_U, u0.ravel())
+    tv.tvcs_set_state(h, tv.TVCS_STATE_LAMBDA, lam0.ravel())
+    # stage 1: w-step and right-hand side
+    tv.tvcs_run_stage(h, 1)
+    w = tv.get_state(h, tv.TVCS_STATE_W).reshape(2, n, n)
+    lam = tv.get_state(h, tv.TVCS_STATE_LAMBDA).reshape(2, n, n)
+    rhs = tv.get_state(h, tv.TVCS_STATE_RHS).reshape(n, n)
+    u64 = u0.astype(np.float64)
+    d1, d2 = oracle.D(u64)
+    z1 = d1 + lam0[0] / P.beta
+    z2 = d2 + lam0[1] / P.beta
+    w1, w2 = oracle.shrink(z1, z2, 1.0 / P.beta)
+    w_ref = np.stack([w1.reshape(n, n), w2.reshape(n, n)])
+    assert np.array_equal(lam, lam0)
+    assert rel(w, w_ref) <= 1e-5
+    g = oracle.At(P.A, oracle.Au(P.A, u64, P.f))
+    y = P.beta * w_ref - lam0
+    rhs_ref = oracle.Dt(y[0], y[1]) + (P.mu / tau) * u64 - P.mu * g.reshape(n, n)
+    assert rel(rhs, rhs_ref) <= 1e-5
+    # stage 2: FFT u-solve of (beta D^T D + mu/tau I) u = rhs, i.e. eq. (eqnorm11) times beta
+    tv.tvcs_run_stage(h, 2)
+    u1 = tv.get_state(h, tv.TVCS_STATE_U).reshape(n, n)
+    u_ref = oracle.usolve(rhs.astype(np.float64) / P.beta, P.mu / (P.beta * tau))
+    assert rel(u1, u_ref) <= 1e-5
+    # stage 3 then stage 1 again applies the deferred multiplier update (eq. (udlamb))
+    tv.tvcs_run_stage(h, 3)
+    tv.tvcs_run_stage(h, 1)
+    lam2 = tv.get_state(h, tv.TVCS_STATE_LAMBDA).reshape(2, n, n)
+    e1, e2 = oracle.D(u1.astype(np.float64))
+    lam_ref = lam0 - P.beta * (w.astype(np.float64) - np.stack([e1, e2]))
+    assert rel(lam2, lam_ref) <= 1e-5
+    tv.tvcs_destroy(h)
+
+
+# ----------------------------------------------------------------------------- whole iterations
+
+@pytest.mark.parametrize("algo", [0, 1])
+def test_one_iteration_from_random_state(tv, algo):
+    P = small_problem(64, 1229)
+    n = P.n
+    tau = oracle.default_tau(P.A)
+    rng = np.random.default_rng(9)
+    u0 = (P.ubar + 0.05 * rng.standard_normal((n, n))).astype(np.float32)
+    lam0 = (0.5 * rng.standard_normal((2, n, n))).astype(np.float32) if algo == 0 else \
+        np.zeros((2, n, n), np.float32)
+    h = make_handle(tv, P, tau, algo=algo)
+    tv.tvcs_set_state(h, tv.TVCS_STATE_F, P.f)
+    tv.tvcs_set_state(h, tv.TVCS_STATE_U, u0.ravel())
+    tv.tvcs_set_state(h, tv.TVCS_STATE_LAMBDA, lam0.ravel())
+    res = tv.tvcs_iterate(h, 1)
+    assert res.iters == 1
+    ref = oracle.solve(P.A, P.f, n, P.mu, P.beta, tau, max_iter=1, algo=algo,
+                       u0=u0, lam0=lam0 if algo == 0 else None)
+    assert rel(tv.get_state(h, tv.TVCS_STATE_U), ref.u) <= 1e-5
+    assert rel(tv.get_state(h, tv.TVCS_STATE_W), ref.w) <= 1e-5
+    if algo == 0:
+        assert rel(tv.get_state(h, tv.TVCS_STATE_LAMBDA), ref.lam) <= 1e-5
+    tv.tvcs_destroy(h)
+
+
+def test_fixed_50_iterations_n32(tv):
+    P = synth.workload_n32()
+    tau = oracle.default_tau(P.A)
+    h = make_handle(tv, P, tau, max_iter=50)
+    u = torch.empty(P.N, dtype=torch.float32, device="cuda")
+    res = tv.tvcs_solve(h, torch.from_numpy(P.f).cuda(), u)
+    ref = oracle.solve(P.A, P.f, P.n, P.mu, P.beta, tau, max_iter=50)
+    assert res.iters == 50
+    assert rel(u.cpu().numpy(), ref.u) <= 1e-5
+    assert abs(res.objective - ref.info["objective"]) <= 1e-6 * ref.info["objective"]
+    tv.tvcs_destroy(h)
+
+
+def test_convergence_parity_fast_setting(tv):
+    # A setting that converges in a few hundred iterations (mu=50, beta=20 at
+    # n=32): eq. (stop) must fire at (nearly) the same iteration, and the
+    # results must agree at the tolerances of a converged run.
+    P = synth.make_problem(32, 0.3, 0, 6, 50.0, 20.0, noise_c=1e-3)
+    tau = oracle.default_tau(P.A)
+    tol = 1e-4
+    h = make_handle(tv, P, tau, max_iter=3000, tol=tol)
+    u = np.empty(P.N, np.float32)
+    res = tv.tvcs_solve(h, P.f, u)          # host pointers
+    ref = oracle.solve(P.A, P.f, P.n, P.mu, P.beta, tau, tol=tol, max_iter=3000)
+    assert res.status == tv.TVCS_OK and res.stopped_by_tol == 1
+    assert abs(res.iters - ref.info["iters"]) <= 1
+    same = oracle.solve(P.A, P.f, P.n, P.mu, P.beta, tau, max_iter=res.iters)
+    assert rel(u, same.u) <= 1e-4
+    assert abs(res.objective - same.info["objective"]) <= 1e-6 * same.info["objective"]
+    tv.tvcs_destroy(h)
+
+
+def test_workload_n32_to_500_iterations(tv):
+    # n=32, m=307, mu=1e3, beta=10, tol 1e-4, <= 500 iterations.
+    P = synth.workload_n32()
+    tau = oracle.default_tau(P.A)
+    h = make_handle(tv, P, tau, max_iter=P.max_iter, tol=P.tol)
+    u = torch.empty(P.N, dtype=torch.float32, device="cuda")
+    res = tv.tvcs_solve(h, torch.from_numpy(P.f).cuda(), u)
+    ref = oracle.solve(P.A, P.f, P.n, P.mu, P.beta, tau, tol=P.tol, max_iter=P.max_iter)
+    assert abs(res.iters - ref.info["iters"]) <= 1
+    same = ref if res.iters == ref.info["iters"] else oracle.solve(
+        P.A, P.f, P.n, P.mu, P.beta, tau, max_iter=res.iters)
+    assert rel(u.cpu().numpy(), same.u) <= 1e-4
+    assert abs(res.objective - same.info["objective"]) <= 1e-6 * same.info["objective"]
+    assert res.kkt_dual == pytest.approx(same.info["kkt_dual"], rel=1e-3)
+    assert res.lambda_max_norm == pytest.approx(same.info["lambda_max_norm"], rel=1e-4)
+    tv.tvcs_destroy(h)
+
+
+def test_ftvcs_mode_50_iterations(tv):
+    P = synth.workload_n32()
+    tau = oracle.default_tau(P.A)
+    h = make_handle(tv, P, tau, algo=1, max_iter=50)
+    u = torch.empty(P.N, dtype=torch.float32, device="cuda")
+    tv.tvcs_solve(h, torch.from_numpy(P.f).cuda(), u)
+    ref = oracle.solve(P.A, P.f, P.n, P.mu, P.beta, tau, max_iter=50, algo=oracle.FTVCS)
+    assert rel(u.cpu().numpy(), ref.u) <= 1e-5
+    assert np.all(tv.get_state(h, tv.TVCS_STATE_LAMBDA) == 0)
+    tv.tvcs_destroy(h)
+
+
+@pytest.mark.parametrize("n,m,iters", [(16, 1, 20), (16, 76, 30), (48, 77, 30), (96, 921, 30),
+                                       (64, 409, 30)])
+def test_ragged_and_small_sizes(tv, n, m, iters):
+    P = small_problem(n, m)
+    tau = oracle.default_tau(P.A)
+    h = make_handle(tv, P, tau, max_iter=iters)
+    u = torch.empty(P.N, dtype=torch.float32, device="cuda")
+    res = tv.tvcs_solve(h, torch.from_numpy(P.f).cuda(), u)
+    ref = oracle.solve(P.A, P.f, n, P.mu, P.beta, tau, max_iter=iters)
+    assert res.iters == iters
+    assert rel(u.cpu().numpy(), ref.u) <= 1e-5
+    tv.tvcs_destroy(h)
+
+
+def test_init_modes_and_zero_iterations(tv):
+    P = small_problem(32, 307)
+    tau = oracle.default_tau(P.A)
+    h = make_handle(tv, P, tau, max_iter=1)
+    u = np.empty(P.N, np.float32)
+    # u^0 = A^T f (reading C3): zero iterations via tvcs_iterate after set_state of f
+    hz = make_handle(tv, P, tau, init=tv.TVCS_INIT_ZERO, max_iter=20)
+    tv.tvcs_solve(hz, P.f, u)
+    ref = oracle.solve(P.A, P.f, 32, P.mu, P.beta, tau, max_iter=20, init=oracle.INIT_ZERO)
+    assert rel(u, ref.u) <= 1e-5
+    tv.tvcs_solve(h, P.f, u)
+    ref1 = oracle.solve(P.A, P.f, 32, P.mu, P.beta, tau, max_iter=1)
+    assert rel(u, ref1.u) <= 1e-5
+    tv.tvcs_destroy(h)
+    tv.tvcs_destroy(hz)
+
+
+def test_auto_tau_matches_oracle_power_iteration(tv):
+    P = synth.workload_n32()
+    opt = tv.tvcs_default_options()
+    h = tv.tvcs_create(torch.from_numpy(P.A).cuda(), 0, P.m, P.n, P.mu, P.beta, 0.0, opt)
+    assert tv.tvcs_get_tau(h) == pytest.approx(oracle.default_tau(P.A), rel=1e-4)
+    tv.tvcs_destroy(h)
+
+
+def test_seed_generated_A_solve(tv):
+    P = small_problem(64, 1229, seed=21)
+    tau = oracle.default_tau(P.A)
+    h = make_handle(tv, P, tau, max_iter=30, seed_only=True)
+    u = torch.empty(P.N, dtype=torch.float32, device="cuda")
+    tv.tvcs_solve(h, torch.from_numpy(P.f).cuda(), u)
+    ref = oracle.solve(P.A, P.f, 64, P.mu, P.beta, tau, max_iter=30)
+    assert rel(u.cpu().numpy(), ref.u) <= 1e-5
+    tv.tvcs_destroy(h)
+
+
+def test_batched_entry_point_matches_single_solves(tv):
+    probs = [small_problem(32, 307, seed=s) for s in (1, 2, 3)]
+    hs, fs, us = [], [], []
+    for P in probs:
+        hs.append(make_handle(tv, P, 0.12, max_iter=25))
+        fs.append(P.f)
+        us.append(np.empty(P.N, np.float32))
+    mus = [200.0, 500.0, 1000.0]
+    res = tv.tvcs_solve_batched(hs, fs, us, mus)
+    for P, u, r, mu in zip(probs, us, res, mus):
+        ref = oracle.solve(P.A, P.f, 32, mu, P.beta, 0.12, max_iter=25)
+        assert r.iters == 25
+        assert rel(u, ref.u) <= 1e-5
+    for h in hs:
+        tv.tvcs_destroy(h)
+
+
+def test_workload_n128_300_iterations(tv):
+    # The benchmark workload at full size, in the launch configuration bench.py times.
+    P = synth.workload_n128()
+    tau = oracle.default_tau(P.A, 100)
+    h = make_handle(tv, P, tau, max_iter=300)
+    u = torch.empty(P.N, dtype=torch.float32, device="cuda")
+    res = tv.tvcs_solve(h, torch.from_numpy(P.f).cuda(), u)
+    ref = oracle.solve(P.A, P.f, P.n, P.mu, P.beta, tau, max_iter=300)
+    assert res.iters == 300
+    assert rel(u.cpu().numpy(), ref.u) <= 1e-4
+    assert abs(res.objective - ref.info["objective"]) <= 1e-5 * ref.info["objective"]
+    tv.tvcs_destroy(h)
