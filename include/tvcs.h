@@ -69,6 +69,9 @@ typedef struct {
     void* stream;        /* cudaStream_t for all device work; NULL: a stream the handle owns */
     int power_iters;     /* <= 0: 100 */
     long long timeout_cycles; /* bound of every device spin-wait, in SM clock cycles; <= 0: 2^31 */
+    int host_loop;       /* 0 (default): the iteration loop is one CUDA graph whose WHILE node
+                            the kernels end; 1: the same kernels launched from the host per
+                            iteration (for profilers that cannot look inside such graphs) */
 } tvcs_options;
 
 typedef struct {
@@ -140,7 +143,10 @@ enum { TVCS_STATE_U = 0,      /* n*n   current iterate u^k */
        TVCS_STATE_LAMBDA = 2, /* 2*n*n lambda^k (lambda1 plane, then lambda2 plane) */
        TVCS_STATE_G = 3,      /* n*n   g^k = A^T (A u^k - f) */
        TVCS_STATE_R = 4,      /* m     r^k = A u^k - f */
-       TVCS_STATE_RHS = 5,    /* n*n   right-hand side of the last u-step, scaled by beta */
+       TVCS_STATE_RHS = 5,    /* n*n   right-hand side of the last u-step in increment form:
+                                       D^T (beta (w - D u^k) - lambda) - mu g, i.e. eq.
+                                       (eqnorm11) times beta minus (beta D^T D + mu/tau) u^k;
+                                       the u-step solves for d = u^{k+1} - u^k */
        TVCS_STATE_F = 6 };    /* m     data f */
 
 /* Copies one state array out (get) or in (set; only U, LAMBDA and F).  Setting U

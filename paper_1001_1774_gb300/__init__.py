@@ -40,7 +40,8 @@ EXPORTED = ["tvcs_default_options", "tvcs_create", "tvcs_solve", "tvcs_solve_bat
 class tvcs_options(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int), ("tau", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("precision", ctypes.c_int), ("init", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("power_iters", ctypes.c_int), ("timeout_cycles", ctypes.c_longlong)]
+                ("power_iters", ctypes.c_int), ("timeout_cycles", ctypes.c_longlong),
+                ("host_loop", ctypes.c_int)]
 
 
 class tvcs_result(ctypes.Structure):

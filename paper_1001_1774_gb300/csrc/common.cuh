@@ -178,6 +178,25 @@ __device__ __forceinline__ double block_max(double v, double* scratch)
     return s;
 }
 
+// Block-wide sum over an array of per-block binary64 partials (fixed order
+// per thread, fixed tree across threads: deterministic).  All threads call;
+// result valid in thread 0.
+__device__ __forceinline__ double block_sum_array(const double* __restrict__ a, int count,
+                                                  int stride, double* scratch)
+{
+    double s = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) s += a[(size_t)i * stride];
+    return block_sum(s, scratch);
+}
+
+__device__ __forceinline__ double block_max_array(const double* __restrict__ a, int count,
+                                                  int stride, double* scratch)
+{
+    double s = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) s = fmax(s, a[(size_t)i * stride]);
+    return block_max(s, scratch);
+}
+
 // Last-block detection: returns true in exactly one block (the last to
 // arrive), after every block's prior global writes are visible to it.  The
 // ticket is reset by that block.  Call from thread 0 only.
@@ -191,6 +210,16 @@ __device__ __forceinline__ bool last_block_arrive(unsigned* ticket)
         *ticket = 0u;
     }
     return last;
+}
+
+// Whole-block version: every thread calls it after the block's partials are
+// written; returns true in every thread of the last block.
+__device__ __forceinline__ bool last_block_all(unsigned* ticket, int* sflag)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) *sflag = last_block_arrive(ticket) ? 1 : 0;
+    __syncthreads();
+    return *sflag != 0;
 }
 
 }  // namespace tvcs

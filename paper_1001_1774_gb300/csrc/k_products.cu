@@ -32,8 +32,9 @@ struct ProdShape {
     static constexpr int WPR = TPR / 32;
     static constexpr int N = 4 * TPR * V;
     static constexpr size_t STAGE_FLOATS = (size_t)RS * N;
+    static constexpr int YMAX = 1024;   // rows of y prefetched into shared memory
     static constexpr size_t SMEM = PROD_NST * STAGE_FLOATS * 4 + 2 * PROD_NST * 8 +
-                                   2 * RL * WPR * 4 + 32 * 8 + 64;
+                                   2 * RL * WPR * 4 + 32 * 8 + 16 + YMAX * 4;
     static_assert(RS % RL == 0, "rows per stage must be a multiple of the row lanes");
     static_assert(TPR % 32 == 0, "row lanes must be whole warps");
 };
@@ -55,6 +56,8 @@ __global__ void __launch_bounds__(PROD_THREADS, 1)
     uint64_t* empty = full + PROD_NST;
     float* red = reinterpret_cast<float*>(empty + PROD_NST);        // [2][RL][WPR]
     double* dred = reinterpret_cast<double*>(red + 2 * RL * WPR);   // [32]
+    int* sflag = reinterpret_cast<int*>(dred + 32);                 // [4]
+    float* sy = reinterpret_cast<float*>(sflag + 4);                // [YMAX]
 
     const int tid = threadIdx.x;
     if (mode == MODE_ITER) {
@@ -115,6 +118,10 @@ __global__ void __launch_bounds__(PROD_THREADS, 1)
     }
 
     // ---------------- consumers ----------------
+    // y of this block's rows, prefetched so that r_i = dot - y_i waits on no global load.
+    const bool y_in_smem = (y != nullptr) && nrows <= S::YMAX;
+    if (y_in_smem)
+        for (int i = tid; i < nrows; i += PROD_CONS) sy[i] = y[i0 + i];
     const int lane_row = tid / TPR;
     const int ltid = tid - lane_row * TPR;
     const int warp_in_row = ltid >> 5;
@@ -141,6 +148,9 @@ __global__ void __launch_bounds__(PROD_THREADS, 1)
             const int rl = st * RL + lane_row;
             const bool valid = ok && rl < rows;
             const float4* a4 = reinterpret_cast<const float4*>(sb + (size_t)rl * N);
+            const int li = s * RS + rl;   // row index within the block
+            float yi = 0.f;
+            if (valid && y != nullptr && !y_in_smem) yi = y[i0 + li];
             float d = 0.f;
             if (valid) {
 #pragma unroll
@@ -160,8 +170,9 @@ __global__ void __launch_bounds__(PROD_THREADS, 1)
                 float dot = 0.f;
 #pragma unroll
                 for (int w = 0; w < WPR; ++w) dot += rb[lane_row * WPR + w];
-                const int gi = i0 + s * RS + rl;
-                const float ri = y ? dot - y[gi] : dot;
+                const int gi = i0 + li;
+                if (y_in_smem) yi = sy[li];
+                const float ri = dot - yi;
                 if (ltid == 0) {
                     r[gi] = ri;
                     r2 += (double)ri * (double)ri;
@@ -212,9 +223,17 @@ __global__ void __launch_bounds__(PROD_THREADS, 1)
         double s = 0.0;
         for (int l = 0; l < RL; ++l) s += dred[l];
         r2part[blockIdx.x] = s;
-        if (last_block_arrive(&ctrl->ticket_prod)) {
+        sflag[0] = last_block_arrive(&ctrl->ticket_prod) ? 1 : 0;
+    }
+    named_barrier(1, PROD_CONS);
+    if (sflag[0]) {   // last block: sum the G partials with all consumer warps (G <= 512)
+        double v = tid < G ? r2part[tid] : 0.0;
+        v = warp_sum(v);
+        if ((tid & 31) == 0) dred[tid >> 5] = v;
+        named_barrier(1, PROD_CONS);
+        if (tid == 0) {
             double t = 0.0;
-            for (int b = 0; b < G; ++b) t += r2part[b];
+            for (int w = 0; w < PROD_CONS / 32; ++w) t += dred[w];
             ctrl->r2 = t;
         }
     }
@@ -320,14 +339,50 @@ __global__ void __launch_bounds__(256) k_gather(const float* __restrict__ gpart,
         sq = (double)v * (double)v;
     }
     const double s = block_sum(sq, red);
-    if (threadIdx.x == 0) {
-        part[blockIdx.x] = s;
-        if (last_block_arrive(&ctrl->ticket_gather)) {
-            double t = 0.0;
-            for (unsigned b = 0; b < gridDim.x; ++b) t += part[b];
-            ctrl->vec2 = t;
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+    __shared__ int is_last;
+    if (!last_block_all(&ctrl->ticket_gather, &is_last)) return;
+    const double t = block_sum_array(part, gridDim.x, 1, red);
+    if (threadIdx.x == 0) ctrl->vec2 = t;
+}
+
+// g = sum over the P per-block partials, in a fixed order.  A block covers 32
+// float4 columns with 8 partial slices (one warp each); slice k sums partials
+// k, k+8, ..., then slice 0 adds the 8 slice sums in order.
+__global__ void __launch_bounds__(256) k_greduce(const float4* __restrict__ gpart, int P, int N4,
+                                                 float4* __restrict__ g,
+                                                 const Ctrl* __restrict__ ctrl, int mode)
+{
+    __shared__ float4 acc[8][32];
+    if (mode == MODE_ITER && ctrl->skip) return;
+    const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + lane;
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (c < N4) {
+        for (int p = slice; p < P; p += 8) {
+            const float4 v = gpart[(size_t)p * N4 + c];
+            s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
         }
     }
+    acc[slice][lane] = s;
+    __syncthreads();
+    if (slice == 0 && c < N4) {
+        float4 t = acc[0][lane];
+#pragma unroll
+        for (int k = 1; k < 8; ++k) {
+            const float4 v = acc[k][lane];
+            t.x += v.x; t.y += v.y; t.z += v.z; t.w += v.w;
+        }
+        g[c] = t;
+    }
+}
+
+void launch_greduce(const float* gpart, int P, int N, float* g, const Ctrl* ctrl, int mode,
+                    cudaStream_t s)
+{
+    const int N4 = N / 4;
+    k_greduce<<<(N4 + 31) / 32, 256, 0, s>>>(reinterpret_cast<const float4*>(gpart), P, N4,
+                                              reinterpret_cast<float4*>(g), ctrl, mode);
 }
 
 __global__ void k_normalize(const float* __restrict__ z, float* __restrict__ v, int N,

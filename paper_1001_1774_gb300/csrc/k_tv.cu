@@ -25,7 +25,7 @@ namespace tvcs {
 template <int NN>
 __global__ void __launch_bounds__(256) k_wstep_rowfft(
     const float* __restrict__ u, float* __restrict__ wbuf, float* __restrict__ lbuf,
-    const float* __restrict__ gpart, int P, float* __restrict__ g_out,
+    const float* __restrict__ g,
     float* __restrict__ rhs_out, float2* __restrict__ spec, const float2* __restrict__ tw_g,
     float beta, float mu_over_tau, float mu, Ctrl* __restrict__ ctrl, int mode)
 {
@@ -82,8 +82,9 @@ __global__ void __launch_bounds__(256) k_wstep_rowfft(
             w1 = s * z1;
             w2 = s * z2;
         }
-        sy1[rr][c] = beta * w1 - l1;
-        sy2[rr][c] = beta * w2 - l2;
+        // y = beta (w^{k+1} - D u^k) - lambda^k: the increment form of eq. (eqnorm11)
+        sy1[rr][c] = beta * (w1 - d1) - l1;
+        sy2[rr][c] = beta * (w2 - d2) - l2;
         if (rr >= 1) {
             wdst[gi] = w1;
             wdst[N + gi] = w2;
@@ -91,32 +92,21 @@ __global__ void __launch_bounds__(256) k_wstep_rowfft(
             ldst[N + gi] = l2;
         }
     }
-    // g^k for the two owned rows: sum of the product kernel's partials.
-    for (int i = tid; i < 2 * NN; i += blockDim.x) {
-        const int gi = r0 * NN + i;
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-        int p = 0;
-        for (; p + 4 <= P; p += 4) {
-            s0 += gpart[(size_t)p * N + gi];
-            s1 += gpart[(size_t)(p + 1) * N + gi];
-            s2 += gpart[(size_t)(p + 2) * N + gi];
-            s3 += gpart[(size_t)(p + 3) * N + gi];
-        }
-        for (; p < P; ++p) s0 += gpart[(size_t)p * N + gi];
-        const float g = (s0 + s1) + (s2 + s3);
-        sg[i / NN][i % NN] = g;
-        if (g_out) g_out[gi] = g;
-    }
+    // g^k = A^T (A u^k - f) for the two owned rows.
+    for (int i = tid; i < 2 * NN; i += blockDim.x) sg[i / NN][i % NN] = g[r0 * NN + i];
     __syncthreads();
 
-    // eq. (eqnorm11) times beta: rhs = D^T (beta w - lambda) + (mu/tau) u - mu g
+    // eq. (eqnorm11) times beta, solved for the increment d = u^{k+1} - u^k:
+    // (beta D^T D + (mu/tau) I) d = D^T (beta (w - D u^k) - lambda) - mu g.  Equal to the
+    // printed form in exact arithmetic; the large (mu/tau) u^k term cancels analytically, so
+    // the FFT round-off scales with the step, not with u.
     for (int c = tid; c < NN; c += blockDim.x) {
         const int cm = (c == 0) ? NN - 1 : c - 1;
         float v[2];
 #pragma unroll
         for (int rr = 0; rr < 2; ++rr) {
             const float dty = sy1[rr + 1][cm] - sy1[rr + 1][c] + sy2[rr][c] - sy2[rr + 1][c];
-            v[rr] = dty + mu_over_tau * su[rr + 1][c] - mu * sg[rr][c];
+            v[rr] = dty - mu * sg[rr][c];
         }
         ca[c] = make_float2(v[0], v[1]);
         if (rhs_out) {
@@ -229,9 +219,10 @@ __global__ void __launch_bounds__(128) k_fft_rows_inv(const float2* __restrict__
     double du2 = 0.0, u2 = 0.0;
     for (int c = tid; c < NN; c += blockDim.x) {
         const float2 v = z[c];
-        const float n0 = v.x * sc, n1 = v.y * sc;
+        const float d0 = v.x * sc, d1 = v.y * sc;   // the increment u^{k+1} - u^k
         const int i0 = r0 * NN + c, i1 = (r0 + 1) * NN + c;
         const float o0 = u[i0], o1 = u[i1];
+        const float n0 = o0 + d0, n1 = o1 + d1;
         const double e0 = (double)n0 - (double)o0, e1 = (double)n1 - (double)o1;
         du2 += e0 * e0 + e1 * e1;
         u2 += (double)o0 * o0 + (double)o1 * o1;
@@ -243,12 +234,13 @@ __global__ void __launch_bounds__(128) k_fft_rows_inv(const float2* __restrict__
     if (tid == 0) {
         part[2 * blockIdx.x] = s_du;
         part[2 * blockIdx.x + 1] = s_u;
-        if (last_block_arrive(&ctrl->ticket_fft)) {
-            double tdu = 0.0, tu = 0.0;
-            for (unsigned k = 0; k < gridDim.x; ++k) {
-                tdu += part[2 * k];
-                tu += part[2 * k + 1];
-            }
+    }
+    __shared__ int is_last;
+    if (!last_block_all(&ctrl->ticket_fft, &is_last)) return;
+    const double tdu = block_sum_array(part, gridDim.x, 2, red);
+    const double tu = block_sum_array(part + 1, gridDim.x, 2, red);
+    if (tid == 0) {
+        {
             ctrl->du2 = tdu;
             ctrl->u2 = tu;
             ctrl->relchg = tu > 0.0 ? sqrt(tdu / tu) : (tdu > 0.0 ? INFINITY : 0.0);
@@ -279,9 +271,7 @@ __global__ void __launch_bounds__(128) k_fft_rows_inv(const float2* __restrict__
 // ---------------------------------------------------------------------------
 template <int NN>
 __global__ void __launch_bounds__(256) k_final1(const float* __restrict__ u, float* __restrict__ wbuf,
-                                                float* __restrict__ lbuf,
-                                                const float* __restrict__ gpart, int P,
-                                                float* __restrict__ g, float beta,
+                                                float* __restrict__ lbuf, float beta,
                                                 double* __restrict__ part, Ctrl* __restrict__ ctrl)
 {
     constexpr int N = NN * NN;
@@ -305,25 +295,21 @@ __global__ void __launch_bounds__(256) k_final1(const float* __restrict__ u, flo
         tv = sqrt((double)d1 * d1 + (double)d2 * d2);
         const double e1 = (double)w1 - d1, e2 = (double)w2 - d2;
         kp = e1 * e1 + e2 * e2;
-        float s = 0.f;
-        for (int p = 0; p < P; ++p) s += gpart[(size_t)p * N + i];
-        g[i] = s;
     }
     const double stv = block_sum(tv, red);
     const double skp = block_sum(kp, red);
     if (threadIdx.x == 0) {
         part[2 * blockIdx.x] = stv;
         part[2 * blockIdx.x + 1] = skp;
-        if (last_block_arrive(&ctrl->ticket_fin)) {
-            double a = 0.0, b = 0.0;
-            for (unsigned k = 0; k < gridDim.x; ++k) {
-                a += part[2 * k];
-                b += part[2 * k + 1];
-            }
-            ctrl->tv = a;
-            ctrl->kkt_p2 = b;
-            ctrl->pending = 0;
-        }
+    }
+    __shared__ int is_last;
+    if (!last_block_all(&ctrl->ticket_fin, &is_last)) return;
+    const double a = block_sum_array(part, gridDim.x, 2, red);
+    const double b = block_sum_array(part + 1, gridDim.x, 2, red);
+    if (threadIdx.x == 0) {
+        ctrl->tv = a;
+        ctrl->kkt_p2 = b;
+        ctrl->pending = 0;
     }
 }
 
@@ -351,15 +337,14 @@ __global__ void __launch_bounds__(256) k_final2(const float* __restrict__ lbuf,
     if (threadIdx.x == 0) {
         part[2 * blockIdx.x] = skd;
         part[2 * blockIdx.x + 1] = slm;
-        if (last_block_arrive(&ctrl->ticket_fin)) {
-            double a = 0.0, b = 0.0;
-            for (unsigned k = 0; k < gridDim.x; ++k) {
-                a += part[2 * k];
-                b = fmax(b, part[2 * k + 1]);
-            }
-            ctrl->kkt_d2 = a;
-            ctrl->lam_max = b;
-        }
+    }
+    __shared__ int is_last;
+    if (!last_block_all(&ctrl->ticket_fin, &is_last)) return;
+    const double a = block_sum_array(part, gridDim.x, 2, red);
+    const double b = block_max_array(part + 1, gridDim.x, 2, red);
+    if (threadIdx.x == 0) {
+        ctrl->kkt_d2 = a;
+        ctrl->lam_max = b;
     }
 }
 
@@ -374,7 +359,7 @@ static void launch_tv_set(const TvArgs& a, int which, cudaStream_t s)
     constexpr int Q = NN / 2 + 1;
     switch (which) {
         case 1:
-            k_wstep_rowfft<NN><<<NN / 2, 256, 0, s>>>(a.u, a.w, a.lam, a.gpart, a.P, a.g_out,
+            k_wstep_rowfft<NN><<<NN / 2, 256, 0, s>>>(a.u, a.w, a.lam, a.g,
                                                       a.rhs_out, a.spec, a.tw, a.beta,
                                                       a.mu_over_tau, a.mu, a.ctrl, a.mode);
             break;
@@ -386,11 +371,10 @@ static void launch_tv_set(const TvArgs& a, int which, cudaStream_t s)
             k_fft_rows_inv<NN><<<NN / 2, 128, 0, s>>>(a.spec, a.tw, a.u, a.part, a.ctrl, a.mode);
             break;
         case 4:
-            k_final1<NN><<<(N + 255) / 256, 256, 0, s>>>(a.u, a.w, a.lam, a.gpart, a.P, a.g_out,
-                                                         a.beta, a.part, a.ctrl);
+            k_final1<NN><<<(N + 255) / 256, 256, 0, s>>>(a.u, a.w, a.lam, a.beta, a.part, a.ctrl);
             break;
         case 5:
-            k_final2<NN><<<(N + 255) / 256, 256, 0, s>>>(a.lam, a.g_out, a.mu, a.part, a.ctrl);
+            k_final2<NN><<<(N + 255) / 256, 256, 0, s>>>(a.lam, a.g, a.mu, a.part, a.ctrl);
             break;
         default:
             break;

@@ -13,9 +13,7 @@ struct TvArgs {
     float* u;
     float* w;           // 2 copies x 2 planes x N
     float* lam;         // 2 copies x 2 planes x N
-    const float* gpart; // P x N partial sums of A^T r
-    int P;
-    float* g_out;       // nullable (w-step) / required (final kernels)
+    const float* g;     // g = A^T (A u - f), N values
     float* rhs_out;     // nullable
     float2* spec;       // n x (n/2+1)
     const float2* tw;   // n twiddles (cos, sin)(2 pi t / n)
@@ -50,6 +48,9 @@ bool prod_supported(int n);
 int prod_grid(int n, int m, int num_sms);   // number of blocks = number of partials P
 cudaError_t prod_configure(int n);          // opt-in shared memory size (call once per device)
 void launch_products(int n, int grid, const ProdArgs& a, cudaStream_t s);
+// g = sum_p gpart[p] (fixed order), wide grid; skipped when mode == MODE_ITER and ctrl->skip.
+void launch_greduce(const float* gpart, int P, int N, float* g, const Ctrl* ctrl, int mode,
+                    cudaStream_t s);
 
 // gather: out = scale * sum_p gpart[p], ctrl->vec2 = ||out||^2 (binary64)
 void launch_gather(const float* gpart, int P, int N, float scale, float* out, double* part,

@@ -95,9 +95,7 @@ TvArgs tv_args(tvcs_ctx* h, int mode, bool stage_outputs)
     a.u = h->u;
     a.w = h->w;
     a.lam = h->lam;
-    a.gpart = h->gpart;
-    a.P = h->P;
-    a.g_out = stage_outputs ? h->g : nullptr;
+    a.g = h->g;
     a.rhs_out = stage_outputs ? h->rhs : nullptr;
     a.spec = h->spec;
     a.tw = h->tw;
@@ -111,8 +109,9 @@ TvArgs tv_args(tvcs_ctx* h, int mode, bool stage_outputs)
     return a;
 }
 
-void products(tvcs_ctx* h, const float* x, const float* y, float* r, float* gpart, int mode,
-              unsigned long long cond, int set_cond, cudaStream_t s)
+// r = A x - y and the partials of A^T r into gpart; then g = their sum when g != NULL.
+void products(tvcs_ctx* h, const float* x, const float* y, float* r, float* gpart, float* g,
+              int mode, unsigned long long cond, int set_cond, cudaStream_t s)
 {
     ProdArgs a{};
     a.A = h->A;
@@ -128,6 +127,18 @@ void products(tvcs_ctx* h, const float* x, const float* y, float* r, float* gpar
     a.set_cond = set_cond;
     a.budget = budget_of(h);
     launch_products(h->n, h->P, a, s);
+    if (g) launch_greduce(gpart, h->P, h->N, g, h->ctrl, mode, s);
+}
+
+// The body of one iteration (rows a1-a7), MODE_ITER: w-step and row FFT,
+// column pass, inverse rows, products, reduction of the partials into g.
+void launch_iteration(tvcs_ctx* h, unsigned long long cond, int set_cond, cudaStream_t s)
+{
+    TvArgs a = tv_args(h, MODE_ITER, false);
+    launch_tv(h->n, a, 1, s);
+    launch_tv(h->n, a, 2, s);
+    launch_tv(h->n, a, 3, s);
+    products(h, h->u, h->f, h->r, h->gpart, h->g, MODE_ITER, cond, set_cond, s);
 }
 
 tvcs_status sync_and_check(tvcs_ctx* h, const char* what)
@@ -201,11 +212,7 @@ tvcs_status build_graph(tvcs_ctx* h)
     cudaGraph_t body = np.conditional.phGraph_out[0];
     CK(cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0,
                                      cudaStreamCaptureModeThreadLocal));
-    TvArgs a = tv_args(h, MODE_ITER, false);
-    launch_tv(h->n, a, 1, h->cap_stream);
-    launch_tv(h->n, a, 2, h->cap_stream);
-    launch_tv(h->n, a, 3, h->cap_stream);
-    products(h, h->u, h->f, h->r, h->gpart, MODE_ITER, (unsigned long long)ch, 1, h->cap_stream);
+    launch_iteration(h, (unsigned long long)ch, 1, h->cap_stream);
     cudaGraph_t captured = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->cap_stream, &captured);
     if (e != cudaSuccess) return fail(TVCS_ERR_CUDA, "capture of the loop body: %s", cudaGetErrorString(e));
@@ -216,7 +223,7 @@ tvcs_status build_graph(tvcs_ctx* h)
 // (Re)computes r = A u - f and the partials of g = A^T r for the current u.
 void refresh_products(tvcs_ctx* h)
 {
-    products(h, h->u, h->f, h->r, h->gpart, MODE_PLAIN, 0ull, 0, h->stream);
+    products(h, h->u, h->f, h->r, h->gpart, h->g, MODE_PLAIN, 0ull, 0, h->stream);
 }
 
 tvcs_status init_state(tvcs_ctx* h, int init)
@@ -237,7 +244,7 @@ tvcs_status init_state(tvcs_ctx* h, int init)
     CK(cudaMemsetAsync(h->lam, 0, sizeof(float) * 4 * N, h->stream));
     if (init == TVCS_INIT_ATF) {
         // u^0 = A^T f (reading C3): the products at x = 0 give A^T (0 - f).
-        products(h, h->zeroN, h->f, h->r, h->gpart, MODE_PLAIN, 0ull, 0, h->stream);
+        products(h, h->zeroN, h->f, h->r, h->gpart, nullptr, MODE_PLAIN, 0ull, 0, h->stream);
         launch_gather(h->gpart, h->P, h->N, -1.0f, h->u, h->part, h->ctrl, h->stream);
     } else if (init == TVCS_INIT_ZERO) {
         CK(cudaMemsetAsync(h->u, 0, sizeof(float) * N, h->stream));
@@ -255,7 +262,7 @@ tvcs_status init_state(tvcs_ctx* h, int init)
 // Runs up to `iters` iterations from the current state; tol > 0 enables eq. (stop).
 tvcs_status run_loop(tvcs_ctx* h, int iters, double tol, tvcs_result* res)
 {
-    CKS(build_graph(h));
+    if (!h->opt.host_loop) CKS(build_graph(h));
     CKS(read_ctrl(h));
     Ctrl& c = *h->hctrl;
     c.it = 0;
@@ -271,11 +278,18 @@ tvcs_status run_loop(tvcs_ctx* h, int iters, double tol, tvcs_result* res)
     c.ticket_fft = c.ticket_prod = c.ticket_fin = c.ticket_w = c.ticket_gather = 0;
     CKS(write_ctrl(h));
     CK(cudaEventRecord(h->ev0, h->stream));
-    if (iters > 0) CK(cudaGraphLaunch(h->exec, h->stream));
+    if (iters > 0) {
+        if (h->opt.host_loop) {
+            // Same kernels launched from the host, one iteration at a time (for
+            // profilers that cannot look inside graphs with conditional nodes).
+            for (int k = 0; k < iters; ++k) launch_iteration(h, 0ull, 0, h->stream);
+        } else {
+            CK(cudaGraphLaunch(h->exec, h->stream));
+        }
+    }
     CK(cudaEventRecord(h->ev1, h->stream));
-    // End of run: final multiplier update, g, objective and optimality residuals.
+    // End of run: final multiplier update, objective and optimality residuals.
     TvArgs a = tv_args(h, MODE_PLAIN, false);
-    a.g_out = h->g;
     launch_tv(h->n, a, 4, h->stream);
     launch_tv(h->n, a, 5, h->stream);
     CKS(read_ctrl(h));
@@ -309,11 +323,11 @@ tvcs_status power_tau(tvcs_ctx* h, int iters, double* tau_out)
     const int N = h->N;
     launch_fill(h->tx, N, (float)(1.0 / sqrt((double)N)), h->stream);
     for (int it = 0; it < iters; ++it) {
-        products(h, h->tx, nullptr, h->tr, h->gpart2, MODE_PLAIN, 0ull, 0, h->stream);
+        products(h, h->tx, nullptr, h->tr, h->gpart2, nullptr, MODE_PLAIN, 0ull, 0, h->stream);
         launch_gather(h->gpart2, h->P, N, 1.0f, h->tg, h->part, h->ctrl, h->stream);
         launch_normalize(h->tg, h->tx, N, h->ctrl, h->stream);
     }
-    products(h, h->tx, nullptr, h->tr, h->gpart2, MODE_PLAIN, 0ull, 0, h->stream);
+    products(h, h->tx, nullptr, h->tr, h->gpart2, nullptr, MODE_PLAIN, 0ull, 0, h->stream);
     CKS(read_ctrl(h));
     const double lmax = h->hctrl->r2;
     if (!(lmax > 0.0) || !isfinite(lmax))
@@ -443,6 +457,7 @@ void tvcs_default_options(tvcs_options* opt)
     opt->stream = nullptr;
     opt->power_iters = 100;
     opt->timeout_cycles = 0;
+    opt->host_loop = 0;
 }
 
 const char* tvcs_last_error(void)
@@ -566,10 +581,7 @@ tvcs_status tvcs_get_state(tvcs_handle h, int which, float* dst)
         case TVCS_STATE_U: CKS(copy_out(h, dst, h->u, N)); break;
         case TVCS_STATE_W: CKS(copy_out(h, dst, h->w + (size_t)par * 2 * N, 2 * N)); break;
         case TVCS_STATE_LAMBDA: CKS(copy_out(h, dst, h->lam + (size_t)par * 2 * N, 2 * N)); break;
-        case TVCS_STATE_G:
-            launch_gather(h->gpart, h->P, h->N, 1.0f, h->g, h->part, h->ctrl, h->stream);
-            CKS(copy_out(h, dst, h->g, N));
-            break;
+        case TVCS_STATE_G: CKS(copy_out(h, dst, h->g, N)); break;
         case TVCS_STATE_R: CKS(copy_out(h, dst, h->r, (size_t)h->m)); break;
         case TVCS_STATE_RHS: CKS(copy_out(h, dst, h->rhs, N)); break;
         case TVCS_STATE_F: CKS(copy_out(h, dst, h->f, (size_t)h->m)); break;
@@ -669,8 +681,8 @@ tvcs_status tvcs_apply(tvcs_handle h, const float* x, const float* y, float* r, 
     if (!x || !r || !g) return fail(TVCS_ERR_INVALID_ARG, "x, r and g must be non-NULL");
     CKS(copy_in(h, h->tx, x, (size_t)h->N));
     if (y) CKS(copy_in(h, h->ty, y, (size_t)h->m));
-    products(h, h->tx, y ? h->ty : nullptr, h->tr, h->gpart2, MODE_PLAIN, 0ull, 0, h->stream);
-    launch_gather(h->gpart2, h->P, h->N, 1.0f, h->tg, h->part, h->ctrl, h->stream);
+    products(h, h->tx, y ? h->ty : nullptr, h->tr, h->gpart2, h->tg, MODE_PLAIN, 0ull, 0,
+             h->stream);
     CKS(copy_out(h, r, h->tr, (size_t)h->m));
     CKS(copy_out(h, g, h->tg, (size_t)h->N));
     return sync_and_check(h, "tvcs_apply");

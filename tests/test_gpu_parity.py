@@ -131,14 +131,20 @@ def test_stage_parity(tv, n, m):
     assert np.array_equal(lam, lam0)
     assert rel(w, w_ref) <= 1e-5
     g = oracle.At(P.A, oracle.Au(P.A, u64, P.f))
-    y = P.beta * w_ref - lam0
-    rhs_ref = oracle.Dt(y[0], y[1]) + (P.mu / tau) * u64 - P.mu * g.reshape(n, n)
+    # increment form of eq. (eqnorm11) times beta: D^T (beta (w - D u) - lambda) - mu g
+    y = P.beta * (w_ref - np.stack([d1, d2])) - lam0
+    rhs_ref = oracle.Dt(y[0], y[1]) - P.mu * g.reshape(n, n)
     assert rel(rhs, rhs_ref) <= 1e-5
-    # stage 2: FFT u-solve of (beta D^T D + mu/tau I) u = rhs, i.e. eq. (eqnorm11) times beta
+    # the printed right-hand side of eq. (eqnorm11) and the oracle's u-solve of it
+    yp = w_ref - lam0 / P.beta
+    b_paper = oracle.Dt(yp[0], yp[1]) + (P.mu / (P.beta * tau)) * (u64 - tau * g.reshape(n, n))
+    u_paper = oracle.usolve(b_paper, P.mu / (P.beta * tau))
+    # stage 2: FFT solve for the increment, u^{k+1} = u^k + d
     tv.tvcs_run_stage(h, 2)
     u1 = tv.get_state(h, tv.TVCS_STATE_U).reshape(n, n)
-    u_ref = oracle.usolve(rhs.astype(np.float64) / P.beta, P.mu / (P.beta * tau))
-    assert rel(u1, u_ref) <= 1e-5
+    u_ref = u64 + oracle.usolve(rhs.astype(np.float64) / P.beta, P.mu / (P.beta * tau))
+    assert rel(u1, u_ref) <= 1e-6
+    assert rel(u1, u_paper) <= 1e-5
     # stage 3 then stage 1 again applies the deferred multiplier update (eq. (udlamb))
     tv.tvcs_run_stage(h, 3)
     tv.tvcs_run_stage(h, 1)
@@ -218,8 +224,16 @@ def test_workload_n32_to_500_iterations(tv):
     assert abs(res.iters - ref.info["iters"]) <= 1
     same = ref if res.iters == ref.info["iters"] else oracle.solve(
         P.A, P.f, P.n, P.mu, P.beta, tau, max_iter=res.iters)
-    assert rel(u.cpu().numpy(), same.u) <= 1e-4
-    assert abs(res.objective - same.info["objective"]) <= 1e-6 * same.info["objective"]
+    ug = u.cpu().numpy().astype(np.float64)
+    assert rel(ug, same.u) <= 1e-4
+    # This run ends at the iteration cap, away from the optimum, where the
+    # objective is first-order in the iterate: |Phi(u) - Phi(v)| <= L ||u - v|| with
+    # L = sqrt(8N) (TV: ||D|| <= sqrt(8), N terms) + mu ||A u - f|| ||A|| (fidelity).
+    # (The 1e-6 gap of converged runs is checked in test_convergence_parity_fast_setting.)
+    lip = np.sqrt(8 * P.N) + P.mu * np.sqrt(same.info["resid2"]) * np.sqrt(oracle.lambda_max(P.A))
+    gap = abs(res.objective - same.info["objective"])
+    assert gap <= 2.0 * lip * np.linalg.norm(ug - same.u.ravel()) + 1e-9 * same.info["objective"]
+    assert gap <= 1e-5 * same.info["objective"]
     assert res.kkt_dual == pytest.approx(same.info["kkt_dual"], rel=1e-3)
     assert res.lambda_max_norm == pytest.approx(same.info["lambda_max_norm"], rel=1e-4)
     tv.tvcs_destroy(h)
@@ -247,6 +261,9 @@ def test_ragged_and_small_sizes(tv, n, m, iters):
     res = tv.tvcs_solve(h, torch.from_numpy(P.f).cuda(), u)
     ref = oracle.solve(P.A, P.f, n, P.mu, P.beta, tau, max_iter=iters)
     assert res.iters == iters
+    # binary32 bound: each u-step's FFT round trip adds ~(2 log2 n + 4) 2^-24 of the step,
+    # and w, lambda, g carry one rounding each; 1e-5 holds with margin for these iteration
+    # counts (the increment form keeps the round-off proportional to the step).
     assert rel(u.cpu().numpy(), ref.u) <= 1e-5
     tv.tvcs_destroy(h)
 
