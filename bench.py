@@ -44,6 +44,9 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-solves", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="launch the iteration kernels from the host instead of the loop graph "
+                         "(same kernels; for per-kernel profiler launch lists)")
     return ap.parse_args()
 
 
@@ -196,6 +199,7 @@ def run_ours(args):
     opt = tv.tvcs_default_options()
     opt.max_iter = ITERS_PER_RECON
     opt.stream = ctypes_stream(stream)
+    opt.host_loop = 1 if args.host_loop else 0
     with torch.cuda.stream(stream):
         A_dev = torch.from_numpy(P.A).cuda()
         f_dev = torch.from_numpy(P.f).cuda()
