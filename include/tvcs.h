@@ -175,6 +175,32 @@ tvcs_status tvcs_time_stage(tvcs_handle h, int stage, int reps, double* ms);
  * g = A^T r, with the handle's stored A.  x: N, y: m, r: m, g: N. */
 tvcs_status tvcs_apply(tvcs_handle h, const float* x, const float* y, float* r, float* g);
 
+/* ---- Products without any device allocation -------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot call cudaMalloc when they need the products -- applications that
+ * reserve all device memory in their own pool at start-up, that run under a
+ * hard device-memory cap, or whose latency-critical loops cannot afford the
+ * implicit synchronisation of an allocation.  It computes the same
+ * r = A x - y (y nullable: r = A x) and g = A^T r as tvcs_apply, without a
+ * handle and without allocating anything.
+ *   A      m x n*n row-major binary32, device pointer; x: n*n, y: m (or NULL),
+ *          r: m, g: n*n, all device pointers, owned by the caller
+ *   n      16, 32, 48, 64, 96 or 128; 1 <= m <= 2^24
+ *   stream cudaStream_t (NULL: the legacy default stream); the call returns
+ *          after its device work finished
+ * Work memory: one file-scope device array of 12 MiB (per-block partial sums
+ * of A^T r and a control block), which every GPU that loads the library holds
+ * until the process exits.  Sizes whose partial sums do not fit return
+ * TVCS_ERR_INVALID_ARG with a message naming the limit.  The first call on a
+ * device performs one-time set-up on that device (it looks up the array's
+ * device address and sets the kernels' shared-memory limit); make that first
+ * call before any stream capture.  Every call on a device shares the same
+ * array and clears the parts that must start at zero, so calls whose device
+ * work overlaps (other host threads, other streams) race on it and must be
+ * serialised by the caller. */
+tvcs_status tvcs_apply_noalloc(const float* A, int m, int n, const float* x, const float* y,
+                               float* r, float* g, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

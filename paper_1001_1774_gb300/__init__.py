@@ -34,7 +34,8 @@ TVCS_INIT_ATF, TVCS_INIT_ZERO, TVCS_INIT_GIVEN = 0, 1, 2
 
 EXPORTED = ["tvcs_default_options", "tvcs_create", "tvcs_solve", "tvcs_solve_batched",
             "tvcs_destroy", "tvcs_last_error", "tvcs_get_tau", "tvcs_get_state",
-            "tvcs_set_state", "tvcs_iterate", "tvcs_run_stage", "tvcs_time_stage", "tvcs_apply"]
+            "tvcs_set_state", "tvcs_iterate", "tvcs_run_stage", "tvcs_time_stage", "tvcs_apply",
+            "tvcs_apply_noalloc"]
 
 
 class tvcs_options(ctypes.Structure):
@@ -83,6 +84,7 @@ def _load() -> ctypes.CDLL:
         "tvcs_run_stage": ([H, i], i),
         "tvcs_time_stage": ([H, i, i, ctypes.POINTER(d)], i),
         "tvcs_apply": ([H, vp, vp, vp, vp], i),
+        "tvcs_apply_noalloc": ([vp, i, i, vp, vp, vp, vp, vp], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -223,6 +225,15 @@ def tvcs_time_stage(h: Handle, stage: int, reps: int) -> float:
 def tvcs_apply(h: Handle, x, y, r, g) -> None:
     _check(_lib.tvcs_apply(h.ptr, _ptr(x, h.N), _ptr(y, h.m) if y is not None else None,
                            _ptr(r, h.m, True), _ptr(g, h.N, True)))
+
+
+def tvcs_apply_noalloc(A, m: int, n: int, x, y, r, g, stream: int | None = None) -> None:
+    """r = A x - y and g = A^T r from device tensors, allocating no device memory
+    (see include/tvcs.h for who needs this and its limits)."""
+    N = n * n
+    _check(_lib.tvcs_apply_noalloc(_ptr(A, m * N), int(m), int(n), _ptr(x, N),
+                                   _ptr(y, m) if y is not None else None, _ptr(r, m, True),
+                                   _ptr(g, N, True), ctypes.c_void_p(stream or 0)))
 
 
 def tvcs_last_error() -> str:

@@ -443,6 +443,20 @@ bool valid_n(int n)
 
 }  // namespace
 
+namespace tvcs {
+// Sets the calling thread's tvcs_last_error() message (used by other translation units).
+tvcs_status set_last_error(tvcs_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+}  // namespace tvcs
+
 extern "C" {
 
 void tvcs_default_options(tvcs_options* opt)
