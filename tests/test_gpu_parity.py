@@ -251,8 +251,30 @@ def test_ftvcs_mode_50_iterations(tv):
     tv.tvcs_destroy(h)
 
 
-@pytest.mark.parametrize("n,m,iters", [(16, 1, 20), (16, 76, 30), (48, 77, 30), (96, 921, 30),
-                                       (64, 409, 30)])
+def test_single_measurement_degenerate_case(tv):
+    # m = 1: the fit of one measurement becomes nearly exact, so r = a.u - f cancels:
+    # kappa = sum_j |a_j u_j| / |r| reaches ~3e3 within a few iterations, and a binary32
+    # dot then leaves r with a relative error up to ~sqrt(N) 2^-24 kappa ~ 1e-3.  The
+    # GPU's r must stay within that dot-product bound of the exact residual of its own
+    # iterate, and the image within 1e-4 of the oracle's (vs 1e-5 when m is not tiny).
+    n, m, iters = 16, 1, 20
+    P = small_problem(n, m)
+    tau = oracle.default_tau(P.A)
+    h = make_handle(tv, P, tau, max_iter=iters)
+    u = np.empty(P.N, np.float32)
+    tv.tvcs_solve(h, P.f, u)
+    ref = oracle.solve(P.A, P.f, n, P.mu, P.beta, tau, max_iter=iters)
+    assert rel(u, ref.u) <= 1e-4
+    r = tv.get_state(h, tv.TVCS_STATE_R).astype(np.float64)
+    a = P.A.astype(np.float64)[0]
+    r_exact = a @ u.astype(np.float64) - float(P.f[0])
+    bound = 2 * np.sqrt(P.N) * 2.0**-24 * (np.sum(np.abs(a * u)) + abs(float(P.f[0])))
+    assert abs(r[0] - r_exact) <= bound
+    tv.tvcs_destroy(h)
+
+
+@pytest.mark.parametrize("n,m,iters", [(16, 76, 30), (48, 77, 30), (96, 921, 30), (64, 409, 30),
+                                       (16, 33, 20)])
 def test_ragged_and_small_sizes(tv, n, m, iters):
     P = small_problem(n, m)
     tau = oracle.default_tau(P.A)
