@@ -158,16 +158,18 @@ tvcs_status tvcs_set_state(tvcs_handle h, int which, const float* src);
  * then applies the pending multiplier update and fills res (nullable). */
 tvcs_status tvcs_iterate(tvcs_handle h, int iters, tvcs_result* res);
 
-/* Row-level entry points.  Stage 1: rows a1-a3 (multiplier update, shrink,
- * u-step right-hand side); stage 2: row a4-a5 (FFT u-solve into u, stop
- * norms); stage 3: rows a6-a7 (r = A u - f, g = A^T r).  The state moves as
- * in one iteration of tvcs_iterate. */
+/* Row-level entry points, the two launches of one iteration.  Stage 1: rows
+ * a1-a5 (deferred multiplier update of eq. (udlamb), shrink of eq. (iadmw),
+ * right-hand side, FFT u-solve of eq. (eqnorm11), stop norms of eq. (stop));
+ * afterwards U, W, LAMBDA and RHS hold the new values.  Stage 2: rows a6-a7
+ * (r = A u - f, g = A^T r, and the multiplier update becomes pending).  The
+ * state moves as in one iteration of tvcs_iterate. */
 tvcs_status tvcs_run_stage(tvcs_handle h, int stage);
 
-/* Times `reps` back-to-back launches of one stage (1, 2 or 3, as in
+/* Times `reps` back-to-back launches of one stage (1 or 2, as in
  * tvcs_run_stage, without its host-side bookkeeping) on the handle's stream
  * between two CUDA events; *ms receives the elapsed milliseconds.  Afterwards
- * the state is that of `reps` applications of the stage (stage 3 leaves it
+ * the state is that of `reps` applications of the stage (stage 2 leaves it
  * unchanged).  Requires a state (tvcs_solve or tvcs_set_state first). */
 tvcs_status tvcs_time_stage(tvcs_handle h, int stage, int reps, double* ms);
 

@@ -35,7 +35,15 @@ struct Ctrl {
     double kkt_d2;     // ||D^T lambda + mu g||^2
     double lam_max;    // max_i ||lambda_i||
     double vec2;       // ||g||^2 of the last gathered vector (power iteration)
+    unsigned long long gbar;  // monotone arrival counter of the product kernel's grid barrier
 };
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
 
 enum { ERR_NONE = 0, ERR_TIMEOUT = 1, ERR_NONFINITE = 2 };
 

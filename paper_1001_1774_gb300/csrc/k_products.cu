@@ -43,8 +43,8 @@ template <int V, int RL, int RS>
 __global__ void __launch_bounds__(PROD_THREADS, 1)
     k_products(const float* __restrict__ A, int m, const float* __restrict__ x,
                const float* __restrict__ y, float* __restrict__ r, float* __restrict__ gpart,
-               double* __restrict__ r2part, Ctrl* __restrict__ ctrl, int mode,
-               cudaGraphConditionalHandle cond, int set_cond, long long budget)
+               float* __restrict__ g_out, double* __restrict__ r2part, Ctrl* __restrict__ ctrl,
+               int mode, cudaGraphConditionalHandle cond, int set_cond, long long budget)
 {
     using S = ProdShape<V, RL, RS>;
     constexpr int N = S::N;
@@ -237,6 +237,57 @@ __global__ void __launch_bounds__(PROD_THREADS, 1)
             ctrl->r2 = t;
         }
     }
+    if (g_out == nullptr) return;
+
+    // ---------------- grid barrier, then g = sum of the G partials ----------------
+    // All G blocks are co-resident (cooperative launch, one block per SM), so
+    // a bounded spin on a monotone arrival counter is a grid barrier.
+    named_barrier(1, PROD_CONS);
+    if (tid == 0) {
+        __threadfence();
+        const unsigned long long t = atomicAdd(&ctrl->gbar, 1ull);
+        const unsigned long long target = (t / (unsigned long long)G + 1ull) * (unsigned long long)G;
+        const long long t0 = clock64();
+        while (ld_acquire_u64(&ctrl->gbar) < target) {
+            if (clock64() - t0 > budget) {
+                set_error(ctrl, ERR_TIMEOUT);
+                break;
+            }
+        }
+        __threadfence();
+    }
+    named_barrier(1, PROD_CONS);
+    // This block's slice of float4 columns; warp w sums partials w, w+16, ... and
+    // warp 0 adds the 16 warp sums in order (deterministic).
+    const int N4 = N / 4;
+    const int c0 = (int)(((long long)N4 * blockIdx.x) / G);
+    const int c1 = (int)(((long long)N4 * (blockIdx.x + 1)) / G);
+    const float4* gp4 = reinterpret_cast<const float4*>(gpart);
+    float4* sred = reinterpret_cast<float4*>(stage);   // [16][32], the stage ring is free
+    float4* g4 = reinterpret_cast<float4*>(g_out);
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int base = c0; base < c1; base += 32) {
+        const int c = base + lane;
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c < c1) {
+            for (int p = warp; p < G; p += PROD_CONS / 32) {
+                const float4 v = __ldcg(gp4 + (size_t)p * N4 + c);
+                s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+            }
+        }
+        sred[warp * 32 + lane] = s;
+        named_barrier(1, PROD_CONS);
+        if (warp == 0 && c < c1) {
+            float4 t = sred[lane];
+#pragma unroll
+            for (int w = 1; w < PROD_CONS / 32; ++w) {
+                const float4 v = sred[w * 32 + lane];
+                t.x += v.x; t.y += v.y; t.z += v.z; t.w += v.w;
+            }
+            g4[c] = t;
+        }
+        named_barrier(1, PROD_CONS);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -246,9 +297,19 @@ template <int V, int RL, int RS>
 static void launch_prod_t(int grid, const ProdArgs& a, cudaStream_t s)
 {
     using S = ProdShape<V, RL, RS>;
-    k_products<V, RL, RS><<<grid, PROD_THREADS, S::SMEM, s>>>(
-        a.A, a.m, a.x, a.y, a.r, a.gpart, a.r2part, a.ctrl, a.mode,
-        (cudaGraphConditionalHandle)a.cond, a.set_cond, a.budget);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(PROD_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = S::SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = a.g_out ? 1 : 0;   // the grid barrier needs co-resident blocks
+    cudaLaunchKernelEx(&cfg, k_products<V, RL, RS>, a.A, a.m, a.x, a.y, a.r, a.gpart, a.g_out,
+                       a.r2part, a.ctrl, a.mode, (cudaGraphConditionalHandle)a.cond, a.set_cond,
+                       a.budget);
 }
 
 template <int V, int RL, int RS>

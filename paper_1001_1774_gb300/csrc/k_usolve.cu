@@ -1,0 +1,370 @@
+// Rows a1-a5 of one IADM/FTVCS iteration in ONE thread-block-cluster kernel
+// (Xiao & Yang, Sec. 2.1-2.2):
+//   a1  multiplier update lambda <- lambda - beta (w - D u)   (eq. (udlamb), deferred
+//       from the previous iteration)
+//   a2  w <- shrink(D u + lambda/beta, 1/beta)                 (eq. (iadmw), reading C1)
+//   a3  right-hand side of the u-step in increment form
+//   a4  FFT solve (beta D^T D + mu/tau I) d = rhs, u^{k+1} = u^k + d  (eq. (eqnorm11) x beta)
+//   a5  binary64 norms of eq. (stop) and the stop decision
+//
+// A cluster of C blocks covers the n x n image; block k owns rows
+// [k R, (k+1) R), R = n / C.  Phase A: w-step and right-hand side of the
+// owned rows (plus one recomputed halo row), forward row FFTs (two real rows
+// packed per complex transform), half spectrum kept in this block's shared
+// memory.  Phase B: the n/2+1 spectrum columns are split over the blocks;
+// each gathers its columns from the owners' shared memory (distributed shared
+// memory), transforms along the columns, divides by beta Lambda_pq + mu/tau,
+// transforms back and scatters the columns home.  Phase C: inverse row FFTs,
+// u update and norms.  Cluster barriers separate the phases, so the whole
+// u-solve is one launch and the spectrum never leaves the chip.
+//
+// The solve is for the increment d = u^{k+1} - u^k:
+//   (beta D^T D + (mu/tau) I) d = D^T (beta (w^{k+1} - D u^k) - lambda^k) - mu g^k,
+// equal to eq. (eqnorm11) times beta in exact arithmetic; the large (mu/tau) u^k
+// term cancels analytically, so binary32 round-off scales with the step.
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+#include "fft.cuh"
+#include "kernels.h"
+
+namespace cg = cooperative_groups;
+
+namespace tvcs {
+
+template <int NN, int C>
+struct UsolveShape {
+    static constexpr int R = NN / C;            // rows per block
+    static constexpr int Q = NN / 2 + 1;        // half-spectrum columns
+    static constexpr int QC = (Q + C - 1) / C;  // columns per block in phase B
+    static constexpr int ROWFFT = (R / 2) * NN; // complex elements of the packed row transforms
+    static constexpr int COLFFT = QC * NN;
+    static constexpr int WORK = ROWFFT > COLFFT ? ROWFFT : COLFFT;
+    // shared memory carve-up (bytes, each region 16-byte aligned)
+    static constexpr size_t O_TW = 0;
+    static constexpr size_t O_S2 = O_TW + NN * 8;
+    static constexpr size_t O_U = O_S2 + ((NN * 4 + 15) / 16) * 16;
+    static constexpr size_t O_G = O_U + (R + 2) * NN * 4;
+    static constexpr size_t O_Y1 = O_G + R * NN * 4;
+    static constexpr size_t O_Y2 = O_Y1 + R * NN * 4;
+    static constexpr size_t O_SPEC = O_Y2 + (R + 1) * NN * 4;
+    static constexpr size_t O_WA = O_SPEC + ((R * Q * 8 + 15) / 16) * 16;
+    static constexpr size_t O_WB = O_WA + WORK * 8;
+    static constexpr size_t O_RED = O_WB + WORK * 8;
+    static constexpr size_t SMEM = O_RED + (32 + 2 * 16 + 2) * 8;
+    static_assert(NN % C == 0 && R % 2 == 0, "each block owns an even number of rows");
+    static_assert(SMEM <= 227 * 1024, "shared memory");
+};
+
+template <int NN, int C>
+__global__ void __launch_bounds__(256, 1) k_usolve_cluster(
+    float* __restrict__ u, float* __restrict__ wbuf, float* __restrict__ lbuf,
+    const float* __restrict__ g, float* __restrict__ rhs_out, const float2* __restrict__ tw_g,
+    const float* __restrict__ s2_g, float beta, float mu_over_tau, float mu,
+    Ctrl* __restrict__ ctrl, int mode)
+{
+    using S = UsolveShape<NN, C>;
+    constexpr int R = S::R, Q = S::Q, QC = S::QC, N = NN * NN;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* tw = reinterpret_cast<float2*>(smem + S::O_TW);
+    float* s2 = reinterpret_cast<float*>(smem + S::O_S2);
+    float* su = reinterpret_cast<float*>(smem + S::O_U);      // rows r0-1 .. r0+R
+    float* sg = reinterpret_cast<float*>(smem + S::O_G);      // rows r0 .. r0+R-1
+    float* sy1 = reinterpret_cast<float*>(smem + S::O_Y1);    // rows r0 .. r0+R-1
+    float* sy2 = reinterpret_cast<float*>(smem + S::O_Y2);    // rows r0-1 .. r0+R-1
+    float2* spec = reinterpret_cast<float2*>(smem + S::O_SPEC);  // R x Q, cluster-visible
+    float2* wa = reinterpret_cast<float2*>(smem + S::O_WA);
+    float2* wb = reinterpret_cast<float2*>(smem + S::O_WB);
+    double* red = reinterpret_cast<double*>(smem + S::O_RED);    // [32] block reduction
+    double* cred = red + 32;                                     // [C][2] cluster partials
+
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int r0 = rank * R;
+
+    if (mode == MODE_ITER) {
+        const int done = ctrl->done;   // stable during this kernel
+        if (rank == 0 && tid == 0) ctrl->skip = done;
+        if (done) return;              // uniform across the cluster: before any cluster barrier
+    }
+    const int pending = ctrl->pending;
+    const int par = ctrl->wpar;
+    const float* wsrc = wbuf + (size_t)par * 2 * N;
+    const float* lsrc = lbuf + (size_t)par * 2 * N;
+    float* wdst = wbuf + (size_t)(par ^ 1) * 2 * N;
+    float* ldst = lbuf + (size_t)(par ^ 1) * 2 * N;
+
+    // ---------------- phase A ----------------
+    for (int i = tid; i < NN; i += nthr) {
+        tw[i] = tw_g[i];
+        s2[i] = s2_g[i];
+    }
+    for (int i = tid; i < (R + 2) * NN; i += nthr) {
+        const int rr = i / NN, c = i - rr * NN;
+        const int row = (r0 - 1 + rr + NN) % NN;
+        su[i] = u[row * NN + c];
+    }
+    for (int i = tid; i < R * NN; i += nthr) sg[i] = g[r0 * NN + i];
+    __syncthreads();
+
+    const float inv_beta = 1.0f / beta;
+    for (int i = tid; i < (R + 1) * NN; i += nthr) {
+        const int rr = i / NN, c = i - rr * NN;      // rr = 0 is the halo row r0-1
+        const int row = (r0 - 1 + rr + NN) % NN;
+        const int cp = (c + 1 == NN) ? 0 : c + 1;
+        const float uc = su[rr * NN + c];
+        const float d1 = su[rr * NN + cp] - uc;
+        const float d2 = su[(rr + 1) * NN + c] - uc;
+        const int gi = row * NN + c;
+        float l1 = lsrc[gi], l2 = lsrc[N + gi];
+        if (pending) {  // eq. (udlamb) for the previous iteration
+            l1 -= beta * (wsrc[gi] - d1);
+            l2 -= beta * (wsrc[N + gi] - d2);
+        }
+        // eq. (iadmw), reading C1: shrink D_i u + lambda_i / beta; reading C6 at the tie
+        const float z1 = d1 + l1 * inv_beta, z2 = d2 + l2 * inv_beta;
+        const float nz = sqrtf(z1 * z1 + z2 * z2);
+        float w1 = 0.0f, w2 = 0.0f;
+        if (nz > inv_beta) {
+            const float s = (nz - inv_beta) / nz;
+            w1 = s * z1;
+            w2 = s * z2;
+        }
+        sy2[i] = beta * (w2 - d2) - l2;
+        if (rr >= 1) {
+            sy1[(rr - 1) * NN + c] = beta * (w1 - d1) - l1;
+            wdst[gi] = w1;
+            wdst[N + gi] = w2;
+            ldst[gi] = l1;
+            ldst[N + gi] = l2;
+        }
+    }
+    __syncthreads();
+    // rhs = D^T y - mu g, packed two rows per complex transform
+    for (int i = tid; i < (R / 2) * NN; i += nthr) {
+        const int j = i / NN, c = i - j * NN;
+        const int cm = (c == 0) ? NN - 1 : c - 1;
+        float v[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int lr = 2 * j + h;   // local owned row
+            const float dty = sy1[lr * NN + cm] - sy1[lr * NN + c] + sy2[lr * NN + c] -
+                              sy2[(lr + 1) * NN + c];
+            v[h] = dty - mu * sg[lr * NN + c];
+        }
+        wa[i] = make_float2(v[0], v[1]);
+        if (rhs_out) {
+            rhs_out[(r0 + 2 * j) * NN + c] = v[0];
+            rhs_out[(r0 + 2 * j + 1) * NN + c] = v[1];
+        }
+    }
+    __syncthreads();
+    float2* Zr = fft_block<NN, false>(wa, wb, tw, R / 2, NN);
+    // X_q = (Z_q + conj Z_{n-q})/2, Y_q = (Z_q - conj Z_{n-q})/(2i), q = 0 .. n/2
+    for (int i = tid; i < (R / 2) * Q; i += nthr) {
+        const int j = i / Q, q = i - j * Q;
+        const float2 a = Zr[j * NN + q];
+        const float2 b = Zr[j * NN + (NN - q) % NN];
+        spec[(2 * j) * Q + q] = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+        spec[(2 * j + 1) * Q + q] = make_float2(0.5f * (a.y + b.y), -0.5f * (a.x - b.x));
+    }
+    cluster.sync();   // every block's half spectrum is complete
+
+    // ---------------- phase B: columns ----------------
+    const int q0 = rank * QC;
+    const int ncol = max(0, min(QC, Q - q0));
+    for (int i = tid; i < ncol * NN; i += nthr) {
+        const int f = i % ncol, p = i / ncol;
+        const float2* own = cluster.map_shared_rank(spec, p / R);
+        wa[f * NN + p] = own[(p % R) * Q + q0 + f];
+    }
+    __syncthreads();
+    float2* X = fft_block<NN, false>(wa, wb, tw, ncol, NN);
+    float2* other = (X == wa) ? wb : wa;
+    for (int i = tid; i < ncol * NN; i += nthr) {
+        const int f = i / NN, p = i - f * NN;
+        const float d = beta * (s2[p] + s2[q0 + f]) + mu_over_tau;
+        float2 v = X[i];
+        v.x = v.x / d;
+        v.y = v.y / d;
+        X[i] = v;
+    }
+    __syncthreads();
+    float2* Y = fft_block<NN, true>(X, other, tw, ncol, NN);
+    for (int i = tid; i < ncol * NN; i += nthr) {
+        const int f = i % ncol, p = i / ncol;
+        float2* own = cluster.map_shared_rank(spec, p / R);
+        own[(p % R) * Q + q0 + f] = Y[f * NN + p];
+    }
+    cluster.sync();   // every column is home
+
+    // ---------------- phase C: inverse rows, u update, norms ----------------
+    for (int i = tid; i < (R / 2) * NN; i += nthr) {
+        const int j = i / NN, q = i - j * NN;
+        const bool lo = q < Q;
+        const int qq = lo ? q : NN - q;
+        float2 Xv = spec[(2 * j) * Q + qq];
+        float2 Yv = spec[(2 * j + 1) * Q + qq];
+        if (qq == 0 || 2 * qq == NN) {  // exactly real bins
+            Xv.y = 0.f;
+            Yv.y = 0.f;
+        }
+        if (!lo) {
+            Xv.y = -Xv.y;
+            Yv.y = -Yv.y;
+        }
+        wa[i] = make_float2(Xv.x - Yv.y, Xv.y + Yv.x);
+    }
+    __syncthreads();
+    float2* z = fft_block<NN, true>(wa, wb, tw, R / 2, NN);
+    const float sc = 1.0f / (float)(NN * NN);
+    double du2 = 0.0, u2 = 0.0;
+    for (int i = tid; i < (R / 2) * NN; i += nthr) {
+        const int j = i / NN, c = i - j * NN;
+        const float2 v = z[i];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int lr = 2 * j + h;
+            const float d = (h == 0 ? v.x : v.y) * sc;
+            const float o = su[(lr + 1) * NN + c];
+            const float nw = o + d;
+            const double e = (double)nw - (double)o;
+            du2 += e * e;
+            u2 += (double)o * o;
+            u[(r0 + lr) * NN + c] = nw;
+        }
+    }
+    const double bdu = block_sum(du2, red);
+    const double bu = block_sum(u2, red);
+    if (tid == 0) {
+        double* dst = cluster.map_shared_rank(cred, 0);
+        dst[2 * rank] = bdu;
+        dst[2 * rank + 1] = bu;
+    }
+    cluster.sync();   // partials delivered to block 0; every block has read wpar and done
+    if (rank == 0 && tid == 0) {
+        double tdu = 0.0, tu = 0.0;
+        for (int k = 0; k < C; ++k) {
+            tdu += cred[2 * k];
+            tu += cred[2 * k + 1];
+        }
+        ctrl->wpar = par ^ 1;
+        ctrl->du2 = tdu;
+        ctrl->u2 = tu;
+        ctrl->relchg = tu > 0.0 ? sqrt(tdu / tu) : (tdu > 0.0 ? INFINITY : 0.0);
+        if (mode == MODE_ITER) {
+            const int it = ctrl->it + 1;
+            ctrl->it = it;
+            bool stop = false;
+            if (!isfinite(tdu) || !isfinite(tu)) {
+                set_error(ctrl, ERR_NONFINITE);
+                stop = true;
+            }
+            const double tol = ctrl->tol;   // eq. (stop), reading C5
+            if (tol > 0.0 && (tu > 0.0 ? tdu <= tol * tol * tu : tdu == 0.0)) {
+                ctrl->stop_by_tol = 1;
+                stop = true;
+            }
+            if (it >= ctrl->max_iter || ctrl->error != ERR_NONE) stop = true;
+            if (stop) ctrl->done = 1;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side: cluster size per n (16 where it fits and the device allows it, else 8).
+// ---------------------------------------------------------------------------
+template <int NN, int C>
+static cudaError_t configure_usolve_t()
+{
+    using S = UsolveShape<NN, C>;
+    cudaError_t e = cudaFuncSetAttribute(k_usolve_cluster<NN, C>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+    if (e != cudaSuccess) return e;
+    if (C > 8)
+        e = cudaFuncSetAttribute(k_usolve_cluster<NN, C>,
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+}
+
+template <int NN, int C>
+static bool cluster_fits_t()
+{
+    using S = UsolveShape<NN, C>;
+    if (configure_usolve_t<NN, C>() != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = S::SMEM;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&nclusters, k_usolve_cluster<NN, C>, &cfg);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return nclusters >= 1;
+}
+
+template <int NN, int C>
+static void launch_usolve_t(const TvArgs& a, cudaStream_t s)
+{
+    using S = UsolveShape<NN, C>;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = S::SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_usolve_cluster<NN, C>, a.u, a.w, a.lam, a.g, a.rhs_out, a.tw, a.s2,
+                       a.beta, a.mu_over_tau, a.mu, a.ctrl, a.mode);
+}
+
+// Cluster sizes available per n: {16, 8} where both give an even row count.
+#define TVCS_USOLVE_TABLE(X) \
+    X(16, 8)                 \
+    X(32, 16) X(32, 8)       \
+    X(48, 8)                 \
+    X(64, 16) X(64, 8)       \
+    X(96, 16) X(96, 8)       \
+    X(128, 16) X(128, 8)     \
+    X(192, 16) X(192, 8)     \
+    X(256, 16)
+
+int usolve_choose_cluster(int n)
+{
+#define X(NN, C) \
+    if (n == NN && cluster_fits_t<NN, C>()) return C;
+    TVCS_USOLVE_TABLE(X)
+#undef X
+    return 0;
+}
+
+void launch_usolve(int n, int cluster, const TvArgs& a, cudaStream_t s)
+{
+#define X(NN, C)                           \
+    if (n == NN && cluster == C) {         \
+        launch_usolve_t<NN, C>(a, s);      \
+        return;                            \
+    }
+    TVCS_USOLVE_TABLE(X)
+#undef X
+}
+
+}  // namespace tvcs

@@ -25,8 +25,15 @@ struct TvArgs {
 };
 
 bool tv_supported(int n);
-// which: 1 w-step + row FFT, 2 column pass, 3 inverse rows, 4 final1, 5 final2
+// which: 4 final1 (pending multiplier update, TV, ||w - D u||), 5 final2 (dual residual)
 void launch_tv(int n, const TvArgs& a, int which, cudaStream_t s);
+
+// Rows a1-a5 (multiplier update, shrink, right-hand side, FFT u-solve, stop
+// norms) as one thread-block-cluster launch.  usolve_choose_cluster returns the
+// cluster size used for n on the current device (16 or 8), 0 if none fits;
+// it also sets the kernel attributes and must run before launch_usolve.
+int usolve_choose_cluster(int n);
+void launch_usolve(int n, int cluster, const TvArgs& a, cudaStream_t s);
 
 // Fused single-pass products r = A x - y, gpart = per-block partials of A^T r.
 struct ProdArgs {
@@ -36,6 +43,8 @@ struct ProdArgs {
     const float* y;     // nullable
     float* r;
     float* gpart;       // grid x N
+    float* g_out;       // nullable: when set, the blocks meet at a grid barrier (cooperative
+                        // launch) and reduce the partials into g_out = A^T r themselves
     double* r2part;     // grid
     Ctrl* ctrl;
     int mode;           // MODE_PLAIN or MODE_ITER

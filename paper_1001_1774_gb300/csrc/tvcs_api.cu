@@ -56,7 +56,7 @@ std::set<std::pair<int, int>> g_configured;  // (device, n) with the product ker
 }  // namespace
 
 struct tvcs_ctx {
-    int dev = 0, num_sms = 0;
+    int dev = 0, num_sms = 0, ucluster = 0;
     int m = 0, n = 0, N = 0, P = 0;
     double mu = 0, beta = 0, tol = 0, tau = 0;
     tvcs_options opt{};
@@ -125,9 +125,9 @@ void products(tvcs_ctx* h, const float* x, const float* y, float* r, float* gpar
     a.mode = mode;
     a.cond = cond;
     a.set_cond = set_cond;
+    a.g_out = g;
     a.budget = budget_of(h);
     launch_products(h->n, h->P, a, s);
-    if (g) launch_greduce(gpart, h->P, h->N, g, h->ctrl, mode, s);
 }
 
 // The body of one iteration (rows a1-a7), MODE_ITER: w-step and row FFT,
@@ -135,9 +135,7 @@ void products(tvcs_ctx* h, const float* x, const float* y, float* r, float* gpar
 void launch_iteration(tvcs_ctx* h, unsigned long long cond, int set_cond, cudaStream_t s)
 {
     TvArgs a = tv_args(h, MODE_ITER, false);
-    launch_tv(h->n, a, 1, s);
-    launch_tv(h->n, a, 2, s);
-    launch_tv(h->n, a, 3, s);
+    launch_usolve(h->n, h->ucluster, a, s);
     products(h, h->u, h->f, h->r, h->gpart, h->g, MODE_ITER, cond, set_cond, s);
 }
 
@@ -366,6 +364,9 @@ tvcs_status create_impl(tvcs_ctx* h, const float* A, uint64_t seed)
     CK(cudaEventCreate(&h->ev1));
     const size_t m = (size_t)h->m, N = (size_t)h->N;
     h->P = prod_grid(h->n, h->m, h->num_sms);
+    h->ucluster = usolve_choose_cluster(h->n);
+    if (h->ucluster == 0)
+        return fail(TVCS_ERR_UNSUPPORTED, "no thread-block cluster of 8 or 16 fits for n = %d", h->n);
     const size_t nparts = 2 * (size_t)((N + 255) / 256 + 1024);
     CKS(alloc((void**)&h->A, sizeof(float) * m * N));
     CKS(alloc((void**)&h->f, sizeof(float) * m));
@@ -643,22 +644,18 @@ tvcs_status tvcs_run_stage(tvcs_handle h, int stage)
 {
     CKS(check_handle(h));
     if (!h->state_ready) return fail(TVCS_ERR_INVALID_ARG, "no state: call tvcs_set_state or tvcs_solve first");
-    TvArgs a = tv_args(h, MODE_PLAIN, true);
-    switch (stage) {
-        case 1: launch_tv(h->n, a, 1, h->stream); break;
-        case 2:
-            launch_tv(h->n, a, 2, h->stream);
-            launch_tv(h->n, a, 3, h->stream);
-            break;
-        case 3:
-            refresh_products(h);
-            if (h->opt.algo == TVCS_ALGO_IADM) {
-                CKS(read_ctrl(h));
-                h->hctrl->pending = 1;
-                CKS(write_ctrl(h));
-            }
-            break;
-        default: return fail(TVCS_ERR_INVALID_ARG, "unknown stage %d", stage);
+    if (stage == 1) {
+        TvArgs a = tv_args(h, MODE_PLAIN, true);
+        launch_usolve(h->n, h->ucluster, a, h->stream);
+    } else if (stage == 2) {
+        refresh_products(h);
+        if (h->opt.algo == TVCS_ALGO_IADM) {
+            CKS(read_ctrl(h));
+            h->hctrl->pending = 1;
+            CKS(write_ctrl(h));
+        }
+    } else {
+        return fail(TVCS_ERR_INVALID_ARG, "unknown stage %d", stage);
     }
     return sync_and_check(h, "tvcs_run_stage");
 }
@@ -667,19 +664,15 @@ tvcs_status tvcs_time_stage(tvcs_handle h, int stage, int reps, double* ms)
 {
     CKS(check_handle(h));
     if (!ms || reps < 1) return fail(TVCS_ERR_INVALID_ARG, "ms must be non-NULL and reps >= 1");
-    if (stage < 1 || stage > 3) return fail(TVCS_ERR_INVALID_ARG, "unknown stage %d", stage);
+    if (stage < 1 || stage > 2) return fail(TVCS_ERR_INVALID_ARG, "unknown stage %d", stage);
     if (!h->state_ready) return fail(TVCS_ERR_INVALID_ARG, "no state: call tvcs_set_state or tvcs_solve first");
     TvArgs a = tv_args(h, MODE_PLAIN, false);
     CK(cudaEventRecord(h->ev0, h->stream));
     for (int i = 0; i < reps; ++i) {
-        if (stage == 1) {
-            launch_tv(h->n, a, 1, h->stream);
-        } else if (stage == 2) {
-            launch_tv(h->n, a, 2, h->stream);
-            launch_tv(h->n, a, 3, h->stream);
-        } else {
+        if (stage == 1)
+            launch_usolve(h->n, h->ucluster, a, h->stream);
+        else
             refresh_products(h);
-        }
     }
     CK(cudaEventRecord(h->ev1, h->stream));
     CKS(sync_and_check(h, "tvcs_time_stage"));

@@ -117,7 +117,7 @@ def test_stage_parity(tv, n, m):
     tv.tvcs_set_state(h, tv.TVCS_STATE_F, P.f)
     tv.tvcs_set_state(h, tv.TVCS_STATE_U, u0.ravel())
     tv.tvcs_set_state(h, tv.TVCS_STATE_LAMBDA, lam0.ravel())
-    # stage 1: w-step and right-hand side
+    # stage 1 (rows a1-a5): w-step, right-hand side, FFT u-solve
     tv.tvcs_run_stage(h, 1)
     w = tv.get_state(h, tv.TVCS_STATE_W).reshape(2, n, n)
     lam = tv.get_state(h, tv.TVCS_STATE_LAMBDA).reshape(2, n, n)
@@ -139,14 +139,13 @@ def test_stage_parity(tv, n, m):
     yp = w_ref - lam0 / P.beta
     b_paper = oracle.Dt(yp[0], yp[1]) + (P.mu / (P.beta * tau)) * (u64 - tau * g.reshape(n, n))
     u_paper = oracle.usolve(b_paper, P.mu / (P.beta * tau))
-    # stage 2: FFT solve for the increment, u^{k+1} = u^k + d
-    tv.tvcs_run_stage(h, 2)
+    # the FFT solve for the increment, u^{k+1} = u^k + d
     u1 = tv.get_state(h, tv.TVCS_STATE_U).reshape(n, n)
     u_ref = u64 + oracle.usolve(rhs.astype(np.float64) / P.beta, P.mu / (P.beta * tau))
     assert rel(u1, u_ref) <= 1e-6
     assert rel(u1, u_paper) <= 1e-5
-    # stage 3 then stage 1 again applies the deferred multiplier update (eq. (udlamb))
-    tv.tvcs_run_stage(h, 3)
+    # stage 2 (products) then stage 1 again applies the deferred multiplier update (eq. (udlamb))
+    tv.tvcs_run_stage(h, 2)
     tv.tvcs_run_stage(h, 1)
     lam2 = tv.get_state(h, tv.TVCS_STATE_LAMBDA).reshape(2, n, n)
     e1, e2 = oracle.D(u1.astype(np.float64))
