@@ -44,6 +44,11 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-solves", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["n128", "n256"], default="n128",
+                    help="n128: 128x128, m=4915, binary32 A (the benchmark workload); "
+                         "n256: 256x256, m=13107, A stored per --precision")
+    ap.add_argument("--precision", type=int, default=0,
+                    help="storage of A: 0 binary32, 1 bf16 hi+lo, 2 fp8 e4m3 + bf16 correction")
     ap.add_argument("--host-loop", action="store_true",
                     help="launch the iteration kernels from the host instead of the loop graph "
                          "(same kernels; for per-kernel profiler launch lists)")
@@ -67,8 +72,21 @@ def hbm_peak():
         return 6800.0, "fallback 6.8 TB/s"
 
 
-def workload_config(P, A_bytes):
-    return {"workload": "n128_m4915_fp32_single_image", "n": P.n, "m": P.m, "N": P.N,
+STORAGE = {0: ("fp32", 4), 1: ("bf16x2", 4), 2: ("fp8e4m3+bf16", 3)}
+
+
+def make_workload(args, rank):
+    import synth
+    if args.workload == "n256":
+        return synth.workload_n256() if rank == 0 else synth.make_problem(
+            256, 0.2, 2 + rank, 20, 5e2, 10.0, 0.0, ITERS_PER_RECON, 5e-3)
+    return synth.workload_n128() if rank == 0 else synth.make_problem(
+        128, 0.3, 1 + rank, 12, 1e3, 10.0, 0.0, ITERS_PER_RECON, 1e-3, rect_grid=True)
+
+
+def workload_config(P, A_bytes, precision=0):
+    name = "n%d_m%d_%s_single_image" % (P.n, P.m, STORAGE[precision][0])
+    return {"workload": name, "n": P.n, "m": P.m, "N": P.N, "A_storage": STORAGE[precision][0],
             "mu": P.mu, "beta": P.beta, "iters_per_recon": ITERS_PER_RECON,
             "A_bytes": A_bytes, "algo": "IADM",
             "l2": "inputs larger than L2 (A = %.0f MB > 129 MB); no flush" % (A_bytes / 1e6),
@@ -193,11 +211,11 @@ def run_ours(args):
         dist.barrier()
     import paper_1001_1774_gb300 as tv
 
-    P = synth.workload_n128() if rank == 0 else synth.make_problem(
-        128, 0.3, 1 + rank, 12, 1e3, 10.0, 0.0, ITERS_PER_RECON, 1e-3, rect_grid=True)
+    P = make_workload(args, rank)
     stream = torch.cuda.Stream()
     opt = tv.tvcs_default_options()
     opt.max_iter = ITERS_PER_RECON
+    opt.precision = args.precision
     opt.stream = ctypes_stream(stream)
     opt.host_loop = 1 if args.host_loop else 0
     with torch.cuda.stream(stream):
@@ -275,10 +293,10 @@ def run_ours(args):
     out = None
     if rank == 0:
         peak, peak_src = hbm_peak()
-        A_bytes = P.m * P.N * 4
+        A_bytes = P.m * P.N * STORAGE[args.precision][1] + (4 * P.m if args.precision == 2 else 0)
         alg_bytes = A_bytes + 4 * (P.N + 2 * P.m)
         achieved = alg_bytes / (prod_us * 1e-6) / 1e9
-        traffic = traffic_from_profile()
+        traffic = traffic_from_profile() if args.workload == "n128" else None
         value = ws * args.steps / (ms / 1e3)
         e2e_iters = ws * args.e2e_solves * ITERS_PER_RECON
         out = {
@@ -287,7 +305,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic (seeded phantom, Philox Gaussian A)",
             "recons_per_s": value / ITERS_PER_RECON,
-            "config": workload_config(P, A_bytes),
+            "config": workload_config(P, A_bytes, args.precision),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_products (fused A u - f and A^T r, one pass over A)",
@@ -334,8 +352,8 @@ def run_reference(args):
         return
     import oracle
     import synth
-    P = synth.workload_n128()
-    tau = oracle.default_tau(P.A, 100)
+    P = make_workload(args, 0)
+    tau = oracle.default_tau(P.A, 100 if args.workload == "n128" else 20)
     budget = 60.0
     # warm-up: W oracle iterations at most, bounded in time
     t0 = time.perf_counter()

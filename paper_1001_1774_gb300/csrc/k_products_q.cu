@@ -1,0 +1,550 @@
+// Rows a6-a7 with A in reduced or split precision, and for images whose rows
+// are too long for one block: r = A x - y, partials of g = A^T r, one pass
+// over A (Xiao & Yang, eq. (line): g_k = A^T (A u^k - f)).
+//
+// Storage of A (m x N, row-major planes):
+//   FP32      one binary32 plane;
+//   BF16X2    A = hi + lo, hi = bf16(A), lo = bf16(A - hi) (both round to
+//             nearest even); hi + lo is exact in binary32 and within 2^-16 |A|;
+//   FP8_BF16  A = s_i q + c, s_i = max_j |A_ij| / 448 per row, q = e4m3(A / s_i)
+//             (round to nearest even, saturating), c = bf16(A - s_i q).
+// Products accumulate in binary32; ||r||^2 in binary64.
+//
+// A cluster of CS blocks shares each row: block k of the cluster owns columns
+// [k N/CS, (k+1) N/CS).  Each streams its column slice of the rows through a
+// shared-memory ring filled by bulk asynchronous copies (TMA, one mbarrier per
+// stage), forms its part of every row's dot product, and sends it to every
+// block of the cluster: a store into the peer's shared memory followed by a
+// remote mbarrier arrival (release at cluster scope).  Each block waits, with a
+// bounded spin, for the CS parts of a row, adds them in rank order (every block
+// gets the same r_i), and folds r_i times its slice of the row into per-thread
+// accumulators.  A decoded row slice stays in registers between the dot and the
+// update.  Cluster c writes its partial of A^T r to gpart[c]; the partials are
+// summed afterwards in a fixed order.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace tvcs {
+
+constexpr int QPROD_YMAX = 1024;
+
+template <int PREC>
+struct QPrec;
+
+template <>
+struct QPrec<0> {   // binary32
+    static constexpr int PLANE_BYTES_NUM = 4;   // bytes per element in the stage
+};
+template <>
+struct QPrec<1> {   // bf16 hi + lo
+    static constexpr int PLANE_BYTES_NUM = 4;
+};
+template <>
+struct QPrec<2> {   // fp8 e4m3 + bf16 correction
+    static constexpr int PLANE_BYTES_NUM = 3;
+};
+
+template <int PREC, int V, int CS, int CONS, int NST>
+struct QShape {
+    static constexpr int NS = 4 * CONS * V;        // columns per block (the slice)
+    static constexpr int N = NS * CS;
+    static constexpr int THREADS = CONS + 32;
+    static constexpr size_t STAGE_BYTES = (size_t)NS * QPrec<PREC>::PLANE_BYTES_NUM;
+    static constexpr size_t O_BAR = NST * STAGE_BYTES;               // full[NST], empty[NST], xbar[2]
+    static constexpr size_t O_RED = O_BAR + (2 * NST + 2) * 8;       // [2][CONS/32] floats
+    static constexpr size_t O_XRED = O_RED + 2 * (CONS / 32) * 4;    // [2][CS] floats
+    static constexpr size_t O_DRED = ((O_XRED + 2 * CS * 4 + 15) / 16) * 16;   // [32] doubles
+    static constexpr size_t O_Y = O_DRED + 32 * 8;                   // y of the rows
+    static constexpr size_t O_S = O_Y + QPROD_YMAX * 4;              // row scales (FP8)
+    static constexpr size_t SMEM = O_S + QPROD_YMAX * 4 + 16;
+    static_assert(STAGE_BYTES % 16 == 0, "TMA sizes are multiples of 16 bytes");
+    static_assert(CONS % 32 == 0 && CONS <= 512, "consumer warps");
+    static_assert(SMEM <= 227 * 1024, "shared memory");
+};
+
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t map_remote(uint32_t local_smem, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_smem), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void st_remote_f32(uint32_t addr, float v)
+{
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t addr)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                     : "memory");
+}
+
+__device__ __forceinline__ float bf16_lo_f(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi_f(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+// Decodes column chunk `ch` (4 consecutive columns) of the row slice at `sb`.
+template <int PREC, int NS>
+__device__ __forceinline__ float4 decode_chunk(const unsigned char* sb, int ch, float scale)
+{
+    if constexpr (PREC == 0) {
+        return reinterpret_cast<const float4*>(sb)[ch];
+    } else if constexpr (PREC == 1) {
+        const uint2 h = reinterpret_cast<const uint2*>(sb)[ch];
+        const uint2 l = reinterpret_cast<const uint2*>(sb + (size_t)NS * 2)[ch];
+        return make_float4(bf16_lo_f(h.x) + bf16_lo_f(l.x), bf16_hi_f(h.x) + bf16_hi_f(l.x),
+                           bf16_lo_f(h.y) + bf16_lo_f(l.y), bf16_hi_f(h.y) + bf16_hi_f(l.y));
+    } else {
+        const uint32_t q = reinterpret_cast<const uint32_t*>(sb)[ch];
+        const uint2 c = reinterpret_cast<const uint2*>(sb + (size_t)NS)[ch];
+        __nv_fp8x2_storage_t q01 = (__nv_fp8x2_storage_t)(q & 0xffffu);
+        __nv_fp8x2_storage_t q23 = (__nv_fp8x2_storage_t)(q >> 16);
+        const float2 a01 = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(q01, __NV_E4M3)));
+        const float2 a23 = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(q23, __NV_E4M3)));
+        return make_float4(fmaf(scale, a01.x, bf16_lo_f(c.x)), fmaf(scale, a01.y, bf16_hi_f(c.x)),
+                           fmaf(scale, a23.x, bf16_lo_f(c.y)), fmaf(scale, a23.y, bf16_hi_f(c.y)));
+    }
+}
+
+template <int PREC, int V, int CS, int CONS, int NST>
+__global__ void __launch_bounds__(CONS + 32, 1)
+    k_products_q(const unsigned char* __restrict__ P0, const unsigned char* __restrict__ P1,
+                 const float* __restrict__ rscale, int m, const float* __restrict__ x,
+                 const float* __restrict__ y, float* __restrict__ r, float* __restrict__ gpart,
+                 double* __restrict__ r2part, Ctrl* __restrict__ ctrl, int mode,
+                 cudaGraphConditionalHandle cond, int set_cond, long long budget)
+{
+    using S = QShape<PREC, V, CS, CONS, NST>;
+    constexpr int NS = S::NS, N = S::N, WARPS = CONS / 32;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::O_BAR);
+    uint64_t* empty = full + NST;
+    uint64_t* xbar = empty + NST;                                   // [2]
+    float* red = reinterpret_cast<float*>(smem + S::O_RED);         // [2][WARPS]
+    float* xred = reinterpret_cast<float*>(smem + S::O_XRED);       // [2][CS]
+    double* dred = reinterpret_cast<double*>(smem + S::O_DRED);
+    float* sy = reinterpret_cast<float*>(smem + S::O_Y);
+    float* ss = reinterpret_cast<float*>(smem + S::O_S);
+    int* sflag = reinterpret_cast<int*>(smem + S::O_S + QPROD_YMAX * 4);
+
+    const int tid = threadIdx.x;
+    const uint32_t rank = CS > 1 ? cluster_rank() : 0u;
+    const int cidx = blockIdx.x / CS;          // cluster index = partial index
+    const int G = gridDim.x / CS;              // number of clusters
+    if (mode == MODE_ITER) {
+        const int skip = ctrl->skip;
+        if (blockIdx.x == 0 && tid == 0) {
+            if (!skip && ctrl->algo == 0) ctrl->pending = 1;
+            if (set_cond) {
+                const int lc = ++ctrl->loops;
+                const int cont =
+                    (!ctrl->done && ctrl->error == ERR_NONE && lc < ctrl->loops_max) ? 1 : 0;
+                cudaGraphSetConditional(cond, (unsigned)cont);
+            }
+        }
+        if (skip) return;   // uniform over the grid
+    }
+    const int i0 = (int)(((long long)m * cidx) / G);
+    const int i1 = (int)(((long long)m * (cidx + 1)) / G);
+    const int nrows = i1 - i0;
+
+    if (tid == 0) {
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], WARPS);
+        }
+        mbar_init(&xbar[0], CS);
+        mbar_init(&xbar[1], CS);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if constexpr (CS > 1) cluster_sync_all();   // peers' barriers exist before any remote arrival
+
+    if (tid >= CONS) {
+        // ---------------- producer warp: row slices into the ring ----------------
+        if (tid == CONS) {
+            const uint64_t pol = l2_policy_evict_first();
+            const size_t col0 = (size_t)rank * NS;
+            bool ok = true;
+            for (int s = 0; s < nrows; ++s) {
+                const int slot = s % NST;
+                if (s >= NST && !mbar_wait(&empty[slot], ((s / NST) - 1) & 1, budget)) {
+                    set_error(ctrl, ERR_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+                const size_t row = (size_t)(i0 + s);
+                unsigned char* dst = smem + (size_t)slot * S::STAGE_BYTES;
+                if constexpr (PREC == 0) {
+                    mbar_arrive_expect_tx(&full[slot], NS * 4u);
+                    tma_load_1d(dst, P0 + (row * N + col0) * 4, NS * 4u, &full[slot], pol);
+                } else if constexpr (PREC == 1) {
+                    mbar_arrive_expect_tx(&full[slot], NS * 4u);
+                    tma_load_1d(dst, P0 + (row * N + col0) * 2, NS * 2u, &full[slot], pol);
+                    tma_load_1d(dst + (size_t)NS * 2, P1 + (row * N + col0) * 2, NS * 2u,
+                                &full[slot], pol);
+                } else {
+                    mbar_arrive_expect_tx(&full[slot], NS * 3u);
+                    tma_load_1d(dst, P0 + (row * N + col0), NS * 1u, &full[slot], pol);
+                    tma_load_1d(dst + (size_t)NS, P1 + (row * N + col0) * 2, NS * 2u,
+                                &full[slot], pol);
+                }
+            }
+            const int first = ok ? max(0, nrows - NST) : nrows;
+            for (int s = first; s < nrows; ++s) mbar_wait(&full[s % NST], (s / NST) & 1, budget);
+        }
+        __syncwarp();
+        // stay for the final cluster barrier: no block leaves while peers may still write to it
+        if constexpr (CS > 1) cluster_sync_all();
+        return;
+    }
+
+    // ---------------- consumers ----------------
+    const bool y_in_smem = (y != nullptr) && nrows <= QPROD_YMAX;
+    const bool s_in_smem = (PREC == 2) && nrows <= QPROD_YMAX;
+    if (y_in_smem)
+        for (int i = tid; i < nrows; i += CONS) sy[i] = y[i0 + i];
+    if (s_in_smem)
+        for (int i = tid; i < nrows; i += CONS) ss[i] = rscale[i0 + i];
+    const float4* x4 = reinterpret_cast<const float4*>(x + (size_t)rank * NS);
+    float4 xu[V], acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        xu[v] = x4[tid + v * CONS];
+        acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    named_barrier(1, CONS);
+    uint32_t xred_remote[CS];
+    uint32_t xbar_remote[CS];
+#pragma unroll
+    for (int k = 0; k < CS; ++k) {
+        xred_remote[k] = CS > 1 ? map_remote(smem_u32(xred), (uint32_t)k) : 0u;
+        xbar_remote[k] = CS > 1 ? map_remote(smem_u32(xbar), (uint32_t)k) : 0u;
+    }
+    double r2 = 0.0;
+    bool ok = true;
+    for (int s = 0; s < nrows; ++s) {
+        const int slot = s % NST;
+        if (ok && !mbar_wait(&full[slot], (s / NST) & 1, budget)) {
+            set_error(ctrl, ERR_TIMEOUT);
+            ok = false;
+        }
+        const unsigned char* sb = smem + (size_t)slot * S::STAGE_BYTES;
+        float scale = 1.0f;
+        if constexpr (PREC == 2) scale = s_in_smem ? ss[s] : rscale[i0 + s];
+        float yi = 0.f;
+        if (y != nullptr) yi = y_in_smem ? sy[s] : y[i0 + s];
+        float d = 0.f;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const float4 a = decode_chunk<PREC, NS>(sb, tid + v * CONS, scale);
+            d = fmaf(a.x, xu[v].x, d);
+            d = fmaf(a.y, xu[v].y, d);
+            d = fmaf(a.z, xu[v].z, d);
+            d = fmaf(a.w, xu[v].w, d);
+        }
+        d = warp_sum(d);
+        float* rb = red + (s & 1) * WARPS;
+        if ((tid & 31) == 0) rb[tid >> 5] = d;
+        named_barrier(1, CONS);
+        float part = 0.f;
+#pragma unroll
+        for (int w = 0; w < WARPS; ++w) part += rb[w];
+        float dot;
+        if constexpr (CS == 1) {
+            dot = part;
+        } else {
+            // send this block's part to every block of the cluster, then wait for all CS parts
+            const int par = s & 1;
+            if (tid < CS) {
+                st_remote_f32(xred_remote[tid] + (uint32_t)((par * CS + rank) * 4), part);
+                mbar_arrive_remote(xbar_remote[tid] + (uint32_t)(par * 8));
+            }
+            const uint32_t phase = (uint32_t)((s >> 1) & 1);
+            if (ok) {
+                if (!mbar_try_wait_cluster(&xbar[par], phase)) {
+                    const long long t0 = clock64();
+                    while (!mbar_try_wait_cluster(&xbar[par], phase)) {
+                        if (clock64() - t0 > budget) {
+                            set_error(ctrl, ERR_TIMEOUT);
+                            ok = false;
+                            break;
+                        }
+                    }
+                }
+            }
+            dot = 0.f;
+#pragma unroll
+            for (int k = 0; k < CS; ++k) dot += xred[par * CS + k];
+        }
+        const float ri = dot - yi;
+        if (rank == 0 && tid == 0) {
+            r[i0 + s] = ri;
+            r2 += (double)ri * (double)ri;
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const float4 a = decode_chunk<PREC, NS>(sb, tid + v * CONS, scale);   // decoded again
+            acc[v].x = fmaf(ri, a.x, acc[v].x);
+            acc[v].y = fmaf(ri, a.y, acc[v].y);
+            acc[v].z = fmaf(ri, a.z, acc[v].z);
+            acc[v].w = fmaf(ri, a.w, acc[v].w);
+        }
+        // this warp is done with the slot: release it to the producer
+        __syncwarp();
+        if ((tid & 31) == 0) mbar_arrive(&empty[slot]);
+    }
+
+    // ---------------- epilogue ----------------
+    float4* out4 = reinterpret_cast<float4*>(gpart + (size_t)cidx * N + (size_t)rank * NS);
+#pragma unroll
+    for (int v = 0; v < V; ++v) out4[tid + v * CONS] = acc[v];
+    if (tid == 0) {
+        sflag[0] = 0;
+        if (rank == 0) {   // one arrival per cluster: the last of the G clusters sums ||r||^2
+            r2part[cidx] = r2;
+            __threadfence();
+            const unsigned t = atomicAdd(&ctrl->ticket_prod, 1u);
+            if (t == (unsigned)G - 1u) {
+                __threadfence();
+                ctrl->ticket_prod = 0u;
+                sflag[0] = 1;
+            }
+        }
+    }
+    named_barrier(1, CONS);
+    if (sflag[0]) {
+        double v = 0.0;
+        for (int b = tid; b < G; b += CONS) v += r2part[b];
+        v = warp_sum(v);
+        if ((tid & 31) == 0) dred[tid >> 5] = v;
+        named_barrier(1, CONS);
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < WARPS; ++w) t += dred[w];
+            ctrl->r2 = t;
+        }
+    }
+    __syncwarp();
+    if constexpr (CS > 1) cluster_sync_all();
+}
+
+// ---------------------------------------------------------------------------
+// Quantisation of a binary32 A into the split / reduced storages.
+// ---------------------------------------------------------------------------
+__global__ void k_split_bf16x2(const float4* __restrict__ A, uint2* __restrict__ hi,
+                               uint2* __restrict__ lo, long long total4)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total4;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float4 a = A[i];
+        const float av[4] = {a.x, a.y, a.z, a.w};
+        unsigned short h[4], l[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const __nv_bfloat16 hb = __float2bfloat16_rn(av[k]);
+            const float rem = av[k] - __bfloat162float(hb);    // exact
+            const __nv_bfloat16 lb = __float2bfloat16_rn(rem);
+            h[k] = __bfloat16_as_ushort(hb);
+            l[k] = __bfloat16_as_ushort(lb);
+        }
+        hi[i] = make_uint2((uint32_t)h[0] | ((uint32_t)h[1] << 16), (uint32_t)h[2] | ((uint32_t)h[3] << 16));
+        lo[i] = make_uint2((uint32_t)l[0] | ((uint32_t)l[1] << 16), (uint32_t)l[2] | ((uint32_t)l[3] << 16));
+    }
+}
+
+// One block per row: s = max|A_i.| / 448, q = e4m3(A / s), c = bf16(A - s q).
+__global__ void __launch_bounds__(256) k_quant_fp8(const float* __restrict__ A, int N,
+                                                   unsigned char* __restrict__ q,
+                                                   unsigned short* __restrict__ c,
+                                                   float* __restrict__ scale)
+{
+    __shared__ float wmax[8];
+    const float* a = A + (size_t)blockIdx.x * N;
+    float mx = 0.f;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) mx = fmaxf(mx, fabsf(a[j]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < 8; ++w) t = fmaxf(t, wmax[w]);
+        wmax[0] = t;
+    }
+    __syncthreads();
+    const float s = wmax[0] > 0.f ? wmax[0] / 448.0f : 1.0f;
+    if (threadIdx.x == 0) scale[blockIdx.x] = s;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        const float v = a[j];
+        const __nv_fp8_storage_t qq = __nv_cvt_float_to_fp8(v / s, __NV_SATFINITE, __NV_E4M3);
+        const float qf = __half2float(__half(__nv_cvt_fp8_to_halfraw(qq, __NV_E4M3)));
+        const float rem = __fmaf_rn(-s, qf, v);   // one rounding of v - s q
+        q[(size_t)blockIdx.x * N + j] = (unsigned char)qq;
+        c[(size_t)blockIdx.x * N + j] = __bfloat16_as_ushort(__float2bfloat16_rn(rem));
+    }
+}
+
+void launch_split_bf16x2(const float* A, void* hi, void* lo, long long count, cudaStream_t s)
+{
+    const long long total4 = count / 4;
+    int grid = (int)((total4 + 255) / 256);
+    if (grid > 152 * 16) grid = 152 * 16;
+    k_split_bf16x2<<<grid, 256, 0, s>>>(reinterpret_cast<const float4*>(A),
+                                        reinterpret_cast<uint2*>(hi), reinterpret_cast<uint2*>(lo),
+                                        total4);
+}
+
+void launch_quant_fp8(const float* A, int m, int N, void* q, void* c, float* scale, cudaStream_t s)
+{
+    k_quant_fp8<<<m, 256, 0, s>>>(A, N, reinterpret_cast<unsigned char*>(q),
+                                  reinterpret_cast<unsigned short*>(c), scale);
+}
+
+// ---------------------------------------------------------------------------
+// Shape table: (precision, n) -> (V, CS, CONS, NST).  N = n^2 = 4 CONS V CS.
+// ---------------------------------------------------------------------------
+#define TVCS_QPROD_TABLE(X)                                                              \
+    X(0, 192, 9, 2, 512, 3) X(0, 256, 8, 4, 512, 3)                                      \
+    X(1, 32, 1, 1, 256, 3) X(1, 64, 2, 1, 512, 3) X(1, 128, 8, 1, 512, 3)                \
+    X(1, 192, 9, 2, 512, 3) X(1, 256, 8, 4, 512, 3)                                      \
+    X(2, 32, 1, 1, 256, 4) X(2, 64, 2, 1, 512, 4) X(2, 128, 8, 1, 512, 4)                \
+    X(2, 192, 9, 2, 512, 4) X(2, 256, 8, 4, 512, 4)
+
+template <int PREC, int V, int CS, int CONS, int NST>
+static cudaError_t qconfigure_t()
+{
+    using S = QShape<PREC, V, CS, CONS, NST>;
+    return cudaFuncSetAttribute(k_products_q<PREC, V, CS, CONS, NST>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+}
+
+template <int PREC, int V, int CS, int CONS, int NST>
+static int qmax_clusters_t()
+{
+    using S = QShape<PREC, V, CS, CONS, NST>;
+    if (qconfigure_t<PREC, V, CS, CONS, NST>() != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (CS == 1) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        return sms;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CS, 1, 1);
+    cfg.blockDim = dim3(S::THREADS, 1, 1);
+    cfg.dynamicSmemBytes = S::SMEM;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_products_q<PREC, V, CS, CONS, NST>, &cfg) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+template <int PREC, int V, int CS, int CONS, int NST>
+static void qlaunch_t(int clusters, const QProdArgs& a, cudaStream_t s)
+{
+    using S = QShape<PREC, V, CS, CONS, NST>;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(clusters * CS, 1, 1);
+    cfg.blockDim = dim3(S::THREADS, 1, 1);
+    cfg.dynamicSmemBytes = S::SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = CS > 1 ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, k_products_q<PREC, V, CS, CONS, NST>, a.P0, a.P1, a.rscale, a.m, a.x,
+                       a.y, a.r, a.gpart, a.r2part, a.ctrl, a.mode,
+                       (cudaGraphConditionalHandle)a.cond, a.set_cond, a.budget);
+}
+
+bool qprod_supported(int prec, int n)
+{
+#define X(PR, NN, V, CS, CONS, NST) \
+    if (prec == PR && n == NN) return true;
+    TVCS_QPROD_TABLE(X)
+#undef X
+    return false;
+}
+
+int qprod_cluster_size(int prec, int n)
+{
+#define X(PR, NN, V, CS, CONS, NST) \
+    if (prec == PR && n == NN) return CS;
+    TVCS_QPROD_TABLE(X)
+#undef X
+    return 0;
+}
+
+// Number of clusters (= partials) to launch: every row group on the GPU at once.
+int qprod_grid_clusters(int prec, int n, int m)
+{
+#define X(PR, NN, V, CS, CONS, NST)                                   \
+    if (prec == PR && n == NN) {                                      \
+        int c = qmax_clusters_t<PR, V, CS, CONS, NST>();              \
+        if (c <= 0) return 0;                                         \
+        return c < m ? c : m;                                         \
+    }
+    TVCS_QPROD_TABLE(X)
+#undef X
+    return 0;
+}
+
+void launch_qproducts(int prec, int n, int clusters, const QProdArgs& a, cudaStream_t s)
+{
+#define X(PR, NN, V, CS, CONS, NST)                          \
+    if (prec == PR && n == NN) {                             \
+        qlaunch_t<PR, V, CS, CONS, NST>(clusters, a, s);     \
+        return;                                              \
+    }
+    TVCS_QPROD_TABLE(X)
+#undef X
+}
+
+}  // namespace tvcs

@@ -50,7 +50,8 @@ struct UsolveShape {
     static constexpr size_t O_SPEC = O_Y2 + (R + 1) * NN * 4;
     static constexpr size_t O_WA = O_SPEC + ((R * Q * 8 + 15) / 16) * 16;
     static constexpr size_t O_WB = O_WA + WORK * 8;
-    static constexpr size_t O_RED = O_WB + WORK * 8;
+    static constexpr size_t O_WL = O_WB + WORK * 8;            // w1, w2, l1, l2 of rows r0-1 .. r0+R-1
+    static constexpr size_t O_RED = O_WL + 4 * (R + 1) * NN * 4;
     static constexpr size_t SMEM = O_RED + (32 + 2 * 16 + 2) * 8;
     static_assert(NN % C == 0 && R % 2 == 0, "each block owns an even number of rows");
     static_assert(SMEM <= 227 * 1024, "shared memory");
@@ -75,6 +76,7 @@ __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
     float2* spec = reinterpret_cast<float2*>(smem + S::O_SPEC);  // R x Q, cluster-visible
     float2* wa = reinterpret_cast<float2*>(smem + S::O_WA);
     float2* wb = reinterpret_cast<float2*>(smem + S::O_WB);
+    float* swl = reinterpret_cast<float*>(smem + S::O_WL);       // [4][(R+1) NN]
     double* red = reinterpret_cast<double*>(smem + S::O_RED);    // [32] block reduction
     double* cred = red + 32;                                     // [C][2] cluster partials
 
@@ -106,6 +108,16 @@ __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
         su[i] = u[row * NN + c];
     }
     for (int i = tid; i < R * NN; i += nthr) sg[i] = g[r0 * NN + i];
+    // w and lambda of rows r0-1 .. r0+R-1, all loads issued before any store below
+    constexpr int WL = (R + 1) * NN;
+    for (int i = tid; i < WL; i += nthr) {
+        const int rr = i / NN, c = i - rr * NN;
+        const int gi = ((r0 - 1 + rr + NN) % NN) * NN + c;
+        swl[i] = wsrc[gi];
+        swl[WL + i] = wsrc[N + gi];
+        swl[2 * WL + i] = lsrc[gi];
+        swl[3 * WL + i] = lsrc[N + gi];
+    }
     __syncthreads();
 
     const float inv_beta = 1.0f / beta;
@@ -117,10 +129,10 @@ __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
         const float d1 = su[rr * NN + cp] - uc;
         const float d2 = su[(rr + 1) * NN + c] - uc;
         const int gi = row * NN + c;
-        float l1 = lsrc[gi], l2 = lsrc[N + gi];
+        float l1 = swl[2 * WL + i], l2 = swl[3 * WL + i];
         if (pending) {  // eq. (udlamb) for the previous iteration
-            l1 -= beta * (wsrc[gi] - d1);
-            l2 -= beta * (wsrc[N + gi] - d2);
+            l1 -= beta * (swl[i] - d1);
+            l2 -= beta * (swl[WL + i] - d2);
         }
         // eq. (iadmw), reading C1: shrink D_i u + lambda_i / beta; reading C6 at the tie
         const float z1 = d1 + l1 * inv_beta, z2 = d2 + l2 * inv_beta;

@@ -61,6 +61,31 @@ void launch_products(int n, int grid, const ProdArgs& a, cudaStream_t s);
 void launch_greduce(const float* gpart, int P, int N, float* g, const Ctrl* ctrl, int mode,
                     cudaStream_t s);
 
+// Products with A in binary32 (n = 192, 256), bf16 hi+lo, or fp8 e4m3 + bf16
+// correction: clusters of CS blocks split each row's columns.
+struct QProdArgs {
+    const unsigned char* P0;  // binary32 plane | bf16 hi plane | e4m3 plane
+    const unsigned char* P1;  // unused | bf16 lo plane | bf16 correction plane
+    const float* rscale;      // per-row scale (fp8 storage), else unused
+    int m;
+    const float* x;
+    const float* y;           // nullable
+    float* r;
+    float* gpart;             // clusters x N
+    double* r2part;           // clusters
+    Ctrl* ctrl;
+    int mode;
+    unsigned long long cond;
+    int set_cond;
+    long long budget;
+};
+bool qprod_supported(int prec, int n);
+int qprod_cluster_size(int prec, int n);
+int qprod_grid_clusters(int prec, int n, int m);   // sets kernel attributes; 0 if none fits
+void launch_qproducts(int prec, int n, int clusters, const QProdArgs& a, cudaStream_t s);
+void launch_split_bf16x2(const float* A, void* hi, void* lo, long long count, cudaStream_t s);
+void launch_quant_fp8(const float* A, int m, int N, void* q, void* c, float* scale, cudaStream_t s);
+
 // gather: out = scale * sum_p gpart[p], ctrl->vec2 = ||out||^2 (binary64)
 void launch_gather(const float* gpart, int P, int N, float scale, float* out, double* part,
                    Ctrl* ctrl, cudaStream_t s);

@@ -64,7 +64,10 @@ struct tvcs_ctx {
     bool own_stream = false;
     cudaStream_t cap_stream = nullptr;
     // device buffers
-    float* A = nullptr;
+    float* A = nullptr;            // binary32 A for the single-block-row product kernel (n <= 128)
+    bool use_q = false;            // products by clusters / reduced precision (k_products_q)
+    unsigned char *P0 = nullptr, *P1 = nullptr;   // storage planes of A on that path
+    float* rscale = nullptr;       // per-row scales of the fp8 storage
     float *f = nullptr, *u = nullptr, *w = nullptr, *lam = nullptr, *g = nullptr, *r = nullptr,
           *rhs = nullptr, *zeroN = nullptr;
     float *tx = nullptr, *ty = nullptr, *tr = nullptr, *tg = nullptr;
@@ -113,6 +116,26 @@ TvArgs tv_args(tvcs_ctx* h, int mode, bool stage_outputs)
 void products(tvcs_ctx* h, const float* x, const float* y, float* r, float* gpart, float* g,
               int mode, unsigned long long cond, int set_cond, cudaStream_t s)
 {
+    if (h->use_q) {
+        QProdArgs q{};
+        q.P0 = h->P0;
+        q.P1 = h->P1;
+        q.rscale = h->rscale;
+        q.m = h->m;
+        q.x = x;
+        q.y = y;
+        q.r = r;
+        q.gpart = gpart;
+        q.r2part = h->r2part;
+        q.ctrl = h->ctrl;
+        q.mode = mode;
+        q.cond = cond;
+        q.set_cond = set_cond;
+        q.budget = budget_of(h);
+        launch_qproducts(h->opt.precision, h->n, h->P, q, s);
+        if (g) launch_greduce(gpart, h->P, h->N, g, h->ctrl, mode, s);
+        return;
+    }
     ProdArgs a{};
     a.A = h->A;
     a.m = h->m;
@@ -170,7 +193,7 @@ void free_ctx(tvcs_ctx* h)
     if (h->graph) cudaGraphDestroy(h->graph);
     void* bufs[] = {h->A, h->f, h->u, h->w, h->lam, h->g, h->r, h->rhs, h->zeroN, h->tx, h->ty,
                     h->tr, h->tg, h->spec, h->tw, h->s2, h->gpart, h->gpart2, h->r2part, h->part,
-                    h->ctrl};
+                    h->ctrl, h->P0, h->P1, h->rscale};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (h->hctrl) cudaFreeHost(h->hctrl);
@@ -363,11 +386,20 @@ tvcs_status create_impl(tvcs_ctx* h, const float* A, uint64_t seed)
     CK(cudaEventCreate(&h->ev0));
     CK(cudaEventCreate(&h->ev1));
     const size_t m = (size_t)h->m, N = (size_t)h->N;
-    h->P = prod_grid(h->n, h->m, h->num_sms);
+    const int prec = h->opt.precision;
+    h->use_q = !(prec == TVCS_PREC_FP32 && prod_supported(h->n));
+    if (h->use_q) {
+        h->P = qprod_grid_clusters(prec, h->n, h->m);
+        if (h->P == 0)
+            return fail(TVCS_ERR_UNSUPPORTED, "no cluster of the product kernel fits (n = %d)", h->n);
+    } else {
+        h->P = prod_grid(h->n, h->m, h->num_sms);
+    }
     h->ucluster = usolve_choose_cluster(h->n);
     if (h->ucluster == 0)
         return fail(TVCS_ERR_UNSUPPORTED, "no thread-block cluster of 8 or 16 fits for n = %d", h->n);
     const size_t nparts = 2 * (size_t)((N + 255) / 256 + 1024);
+    // A: binary32 for the classic path and as the source of the split storages.
     CKS(alloc((void**)&h->A, sizeof(float) * m * N));
     CKS(alloc((void**)&h->f, sizeof(float) * m));
     CKS(alloc((void**)&h->r, sizeof(float) * m));
@@ -417,6 +449,26 @@ tvcs_status create_impl(tvcs_ctx* h, const float* A, uint64_t seed)
         launch_gen_gauss(h->A, h->m, (int64_t)N, seed, scale, h->stream);
     }
     CKS(sync_and_check(h, "uploading A"));
+    if (h->use_q) {
+        if (prec == TVCS_PREC_FP32) {
+            h->P0 = reinterpret_cast<unsigned char*>(h->A);   // the plane is A itself
+            h->A = nullptr;
+        } else if (prec == TVCS_PREC_BF16X2) {
+            CKS(alloc((void**)&h->P0, sizeof(uint16_t) * m * N));
+            CKS(alloc((void**)&h->P1, sizeof(uint16_t) * m * N));
+            launch_split_bf16x2(h->A, h->P0, h->P1, (long long)(m * N), h->stream);
+        } else {
+            CKS(alloc((void**)&h->P0, m * N));
+            CKS(alloc((void**)&h->P1, sizeof(uint16_t) * m * N));
+            CKS(alloc((void**)&h->rscale, sizeof(float) * m));
+            launch_quant_fp8(h->A, h->m, h->N, h->P0, h->P1, h->rscale, h->stream);
+        }
+        CKS(sync_and_check(h, "storing A"));
+        if (h->A) {   // the binary32 copy is no longer needed
+            cudaFree(h->A);
+            h->A = nullptr;
+        }
+    }
     if (h->opt.tau > 0.0) {
         h->tau = h->opt.tau;
     } else {
@@ -437,9 +489,11 @@ tvcs_status copy_out(tvcs_ctx* h, float* dst, const float* src, size_t count)
     return TVCS_OK;
 }
 
-bool valid_n(int n)
+bool valid_n(int n, int prec)
 {
-    return tv_supported(n) && prod_supported(n);
+    if (!tv_supported(n)) return false;
+    if (prec == TVCS_PREC_FP32) return prod_supported(n) || qprod_supported(prec, n);
+    return qprod_supported(prec, n);
 }
 
 }  // namespace
@@ -486,8 +540,6 @@ tvcs_status tvcs_create(tvcs_handle* out, const float* A, uint64_t seed, int m, 
     if (!out) return fail(TVCS_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (m < 1 || m > (1 << 24)) return fail(TVCS_ERR_INVALID_ARG, "m = %d outside [1, 2^24]", m);
-    if (!valid_n(n))
-        return fail(TVCS_ERR_INVALID_ARG, "n = %d not supported (16, 32, 48, 64, 96, 128)", n);
     if (!(mu > 0.0) || !isfinite(mu)) return fail(TVCS_ERR_INVALID_ARG, "mu must be > 0");
     if (!(beta > 0.0) || !isfinite(beta)) return fail(TVCS_ERR_INVALID_ARG, "beta must be > 0");
     if (!(tol >= 0.0) || !isfinite(tol)) return fail(TVCS_ERR_INVALID_ARG, "tol must be >= 0");
@@ -498,11 +550,13 @@ tvcs_status tvcs_create(tvcs_handle* out, const float* A, uint64_t seed, int m, 
         return fail(TVCS_ERR_INVALID_ARG, "unknown algo %d", o.algo);
     if (o.init < TVCS_INIT_ATF || o.init > TVCS_INIT_GIVEN)
         return fail(TVCS_ERR_INVALID_ARG, "unknown init %d", o.init);
-    if (o.precision != TVCS_PREC_FP32) {
-        if (o.precision == TVCS_PREC_BF16X2 || o.precision == TVCS_PREC_FP8_BF16)
-            return fail(TVCS_ERR_UNSUPPORTED, "precision %d not available for the single-image path", o.precision);
+    if (o.precision < TVCS_PREC_FP32 || o.precision > TVCS_PREC_FP8_BF16)
         return fail(TVCS_ERR_INVALID_ARG, "unknown precision %d", o.precision);
-    }
+    if (!valid_n(n, o.precision))
+        return fail(TVCS_ERR_INVALID_ARG,
+                    "n = %d not supported with precision %d (binary32: 16, 32, 48, 64, 96, 128, 192, "
+                    "256; bf16x2 / fp8: 32, 64, 128, 192, 256)",
+                    n, o.precision);
     if (!isfinite(o.tau)) return fail(TVCS_ERR_INVALID_ARG, "tau must be finite");
     if (o.max_iter <= 0) o.max_iter = 500;
     tvcs_ctx* h = new (std::nothrow) tvcs_ctx();

@@ -247,6 +247,12 @@ def workload_n32() -> Problem:
     return make_problem(32, 0.3, 0, 6, 1e3, 10.0, 1e-4, 500, 1e-3, name="n32_m307")
 
 
+def workload_n256() -> Problem:
+    """Single 256 x 256 image, m = 13107 (ratio 0.2), 20 ellipses, noise 5e-3 * RMS,
+    mu = 5e2, beta = 10 (the reduced-precision storage workload; A is 3.4 GB in binary32)."""
+    return make_problem(256, 0.2, 2, 20, 5e2, 10.0, 0.0, 300, 5e-3, name="n256_m13107")
+
+
 def workload_n128() -> Problem:
     """Single 128 x 128 image, m = 4915 (ratio 0.3), 12 ellipses plus a random
     rectangle grid, noise 1e-3 * RMS, mu = 1e3, beta = 10, 300 iterations."""
