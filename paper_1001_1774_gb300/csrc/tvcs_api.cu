@@ -371,7 +371,7 @@ tvcs_status create_impl(tvcs_ctx* h, const float* A, uint64_t seed)
     CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->dev));
     {
         std::lock_guard<std::mutex> lk(g_cfg_mutex);
-        if (!g_configured.count({h->dev, h->n})) {
+        if (prod_supported(h->n) && !g_configured.count({h->dev, h->n})) {
             CK(prod_configure(h->n));
             g_configured.insert({h->dev, h->n});
         }
