@@ -17,10 +17,11 @@
 // block of the cluster: a store into the peer's shared memory followed by a
 // remote mbarrier arrival (release at cluster scope).  Each block waits, with a
 // bounded spin, for the CS parts of a row, adds them in rank order (every block
-// gets the same r_i), and folds r_i times its slice of the row into per-thread
-// accumulators.  A decoded row slice stays in registers between the dot and the
-// update.  Cluster c writes its partial of A^T r to gpart[c]; the partials are
-// summed afterwards in a fixed order.
+// gets the same r_i), and folds r_i times its slice of the row (decoded again
+// from shared memory) into per-thread accumulators.  The exchange is software-
+// pipelined: the part of row s+1 is sent before the parts of row s are awaited.
+// Cluster c writes its partial of A^T r to gpart[c]; the partials are summed
+// afterwards in a fixed order.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -54,10 +55,10 @@ struct QShape {
     static constexpr int N = NS * CS;
     static constexpr int THREADS = CONS + 32;
     static constexpr size_t STAGE_BYTES = (size_t)NS * QPrec<PREC>::PLANE_BYTES_NUM;
-    static constexpr size_t O_BAR = NST * STAGE_BYTES;               // full[NST], empty[NST], xbar[2]
-    static constexpr size_t O_RED = O_BAR + (2 * NST + 2) * 8;       // [2][CONS/32] floats
-    static constexpr size_t O_XRED = O_RED + 2 * (CONS / 32) * 4;    // [2][CS] floats
-    static constexpr size_t O_DRED = ((O_XRED + 2 * CS * 4 + 15) / 16) * 16;   // [32] doubles
+    static constexpr size_t O_BAR = NST * STAGE_BYTES;               // full[NST], empty[NST], xbar[4]
+    static constexpr size_t O_RED = O_BAR + (2 * NST + 4) * 8;       // [2][CONS/32] floats
+    static constexpr size_t O_XRED = O_RED + 2 * (CONS / 32) * 4;    // [4][CS] floats
+    static constexpr size_t O_DRED = ((O_XRED + 4 * CS * 4 + 15) / 16) * 16;   // [32] doubles
     static constexpr size_t O_Y = O_DRED + 32 * 8;                   // y of the rows
     static constexpr size_t O_S = O_Y + QPROD_YMAX * 4;              // row scales (FP8)
     static constexpr size_t SMEM = O_S + QPROD_YMAX * 4 + 16;
@@ -149,9 +150,9 @@ __global__ void __launch_bounds__(CONS + 32, 1)
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::O_BAR);
     uint64_t* empty = full + NST;
-    uint64_t* xbar = empty + NST;                                   // [2]
+    uint64_t* xbar = empty + NST;                                   // [4]
     float* red = reinterpret_cast<float*>(smem + S::O_RED);         // [2][WARPS]
-    float* xred = reinterpret_cast<float*>(smem + S::O_XRED);       // [2][CS]
+    float* xred = reinterpret_cast<float*>(smem + S::O_XRED);       // [4][CS]
     double* dred = reinterpret_cast<double*>(smem + S::O_DRED);
     float* sy = reinterpret_cast<float*>(smem + S::O_Y);
     float* ss = reinterpret_cast<float*>(smem + S::O_S);
@@ -183,8 +184,7 @@ __global__ void __launch_bounds__(CONS + 32, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], WARPS);
         }
-        mbar_init(&xbar[0], CS);
-        mbar_init(&xbar[1], CS);
+        for (int b = 0; b < 4; ++b) mbar_init(&xbar[b], CS);
         fence_mbar_init();
     }
     __syncthreads();
@@ -253,7 +253,8 @@ __global__ void __launch_bounds__(CONS + 32, 1)
     }
     double r2 = 0.0;
     bool ok = true;
-    for (int s = 0; s < nrows; ++s) {
+    // This block's part of the dot product of row s (waits for the row's stage).
+    auto part_of_row = [&](int s) -> float {
         const int slot = s % NST;
         if (ok && !mbar_wait(&full[slot], (s / NST) & 1, budget)) {
             set_error(ctrl, ERR_TIMEOUT);
@@ -262,8 +263,6 @@ __global__ void __launch_bounds__(CONS + 32, 1)
         const unsigned char* sb = smem + (size_t)slot * S::STAGE_BYTES;
         float scale = 1.0f;
         if constexpr (PREC == 2) scale = s_in_smem ? ss[s] : rscale[i0 + s];
-        float yi = 0.f;
-        if (y != nullptr) yi = y_in_smem ? sy[s] : y[i0 + s];
         float d = 0.f;
 #pragma unroll
         for (int v = 0; v < V; ++v) {
@@ -280,47 +279,71 @@ __global__ void __launch_bounds__(CONS + 32, 1)
         float part = 0.f;
 #pragma unroll
         for (int w = 0; w < WARPS; ++w) part += rb[w];
+        return part;
+    };
+    // Sends the part of row s to every block of the cluster (slot s mod 4).
+    auto send_part = [&](int s, float part) {
+        if constexpr (CS > 1) {
+            const int b = s & 3;
+            if (tid < CS) {
+                st_remote_f32(xred_remote[tid] + (uint32_t)((b * CS + rank) * 4), part);
+                mbar_arrive_remote(xbar_remote[tid] + (uint32_t)(b * 8));
+            }
+        }
+    };
+    // Software pipeline: the part of row s+1 is computed and sent before the
+    // cluster's parts of row s are awaited, hiding the exchange latency.  A
+    // peer writes slot s mod 4 for row s+4 only after receiving this block's
+    // part of row s+2, which is sent after this block has read row s: four
+    // slots make the reuse safe.
+    float part_next = nrows > 0 ? part_of_row(0) : 0.f;
+    if (nrows > 0) send_part(0, part_next);
+    for (int s = 0; s < nrows; ++s) {
+        const float part_s = part_next;
+        if (s + 1 < nrows) {
+            part_next = part_of_row(s + 1);
+            send_part(s + 1, part_next);
+        }
         float dot;
         if constexpr (CS == 1) {
-            dot = part;
+            dot = part_s;
         } else {
-            // send this block's part to every block of the cluster, then wait for all CS parts
-            const int par = s & 1;
-            if (tid < CS) {
-                st_remote_f32(xred_remote[tid] + (uint32_t)((par * CS + rank) * 4), part);
-                mbar_arrive_remote(xbar_remote[tid] + (uint32_t)(par * 8));
-            }
-            const uint32_t phase = (uint32_t)((s >> 1) & 1);
-            if (ok) {
-                if (!mbar_try_wait_cluster(&xbar[par], phase)) {
-                    const long long t0 = clock64();
-                    while (!mbar_try_wait_cluster(&xbar[par], phase)) {
-                        if (clock64() - t0 > budget) {
-                            set_error(ctrl, ERR_TIMEOUT);
-                            ok = false;
-                            break;
-                        }
+            const int b = s & 3;
+            const uint32_t phase = (uint32_t)((s >> 2) & 1);
+            if (ok && !mbar_try_wait_cluster(&xbar[b], phase)) {
+                const long long t0 = clock64();
+                while (!mbar_try_wait_cluster(&xbar[b], phase)) {
+                    if (clock64() - t0 > budget) {
+                        set_error(ctrl, ERR_TIMEOUT);
+                        ok = false;
+                        break;
                     }
                 }
             }
             dot = 0.f;
 #pragma unroll
-            for (int k = 0; k < CS; ++k) dot += xred[par * CS + k];
+            for (int k = 0; k < CS; ++k) dot += xred[b * CS + k];
         }
+        float yi = 0.f;
+        if (y != nullptr) yi = y_in_smem ? sy[s] : y[i0 + s];
         const float ri = dot - yi;
         if (rank == 0 && tid == 0) {
             r[i0 + s] = ri;
             r2 += (double)ri * (double)ri;
         }
+        const int slot = s % NST;
+        const unsigned char* sb = smem + (size_t)slot * S::STAGE_BYTES;
+        float scale = 1.0f;
+        if constexpr (PREC == 2) scale = s_in_smem ? ss[s] : rscale[i0 + s];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            const float4 a = decode_chunk<PREC, NS>(sb, tid + v * CONS, scale);   // decoded again
+            const float4 a = decode_chunk<PREC, NS>(sb, tid + v * CONS, scale);
             acc[v].x = fmaf(ri, a.x, acc[v].x);
             acc[v].y = fmaf(ri, a.y, acc[v].y);
             acc[v].z = fmaf(ri, a.z, acc[v].z);
             acc[v].w = fmaf(ri, a.w, acc[v].w);
         }
-        // this warp is done with the slot: release it to the producer
+        // this warp is done with row s: release its slot to the producer
         __syncwarp();
         if ((tid & 31) == 0) mbar_arrive(&empty[slot]);
     }

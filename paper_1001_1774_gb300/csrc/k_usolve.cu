@@ -98,26 +98,29 @@ __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
     float* ldst = lbuf + (size_t)(par ^ 1) * 2 * N;
 
     // ---------------- phase A ----------------
-    for (int i = tid; i < NN; i += nthr) {
-        tw[i] = tw_g[i];
-        s2[i] = s2_g[i];
-    }
-    for (int i = tid; i < (R + 2) * NN; i += nthr) {
-        const int rr = i / NN, c = i - rr * NN;
-        const int row = (r0 - 1 + rr + NN) % NN;
-        su[i] = u[row * NN + c];
-    }
-    for (int i = tid; i < R * NN; i += nthr) sg[i] = g[r0 * NN + i];
-    // w and lambda of rows r0-1 .. r0+R-1, all loads issued before any store below
+    // Every input of the block in one round of asynchronous 16-byte copies:
+    // twiddles, 4 sin^2 table, u rows r0-1 .. r0+R, g rows r0 .. r0+R-1, and
+    // w, lambda rows r0-1 .. r0+R-1.
+    constexpr int CPR = NN / 4;       // 16-byte chunks per row
     constexpr int WL = (R + 1) * NN;
-    for (int i = tid; i < WL; i += nthr) {
-        const int rr = i / NN, c = i - rr * NN;
-        const int gi = ((r0 - 1 + rr + NN) % NN) * NN + c;
-        swl[i] = wsrc[gi];
-        swl[WL + i] = wsrc[N + gi];
-        swl[2 * WL + i] = lsrc[gi];
-        swl[3 * WL + i] = lsrc[N + gi];
+    for (int i = tid; i < NN / 2; i += nthr) cp_async16(tw + 2 * i, tw_g + 2 * i);
+    for (int i = tid; i < CPR; i += nthr) cp_async16(s2 + 4 * i, s2_g + 4 * i);
+    for (int i = tid; i < (R + 2) * CPR; i += nthr) {
+        const int rr = i / CPR, c4 = i - rr * CPR;
+        const int row = (r0 - 1 + rr + NN) % NN;
+        cp_async16(su + rr * NN + 4 * c4, u + row * NN + 4 * c4);
     }
+    for (int i = tid; i < R * CPR; i += nthr) cp_async16(sg + 4 * i, g + r0 * NN + 4 * i);
+    for (int i = tid; i < (R + 1) * CPR; i += nthr) {
+        const int rr = i / CPR, c4 = i - rr * CPR;
+        const int gi = ((r0 - 1 + rr + NN) % NN) * NN + 4 * c4;
+        const int li = rr * NN + 4 * c4;
+        cp_async16(swl + li, wsrc + gi);
+        cp_async16(swl + WL + li, wsrc + N + gi);
+        cp_async16(swl + 2 * WL + li, lsrc + gi);
+        cp_async16(swl + 3 * WL + li, lsrc + N + gi);
+    }
+    cp_async_wait_all();
     __syncthreads();
 
     const float inv_beta = 1.0f / beta;
@@ -186,10 +189,24 @@ __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
     // ---------------- phase B: columns ----------------
     const int q0 = rank * QC;
     const int ncol = max(0, min(QC, Q - q0));
-    for (int i = tid; i < ncol * NN; i += nthr) {
-        const int f = i % ncol, p = i / ncol;
-        const float2* own = cluster.map_shared_rank(spec, p / R);
-        wa[f * NN + p] = own[(p % R) * Q + q0 + f];
+    {
+        // all remote loads first (independent, in registers), then the local stores
+        constexpr int GPT = (QC * NN + 255) / 256;
+        float2 v[GPT];
+#pragma unroll
+        for (int k = 0; k < GPT; ++k) {
+            const int i = tid + k * nthr;
+            if (i < ncol * NN) {
+                const int f = i % ncol, p = i / ncol;
+                const float2* own = cluster.map_shared_rank(spec, p / R);
+                v[k] = own[(p % R) * Q + q0 + f];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < GPT; ++k) {
+            const int i = tid + k * nthr;
+            if (i < ncol * NN) wa[(i % ncol) * NN + i / ncol] = v[k];
+        }
     }
     __syncthreads();
     float2* X = fft_block<NN, false>(wa, wb, tw, ncol, NN);
@@ -231,7 +248,8 @@ __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
     __syncthreads();
     float2* z = fft_block<NN, true>(wa, wb, tw, R / 2, NN);
     const float sc = 1.0f / (float)(NN * NN);
-    double du2 = 0.0, u2 = 0.0;
+    // per-thread sums of a few squares in binary32, combined across threads in binary64
+    float du2f = 0.f, u2f = 0.f;
     for (int i = tid; i < (R / 2) * NN; i += nthr) {
         const int j = i / NN, c = i - j * NN;
         const float2 v = z[i];
@@ -240,15 +258,13 @@ __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
             const int lr = 2 * j + h;
             const float d = (h == 0 ? v.x : v.y) * sc;
             const float o = su[(lr + 1) * NN + c];
-            const float nw = o + d;
-            const double e = (double)nw - (double)o;
-            du2 += e * e;
-            u2 += (double)o * o;
-            u[(r0 + lr) * NN + c] = nw;
+            du2f = fmaf(d, d, du2f);
+            u2f = fmaf(o, o, u2f);
+            u[(r0 + lr) * NN + c] = o + d;
         }
     }
-    const double bdu = block_sum(du2, red);
-    const double bu = block_sum(u2, red);
+    const double bdu = block_sum((double)du2f, red);
+    const double bu = block_sum((double)u2f, red);
     if (tid == 0) {
         double* dst = cluster.map_shared_rank(cred, 0);
         dst[2 * rank] = bdu;
