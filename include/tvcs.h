@@ -120,9 +120,11 @@ tvcs_status tvcs_solve(tvcs_handle h, const float* f, float* u, tvcs_result* res
  * Solves `count` problems.  hs[i] are handles, f[i] (m_i values) and u[i]
  * (n_i*n_i values) host or device pointers; mu (nullable) overrides each
  * handle's mu; res (nullable) receives count summaries.  When every hs[i] is
- * the same handle the products run as batched GEMMs over all images;
- * otherwise the problems are solved one after another on the first handle's
- * stream.
+ * the same handle created with precision TVCS_PREC_BF16X2 (and count <= 256),
+ * all images iterate together: their u-steps run as one batched launch and
+ * their products as tensor-core GEMMs (see tvcs_apply_batched); each image
+ * stops on its own eq. (stop).  Otherwise the problems are solved one after
+ * another, each on its handle's stream.
  */
 tvcs_status tvcs_solve_batched(const tvcs_handle* hs, int count, const float* const* f,
                                float* const* u, const double* mu, tvcs_result* res);
@@ -172,6 +174,16 @@ tvcs_status tvcs_run_stage(tvcs_handle h, int stage);
  * the state is that of `reps` applications of the stage (stage 2 leaves it
  * unchanged).  Requires a state (tvcs_solve or tvcs_set_state first). */
 tvcs_status tvcs_time_stage(tvcs_handle h, int stage, int reps, double* ms);
+
+/* Products for `count` images that share the handle's A, the batched form of
+ * tvcs_apply (the two matrix-vector products of eq. (line) for many images at
+ * once): R = A X - Y and G = A^T R, computed as tensor-core GEMMs on bfloat16
+ * hi+lo splits of A and of the operands (X_hi A_hi + X_lo A_hi + X_hi A_lo,
+ * binary32 accumulation).  X: count x n*n, Y: count x m (nullable), R: count x m,
+ * G: count x n*n, image after image, host or device.  Requires a handle created
+ * with precision TVCS_PREC_BF16X2, n*n a multiple of 128 and 1 <= count <= 256. */
+tvcs_status tvcs_apply_batched(tvcs_handle h, int count, const float* X, const float* Y,
+                               float* R, float* G);
 
 /* Products alone on caller data: r = A x - y (y nullable: r = A x) and
  * g = A^T r, with the handle's stored A.  x: N, y: m, r: m, g: N. */

@@ -35,7 +35,7 @@ TVCS_INIT_ATF, TVCS_INIT_ZERO, TVCS_INIT_GIVEN = 0, 1, 2
 EXPORTED = ["tvcs_default_options", "tvcs_create", "tvcs_solve", "tvcs_solve_batched",
             "tvcs_destroy", "tvcs_last_error", "tvcs_get_tau", "tvcs_get_state",
             "tvcs_set_state", "tvcs_iterate", "tvcs_run_stage", "tvcs_time_stage", "tvcs_apply",
-            "tvcs_apply_noalloc"]
+            "tvcs_apply_noalloc", "tvcs_apply_batched"]
 
 
 class tvcs_options(ctypes.Structure):
@@ -85,6 +85,7 @@ def _load() -> ctypes.CDLL:
         "tvcs_time_stage": ([H, i, i, ctypes.POINTER(d)], i),
         "tvcs_apply": ([H, vp, vp, vp, vp], i),
         "tvcs_apply_noalloc": ([vp, i, i, vp, vp, vp, vp, vp], i),
+        "tvcs_apply_batched": ([H, i, vp, vp, vp, vp], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -234,6 +235,13 @@ def tvcs_apply_noalloc(A, m: int, n: int, x, y, r, g, stream: int | None = None)
     _check(_lib.tvcs_apply_noalloc(_ptr(A, m * N), int(m), int(n), _ptr(x, N),
                                    _ptr(y, m) if y is not None else None, _ptr(r, m, True),
                                    _ptr(g, N, True), ctypes.c_void_p(stream or 0)))
+
+
+def tvcs_apply_batched(h: Handle, count: int, X, Y, R, G) -> None:
+    """R = A X - Y and G = A^T R for `count` images (rows of X, Y, R, G)."""
+    _check(_lib.tvcs_apply_batched(h.ptr, int(count), _ptr(X, count * h.N),
+                                   _ptr(Y, count * h.m) if Y is not None else None,
+                                   _ptr(R, count * h.m, True), _ptr(G, count * h.N, True)))
 
 
 def tvcs_last_error() -> str:

@@ -1,0 +1,411 @@
+// Many images sharing one encoding matrix (row a8): IADM for every image at
+// once, with the two products of all images as tcgen05 BF16x3 GEMMs (k_gemm.cu)
+// and the u-steps as one batched thread-block-cluster launch (k_usolve.cu).
+//
+// Loop body (a CUDA graph with a WHILE node): batched u-solve (rows a1-a5 per
+// image, with per-image mu, stop test and control block) -> GEMM R = A U - F ->
+// fix-up (R, its bf16 planes, ||r_b||^2) -> GEMM G = A^T R -> fix-up (G) ->
+// loop condition (any image still running).  Images that met eq. (stop) skip
+// their u-steps; the GEMMs keep all columns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "ctx.h"
+#include "kernels.h"
+
+namespace tvcs {
+
+// ctrls[b].r2 = sum over tiles of the fix-up's partials of ||r_b||^2.
+__global__ void k_batch_r2(const double* __restrict__ r2part, int tiles, Ctrl* __restrict__ ctrls)
+{
+    __shared__ double red[32];
+    const double s = block_sum_array(r2part + (size_t)blockIdx.x * tiles, tiles, 1, red);
+    if (threadIdx.x == 0) ctrls[blockIdx.x].r2 = s;
+}
+
+// Continue while any image runs and the loop bound holds.
+__global__ void k_batch_cond(const Ctrl* __restrict__ ctrls, int count, Ctrl* __restrict__ bctrl,
+                             cudaGraphConditionalHandle cond, int set_cond)
+{
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    for (int b = threadIdx.x; b < count; b += blockDim.x)
+        if (!ctrls[b].done && ctrls[b].error == ERR_NONE) atomicOr(&any, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int lc = ++bctrl->loops;
+        const int cont = (any && lc < bctrl->loops_max) ? 1 : 0;
+        bctrl->done = !cont;
+        if (set_cond) cudaGraphSetConditional(cond, (unsigned)cont);
+    }
+}
+
+// A_eff = hi + lo (exact in binary32) from the two bf16 planes.
+__global__ void k_join_bf16x2(const unsigned short* __restrict__ hi, const unsigned short* __restrict__ lo,
+                              float* __restrict__ out, long long count)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = __uint_as_float((unsigned)hi[i] << 16) + __uint_as_float((unsigned)lo[i] << 16);
+}
+
+__global__ void k_scale_copy(const float* __restrict__ in, float* __restrict__ out, long long n, float s)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = s * in[i];
+}
+
+namespace {
+
+#define BCK(call)                                                                             \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return set_last_error(e_ == cudaErrorMemoryAllocation ? TVCS_ERR_OOM : TVCS_ERR_CUDA, \
+                                  "%s failed: %s", #call, cudaGetErrorString(e_));            \
+    } while (0)
+
+#define BCKS(expr)                                  \
+    do {                                            \
+        tvcs_status s_ = (expr);                    \
+        if (s_ != TVCS_OK) return s_;               \
+    } while (0)
+
+tvcs_status balloc(void** p, size_t bytes)
+{
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return set_last_error(TVCS_ERR_OOM, "cudaMalloc of %zu bytes failed", bytes);
+    }
+    return TVCS_OK;
+}
+
+void free_buffers(tvcs_batch* b)
+{
+    void* bufs[] = {b->U, b->W, b->L, b->G, b->R, b->F, b->mu, b->Uh, b->Ul, b->Rh, b->Rl,
+                    b->ctrls, b->bctrl, b->r2part, b->part, b->ws, b->tsb1, b->ss1, b->tsb2, b->ss2};
+    for (void* p : bufs)
+        if (p) cudaFree(p);
+    if (b->hctrls) cudaFreeHost(b->hctrls);
+    if (b->hbctrl) cudaFreeHost(b->hbctrl);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->U = b->W = b->L = b->G = b->R = b->F = b->mu = nullptr;
+    b->Uh = b->Ul = b->Rh = b->Rl = nullptr;
+    b->ctrls = b->bctrl = b->hctrls = b->hbctrl = nullptr;
+    b->r2part = b->part = nullptr;
+    b->ws = nullptr;
+    b->tsb1 = b->ss1 = b->tsb2 = b->ss2 = nullptr;
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->cap = 0;
+}
+
+tvcs_status upload_plan(const GemmPlan& p, int** tsb, int** ss, cudaStream_t s)
+{
+    BCKS(balloc((void**)tsb, sizeof(int) * p.tile_seg_begin.size()));
+    BCKS(balloc((void**)ss, sizeof(int) * (p.seg_slot.size() ? p.seg_slot.size() : 1)));
+    BCK(cudaMemcpyAsync(*tsb, p.tile_seg_begin.data(), sizeof(int) * p.tile_seg_begin.size(),
+                        cudaMemcpyHostToDevice, s));
+    if (!p.seg_slot.empty())
+        BCK(cudaMemcpyAsync(*ss, p.seg_slot.data(), sizeof(int) * p.seg_slot.size(),
+                            cudaMemcpyHostToDevice, s));
+    return TVCS_OK;
+}
+
+tvcs_status make_maps(tvcs_ctx* h, int count)
+{
+    tvcs_batch* b = h->batch;
+    bool ok = make_bf16_map(&b->mAh, h->P0, h->N, h->m, h->N, 128) &&
+              make_bf16_map(&b->mAl, h->P1, h->N, h->m, h->N, 128) &&
+              make_bf16_map(&b->mAth, b->Ath, h->m, h->N, b->mpad, 128) &&
+              make_bf16_map(&b->mAtl, b->Atl, h->m, h->N, b->mpad, 128) &&
+              make_bf16_map(&b->mUh, b->Uh, h->N, count, h->N, 256) &&
+              make_bf16_map(&b->mUl, b->Ul, h->N, count, h->N, 256) &&
+              make_bf16_map(&b->mRh, b->Rh, h->m, count, b->mpad, 256) &&
+              make_bf16_map(&b->mRl, b->Rl, h->m, count, b->mpad, 256);
+    if (!ok) return set_last_error(TVCS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    return TVCS_OK;
+}
+
+// Buffers for `count` images (reallocated when count grows), A^T planes, plans.
+tvcs_status ensure_batch(tvcs_ctx* h, int count)
+{
+    if (h->opt.precision != TVCS_PREC_BF16X2)
+        return set_last_error(TVCS_ERR_UNSUPPORTED,
+                              "the shared-A batched path needs A stored as bf16 hi+lo "
+                              "(precision TVCS_PREC_BF16X2)");
+    if (count > 256)
+        return set_last_error(TVCS_ERR_INVALID_ARG, "at most 256 images per batched call");
+    if (h->N % 128 != 0)
+        return set_last_error(TVCS_ERR_UNSUPPORTED, "batched path needs n*n a multiple of 128");
+    if (!h->batch) {
+        h->batch = new (std::nothrow) tvcs_batch();
+        if (!h->batch) return set_last_error(TVCS_ERR_OOM, "host allocation failed");
+    }
+    tvcs_batch* b = h->batch;
+    cudaStream_t s = h->stream;
+    const size_t N = h->N, m = h->m;
+    if (!b->Ath) {
+        b->mpad = (int)((m + 7) / 8 * 8);
+        BCK(gemm_configure());
+        BCKS(balloc((void**)&b->Ath, sizeof(unsigned short) * N * b->mpad));
+        BCKS(balloc((void**)&b->Atl, sizeof(unsigned short) * N * b->mpad));
+        float* tmp = nullptr;
+        BCKS(balloc((void**)&tmp, sizeof(float) * m * N));
+        k_join_bf16x2<<<152 * 8, 256, 0, s>>>(reinterpret_cast<const unsigned short*>(h->P0),
+                                              reinterpret_cast<const unsigned short*>(h->P1), tmp,
+                                              (long long)(m * N));
+        launch_transpose_split(tmp, h->m, h->N, b->Ath, b->Atl, b->mpad, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        cudaFree(tmp);
+        if (e != cudaSuccess)
+            return set_last_error(TVCS_ERR_CUDA, "building A^T: %s", cudaGetErrorString(e));
+    }
+    if (b->cap < count) {
+        // keep A^T, replace the per-image buffers
+        unsigned short *ath = b->Ath, *atl = b->Atl;
+        const int mpad = b->mpad;
+        b->Ath = b->Atl = nullptr;
+        free_buffers(b);
+        b->Ath = ath;
+        b->Atl = atl;
+        b->mpad = mpad;
+        const size_t B = (size_t)count;
+        gemm_plan(h->m, h->N, h->num_sms, &b->p1);
+        gemm_plan(h->N, h->m, h->num_sms, &b->p2);
+        BCKS(upload_plan(b->p1, &b->tsb1, &b->ss1, s));
+        BCKS(upload_plan(b->p2, &b->tsb2, &b->ss2, s));
+        const size_t wsf = b->p1.ws_floats > b->p2.ws_floats ? b->p1.ws_floats : b->p2.ws_floats;
+        BCKS(balloc((void**)&b->ws, sizeof(float) * wsf));
+        BCKS(balloc((void**)&b->U, sizeof(float) * B * N));
+        BCKS(balloc((void**)&b->G, sizeof(float) * B * N));
+        BCKS(balloc((void**)&b->W, sizeof(float) * B * 4 * N));
+        BCKS(balloc((void**)&b->L, sizeof(float) * B * 4 * N));
+        BCKS(balloc((void**)&b->R, sizeof(float) * B * m));
+        BCKS(balloc((void**)&b->F, sizeof(float) * B * m));
+        BCKS(balloc((void**)&b->mu, sizeof(float) * B));
+        BCKS(balloc((void**)&b->Uh, sizeof(unsigned short) * B * N));
+        BCKS(balloc((void**)&b->Ul, sizeof(unsigned short) * B * N));
+        BCKS(balloc((void**)&b->Rh, sizeof(unsigned short) * B * b->mpad));
+        BCKS(balloc((void**)&b->Rl, sizeof(unsigned short) * B * b->mpad));
+        BCKS(balloc((void**)&b->ctrls, sizeof(Ctrl) * B));
+        BCKS(balloc((void**)&b->bctrl, sizeof(Ctrl)));
+        BCKS(balloc((void**)&b->r2part, sizeof(double) * B * b->p1.tiles_m));
+        BCKS(balloc((void**)&b->part, sizeof(double) * B * 2 * ((N + 255) / 256)));
+        BCK(cudaMallocHost((void**)&b->hctrls, sizeof(Ctrl) * B));
+        BCK(cudaMallocHost((void**)&b->hbctrl, sizeof(Ctrl)));
+        BCK(cudaMemsetAsync(b->Rh, 0, sizeof(unsigned short) * B * b->mpad, s));
+        BCK(cudaMemsetAsync(b->Rl, 0, sizeof(unsigned short) * B * b->mpad, s));
+        b->cap = count;
+    }
+    if (b->exec) {   // the loop graph's launch shapes depend on count
+        cudaGraphExecDestroy(b->exec);
+        cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+    }
+    return make_maps(h, count);
+}
+
+// R = A U - F (R planes, ||r||^2 partials), then G = A^T R, for `count` images.
+void batch_products(tvcs_ctx* h, int count, bool subtract_f, cudaStream_t s)
+{
+    tvcs_batch* b = h->batch;
+    const long long budget = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : (1LL << 31);
+    launch_gemm(&b->mAh, &b->mAl, &b->mUh, &b->mUl, b->p1, b->ws, b->bctrl, 0, budget, s);
+    launch_gemm_fixup(b->ws, b->tsb1, b->ss1, h->m, b->p1.tiles_m, count,
+                      subtract_f ? b->F : nullptr, h->m, b->R, h->m, b->Rh, b->Rl, b->mpad,
+                      b->r2part, b->bctrl, 0, s);
+    launch_gemm(&b->mAth, &b->mAtl, &b->mRh, &b->mRl, b->p2, b->ws, b->bctrl, 0, budget, s);
+    launch_gemm_fixup(b->ws, b->tsb2, b->ss2, h->N, b->p2.tiles_m, count, nullptr, 0, b->G, h->N,
+                      nullptr, nullptr, 0, nullptr, b->bctrl, 0, s);
+}
+
+TvArgs batch_tv_args(tvcs_ctx* h, int count, int mode)
+{
+    tvcs_batch* b = h->batch;
+    TvArgs a{};
+    a.u = b->U;
+    a.w = b->W;
+    a.lam = b->L;
+    a.g = b->G;
+    a.rhs_out = nullptr;
+    a.tw = h->tw;
+    a.s2 = h->s2;
+    a.part = b->part;
+    a.beta = (float)h->beta;
+    a.mu_over_tau = (float)(h->mu / h->tau);
+    a.mu = (float)h->mu;
+    a.ctrl = b->ctrls;
+    a.mode = mode;
+    a.nimg = count;
+    a.mu_img = b->mu;
+    a.tau = (float)h->tau;
+    a.u_hi = b->Uh;
+    a.u_lo = b->Ul;
+    return a;
+}
+
+tvcs_status build_batch_graph(tvcs_ctx* h, int count)
+{
+    tvcs_batch* b = h->batch;
+    if (b->exec) return TVCS_OK;
+    BCK(cudaGraphCreate(&b->graph, 0));
+    cudaGraphConditionalHandle ch;
+    BCK(cudaGraphConditionalHandleCreate(&ch, b->graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = ch;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    BCK(cudaGraphAddNode(&node, b->graph, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    cudaStream_t cs = h->cap_stream;
+    BCK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal));
+    TvArgs a = batch_tv_args(h, count, MODE_ITER);
+    launch_usolve(h->n, h->ucluster, a, cs);
+    batch_products(h, count, true, cs);
+    k_batch_cond<<<1, 256, 0, cs>>>(b->ctrls, count, b->bctrl, ch, 1);
+    cudaGraph_t captured = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &captured);
+    if (e != cudaSuccess)
+        return set_last_error(TVCS_ERR_CUDA, "capture of the batched loop: %s", cudaGetErrorString(e));
+    BCK(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    return TVCS_OK;
+}
+
+tvcs_status sync_check(tvcs_ctx* h, const char* what)
+{
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return set_last_error(TVCS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return TVCS_OK;
+}
+
+}  // namespace
+
+void free_batch(tvcs_ctx* h)
+{
+    if (!h || !h->batch) return;
+    tvcs_batch* b = h->batch;
+    free_buffers(b);
+    if (b->Ath) cudaFree(b->Ath);
+    if (b->Atl) cudaFree(b->Atl);
+    delete b;
+    h->batch = nullptr;
+}
+
+tvcs_status apply_batch(tvcs_ctx* h, int count, const float* X, const float* Y, float* R, float* G)
+{
+    BCKS(ensure_batch(h, count));
+    tvcs_batch* b = h->batch;
+    cudaStream_t s = h->stream;
+    const size_t N = h->N, m = h->m;
+    BCK(cudaMemcpyAsync(b->U, X, sizeof(float) * count * N, cudaMemcpyDefault, s));
+    if (Y) BCK(cudaMemcpyAsync(b->F, Y, sizeof(float) * count * m, cudaMemcpyDefault, s));
+    launch_split_rows(b->U, count, h->N, h->N, b->Uh, b->Ul, h->N, s);
+    batch_products(h, count, Y != nullptr, s);
+    BCK(cudaMemcpyAsync(R, b->R, sizeof(float) * count * m, cudaMemcpyDefault, s));
+    BCK(cudaMemcpyAsync(G, b->G, sizeof(float) * count * N, cudaMemcpyDefault, s));
+    return sync_check(h, "batched products");
+}
+
+tvcs_status solve_batch(tvcs_ctx* h, int count, const float* const* f, float* const* u,
+                        const double* mu, tvcs_result* res)
+{
+    BCKS(ensure_batch(h, count));
+    tvcs_batch* b = h->batch;
+    cudaStream_t s = h->stream;
+    const size_t N = h->N, m = h->m;
+    for (int i = 0; i < count; ++i)
+        BCK(cudaMemcpyAsync(b->F + i * m, f[i], sizeof(float) * m, cudaMemcpyDefault, s));
+    std::vector<float> mus(count);
+    for (int i = 0; i < count; ++i) mus[i] = (float)(mu ? mu[i] : h->mu);
+    BCK(cudaMemcpyAsync(b->mu, mus.data(), sizeof(float) * count, cudaMemcpyHostToDevice, s));
+    BCK(cudaMemsetAsync(b->W, 0, sizeof(float) * count * 4 * N, s));
+    BCK(cudaMemsetAsync(b->L, 0, sizeof(float) * count * 4 * N, s));
+    memset(b->hctrls, 0, sizeof(Ctrl) * count);
+    for (int i = 0; i < count; ++i) {
+        b->hctrls[i].max_iter = h->opt.max_iter;
+        b->hctrls[i].tol = h->tol;
+        b->hctrls[i].algo = h->opt.algo;
+    }
+    BCK(cudaMemcpyAsync(b->ctrls, b->hctrls, sizeof(Ctrl) * count, cudaMemcpyHostToDevice, s));
+    memset(b->hbctrl, 0, sizeof(Ctrl));
+    b->hbctrl->loops_max = h->opt.max_iter + 2;
+    BCK(cudaMemcpyAsync(b->bctrl, b->hbctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
+    // u^0 = A^T f (reading C3) or 0: G = A^T F through the second GEMM.
+    if (h->opt.init == TVCS_INIT_ZERO) {
+        BCK(cudaMemsetAsync(b->U, 0, sizeof(float) * count * N, s));
+    } else {
+        launch_split_rows(b->F, count, h->m, h->m, b->Rh, b->Rl, b->mpad, s);
+        const long long budget = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : (1LL << 31);
+        launch_gemm(&b->mAth, &b->mAtl, &b->mRh, &b->mRl, b->p2, b->ws, b->bctrl, 0, budget, s);
+        launch_gemm_fixup(b->ws, b->tsb2, b->ss2, h->N, b->p2.tiles_m, count, nullptr, 0, b->U,
+                          h->N, nullptr, nullptr, 0, nullptr, b->bctrl, 0, s);
+    }
+    launch_split_rows(b->U, count, h->N, h->N, b->Uh, b->Ul, h->N, s);
+    batch_products(h, count, true, s);
+    BCKS(build_batch_graph(h, count));
+    BCK(cudaEventRecord(h->ev0, s));
+    if (h->opt.max_iter > 0) BCK(cudaGraphLaunch(b->exec, s));
+    BCK(cudaEventRecord(h->ev1, s));
+    // end of run, per image: ||r||^2, final multiplier update, objective, residuals
+    k_batch_r2<<<count, 128, 0, s>>>(b->r2part, b->p1.tiles_m, b->ctrls);
+    TvArgs a = batch_tv_args(h, count, MODE_PLAIN);
+    launch_tv(h->n, a, 4, s);
+    launch_tv(h->n, a, 5, s);
+    for (int i = 0; i < count; ++i)
+        BCK(cudaMemcpyAsync(u[i], b->U + i * N, sizeof(float) * N, cudaMemcpyDefault, s));
+    BCK(cudaMemcpyAsync(b->hctrls, b->ctrls, sizeof(Ctrl) * count, cudaMemcpyDeviceToHost, s));
+    BCK(cudaMemcpyAsync(b->hbctrl, b->bctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    BCKS(sync_check(h, "batched solve"));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    tvcs_status worst = TVCS_OK, err = TVCS_OK;
+    for (int i = 0; i < count; ++i) {
+        const Ctrl& c = b->hctrls[i];
+        tvcs_status st = TVCS_OK;
+        if (c.error == ERR_TIMEOUT)
+            st = TVCS_ERR_TIMEOUT;
+        else if (c.error == ERR_NONFINITE || !isfinite(c.tv) || !isfinite(c.r2))
+            st = TVCS_ERR_DIVERGED;
+        else if (h->tol > 0.0 && !c.stop_by_tol)
+            st = TVCS_NOT_CONVERGED;
+        if (st < 0)
+            err = st;
+        else if (st > worst)
+            worst = st;
+        if (res) {
+            tvcs_result& r = res[i];
+            r.iters = c.it;
+            r.status = st;
+            r.stopped_by_tol = c.stop_by_tol;
+            r.rel_change = c.relchg;
+            r.tv = c.tv;
+            r.resid2 = c.r2;
+            r.objective = c.tv + 0.5 * mus[i] * c.r2;
+            r.kkt_primal = sqrt(c.kkt_p2);
+            r.kkt_dual = sqrt(c.kkt_d2);
+            r.lambda_max_norm = c.lam_max;
+            r.ms = ms;
+        }
+    }
+    if (err < 0) return set_last_error(err, "an image of the batch failed (see its result)");
+    return worst;
+}
+
+}  // namespace tvcs

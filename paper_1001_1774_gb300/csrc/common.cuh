@@ -218,14 +218,16 @@ __device__ __forceinline__ double block_max_array(const double* __restrict__ a, 
     return block_max(s, scratch);
 }
 
-// Last-block detection: returns true in exactly one block (the last to
-// arrive), after every block's prior global writes are visible to it.  The
-// ticket is reset by that block.  Call from thread 0 only.
+// Last-block detection over the gridDim.x blocks that share `ticket` (one row
+// of the grid; batched kernels give every image, grid row y, its own ticket):
+// returns true in exactly one block (the last to arrive), after the prior
+// global writes of every block are visible to it.  The ticket is reset by that
+// block.  Call from thread 0 only.
 __device__ __forceinline__ bool last_block_arrive(unsigned* ticket)
 {
     __threadfence();
     const unsigned t = atomicAdd(ticket, 1u);
-    const bool last = (t == gridDim.x * gridDim.y * gridDim.z - 1);
+    const bool last = (t == gridDim.x - 1);
     if (last) {
         __threadfence();
         *ticket = 0u;

@@ -1,0 +1,71 @@
+// The solver handle (internal to the library).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tvcs.h"
+
+// Device state of the batched path (many images sharing the handle's A).
+struct tvcs_batch {
+    int cap = 0;                   // images the buffers hold
+    int mpad = 0;                  // m rounded up to a multiple of 8 (bf16 row pitch)
+    unsigned short *Ath = nullptr, *Atl = nullptr;   // A^T as bf16 hi/lo planes, N x mpad
+    float *U = nullptr, *W = nullptr, *L = nullptr, *G = nullptr, *R = nullptr, *F = nullptr;
+    float* mu = nullptr;           // per-image mu
+    unsigned short *Uh = nullptr, *Ul = nullptr, *Rh = nullptr, *Rl = nullptr;
+    tvcs::Ctrl* ctrls = nullptr;         // per image
+    tvcs::Ctrl* hctrls = nullptr;        // pinned host mirror
+    tvcs::Ctrl* bctrl = nullptr;         // loop control of the batch
+    tvcs::Ctrl* hbctrl = nullptr;
+    double *r2part = nullptr, *part = nullptr;
+    float* ws = nullptr;           // stream-K partial tiles
+    tvcs::GemmPlan p1, p2;               // R = A U - F (M = m, K = N) and G = A^T R (M = N, K = m)
+    int *tsb1 = nullptr, *ss1 = nullptr, *tsb2 = nullptr, *ss2 = nullptr;
+    CUtensorMap mAh, mAl, mAth, mAtl, mUh, mUl, mRh, mRl;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+struct tvcs_ctx {
+    int dev = 0, num_sms = 0, ucluster = 0;
+    int m = 0, n = 0, N = 0, P = 0;
+    double mu = 0, beta = 0, tol = 0, tau = 0;
+    tvcs_options opt{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t cap_stream = nullptr;
+    // device buffers
+    float* A = nullptr;            // binary32 A for the single-block-row product kernel (n <= 128)
+    bool use_q = false;            // products by clusters / reduced precision (k_products_q)
+    unsigned char *P0 = nullptr, *P1 = nullptr;   // storage planes of A on that path
+    float* rscale = nullptr;       // per-row scales of the fp8 storage
+    float *f = nullptr, *u = nullptr, *w = nullptr, *lam = nullptr, *g = nullptr, *r = nullptr,
+          *rhs = nullptr, *zeroN = nullptr;
+    float *tx = nullptr, *ty = nullptr, *tr = nullptr, *tg = nullptr;
+    float2* spec = nullptr;
+    float2* tw = nullptr;
+    float* s2 = nullptr;
+    float *gpart = nullptr, *gpart2 = nullptr;
+    double *r2part = nullptr, *part = nullptr;
+    tvcs::Ctrl* ctrl = nullptr;
+    tvcs::Ctrl* hctrl = nullptr;  // pinned host mirror
+    // loop graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool state_ready = false;
+    tvcs_batch* batch = nullptr;
+};
+
+namespace tvcs {
+tvcs_status set_last_error(tvcs_status s, const char* fmt, ...);
+void free_batch(tvcs_ctx* h);
+// Many images with the handle's A (all handles of a tvcs_solve_batched call equal).
+tvcs_status solve_batch(tvcs_ctx* h, int count, const float* const* f, float* const* u,
+                        const double* mu, tvcs_result* res);
+tvcs_status apply_batch(tvcs_ctx* h, int count, const float* X, const float* Y, float* R,
+                        float* G);
+}  // namespace tvcs

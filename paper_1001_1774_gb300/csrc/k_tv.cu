@@ -23,6 +23,14 @@ __global__ void __launch_bounds__(256) k_final1(const float* __restrict__ u, flo
 {
     constexpr int N = NN * NN;
     __shared__ double red[32];
+    {   // image blockIdx.y of a batch
+        const int b = blockIdx.y;
+        u += (size_t)b * N;
+        wbuf += (size_t)b * 4 * N;
+        lbuf += (size_t)b * 4 * N;
+        part += (size_t)b * 2 * gridDim.x;
+        ctrl += b;
+    }
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int par = ctrl->wpar;
     const int pending = ctrl->pending;
@@ -64,10 +72,19 @@ __global__ void __launch_bounds__(256) k_final1(const float* __restrict__ u, flo
 template <int NN>
 __global__ void __launch_bounds__(256) k_final2(const float* __restrict__ lbuf,
                                                 const float* __restrict__ g, float mu,
-                                                double* __restrict__ part, Ctrl* __restrict__ ctrl)
+                                                double* __restrict__ part, Ctrl* __restrict__ ctrl,
+                                                const float* __restrict__ mu_img)
 {
     constexpr int N = NN * NN;
     __shared__ double red[32];
+    {   // image blockIdx.y of a batch
+        const int b = blockIdx.y;
+        lbuf += (size_t)b * 4 * N;
+        g += (size_t)b * N;
+        part += (size_t)b * 2 * gridDim.x;
+        ctrl += b;
+        if (mu_img) mu = mu_img[b];
+    }
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const float* lam = lbuf + (size_t)ctrl->wpar * 2 * N;
     double kd = 0.0, lm = 0.0;
@@ -102,10 +119,11 @@ template <int NN>
 static void launch_tv_set(const TvArgs& a, int which, cudaStream_t s)
 {
     constexpr int N = NN * NN;
+    const dim3 grid((N + 255) / 256, a.nimg > 0 ? a.nimg : 1);
     if (which == 4)
-        k_final1<NN><<<(N + 255) / 256, 256, 0, s>>>(a.u, a.w, a.lam, a.beta, a.part, a.ctrl);
+        k_final1<NN><<<grid, 256, 0, s>>>(a.u, a.w, a.lam, a.beta, a.part, a.ctrl);
     else if (which == 5)
-        k_final2<NN><<<(N + 255) / 256, 256, 0, s>>>(a.lam, a.g, a.mu, a.part, a.ctrl);
+        k_final2<NN><<<grid, 256, 0, s>>>(a.lam, a.g, a.mu, a.part, a.ctrl, a.mu_img);
 }
 
 bool tv_supported(int n)

@@ -57,15 +57,36 @@ struct UsolveShape {
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
+// Batches: image b = blockIdx.y uses u + b N, w/lambda + 4 b N, g + b N, its own
+// control block ctrl + b and, when mu_img is set, mu = mu_img[b].  When u_hi is
+// set, the new u is also written as bfloat16 hi/lo planes (operand of the
+// batched products).
 template <int NN, int C>
 __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
     float* __restrict__ u, float* __restrict__ wbuf, float* __restrict__ lbuf,
     const float* __restrict__ g, float* __restrict__ rhs_out, const float2* __restrict__ tw_g,
     const float* __restrict__ s2_g, float beta, float mu_over_tau, float mu,
-    Ctrl* __restrict__ ctrl, int mode)
+    Ctrl* __restrict__ ctrl, int mode, const float* __restrict__ mu_img, float tau,
+    unsigned short* __restrict__ u_hi, unsigned short* __restrict__ u_lo)
 {
     using S = UsolveShape<NN, C>;
     constexpr int R = S::R, Q = S::Q, QC = S::QC, N = NN * NN;
+    {
+        const int b = blockIdx.y;
+        u += (size_t)b * N;
+        wbuf += (size_t)b * 4 * N;
+        lbuf += (size_t)b * 4 * N;
+        g += (size_t)b * N;
+        ctrl += b;
+        if (u_hi) {
+            u_hi += (size_t)b * N;
+            u_lo += (size_t)b * N;
+        }
+        if (mu_img) {
+            mu = mu_img[b];
+            mu_over_tau = mu / tau;
+        }
+    }
     extern __shared__ __align__(16) unsigned char smem[];
     float2* tw = reinterpret_cast<float2*>(smem + S::O_TW);
     float* s2 = reinterpret_cast<float*>(smem + S::O_S2);
@@ -260,7 +281,18 @@ __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
             const float o = su[(lr + 1) * NN + c];
             du2f = fmaf(d, d, du2f);
             u2f = fmaf(o, o, u2f);
-            u[(r0 + lr) * NN + c] = o + d;
+            const float nw = o + d;
+            u[(r0 + lr) * NN + c] = nw;
+            if (u_hi) {
+                const unsigned int bits = __float_as_uint(nw);
+                // bf16 round to nearest even of nw, and of the exact remainder
+                const unsigned int hb = (bits + 0x7fffu + ((bits >> 16) & 1u)) & 0xffff0000u;
+                const float rem = nw - __uint_as_float(hb);
+                const unsigned int rb = __float_as_uint(rem);
+                const unsigned int lb = (rb + 0x7fffu + ((rb >> 16) & 1u)) & 0xffff0000u;
+                u_hi[(r0 + lr) * NN + c] = (unsigned short)(hb >> 16);
+                u_lo[(r0 + lr) * NN + c] = (unsigned short)(lb >> 16);
+            }
         }
     }
     const double bdu = block_sum((double)du2f, red);
@@ -272,6 +304,7 @@ __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
     }
     cluster.sync();   // partials delivered to block 0; every block has read wpar and done
     if (rank == 0 && tid == 0) {
+        if (ctrl->algo == 0) ctrl->pending = 1;   // u moved: its multiplier update is due
         double tdu = 0.0, tu = 0.0;
         for (int k = 0; k < C; ++k) {
             tdu += cred[2 * k];
@@ -349,7 +382,7 @@ static void launch_usolve_t(const TvArgs& a, cudaStream_t s)
 {
     using S = UsolveShape<NN, C>;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(C, 1, 1);
+    cfg.gridDim = dim3(C, a.nimg > 0 ? a.nimg : 1, 1);
     cfg.blockDim = dim3(256, 1, 1);
     cfg.dynamicSmemBytes = S::SMEM;
     cfg.stream = s;
@@ -361,7 +394,8 @@ static void launch_usolve_t(const TvArgs& a, cudaStream_t s)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, k_usolve_cluster<NN, C>, a.u, a.w, a.lam, a.g, a.rhs_out, a.tw, a.s2,
-                       a.beta, a.mu_over_tau, a.mu, a.ctrl, a.mode);
+                       a.beta, a.mu_over_tau, a.mu, a.ctrl, a.mode, a.mu_img, a.tau,
+                       a.u_hi, a.u_lo);
 }
 
 // Cluster sizes available per n: {16, 8} where both give an even row count.

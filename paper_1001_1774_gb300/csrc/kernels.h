@@ -1,8 +1,11 @@
 // Host-side launchers of the solver kernels (internal to the library).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <vector>
 
 namespace tvcs {
 
@@ -20,8 +23,14 @@ struct TvArgs {
     const float* s2;    // n values 4 sin^2(pi k / n)
     double* part;       // per-block binary64 partials (>= 2 * max blocks)
     float beta, mu_over_tau, mu;
-    Ctrl* ctrl;
+    Ctrl* ctrl;                 // per image when nimg > 1 (ctrl + b)
     int mode;
+    // batches of images (the u-solve and the end-of-run kernels)
+    int nimg;                   // images (grid y); 0 or 1 for one image
+    const float* mu_img;        // nullable: per-image mu
+    float tau;
+    unsigned short* u_hi;       // nullable: bf16 hi/lo planes of the new u
+    unsigned short* u_lo;
 };
 
 bool tv_supported(int n);
@@ -85,6 +94,28 @@ int qprod_grid_clusters(int prec, int n, int m);   // sets kernel attributes; 0 
 void launch_qproducts(int prec, int n, int clusters, const QProdArgs& a, cudaStream_t s);
 void launch_split_bf16x2(const float* A, void* hi, void* lo, long long count, cudaStream_t s);
 void launch_quant_fp8(const float* A, int m, int N, void* q, void* c, float* scale, cudaStream_t s);
+
+// Batched products as tcgen05 BF16x3 GEMMs with stream-K scheduling (k_gemm.cu).
+struct GemmPlan {
+    int tiles_m = 0, kblocks = 0, grid = 0, smax = 1;
+    std::vector<int> tile_seg_begin;   // tiles_m + 1 offsets into seg_slot
+    std::vector<int> seg_slot;         // workspace slot of each segment, per tile in K order
+    size_t ws_floats = 0;
+};
+void gemm_plan(int M, int K, int num_sms, GemmPlan* p);
+cudaError_t gemm_configure();
+bool make_bf16_map(CUtensorMap* map, const void* base, int inner, int rows, int ld, int box_rows);
+void launch_gemm(const CUtensorMap* xh, const CUtensorMap* xl, const CUtensorMap* yh,
+                 const CUtensorMap* yl, const GemmPlan& p, float* ws, Ctrl* ctrl, int check_skip,
+                 long long budget, cudaStream_t s);
+void launch_gemm_fixup(const float* ws, const int* tile_seg_begin, const int* seg_slot, int M,
+                       int tiles_m, int count, const float* F, int ldf, float* out, int ldo,
+                       void* out_hi, void* out_lo, int ldh, double* r2part, const Ctrl* ctrl,
+                       int check_skip, cudaStream_t s);
+void launch_split_rows(const float* v, int count, int len, int ld, void* hi, void* lo, int ldh,
+                       cudaStream_t s);
+void launch_transpose_split(const float* A, int m, int N, void* th, void* tl, int ldt,
+                            cudaStream_t s);
 
 // gather: out = scale * sum_p gpart[p], ctrl->vec2 = ||out||^2 (binary64)
 void launch_gather(const float* gpart, int P, int N, float scale, float* out, double* part,

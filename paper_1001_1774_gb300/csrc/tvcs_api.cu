@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "ctx.h"
 #include "kernels.h"
 #include "tvcs.h"
 
@@ -54,36 +55,6 @@ std::mutex g_cfg_mutex;
 std::set<std::pair<int, int>> g_configured;  // (device, n) with the product kernel configured
 
 }  // namespace
-
-struct tvcs_ctx {
-    int dev = 0, num_sms = 0, ucluster = 0;
-    int m = 0, n = 0, N = 0, P = 0;
-    double mu = 0, beta = 0, tol = 0, tau = 0;
-    tvcs_options opt{};
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    cudaStream_t cap_stream = nullptr;
-    // device buffers
-    float* A = nullptr;            // binary32 A for the single-block-row product kernel (n <= 128)
-    bool use_q = false;            // products by clusters / reduced precision (k_products_q)
-    unsigned char *P0 = nullptr, *P1 = nullptr;   // storage planes of A on that path
-    float* rscale = nullptr;       // per-row scales of the fp8 storage
-    float *f = nullptr, *u = nullptr, *w = nullptr, *lam = nullptr, *g = nullptr, *r = nullptr,
-          *rhs = nullptr, *zeroN = nullptr;
-    float *tx = nullptr, *ty = nullptr, *tr = nullptr, *tg = nullptr;
-    float2* spec = nullptr;
-    float2* tw = nullptr;
-    float* s2 = nullptr;
-    float *gpart = nullptr, *gpart2 = nullptr;
-    double *r2part = nullptr, *part = nullptr;
-    Ctrl* ctrl = nullptr;
-    Ctrl* hctrl = nullptr;  // pinned host mirror
-    // loop graph
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    bool state_ready = false;
-};
 
 namespace {
 
@@ -189,6 +160,7 @@ void free_ctx(tvcs_ctx* h)
     if (!h) return;
     cudaSetDevice(h->dev);
     if (h->stream) cudaStreamSynchronize(h->stream);
+    free_batch(h);
     if (h->exec) cudaGraphExecDestroy(h->exec);
     if (h->graph) cudaGraphDestroy(h->graph);
     void* bufs[] = {h->A, h->f, h->u, h->w, h->lam, h->g, h->r, h->rhs, h->zeroN, h->tx, h->ty,
@@ -617,6 +589,12 @@ tvcs_status tvcs_solve_batched(const tvcs_handle* hs, int count, const float* co
         if (!hs[i] || !f[i] || !u[i]) return fail(TVCS_ERR_INVALID_ARG, "entry %d is NULL", i);
         if (mu && !(mu[i] > 0.0)) return fail(TVCS_ERR_INVALID_ARG, "mu[%d] must be > 0", i);
     }
+    bool shared = hs[0]->opt.precision == TVCS_PREC_BF16X2 && count <= 256 && hs[0]->N % 128 == 0;
+    for (int i = 1; i < count && shared; ++i) shared = hs[i] == hs[0];
+    if (shared) {
+        CKS(check_handle(hs[0]));
+        return solve_batch(hs[0], count, f, u, mu, res);
+    }
     tvcs_status worst = TVCS_OK;
     for (int i = 0; i < count; ++i) {
         tvcs_ctx* h = hs[i];
@@ -734,6 +712,15 @@ tvcs_status tvcs_time_stage(tvcs_handle h, int stage, int reps, double* ms)
     CK(cudaEventElapsedTime(&t, h->ev0, h->ev1));
     *ms = t;
     return TVCS_OK;
+}
+
+tvcs_status tvcs_apply_batched(tvcs_handle h, int count, const float* X, const float* Y,
+                               float* R, float* G)
+{
+    CKS(check_handle(h));
+    if (count < 1) return fail(TVCS_ERR_INVALID_ARG, "count must be >= 1");
+    if (!X || !R || !G) return fail(TVCS_ERR_INVALID_ARG, "X, R and G must be non-NULL");
+    return apply_batch(h, count, X, Y, R, G);
 }
 
 tvcs_status tvcs_apply(tvcs_handle h, const float* x, const float* y, float* r, float* g)

@@ -253,6 +253,27 @@ def workload_n256() -> Problem:
     return make_problem(256, 0.2, 2, 20, 5e2, 10.0, 0.0, 300, 5e-3, name="n256_m13107")
 
 
+def workload_shared_batch(count: int = 256, n: int = 128, ratio: float = 0.3, seed: int = 1,
+                          n_ellipses: int = 12):
+    """`count` images sharing one Gaussian A (m = ratio n^2): image b is a seeded
+    ellipse phantom, its noise level is U[1e-3, 1e-2] RMS, and mu cycles over
+    {2e2, 5e2, 1e3, 2e3}.  Returns (A, [ubar_b], F (count x m), [mu_b], [sigma_b])."""
+    m = sampled_m(n, ratio)
+    A = gaussian_matrix(seed, m, n * n)
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0xBA7C]))
+    mus = [2e2, 5e2, 1e3, 2e3]
+    ubars, F, mu, sig = [], np.empty((count, m), np.float32), [], []
+    for b in range(count):
+        ub = phantom(n, n_ellipses, 1000 + 7 * b + seed)
+        c = float(rng.uniform(1e-3, 1e-2))
+        f, s = measure(A, ub, c, 500_000 + b)
+        ubars.append(ub)
+        F[b] = f
+        mu.append(mus[b % 4])
+        sig.append(s)
+    return A, ubars, F, mu, sig
+
+
 def workload_n128() -> Problem:
     """Single 128 x 128 image, m = 4915 (ratio 0.3), 12 ellipses plus a random
     rectangle grid, noise 1e-3 * RMS, mu = 1e3, beta = 10, 300 iterations."""

@@ -1,0 +1,140 @@
+"""Batched path: many images sharing one A, products as tcgen05 BF16x3 GEMMs.
+
+The GEMM computes D = X_hi Y_hi + X_hi Y_lo + X_lo Y_hi with bf16 hi/lo
+splits; the reference below forms exactly that sum in binary64 from the
+test-side emulation of the splits (quant_ref.py), so the comparison checks
+the tensor-core arithmetic at binary32 accumulation tolerance (1e-5 of the
+absolute sums).  Whole solves are compared with the FP64 oracle on the exact
+binary32 A (the split's representation error is part of that difference).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import quant_ref
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tv(cuda_device):
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1001_1774_gb300 as tv
+    return tv
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def bf16x3(Xh, Xl, Yh, Yl):
+    """X (rows x K) times Y^T (cols x K) as the three-term split product, binary64."""
+    Xh, Xl, Yh, Yl = (np.asarray(t, dtype=np.float64) for t in (Xh, Xl, Yh, Yl))
+    return Xh @ Yh.T + Xh @ Yl.T + Xl @ Yh.T
+
+
+def bf16_handle(tv, A, m, n, mu=1.0, beta=10.0, tau=0.1, max_iter=50, tol=0.0):
+    opt = tv.tvcs_default_options()
+    opt.precision = tv.TVCS_PREC_BF16X2
+    opt.tau = tau
+    opt.max_iter = max_iter
+    return tv.tvcs_create(torch.from_numpy(A).cuda(), 0, m, n, mu, beta, tol, opt)
+
+
+@pytest.mark.parametrize("n,m,count", [(32, 307, 1), (32, 307, 7), (32, 300, 256), (64, 1229, 40),
+                                       (128, 4915, 64)])
+def test_batched_products(tv, n, m, count):
+    N = n * n
+    A = synth.gaussian_matrix(70 + n, m, N)
+    rng = np.random.default_rng(count + n)
+    X = rng.standard_normal((count, N)).astype(np.float32)
+    Y = rng.standard_normal((count, m)).astype(np.float32)
+    h = bf16_handle(tv, A, m, n)
+    R = np.empty((count, m), np.float32)
+    G = np.empty((count, N), np.float32)
+    tv.tvcs_apply_batched(h, count, X, Y, R, G)
+    Ah, Al = quant_ref.split_bf16x2(A)
+    Xh, Xl = quant_ref.split_bf16x2(X)
+    # rows of A checked: all for small m, a seeded sample for the full-size case
+    rows = np.arange(m) if m * N <= 2_000_000 else np.sort(rng.choice(m, 400, replace=False))
+    Rref = bf16x3(Ah[rows], Al[rows], Xh, Xl).T - Y[:, rows].astype(np.float64)
+    scale = (np.abs(Ah[rows].astype(np.float64)) + np.abs(Al[rows])) @ np.abs(X.astype(np.float64)).T
+    assert np.all(np.abs(R[:, rows].astype(np.float64) - Rref) <= 1e-5 * scale.T + 1e-30)
+    # G = A^T R with the GPU's own R (its bf16 split) as input
+    Rh, Rl = quant_ref.split_bf16x2(R)
+    Aeff = (Ah + Al).astype(np.float32)
+    Th, Tl = quant_ref.split_bf16x2(np.ascontiguousarray(Aeff.T))
+    cols = np.arange(N) if m * N <= 2_000_000 else np.sort(rng.choice(N, 400, replace=False))
+    Gref = bf16x3(Th[cols], Tl[cols], Rh, Rl).T
+    gscale = np.abs(Aeff.T[cols].astype(np.float64)) @ np.abs(R.astype(np.float64)).T
+    assert np.all(np.abs(G[:, cols].astype(np.float64) - Gref) <= 1e-5 * gscale.T + 1e-30)
+    tv.tvcs_destroy(h)
+
+
+def test_batched_solve_matches_oracle_and_single_image(tv):
+    A, ubars, F, mus, _ = synth.workload_shared_batch(count=8, n=32, ratio=0.3, seed=3, n_ellipses=6)
+    m, N = A.shape
+    n = 32
+    tau = oracle.default_tau(A)
+    iters = 40
+    h = bf16_handle(tv, A, m, n, mu=1e3, tau=tau, max_iter=iters)
+    us = [np.empty(N, np.float32) for _ in range(8)]
+    res = tv.tvcs_solve_batched([h] * 8, [F[b] for b in range(8)], us, mus)
+    for b in range(8):
+        assert res[b].iters == iters
+        ref = oracle.solve(A, F[b], n, mus[b], 10.0, tau, max_iter=iters)
+        err = rel(us[b], ref.u)
+        assert err <= 1e-4, (b, err)
+        assert res[b].objective == pytest.approx(ref.info["objective"], rel=1e-4)
+    # one image through the single-image bf16x2 path (binary32 u, same storage of A)
+    h1 = bf16_handle(tv, A, m, n, mu=mus[5], tau=tau, max_iter=iters)
+    u1 = np.empty(N, np.float32)
+    tv.tvcs_solve(h1, F[5], u1)
+    assert rel(us[5], u1) <= 1e-4
+    tv.tvcs_destroy(h)
+    tv.tvcs_destroy(h1)
+
+
+def test_batched_per_image_stop(tv):
+    # images stop on their own eq. (stop): a run to tol gives per-image iteration counts
+    A, ubars, F, mus, _ = synth.workload_shared_batch(count=4, n=32, ratio=0.3, seed=4, n_ellipses=6)
+    m, N = A.shape
+    tau = oracle.default_tau(A)
+    mus = [20.0, 50.0, 100.0, 200.0]
+    h = bf16_handle(tv, A, m, 32, mu=1e3, beta=20.0, tau=tau, max_iter=3000, tol=1e-4)
+    us = [np.empty(N, np.float32) for _ in range(4)]
+    res = tv.tvcs_solve_batched([h] * 4, [F[b] for b in range(4)], us, mus)
+    for b in range(4):
+        ref = oracle.solve(A, F[b], 32, mus[b], 20.0, tau, tol=1e-4, max_iter=3000)
+        assert res[b].stopped_by_tol == 1
+        assert abs(res[b].iters - ref.info["iters"]) <= max(2, ref.info["iters"] // 50)
+        assert rel(us[b], ref.u) <= 1e-3
+    assert len({r.iters for r in res}) > 1
+    tv.tvcs_destroy(h)
+
+
+def test_batched_workload_256_images_n128(tv):
+    # 256 images of 128 x 128 sharing one 4915 x 16384 A (bf16 hi/lo), mu cycling over
+    # {2e2, 5e2, 1e3, 2e3}, noise U[1e-3, 1e-2] RMS; a fixed 30 iterations, a sample
+    # of 8 images (2 per mu) compared with the FP64 oracle.
+    A, ubars, F, mus, _ = synth.workload_shared_batch(count=256, n=128, ratio=0.3, seed=1)
+    m, N = A.shape
+    tau = oracle.default_tau(A, 30)
+    iters = 30
+    h = bf16_handle(tv, A, m, 128, mu=1e3, tau=tau, max_iter=iters)
+    U = torch.empty((256, N), dtype=torch.float32, device="cuda")
+    Fd = torch.from_numpy(F).cuda()
+    res = tv.tvcs_solve_batched([h] * 256, [Fd[b] for b in range(256)], [U[b] for b in range(256)], mus)
+    Uh = U.cpu().numpy()
+    for b in [0, 1, 2, 3, 128, 129, 130, 255]:
+        assert res[b].iters == iters
+        ref = oracle.solve(A, F[b], 128, mus[b], 10.0, tau, max_iter=iters)
+        err = rel(Uh[b], ref.u)
+        print("image %d mu %.0f rel err %.2e" % (b, mus[b], err))
+        assert err <= 1e-4
+    tv.tvcs_destroy(h)
