@@ -44,9 +44,10 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-solves", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["n128", "n256"], default="n128",
+    ap.add_argument("--workload", choices=["n128", "n256", "batch256"], default="n128",
                     help="n128: 128x128, m=4915, binary32 A (the benchmark workload); "
-                         "n256: 256x256, m=13107, A stored per --precision")
+                         "n256: 256x256, m=13107, A stored per --precision; "
+                         "batch256: 256 images of 128x128 sharing one A (bf16 hi/lo)")
     ap.add_argument("--precision", type=int, default=0,
                     help="storage of A: 0 binary32, 1 bf16 hi+lo, 2 fp8 e4m3 + bf16 correction")
     ap.add_argument("--host-loop", action="store_true",
@@ -344,6 +345,125 @@ def ctypes_stream(stream) -> int:
     return int(stream.cuda_stream)
 
 
+# ----------------------------------------------------------------------------- batched arm
+
+def run_batched(args):
+    """256 images of 128 x 128 sharing one 4915 x 16384 A stored as bf16 hi/lo; a
+    step is one iteration of all 256 images (u-steps as one batched launch, the
+    products as two tcgen05 BF16x3 GEMMs)."""
+    import numpy as np
+    import torch
+
+    import synth
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1001_1774_gb300 as tv
+    B = 256
+    A, ubars, F, mus, _ = synth.workload_shared_batch(count=B, n=128, ratio=0.3, seed=1)
+    m, N = A.shape
+    stream = torch.cuda.Stream()
+    opt = tv.tvcs_default_options()
+    opt.precision = tv.TVCS_PREC_BF16X2
+    opt.stream = ctypes_stream(stream)
+    opt.max_iter = max(args.warmup, 3)
+    with torch.cuda.stream(stream):
+        A_dev = torch.from_numpy(A).cuda()
+        F_dev = torch.from_numpy(F).cuda()
+        U_dev = torch.empty((B, N), dtype=torch.float32, device="cuda")
+    stream.synchronize()
+    h = tv.tvcs_create(A_dev, 0, m, 128, 1e3, 10.0, 0.0, opt)
+    del A_dev
+    tau = tv.tvcs_get_tau(h)
+    fl = [F_dev[b] for b in range(B)]
+    ul = [U_dev[b] for b in range(B)]
+    tv.tvcs_solve_batched([h] * B, fl, ul, mus)      # warm-up: builds A^T, plans, the graph
+    # the timed run: args.steps iterations of all images (tol 0: fixed count)
+    h2_opt = opt
+    tv.tvcs_destroy(h)
+    h2_opt.max_iter = args.steps
+    h2_opt.tau = tau
+    with torch.cuda.stream(stream):
+        A_dev = torch.from_numpy(A).cuda()
+    stream.synchronize()
+    h = tv.tvcs_create(A_dev, 0, m, 128, 1e3, 10.0, 0.0, h2_opt)
+    del A_dev
+    tv.tvcs_solve_batched([h] * B, fl, ul, mus)      # builds the state and the loop graph
+    sampler = ClockSampler(0)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.2)
+    ev0.record(stream)
+    res = tv.tvcs_solve_batched([h] * B, fl, ul, mus)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    assert all(r.iters == args.steps for r in res)
+    loop_ms = res[0].ms
+    reps = 50
+    gemm_us = tv.tvcs_time_stage(h, 3, reps) * 1e3 / reps
+    fix_us = tv.tvcs_time_stage(h, 4, reps) * 1e3 / reps
+    us_us = tv.tvcs_time_stage(h, 5, reps) * 1e3 / reps
+    # end to end with pinned host buffers (f in, images out inside the timed call)
+    F_host = torch.from_numpy(F).pin_memory()
+    U_host = torch.empty((B, N), dtype=torch.float32).pin_memory()
+    t0 = time.perf_counter()
+    tv.tvcs_solve_batched([h] * B, [F_host[b] for b in range(B)], [U_host[b] for b in range(B)], mus)
+    e2e_s = time.perf_counter() - t0
+    U_gpu = U_host.numpy().copy()
+    tv.tvcs_destroy(h)
+
+    flops_gemm_pair = 2 * 3 * 2.0 * m * N * B        # two GEMMs, three bf16 terms each
+    peak = bf16_peak()
+    value = B * args.steps / (ms / 1e3)
+    out = {"metric": METRIC, "value": value, "unit": "image-iter/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3->f32",
+           "data": "synthetic (seeded phantoms, Philox Gaussian A)",
+           "recons_per_s": value / ITERS_PER_RECON,
+           "config": {"workload": "batch256_n128_m4915_bf16x2_shared_A", "images": B, "n": 128,
+                      "m": m, "mu": "cycling 2e2, 5e2, 1e3, 2e3", "iters_per_recon": ITERS_PER_RECON,
+                      "l2": "inputs larger than L2 (A and A^T bf16 hi/lo = 644 MB); no flush"},
+           "roofline": {"bound": "tensor", "achieved": flops_gemm_pair / (gemm_us * 1e-6) / 1e12,
+                        "peak": peak[0], "unit": "TFLOP/s",
+                        "frac": flops_gemm_pair / (gemm_us * 1e-6) / 1e12 / peak[0], "traffic": None,
+                        "kernel": "k_gemm_bf16x3 (R = A U and G = A^T R, 3 bf16 MMAs per product)",
+                        "flops_per_iteration": flops_gemm_pair, "launch_pair_us": gemm_us,
+                        "peak_source": peak[1]},
+           "stage_us": {"gemm_pair": gemm_us, "fixups": fix_us, "usolve_batched": us_us,
+                        "loop_per_iteration": loop_ms * 1e3 / args.steps},
+           "e2e": {"value": B * args.steps / e2e_s, "unit": "image-iter/s",
+                   "h2d_bytes_per_step": 4 * m * B / args.steps,
+                   "d2h_bytes_per_step": 4 * N * B / args.steps},
+           "gpu_launches": 6 * args.steps + 8, "clocks": clocks, "tau": tau}
+    if not args.no_cpu_baseline:
+        import oracle
+        P = synth.Problem("batch_img0", 128, m, 1, mus[0], 10.0, 0.0, args.steps, 0.0, ubars[0], A,
+                          F[0])
+        cb = oracle_sample(P, tau, budget_s=20.0, want_u=True)
+        out["cpu_baseline"] = {"value": cb["value"], "unit": "image-iter/s", "cores": cb["cores"],
+                               "kind": "oracle",
+                               "sample": "%d IADM iterations of image 0 (FP64 C oracle, OpenMP), "
+                                         "%.1f s" % (cb["iters"], cb["seconds"])}
+        if cb["iters"] == min(args.steps, ITERS_PER_RECON) and args.steps <= ITERS_PER_RECON:
+            err = float(np.linalg.norm(U_gpu[0] - cb["u"].ravel()) / np.linalg.norm(cb["u"]))
+            out["parity_vs_oracle"] = {"rel_image_err": err, "image": 0, "iters": args.steps,
+                                       "ok": err <= 1e-4}
+    print(json.dumps(out), flush=True)
+
+
+def bf16_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["bf16_tflops"]), "measured burst (MEASURED_PEAKS.json bf16_tflops)"
+    except Exception:
+        return 1900.0, "fallback 1.9 PFLOP/s"
+
+
 # ----------------------------------------------------------------------------- reference arm
 
 def run_reference(args):
@@ -381,6 +501,8 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch256":
+        run_batched(args)
     else:
         run_ours(args)
 

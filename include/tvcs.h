@@ -172,7 +172,10 @@ tvcs_status tvcs_run_stage(tvcs_handle h, int stage);
  * tvcs_run_stage, without its host-side bookkeeping) on the handle's stream
  * between two CUDA events; *ms receives the elapsed milliseconds.  Afterwards
  * the state is that of `reps` applications of the stage (stage 2 leaves it
- * unchanged).  Requires a state (tvcs_solve or tvcs_set_state first). */
+ * unchanged).  Requires a state (tvcs_solve or tvcs_set_state first).
+ * Stages 3-5 time the parts of a batched iteration on the state of the last
+ * tvcs_solve_batched call: 3 the two GEMM kernels (R = A U, G = A^T R), 4 their
+ * two epilogue kernels, 5 the batched u-solve. */
 tvcs_status tvcs_time_stage(tvcs_handle h, int stage, int reps, double* ms);
 
 /* Products for `count` images that share the handle's A, the batched form of

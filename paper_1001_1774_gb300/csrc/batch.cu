@@ -210,12 +210,13 @@ tvcs_status ensure_batch(tvcs_ctx* h, int count)
         BCK(cudaMemsetAsync(b->Rl, 0, sizeof(unsigned short) * B * b->mpad, s));
         b->cap = count;
     }
-    if (b->exec) {   // the loop graph's launch shapes depend on count
+    if (b->exec && b->graph_count != count) {   // the loop graph's launch shapes depend on count
         cudaGraphExecDestroy(b->exec);
         cudaGraphDestroy(b->graph);
         b->exec = nullptr;
         b->graph = nullptr;
     }
+    b->last_count = count;
     return make_maps(h, count);
 }
 
@@ -284,6 +285,7 @@ tvcs_status build_batch_graph(tvcs_ctx* h, int count)
     if (e != cudaSuccess)
         return set_last_error(TVCS_ERR_CUDA, "capture of the batched loop: %s", cudaGetErrorString(e));
     BCK(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    b->graph_count = count;
     return TVCS_OK;
 }
 
@@ -306,6 +308,40 @@ void free_batch(tvcs_ctx* h)
     if (b->Atl) cudaFree(b->Atl);
     delete b;
     h->batch = nullptr;
+}
+
+// Back-to-back launches of one part of a batched iteration on the current batch
+// state, between two events: 3 the two GEMM kernels, 4 their two fix-ups, 5 the
+// batched u-solve.
+tvcs_status time_batch_stage(tvcs_ctx* h, int stage, int reps, double* ms)
+{
+    tvcs_batch* b = h->batch;
+    if (!b || b->cap == 0 || b->last_count <= 0)
+        return set_last_error(TVCS_ERR_INVALID_ARG, "no batched state: call tvcs_solve_batched first");
+    const int count = b->last_count;
+    cudaStream_t s = h->stream;
+    const long long budget = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : (1LL << 31);
+    TvArgs a = batch_tv_args(h, count, MODE_PLAIN);
+    BCK(cudaEventRecord(h->ev0, s));
+    for (int i = 0; i < reps; ++i) {
+        if (stage == 3) {
+            launch_gemm(&b->mAh, &b->mAl, &b->mUh, &b->mUl, b->p1, b->ws, b->bctrl, 0, budget, s);
+            launch_gemm(&b->mAth, &b->mAtl, &b->mRh, &b->mRl, b->p2, b->ws, b->bctrl, 0, budget, s);
+        } else if (stage == 4) {
+            launch_gemm_fixup(b->ws, b->tsb1, b->ss1, h->m, b->p1.tiles_m, count, b->F, h->m, b->R,
+                              h->m, b->Rh, b->Rl, b->mpad, b->r2part, b->bctrl, 0, s);
+            launch_gemm_fixup(b->ws, b->tsb2, b->ss2, h->N, b->p2.tiles_m, count, nullptr, 0, b->G,
+                              h->N, nullptr, nullptr, 0, nullptr, b->bctrl, 0, s);
+        } else {
+            launch_usolve(h->n, h->ucluster, a, s);
+        }
+    }
+    BCK(cudaEventRecord(h->ev1, s));
+    BCKS(sync_check(h, "timing a batched stage"));
+    float t = 0.f;
+    BCK(cudaEventElapsedTime(&t, h->ev0, h->ev1));
+    *ms = t;
+    return TVCS_OK;
 }
 
 tvcs_status apply_batch(tvcs_ctx* h, int count, const float* X, const float* Y, float* R, float* G)

@@ -27,6 +27,8 @@ struct tvcs_batch {
     CUtensorMap mAh, mAl, mAth, mAtl, mUh, mUl, mRh, mRl;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    int graph_count = 0;           // images the loop graph was built for
+    int last_count = 0;            // images of the last batched call
 };
 
 struct tvcs_ctx {
@@ -68,4 +70,5 @@ tvcs_status solve_batch(tvcs_ctx* h, int count, const float* const* f, float* co
                         const double* mu, tvcs_result* res);
 tvcs_status apply_batch(tvcs_ctx* h, int count, const float* X, const float* Y, float* R,
                         float* G);
+tvcs_status time_batch_stage(tvcs_ctx* h, int stage, int reps, double* ms);
 }  // namespace tvcs

@@ -696,6 +696,7 @@ tvcs_status tvcs_time_stage(tvcs_handle h, int stage, int reps, double* ms)
 {
     CKS(check_handle(h));
     if (!ms || reps < 1) return fail(TVCS_ERR_INVALID_ARG, "ms must be non-NULL and reps >= 1");
+    if (stage >= 3 && stage <= 5) return time_batch_stage(h, stage, reps, ms);
     if (stage < 1 || stage > 2) return fail(TVCS_ERR_INVALID_ARG, "unknown stage %d", stage);
     if (!h->state_ready) return fail(TVCS_ERR_INVALID_ARG, "no state: call tvcs_set_state or tvcs_solve first");
     TvArgs a = tv_args(h, MODE_PLAIN, false);
