@@ -29,6 +29,7 @@ struct tvcs_batch {
     cudaGraphExec_t exec = nullptr;
     int graph_count = 0;           // images the loop graph was built for
     int last_count = 0;            // images of the last batched call
+    int ucluster = 0;              // cluster size of the batched u-solve
 };
 
 struct tvcs_ctx {

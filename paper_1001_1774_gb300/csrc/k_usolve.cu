@@ -409,6 +409,15 @@ static void launch_usolve_t(const TvArgs& a, cudaStream_t s)
     X(192, 16) X(192, 8)     \
     X(256, 16)
 
+bool usolve_cluster_fits(int n, int c)
+{
+#define X(NN, C) \
+    if (n == NN && c == C) return cluster_fits_t<NN, C>();
+    TVCS_USOLVE_TABLE(X)
+#undef X
+    return false;
+}
+
 int usolve_choose_cluster(int n)
 {
 #define X(NN, C) \

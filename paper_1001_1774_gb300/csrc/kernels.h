@@ -42,6 +42,7 @@ void launch_tv(int n, const TvArgs& a, int which, cudaStream_t s);
 // cluster size used for n on the current device (16 or 8), 0 if none fits;
 // it also sets the kernel attributes and must run before launch_usolve.
 int usolve_choose_cluster(int n);
+bool usolve_cluster_fits(int n, int c);   // also sets the kernel attributes
 void launch_usolve(int n, int cluster, const TvArgs& a, cudaStream_t s);
 
 // Fused single-pass products r = A x - y, gpart = per-block partials of A^T r.
