@@ -58,6 +58,10 @@ enum { TVCS_ALGO_IADM = 0, TVCS_ALGO_FTVCS = 1 };
 enum { TVCS_PREC_FP32 = 0, TVCS_PREC_BF16X2 = 1, TVCS_PREC_FP8_BF16 = 2 };
 /* Initial point: A^T f (back-projection), zero, or caller-given (tvcs_set_state). */
 enum { TVCS_INIT_ATF = 0, TVCS_INIT_ZERO = 1, TVCS_INIT_GIVEN = 2 };
+/* Where the products get A from: device memory (stored once by tvcs_create), or
+ * the counter-based generator inside the product kernel, so that A occupies no
+ * memory and costs no memory traffic. */
+enum { TVCS_A_STORED = 0, TVCS_A_REGENERATE = 1 };
 
 typedef struct {
     int algo;            /* TVCS_ALGO_IADM (default) or TVCS_ALGO_FTVCS */
@@ -72,6 +76,10 @@ typedef struct {
     int host_loop;       /* 0 (default): the iteration loop is one CUDA graph whose WHILE node
                             the kernels end; 1: the same kernels launched from the host per
                             iteration (for profilers that cannot look inside such graphs) */
+    int a_mode;          /* TVCS_A_STORED (default) or TVCS_A_REGENERATE: every product
+                            regenerates A's entries from the seed given to tvcs_create (A must
+                            be NULL and precision TVCS_PREC_FP32; the entries are the binary32
+                            values the generator would store, so both modes apply the same A) */
 } tvcs_options;
 
 typedef struct {
@@ -123,8 +131,16 @@ tvcs_status tvcs_solve(tvcs_handle h, const float* f, float* u, tvcs_result* res
  * the same handle created with precision TVCS_PREC_BF16X2 (and count <= 256),
  * all images iterate together: their u-steps run as one batched launch and
  * their products as tensor-core GEMMs (see tvcs_apply_batched); each image
- * stops on its own eq. (stop).  Otherwise the problems are solved one after
- * another, each on its handle's stream.
+ * stops on its own eq. (stop).  When every hs[i] was created with a_mode
+ * TVCS_A_REGENERATE (count <= 1024, all on one device with equal algo, beta
+ * and init, init TVCS_INIT_ATF or TVCS_INIT_ZERO; n, m, seed, mu, tau, tol and
+ * max_iter may differ), all problems iterate together in one loop graph on
+ * hs[0]'s stream: one batched u-step launch per image side n, then one
+ * persistent product launch over all problems that regenerates every A in
+ * the kernel; each problem stops on its own eq. (stop) and then leaves the
+ * product launch's work.  hs[0] keeps that batch's device state until it is
+ * destroyed or called with another problem set.  Otherwise the problems are
+ * solved one after another, each on its handle's stream.
  */
 tvcs_status tvcs_solve_batched(const tvcs_handle* hs, int count, const float* const* f,
                                float* const* u, const double* mu, tvcs_result* res);
@@ -175,7 +191,10 @@ tvcs_status tvcs_run_stage(tvcs_handle h, int stage);
  * unchanged).  Requires a state (tvcs_solve or tvcs_set_state first).
  * Stages 3-5 time the parts of a batched iteration on the state of the last
  * tvcs_solve_batched call: 3 the two GEMM kernels (R = A U, G = A^T R), 4 their
- * two epilogue kernels, 5 the batched u-solve. */
+ * two epilogue kernels, 5 the batched u-solve.  Stages 6-7 time the parts of an
+ * iteration of the last uneven batch whose first handle is h: 6 the
+ * regenerating product launch over all problems with its reduction, 7 the
+ * u-solve launches of all image sizes. */
 tvcs_status tvcs_time_stage(tvcs_handle h, int stage, int reps, double* ms);
 
 /* Products for `count` images that share the handle's A, the batched form of

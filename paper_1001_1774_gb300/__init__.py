@@ -29,6 +29,7 @@ TVCS_ERR_UNSUPPORTED = -6
 TVCS_ALGO_IADM, TVCS_ALGO_FTVCS = 0, 1
 TVCS_PREC_FP32, TVCS_PREC_BF16X2, TVCS_PREC_FP8_BF16 = 0, 1, 2
 TVCS_INIT_ATF, TVCS_INIT_ZERO, TVCS_INIT_GIVEN = 0, 1, 2
+TVCS_A_STORED, TVCS_A_REGENERATE = 0, 1
 (TVCS_STATE_U, TVCS_STATE_W, TVCS_STATE_LAMBDA, TVCS_STATE_G, TVCS_STATE_R, TVCS_STATE_RHS,
  TVCS_STATE_F) = range(7)
 
@@ -42,7 +43,7 @@ class tvcs_options(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int), ("tau", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("precision", ctypes.c_int), ("init", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("power_iters", ctypes.c_int), ("timeout_cycles", ctypes.c_longlong),
-                ("host_loop", ctypes.c_int)]
+                ("host_loop", ctypes.c_int), ("a_mode", ctypes.c_int)]
 
 
 class tvcs_result(ctypes.Structure):

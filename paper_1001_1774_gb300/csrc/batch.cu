@@ -48,6 +48,12 @@ __global__ void k_batch_cond(const Ctrl* __restrict__ ctrls, int count, Ctrl* __
     }
 }
 
+void launch_batch_cond(const Ctrl* ctrls, int count, Ctrl* bctrl, unsigned long long cond,
+                       int set_cond, cudaStream_t s)
+{
+    k_batch_cond<<<1, 256, 0, s>>>(ctrls, count, bctrl, (cudaGraphConditionalHandle)cond, set_cond);
+}
+
 // A_eff = hi + lo (exact in binary32) from the two bf16 planes.
 __global__ void k_join_bf16x2(const unsigned short* __restrict__ hi, const unsigned short* __restrict__ lo,
                               float* __restrict__ out, long long count)

@@ -8,6 +8,8 @@
 #include "kernels.h"
 #include "tvcs.h"
 
+#include <vector>
+
 // Device state of the batched path (many images sharing the handle's A).
 struct tvcs_batch {
     int cap = 0;                   // images the buffers hold
@@ -31,6 +33,19 @@ struct tvcs_batch {
     int last_count = 0;            // images of the last batched call
     int ucluster = 0;              // cluster size of the batched u-solve
 };
+
+// Products with A regenerated in the kernel (handles created with
+// TVCS_A_REGENERATE): a small device table of (x, y, r, g) pointer sets, one
+// per call pattern of the handle, and the partial-slot buffers.
+struct tvcs_regen {
+    tvcs::RegenPlan plan;
+    tvcs::RegenProb* dtab = nullptr;       // device entries
+    std::vector<tvcs::RegenProb> htab;     // host copies, same order
+    float* gslot = nullptr;
+    double* r2slot = nullptr;
+    int* pre = nullptr;
+};
+struct tvcs_uneven;   // state of the uneven batch (regen.cu)
 
 struct tvcs_ctx {
     int dev = 0, num_sms = 0, ucluster = 0;
@@ -61,6 +76,9 @@ struct tvcs_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool state_ready = false;
     tvcs_batch* batch = nullptr;
+    uint64_t seed = 0;
+    tvcs_regen* regen = nullptr;   // set for TVCS_A_REGENERATE
+    tvcs_uneven* uneven = nullptr; // uneven batch whose first handle is this one
 };
 
 namespace tvcs {
@@ -72,4 +90,14 @@ tvcs_status solve_batch(tvcs_ctx* h, int count, const float* const* f, float* co
 tvcs_status apply_batch(tvcs_ctx* h, int count, const float* X, const float* Y, float* R,
                         float* G);
 tvcs_status time_batch_stage(tvcs_ctx* h, int stage, int reps, double* ms);
+// Regenerated-A products of one handle (regen.cu).
+tvcs_status regen_init(tvcs_ctx* h);
+void regen_products(tvcs_ctx* h, const float* x, const float* y, float* r, float* g, int mode,
+                    unsigned long long cond, int set_cond, cudaStream_t s);
+void free_regen(tvcs_ctx* h);
+// Many problems of different sizes, all with regenerated A, in one loop graph.
+bool uneven_eligible(const tvcs_handle* hs, int count);
+tvcs_status solve_uneven(const tvcs_handle* hs, int count, const float* const* f, float* const* u,
+                         const double* mu, tvcs_result* res);
+tvcs_status time_uneven_stage(tvcs_ctx* h, int stage, int reps, double* ms);
 }  // namespace tvcs

@@ -58,7 +58,8 @@ struct UsolveShape {
 };
 
 // Batches: image b = blockIdx.y uses u + b N, w/lambda + 4 b N, g + b N, its own
-// control block ctrl + b and, when mu_img is set, mu = mu_img[b].  When u_hi is
+// control block ctrl + b and, when mu_img is set, mu = mu_img[b] (and tau =
+// tau_img[b] when that is set too).  When u_hi is
 // set, the new u is also written as bfloat16 hi/lo planes (operand of the
 // batched products).
 template <int NN, int C>
@@ -66,8 +67,9 @@ __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
     float* __restrict__ u, float* __restrict__ wbuf, float* __restrict__ lbuf,
     const float* __restrict__ g, float* __restrict__ rhs_out, const float2* __restrict__ tw_g,
     const float* __restrict__ s2_g, float beta, float mu_over_tau, float mu,
-    Ctrl* __restrict__ ctrl, int mode, const float* __restrict__ mu_img, float tau,
-    unsigned short* __restrict__ u_hi, unsigned short* __restrict__ u_lo)
+    Ctrl* __restrict__ ctrl, int mode, const float* __restrict__ mu_img,
+    const float* __restrict__ tau_img, float tau, unsigned short* __restrict__ u_hi,
+    unsigned short* __restrict__ u_lo)
 {
     using S = UsolveShape<NN, C>;
     constexpr int R = S::R, Q = S::Q, QC = S::QC, N = NN * NN;
@@ -84,7 +86,7 @@ __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
         }
         if (mu_img) {
             mu = mu_img[b];
-            mu_over_tau = mu / tau;
+            mu_over_tau = mu / (tau_img ? tau_img[b] : tau);
         }
     }
     extern __shared__ __align__(16) unsigned char smem[];
@@ -394,8 +396,8 @@ static void launch_usolve_t(const TvArgs& a, cudaStream_t s)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, k_usolve_cluster<NN, C>, a.u, a.w, a.lam, a.g, a.rhs_out, a.tw, a.s2,
-                       a.beta, a.mu_over_tau, a.mu, a.ctrl, a.mode, a.mu_img, a.tau,
-                       a.u_hi, a.u_lo);
+                       a.beta, a.mu_over_tau, a.mu, a.ctrl, a.mode, a.mu_img, a.tau_img,
+                       a.tau, a.u_hi, a.u_lo);
 }
 
 // Cluster sizes available per n: {16, 8} where both give an even row count.

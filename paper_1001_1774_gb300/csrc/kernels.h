@@ -28,6 +28,7 @@ struct TvArgs {
     // batches of images (the u-solve and the end-of-run kernels)
     int nimg;                   // images (grid y); 0 or 1 for one image
     const float* mu_img;        // nullable: per-image mu
+    const float* tau_img;       // nullable: per-image tau (used with mu_img)
     float tau;
     unsigned short* u_hi;       // nullable: bf16 hi/lo planes of the new u
     unsigned short* u_lo;
@@ -117,6 +118,50 @@ void launch_split_rows(const float* v, int count, int len, int ld, void* hi, voi
                        cudaStream_t s);
 void launch_transpose_split(const float* A, int m, int N, void* th, void* tl, int ldt,
                             cudaStream_t s);
+
+// Products with A regenerated inside the kernel (k_regen.cu): r = A x - y and
+// g = A^T r for many problems of different sizes in one persistent launch.
+// Problem p's rows are cut into `chunks` chunks of rows_per_chunk rows; the
+// clusters take contiguous ranges of the active chunks.  A cluster keeps one
+// partial A^T r per run of consecutive chunks of one problem, written to the
+// slot of the run's first chunk; k_regen_reduce adds the slots in chunk order.
+struct RegenProb {
+    unsigned long long seed;
+    const float* x;      // N
+    const float* y;      // m, nullable (y = 0)
+    float* r;            // m
+    float* g;            // N, written by the reduction
+    float* gslot;        // chunks x N partial slots
+    double* r2slot;      // chunks
+    Ctrl* ctrl;          // receives r2; with MODE_ITER, ctrl->skip marks a problem as inactive
+    int m, N;
+    int rows_per_chunk, chunks;
+    float scale;         // binary32(1/sqrt(m))
+    int pad;
+};
+struct RegenPlan {
+    int cs = 8;          // cluster size (blocks splitting each row's columns)
+    int tile_cap = 0;    // floats of one tile buffer (rows per tile = tile_cap / (N / cs), power of 2)
+    int wmax = 0;        // max over problems of N / cs
+    int clusters = 0;    // persistent grid, in clusters
+    size_t smem = 0;
+};
+constexpr int REGEN_PMAX = 1024;   // problems per launch
+// Fills plan->clusters and plan->smem for (cs, tile_cap, wmax); false if no cluster fits.
+bool regen_configure(RegenPlan* plan);
+// Rows per tile for a problem of N columns under `plan` (a power of 2 <= 16).
+int regen_tile_rows(const RegenPlan& plan, int N);
+void launch_regen(const RegenProb* probs, int P, int mode, const RegenPlan& plan, int* pre_out,
+                  cudaStream_t s);
+// g of every active problem from its slots, ctrl->r2 from its r2 slots; with
+// set_cond, probs[0].ctrl drives the loop condition (single-problem loops).
+void launch_regen_reduce(const RegenProb* probs, int P, int maxN, int mode, const RegenPlan& plan,
+                         const int* pre, unsigned long long cond, int set_cond, cudaStream_t s);
+
+// Loop condition of a batch: continue while any of ctrls[0..count) runs and
+// bctrl->loops stays below bctrl->loops_max (batch.cu).
+void launch_batch_cond(const Ctrl* ctrls, int count, Ctrl* bctrl, unsigned long long cond,
+                       int set_cond, cudaStream_t s);
 
 // gather: out = scale * sum_p gpart[p], ctrl->vec2 = ||out||^2 (binary64)
 void launch_gather(const float* gpart, int P, int N, float scale, float* out, double* part,

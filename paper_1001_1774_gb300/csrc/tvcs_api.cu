@@ -87,6 +87,10 @@ TvArgs tv_args(tvcs_ctx* h, int mode, bool stage_outputs)
 void products(tvcs_ctx* h, const float* x, const float* y, float* r, float* gpart, float* g,
               int mode, unsigned long long cond, int set_cond, cudaStream_t s)
 {
+    if (h->regen) {   // A regenerated in the kernel; A^T r whole in g, else in gpart (P = 1)
+        regen_products(h, x, y, r, g ? g : gpart, mode, cond, set_cond, s);
+        return;
+    }
     if (h->use_q) {
         QProdArgs q{};
         q.P0 = h->P0;
@@ -161,6 +165,7 @@ void free_ctx(tvcs_ctx* h)
     cudaSetDevice(h->dev);
     if (h->stream) cudaStreamSynchronize(h->stream);
     free_batch(h);
+    free_regen(h);
     if (h->exec) cudaGraphExecDestroy(h->exec);
     if (h->graph) cudaGraphDestroy(h->graph);
     void* bufs[] = {h->A, h->f, h->u, h->w, h->lam, h->g, h->r, h->rhs, h->zeroN, h->tx, h->ty,
@@ -359,8 +364,11 @@ tvcs_status create_impl(tvcs_ctx* h, const float* A, uint64_t seed)
     CK(cudaEventCreate(&h->ev1));
     const size_t m = (size_t)h->m, N = (size_t)h->N;
     const int prec = h->opt.precision;
-    h->use_q = !(prec == TVCS_PREC_FP32 && prod_supported(h->n));
-    if (h->use_q) {
+    const bool regen = h->opt.a_mode == TVCS_A_REGENERATE;
+    h->use_q = !regen && !(prec == TVCS_PREC_FP32 && prod_supported(h->n));
+    if (regen) {
+        h->P = 1;   // the regenerating products leave A^T r whole
+    } else if (h->use_q) {
         h->P = qprod_grid_clusters(prec, h->n, h->m);
         if (h->P == 0)
             return fail(TVCS_ERR_UNSUPPORTED, "no cluster of the product kernel fits (n = %d)", h->n);
@@ -372,7 +380,7 @@ tvcs_status create_impl(tvcs_ctx* h, const float* A, uint64_t seed)
         return fail(TVCS_ERR_UNSUPPORTED, "no thread-block cluster of 8 or 16 fits for n = %d", h->n);
     const size_t nparts = 2 * (size_t)((N + 255) / 256 + 1024);
     // A: binary32 for the classic path and as the source of the split storages.
-    CKS(alloc((void**)&h->A, sizeof(float) * m * N));
+    if (!regen) CKS(alloc((void**)&h->A, sizeof(float) * m * N));
     CKS(alloc((void**)&h->f, sizeof(float) * m));
     CKS(alloc((void**)&h->r, sizeof(float) * m));
     CKS(alloc((void**)&h->ty, sizeof(float) * m));
@@ -414,14 +422,17 @@ tvcs_status create_impl(tvcs_ctx* h, const float* A, uint64_t seed)
     CK(cudaMemcpyAsync(h->tw, tw.data(), sizeof(float2) * h->n, cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(h->s2, s2.data(), sizeof(float) * h->n, cudaMemcpyHostToDevice, h->stream));
 
-    if (A) {
+    if (regen) {
+        CKS(sync_and_check(h, "tvcs_create"));
+        CKS(regen_init(h));
+    } else if (A) {
         CK(cudaMemcpyAsync(h->A, A, sizeof(float) * m * N, cudaMemcpyDefault, h->stream));
     } else {
         const float scale = (float)(1.0 / sqrt((double)h->m));
         launch_gen_gauss(h->A, h->m, (int64_t)N, seed, scale, h->stream);
     }
     CKS(sync_and_check(h, "uploading A"));
-    if (h->use_q) {
+    if (h->use_q && !regen) {
         if (prec == TVCS_PREC_FP32) {
             h->P0 = reinterpret_cast<unsigned char*>(h->A);   // the plane is A itself
             h->A = nullptr;
@@ -499,6 +510,7 @@ void tvcs_default_options(tvcs_options* opt)
     opt->power_iters = 100;
     opt->timeout_cycles = 0;
     opt->host_loop = 0;
+    opt->a_mode = TVCS_A_STORED;
 }
 
 const char* tvcs_last_error(void)
@@ -524,7 +536,13 @@ tvcs_status tvcs_create(tvcs_handle* out, const float* A, uint64_t seed, int m, 
         return fail(TVCS_ERR_INVALID_ARG, "unknown init %d", o.init);
     if (o.precision < TVCS_PREC_FP32 || o.precision > TVCS_PREC_FP8_BF16)
         return fail(TVCS_ERR_INVALID_ARG, "unknown precision %d", o.precision);
-    if (!valid_n(n, o.precision))
+    if (o.a_mode != TVCS_A_STORED && o.a_mode != TVCS_A_REGENERATE)
+        return fail(TVCS_ERR_INVALID_ARG, "unknown a_mode %d", o.a_mode);
+    if (o.a_mode == TVCS_A_REGENERATE && (A || o.precision != TVCS_PREC_FP32))
+        return fail(TVCS_ERR_INVALID_ARG,
+                    "TVCS_A_REGENERATE needs A = NULL (A comes from the seed) and precision "
+                    "TVCS_PREC_FP32");
+    if (o.a_mode == TVCS_A_REGENERATE ? !tv_supported(n) : !valid_n(n, o.precision))
         return fail(TVCS_ERR_INVALID_ARG,
                     "n = %d not supported with precision %d (binary32: 16, 32, 48, 64, 96, 128, 192, "
                     "256; bf16x2 / fp8: 32, 64, 128, 192, 256)",
@@ -540,6 +558,7 @@ tvcs_status tvcs_create(tvcs_handle* out, const float* A, uint64_t seed, int m, 
     h->beta = beta;
     h->tol = tol;
     h->opt = o;
+    h->seed = seed;
     tvcs_status st = create_impl(h, A, seed);
     if (st != TVCS_OK) {
         std::string msg = g_last_error;
@@ -594,6 +613,10 @@ tvcs_status tvcs_solve_batched(const tvcs_handle* hs, int count, const float* co
     if (shared) {
         CKS(check_handle(hs[0]));
         return solve_batch(hs[0], count, f, u, mu, res);
+    }
+    if (uneven_eligible(hs, count)) {
+        CKS(check_handle(hs[0]));
+        return solve_uneven(hs, count, f, u, mu, res);
     }
     tvcs_status worst = TVCS_OK;
     for (int i = 0; i < count; ++i) {
@@ -697,6 +720,7 @@ tvcs_status tvcs_time_stage(tvcs_handle h, int stage, int reps, double* ms)
     CKS(check_handle(h));
     if (!ms || reps < 1) return fail(TVCS_ERR_INVALID_ARG, "ms must be non-NULL and reps >= 1");
     if (stage >= 3 && stage <= 5) return time_batch_stage(h, stage, reps, ms);
+    if (stage == 6 || stage == 7) return time_uneven_stage(h, stage, reps, ms);
     if (stage < 1 || stage > 2) return fail(TVCS_ERR_INVALID_ARG, "unknown stage %d", stage);
     if (!h->state_ready) return fail(TVCS_ERR_INVALID_ARG, "no state: call tvcs_set_state or tvcs_solve first");
     TvArgs a = tv_args(h, MODE_PLAIN, false);

@@ -66,6 +66,10 @@ def _load():
                                           ctypes.c_void_p, ctypes.c_double, ctypes.c_uint64,
                                           ctypes.c_void_p]
             lib.synth_measure.restype = ctypes.c_double
+            lib.synth_measure_seeded.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int64,
+                                                 ctypes.c_void_p, ctypes.c_double,
+                                                 ctypes.c_uint64, ctypes.c_void_p]
+            lib.synth_measure_seeded.restype = ctypes.c_double
             lib.synth_ln_array.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
             lib.synth_ln_array.restype = None
             lib.synth_cossin_array.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
@@ -153,6 +157,18 @@ def measure(A: np.ndarray, ubar: np.ndarray, c: float, noise_seed: int):
     return f, float(sigma)
 
 
+def measure_seeded(seed: int, m: int, N: int, ubar: np.ndarray, c: float, noise_seed: int):
+    """measure(gaussian_matrix(seed, m, N), ubar, c, noise_seed), bit for bit, with
+    each row of A generated while it is used (no m x N array)."""
+    ub = np.ascontiguousarray(ubar, dtype=np.float32).reshape(-1)
+    assert ub.size == N
+    f = np.empty(m, dtype=np.float32)
+    sigma = _load().synth_measure_seeded(seed, m, N, ub.ctypes.data, c, noise_seed, f.ctypes.data)
+    if sigma < 0:
+        raise MemoryError("synth_measure_seeded: allocation failed")
+    return f, float(sigma)
+
+
 # ----------------------------------------------------------------------------
 # Phantoms (stand-ins for the paper's Shepp-Logan and natural test images)
 # ----------------------------------------------------------------------------
@@ -230,14 +246,21 @@ def make_problem(n: int, ratio: float, seed: int, n_ellipses: int, mu: float,
                  beta: float = 10.0, tol: float = 1e-4, max_iter: int = 500,
                  noise_c: float = 1e-3, rect_grid: bool = False, name: str = "custom",
                  m: int | None = None, phantom_seed: int | None = None,
-                 noise_seed: int | None = None) -> Problem:
+                 noise_seed: int | None = None, materialise: bool = True) -> Problem:
+    """One problem: phantom, A from `seed`, f = A ubar + noise.  With
+    materialise=False, A is not kept (Problem.A is None) and f comes from
+    measure_seeded, identical to the materialised f."""
     if m is None:
         m = sampled_m(n, ratio)
     ps = seed if phantom_seed is None else phantom_seed
     ns = seed + 1_000_003 if noise_seed is None else noise_seed
     ubar = phantom(n, n_ellipses, ps, rect_grid=rect_grid)
-    A = gaussian_matrix(seed, m, n * n)
-    f, sigma = measure(A, ubar, noise_c, ns)
+    if materialise:
+        A = gaussian_matrix(seed, m, n * n)
+        f, sigma = measure(A, ubar, noise_c, ns)
+    else:
+        A = None
+        f, sigma = measure_seeded(seed, m, n * n, ubar, noise_c, ns)
     return Problem(name, n, m, seed, mu, beta, tol, max_iter, noise_c, ubar, A, f, sigma)
 
 
@@ -279,3 +302,30 @@ def workload_n128() -> Problem:
     rectangle grid, noise 1e-3 * RMS, mu = 1e3, beta = 10, 300 iterations."""
     return make_problem(128, 0.3, 1, 12, 1e3, 10.0, 0.0, 300, 1e-3, rect_grid=True,
                         name="n128_m4915")
+
+
+UNEVEN_SIDES = (64, 96, 128, 192)
+UNEVEN_RATIOS = (0.1, 0.2, 0.3, 0.5)
+
+
+def uneven_shape(seed: int):
+    """(n, ratio) of problem `seed` of the uneven batch: each drawn uniformly
+    from UNEVEN_SIDES and UNEVEN_RATIOS by a generator seeded with `seed`."""
+    rng = np.random.default_rng(np.random.SeedSequence([int(seed), 0x0E7E]))
+    return UNEVEN_SIDES[int(rng.integers(4))], UNEVEN_RATIOS[int(rng.integers(4))]
+
+
+def workload_uneven(count: int = 64, first_seed: int = 1, materialise: bool = False,
+                    sides=None) -> list:
+    """`count` independent problems with seeds first_seed, first_seed+1, ...:
+    n and m/n^2 from uneven_shape (or n restricted to `sides`, redrawn in turn),
+    A ~ N(0, 1/m) from the problem's seed, a 10-ellipse phantom, noise
+    1e-3 * RMS, mu = 1e3, beta = 10, tol 1e-4, <= 500 iterations."""
+    out = []
+    for s in range(first_seed, first_seed + count):
+        n, ratio = uneven_shape(s)
+        if sides is not None:
+            n = tuple(sides)[(s - first_seed) % len(sides)]
+        out.append(make_problem(n, ratio, s, 10, 1e3, 10.0, 1e-4, 500, 1e-3,
+                                name="uneven_%d" % s, materialise=materialise))
+    return out

@@ -238,6 +238,40 @@ SYNTH_EXPORT double synth_measure(const float* A, int m, int64_t N, const float*
     return sigma;
 }
 
+/* The same measurements without a stored A: row i of A is generated, as in
+ * synth_gaussian_rows, while it is multiplied with ubar (same binary64
+ * accumulation order), so f equals synth_measure's for the same seed. */
+SYNTH_EXPORT double synth_measure_seeded(uint64_t seed, int m, int64_t N, const float* ubar,
+                                         double c, uint64_t noise_seed, float* f_out)
+{
+    double* y = (double*)malloc(sizeof(double) * (size_t)m);
+    float* eps = (float*)malloc(sizeof(float) * (size_t)m);
+    if (!y || !eps) { free(y); free(eps); return -1.0; }
+    const float scale = synth_gauss_scale(m);
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int i = 0; i < m; ++i) {
+        const uint64_t base = (uint64_t)i * (uint64_t)N;
+        double acc = 0.0;
+        int64_t j = 0;
+        while (j < N) {
+            uint64_t e = base + (uint64_t)j;
+            float z[4];
+            normals_block(seed, 0u, e >> 2, z);
+            for (uint32_t l = (uint32_t)(e & 3u); l < 4u && j < N; ++l, ++j)
+                acc += (double)(z[l] * scale) * (double)ubar[j];
+        }
+        y[i] = acc;
+    }
+    double ss = 0.0;
+    for (int i = 0; i < m; ++i) ss += y[i] * y[i];
+    double sigma = c * sqrt(ss) / sqrt((double)m);
+    synth_normals(noise_seed, 1u, 0u, m, eps);
+    for (int i = 0; i < m; ++i) f_out[i] = (float)(y[i] + sigma * (double)eps[i]);
+    free(y);
+    free(eps);
+    return sigma;
+}
+
 /* Array forms of the two elementary functions, for tests. */
 SYNTH_EXPORT void synth_ln_array(int64_t count, const float* x, float* out)
 {

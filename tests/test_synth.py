@@ -177,3 +177,19 @@ def test_sampled_m_matches_workloads():
     assert synth.sampled_m(128, 0.3) == 4915
     assert synth.sampled_m(256, 0.2) == 13107
     assert synth.sampled_m(96, 0.1) == 921
+
+
+def test_measure_seeded_equals_materialised():
+    for n, ratio, seed in [(16, 0.3, 3), (48, 0.1, 9)]:
+        P = synth.make_problem(n, ratio, seed, 4, 1e3)
+        Q = synth.make_problem(n, ratio, seed, 4, 1e3, materialise=False)
+        assert Q.A is None
+        assert np.array_equal(P.f, Q.f) and P.sigma == Q.sigma
+
+
+def test_uneven_shapes_cover_the_grid():
+    shapes = [synth.uneven_shape(s) for s in range(1, 65)]
+    assert all(n in synth.UNEVEN_SIDES and r in synth.UNEVEN_RATIOS for n, r in shapes)
+    assert {n for n, _ in shapes} == set(synth.UNEVEN_SIDES)
+    assert {r for _, r in shapes} == set(synth.UNEVEN_RATIOS)
+    assert shapes == [synth.uneven_shape(s) for s in range(1, 65)]   # seeded
