@@ -228,7 +228,8 @@ def test_uneven_batch_single_problem_and_single_measurement(tv):
     # count = 1, and a problem with m = 1 next to a regular one
     P = synth.make_problem(16, 0.0, 81, 3, 1e3, 10.0, m=1, noise_c=0.0)
     Q = synth.make_problem(32, 0.3, 82, 3, 1e3, 10.0, noise_c=1e-3)
-    hp = regen_handle(tv, P.seed, P.m, P.n, P.mu, P.beta, 0.5, max_iter=20)
+    taup = oracle.default_tau(P.A)
+    hp = regen_handle(tv, P.seed, P.m, P.n, P.mu, P.beta, taup, max_iter=20)
     hq = regen_handle(tv, Q.seed, Q.m, Q.n, Q.mu, Q.beta, 0.1, max_iter=20)
     u1 = np.empty(Q.N, np.float32)
     tv.tvcs_solve_batched([hq], [Q.f], [u1])
@@ -236,7 +237,7 @@ def test_uneven_batch_single_problem_and_single_measurement(tv):
     up, uq = np.empty(P.N, np.float32), np.empty(Q.N, np.float32)
     tv.tvcs_solve_batched([hp, hq], [P.f, Q.f], [up, uq])
     # m = 1 cancels the residual (see test_single_measurement_degenerate_case): 1e-4
-    refp = oracle.solve(P.A, P.f, P.n, P.mu, P.beta, 0.5, max_iter=20)
+    refp = oracle.solve(P.A, P.f, P.n, P.mu, P.beta, taup, max_iter=20)
     assert rel(up, refp.u) <= 1e-4
     assert rel(uq, u1) <= 1e-5
     tv.tvcs_destroy(hp)
