@@ -44,7 +44,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-solves", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["n128", "n256", "batch256"], default="n128",
+    ap.add_argument("--workload", choices=["n128", "n256", "batch256", "uneven64"], default="n128",
                     help="n128: 128x128, m=4915, binary32 A (the benchmark workload); "
                          "n256: 256x256, m=13107, A stored per --precision; "
                          "batch256: 256 images of 128x128 sharing one A (bf16 hi/lo)")
@@ -454,6 +454,163 @@ def run_batched(args):
     print(json.dumps(out), flush=True)
 
 
+# ----------------------------------------------------------------------------- uneven arm
+
+# Algorithmic operations per regenerated entry of A (32-bit integer or binary32
+# operations of the generator recipe, plus the products' three FLOPs):
+# Philox4x32-10 = 10 rounds x (2 wide multiplies as 4 ops, 4 xors, 2 key adds)
+# per 4 entries = 25; Box-Muller per pair = uniform 4 + ln 27 + sqrt 2 +
+# cos/sin 32 + 2 products = 67, i.e. 33.5 per entry; scale, dot and update 3.
+ALU_OPS_PER_ENTRY = 61.5
+
+
+def alu_peak():
+    """Entries/s at the FP32/INT32 lane rate: 152 SMs x 128 lanes x max SM clock,
+    divided by the algorithmic operations per entry."""
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            mhz = float(json.load(fh).get("sm_max_mhz", mhz))
+    except Exception:
+        pass
+    return 152 * 128 * mhz * 1e6 / ALU_OPS_PER_ENTRY / 1e9, (
+        "derived: 152 SMs x 128 lanes x %.0f MHz / %.1f ops per entry" % (mhz, ALU_OPS_PER_ENTRY))
+
+
+def run_uneven(args):
+    """64 independent problems (n in {64, 96, 128, 192}, m/n^2 in {0.1, 0.2, 0.3,
+    0.5}), every A regenerated in the product kernel, solved together to tol 1e-4
+    (<= 500 iterations) by one loop graph; compared with the same 64 solves one
+    at a time on the binary32 path with A stored in HBM."""
+    import numpy as np
+    import torch
+
+    import synth
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1001_1774_gb300 as tv
+    t0 = time.perf_counter()
+    probs = synth.workload_uneven(64, materialise=False)
+    t_gen = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    opt = tv.tvcs_default_options()
+    opt.a_mode = tv.TVCS_A_REGENERATE
+    opt.stream = ctypes_stream(stream)
+    hs, taus = [], []
+    t0 = time.perf_counter()
+    for P in probs:
+        opt.max_iter = P.max_iter
+        h = tv.tvcs_create(None, P.seed, P.m, P.n, P.mu, P.beta, P.tol, opt)
+        hs.append(h)
+        taus.append(tv.tvcs_get_tau(h))
+    t_create = time.perf_counter() - t0
+    with torch.cuda.stream(stream):
+        fs = [torch.from_numpy(P.f).cuda() for P in probs]
+        us = [torch.empty(P.N, dtype=torch.float32, device="cuda") for P in probs]
+    stream.synchronize()
+    t0 = time.perf_counter()
+    tv.tvcs_solve_batched(hs, fs, us)      # warm-up: batch state, tile tuning, loop graph, a full solve
+    t_warm = time.perf_counter() - t0
+    sampler = ClockSampler(0)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.2)
+    ev0.record(stream)
+    res = tv.tvcs_solve_batched(hs, fs, us)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    iters = [r.iters for r in res]
+    loops = max(iters)
+    U_gpu = [u.cpu().numpy() for u in us]
+    reps = 3
+    prod_ms = tv.tvcs_time_stage(hs[0], 6, reps) / reps
+    usolve_ms = tv.tvcs_time_stage(hs[0], 7, reps) / reps
+    entries = sum(P.m * P.N for P in probs)
+    entries_solve = sum(P.m * P.N * it for P, it in zip(probs, iters))
+    # end to end: pinned host f in, host images out, inside the timed call
+    F_host = [torch.from_numpy(P.f).pin_memory() for P in probs]
+    U_host = [torch.empty(P.N, dtype=torch.float32).pin_memory() for P in probs]
+    t0 = time.perf_counter()
+    res_e = tv.tvcs_solve_batched(hs, F_host, U_host)
+    e2e_s = time.perf_counter() - t0
+    for h in hs:
+        tv.tvcs_destroy(h)
+    # the same 64 solves one at a time, binary32 with A stored in HBM (generated from the seed)
+    one_ms, agree = 0.0, 0.0
+    for k, (P, tau, ug) in enumerate(zip(probs, taus, U_gpu)):
+        o2 = tv.tvcs_default_options()
+        o2.stream = ctypes_stream(stream)
+        o2.tau = tau
+        o2.max_iter = P.max_iter
+        h = tv.tvcs_create(None, P.seed, P.m, P.n, P.mu, P.beta, P.tol, o2)
+        u = torch.empty(P.N, dtype=torch.float32, device="cuda")
+        r = tv.tvcs_solve(h, fs[k], u)
+        one_ms += r.ms
+        ref = u.cpu().numpy()
+        agree = max(agree, float(np.linalg.norm(ref - ug) / np.linalg.norm(ref)))
+        tv.tvcs_destroy(h)
+    peak = alu_peak()
+    achieved = entries / (prod_ms * 1e-3) / 1e9
+    value = sum(iters) / (ms / 1e3)
+    out = {"metric": METRIC, "value": value, "unit": "problem-iter/s", "n_gpus": 1,
+           "steps": loops, "warmup": loops, "ms_per_step": ms / loops,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded phantoms; every A regenerated from its Philox seed in the kernel)",
+           "recons_per_s": len(probs) / (ms / 1e3),
+           "config": {"workload": "uneven64_regenerated_A", "problems": len(probs),
+                      "sides": sorted({P.n for P in probs}),
+                      "ratios": sorted({round(P.m / P.N, 1) for P in probs}),
+                      "entries_per_product_launch": entries, "mu": 1e3, "tol": 1e-4,
+                      "max_iter": 500, "iterations": {"min": min(iters), "max": loops,
+                                                      "sum": sum(iters)},
+                      "l2": "A is never read from memory; x, r, g slices stay in shared memory"},
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak[0], "unit": "Gentries/s",
+                        "frac": achieved / peak[0], "traffic": None,
+                        "kernel": "k_regen_products (+ k_regen_reduce), all 64 problems per launch",
+                        "launch_ms": prod_ms, "peak_source": peak[1]},
+           "stage_ms": {"regen_products_all": prod_ms, "usolves_all": usolve_ms,
+                        "loop_per_iteration": res[0].ms / loops},
+           "entries_per_s_over_solve": entries_solve / (ms / 1e3),
+           "vs_one_at_a_time_fp32_stored": {"recons_per_s": len(probs) / (one_ms / 1e3),
+                                            "seconds": one_ms / 1e3,
+                                            "speedup": one_ms / ms,
+                                            "max_rel_image_diff": agree},
+           "e2e": {"value": sum(r.iters for r in res_e) / e2e_s, "unit": "problem-iter/s",
+                   "h2d_bytes_per_step": 4 * sum(P.m for P in probs) / loops,
+                   "d2h_bytes_per_step": 4 * sum(P.N for P in probs) / loops},
+           "gpu_launches": (len({P.n for P in probs}) + 3) * loops + 6,
+           "setup_seconds": {"inputs": t_gen, "create_64_handles": t_create, "warmup_solve": t_warm},
+           "clocks": clocks}
+    if not args.no_cpu_baseline:
+        import oracle
+        # parity on the problems the oracle finishes in seconds, at the GPU's iteration counts
+        checks = []
+        for P, tau, ug, it in zip(probs, taus, U_gpu, iters):
+            if P.n == 64 and P.m <= 1229 and len(checks) < 3:
+                A = synth.gaussian_matrix(P.seed, P.m, P.N)
+                ref = oracle.solve(A, P.f, P.n, P.mu, P.beta, tau, max_iter=it)
+                checks.append(float(np.linalg.norm(ug - ref.u.ravel()) / np.linalg.norm(ref.u)))
+        out["parity_vs_oracle"] = {"problems": len(checks), "max_rel_image_err": max(checks),
+                                   "ok": max(checks) <= 1e-4}
+        # oracle speed on one n = 128 problem, scaled to the batch's mean entries per iteration
+        ks = next(k for k, P in enumerate(probs) if P.n == 128)
+        Ps = probs[ks]
+        Ps.A = synth.gaussian_matrix(Ps.seed, Ps.m, Ps.N)
+        cb = oracle_sample(Ps, taus[ks], budget_s=20.0)
+        mean_entries = entries / len(probs)
+        out["cpu_baseline"] = {"value": cb["value"] * Ps.m * Ps.N / mean_entries,
+                               "unit": "problem-iter/s", "cores": cb["cores"], "kind": "oracle",
+                               "sample": "%d IADM iterations of one n=128, m=%d problem (FP64 C "
+                                         "oracle, OpenMP), %.1f s, scaled by entries of A per "
+                                         "iteration to the batch mean" % (cb["iters"], Ps.m,
+                                                                          cb["seconds"])}
+    print(json.dumps(out), flush=True)
+
+
 def bf16_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -503,6 +660,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch256":
         run_batched(args)
+    elif args.workload == "uneven64":
+        run_uneven(args)
     else:
         run_ours(args)
 
