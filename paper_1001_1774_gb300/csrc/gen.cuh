@@ -35,10 +35,9 @@ __device__ __forceinline__ float gen_ln(float x)
     const uint32_t b = __float_as_uint(x);
     int e = (int)((b >> 23) & 0xffu) - 127;
     float mf = __uint_as_float((b & 0x7fffffu) | 0x3f800000u);
-    if (mf > 0x1.6a09e6p+0f) {
-        mf = __fmul_rn(mf, 0.5f);
-        e += 1;
-    }
+    const bool big = mf > 0x1.6a09e6p+0f;   // selects, not branches
+    mf = big ? __fmul_rn(mf, 0.5f) : mf;
+    e += big ? 1 : 0;
     const float s = __fdiv_rn(__fsub_rn(mf, 1.0f), __fadd_rn(mf, 1.0f));
     const float z = __fmul_rn(s, s);
     float q = 0x1.745d18p-4f;
@@ -58,18 +57,9 @@ __device__ __forceinline__ void gen_cossin(uint32_t xb, float& c, float& s)
 {
     const uint32_t o = xb >> 29;
     const float r = __fmul_rn((float)((xb >> 8) & 0x1fffffu), 0x1.0p-21f);
-    float t;
-    uint32_t quad;
-    bool neg;
-    if (o & 1u) {
-        t = __fsub_rn(1.0f, r);
-        quad = ((o + 1u) >> 1) & 3u;
-        neg = true;
-    } else {
-        t = r;
-        quad = (o >> 1) & 3u;
-        neg = false;
-    }
+    const bool odd = (o & 1u) != 0u;
+    const float t = odd ? __fsub_rn(1.0f, r) : r;
+    const uint32_t quad = ((o + (odd ? 1u : 0u)) >> 1) & 3u;
     const float psi = __fmul_rn(t, 0x1.921fb6p-1f);
     const float z = __fmul_rn(psi, psi);
     float ps = 0x1.71de3ap-19f;
@@ -83,13 +73,13 @@ __device__ __forceinline__ void gen_cossin(uint32_t xb, float& c, float& s)
     pc = __fadd_rn(__fmul_rn(pc, z), 0x1.555556p-5f);
     pc = __fadd_rn(__fmul_rn(pc, z), -0x1.0p-1f);
     const float cp = __fadd_rn(1.0f, __fmul_rn(pc, z));
-    if (neg) sp = -sp;
-    switch (quad) {
-        case 0: c = cp; s = sp; break;
-        case 1: c = -sp; s = cp; break;
-        case 2: c = -cp; s = -sp; break;
-        default: c = sp; s = -cp; break;
-    }
+    if (odd) sp = -sp;
+    // rotate by quad quarter turns: (c, s) = (cp, sp), (-sp, cp), (-cp, -sp), (sp, -cp)
+    const bool swap = (quad & 1u) != 0u;
+    const float cc = swap ? sp : cp;
+    const float ss = swap ? cp : sp;
+    c = (quad == 1u || quad == 2u) ? -cc : cc;
+    s = (quad >= 2u) ? -ss : ss;
 }
 
 // Four consecutive standard normals of block b of stream `stream`.

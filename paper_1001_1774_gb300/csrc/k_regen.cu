@@ -15,10 +15,11 @@
 //           cluster (distributed shared memory) and adds them in rank order,
 //           so all blocks hold the same r_i;
 //   update  g_slice += A_tile^T r_tile from the tile buffer.
-// Two tile buffers and split cluster barriers (arrive after the partial dots
-// of tile t, wait before reading them) let the generation of tile t+1 run
-// while the exchange of tile t completes.  Each element of A is generated once
-// per launch.
+// With two tile buffers, split cluster barriers (arrive after the partial
+// dots of tile t, wait before reading them) let the generation of tile t+1
+// run while the exchange of tile t completes; with one, the shared memory
+// halves and the other blocks resident on the SM cover the wait.  Each
+// element of A is generated once per launch.
 //
 // Many problems (own m, N, seed, x, y) share one launch.  Problem p's rows are
 // cut into `chunks` chunks; the chunks of the active problems are numbered in
@@ -118,7 +119,12 @@ __device__ __forceinline__ void fma4(float4& acc, const float4& a, float s)
 
 }  // namespace
 
-__global__ void __launch_bounds__(RG_THREADS, 2)
+// MINB: blocks per SM the registers are budgeted for (2: up to 128 registers
+// a thread, 4: up to 64).  NBUF: tile buffers; with 2 the generation of tile
+// t+1 overlaps the exchange of tile t inside a block, with 1 the shared memory
+// halves and other resident blocks fill the wait.  The tuner picks the variant.
+template <int MINB, int NBUF>
+__global__ void __launch_bounds__(RG_THREADS, MINB)
 k_regen_products(const RegenProb* __restrict__ probs, int P, int mode, int wmax, int tile_cap,
                  int* __restrict__ pre_out)
 {
@@ -127,8 +133,8 @@ k_regen_products(const RegenProb* __restrict__ probs, int P, int mode, int wmax,
     int* scan = pre + REGEN_PMAX + 4;                           // RG_THREADS
     float* us = reinterpret_cast<float*>(scan + RG_THREADS);    // x slice, wmax
     float* gs = us + wmax;                                      // A^T r slice, wmax
-    float* tile = gs + wmax;                                    // 2 x tile_cap
-    float* wpart = tile + 2 * tile_cap;                         // 2 x RTMAX x NWMAX
+    float* tile = gs + wmax;                                    // NBUF x tile_cap
+    float* wpart = tile + NBUF * tile_cap;                      // 2 x RTMAX x NWMAX
     float* slotv = wpart + 2 * RG_RTMAX * RG_NWMAX;             // 2 x RTMAX, read by the peers
     float* rvec = slotv + 2 * RG_RTMAX;                         // 2 x RTMAX
 
@@ -161,12 +167,52 @@ k_regen_products(const RegenProb* __restrict__ probs, int P, int mode, int wmax,
     int head = c;
     int loaded = -1;
 
+    double r2acc = 0.0;
+    // exch + update of tile tm: partial dots from slot buffer sb, entries from tile buffer tb
+    auto finish = [&](const TileMeta& tm, int sb, int tb) {
+        cluster_wait();   // every block's partial dots of tile tm are visible
+        const RegenProb* pp = probs + tm.p;
+        if (tid < tm.nr) {
+            float s = 0.f;
+            for (int k = 0; k < CS; ++k) s += cluster.map_shared_rank(slotv, k)[sb * RG_RTMAX + tid];
+            const int i = tm.i0 + tid;
+            const float rv = pp->y ? s - pp->y[i] : s;
+            rvec[sb * RG_RTMAX + tid] = rv;
+            if (rank == 0) {
+                pp->r[i] = rv;
+                r2acc += (double)rv * (double)rv;
+            }
+        }
+        __syncthreads();
+        const float4* tbuf = reinterpret_cast<const float4*>(tile + tb * tile_cap);
+        float4* g4 = reinterpret_cast<float4*>(gs);
+        const int G = tm.W / 4;
+        for (int q4 = tid; q4 < G; q4 += RG_THREADS) {
+            float4 acc = g4[q4];
+            for (int rr = 0; rr < tm.nr; ++rr) fma4(acc, tbuf[rr * G + q4], rvec[sb * RG_RTMAX + rr]);
+            g4[q4] = acc;
+        }
+        if (tm.last) {   // each thread stores and clears the groups it accumulated
+            float4* dst = reinterpret_cast<float4*>(pp->gslot + (size_t)tm.head * pp->N +
+                                                    (size_t)rank * tm.W);
+            for (int q4 = tid; q4 < G; q4 += RG_THREADS) {
+                dst[q4] = g4[q4];
+                g4[q4] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            if (rank == 0 && tid < 32) {   // r2acc lives in threads < 16 of block 0
+                const double v = warp_sum(r2acc);
+                if (tid == 0) pp->r2slot[tm.head] = v;
+            }
+            r2acc = 0.0;
+        }
+    };
+
     TileMeta prev{};
     bool have_prev = false;
-    double r2acc = 0.0;
     for (int t = 0;; ++t) {
         const bool have_cur = j < j1;
-        const int buf = t & 1;
+        const int sb = t & 1;                  // partial-dot and r buffers
+        const int tb = NBUF == 2 ? sb : 0;     // tile buffer
         TileMeta cur{};
         if (have_cur) {
             if (loaded != p) {   // x slice of a new problem (every thread is past the last gen)
@@ -192,29 +238,37 @@ k_regen_products(const RegenProb* __restrict__ probs, int P, int mode, int wmax,
                     const unsigned long long i = (unsigned long long)(cur.i0 + rr);
                     const unsigned long long b0 =
                         (i * (unsigned long long)N + (unsigned long long)rank * W) >> 2;
-                    float4* trow = reinterpret_cast<float4*>(tile + buf * tile_cap) + rr * G;
+                    float4* trow = reinterpret_cast<float4*>(tile + tb * tile_cap) + rr * G;
                     const float4* x4 = reinterpret_cast<const float4*>(us);
                     const float scale = pr->scale;
                     const unsigned long long seed = pr->seed;
-                    for (int q4 = lane; q4 < G; q4 += tpr) {
-                        const float4 z = gen_normals4(seed, 0u, b0 + q4);
+                    auto emit = [&](int q, const float4& z) {
                         float4 a;
                         a.x = __fmul_rn(z.x, scale);
                         a.y = __fmul_rn(z.y, scale);
                         a.z = __fmul_rn(z.z, scale);
                         a.w = __fmul_rn(z.w, scale);
-                        trow[q4] = a;
-                        const float4 xv = x4[q4];
+                        trow[q] = a;
+                        const float4 xv = x4[q];
                         dot = fmaf(a.x, xv.x, dot);
                         dot = fmaf(a.y, xv.y, dot);
                         dot = fmaf(a.z, xv.z, dot);
                         dot = fmaf(a.w, xv.w, dot);
+                    };
+                    // two independent Philox blocks in flight per thread (latency hiding)
+                    int q4 = lane;
+                    for (; q4 + tpr < G; q4 += 2 * tpr) {
+                        const float4 z0 = gen_normals4(seed, 0u, b0 + q4);
+                        const float4 z1 = gen_normals4(seed, 0u, b0 + q4 + tpr);
+                        emit(q4, z0);
+                        emit(q4 + tpr, z1);
                     }
+                    if (q4 < G) emit(q4, gen_normals4(seed, 0u, b0 + q4));
                 }
                 const int wl = tpr < 32 ? tpr : 32;
                 for (int off = wl >> 1; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
                 if (rr < cur.nr && (lane & (wl - 1)) == 0)
-                    wpart[(buf * RG_RTMAX + rr) * RG_NWMAX + (lane >> 5)] = dot;
+                    wpart[(sb * RG_RTMAX + rr) * RG_NWMAX + (lane >> 5)] = dot;
             }
             // advance the cursor
             row += cur.nr;
@@ -240,55 +294,23 @@ k_regen_products(const RegenProb* __restrict__ probs, int P, int mode, int wmax,
             }
             cur.last = (j >= j1 || p != cur.p) ? 1 : 0;
         }
-        if (have_prev) {
-            cluster_wait();   // every block's partial dots of the previous tile are visible
-            const int pb = buf ^ 1;
-            const RegenProb* pp = probs + prev.p;
-            if (tid < prev.nr) {
-                float s = 0.f;
-                for (int k = 0; k < CS; ++k) s += cluster.map_shared_rank(slotv, k)[pb * RG_RTMAX + tid];
-                const int i = prev.i0 + tid;
-                const float rv = pp->y ? s - pp->y[i] : s;
-                rvec[pb * RG_RTMAX + tid] = rv;
-                if (rank == 0) {
-                    pp->r[i] = rv;
-                    r2acc += (double)rv * (double)rv;
-                }
-            }
-            __syncthreads();
-            const float4* tb = reinterpret_cast<const float4*>(tile + pb * tile_cap);
-            float4* g4 = reinterpret_cast<float4*>(gs);
-            const int G = prev.W / 4;
-            for (int q4 = tid; q4 < G; q4 += RG_THREADS) {
-                float4 acc = g4[q4];
-                for (int rr = 0; rr < prev.nr; ++rr) fma4(acc, tb[rr * G + q4], rvec[pb * RG_RTMAX + rr]);
-                g4[q4] = acc;
-            }
-            if (prev.last) {   // each thread stores and clears the groups it accumulated
-                float4* dst = reinterpret_cast<float4*>(pp->gslot + (size_t)prev.head * pp->N +
-                                                        (size_t)rank * prev.W);
-                for (int q4 = tid; q4 < G; q4 += RG_THREADS) {
-                    dst[q4] = g4[q4];
-                    g4[q4] = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-                if (rank == 0 && tid < 32) {   // r2acc lives in threads < 16 of block 0
-                    const double v = warp_sum(r2acc);
-                    if (tid == 0) pp->r2slot[prev.head] = v;
-                }
-                r2acc = 0.0;
-            }
-        }
+        if (NBUF == 2 && have_prev) finish(prev, sb ^ 1, tb ^ 1);
         if (!have_cur) break;
-        __syncthreads();   // partial dots of this tile complete; previous tile buffer free
+        __syncthreads();   // partial dots of this tile complete; the other tile buffer is free
         if (tid < cur.nr) {
             const int nw = (RG_THREADS / cur.rt) / 32;
             float s = 0.f;
-            for (int w = 0; w < (nw > 0 ? nw : 1); ++w) s += wpart[(buf * RG_RTMAX + tid) * RG_NWMAX + w];
-            slotv[buf * RG_RTMAX + tid] = s;
+            for (int w = 0; w < (nw > 0 ? nw : 1); ++w) s += wpart[(sb * RG_RTMAX + tid) * RG_NWMAX + w];
+            slotv[sb * RG_RTMAX + tid] = s;
         }
         cluster_arrive();
-        prev = cur;
-        have_prev = true;
+        if (NBUF == 1) {
+            finish(cur, sb, 0);
+            __syncthreads();   // the tile buffer is free for the next tile
+        } else {
+            prev = cur;
+            have_prev = true;
+        }
     }
     // the peers may still read this block's slots: leave together
     cluster_arrive();
@@ -346,10 +368,10 @@ k_regen_reduce(const RegenProb* __restrict__ probs, int P, int Q, const int* __r
     }
 }
 
-static size_t regen_smem(int wmax, int tile_cap)
+static size_t regen_smem(int wmax, int tile_cap, int nbuf)
 {
     return sizeof(int) * (REGEN_PMAX + 4 + RG_THREADS) +
-           sizeof(float) * (2 * (size_t)wmax + 2 * (size_t)tile_cap + 2 * RG_RTMAX * RG_NWMAX +
+           sizeof(float) * (2 * (size_t)wmax + (size_t)nbuf * tile_cap + 2 * RG_RTMAX * RG_NWMAX +
                             4 * RG_RTMAX);
 }
 
@@ -358,26 +380,13 @@ int regen_tile_rows(const RegenPlan& plan, int N)
     return tile_rows_for(N / plan.cs, plan.tile_cap);
 }
 
-bool regen_configure(RegenPlan* plan)
+template <int MINB, int NBUF>
+static bool configure_t(RegenPlan* plan, int optin)
 {
-    plan->clusters = 0;
-    if (plan->cs < 1 || plan->cs > 16 || plan->wmax <= 0 || plan->wmax % 4 != 0 ||
-        plan->tile_cap < plan->wmax || plan->tile_cap % 4 != 0)
-        return false;
-    plan->smem = regen_smem(plan->wmax, plan->tile_cap);
-    // The attributes are per kernel, not per plan: allow the largest opt-in
-    // size once, so that plans of different sizes can alternate.
-    int dev = 0, optin = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    if (plan->smem > (size_t)optin) return false;
-    if (cudaFuncSetAttribute(k_regen_products, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(k_regen_products, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-            cudaSuccess) {
+    if (cudaFuncSetAttribute(k_regen_products<MINB, NBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin) != cudaSuccess ||
+        cudaFuncSetAttribute(k_regen_products<MINB, NBUF>, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                             1) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
@@ -393,13 +402,35 @@ bool regen_configure(RegenPlan* plan)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_regen_products, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, k_regen_products<MINB, NBUF>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
     if (n > RG_QMAX) n = RG_QMAX;
     plan->clusters = n;
     return n >= 1;
+}
+
+bool regen_configure(RegenPlan* plan)
+{
+    plan->clusters = 0;
+    if (plan->cs < 1 || plan->cs > 16 || plan->wmax <= 0 || plan->wmax % 4 != 0 ||
+        plan->tile_cap < plan->wmax || plan->tile_cap % 4 != 0 ||
+        (plan->minb != 2 && plan->minb != 4) || (plan->nbuf != 1 && plan->nbuf != 2))
+        return false;
+    plan->smem = regen_smem(plan->wmax, plan->tile_cap, plan->nbuf);
+    // The attributes are per kernel, not per plan: allow the largest opt-in
+    // size once, so that plans of different sizes can alternate.
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (plan->smem > (size_t)optin) return false;
+    if (plan->minb == 2)
+        return plan->nbuf == 2 ? configure_t<2, 2>(plan, optin) : configure_t<2, 1>(plan, optin);
+    return plan->nbuf == 2 ? configure_t<4, 2>(plan, optin) : configure_t<4, 1>(plan, optin);
 }
 
 void launch_regen(const RegenProb* probs, int P, int mode, const RegenPlan& plan, int* pre_out,
@@ -417,7 +448,9 @@ void launch_regen(const RegenProb* probs, int P, int mode, const RegenPlan& plan
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_regen_products, probs, P, mode, plan.wmax, plan.tile_cap, pre_out);
+    auto k = plan.minb == 4 ? (plan.nbuf == 2 ? k_regen_products<4, 2> : k_regen_products<4, 1>)
+                            : (plan.nbuf == 2 ? k_regen_products<2, 2> : k_regen_products<2, 1>);
+    cudaLaunchKernelEx(&cfg, k, probs, P, mode, plan.wmax, plan.tile_cap, pre_out);
 }
 
 void launch_regen_reduce(const RegenProb* probs, int P, int maxN, int mode, const RegenPlan& plan,

@@ -14,9 +14,10 @@
 // reduction, and the loop condition (a WHILE node, as in the other paths).
 // Problems that met eq. (stop) drop out of the product launch's work list.
 //
-// Tiles are chosen by measurement: the candidate cluster sizes (4, 8, 16) and
-// tile heights (4, 8, 16 rows of the largest problem) are each timed on the
-// actual problem set and the fastest is kept.
+// Tiles are chosen by measurement: every candidate of cluster size (4, 8, 16),
+// tile height (2, 4, 8 rows of the largest problem) and kernel variant
+// (registers for 2 or 4 blocks per SM; one or two tile buffers) is timed on
+// the actual problem set and the fastest is kept.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -124,15 +125,19 @@ void chunking(const RegenPlan& plan, int m, int N, double target, int* rpc, int*
 std::vector<RegenPlan> candidates(int maxN)
 {
     std::vector<RegenPlan> out;
-    for (int cs : {4, 8, 16})
-        for (int rt : {4, 8, 16}) {
-            RegenPlan p;
-            p.cs = cs;
-            p.wmax = maxN / cs;
-            p.tile_cap = rt * p.wmax;
-            if (maxN % (4 * cs) != 0) continue;
-            if (regen_configure(&p)) out.push_back(p);
-        }
+    const int variants[3][2] = {{2, 2}, {4, 2}, {4, 1}};   // (blocks per SM, tile buffers)
+    for (const auto& v : variants)
+        for (int cs : {4, 8, 16})
+            for (int rt : {2, 4, 8}) {
+                RegenPlan p;
+                p.cs = cs;
+                p.minb = v[0];
+                p.nbuf = v[1];
+                p.wmax = maxN / cs;
+                p.tile_cap = rt * p.wmax;
+                if (maxN % (4 * cs) != 0) continue;
+                if (regen_configure(&p)) out.push_back(p);
+            }
     return out;
 }
 
@@ -173,7 +178,7 @@ void apply_layout(const Layout& L, float* gslot, double* r2slot, std::vector<Reg
     }
 }
 
-// Times each candidate plan on the problem set (one warm-up launch, two timed)
+// Times each candidate plan on the problem set (one warm-up launch, one timed)
 // and returns the fastest.  gslot / r2slot must hold the largest layout.
 tvcs_status autotune(std::vector<RegenProb> probs, int maxN, int per_cluster, RegenProb* dtab,
                      float* gslot, double* r2slot, int* pre, cudaStream_t s, RegenPlan* best)
@@ -194,10 +199,8 @@ tvcs_status autotune(std::vector<RegenProb> probs, int maxN, int per_cluster, Re
         launch_regen(dtab, P, MODE_PLAIN, c, pre, s);
         launch_regen_reduce(dtab, P, maxN, MODE_PLAIN, c, pre, 0ull, 0, s);
         cudaEventRecord(e0, s);
-        for (int k = 0; k < 2; ++k) {
-            launch_regen(dtab, P, MODE_PLAIN, c, pre, s);
-            launch_regen_reduce(dtab, P, maxN, MODE_PLAIN, c, pre, 0ull, 0, s);
-        }
+        launch_regen(dtab, P, MODE_PLAIN, c, pre, s);
+        launch_regen_reduce(dtab, P, maxN, MODE_PLAIN, c, pre, 0ull, 0, s);
         cudaEventRecord(e1, s);
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {
