@@ -43,11 +43,16 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=300)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-solves", type=int, default=5)
+    ap.add_argument("--ref-budget", type=float, default=60.0,
+                    help="seconds of oracle iterations the reference arm times")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["n128", "n256", "batch256", "uneven64"], default="n128",
+    ap.add_argument("--workload", choices=["n128", "n32", "n256", "batch256", "uneven64"],
+                    default="n128",
                     help="n128: 128x128, m=4915, binary32 A (the benchmark workload); "
+                         "n32: 32x32, m=307, to tol 1e-4; "
                          "n256: 256x256, m=13107, A stored per --precision; "
-                         "batch256: 256 images of 128x128 sharing one A (bf16 hi/lo)")
+                         "batch256: 256 images of 128x128 sharing one A (bf16 hi/lo); "
+                         "uneven64: 64 problems of n in {64..192}, A regenerated in the kernel")
     ap.add_argument("--precision", type=int, default=0,
                     help="storage of A: 0 binary32, 1 bf16 hi+lo, 2 fp8 e4m3 + bf16 correction")
     ap.add_argument("--host-loop", action="store_true",
@@ -76,13 +81,42 @@ def hbm_peak():
 STORAGE = {0: ("fp32", 4), 1: ("bf16x2", 4), 2: ("fp8e4m3+bf16", 3)}
 
 
+def workload_spec(workload: str, rank: int) -> dict:
+    """The problem rank `rank` solves: the named single-image configuration on
+    rank 0 and, on the other ranks, the same configuration with seed + rank (an
+    independent problem of the same shape: weak scaling, no data exchange)."""
+    if workload == "n256":
+        return dict(n=256, ratio=0.2, seed=2 + rank, n_ellipses=20, mu=5e2, beta=10.0, tol=0.0,
+                    max_iter=ITERS_PER_RECON, noise_c=5e-3, rect_grid=False)
+    if workload == "n32":
+        return dict(n=32, ratio=0.3, seed=0 + rank, n_ellipses=6, mu=1e3, beta=10.0, tol=1e-4,
+                    max_iter=500, noise_c=1e-3, rect_grid=False)
+    return dict(n=128, ratio=0.3, seed=1 + rank, n_ellipses=12, mu=1e3, beta=10.0, tol=0.0,
+                max_iter=ITERS_PER_RECON, noise_c=1e-3, rect_grid=True)
+
+
 def make_workload(args, rank):
     import synth
-    if args.workload == "n256":
-        return synth.workload_n256() if rank == 0 else synth.make_problem(
-            256, 0.2, 2 + rank, 20, 5e2, 10.0, 0.0, ITERS_PER_RECON, 5e-3)
-    return synth.workload_n128() if rank == 0 else synth.make_problem(
-        128, 0.3, 1 + rank, 12, 1e3, 10.0, 0.0, ITERS_PER_RECON, 1e-3, rect_grid=True)
+    sp = workload_spec(args.workload, rank)
+    return synth.make_problem(sp["n"], sp["ratio"], sp["seed"], sp["n_ellipses"], sp["mu"],
+                              sp["beta"], sp["tol"], sp["max_iter"], sp["noise_c"],
+                              rect_grid=sp["rect_grid"], name="%s_rank%d" % (args.workload, rank))
+
+
+def max_over_ranks(x: float, ws: int, device: str = "cpu") -> float:
+    """The largest of the ranks' values (a time: the job ends with its slowest rank)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ws: int, units_per_rank: float, ms: float) -> float:
+    """Units all ranks processed per second, over the slowest rank's time."""
+    return ws * units_per_rank / (ms / 1e3)
 
 
 def workload_config(P, A_bytes, precision=0):
@@ -202,9 +236,11 @@ def run_ours(args):
     import synth
     import __graft_entry__
     ws, rank, local = dist_env()
+    dev = "cuda"
     if ws > 1:
         backend = "nccl" if torch.cuda.is_available() else "gloo"
         dist.init_process_group(backend)
+        dev = "cuda" if backend == "nccl" else "cpu"
     torch.cuda.set_device(local)
     if rank == 0:
         __graft_entry__.build()
@@ -250,11 +286,7 @@ def run_ours(args):
     torch.cuda.nvtx.range_pop()
     clocks = sampler.stop()
     barrier()
-    ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), ws, dev)
     assert res.iters == args.steps, res.iters
 
     # Dominant kernel (products, one pass over A, with the reduction of its
@@ -284,11 +316,7 @@ def run_ours(args):
     for _ in range(args.e2e_solves):
         r = tv.tvcs_solve(h, f_host, u_host)
         assert r.iters == ITERS_PER_RECON
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws, dev)
     u_gpu = u_host.numpy().copy()
 
     out = None
@@ -298,7 +326,7 @@ def run_ours(args):
         alg_bytes = A_bytes + 4 * (P.N + 2 * P.m)
         achieved = alg_bytes / (prod_us * 1e-6) / 1e9
         traffic = traffic_from_profile() if args.workload == "n128" else None
-        value = ws * args.steps / (ms / 1e3)
+        value = whole_job_rate(ws, args.steps, ms)
         e2e_iters = ws * args.e2e_solves * ITERS_PER_RECON
         out = {
             "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": ws,
@@ -630,8 +658,8 @@ def run_reference(args):
     import oracle
     import synth
     P = make_workload(args, 0)
-    tau = oracle.default_tau(P.A, 100 if args.workload == "n128" else 20)
-    budget = 60.0
+    tau = oracle.default_tau(P.A, 20 if args.workload == "n256" else 100)
+    budget = args.ref_budget
     # warm-up: W oracle iterations at most, bounded in time
     t0 = time.perf_counter()
     oracle.solve(P.A, P.f, P.n, P.mu, P.beta, tau, max_iter=min(args.warmup, 3))

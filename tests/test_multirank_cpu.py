@@ -1,0 +1,77 @@
+"""Host logic of the bench's multi-GPU path on CPU: two ranks over gloo (one
+process per rank, rendezvous on 127.0.0.1), and the reference arm's rank
+gating.  Ranks solve independent problems (weak scaling, no exchange on the
+data path); the job's time is the slowest rank's and its rate counts every
+rank's units."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, ws, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(ws), LOCAL_RANK=str(rank))
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    sys.path.insert(0, ROOT)
+    import bench
+    spec = bench.workload_spec("n128", rank)
+    ms = bench.max_over_ranks(10.0 * (rank + 1), ws, "cpu")
+    rate = bench.whole_job_rate(ws, 100, ms)
+    with open(os.path.join(out_dir, "r%d.json" % rank), "w") as fh:
+        json.dump({"spec": spec, "ms": ms, "rate": rate, "env": bench.dist_env()}, fh)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_gloo_max_time_and_whole_job_rate(tmp_path):
+    import torch.multiprocessing as mp
+    mp.spawn(_worker, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    r = [json.load(open(tmp_path / ("r%d.json" % k))) for k in range(2)]
+    assert r[0]["ms"] == r[1]["ms"] == 20.0          # slowest rank
+    assert r[0]["rate"] == pytest.approx(2 * 100 / 0.020)
+    assert r[0]["env"] == [2, 0, 0] and r[1]["env"] == [2, 1, 1]
+    s0, s1 = r[0]["spec"], r[1]["spec"]
+    assert s0["seed"] != s1["seed"]                  # independent problems ...
+    assert {k: v for k, v in s0.items() if k != "seed"} == {k: v for k, v in s1.items() if k != "seed"}
+
+
+def _run_bench(args, env_extra, timeout=600):
+    env = dict(os.environ, **env_extra)
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args, cwd=ROOT,
+                          env=env, capture_output=True, text=True, timeout=timeout)
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    p = _run_bench(["--impl", "reference", "--gpus", "2", "--workload", "n32", "--steps", "5",
+                    "--warmup", "1", "--ref-budget", "1"],
+                   {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert p.returncode == 0, p.stderr[-2000:]
+    assert p.stdout.strip() == ""
+
+
+def test_reference_arm_prints_one_contract_line():
+    p = _run_bench(["--impl", "reference", "--workload", "n32", "--steps", "5", "--warmup", "1",
+                    "--ref-budget", "2"], {"RANK": "0", "WORLD_SIZE": "1", "LOCAL_RANK": "0"})
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [ln for ln in p.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["higher_is_better"] is True
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "dtype",
+              "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
