@@ -431,7 +431,9 @@ def run_batched(args):
     assert all(r.iters == args.steps for r in res)
     loop_ms = res[0].ms
     reps = 50
+    torch.cuda.nvtx.range_push("stage3")
     gemm_us = tv.tvcs_time_stage(h, 3, reps) * 1e3 / reps
+    torch.cuda.nvtx.range_pop()
     fix_us = tv.tvcs_time_stage(h, 4, reps) * 1e3 / reps
     us_us = tv.tvcs_time_stage(h, 5, reps) * 1e3 / reps
     # end to end with pinned host buffers (f in, images out inside the timed call)
@@ -555,7 +557,9 @@ def run_uneven(args):
     loops = max(iters)
     U_gpu = [u.cpu().numpy() for u in us]
     reps = 3
+    torch.cuda.nvtx.range_push("stage6")
     prod_ms = tv.tvcs_time_stage(hs[0], 6, reps) / reps
+    torch.cuda.nvtx.range_pop()
     usolve_ms = tv.tvcs_time_stage(hs[0], 7, reps) / reps
     entries = sum(P.m * P.N for P in probs)
     entries_solve = sum(P.m * P.N * it for P, it in zip(probs, iters))
