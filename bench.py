@@ -124,7 +124,9 @@ def workload_config(P, A_bytes, precision=0):
     return {"workload": name, "n": P.n, "m": P.m, "N": P.N, "A_storage": STORAGE[precision][0],
             "mu": P.mu, "beta": P.beta, "iters_per_recon": ITERS_PER_RECON,
             "A_bytes": A_bytes, "algo": "IADM",
-            "l2": "inputs larger than L2 (A = %.0f MB > 129 MB); no flush" % (A_bytes / 1e6),
+            "l2": ("inputs larger than L2 (A = %.0f MB > 129 MB); no flush" % (A_bytes / 1e6)
+                   if A_bytes > 129e6 else
+                   "A (%.1f MB) is L2-resident: latency-bound, no roofline claim" % (A_bytes / 1e6)),
             "parallelism": "one independent problem per GPU"}
 
 
