@@ -2,8 +2,9 @@
 // encoding matrix: k_gen.cu writes A to memory, k_regen.cu regenerates it tile
 // by tile inside the product kernel.  The recipe is stated at the top of
 // k_gen.cu; every floating-point step is a single binary32 operation with
-// round-to-nearest (explicit __f*_rn intrinsics, so nothing is contracted),
-// which makes the values identical to the host-side input generator.
+// round-to-nearest (explicit __f*_rn intrinsics: the polynomial steps are fused
+// multiply-adds, nothing else is contracted), which makes the values identical
+// to the host-side input generator.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -41,15 +42,15 @@ __device__ __forceinline__ float gen_ln(float x)
     const float s = __fdiv_rn(__fsub_rn(mf, 1.0f), __fadd_rn(mf, 1.0f));
     const float z = __fmul_rn(s, s);
     float q = 0x1.745d18p-4f;
-    q = __fadd_rn(__fmul_rn(q, z), 0x1.c71c72p-4f);
-    q = __fadd_rn(__fmul_rn(q, z), 0x1.24924ap-3f);
-    q = __fadd_rn(__fmul_rn(q, z), 0x1.99999ap-3f);
-    q = __fadd_rn(__fmul_rn(q, z), 0x1.555556p-2f);
+    q = __fmaf_rn(q, z, 0x1.c71c72p-4f);
+    q = __fmaf_rn(q, z, 0x1.24924ap-3f);
+    q = __fmaf_rn(q, z, 0x1.99999ap-3f);
+    q = __fmaf_rn(q, z, 0x1.555556p-2f);
     const float t = __fmul_rn(__fmul_rn(s, z), q);
     const float lnm = __fmul_rn(__fadd_rn(s, t), 2.0f);
     const float ef = (float)e;
     const float hi = __fmul_rn(ef, 0x1.62e4p-1f);
-    const float lo = __fadd_rn(__fmul_rn(ef, 0x1.7f7d1cp-20f), lnm);
+    const float lo = __fmaf_rn(ef, 0x1.7f7d1cp-20f, lnm);
     return __fadd_rn(hi, lo);
 }
 
@@ -63,16 +64,16 @@ __device__ __forceinline__ void gen_cossin(uint32_t xb, float& c, float& s)
     const float psi = __fmul_rn(t, 0x1.921fb6p-1f);
     const float z = __fmul_rn(psi, psi);
     float ps = 0x1.71de3ap-19f;
-    ps = __fadd_rn(__fmul_rn(ps, z), -0x1.a01a02p-13f);
-    ps = __fadd_rn(__fmul_rn(ps, z), 0x1.111112p-7f);
-    ps = __fadd_rn(__fmul_rn(ps, z), -0x1.555556p-3f);
-    float sp = __fadd_rn(psi, __fmul_rn(__fmul_rn(psi, z), ps));
+    ps = __fmaf_rn(ps, z, -0x1.a01a02p-13f);
+    ps = __fmaf_rn(ps, z, 0x1.111112p-7f);
+    ps = __fmaf_rn(ps, z, -0x1.555556p-3f);
+    float sp = __fmaf_rn(__fmul_rn(psi, z), ps, psi);
     float pc = -0x1.27e4fcp-22f;
-    pc = __fadd_rn(__fmul_rn(pc, z), 0x1.a01a02p-16f);
-    pc = __fadd_rn(__fmul_rn(pc, z), -0x1.6c16c2p-10f);
-    pc = __fadd_rn(__fmul_rn(pc, z), 0x1.555556p-5f);
-    pc = __fadd_rn(__fmul_rn(pc, z), -0x1.0p-1f);
-    const float cp = __fadd_rn(1.0f, __fmul_rn(pc, z));
+    pc = __fmaf_rn(pc, z, 0x1.a01a02p-16f);
+    pc = __fmaf_rn(pc, z, -0x1.6c16c2p-10f);
+    pc = __fmaf_rn(pc, z, 0x1.555556p-5f);
+    pc = __fmaf_rn(pc, z, -0x1.0p-1f);
+    const float cp = __fmaf_rn(pc, z, 1.0f);
     if (odd) sp = -sp;
     // rotate by quad quarter turns: (c, s) = (cp, sp), (-sp, cp), (-cp, -sp), (sp, -cp)
     const bool swap = (quad & 1u) != 0u;

@@ -1,7 +1,8 @@
 // Counter-based Gaussian encoding matrix, generated on the device.
 //
 // Recipe (every floating-point step a single IEEE binary32 operation with
-// round-to-nearest; the explicit __f*_rn intrinsics forbid contraction):
+// round-to-nearest -- fused multiply-adds where the recipe says so, nothing
+// else contracted: the explicit __f*_rn intrinsics fix each step):
 //   element e of stream s -> block b = e >> 2, lane = e & 3
 //   (x0..x3) = Philox4x32-10(counter (lo32 b, hi32 b, s, 0), key (lo32 seed, hi32 seed))
 //              (Salmon, Moraes, Dror, Shaw, SC'11: multipliers 0xD2511F53,
@@ -9,11 +10,12 @@
 //   lanes 0,1 take (x0,x1), lanes 2,3 take (x2,x3); for a pair (xa, xb):
 //     ua  = ((xa >> 8) + 1) * 2^-24,  rad = sqrt(-2 ln ua)       (Box-Muller, 1958)
 //     ln  : ua = 2^e m, m in [sqrt(1/2), sqrt(2)), s = (m-1)/(m+1),
-//           ln m = 2 (s + s^3/3 + ... + s^11/11) (Horner in s^2), ln 2 split in
-//           a 16-bit head and a tail
+//           ln m = 2 (s + s^3/3 + ... + s^11/11) (Horner in s^2 with fused
+//           multiply-adds), ln 2 split in a 16-bit head and a tail
 //     angle 2 pi (xb >> 8) 2^-24: octant o = xb >> 29, r = ((xb >> 8) & 0x1fffff) 2^-21,
 //           angle = Q pi/2 +- psi with psi = t pi/4, t = r or 1 - r; sin psi and
-//           cos psi by Taylor series to degree 9 and 10
+//           cos psi by Taylor series to degree 9 and 10 (Horner, fused
+//           multiply-adds)
 //     even lane: rad * cos, odd lane: rad * sin
 //   A[i][j] = z(i*N + j) * scale, scale = binary32(1/sqrt(m)) (passed in).
 // The same values are produced by the host-side input generator; tests check

@@ -126,11 +126,11 @@ __device__ __forceinline__ void fma4(float4& acc, const float4& a, float s)
 template <int MINB, int NBUF>
 __global__ void __launch_bounds__(RG_THREADS, MINB)
 k_regen_products(const RegenProb* __restrict__ probs, int P, int mode, int wmax, int tile_cap,
-                 int* __restrict__ pre_out)
+                 int pcap, int* __restrict__ pre_out)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    int* pre = reinterpret_cast<int*>(smem);                    // REGEN_PMAX + 4
-    int* scan = pre + REGEN_PMAX + 4;                           // RG_THREADS
+    int* pre = reinterpret_cast<int*>(smem);                    // pcap + 4 (pcap >= P, multiple of 4)
+    int* scan = pre + pcap + 4;                                 // RG_THREADS
     float* us = reinterpret_cast<float*>(scan + RG_THREADS);    // x slice, wmax
     float* gs = us + wmax;                                      // A^T r slice, wmax
     float* tile = gs + wmax;                                    // NBUF x tile_cap
@@ -368,9 +368,9 @@ k_regen_reduce(const RegenProb* __restrict__ probs, int P, int Q, const int* __r
     }
 }
 
-static size_t regen_smem(int wmax, int tile_cap, int nbuf)
+static size_t regen_smem(int wmax, int tile_cap, int nbuf, int pcap)
 {
-    return sizeof(int) * (REGEN_PMAX + 4 + RG_THREADS) +
+    return sizeof(int) * ((size_t)pcap + 4 + RG_THREADS) +
            sizeof(float) * (2 * (size_t)wmax + (size_t)nbuf * tile_cap + 2 * RG_RTMAX * RG_NWMAX +
                             4 * RG_RTMAX);
 }
@@ -416,9 +416,11 @@ bool regen_configure(RegenPlan* plan)
     plan->clusters = 0;
     if (plan->cs < 1 || plan->cs > 16 || plan->wmax <= 0 || plan->wmax % 4 != 0 ||
         plan->tile_cap < plan->wmax || plan->tile_cap % 4 != 0 ||
-        (plan->minb != 2 && plan->minb != 4) || (plan->nbuf != 1 && plan->nbuf != 2))
+        (plan->minb != 2 && plan->minb != 4) || (plan->nbuf != 1 && plan->nbuf != 2) ||
+        plan->pcap < 1 || plan->pcap > REGEN_PMAX)
         return false;
-    plan->smem = regen_smem(plan->wmax, plan->tile_cap, plan->nbuf);
+    plan->pcap = (plan->pcap + 3) / 4 * 4;
+    plan->smem = regen_smem(plan->wmax, plan->tile_cap, plan->nbuf, plan->pcap);
     // The attributes are per kernel, not per plan: allow the largest opt-in
     // size once, so that plans of different sizes can alternate.
     int dev = 0, optin = 0;
@@ -450,7 +452,7 @@ void launch_regen(const RegenProb* probs, int P, int mode, const RegenPlan& plan
     cfg.numAttrs = 1;
     auto k = plan.minb == 4 ? (plan.nbuf == 2 ? k_regen_products<4, 2> : k_regen_products<4, 1>)
                             : (plan.nbuf == 2 ? k_regen_products<2, 2> : k_regen_products<2, 1>);
-    cudaLaunchKernelEx(&cfg, k, probs, P, mode, plan.wmax, plan.tile_cap, pre_out);
+    cudaLaunchKernelEx(&cfg, k, probs, P, mode, plan.wmax, plan.tile_cap, plan.pcap, pre_out);
 }
 
 void launch_regen_reduce(const RegenProb* probs, int P, int maxN, int mode, const RegenPlan& plan,

@@ -15,7 +15,7 @@
 // Problems that met eq. (stop) drop out of the product launch's work list.
 //
 // Tiles are chosen by measurement: every candidate of cluster size (4, 8, 16),
-// tile height (2, 4, 8 rows of the largest problem) and kernel variant
+// tile height (1, 2, 4, 8 rows of the largest problem) and kernel variant
 // (registers for 2 or 4 blocks per SM; one or two tile buffers) is timed on
 // the actual problem set and the fastest is kept.
 #include <cuda_runtime.h>
@@ -122,17 +122,18 @@ void chunking(const RegenPlan& plan, int m, int N, double target, int* rpc, int*
     *chunks = (int)((m + rows - 1) / rows);
 }
 
-std::vector<RegenPlan> candidates(int maxN)
+std::vector<RegenPlan> candidates(int maxN, int P)
 {
     std::vector<RegenPlan> out;
     const int variants[3][2] = {{2, 2}, {4, 2}, {4, 1}};   // (blocks per SM, tile buffers)
     for (const auto& v : variants)
         for (int cs : {4, 8, 16})
-            for (int rt : {2, 4, 8}) {
+            for (int rt : {1, 2, 4, 8}) {
                 RegenPlan p;
                 p.cs = cs;
                 p.minb = v[0];
                 p.nbuf = v[1];
+                p.pcap = P;
                 p.wmax = maxN / cs;
                 p.tile_cap = rt * p.wmax;
                 if (maxN % (4 * cs) != 0) continue;
@@ -183,7 +184,7 @@ void apply_layout(const Layout& L, float* gslot, double* r2slot, std::vector<Reg
 tvcs_status autotune(std::vector<RegenProb> probs, int maxN, int per_cluster, RegenProb* dtab,
                      float* gslot, double* r2slot, int* pre, cudaStream_t s, RegenPlan* best)
 {
-    std::vector<RegenPlan> cands = candidates(maxN);
+    std::vector<RegenPlan> cands = candidates(maxN, (int)probs.size());
     if (cands.empty()) return set_last_error(TVCS_ERR_UNSUPPORTED, "no cluster of the regenerating product kernel fits");
     cudaEvent_t e0, e1;
     RCK(cudaEventCreate(&e0));
@@ -227,7 +228,7 @@ size_t max_layout_floats(const std::vector<RegenProb>& probs, int maxN, int per_
                          size_t* rslots)
 {
     size_t g = 0, r = 0;
-    for (RegenPlan c : candidates(maxN)) {
+    for (RegenPlan c : candidates(maxN, (int)probs.size())) {
         Layout L = layout_for(c, probs, per_cluster);
         if (L.gfloats > g) g = L.gfloats;
         if (L.rslots > r) r = L.rslots;

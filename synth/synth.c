@@ -15,9 +15,11 @@
  * regenerated anywhere.  Gaussians come from the Box-Muller transform
  * (Box & Muller, Ann. Math. Stat. 1958) with a natural logarithm and a
  * sine/cosine written here from their Taylor series; every floating-point
- * operation is a single IEEE binary32 operation in a fixed order (this
- * translation unit must be compiled with -ffp-contract=off), so the values
- * are bit-reproducible on any IEEE machine.
+ * operation is a single IEEE binary32 operation in a fixed order -- the
+ * polynomial steps are fused multiply-adds (C99 fmaf, one rounding), every
+ * other step a plain operation (this translation unit must be compiled with
+ * -ffp-contract=off so that nothing else is fused) -- so the values are
+ * bit-reproducible on any IEEE machine.
  *
  * The generator recipe, stated once (the GPU path implements the same recipe
  * independently for in-kernel regeneration):
@@ -90,18 +92,17 @@ SYNTH_EXPORT float synth_ln(float x)
     float s = num / den;
     float z = s * s;
     float q = Q11;
-    q = q * z; q = q + Q9;
-    q = q * z; q = q + Q7;
-    q = q * z; q = q + Q5;
-    q = q * z; q = q + Q3;
+    q = fmaf(q, z, Q9);
+    q = fmaf(q, z, Q7);
+    q = fmaf(q, z, Q5);
+    q = fmaf(q, z, Q3);
     float t = s * z;
     t = t * q;
     float lnm = s + t;
     lnm = lnm * 2.0f;
     float ef = (float)e;
     float hi = ef * LN2_HI;
-    float lo = ef * LN2_LO;
-    lo = lo + lnm;
+    float lo = fmaf(ef, LN2_LO, lnm);
     return hi + lo;
 }
 
@@ -127,19 +128,17 @@ SYNTH_EXPORT void synth_cossin_turns(uint32_t xb, float* c_out, float* s_out)
     float psi = t * PI_4;
     float z = psi * psi;
     float ps = S9;
-    ps = ps * z; ps = ps + S7;
-    ps = ps * z; ps = ps + S5;
-    ps = ps * z; ps = ps + S3;
+    ps = fmaf(ps, z, S7);
+    ps = fmaf(ps, z, S5);
+    ps = fmaf(ps, z, S3);
     float sp = psi * z;
-    sp = sp * ps;
-    sp = psi + sp;
+    sp = fmaf(sp, ps, psi);
     float pc = C10;
-    pc = pc * z; pc = pc + C8;
-    pc = pc * z; pc = pc + C6;
-    pc = pc * z; pc = pc + C4;
-    pc = pc * z; pc = pc + C2;
-    pc = pc * z;
-    float cp = 1.0f + pc;
+    pc = fmaf(pc, z, C8);
+    pc = fmaf(pc, z, C6);
+    pc = fmaf(pc, z, C4);
+    pc = fmaf(pc, z, C2);
+    float cp = fmaf(pc, z, 1.0f);
     if (neg) sp = -sp;
     float c, s;
     switch (quad) {

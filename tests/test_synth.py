@@ -67,6 +67,38 @@ def test_cossin_accuracy_on_whole_angle_grid():
     assert abs(c4) < 1e-7 and s4 == 1.0
 
 
+def fma32(a, b, c):
+    """Correctly rounded binary32 fused multiply-add, emulated in binary64: a*b is
+    exact in binary64, the sum is rounded to odd (TwoSum error, then the last bit
+    forced), and the odd-rounded binary64 value rounds correctly to binary32
+    (Boldo and Melquiond, "Emulation of FMA and correctly rounded sums: proved
+    algorithms using rounding to odd", IEEE Trans. Computers 2008)."""
+    p = np.float64(a) * np.float64(b)
+    c = np.float64(c)
+    s = p + c
+    bb = s - p
+    err = (p - (s - bb)) + (c - bb)
+    if err != 0.0 and (np.array([s]).view(np.uint64)[0] & 1) == 0:
+        s = np.nextafter(s, np.inf if err > 0 else -np.inf)
+    return np.float32(s)
+
+
+def test_fma32_emulation_on_hard_cases():
+    # a*b + c whose exact value sits just beside a binary32 rounding boundary
+    one = np.float32(1.0)
+    eps = np.float32(2.0**-23)
+    assert fma32(one + eps, one + eps, -one) == np.float32(2.0**-22 + 2.0**-46)
+    assert fma32(one + eps, one - eps, -one) == np.float32(-(2.0**-46))
+    rng = np.random.default_rng(3)
+    for _ in range(2000):
+        a, b, c = (np.float32(v) for v in rng.standard_normal(3))
+        exact = np.longdouble(a) * np.longdouble(b) + np.longdouble(c)
+        got = fma32(a, b, c)
+        lo, hi = np.nextafter(got, np.float32(-np.inf)), np.nextafter(got, np.float32(np.inf))
+        assert abs(np.longdouble(got) - exact) <= min(abs(np.longdouble(lo) - exact),
+                                                     abs(np.longdouble(hi) - exact))
+
+
 def _emulated_normals_block(seed, stream, b):
     """Second implementation of the generator recipe in numpy binary32 scalars,
     operation by operation, to catch transcription errors in synth.c."""
@@ -88,12 +120,11 @@ def _emulated_normals_block(seed, stream, b):
         z = s * s
         q = f32(float.fromhex("0x1.745d18p-4"))
         for cst in ["0x1.c71c72p-4", "0x1.24924ap-3", "0x1.99999ap-3", "0x1.555556p-2"]:
-            q = q * z
-            q = q + f32(float.fromhex(cst))
+            q = fma32(q, z, f32(float.fromhex(cst)))
         t = (s * z) * q
         lnm = (s + t) * f32(2)
         ef = f32(e)
-        ln = ef * f32(float.fromhex("0x1.62e4p-1")) + (ef * f32(float.fromhex("0x1.7f7d1cp-20")) + lnm)
+        ln = ef * f32(float.fromhex("0x1.62e4p-1")) + fma32(ef, f32(float.fromhex("0x1.7f7d1cp-20")), lnm)
         rad = np.sqrt(f32(-2) * ln, dtype=np.float32)
         # cos/sin
         o = xb >> 29
@@ -106,14 +137,12 @@ def _emulated_normals_block(seed, stream, b):
         zz = psi * psi
         ps = f32(float.fromhex("0x1.71de3ap-19"))
         for cst in ["-0x1.a01a02p-13", "0x1.111112p-7", "-0x1.555556p-3"]:
-            ps = ps * zz
-            ps = ps + f32(float.fromhex(cst))
-        sp = psi + (psi * zz) * ps
+            ps = fma32(ps, zz, f32(float.fromhex(cst)))
+        sp = fma32(psi * zz, ps, psi)
         pc = f32(float.fromhex("-0x1.27e4fcp-22"))
         for cst in ["0x1.a01a02p-16", "-0x1.6c16c2p-10", "0x1.555556p-5", "-0x1.0p-1"]:
-            pc = pc * zz
-            pc = pc + f32(float.fromhex(cst))
-        cp = f32(1) + pc * zz
+            pc = fma32(pc, zz, f32(float.fromhex(cst)))
+        cp = fma32(pc, zz, f32(1))
         if neg:
             sp = -sp
         c, s_ = [(cp, sp), (-sp, cp), (-cp, -sp), (sp, -cp)][quad]
