@@ -488,12 +488,13 @@ def run_batched(args):
 
 # ----------------------------------------------------------------------------- uneven arm
 
-# Algorithmic operations per regenerated entry of A (32-bit integer or binary32
-# operations of the generator recipe, plus the products' three FLOPs):
-# Philox4x32-10 = 10 rounds x (2 wide multiplies as 4 ops, 4 xors, 2 key adds)
-# per 4 entries = 25; Box-Muller per pair = uniform 4 + ln 27 + sqrt 2 +
-# cos/sin 32 + 2 products = 67, i.e. 33.5 per entry; scale, dot and update 3.
-ALU_OPS_PER_ENTRY = 61.5
+# Algorithmic operations per regenerated entry of A: 32-bit integer or binary32
+# operations as the generator recipe writes them (a 32x32->64 multiply is 2, a
+# three-way xor 2, a fused multiply-add 1), plus the products' 3 operations.
+# Philox4x32-10: 10 rounds x (4 + 4 + 2 key additions) per 4 entries = 25 per
+# entry; Box-Muller per pair: uniform 4 + ln 24 + sqrt 2 + cos/sin 26 + 2
+# products = 58, i.e. 29 per entry; scale, dot and update 3.  Total 57.
+ALU_OPS_PER_ENTRY = 57.0
 
 
 def alu_peak():

@@ -120,7 +120,7 @@ __device__ __forceinline__ void fma4(float4& acc, const float4& a, float s)
 }  // namespace
 
 // MINB: blocks per SM the registers are budgeted for (2: up to 128 registers
-// a thread, 4: up to 64).  NBUF: tile buffers; with 2 the generation of tile
+// a thread, 3: up to 80, 4: up to 64).  NBUF: tile buffers; with 2 the generation of tile
 // t+1 overlaps the exchange of tile t inside a block, with 1 the shared memory
 // halves and other resident blocks fill the wait.  The tuner picks the variant.
 template <int MINB, int NBUF>
@@ -416,7 +416,7 @@ bool regen_configure(RegenPlan* plan)
     plan->clusters = 0;
     if (plan->cs < 1 || plan->cs > 16 || plan->wmax <= 0 || plan->wmax % 4 != 0 ||
         plan->tile_cap < plan->wmax || plan->tile_cap % 4 != 0 ||
-        (plan->minb != 2 && plan->minb != 4) || (plan->nbuf != 1 && plan->nbuf != 2) ||
+        plan->minb < 2 || plan->minb > 4 || (plan->nbuf != 1 && plan->nbuf != 2) ||
         plan->pcap < 1 || plan->pcap > REGEN_PMAX)
         return false;
     plan->pcap = (plan->pcap + 3) / 4 * 4;
@@ -432,6 +432,8 @@ bool regen_configure(RegenPlan* plan)
     if (plan->smem > (size_t)optin) return false;
     if (plan->minb == 2)
         return plan->nbuf == 2 ? configure_t<2, 2>(plan, optin) : configure_t<2, 1>(plan, optin);
+    if (plan->minb == 3)
+        return plan->nbuf == 2 ? configure_t<3, 2>(plan, optin) : configure_t<3, 1>(plan, optin);
     return plan->nbuf == 2 ? configure_t<4, 2>(plan, optin) : configure_t<4, 1>(plan, optin);
 }
 
@@ -450,8 +452,9 @@ void launch_regen(const RegenProb* probs, int P, int mode, const RegenPlan& plan
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    auto k = plan.minb == 4 ? (plan.nbuf == 2 ? k_regen_products<4, 2> : k_regen_products<4, 1>)
-                            : (plan.nbuf == 2 ? k_regen_products<2, 2> : k_regen_products<2, 1>);
+    auto k = plan.minb == 4   ? (plan.nbuf == 2 ? k_regen_products<4, 2> : k_regen_products<4, 1>)
+             : plan.minb == 3 ? (plan.nbuf == 2 ? k_regen_products<3, 2> : k_regen_products<3, 1>)
+                              : (plan.nbuf == 2 ? k_regen_products<2, 2> : k_regen_products<2, 1>);
     cudaLaunchKernelEx(&cfg, k, probs, P, mode, plan.wmax, plan.tile_cap, plan.pcap, pre_out);
 }
 

@@ -143,7 +143,7 @@ struct RegenPlan {
     int cs = 8;          // cluster size (blocks splitting each row's columns)
     int tile_cap = 0;    // floats of one tile buffer (rows per tile = tile_cap / (N / cs), power of 2)
     int wmax = 0;        // max over problems of N / cs
-    int minb = 2;        // kernel variant: registers budgeted for 2 or 4 blocks per SM
+    int minb = 2;        // kernel variant: registers budgeted for 2, 3 or 4 blocks per SM
     int nbuf = 2;        // kernel variant: tile buffers (2: generation overlaps the exchange)
     int pcap = 1;        // problems a launch may carry (<= REGEN_PMAX; sizes a shared-memory table)
     int clusters = 0;    // persistent grid, in clusters

@@ -16,7 +16,7 @@
 //
 // Tiles are chosen by measurement: every candidate of cluster size (4, 8, 16),
 // tile height (1, 2, 4, 8 rows of the largest problem) and kernel variant
-// (registers for 2 or 4 blocks per SM; one or two tile buffers) is timed on
+// (registers for 2, 3 or 4 blocks per SM; one or two tile buffers) is timed on
 // the actual problem set and the fastest is kept.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -125,7 +125,7 @@ void chunking(const RegenPlan& plan, int m, int N, double target, int* rpc, int*
 std::vector<RegenPlan> candidates(int maxN, int P)
 {
     std::vector<RegenPlan> out;
-    const int variants[3][2] = {{2, 2}, {4, 2}, {4, 1}};   // (blocks per SM, tile buffers)
+    const int variants[5][2] = {{2, 2}, {3, 2}, {3, 1}, {4, 2}, {4, 1}};   // (blocks/SM, tile buffers)
     for (const auto& v : variants)
         for (int cs : {4, 8, 16})
             for (int rt : {1, 2, 4, 8}) {
