@@ -6,8 +6,8 @@
 // eq. (line), Sec. 2.1, with A given by its seed).
 //
 // A cluster of CS blocks splits each row's N columns into CS slices of
-// W = N / CS; block `rank` keeps x's slice in shared memory and accumulates its
-// slice of A^T r.  A tile is up to 16 consecutive rows.  Per tile:
+// W = N / CS; block `rank` reads x's slice through the read-only cache and
+// accumulates its slice of A^T r in shared memory.  A tile is up to 16 consecutive rows.  Per tile:
 //   gen     each thread generates four-element groups (one Philox block each)
 //           of one row, stores them in the tile buffer and accumulates the
 //           row's dot product with x;
@@ -131,8 +131,7 @@ k_regen_products(const RegenProb* __restrict__ probs, int P, int mode, int wmax,
     extern __shared__ __align__(16) unsigned char smem[];
     int* pre = reinterpret_cast<int*>(smem);                    // pcap + 4 (pcap >= P, multiple of 4)
     int* scan = pre + pcap + 4;                                 // RG_THREADS
-    float* us = reinterpret_cast<float*>(scan + RG_THREADS);    // x slice, wmax
-    float* gs = us + wmax;                                      // A^T r slice, wmax
+    float* gs = reinterpret_cast<float*>(scan + RG_THREADS);    // A^T r slice, wmax
     float* tile = gs + wmax;                                    // NBUF x tile_cap
     float* wpart = tile + NBUF * tile_cap;                      // 2 x RTMAX x NWMAX
     float* slotv = wpart + 2 * RG_RTMAX * RG_NWMAX;             // 2 x RTMAX, read by the peers
@@ -165,7 +164,6 @@ k_regen_products(const RegenProb* __restrict__ probs, int P, int mode, int wmax,
     int row = c * RC;
     int cend = min(m, row + RC);
     int head = c;
-    int loaded = -1;
 
     double r2acc = 0.0;
     // exch + update of tile tm: partial dots from slot buffer sb, entries from tile buffer tb
@@ -215,13 +213,6 @@ k_regen_products(const RegenProb* __restrict__ probs, int P, int mode, int wmax,
         const int tb = NBUF == 2 ? sb : 0;     // tile buffer
         TileMeta cur{};
         if (have_cur) {
-            if (loaded != p) {   // x slice of a new problem (every thread is past the last gen)
-                const float4* src = reinterpret_cast<const float4*>(pr->x + (size_t)rank * W);
-                float4* dst = reinterpret_cast<float4*>(us);
-                for (int q4 = tid; q4 < W / 4; q4 += RG_THREADS) dst[q4] = src[q4];
-                loaded = p;
-                __syncthreads();
-            }
             cur.p = p;
             cur.i0 = row;
             cur.nr = min(rt, cend - row);
@@ -239,7 +230,8 @@ k_regen_products(const RegenProb* __restrict__ probs, int P, int mode, int wmax,
                     const unsigned long long b0 =
                         (i * (unsigned long long)N + (unsigned long long)rank * W) >> 2;
                     float4* trow = reinterpret_cast<float4*>(tile + tb * tile_cap) + rr * G;
-                    const float4* x4 = reinterpret_cast<const float4*>(us);
+                    // x slice through the read-only path: L1 keeps it across the tile's rows
+                    const float4* x4 = reinterpret_cast<const float4*>(pr->x + (size_t)rank * W);
                     const float scale = pr->scale;
                     const unsigned long long seed = pr->seed;
                     auto emit = [&](int q, const float4& z) {
@@ -249,7 +241,7 @@ k_regen_products(const RegenProb* __restrict__ probs, int P, int mode, int wmax,
                         a.z = __fmul_rn(z.z, scale);
                         a.w = __fmul_rn(z.w, scale);
                         trow[q] = a;
-                        const float4 xv = x4[q];
+                        const float4 xv = __ldg(x4 + q);
                         dot = fmaf(a.x, xv.x, dot);
                         dot = fmaf(a.y, xv.y, dot);
                         dot = fmaf(a.z, xv.z, dot);
@@ -371,7 +363,7 @@ k_regen_reduce(const RegenProb* __restrict__ probs, int P, int Q, const int* __r
 static size_t regen_smem(int wmax, int tile_cap, int nbuf, int pcap)
 {
     return sizeof(int) * ((size_t)pcap + 4 + RG_THREADS) +
-           sizeof(float) * (2 * (size_t)wmax + (size_t)nbuf * tile_cap + 2 * RG_RTMAX * RG_NWMAX +
+           sizeof(float) * ((size_t)wmax + (size_t)nbuf * tile_cap + 2 * RG_RTMAX * RG_NWMAX +
                             4 * RG_RTMAX);
 }
 
