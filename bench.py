@@ -437,7 +437,9 @@ def run_batched(args):
     gemm_us = tv.tvcs_time_stage(h, 3, reps) * 1e3 / reps
     torch.cuda.nvtx.range_pop()
     fix_us = tv.tvcs_time_stage(h, 4, reps) * 1e3 / reps
+    torch.cuda.nvtx.range_push("stage5")
     us_us = tv.tvcs_time_stage(h, 5, reps) * 1e3 / reps
+    torch.cuda.nvtx.range_pop()
     # end to end with pinned host buffers (f in, images out inside the timed call)
     F_host = torch.from_numpy(F).pin_memory()
     U_host = torch.empty((B, N), dtype=torch.float32).pin_memory()

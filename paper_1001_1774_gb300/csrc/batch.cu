@@ -164,7 +164,9 @@ tvcs_status ensure_batch(tvcs_ctx* h, int count)
     cudaStream_t s = h->stream;
     const size_t N = h->N, m = h->m;
     if (b->ucluster == 0) {
-        // Many images in flight: 8-block clusters pack the SMs more densely than 16.
+        // Many images in flight: one block per image where n allows it, else
+        // 8-block clusters (they pack the SMs more densely than 16).
+        b->uimg = usolve_img_configure(h->n);
         b->ucluster = usolve_cluster_fits(h->n, 8) ? 8 : h->ucluster;
         usolve_cluster_fits(h->n, b->ucluster);   // kernel attributes of the chosen size
     }
@@ -270,6 +272,14 @@ TvArgs batch_tv_args(tvcs_ctx* h, int count, int mode)
     return a;
 }
 
+void batch_usolve(tvcs_ctx* h, const TvArgs& a, cudaStream_t s)
+{
+    if (h->batch->uimg)
+        launch_usolve_img(h->n, a, s);
+    else
+        launch_usolve(h->n, h->batch->ucluster, a, s);
+}
+
 tvcs_status build_batch_graph(tvcs_ctx* h, int count)
 {
     tvcs_batch* b = h->batch;
@@ -288,7 +298,7 @@ tvcs_status build_batch_graph(tvcs_ctx* h, int count)
     BCK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
                                       cudaStreamCaptureModeThreadLocal));
     TvArgs a = batch_tv_args(h, count, MODE_ITER);
-    launch_usolve(h->n, h->batch->ucluster, a, cs);
+    batch_usolve(h, a, cs);
     batch_products(h, count, true, cs);
     k_batch_cond<<<1, 256, 0, cs>>>(b->ctrls, count, b->bctrl, ch, 1);
     cudaGraph_t captured = nullptr;
@@ -344,7 +354,7 @@ tvcs_status time_batch_stage(tvcs_ctx* h, int stage, int reps, double* ms)
             launch_gemm_fixup(b->ws, b->tsb2, b->ss2, h->N, b->p2.tiles_m, count, nullptr, 0, b->G,
                               h->N, nullptr, nullptr, 0, nullptr, b->bctrl, 0, s);
         } else {
-            launch_usolve(h->n, h->batch->ucluster, a, s);
+            batch_usolve(h, a, s);
         }
     }
     BCK(cudaEventRecord(h->ev1, s));

@@ -32,6 +32,7 @@ struct tvcs_batch {
     int graph_count = 0;           // images the loop graph was built for
     int last_count = 0;            // images of the last batched call
     int ucluster = 0;              // cluster size of the batched u-solve
+    bool uimg = false;             // the u-solve runs one block per image (k_usolve_img)
 };
 
 // Products with A regenerated in the kernel (handles created with

@@ -27,6 +27,7 @@
 #include "common.cuh"
 #include "fft.cuh"
 #include "kernels.h"
+#include "usolve_steps.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -146,67 +147,12 @@ __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
     cp_async_wait_all();
     __syncthreads();
 
-    const float inv_beta = 1.0f / beta;
-    for (int i = tid; i < (R + 1) * NN; i += nthr) {
-        const int rr = i / NN, c = i - rr * NN;      // rr = 0 is the halo row r0-1
-        const int row = (r0 - 1 + rr + NN) % NN;
-        const int cp = (c + 1 == NN) ? 0 : c + 1;
-        const float uc = su[rr * NN + c];
-        const float d1 = su[rr * NN + cp] - uc;
-        const float d2 = su[(rr + 1) * NN + c] - uc;
-        const int gi = row * NN + c;
-        float l1 = swl[2 * WL + i], l2 = swl[3 * WL + i];
-        if (pending) {  // eq. (udlamb) for the previous iteration
-            l1 -= beta * (swl[i] - d1);
-            l2 -= beta * (swl[WL + i] - d2);
-        }
-        // eq. (iadmw), reading C1: shrink D_i u + lambda_i / beta; reading C6 at the tie
-        const float z1 = d1 + l1 * inv_beta, z2 = d2 + l2 * inv_beta;
-        const float nz = sqrtf(z1 * z1 + z2 * z2);
-        float w1 = 0.0f, w2 = 0.0f;
-        if (nz > inv_beta) {
-            const float s = (nz - inv_beta) / nz;
-            w1 = s * z1;
-            w2 = s * z2;
-        }
-        sy2[i] = beta * (w2 - d2) - l2;
-        if (rr >= 1) {
-            sy1[(rr - 1) * NN + c] = beta * (w1 - d1) - l1;
-            wdst[gi] = w1;
-            wdst[N + gi] = w2;
-            ldst[gi] = l1;
-            ldst[N + gi] = l2;
-        }
-    }
+    step_wshrink<NN>(su, swl, WL, R, r0, beta, pending, sy1, sy2, wdst, ldst, tid, nthr);
     __syncthreads();
-    // rhs = D^T y - mu g, packed two rows per complex transform
-    for (int i = tid; i < (R / 2) * NN; i += nthr) {
-        const int j = i / NN, c = i - j * NN;
-        const int cm = (c == 0) ? NN - 1 : c - 1;
-        float v[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int lr = 2 * j + h;   // local owned row
-            const float dty = sy1[lr * NN + cm] - sy1[lr * NN + c] + sy2[lr * NN + c] -
-                              sy2[(lr + 1) * NN + c];
-            v[h] = dty - mu * sg[lr * NN + c];
-        }
-        wa[i] = make_float2(v[0], v[1]);
-        if (rhs_out) {
-            rhs_out[(r0 + 2 * j) * NN + c] = v[0];
-            rhs_out[(r0 + 2 * j + 1) * NN + c] = v[1];
-        }
-    }
+    step_rhs<NN>(sy1, sy2, sg, R, r0, mu, wa, rhs_out, tid, nthr);
     __syncthreads();
     float2* Zr = fft_block<NN, false>(wa, wb, tw, R / 2, NN);
-    // X_q = (Z_q + conj Z_{n-q})/2, Y_q = (Z_q - conj Z_{n-q})/(2i), q = 0 .. n/2
-    for (int i = tid; i < (R / 2) * Q; i += nthr) {
-        const int j = i / Q, q = i - j * Q;
-        const float2 a = Zr[j * NN + q];
-        const float2 b = Zr[j * NN + (NN - q) % NN];
-        spec[(2 * j) * Q + q] = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
-        spec[(2 * j + 1) * Q + q] = make_float2(0.5f * (a.y + b.y), -0.5f * (a.x - b.x));
-    }
+    step_split<NN>(Zr, R, spec, Q, 1, tid, nthr);
     cluster.sync();   // every block's half spectrum is complete
 
     // ---------------- phase B: columns ----------------
@@ -236,7 +182,7 @@ __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
     float2* other = (X == wa) ? wb : wa;
     for (int i = tid; i < ncol * NN; i += nthr) {
         const int f = i / NN, p = i - f * NN;
-        const float d = beta * (s2[p] + s2[q0 + f]) + mu_over_tau;
+        const float d = solve_divisor(s2, p, q0 + f, beta, mu_over_tau);
         float2 v = X[i];
         v.x = v.x / d;
         v.y = v.y / d;
@@ -252,51 +198,12 @@ __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
     cluster.sync();   // every column is home
 
     // ---------------- phase C: inverse rows, u update, norms ----------------
-    for (int i = tid; i < (R / 2) * NN; i += nthr) {
-        const int j = i / NN, q = i - j * NN;
-        const bool lo = q < Q;
-        const int qq = lo ? q : NN - q;
-        float2 Xv = spec[(2 * j) * Q + qq];
-        float2 Yv = spec[(2 * j + 1) * Q + qq];
-        if (qq == 0 || 2 * qq == NN) {  // exactly real bins
-            Xv.y = 0.f;
-            Yv.y = 0.f;
-        }
-        if (!lo) {
-            Xv.y = -Xv.y;
-            Yv.y = -Yv.y;
-        }
-        wa[i] = make_float2(Xv.x - Yv.y, Xv.y + Yv.x);
-    }
+    step_pack_inverse<NN>(spec, Q, 1, R, wa, tid, nthr);
     __syncthreads();
     float2* z = fft_block<NN, true>(wa, wb, tw, R / 2, NN);
-    const float sc = 1.0f / (float)(NN * NN);
     // per-thread sums of a few squares in binary32, combined across threads in binary64
     float du2f = 0.f, u2f = 0.f;
-    for (int i = tid; i < (R / 2) * NN; i += nthr) {
-        const int j = i / NN, c = i - j * NN;
-        const float2 v = z[i];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int lr = 2 * j + h;
-            const float d = (h == 0 ? v.x : v.y) * sc;
-            const float o = su[(lr + 1) * NN + c];
-            du2f = fmaf(d, d, du2f);
-            u2f = fmaf(o, o, u2f);
-            const float nw = o + d;
-            u[(r0 + lr) * NN + c] = nw;
-            if (u_hi) {
-                const unsigned int bits = __float_as_uint(nw);
-                // bf16 round to nearest even of nw, and of the exact remainder
-                const unsigned int hb = (bits + 0x7fffu + ((bits >> 16) & 1u)) & 0xffff0000u;
-                const float rem = nw - __uint_as_float(hb);
-                const unsigned int rb = __float_as_uint(rem);
-                const unsigned int lb = (rb + 0x7fffu + ((rb >> 16) & 1u)) & 0xffff0000u;
-                u_hi[(r0 + lr) * NN + c] = (unsigned short)(hb >> 16);
-                u_lo[(r0 + lr) * NN + c] = (unsigned short)(lb >> 16);
-            }
-        }
-    }
+    step_update<NN>(z, su + NN, R, r0, u, u_hi, u_lo, du2f, u2f, tid, nthr);
     const double bdu = block_sum((double)du2f, red);
     const double bu = block_sum((double)u2f, red);
     if (tid == 0) {
@@ -306,32 +213,12 @@ __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
     }
     cluster.sync();   // partials delivered to block 0; every block has read wpar and done
     if (rank == 0 && tid == 0) {
-        if (ctrl->algo == 0) ctrl->pending = 1;   // u moved: its multiplier update is due
         double tdu = 0.0, tu = 0.0;
         for (int k = 0; k < C; ++k) {
             tdu += cred[2 * k];
             tu += cred[2 * k + 1];
         }
-        ctrl->wpar = par ^ 1;
-        ctrl->du2 = tdu;
-        ctrl->u2 = tu;
-        ctrl->relchg = tu > 0.0 ? sqrt(tdu / tu) : (tdu > 0.0 ? INFINITY : 0.0);
-        if (mode == MODE_ITER) {
-            const int it = ctrl->it + 1;
-            ctrl->it = it;
-            bool stop = false;
-            if (!isfinite(tdu) || !isfinite(tu)) {
-                set_error(ctrl, ERR_NONFINITE);
-                stop = true;
-            }
-            const double tol = ctrl->tol;   // eq. (stop), reading C5
-            if (tol > 0.0 && (tu > 0.0 ? tdu <= tol * tol * tu : tdu == 0.0)) {
-                ctrl->stop_by_tol = 1;
-                stop = true;
-            }
-            if (it >= ctrl->max_iter || ctrl->error != ERR_NONE) stop = true;
-            if (stop) ctrl->done = 1;
-        }
+        step_stop(ctrl, par, mode, tdu, tu);
     }
 }
 

@@ -1,0 +1,252 @@
+// Rows a1-a5 of one IADM/FTVCS iteration for many images at once, one block
+// per image (Xiao & Yang, Sec. 2.1-2.2; the same steps as k_usolve.cu, in
+// usolve_steps.cuh).  For batches: with hundreds of images in flight the
+// latency of one image matters less than the rate at which the SMs get through
+// them, so each image stays on one SM and needs no cluster barrier.
+//
+// The block keeps the image's whole half spectrum in shared memory, column-
+// major (spec[q n + p], q = 0 .. n/2), so that phase B transforms all n/2+1
+// columns at once.  Phases A and C stream the image in stripes of S rows
+// through a two-deep ring of asynchronous 16-byte copies (the next stripe's
+// rows arrive while the current one is computed):
+//   A  per stripe: w-step, right-hand side, forward row FFTs (two real rows per
+//      complex transform), half spectra into their columns;
+//   B  column FFTs, divide by beta Lambda_pq + mu/tau, inverse column FFTs;
+//   C  per stripe: inverse row FFTs, u += d, binary32 partial norms;
+// then binary64 block sums and eq. (stop) for the image.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "fft.cuh"
+#include "kernels.h"
+#include "usolve_steps.cuh"
+
+namespace tvcs {
+
+namespace {
+
+constexpr int IMG_THREADS = 512;
+
+template <int NN, int S>
+struct ImgShape {
+    static constexpr int Q = NN / 2 + 1;
+    static constexpr int NSTRIPE = NN / S;
+    static constexpr int IN_U = (S + 2) * NN;       // u rows r0-1 .. r0+S
+    static constexpr int IN_G = S * NN;             // g rows r0 .. r0+S-1
+    static constexpr int IN_WL = 4 * (S + 1) * NN;  // w1, w2, l1, l2 rows r0-1 .. r0+S-1
+    static constexpr int IN = IN_U + IN_G + IN_WL;  // floats of one stripe's inputs
+    static constexpr size_t O_TW = 0;
+    static constexpr size_t O_S2 = O_TW + NN * 8;
+    static constexpr size_t O_SPEC = O_S2 + ((NN * 4 + 15) / 16) * 16;   // Q x NN complex
+    static constexpr size_t SPEC_BYTES = (size_t)Q * NN * 8;
+    static constexpr size_t O_SCR = O_SPEC + SPEC_BYTES;
+    // phase A, inside the scratch region: two input buffers, y1, y2, two FFT buffers
+    static constexpr size_t A_IN0 = O_SCR;
+    static constexpr size_t A_IN1 = A_IN0 + (size_t)IN * 4;
+    static constexpr size_t A_Y1 = A_IN1 + (size_t)IN * 4;
+    static constexpr size_t A_Y2 = A_Y1 + (size_t)S * NN * 4;
+    static constexpr size_t A_WA = A_Y2 + (size_t)(S + 1) * NN * 4;
+    static constexpr size_t A_WB = A_WA + (size_t)(S / 2) * NN * 8;
+    static constexpr size_t A_END = A_WB + (size_t)(S / 2) * NN * 8;
+    static constexpr size_t B_END = O_SCR + SPEC_BYTES;   // phase B: scratch = the second FFT buffer
+    static constexpr size_t O_RED = A_END > B_END ? A_END : B_END;
+    static constexpr size_t SMEM = O_RED + 32 * 8;
+    // phase C, inside the scratch region (the forward and inverse column FFTs
+    // are 2 x stages ping-pong steps, so the solved spectrum ends in `spec`):
+    // two u-row buffers, two FFT buffers
+    static constexpr size_t C_BYTES = 2 * (size_t)S * NN * 4 + 2 * (size_t)(S / 2) * NN * 8;
+    static_assert(NN % S == 0 && S % 2 == 0, "whole stripes of an even number of rows");
+    static_assert(C_BYTES <= O_RED - O_SCR, "phase C buffers fit in the scratch region");
+    static_assert(SMEM <= 227 * 1024, "shared memory");
+};
+
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_one()
+{
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+
+}  // namespace
+
+// Image b = blockIdx.x uses u + b N, w/lambda + 4 b N, g + b N, ctrl + b and,
+// when mu_img is set, mu_img[b] (and tau_img[b] when set).
+template <int NN, int S>
+__global__ void __launch_bounds__(IMG_THREADS, 1) k_usolve_img(
+    float* __restrict__ u, float* __restrict__ wbuf, float* __restrict__ lbuf,
+    const float* __restrict__ g, const float2* __restrict__ tw_g, const float* __restrict__ s2_g,
+    float beta, float mu_over_tau, float mu, Ctrl* __restrict__ ctrl, int mode,
+    const float* __restrict__ mu_img, const float* __restrict__ tau_img, float tau,
+    unsigned short* __restrict__ u_hi, unsigned short* __restrict__ u_lo)
+{
+    using SH = ImgShape<NN, S>;
+    constexpr int N = NN * NN, Q = SH::Q, CPR = NN / 4, WL = (S + 1) * NN;
+    {
+        const int b = blockIdx.x;
+        u += (size_t)b * N;
+        wbuf += (size_t)b * 4 * N;
+        lbuf += (size_t)b * 4 * N;
+        g += (size_t)b * N;
+        ctrl += b;
+        if (u_hi) {
+            u_hi += (size_t)b * N;
+            u_lo += (size_t)b * N;
+        }
+        if (mu_img) {
+            mu = mu_img[b];
+            mu_over_tau = mu / (tau_img ? tau_img[b] : tau);
+        }
+    }
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* tw = reinterpret_cast<float2*>(smem + SH::O_TW);
+    float* s2 = reinterpret_cast<float*>(smem + SH::O_S2);
+    float2* spec = reinterpret_cast<float2*>(smem + SH::O_SPEC);   // spec[q NN + p]
+    float2* scr = reinterpret_cast<float2*>(smem + SH::O_SCR);
+    float* in0 = reinterpret_cast<float*>(smem + SH::A_IN0);
+    float* in1 = reinterpret_cast<float*>(smem + SH::A_IN1);
+    float* sy1 = reinterpret_cast<float*>(smem + SH::A_Y1);
+    float* sy2 = reinterpret_cast<float*>(smem + SH::A_Y2);
+    float2* wa = reinterpret_cast<float2*>(smem + SH::A_WA);
+    float2* wb = reinterpret_cast<float2*>(smem + SH::A_WB);
+    double* red = reinterpret_cast<double*>(smem + SH::O_RED);
+    const int tid = threadIdx.x, nthr = blockDim.x;
+
+    if (mode == MODE_ITER) {
+        const int done = ctrl->done;   // stable during this kernel
+        if (tid == 0) ctrl->skip = done;
+        if (done) return;              // uniform across the block
+    }
+    const int pending = ctrl->pending;
+    const int par = ctrl->wpar;
+    const float* wsrc = wbuf + (size_t)par * 2 * N;
+    const float* lsrc = lbuf + (size_t)par * 2 * N;
+    float* wdst = wbuf + (size_t)(par ^ 1) * 2 * N;
+    float* ldst = lbuf + (size_t)(par ^ 1) * 2 * N;
+
+    // ---------------- phase A: stripes of S rows ----------------
+    auto load_stripe = [&](int s, float* in) {
+        const int r0 = s * S;
+        float* su = in;
+        float* sg = in + SH::IN_U;
+        float* swl = sg + SH::IN_G;
+        for (int i = tid; i < (S + 2) * CPR; i += nthr) {
+            const int rr = i / CPR, c4 = i - rr * CPR;
+            const int row = (r0 - 1 + rr + NN) % NN;
+            cp_async16(su + rr * NN + 4 * c4, u + row * NN + 4 * c4);
+        }
+        for (int i = tid; i < S * CPR; i += nthr) cp_async16(sg + 4 * i, g + r0 * NN + 4 * i);
+        for (int i = tid; i < (S + 1) * CPR; i += nthr) {
+            const int rr = i / CPR, c4 = i - rr * CPR;
+            const int gi = ((r0 - 1 + rr + NN) % NN) * NN + 4 * c4;
+            const int li = rr * NN + 4 * c4;
+            cp_async16(swl + li, wsrc + gi);
+            cp_async16(swl + WL + li, wsrc + N + gi);
+            cp_async16(swl + 2 * WL + li, lsrc + gi);
+            cp_async16(swl + 3 * WL + li, lsrc + N + gi);
+        }
+    };
+    for (int i = tid; i < NN / 2; i += nthr) cp_async16(tw + 2 * i, tw_g + 2 * i);
+    for (int i = tid; i < CPR; i += nthr) cp_async16(s2 + 4 * i, s2_g + 4 * i);
+    load_stripe(0, in0);
+    cp_async_commit();
+    for (int s = 0; s < SH::NSTRIPE; ++s) {
+        float* cur = (s & 1) ? in1 : in0;
+        if (s + 1 < SH::NSTRIPE) load_stripe(s + 1, (s & 1) ? in0 : in1);
+        cp_async_commit();     // (empty after the last stripe: keeps the group count uniform)
+        cp_async_wait_one();   // this stripe's copies (and the tables) have landed
+        __syncthreads();
+        const int r0 = s * S;
+        step_wshrink<NN>(cur, cur + SH::IN_U + SH::IN_G, WL, S, r0, beta, pending, sy1, sy2, wdst,
+                         ldst, tid, nthr);
+        __syncthreads();
+        step_rhs<NN>(sy1, sy2, cur + SH::IN_U, S, r0, mu, wa, nullptr, tid, nthr);
+        __syncthreads();
+        float2* Z = fft_block<NN, false>(wa, wb, tw, S / 2, NN);
+        step_split<NN>(Z, S, spec + r0, 1, NN, tid, nthr);
+        __syncthreads();       // the ring buffer, y and the FFT buffers are free again
+    }
+
+    // ---------------- phase B: all columns ----------------
+    float2* X = fft_block<NN, false>(spec, scr, tw, Q, NN);
+    for (int i = tid; i < Q * NN; i += nthr) {
+        const int q = i / NN, p = i - q * NN;
+        const float d = solve_divisor(s2, p, q, beta, mu_over_tau);
+        float2 v = X[i];
+        v.x = v.x / d;
+        v.y = v.y / d;
+        X[i] = v;
+    }
+    __syncthreads();
+    const float2* Y = fft_block<NN, true>(X, X == spec ? scr : spec, tw, Q, NN);   // == spec
+
+    // ---------------- phase C: stripes of S rows ----------------
+    float* ub0 = reinterpret_cast<float*>(scr);
+    float* ub1 = ub0 + S * NN;
+    float2* ca = reinterpret_cast<float2*>(ub1 + S * NN);
+    float2* cb = ca + (S / 2) * NN;
+    auto load_u = [&](int s, float* dst) {
+        for (int i = tid; i < S * CPR; i += nthr) cp_async16(dst + 4 * i, u + s * S * NN + 4 * i);
+    };
+    load_u(0, ub0);
+    cp_async_commit();
+    float du2f = 0.f, u2f = 0.f;
+    for (int s = 0; s < SH::NSTRIPE; ++s) {
+        float* cur = (s & 1) ? ub1 : ub0;
+        if (s + 1 < SH::NSTRIPE) load_u(s + 1, (s & 1) ? ub0 : ub1);
+        cp_async_commit();
+        cp_async_wait_one();
+        __syncthreads();
+        const int r0 = s * S;
+        step_pack_inverse<NN>(Y + r0, 1, NN, S, ca, tid, nthr);
+        __syncthreads();
+        float2* z = fft_block<NN, true>(ca, cb, tw, S / 2, NN);
+        step_update<NN>(z, cur, S, r0, u, u_hi, u_lo, du2f, u2f, tid, nthr);
+        __syncthreads();
+    }
+    const double bdu = block_sum((double)du2f, red);
+    const double bu = block_sum((double)u2f, red);
+    if (tid == 0) step_stop(ctrl, par, mode, bdu, bu);
+}
+
+// ---------------------------------------------------------------------------
+// Host side.  Stripe height per n: 16 rows (8 packed transforms per stripe).
+// ---------------------------------------------------------------------------
+#define TVCS_USOLVE_IMG_TABLE(X) X(16, 16) X(32, 16) X(48, 16) X(64, 16) X(96, 16) X(128, 16)
+
+template <int NN, int S>
+static bool configure_img_t()
+{
+    if (cudaFuncSetAttribute(k_usolve_img<NN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ImgShape<NN, S>::SMEM) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+bool usolve_img_configure(int n)
+{
+#define X(NN, S) \
+    if (n == NN) return configure_img_t<NN, S>();
+    TVCS_USOLVE_IMG_TABLE(X)
+#undef X
+    return false;
+}
+
+void launch_usolve_img(int n, const TvArgs& a, cudaStream_t s)
+{
+#define X(NN, S)                                                                                 \
+    if (n == NN) {                                                                               \
+        k_usolve_img<NN, S><<<a.nimg > 0 ? a.nimg : 1, IMG_THREADS, ImgShape<NN, S>::SMEM, s>>>( \
+            a.u, a.w, a.lam, a.g, a.tw, a.s2, a.beta, a.mu_over_tau, a.mu, a.ctrl, a.mode,       \
+            a.mu_img, a.tau_img, a.tau, a.u_hi, a.u_lo);                                         \
+        return;                                                                                  \
+    }
+    TVCS_USOLVE_IMG_TABLE(X)
+#undef X
+}
+
+}  // namespace tvcs

@@ -45,6 +45,10 @@ void launch_tv(int n, const TvArgs& a, int which, cudaStream_t s);
 int usolve_choose_cluster(int n);
 bool usolve_cluster_fits(int n, int c);   // also sets the kernel attributes
 void launch_usolve(int n, int cluster, const TvArgs& a, cudaStream_t s);
+// The same rows for batches, one block per image (k_usolve_img.cu, n <= 128):
+// usolve_img_configure sets the kernel attributes, false if n has no variant.
+bool usolve_img_configure(int n);
+void launch_usolve_img(int n, const TvArgs& a, cudaStream_t s);
 
 // Fused single-pass products r = A x - y, gpart = per-block partials of A^T r.
 struct ProdArgs {

@@ -100,6 +100,23 @@ def test_batched_solve_matches_oracle_and_single_image(tv):
     tv.tvcs_destroy(h1)
 
 
+@pytest.mark.parametrize("n", [64])
+def test_batched_solve_other_sizes(tv, n):
+    # the one-block-per-image u-solve at the bf16 hi+lo sides not covered above (32, 128 are)
+    A, ubars, F, mus, _ = synth.workload_shared_batch(count=5, n=n, ratio=0.2, seed=7 + n, n_ellipses=5)
+    m, N = A.shape
+    tau = oracle.default_tau(A)
+    iters = 25
+    h = bf16_handle(tv, A, m, n, mu=1e3, tau=tau, max_iter=iters)
+    us = [np.empty(N, np.float32) for _ in range(5)]
+    res = tv.tvcs_solve_batched([h] * 5, [F[b] for b in range(5)], us, mus)
+    for b in range(5):
+        assert res[b].iters == iters
+        ref = oracle.solve(A, F[b], n, mus[b], 10.0, tau, max_iter=iters)
+        assert rel(us[b], ref.u) <= 1e-4, (n, b)
+    tv.tvcs_destroy(h)
+
+
 def test_batched_per_image_stop(tv):
     # images stop on their own eq. (stop): a run to tol gives per-image iteration counts
     A, ubars, F, mus, _ = synth.workload_shared_batch(count=4, n=32, ratio=0.3, seed=4, n_ellipses=6)
