@@ -50,6 +50,7 @@ struct tvcs_uneven;   // state of the uneven batch (regen.cu)
 
 struct tvcs_ctx {
     int dev = 0, num_sms = 0, ucluster = 0;
+    int pdl = 1;                   // the loop's product launch overlaps the u-solve's tail
     int m = 0, n = 0, N = 0, P = 0;
     double mu = 0, beta = 0, tol = 0, tau = 0;
     tvcs_options opt{};

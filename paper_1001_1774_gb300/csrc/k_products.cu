@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(PROD_THREADS, 1)
     float* sy = reinterpret_cast<float*>(sflag + 4);                // [YMAX]
 
     const int tid = threadIdx.x;
+    pdl_wait_then_release();   // x and the control block come from the preceding u-solve
     if (mode == MODE_ITER) {
         const int skip = ctrl->skip;
         if (blockIdx.x == 0 && tid == 0) {
@@ -302,11 +303,20 @@ static void launch_prod_t(int grid, const ProdArgs& a, cudaStream_t s)
     cfg.blockDim = dim3(PROD_THREADS, 1, 1);
     cfg.dynamicSmemBytes = S::SMEM;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
+    cudaLaunchAttribute attr[2];
+    int na = 0;
+    if (a.g_out) {   // the grid barrier needs co-resident blocks
+        attr[na].id = cudaLaunchAttributeCooperative;
+        attr[na].val.cooperative = 1;
+        ++na;
+    }
+    if (a.pdl) {
+        attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[na].val.programmaticStreamSerializationAllowed = 1;
+        ++na;
+    }
     cfg.attrs = attr;
-    cfg.numAttrs = a.g_out ? 1 : 0;   // the grid barrier needs co-resident blocks
+    cfg.numAttrs = na;
     cudaLaunchKernelEx(&cfg, k_products<V, RL, RS>, a.A, a.m, a.x, a.y, a.r, a.gpart, a.g_out,
                        a.r2part, a.ctrl, a.mode, (cudaGraphConditionalHandle)a.cond, a.set_cond,
                        a.budget);

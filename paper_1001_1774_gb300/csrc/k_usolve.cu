@@ -108,6 +108,7 @@ __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
     const int rank = (int)cluster.block_rank();
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int r0 = rank * R;
+    pdl_wait_then_release();   // g and the control block come from the preceding products
 
     if (mode == MODE_ITER) {
         const int done = ctrl->done;   // stable during this kernel
@@ -275,13 +276,15 @@ static void launch_usolve_t(const TvArgs& a, cudaStream_t s)
     cfg.blockDim = dim3(256, 1, 1);
     cfg.dynamicSmemBytes = S::SMEM;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = C;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = a.pdl ? 2 : 1;
     cudaLaunchKernelEx(&cfg, k_usolve_cluster<NN, C>, a.u, a.w, a.lam, a.g, a.rhs_out, a.tw, a.s2,
                        a.beta, a.mu_over_tau, a.mu, a.ctrl, a.mode, a.mu_img, a.tau_img,
                        a.tau, a.u_hi, a.u_lo);

@@ -32,6 +32,7 @@ struct TvArgs {
     float tau;
     unsigned short* u_hi;       // nullable: bf16 hi/lo planes of the new u
     unsigned short* u_lo;
+    int pdl;                    // launch with a programmatic dependency on the preceding grid
 };
 
 bool tv_supported(int n);
@@ -66,6 +67,7 @@ struct ProdArgs {
     unsigned long long cond;  // cudaGraphConditionalHandle (MODE_ITER inside the loop graph)
     int set_cond;
     long long budget;   // spin-wait bound, SM cycles
+    int pdl;            // launch with a programmatic dependency on the preceding grid
 };
 
 bool prod_supported(int n);

@@ -85,7 +85,7 @@ TvArgs tv_args(tvcs_ctx* h, int mode, bool stage_outputs)
 
 // r = A x - y and the partials of A^T r into gpart; then g = their sum when g != NULL.
 void products(tvcs_ctx* h, const float* x, const float* y, float* r, float* gpart, float* g,
-              int mode, unsigned long long cond, int set_cond, cudaStream_t s)
+              int mode, unsigned long long cond, int set_cond, cudaStream_t s, int pdl = 0)
 {
     if (h->regen) {   // A regenerated in the kernel; A^T r whole in g, else in gpart (P = 1)
         regen_products(h, x, y, r, g ? g : gpart, mode, cond, set_cond, s);
@@ -125,6 +125,7 @@ void products(tvcs_ctx* h, const float* x, const float* y, float* r, float* gpar
     a.set_cond = set_cond;
     a.g_out = g;
     a.budget = budget_of(h);
+    a.pdl = pdl;
     launch_products(h->n, h->P, a, s);
 }
 
@@ -134,7 +135,7 @@ void launch_iteration(tvcs_ctx* h, unsigned long long cond, int set_cond, cudaSt
 {
     TvArgs a = tv_args(h, MODE_ITER, false);
     launch_usolve(h->n, h->ucluster, a, s);
-    products(h, h->u, h->f, h->r, h->gpart, h->g, MODE_ITER, cond, set_cond, s);
+    products(h, h->u, h->f, h->r, h->gpart, h->g, MODE_ITER, cond, set_cond, s, h->pdl);
 }
 
 tvcs_status sync_and_check(tvcs_ctx* h, const char* what)
