@@ -22,9 +22,9 @@
 
 namespace tvcs {
 
-constexpr int PROD_CONS = 512;
-constexpr int PROD_THREADS = PROD_CONS + 32;
-constexpr int PROD_NST = 3;
+constexpr int PROD_CONS = 512;           // 16 warps; thread 0 also issues the TMA copies
+constexpr int PROD_THREADS = PROD_CONS;
+constexpr int PROD_NST = 2;
 
 template <int V, int RL, int RS>
 struct ProdShape {
@@ -39,8 +39,10 @@ struct ProdShape {
     static_assert(TPR % 32 == 0, "row lanes must be whole warps");
 };
 
+// At most 96 registers a thread: 16 warps x 96 leave room in each of the SM's
+// four register files for a block of the u-solve beside a block of this kernel.
 template <int V, int RL, int RS>
-__global__ void __launch_bounds__(PROD_THREADS, 1)
+__global__ void __maxnreg__(96)
     k_products(const float* __restrict__ A, int m, const float* __restrict__ x,
                const float* __restrict__ y, float* __restrict__ r, float* __restrict__ gpart,
                float* __restrict__ g_out, double* __restrict__ r2part, Ctrl* __restrict__ ctrl,
@@ -60,22 +62,6 @@ __global__ void __launch_bounds__(PROD_THREADS, 1)
     float* sy = reinterpret_cast<float*>(sflag + 4);                // [YMAX]
 
     const int tid = threadIdx.x;
-    pdl_wait_then_release();   // x and the control block come from the preceding u-solve
-    if (mode == MODE_ITER) {
-        const int skip = ctrl->skip;
-        if (blockIdx.x == 0 && tid == 0) {
-            if (!skip && ctrl->algo == 0) ctrl->pending = 1;
-            if (set_cond) {
-                // The loop ends when the run is done; `loops` bounds it independently.
-                const int lc = ++ctrl->loops;
-                const int cont =
-                    (!ctrl->done && ctrl->error == ERR_NONE && lc < ctrl->loops_max) ? 1 : 0;
-                cudaGraphSetConditional(cond, (unsigned)cont);
-            }
-        }
-        if (skip) return;
-    }
-
     const int G = gridDim.x;
     const int i0 = (int)(((long long)m * blockIdx.x) / G);
     const int i1 = (int)(((long long)m * (blockIdx.x + 1)) / G);
@@ -91,31 +77,41 @@ __global__ void __launch_bounds__(PROD_THREADS, 1)
     }
     __syncthreads();
 
-    if (tid >= PROD_CONS) {
-        // ---------------- producer warp ----------------
-        if (tid == PROD_CONS) {
-            const uint64_t pol = l2_policy_evict_first();
-            bool ok = true;
-            for (int s = 0; s < nst; ++s) {
-                const int slot = s % PROD_NST;
-                if (s >= PROD_NST && ok) {
-                    if (!mbar_wait(&empty[slot], ((s / PROD_NST) - 1) & 1, budget)) {
-                        set_error(ctrl, ERR_TIMEOUT);
-                        ok = false;
-                    }
-                }
-                if (!ok) break;
-                const int rows = min(RS, nrows - s * RS);
-                const uint32_t bytes = (uint32_t)rows * N * 4u;
-                mbar_arrive_expect_tx(&full[slot], bytes);
-                tma_load_1d(stage + slot * S::STAGE_FLOATS, A + (size_t)(i0 + s * RS) * N, bytes,
-                            &full[slot], pol);
+    // The TMA copies are issued by thread 0.  A does not depend on the preceding
+    // kernel: the first PROD_NST stages go out before the dependency wait, so
+    // that under a programmatic dependent launch they stream in while the
+    // u-solve still runs.
+    const uint64_t pol = l2_policy_evict_first();
+    auto issue = [&](int s) {
+        const int slot = s % PROD_NST;
+        const int rows = min(RS, nrows - s * RS);
+        const uint32_t bytes = (uint32_t)rows * N * 4u;
+        mbar_arrive_expect_tx(&full[slot], bytes);
+        tma_load_1d(stage + slot * S::STAGE_FLOATS, A + (size_t)(i0 + s * RS) * N, bytes,
+                    &full[slot], pol);
+    };
+    const int pre = min(PROD_NST, nst);
+    int issued = 0;   // stages issued (thread 0)
+    if (tid == 0)
+        for (; issued < pre; ++issued) issue(issued);
+    pdl_wait_then_release();   // x and the control block come from the preceding u-solve
+    if (mode == MODE_ITER) {
+        const int skip = ctrl->skip;
+        if (blockIdx.x == 0 && tid == 0) {
+            if (!skip && ctrl->algo == 0) ctrl->pending = 1;
+            if (set_cond) {
+                // The loop ends when the run is done; `loops` bounds it independently.
+                const int lc = ++ctrl->loops;
+                const int cont =
+                    (!ctrl->done && ctrl->error == ERR_NONE && lc < ctrl->loops_max) ? 1 : 0;
+                cudaGraphSetConditional(cond, (unsigned)cont);
             }
-            // Leave no copy in flight: wait for the last stages to land.
-            const int first = ok ? max(0, nst - PROD_NST) : nst;
-            for (int s = first; s < nst; ++s) mbar_wait(&full[s % PROD_NST], (s / PROD_NST) & 1, budget);
         }
-        return;
+        if (skip) {   // leave no copy in flight
+            if (tid == 0)
+                for (int s = 0; s < pre; ++s) mbar_wait(&full[s], 0u, budget);
+            return;
+        }
     }
 
     // ---------------- consumers ----------------
@@ -190,7 +186,21 @@ __global__ void __launch_bounds__(PROD_THREADS, 1)
         }
         __syncwarp();
         if ((tid & 31) == 0) mbar_arrive(&empty[slot]);
+        // refill this slot with stage s + PROD_NST once every warp is done with it
+        if (tid == 0 && s + PROD_NST < nst) {
+            if (ok && !mbar_wait(&empty[slot], (s / PROD_NST) & 1, budget)) {
+                set_error(ctrl, ERR_TIMEOUT);
+                ok = false;
+            }
+            if (ok) {
+                issue(s + PROD_NST);
+                ++issued;
+            }
+        }
     }
+    if (tid == 0 && !ok)   // a wait gave up: let the copies still in flight land (bounded)
+        for (int s = max(0, issued - PROD_NST); s < issued; ++s)
+            mbar_wait(&full[s % PROD_NST], (s / PROD_NST) & 1, budget);
 
     // ---------------- epilogue: partial A^T r and ||r||^2 ----------------
     named_barrier(1, PROD_CONS);   // every consumer is done with the stage ring
@@ -224,11 +234,13 @@ __global__ void __launch_bounds__(PROD_THREADS, 1)
         double s = 0.0;
         for (int l = 0; l < RL; ++l) s += dred[l];
         r2part[blockIdx.x] = s;
-        sflag[0] = last_block_arrive(&ctrl->ticket_prod) ? 1 : 0;
+        // without the grid barrier below, the last block to arrive sums the partials
+        sflag[0] = (g_out == nullptr && last_block_arrive(&ctrl->ticket_prod)) ? 1 : 0;
     }
     named_barrier(1, PROD_CONS);
-    if (sflag[0]) {   // last block: sum the G partials with all consumer warps (G <= 512)
-        double v = tid < G ? r2part[tid] : 0.0;
+    // ||r||^2 = sum of the G partials with all consumer warps (G <= 512), fixed order
+    auto sum_r2 = [&]() {
+        double v = tid < G ? __ldcg(r2part + tid) : 0.0;
         v = warp_sum(v);
         if ((tid & 31) == 0) dred[tid >> 5] = v;
         named_barrier(1, PROD_CONS);
@@ -237,7 +249,8 @@ __global__ void __launch_bounds__(PROD_THREADS, 1)
             for (int w = 0; w < PROD_CONS / 32; ++w) t += dred[w];
             ctrl->r2 = t;
         }
-    }
+    };
+    if (sflag[0]) sum_r2();
     if (g_out == nullptr) return;
 
     // ---------------- grid barrier, then g = sum of the G partials ----------------
@@ -258,6 +271,7 @@ __global__ void __launch_bounds__(PROD_THREADS, 1)
         __threadfence();
     }
     named_barrier(1, PROD_CONS);
+    if (blockIdx.x == 0) sum_r2();   // every block's partial is visible after the barrier
     // This block's slice of float4 columns; warp w sums partials w, w+16, ... and
     // warp 0 adds the 16 warp sums in order (deterministic).
     const int N4 = N / 4;
@@ -267,13 +281,23 @@ __global__ void __launch_bounds__(PROD_THREADS, 1)
     float4* sred = reinterpret_cast<float4*>(stage);   // [16][32], the stage ring is free
     float4* g4 = reinterpret_cast<float4*>(g_out);
     const int lane = tid & 31, warp = tid >> 5;
+    constexpr int NWC = PROD_CONS / 32;   // consumer warps
+    constexpr int BATCH = 10;             // partials in flight per thread (G <= 160: one round)
     for (int base = c0; base < c1; base += 32) {
         const int c = base + lane;
         float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
         if (c < c1) {
-            for (int p = warp; p < G; p += PROD_CONS / 32) {
-                const float4 v = __ldcg(gp4 + (size_t)p * N4 + c);
-                s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+            for (int p0 = warp; p0 < G; p0 += NWC * BATCH) {
+                float4 v[BATCH];
+#pragma unroll
+                for (int k = 0; k < BATCH; ++k) {   // all loads issued before the first add
+                    const int p = p0 + k * NWC;
+                    v[k] = p < G ? __ldcg(gp4 + (size_t)p * N4 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int k = 0; k < BATCH; ++k) {   // partials in increasing order, as before
+                    s.x += v[k].x; s.y += v[k].y; s.z += v[k].z; s.w += v[k].w;
+                }
             }
         }
         sred[warp * 32 + lane] = s;
