@@ -108,14 +108,17 @@ __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
     const int rank = (int)cluster.block_rank();
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int r0 = rank * R;
-    pdl_wait_then_release();   // g and the control block come from the preceding products
-
+    // u, w, lambda, wpar and done were written by the previous u-solve, which
+    // completed before the preceding product kernel passed its dependency wait;
+    // only g and the products' control fields need this kernel's own wait.
     if (mode == MODE_ITER) {
         const int done = ctrl->done;   // stable during this kernel
         if (rank == 0 && tid == 0) ctrl->skip = done;
-        if (done) return;              // uniform across the cluster: before any cluster barrier
+        if (done) {                    // uniform across the cluster: before any cluster barrier
+            pdl_wait_then_release();   // completes only after the preceding grid
+            return;
+        }
     }
-    const int pending = ctrl->pending;
     const int par = ctrl->wpar;
     const float* wsrc = wbuf + (size_t)par * 2 * N;
     const float* lsrc = lbuf + (size_t)par * 2 * N;
@@ -124,8 +127,9 @@ __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
 
     // ---------------- phase A ----------------
     // Every input of the block in one round of asynchronous 16-byte copies:
-    // twiddles, 4 sin^2 table, u rows r0-1 .. r0+R, g rows r0 .. r0+R-1, and
-    // w, lambda rows r0-1 .. r0+R-1.
+    // twiddles, 4 sin^2 table, u rows r0-1 .. r0+R, and w, lambda rows
+    // r0-1 .. r0+R-1 before the dependency wait (under a programmatic dependent
+    // launch they arrive while the products finish), g rows r0 .. r0+R-1 after it.
     constexpr int CPR = NN / 4;       // 16-byte chunks per row
     constexpr int WL = (R + 1) * NN;
     for (int i = tid; i < NN / 2; i += nthr) cp_async16(tw + 2 * i, tw_g + 2 * i);
@@ -135,7 +139,6 @@ __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
         const int row = (r0 - 1 + rr + NN) % NN;
         cp_async16(su + rr * NN + 4 * c4, u + row * NN + 4 * c4);
     }
-    for (int i = tid; i < R * CPR; i += nthr) cp_async16(sg + 4 * i, g + r0 * NN + 4 * i);
     for (int i = tid; i < (R + 1) * CPR; i += nthr) {
         const int rr = i / CPR, c4 = i - rr * CPR;
         const int gi = ((r0 - 1 + rr + NN) % NN) * NN + 4 * c4;
@@ -145,6 +148,9 @@ __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
         cp_async16(swl + 2 * WL + li, lsrc + gi);
         cp_async16(swl + 3 * WL + li, lsrc + N + gi);
     }
+    pdl_wait_then_release();   // g and the products' control fields are complete
+    const int pending = ctrl->pending;
+    for (int i = tid; i < R * CPR; i += nthr) cp_async16(sg + 4 * i, g + r0 * NN + 4 * i);
     cp_async_wait_all();
     __syncthreads();
 

@@ -129,11 +129,15 @@ void products(tvcs_ctx* h, const float* x, const float* y, float* r, float* gpar
     launch_products(h->n, h->P, a, s);
 }
 
-// The body of one iteration (rows a1-a7), MODE_ITER: w-step and row FFT,
-// column pass, inverse rows, products, reduction of the partials into g.
-void launch_iteration(tvcs_ctx* h, unsigned long long cond, int set_cond, cudaStream_t s)
+// One iteration (rows a1-a7), MODE_ITER: the cluster u-solve, then the products
+// with the reduction of their partials into g.  With pdl_first the
+// u-solve is launched with a programmatic dependency on the preceding product
+// kernel (inside a graph body; not across the WHILE node's iterations).
+void launch_iteration(tvcs_ctx* h, unsigned long long cond, int set_cond, cudaStream_t s,
+                      bool pdl_first)
 {
     TvArgs a = tv_args(h, MODE_ITER, false);
+    a.pdl = (pdl_first && h->pdl) ? 1 : 0;
     launch_usolve(h->n, h->ucluster, a, s);
     products(h, h->u, h->f, h->r, h->gpart, h->g, MODE_ITER, cond, set_cond, s, h->pdl);
 }
@@ -211,7 +215,10 @@ tvcs_status build_graph(tvcs_ctx* h)
     cudaGraph_t body = np.conditional.phGraph_out[0];
     CK(cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0,
                                      cudaStreamCaptureModeThreadLocal));
-    launch_iteration(h, (unsigned long long)ch, 1, h->cap_stream);
+    // two iterations per body, so that both kernel boundaries of one of them are
+    // programmatic; the second half is skipped when the first ends the run
+    launch_iteration(h, (unsigned long long)ch, 0, h->cap_stream, false);
+    launch_iteration(h, (unsigned long long)ch, 1, h->cap_stream, true);
     cudaGraph_t captured = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->cap_stream, &captured);
     if (e != cudaSuccess) return fail(TVCS_ERR_CUDA, "capture of the loop body: %s", cudaGetErrorString(e));
@@ -281,7 +288,7 @@ tvcs_status run_loop(tvcs_ctx* h, int iters, double tol, tvcs_result* res)
         if (h->opt.host_loop) {
             // Same kernels launched from the host, one iteration at a time (for
             // profilers that cannot look inside graphs with conditional nodes).
-            for (int k = 0; k < iters; ++k) launch_iteration(h, 0ull, 0, h->stream);
+            for (int k = 0; k < iters; ++k) launch_iteration(h, 0ull, 0, h->stream, false);
         } else {
             CK(cudaGraphLaunch(h->exec, h->stream));
         }
