@@ -200,6 +200,8 @@ tvcs_status alloc(void** p, size_t bytes)
 
 // Runs the iteration body in a loop graph: K1 -> column pass -> inverse rows ->
 // products; the products kernel sets the WHILE condition from ctrl->done.
+constexpr int ITERS_PER_BODY = 4;
+
 tvcs_status build_graph(tvcs_ctx* h)
 {
     if (h->exec) return TVCS_OK;
@@ -215,10 +217,12 @@ tvcs_status build_graph(tvcs_ctx* h)
     cudaGraph_t body = np.conditional.phGraph_out[0];
     CK(cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0,
                                      cudaStreamCaptureModeThreadLocal));
-    // two iterations per body, so that both kernel boundaries of one of them are
-    // programmatic; the second half is skipped when the first ends the run
-    launch_iteration(h, (unsigned long long)ch, 0, h->cap_stream, false);
-    launch_iteration(h, (unsigned long long)ch, 1, h->cap_stream, true);
+    // ITERS_PER_BODY iterations per body, so that all kernel boundaries but the
+    // one across the WHILE node are programmatic; the rest of a body is skipped
+    // once an iteration ends the run
+    for (int k = 0; k < ITERS_PER_BODY; ++k)
+        launch_iteration(h, (unsigned long long)ch, k + 1 == ITERS_PER_BODY ? 1 : 0,
+                         h->cap_stream, k > 0);
     cudaGraph_t captured = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->cap_stream, &captured);
     if (e != cudaSuccess) return fail(TVCS_ERR_CUDA, "capture of the loop body: %s", cudaGetErrorString(e));
