@@ -140,13 +140,25 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
-// Programmatic dependent launch: wait until the preceding grid in the stream
-// has completed and its memory is visible (a no-op when the launch had no
-// programmatic dependency), then allow the next grid to be launched early.
-__device__ __forceinline__ void pdl_wait_then_release()
+// Programmatic dependent launch.  pdl_wait: until the preceding grid in the
+// stream has completed and its memory is visible (a no-op when the launch had
+// no programmatic dependency).  pdl_release: the next grid may be launched
+// from now on (it still waits for this grid's completion before it reads
+// what this grid writes).
+__device__ __forceinline__ void pdl_wait()
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+__device__ __forceinline__ void pdl_release()
+{
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+__device__ __forceinline__ void pdl_wait_then_release()
+{
+    pdl_wait();
+    pdl_release();
 }
 
 // Named barrier over `count` threads (a multiple of 32).

@@ -94,9 +94,11 @@ __global__ void __maxnreg__(96)
     int issued = 0;   // stages issued (thread 0)
     if (tid == 0)
         for (; issued < pre; ++issued) issue(issued);
-    pdl_wait_then_release();   // x and the control block come from the preceding u-solve
+    pdl_wait();   // x and the control block come from the preceding u-solve
     if (mode == MODE_ITER) {
         const int skip = ctrl->skip;
+        // The next u-solve writes skip before its own wait: release it only now.
+        pdl_release();
         if (blockIdx.x == 0 && tid == 0) {
             if (!skip && ctrl->algo == 0) ctrl->pending = 1;
             if (set_cond) {
@@ -112,6 +114,8 @@ __global__ void __maxnreg__(96)
                 for (int s = 0; s < pre; ++s) mbar_wait(&full[s], 0u, budget);
             return;
         }
+    } else {
+        pdl_release();
     }
 
     // ---------------- consumers ----------------

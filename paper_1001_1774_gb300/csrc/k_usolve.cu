@@ -120,16 +120,17 @@ __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
         }
     }
     const int par = ctrl->wpar;
+    const int pending = ctrl->pending;   // set by the previous u-solve (or the host)
     const float* wsrc = wbuf + (size_t)par * 2 * N;
     const float* lsrc = lbuf + (size_t)par * 2 * N;
     float* wdst = wbuf + (size_t)(par ^ 1) * 2 * N;
     float* ldst = lbuf + (size_t)(par ^ 1) * 2 * N;
 
     // ---------------- phase A ----------------
-    // Every input of the block in one round of asynchronous 16-byte copies:
-    // twiddles, 4 sin^2 table, u rows r0-1 .. r0+R, and w, lambda rows
-    // r0-1 .. r0+R-1 before the dependency wait (under a programmatic dependent
-    // launch they arrive while the products finish), g rows r0 .. r0+R-1 after it.
+    // Inputs by asynchronous 16-byte copies: twiddles, 4 sin^2 table, u rows
+    // r0-1 .. r0+R, and w, lambda rows r0-1 .. r0+R-1 before the dependency wait
+    // (under a programmatic dependent launch they arrive while the products
+    // finish), g rows r0 .. r0+R-1 after it.
     constexpr int CPR = NN / 4;       // 16-byte chunks per row
     constexpr int WL = (R + 1) * NN;
     for (int i = tid; i < NN / 2; i += nthr) cp_async16(tw + 2 * i, tw_g + 2 * i);
@@ -148,15 +149,18 @@ __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
         cp_async16(swl + 2 * WL + li, lsrc + gi);
         cp_async16(swl + 3 * WL + li, lsrc + N + gi);
     }
-    pdl_wait_then_release();   // g and the products' control fields are complete
-    const int pending = ctrl->pending;
+    cp_async_wait_all();
+    __syncthreads();
+    // a1-a3 up to D^T y need no g: under a programmatic dependent launch they run
+    // while the products finish
+    step_wshrink<NN>(su, swl, WL, R, r0, beta, pending, sy1, sy2, wdst, ldst, tid, nthr);
+    __syncthreads();
+    step_dty<NN>(sy1, sy2, R, wa, tid, nthr);
+    pdl_wait_then_release();   // g is complete
     for (int i = tid; i < R * CPR; i += nthr) cp_async16(sg + 4 * i, g + r0 * NN + 4 * i);
     cp_async_wait_all();
     __syncthreads();
-
-    step_wshrink<NN>(su, swl, WL, R, r0, beta, pending, sy1, sy2, wdst, ldst, tid, nthr);
-    __syncthreads();
-    step_rhs<NN>(sy1, sy2, sg, R, r0, mu, wa, rhs_out, tid, nthr);
+    step_sub_g<NN>(sg, R, r0, mu, wa, rhs_out, tid, nthr);
     __syncthreads();
     float2* Zr = fft_block<NN, false>(wa, wb, tw, R / 2, NN);
     step_split<NN>(Zr, R, spec, Q, 1, tid, nthr);

@@ -90,6 +90,43 @@ __device__ __forceinline__ void step_rhs(const float* sy1, const float* sy2, con
     }
 }
 
+// a3 in two parts, for a caller that has y before g: step_dty stores
+// (D^T y)[r0+2j][c], (D^T y)[r0+2j+1][c] packed in wa[j NN + c]; step_sub_g then
+// subtracts mu g, giving the packed rows of step_rhs.
+template <int NN>
+__device__ __forceinline__ void step_dty(const float* sy1, const float* sy2, int R, float2* wa,
+                                         int tid, int nthr)
+{
+    for (int i = tid; i < (R / 2) * NN; i += nthr) {
+        const int j = i / NN, c = i - j * NN;
+        const int cm = (c == 0) ? NN - 1 : c - 1;
+        float v[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int lr = 2 * j + h;
+            v[h] = sy1[lr * NN + cm] - sy1[lr * NN + c] + sy2[lr * NN + c] - sy2[(lr + 1) * NN + c];
+        }
+        wa[i] = make_float2(v[0], v[1]);
+    }
+}
+
+template <int NN>
+__device__ __forceinline__ void step_sub_g(const float* sg, int R, int r0, float mu, float2* wa,
+                                           float* rhs_out, int tid, int nthr)
+{
+    for (int i = tid; i < (R / 2) * NN; i += nthr) {
+        const int j = i / NN, c = i - j * NN;
+        float2 v = wa[i];
+        v.x = v.x - mu * sg[(2 * j) * NN + c];
+        v.y = v.y - mu * sg[(2 * j + 1) * NN + c];
+        wa[i] = v;
+        if (rhs_out) {
+            rhs_out[(r0 + 2 * j) * NN + c] = v.x;
+            rhs_out[(r0 + 2 * j + 1) * NN + c] = v.y;
+        }
+    }
+}
+
 // a4: from the R/2 packed forward row transforms Z, the half spectra of the
 // owned rows, X_q = (Z_q + conj Z_{n-q}) / 2 and Y_q = (Z_q - conj Z_{n-q}) / (2i),
 // q = 0 .. n/2, stored at spec[lr * rs + q * qs] for local row lr.
