@@ -436,7 +436,9 @@ def run_batched(args):
     torch.cuda.nvtx.range_push("stage3")
     gemm_us = tv.tvcs_time_stage(h, 3, reps) * 1e3 / reps
     torch.cuda.nvtx.range_pop()
+    torch.cuda.nvtx.range_push("stage4")
     fix_us = tv.tvcs_time_stage(h, 4, reps) * 1e3 / reps
+    torch.cuda.nvtx.range_pop()
     torch.cuda.nvtx.range_push("stage5")
     us_us = tv.tvcs_time_stage(h, 5, reps) * 1e3 / reps
     torch.cuda.nvtx.range_pop()

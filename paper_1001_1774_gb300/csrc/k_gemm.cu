@@ -280,38 +280,71 @@ __global__ void __launch_bounds__(192, 1)
 
 // ---------------------------------------------------------------------------
 // Fix-up: D = sum of a tile's partials (in K order), then the epilogue.
-// Block (t, b): rows [128 t, 128 t + 128) of column (image) b.
+// Block (t, j): rows [128 t, 128 t + 128) of the columns (images) 8 j .. 8 j + 7.
 // mode 1: R = D - F, R planes, ||r_b||^2 partial;  mode 2: G = D.
 // ---------------------------------------------------------------------------
+constexpr int FX_B = 8;     // images per fix-up block
+constexpr int FX_SEG = 6;   // segments a tile usually has at most (more are added in a second pass)
+
 __global__ void __launch_bounds__(128) k_gemm_fixup(
     const float* __restrict__ ws, const int* __restrict__ tile_seg_begin,
-    const int* __restrict__ seg_slot, int M, const float* __restrict__ F, int ldf,
+    const int* __restrict__ seg_slot, int M, int count, const float* __restrict__ F, int ldf,
     float* __restrict__ out, int ldo, __nv_bfloat16* __restrict__ out_hi,
     __nv_bfloat16* __restrict__ out_lo, int ldh, double* __restrict__ r2part, int tiles_m,
     const Ctrl* __restrict__ ctrl, int check_skip)
 {
-    __shared__ double red[32];
+    __shared__ double red[4][FX_B];
     if (check_skip && ctrl->skip) return;
-    const int t = blockIdx.x, b = blockIdx.y;
+    const int t = blockIdx.x, b0 = blockIdx.y * FX_B;
     const int row = t * GM_BM + threadIdx.x;
     const int s0 = tile_seg_begin[t], s1 = tile_seg_begin[t + 1];
-    float d = 0.f;
-    for (int s = s0; s < s1; ++s)
-        d += ws[((size_t)seg_slot[s] * GM_BN + b) * GM_BM + threadIdx.x];
-    double sq = 0.0;
-    if (row < M) {
-        if (F) d -= F[(size_t)b * ldf + row];
-        out[(size_t)b * ldo + row] = d;
-        if (out_hi) {
-            const __nv_bfloat16 h = __float2bfloat16_rn(d);
-            out_hi[(size_t)b * ldh + row] = h;
-            out_lo[(size_t)b * ldh + row] = __float2bfloat16_rn(d - __bfloat162float(h));
+    const int ns = s1 - s0;
+    // every image's first FX_SEG partials are loaded before any is added
+    int slot[FX_SEG];
+#pragma unroll
+    for (int q = 0; q < FX_SEG; ++q) slot[q] = q < ns ? seg_slot[s0 + q] : 0;
+    float v[FX_B][FX_SEG];
+#pragma unroll
+    for (int k = 0; k < FX_B; ++k)
+#pragma unroll
+        for (int q = 0; q < FX_SEG; ++q)
+            v[k][q] = (q < ns && b0 + k < count)
+                          ? ws[((size_t)slot[q] * GM_BN + b0 + k) * GM_BM + threadIdx.x]
+                          : 0.f;
+    double sq[FX_B];
+#pragma unroll
+    for (int k = 0; k < FX_B; ++k) {
+        const int b = b0 + k;
+        sq[k] = 0.0;
+        if (b >= count) continue;
+        float d = 0.f;   // the tile's segments in K order
+#pragma unroll
+        for (int q = 0; q < FX_SEG; ++q) d += v[k][q];
+        for (int s = s0 + FX_SEG; s < s1; ++s)
+            d += ws[((size_t)seg_slot[s] * GM_BN + b) * GM_BM + threadIdx.x];
+        if (row < M) {
+            if (F) d -= F[(size_t)b * ldf + row];
+            out[(size_t)b * ldo + row] = d;
+            if (out_hi) {
+                const __nv_bfloat16 h = __float2bfloat16_rn(d);
+                out_hi[(size_t)b * ldh + row] = h;
+                out_lo[(size_t)b * ldh + row] = __float2bfloat16_rn(d - __bfloat162float(h));
+            }
+            sq[k] = (double)d * (double)d;
         }
-        sq = (double)d * (double)d;
     }
-    if (r2part) {
-        const double s = block_sum(sq, red);
-        if (threadIdx.x == 0) r2part[(size_t)b * tiles_m + t] = s;
+    if (r2part) {   // per image: the sum over the tile's rows (fixed order)
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+        for (int k = 0; k < FX_B; ++k) {
+            const double v = warp_sum(sq[k]);
+            if (lane == 0) red[w][k] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < FX_B && b0 + (int)threadIdx.x < count) {
+            const int k = threadIdx.x;
+            r2part[(size_t)(b0 + k) * tiles_m + t] = ((red[0][k] + red[1][k]) + red[2][k]) + red[3][k];
+        }
     }
 }
 
@@ -439,8 +472,8 @@ void launch_gemm_fixup(const float* ws, const int* tile_seg_begin, const int* se
                        void* out_hi, void* out_lo, int ldh, double* r2part, const Ctrl* ctrl,
                        int check_skip, cudaStream_t s)
 {
-    dim3 grid(tiles_m, count);
-    k_gemm_fixup<<<grid, 128, 0, s>>>(ws, tile_seg_begin, seg_slot, M, F, ldf, out, ldo,
+    dim3 grid(tiles_m, (count + FX_B - 1) / FX_B);
+    k_gemm_fixup<<<grid, 128, 0, s>>>(ws, tile_seg_begin, seg_slot, M, count, F, ldf, out, ldo,
                                       reinterpret_cast<__nv_bfloat16*>(out_hi),
                                       reinterpret_cast<__nv_bfloat16*>(out_lo), ldh, r2part,
                                       tiles_m, ctrl, check_skip);
