@@ -53,6 +53,8 @@ def parse_args():
                          "n256: 256x256, m=13107, A stored per --precision; "
                          "batch256: 256 images of 128x128 sharing one A (bf16 hi/lo); "
                          "uneven64: 64 problems of n in {64..192}, A regenerated in the kernel")
+    ap.add_argument("--algo", choices=["iadm", "ftvcs"], default="iadm",
+                    help="Algorithm 2 (IADM, default) or Algorithm 1 (FTVCS: lambda = 0, the penalty model)")
     ap.add_argument("--precision", type=int, default=0,
                     help="storage of A: 0 binary32, 1 bf16 hi+lo, 2 fp8 e4m3 + bf16 correction")
     ap.add_argument("--host-loop", action="store_true",
@@ -119,11 +121,11 @@ def whole_job_rate(ws: int, units_per_rank: float, ms: float) -> float:
     return ws * units_per_rank / (ms / 1e3)
 
 
-def workload_config(P, A_bytes, precision=0):
+def workload_config(P, A_bytes, precision=0, algo="iadm"):
     name = "n%d_m%d_%s_single_image" % (P.n, P.m, STORAGE[precision][0])
     return {"workload": name, "n": P.n, "m": P.m, "N": P.N, "A_storage": STORAGE[precision][0],
             "mu": P.mu, "beta": P.beta, "iters_per_recon": ITERS_PER_RECON,
-            "A_bytes": A_bytes, "algo": "IADM",
+            "A_bytes": A_bytes, "algo": algo.upper(),
             "l2": ("inputs larger than L2 (A = %.0f MB > 129 MB); no flush" % (A_bytes / 1e6)
                    if A_bytes > 129e6 else
                    "A (%.1f MB) is L2-resident: latency-bound, no roofline claim" % (A_bytes / 1e6)),
@@ -209,20 +211,20 @@ def traffic_from_profile():
 
 # ----------------------------------------------------------------------------- CPU oracle sample
 
-def oracle_sample(P, tau, budget_s=20.0, want_u=False):
+def oracle_sample(P, tau, budget_s=20.0, want_u=False, algo=0):
     """Times the FP64 oracle (as it stands) on this host: iterations/s measured on
     a bounded number of iterations of the same workload."""
     import numpy as np
     import oracle
     t0 = time.perf_counter()
-    oracle.solve(P.A, P.f, P.n, P.mu, P.beta, tau, max_iter=0)
+    oracle.solve(P.A, P.f, P.n, P.mu, P.beta, tau, max_iter=0, algo=algo)
     t_init = time.perf_counter() - t0
     t0 = time.perf_counter()
-    oracle.solve(P.A, P.f, P.n, P.mu, P.beta, tau, max_iter=2)
+    oracle.solve(P.A, P.f, P.n, P.mu, P.beta, tau, max_iter=2, algo=algo)
     per = max((time.perf_counter() - t0 - t_init) / 2, 1e-6)
     iters = ITERS_PER_RECON if per * ITERS_PER_RECON <= budget_s else max(2, int(budget_s / per))
     t0 = time.perf_counter()
-    res = oracle.solve(P.A, P.f, P.n, P.mu, P.beta, tau, max_iter=iters)
+    res = oracle.solve(P.A, P.f, P.n, P.mu, P.beta, tau, max_iter=iters, algo=algo)
     elapsed = time.perf_counter() - t0 - t_init
     return {"iters": iters, "seconds": elapsed, "value": iters / elapsed,
             "cores": oracle.num_threads(), "u": res.u if want_u else None}
@@ -257,6 +259,7 @@ def run_ours(args):
     opt.precision = args.precision
     opt.stream = ctypes_stream(stream)
     opt.host_loop = 1 if args.host_loop else 0
+    opt.algo = 1 if args.algo == "ftvcs" else 0
     with torch.cuda.stream(stream):
         A_dev = torch.from_numpy(P.A).cuda()
         f_dev = torch.from_numpy(P.f).cuda()
@@ -320,6 +323,9 @@ def run_ours(args):
         assert r.iters == ITERS_PER_RECON
     e2e_s = max_over_ranks(time.perf_counter() - t0, ws, dev)
     u_gpu = u_host.numpy().copy()
+    # relative error of the reconstruction against the phantom (Sec. 3.1)
+    ub = P.ubar.ravel().astype(np.float64)
+    rel_err_ubar = float(np.linalg.norm(u_gpu.astype(np.float64) - ub) / np.linalg.norm(ub))
 
     out = None
     if rank == 0:
@@ -336,7 +342,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic (seeded phantom, Philox Gaussian A)",
             "recons_per_s": value / ITERS_PER_RECON,
-            "config": workload_config(P, A_bytes, args.precision),
+            "config": workload_config(P, A_bytes, args.precision, args.algo),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_products (fused A u - f and A^T r, one pass over A)",
@@ -351,9 +357,10 @@ def run_ours(args):
             "gpu_launches": 2 * args.steps + 2,
             "clocks": clocks,
             "tau": tau,
+            "relative_error_vs_phantom": rel_err_ubar,
         }
         if ws == 1 and not args.no_cpu_baseline:
-            cb = oracle_sample(P, tau, want_u=True)
+            cb = oracle_sample(P, tau, want_u=True, algo=1 if args.algo == "ftvcs" else 0)
             out["cpu_baseline"] = {"value": cb["value"], "unit": "iter/s", "cores": cb["cores"],
                                    "kind": "oracle",
                                    "sample": "%d IADM iterations of the same workload (FP64 C "
@@ -675,7 +682,7 @@ def run_reference(args):
     t0 = time.perf_counter()
     oracle.solve(P.A, P.f, P.n, P.mu, P.beta, tau, max_iter=min(args.warmup, 3))
     warm = time.perf_counter() - t0
-    cb = oracle_sample(P, tau, budget_s=budget)
+    cb = oracle_sample(P, tau, budget_s=budget, algo=1 if args.algo == "ftvcs" else 0)
     A_bytes = P.m * P.N * 4
     value = cb["value"]
     sample = ("%d of %d requested IADM iterations (FP64 C oracle, OpenMP), %.1f s"
@@ -684,7 +691,7 @@ def run_reference(args):
            "n_gpus": ws, "steps": cb["iters"], "warmup": args.warmup,
            "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded phantom, Philox Gaussian A)",
-           "config": workload_config(P, A_bytes),
+           "config": workload_config(P, A_bytes, 0, args.algo),
            "cpu_baseline": {"value": value, "unit": "iter/s", "cores": cb["cores"],
                             "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0,

@@ -145,6 +145,18 @@ tvcs_status tvcs_solve(tvcs_handle h, const float* f, float* u, tvcs_result* res
 tvcs_status tvcs_solve_batched(const tvcs_handle* hs, int count, const float* const* f,
                                float* const* u, const double* mu, tvcs_result* res);
 
+/*
+ * Continuation in beta (the practice of Sec. 3.1 for Algorithm 1): solves with
+ * beta = betas[0] from the handle's initial point, then with betas[1], ...,
+ * each stage warm-started from the previous stage's u and lambda (w restarted
+ * at 0) and run to eq. (stop) or max_iter.  f (m values) and u (n*n values)
+ * host or device; res (nullable) receives nbeta stage summaries.  The handle's
+ * own beta is in force again when the call returns.  Returns the worst stage
+ * status (TVCS_NOT_CONVERGED if a stage hit max_iter) or an error.
+ */
+tvcs_status tvcs_solve_continuation(tvcs_handle h, const float* f, float* u, const double* betas,
+                                    int nbeta, tvcs_result* res);
+
 /* Releases every resource of h (NULL is a no-op). */
 tvcs_status tvcs_destroy(tvcs_handle h);
 

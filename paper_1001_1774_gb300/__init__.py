@@ -34,6 +34,7 @@ TVCS_A_STORED, TVCS_A_REGENERATE = 0, 1
  TVCS_STATE_F) = range(7)
 
 EXPORTED = ["tvcs_default_options", "tvcs_create", "tvcs_solve", "tvcs_solve_batched",
+            "tvcs_solve_continuation",
             "tvcs_destroy", "tvcs_last_error", "tvcs_get_tau", "tvcs_get_state",
             "tvcs_set_state", "tvcs_iterate", "tvcs_run_stage", "tvcs_time_stage", "tvcs_apply",
             "tvcs_apply_noalloc", "tvcs_apply_batched"]
@@ -76,6 +77,7 @@ def _load() -> ctypes.CDLL:
         "tvcs_create": ([ctypes.POINTER(H), vp, u64, i, i, d, d, d, ctypes.POINTER(tvcs_options)], i),
         "tvcs_solve": ([H, vp, vp, ctypes.POINTER(tvcs_result)], i),
         "tvcs_solve_batched": ([vp, i, vp, vp, vp, vp], i),
+        "tvcs_solve_continuation": ([H, vp, vp, vp, i, vp], i),
         "tvcs_destroy": ([H], i),
         "tvcs_last_error": ([], ctypes.c_char_p),
         "tvcs_get_tau": ([H, ctypes.POINTER(d)], i),
@@ -185,6 +187,15 @@ def tvcs_solve_batched(hs, f_list, u_list, mu=None) -> list:
     muarr = (ctypes.c_double * count)(*mu) if mu is not None else None
     res = (tvcs_result * count)()
     _check(_lib.tvcs_solve_batched(harr, count, farr, uarr, muarr, res))
+    return list(res)
+
+
+def tvcs_solve_continuation(h: Handle, f, u, betas) -> list:
+    """Continuation in beta; returns one tvcs_result per stage."""
+    n = len(betas)
+    barr = (ctypes.c_double * n)(*[float(b) for b in betas])
+    res = (tvcs_result * n)()
+    _check(_lib.tvcs_solve_continuation(h.ptr, _ptr(f, h.m), _ptr(u, h.N, True), barr, n, res))
     return list(res)
 
 

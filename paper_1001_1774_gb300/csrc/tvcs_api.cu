@@ -610,6 +610,47 @@ tvcs_status tvcs_solve(tvcs_handle h, const float* f, float* u, tvcs_result* res
     return st;
 }
 
+tvcs_status tvcs_solve_continuation(tvcs_handle h, const float* f, float* u, const double* betas,
+                                    int nbeta, tvcs_result* res)
+{
+    CKS(check_handle(h));
+    if (!f || !u || !betas || nbeta < 1)
+        return fail(TVCS_ERR_INVALID_ARG, "f, u and betas must be non-NULL and nbeta >= 1");
+    for (int k = 0; k < nbeta; ++k)
+        if (!(betas[k] > 0.0) || !isfinite(betas[k]))
+            return fail(TVCS_ERR_INVALID_ARG, "betas[%d] must be > 0", k);
+    const double beta0 = h->beta;
+    auto drop_graph = [&]() {   // beta is a launch argument captured in the loop graph
+        if (h->exec) { cudaGraphExecDestroy(h->exec); h->exec = nullptr; }
+        if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+    };
+    CKS(copy_in(h, h->f, f, (size_t)h->m));
+    tvcs_status worst = TVCS_OK;
+    for (int k = 0; k < nbeta; ++k) {
+        if (betas[k] != h->beta) {
+            h->beta = betas[k];
+            drop_graph();
+        }
+        // stage 0 from the handle's initial point; later stages warm-started from the
+        // previous stage's u (and lambda), with w restarted at 0
+        tvcs_status st = init_state(h, k == 0 ? h->opt.init : TVCS_INIT_GIVEN);
+        if (st == TVCS_OK) st = run_loop(h, h->opt.max_iter, h->tol, res ? &res[k] : nullptr);
+        if (st < 0) {
+            h->beta = beta0;
+            drop_graph();
+            return st;
+        }
+        if (st > worst) worst = st;
+    }
+    if (h->beta != beta0) {
+        h->beta = beta0;
+        drop_graph();
+    }
+    CKS(copy_out(h, u, h->u, (size_t)h->N));
+    CKS(sync_and_check(h, "tvcs_solve_continuation"));
+    return worst;
+}
+
 tvcs_status tvcs_solve_batched(const tvcs_handle* hs, int count, const float* const* f,
                                float* const* u, const double* mu, tvcs_result* res)
 {

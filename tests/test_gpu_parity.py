@@ -354,3 +354,46 @@ def test_workload_n128_300_iterations(tv):
     assert rel(u.cpu().numpy(), ref.u) <= 1e-4
     assert abs(res.objective - ref.info["objective"]) <= 1e-5 * ref.info["objective"]
     tv.tvcs_destroy(h)
+
+
+def test_workload_n128_300_iterations_ftvcs(tv):
+    # Algorithm 1 (FTVCS, lambda = 0) on the benchmark workload at full size.
+    P = synth.workload_n128()
+    tau = oracle.default_tau(P.A, 100)
+    h = make_handle(tv, P, tau, algo=1, max_iter=300)
+    u = torch.empty(P.N, dtype=torch.float32, device="cuda")
+    res = tv.tvcs_solve(h, torch.from_numpy(P.f).cuda(), u)
+    ref = oracle.solve(P.A, P.f, P.n, P.mu, P.beta, tau, max_iter=300, algo=oracle.FTVCS)
+    assert res.iters == 300
+    assert rel(u.cpu().numpy(), ref.u) <= 1e-4
+    assert abs(res.objective - ref.info["objective"]) <= 1e-5 * ref.info["objective"]
+    assert np.all(tv.get_state(h, tv.TVCS_STATE_LAMBDA) == 0)
+    tv.tvcs_destroy(h)
+
+
+@pytest.mark.parametrize("algo", [1, 0])
+def test_beta_continuation_matches_oracle_stages(tv, algo):
+    # Sec. 3.1's practice: beta = 2^4 .. 2^7, each stage warm-started from the last.
+    P = synth.make_problem(32, 0.3, 5, 6, 1e3, 10.0, noise_c=1e-3)
+    tau = oracle.default_tau(P.A)
+    betas = [2.0 ** 4, 2.0 ** 5, 2.0 ** 6, 2.0 ** 7]
+    h = make_handle(tv, P, tau, algo=algo, max_iter=40)
+    u = np.empty(P.N, np.float32)
+    res = tv.tvcs_solve_continuation(h, P.f, u, betas)
+    assert len(res) == 4 and all(r.iters == 40 for r in res)
+    u0 = lam0 = None
+    for b in betas:   # the oracle, stage after stage from the previous stage's u and lambda
+        ref = oracle.solve(P.A, P.f, P.n, P.mu, b, tau, max_iter=40,
+                           algo=oracle.FTVCS if algo == 1 else oracle.IADM, u0=u0,
+                           lam0=lam0 if algo == 0 else None)
+        u0, lam0 = ref.u, ref.lam
+    assert rel(u, ref.u) <= 1e-5
+    # the handle's own beta is in force again: a plain solve equals a fresh handle's
+    u1 = np.empty(P.N, np.float32)
+    tv.tvcs_solve(h, P.f, u1)
+    h2 = make_handle(tv, P, tau, algo=algo, max_iter=40)
+    u2 = np.empty(P.N, np.float32)
+    tv.tvcs_solve(h2, P.f, u2)
+    assert np.array_equal(u1, u2)
+    tv.tvcs_destroy(h)
+    tv.tvcs_destroy(h2)
