@@ -79,6 +79,13 @@ def _load():
                 "oracle_kkt": ([ctypes.POINTER(_Params), vp, vp, vp, vp, vp,
                                 ctypes.POINTER(_Info)], None),
                 "oracle_num_threads": ([], i),
+                "oracle_dct2": ([i, i, vp, vp], None),
+                "oracle_dct_Au": ([i, i, vp, vp, vp, vp], None),
+                "oracle_dct_At": ([i, i, vp, vp, vp], None),
+                "oracle_solve_dct": ([ctypes.POINTER(_Params), vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                      ctypes.POINTER(_Info)], i),
+                "oracle_kkt_dct": ([ctypes.POINTER(_Params), vp, vp, vp, vp, vp,
+                                    ctypes.POINTER(_Info)], None),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(lib, name)
@@ -234,6 +241,71 @@ def solve(A: np.ndarray, f: np.ndarray, n: int, mu: float, beta: float, tau: flo
     k = d["iters"]
     return Result(u, w, lam, d, hist[:k] if hist is not None else None,
                   uh[:k + 1] if uh is not None else None)
+
+
+# ---- partial-DCT encoder (Sec. 3.2, reading C18) ----
+
+def _rows(rows) -> np.ndarray:
+    return np.ascontiguousarray(rows, dtype=np.int32)
+
+
+def dct2(x: np.ndarray, inverse: bool = False) -> np.ndarray:
+    """Orthonormal 2D DCT-II C x C^T of an n x n image (inverse: C^T x C)."""
+    x = _f64(x)
+    n = x.shape[0]
+    out = np.empty((n, n))
+    _load().oracle_dct2(n, 1 if inverse else 0, x.ctypes.data, out.ctypes.data)
+    return out
+
+
+def dct_Au(n: int, rows, u: np.ndarray, f: np.ndarray | None = None) -> np.ndarray:
+    """r = (C u C^T)[rows] - f."""
+    rows = _rows(rows)
+    u = _f64(u)
+    r = np.empty(rows.size)
+    fp = _f32(f) if f is not None else None
+    _load().oracle_dct_Au(n, rows.size, rows.ctypes.data, u.ctypes.data,
+                          fp.ctypes.data if fp is not None else None, r.ctypes.data)
+    return r
+
+
+def dct_At(n: int, rows, r: np.ndarray) -> np.ndarray:
+    """g = A^T r = C^T S C, S zero except S[rows] = r."""
+    rows = _rows(rows)
+    r = _f64(r)
+    g = np.empty(n * n)
+    _load().oracle_dct_At(n, rows.size, rows.ctypes.data, r.ctypes.data, g.ctypes.data)
+    return g
+
+
+def solve_dct(rows, f: np.ndarray, n: int, mu: float, beta: float, tau: float,
+              tol: float = 0.0, max_iter: int = 100, algo: int = IADM, init: int = INIT_ATF,
+              u0: np.ndarray | None = None, lam0: np.ndarray | None = None,
+              record: bool = False) -> Result:
+    """solve() with the partial-DCT encoder A = (rows of the orthonormal 2D DCT)."""
+    rows = _rows(rows)
+    f = _f32(f)
+    m = rows.size
+    assert f.size == m
+    if u0 is not None:
+        init = INIT_GIVEN
+    p = _params(n, m, mu, beta, tau, tol, max_iter, algo, 1, init)
+    u = np.empty((n, n)); w = np.empty((2, n, n)); lam = np.empty((2, n, n))
+    hist = np.zeros((max(max_iter, 1), 4)) if record else None
+    u0a = _f64(u0).reshape(n, n) if u0 is not None else None
+    l0a = _f64(lam0).reshape(2, n, n) if lam0 is not None else None
+    info = _Info()
+    rc = _load().oracle_solve_dct(ctypes.byref(p), rows.ctypes.data, f.ctypes.data,
+                                  u0a.ctypes.data if u0a is not None else None,
+                                  l0a.ctypes.data if l0a is not None else None,
+                                  u.ctypes.data, w.ctypes.data, lam.ctypes.data,
+                                  hist.ctypes.data if hist is not None else None, None,
+                                  ctypes.byref(info))
+    if rc != 0:
+        raise ValueError("oracle_solve_dct failed with code %d" % rc)
+    d = {k: getattr(info, k) for k, _ in _Info._fields_}
+    k = d["iters"]
+    return Result(u, w, lam, d, hist[:k] if hist is not None else None, None)
 
 
 def kkt(A, f, n, mu, beta, u, w, lam) -> dict:

@@ -188,6 +188,96 @@ void oracle_At(int m, int64_t N, const float* A, const double* r, double* g)
     }
 }
 
+/* ---- Partial-DCT encoder (Sec. 3.2): A = rows of the orthonormal 2D DCT ----
+ * C[k][j] = a_k cos(pi (2j+1) k / (2n)), a_0 = sqrt(1/n), a_k = sqrt(2/n) (the
+ * orthonormal DCT-II; reading C18: the 2D transform is C x C^T on the n x n
+ * image).  The cosine is taken at the exactly reduced index (2j+1)k mod 4n. */
+static double* dct_matrix(int n)
+{
+    double* C = (double*)malloc(sizeof(double) * (size_t)n * n);
+    if (!C) return NULL;
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k < n; ++k) {
+        const double a = k == 0 ? sqrt(1.0 / n) : sqrt(2.0 / n);
+        for (int j = 0; j < n; ++j) {
+            const long t = ((long)(2 * j + 1) * k) % (4L * n);
+            C[(int64_t)k * n + j] = a * cos(2.0 * pi * (double)t / (4.0 * n));
+        }
+    }
+    return C;
+}
+
+/* out = C x C^T (forward) or C^T x C (inverse), x and out n x n row-major. */
+void oracle_dct2(int n, int inverse, const double* x, double* out)
+{
+    double* C = dct_matrix(n);
+    double* t = (double*)malloc(sizeof(double) * (size_t)n * n);
+    /* t = x C^T (forward: t[r][k] = sum_c x[r][c] C[k][c]) or x C (inverse) */
+    #pragma omp parallel for schedule(static)
+    for (int r = 0; r < n; ++r)
+        for (int k = 0; k < n; ++k) {
+            double acc = 0.0;
+            for (int c = 0; c < n; ++c)
+                acc += x[(int64_t)r * n + c] * (inverse ? C[(int64_t)c * n + k] : C[(int64_t)k * n + c]);
+            t[(int64_t)r * n + k] = acc;
+        }
+    /* out = C t (forward: out[k][q] = sum_r C[k][r] t[r][q]) or C^T t (inverse) */
+    #pragma omp parallel for schedule(static)
+    for (int k = 0; k < n; ++k)
+        for (int q = 0; q < n; ++q) {
+            double acc = 0.0;
+            for (int r = 0; r < n; ++r)
+                acc += (inverse ? C[(int64_t)r * n + k] : C[(int64_t)k * n + r]) * t[(int64_t)r * n + q];
+            out[(int64_t)k * n + q] = acc;
+        }
+    free(C);
+    free(t);
+}
+
+/* r_i = (C u C^T)[rows_i] - f_i (f may be NULL). */
+void oracle_dct_Au(int n, int m, const int32_t* rows, const double* u, const float* f, double* r)
+{
+    double* X = (double*)malloc(sizeof(double) * (size_t)n * n);
+    oracle_dct2(n, 0, u, X);
+    for (int i = 0; i < m; ++i) r[i] = f ? X[rows[i]] - (double)f[i] : X[rows[i]];
+    free(X);
+}
+
+/* g = A^T r = C^T S C with S zero except S[rows_i] = r_i. */
+void oracle_dct_At(int n, int m, const int32_t* rows, const double* r, double* g)
+{
+    double* S = (double*)calloc((size_t)n * n, sizeof(double));
+    for (int i = 0; i < m; ++i) S[rows[i]] += r[i];
+    oracle_dct2(n, 1, S, g);
+    free(S);
+}
+
+/* The encoder as an operator: a dense binary32 matrix, or partial-DCT rows. */
+typedef struct {
+    int dct;                 /* 0: dense A, 1: partial DCT */
+    int m;
+    int64_t N;
+    const float* A;          /* dense: m x N */
+    int n;
+    const int32_t* rows;     /* partial DCT: m coefficient indices */
+} oracle_op;
+
+static void op_Au(const oracle_op* op, const double* u, const float* f, double* r)
+{
+    if (op->dct)
+        oracle_dct_Au(op->n, op->m, op->rows, u, f, r);
+    else
+        oracle_Au(op->m, op->N, op->A, u, f, r);
+}
+
+static void op_At(const oracle_op* op, const double* r, double* g)
+{
+    if (op->dct)
+        oracle_dct_At(op->n, op->m, op->rows, r, g);
+    else
+        oracle_At(op->m, op->N, op->A, r, g);
+}
+
 static double dot(int64_t len, const double* x, const double* y)
 {
     double s = 0.0;
@@ -226,8 +316,8 @@ double oracle_tv(int n, const double* u)
     return s;
 }
 
-void oracle_kkt(const oracle_params* p, const float* A, const float* f, const double* u,
-                const double* w, const double* lam, oracle_info* info)
+static void kkt_impl(const oracle_params* p, const oracle_op* op, const float* f, const double* u,
+                     const double* w, const double* lam, oracle_info* info)
 {
     int n = p->n, m = p->m;
     int64_t N = (int64_t)n * n;
@@ -244,9 +334,9 @@ void oracle_kkt(const oracle_params* p, const float* A, const float* f, const do
         pr += e1 * e1 + e2 * e2;
         atv += sqrt(w[i] * w[i] + w[N + i] * w[N + i]) + 0.5 * p->beta * (e1 * e1 + e2 * e2);
     }
-    oracle_Au(m, N, A, u, f, r);
+    op_Au(op, u, f, r);
     double r2 = dot(m, r, r);
-    oracle_At(m, N, A, r, g);
+    op_At(op, r, g);
     oracle_Dt(n, lam, lam + N, t);
     double du = 0.0, lmax = 0.0, align = 0.0;
     for (int64_t i = 0; i < N; ++i) {
@@ -273,12 +363,26 @@ void oracle_kkt(const oracle_params* p, const float* A, const float* f, const do
     free(d1); free(d2); free(r); free(g); free(t);
 }
 
-int oracle_solve(const oracle_params* p, const float* A, const float* f,
-                 const double* u0, const double* lam0,
-                 double* u_out, double* w_out, double* lam_out, double* hist, double* u_hist,
-                 oracle_info* info)
+void oracle_kkt(const oracle_params* p, const float* A, const float* f, const double* u,
+                const double* w, const double* lam, oracle_info* info)
 {
-    if (!p || !A || !f || !u_out || !info) return -1;
+    oracle_op op = {0, p->m, (int64_t)p->n * p->n, A, p->n, NULL};
+    kkt_impl(p, &op, f, u, w, lam, info);
+}
+
+void oracle_kkt_dct(const oracle_params* p, const int32_t* rows, const float* f, const double* u,
+                    const double* w, const double* lam, oracle_info* info)
+{
+    oracle_op op = {1, p->m, (int64_t)p->n * p->n, NULL, p->n, rows};
+    kkt_impl(p, &op, f, u, w, lam, info);
+}
+
+static int solve_impl(const oracle_params* p, const oracle_op* op, const float* f,
+                      const double* u0, const double* lam0,
+                      double* u_out, double* w_out, double* lam_out, double* hist, double* u_hist,
+                      oracle_info* info)
+{
+    if (!p || !f || !u_out || !info) return -1;
     if (p->n < 2 || p->m < 1 || !(p->mu > 0) || !(p->beta > 0) || !(p->tau > 0) ||
         p->max_iter < 0 || (p->init == ORACLE_INIT_GIVEN && !u0))
         return -1;
@@ -318,14 +422,14 @@ int oracle_solve(const oracle_params* p, const float* A, const float* f,
         memset(u, 0, sizeof(double) * (size_t)N);
     } else {
         for (int i = 0; i < m; ++i) fd[i] = (double)f[i];
-        oracle_At(m, N, A, fd, u);
+        op_At(op, fd, u);
     }
     if (u_hist) memcpy(u_hist, u, sizeof(double) * (size_t)N);
     oracle_dtd_eigs(n, eig);
 
     /* g_0 = A^T (A u^0 - f), eq. (line). */
-    oracle_Au(m, N, A, u, f, r);
-    oracle_At(m, N, A, r, g);
+    op_Au(op, u, f, r);
+    op_At(op, r, g);
 
     const double c = mu / (beta * tau);   /* mu/(beta tau) in eqs. (eqnorm)/(eqnorm11) */
     int k = 0, stopped = 0;
@@ -380,8 +484,8 @@ int oracle_solve(const oracle_params* p, const float* A, const float* f,
         ++k;
 
         /* g_{k+1} for the next linearisation, and the history record. */
-        oracle_Au(m, N, A, u, f, r);
-        oracle_At(m, N, A, r, g);
+        op_Au(op, u, f, r);
+        op_At(op, r, g);
         if (hist) {
             double r2 = dot(m, r, r);
             double tv = 0.0, pen = 0.0;
@@ -404,7 +508,7 @@ int oracle_solve(const oracle_params* p, const float* A, const float* f,
     }
 
     memset(info, 0, sizeof(*info));
-    oracle_kkt(p, A, f, u, w, lam, info);
+    kkt_impl(p, op, f, u, w, lam, info);
     info->iters = k;
     info->stopped_by_tol = stopped;
     info->rel_change = relchg;
@@ -415,4 +519,24 @@ int oracle_solve(const oracle_params* p, const float* A, const float* f,
     free(u); free(un); free(w); free(lam); free(d1); free(d2); free(z1); free(z2);
     free(b); free(g); free(r); free(fd); free(eig); free(re); free(im);
     return 0;
+}
+
+int oracle_solve(const oracle_params* p, const float* A, const float* f,
+                 const double* u0, const double* lam0,
+                 double* u_out, double* w_out, double* lam_out, double* hist, double* u_hist,
+                 oracle_info* info)
+{
+    if (!p || !A) return -1;
+    oracle_op op = {0, p->m, (int64_t)p->n * p->n, A, p->n, NULL};
+    return solve_impl(p, &op, f, u0, lam0, u_out, w_out, lam_out, hist, u_hist, info);
+}
+
+int oracle_solve_dct(const oracle_params* p, const int32_t* rows, const float* f,
+                     const double* u0, const double* lam0,
+                     double* u_out, double* w_out, double* lam_out, double* hist, double* u_hist,
+                     oracle_info* info)
+{
+    if (!p || !rows) return -1;
+    oracle_op op = {1, p->m, (int64_t)p->n * p->n, NULL, p->n, rows};
+    return solve_impl(p, &op, f, u0, lam0, u_out, w_out, lam_out, hist, u_hist, info);
 }

@@ -26,6 +26,8 @@
  *   C5  stop after the u-update when ||u^{k+1}-u^k|| <= tol ||u^k|| (eq. (stop));
  *       when ||u^k|| = 0 stop only if ||u^{k+1}|| = 0.
  *   C6  shrink returns 0 when ||z|| <= 1/beta (covers z = 0, the 0*(0/0)=0 rule).
+ *   C18 the partial-DCT encoder of Sec. 3.2 is a row subset of the orthonormal
+ *       2D DCT-II applied to the n x n image (C u C^T).
  *
  * Parity pins: every function here is checked in tests/ against something
  * other than itself (closed forms, explicit dense matrices, an independent
@@ -111,6 +113,20 @@ int oracle_solve(const oracle_params* p, const float* A, const float* f,
 /* Residuals of the IADM fixed point at a given (u, w, lambda) (Thm 4). */
 void oracle_kkt(const oracle_params* p, const float* A, const float* f, const double* u,
                 const double* w, const double* lam, oracle_info* info);
+
+/* Partial-DCT encoder (Sec. 3.2; reading C18): the orthonormal 2D DCT-II
+ * out = C x C^T of an n x n image (inverse: C^T x C), C[k][j] = a_k cos(pi (2j+1) k/(2n)),
+ * and A = the rows `rows` (indices k1 n + k2) of that transform. */
+void oracle_dct2(int n, int inverse, const double* x, double* out);
+void oracle_dct_Au(int n, int m, const int32_t* rows, const double* u, const float* f, double* r);
+void oracle_dct_At(int n, int m, const int32_t* rows, const double* r, double* g);
+/* oracle_solve / oracle_kkt with the partial-DCT encoder instead of a dense A. */
+int oracle_solve_dct(const oracle_params* p, const int32_t* rows, const float* f,
+                     const double* u0, const double* lam0,
+                     double* u, double* w, double* lam, double* hist, double* u_hist,
+                     oracle_info* info);
+void oracle_kkt_dct(const oracle_params* p, const int32_t* rows, const float* f, const double* u,
+                    const double* w, const double* lam, oracle_info* info);
 
 /* Number of OpenMP threads the oracle uses. */
 int oracle_num_threads(void);

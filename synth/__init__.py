@@ -329,3 +329,45 @@ def workload_uneven(count: int = 64, first_seed: int = 1, materialise: bool = Fa
         out.append(make_problem(n, ratio, s, 10, 1e3, 10.0, 1e-4, 500, 1e-3,
                                 name="uneven_%d" % s, materialise=materialise))
     return out
+
+
+# ----------------------------------------------------------------------------
+# Partial-DCT encoder inputs (Sec. 3.2): A = m rows of the orthonormal 2D DCT
+# ----------------------------------------------------------------------------
+
+def dct_rows(seed: int, n: int, m: int) -> np.ndarray:
+    """m distinct coefficient indices k1*n + k2 of the n x n DCT, chosen uniformly
+    at random (seeded), in increasing order; int32."""
+    rng = np.random.default_rng(np.random.SeedSequence([int(seed), 0xDC7]))
+    return np.sort(rng.choice(n * n, size=m, replace=False)).astype(np.int32)
+
+
+def measure_dct(rows: np.ndarray, ubar: np.ndarray, sigma: float, noise_seed: int) -> np.ndarray:
+    """f = (orthonormal 2D DCT of ubar)[rows] + sigma * eps (Sec. 3.2: Gaussian noise
+    of standard deviation sigma, absolute), eps from stream 1 of noise_seed; float32."""
+    import scipy.fft
+    X = scipy.fft.dctn(np.asarray(ubar, dtype=np.float64), norm="ortho").ravel()
+    eps = normals(noise_seed, 1, 0, rows.size).astype(np.float64)
+    return (X[rows] + sigma * eps).astype(np.float32)
+
+
+def make_dct_problem(n: int, ratio: float, seed: int, n_ellipses: int, mu: float,
+                     beta: float = 2.0 ** 6, tol: float = 5e-5, max_iter: int = 1000,
+                     sigma: float = 1e-3, name: str = "dct") -> Problem:
+    """One partial-DCT problem: a seeded phantom, m = floor(ratio n^2) DCT rows, f with
+    absolute noise sigma.  Problem.A is None; the rows are in Problem.extra['rows']."""
+    m = sampled_m(n, ratio)
+    rows = dct_rows(seed, n, m)
+    ubar = phantom(n, n_ellipses, seed)
+    f = measure_dct(rows, ubar, sigma, seed + 1_000_003)
+    return Problem(name, n, m, seed, mu, beta, tol, max_iter, sigma, ubar, None, f, sigma,
+                   extra={"rows": rows})
+
+
+def workload_dct128() -> Problem:
+    """Sec. 3.2's partial-DCT experiment: a 128 x 128 phantom (stand-in for the
+    Shepp-Logan image, 10 ellipses), 30% of the DCT coefficients (m = 4915),
+    noise of standard deviation 0.001, mu = 500 (a row of Table 1), beta = 2^6,
+    tol 5e-5 (the step tau = 1.9 of the same section is passed by the caller)."""
+    return make_dct_problem(128, 0.3, 3, 10, 500.0, 2.0 ** 6, 5e-5, 1000, 1e-3,
+                            name="dct128_m4915")
