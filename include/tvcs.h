@@ -116,6 +116,21 @@ tvcs_status tvcs_create(tvcs_handle* out, const float* A, uint64_t seed, int m, 
                         double mu, double beta, double tol, const tvcs_options* opt);
 
 /*
+ * Creates a solver whose encoder is the partial DCT of Sec. 3.2: A u =
+ * (C U C^T)[rows], the m coefficients rows[0..m) (indices k1*n + k2, distinct,
+ * any order; the measurements f follow that order) of the orthonormal 2D
+ * DCT-II of the n x n image U, C[k][j] = a_k cos(pi (2j+1) k / (2n)),
+ * a_0 = sqrt(1/n), a_k = sqrt(2/n).  No matrix is stored: each product is four
+ * dense n x n transforms in one thread-block-cluster kernel.  rows is a host
+ * array; n is 16, 32, 48, 64, 96 or 128; 1 <= m <= n*n.  opt (nullable) must
+ * keep precision TVCS_PREC_FP32 and a_mode TVCS_A_STORED.  Every other entry
+ * point works on the handle as on one with a stored A (tvcs_solve_batched
+ * solves such handles one after another).
+ */
+tvcs_status tvcs_create_partial_dct(tvcs_handle* out, const int32_t* rows, int m, int n,
+                                    double mu, double beta, double tol, const tvcs_options* opt);
+
+/*
  * Solves from the handle's initial point (opt->init) with data f (m values,
  * host or device) and writes the n*n image to u (host or device).  Runs at
  * most max_iter iterations; res (nullable) receives the summary.

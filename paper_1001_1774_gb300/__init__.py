@@ -33,7 +33,8 @@ TVCS_A_STORED, TVCS_A_REGENERATE = 0, 1
 (TVCS_STATE_U, TVCS_STATE_W, TVCS_STATE_LAMBDA, TVCS_STATE_G, TVCS_STATE_R, TVCS_STATE_RHS,
  TVCS_STATE_F) = range(7)
 
-EXPORTED = ["tvcs_default_options", "tvcs_create", "tvcs_solve", "tvcs_solve_batched",
+EXPORTED = ["tvcs_default_options", "tvcs_create", "tvcs_create_partial_dct", "tvcs_solve",
+            "tvcs_solve_batched",
             "tvcs_solve_continuation",
             "tvcs_destroy", "tvcs_last_error", "tvcs_get_tau", "tvcs_get_state",
             "tvcs_set_state", "tvcs_iterate", "tvcs_run_stage", "tvcs_time_stage", "tvcs_apply",
@@ -75,6 +76,8 @@ def _load() -> ctypes.CDLL:
     sig = {
         "tvcs_default_options": ([ctypes.POINTER(tvcs_options)], None),
         "tvcs_create": ([ctypes.POINTER(H), vp, u64, i, i, d, d, d, ctypes.POINTER(tvcs_options)], i),
+        "tvcs_create_partial_dct": ([ctypes.POINTER(H), vp, i, i, d, d, d,
+                                     ctypes.POINTER(tvcs_options)], i),
         "tvcs_solve": ([H, vp, vp, ctypes.POINTER(tvcs_result)], i),
         "tvcs_solve_batched": ([vp, i, vp, vp, vp, vp], i),
         "tvcs_solve_continuation": ([H, vp, vp, vp, i, vp], i),
@@ -164,6 +167,18 @@ def tvcs_create(A, seed: int, m: int, n: int, mu: float, beta: float, tol: float
                             float(mu), float(beta), float(tol),
                             ctypes.byref(opt) if opt is not None else None))
     return Handle(h.value, m, n)
+
+
+def tvcs_create_partial_dct(rows, n: int, mu: float, beta: float, tol: float,
+                            opt: tvcs_options | None = None) -> Handle:
+    """Partial-DCT encoder: the coefficients `rows` (indices k1 n + k2) of the
+    orthonormal 2D DCT of the n x n image."""
+    r = np.ascontiguousarray(rows, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(_lib.tvcs_create_partial_dct(ctypes.byref(h), r.ctypes.data, int(r.size), int(n),
+                                        float(mu), float(beta), float(tol),
+                                        ctypes.byref(opt) if opt is not None else None))
+    return Handle(h.value, int(r.size), n)
 
 
 def tvcs_destroy(h: Handle) -> None:

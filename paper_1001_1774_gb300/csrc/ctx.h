@@ -80,6 +80,9 @@ struct tvcs_ctx {
     tvcs_batch* batch = nullptr;
     uint64_t seed = 0;
     tvcs_regen* regen = nullptr;   // set for TVCS_A_REGENERATE
+    bool dct = false;              // partial-DCT encoder (tvcs_create_partial_dct)
+    float* dctC = nullptr;         // n x n DCT matrix
+    int *dsidx = nullptr, *dsperm = nullptr, *drowptr = nullptr;
     tvcs_uneven* uneven = nullptr; // uneven batch whose first handle is this one
 };
 

@@ -167,6 +167,28 @@ void launch_regen(const RegenProb* probs, int P, int mode, const RegenPlan& plan
 void launch_regen_reduce(const RegenProb* probs, int P, int maxN, int mode, const RegenPlan& plan,
                          const int* pre, unsigned long long cond, int set_cond, cudaStream_t s);
 
+// Products with the partial-DCT encoder (k_dct.cu): r = (C U C^T)[rows] - y and
+// g = C^T S C, one thread-block cluster.  The sampled coefficients are given in
+// increasing index order (sidx) with their positions in the caller's order
+// (sperm); rowptr[k] = first sorted entry with index >= k n (n + 1 values).
+struct DctArgs {
+    const float* C;      // n x n orthonormal DCT-II matrix, binary32
+    const float* x;      // n*n
+    const float* y;      // m, nullable
+    const int* sidx;
+    const int* sperm;
+    const int* rowptr;
+    float* r;            // m (caller's order)
+    float* g;            // n*n
+    Ctrl* ctrl;          // receives r2; MODE_ITER bookkeeping as the other product kernels
+    int mode;
+    unsigned long long cond;
+    int set_cond;
+};
+bool dct_supported(int n);
+bool dct_configure(int n);   // kernel attributes (call once per device)
+void launch_dct_products(int n, const DctArgs& a, cudaStream_t s);
+
 // Loop condition of a batch: continue while any of ctrls[0..count) runs and
 // bctrl->loops stays below bctrl->loops_max (batch.cu).
 void launch_batch_cond(const Ctrl* ctrls, int count, Ctrl* bctrl, unsigned long long cond,

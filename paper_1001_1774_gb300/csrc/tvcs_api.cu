@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <new>
 #include <set>
@@ -89,6 +90,23 @@ void products(tvcs_ctx* h, const float* x, const float* y, float* r, float* gpar
 {
     if (h->regen) {   // A regenerated in the kernel; A^T r whole in g, else in gpart (P = 1)
         regen_products(h, x, y, r, g ? g : gpart, mode, cond, set_cond, s);
+        return;
+    }
+    if (h->dct) {     // partial-DCT encoder; A^T r whole in g, else in gpart (P = 1)
+        DctArgs d{};
+        d.C = h->dctC;
+        d.x = x;
+        d.y = y;
+        d.sidx = h->dsidx;
+        d.sperm = h->dsperm;
+        d.rowptr = h->drowptr;
+        d.r = r;
+        d.g = g ? g : gpart;
+        d.ctrl = h->ctrl;
+        d.mode = mode;
+        d.cond = cond;
+        d.set_cond = set_cond;
+        launch_dct_products(h->n, d, s);
         return;
     }
     if (h->use_q) {
@@ -175,7 +193,7 @@ void free_ctx(tvcs_ctx* h)
     if (h->graph) cudaGraphDestroy(h->graph);
     void* bufs[] = {h->A, h->f, h->u, h->w, h->lam, h->g, h->r, h->rhs, h->zeroN, h->tx, h->ty,
                     h->tr, h->tg, h->spec, h->tw, h->s2, h->gpart, h->gpart2, h->r2part, h->part,
-                    h->ctrl, h->P0, h->P1, h->rscale};
+                    h->ctrl, h->P0, h->P1, h->rscale, h->dctC, h->dsidx, h->dsperm, h->drowptr};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (h->hctrl) cudaFreeHost(h->hctrl);
@@ -354,7 +372,46 @@ tvcs_status check_handle(tvcs_handle h)
     return TVCS_OK;
 }
 
-tvcs_status create_impl(tvcs_ctx* h, const float* A, uint64_t seed)
+// The partial-DCT encoder's tables: C[k][j] = a_k cos(pi (2j+1) k / (2n)) (binary64 at
+// the exactly reduced angle, then rounded), the sampled indices in increasing order
+// with their caller positions, and the first entry of each coefficient row.
+tvcs_status dct_init(tvcs_ctx* h, const int32_t* rows)
+{
+    const int n = h->n, m = h->m;
+    if (!dct_configure(n)) return fail(TVCS_ERR_UNSUPPORTED, "no partial-DCT kernel fits for n = %d", n);
+    std::vector<float> C((size_t)n * n);
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k < n; ++k) {
+        const double a = k == 0 ? sqrt(1.0 / n) : sqrt(2.0 / n);
+        for (int j = 0; j < n; ++j) {
+            const long t = ((long)(2 * j + 1) * k) % (4L * n);
+            C[(size_t)k * n + j] = (float)(a * cos(2.0 * pi * (double)t / (4.0 * n)));
+        }
+    }
+    std::vector<std::pair<int, int>> e(m);
+    for (int i = 0; i < m; ++i) e[i] = {rows[i], i};
+    std::sort(e.begin(), e.end());
+    std::vector<int> sidx(m), sperm(m), rowptr(n + 1);
+    for (int i = 0; i < m; ++i) {
+        sidx[i] = e[i].first;
+        sperm[i] = e[i].second;
+    }
+    for (int k = 0, i = 0; k <= n; ++k) {
+        while (i < m && sidx[i] < k * n) ++i;
+        rowptr[k] = i;
+    }
+    CKS(alloc((void**)&h->dctC, sizeof(float) * (size_t)n * n));
+    CKS(alloc((void**)&h->dsidx, sizeof(int) * (size_t)m));
+    CKS(alloc((void**)&h->dsperm, sizeof(int) * (size_t)m));
+    CKS(alloc((void**)&h->drowptr, sizeof(int) * (size_t)(n + 1)));
+    CK(cudaMemcpy(h->dctC, C.data(), sizeof(float) * (size_t)n * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->dsidx, sidx.data(), sizeof(int) * (size_t)m, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->dsperm, sperm.data(), sizeof(int) * (size_t)m, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->drowptr, rowptr.data(), sizeof(int) * (size_t)(n + 1), cudaMemcpyHostToDevice));
+    return TVCS_OK;
+}
+
+tvcs_status create_impl(tvcs_ctx* h, const float* A, uint64_t seed, const int32_t* dct_rows = nullptr)
 {
     CK(cudaGetDevice(&h->dev));
     CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->dev));
@@ -377,9 +434,11 @@ tvcs_status create_impl(tvcs_ctx* h, const float* A, uint64_t seed)
     const size_t m = (size_t)h->m, N = (size_t)h->N;
     const int prec = h->opt.precision;
     const bool regen = h->opt.a_mode == TVCS_A_REGENERATE;
-    h->use_q = !regen && !(prec == TVCS_PREC_FP32 && prod_supported(h->n));
-    if (regen) {
-        h->P = 1;   // the regenerating products leave A^T r whole
+    h->dct = dct_rows != nullptr;
+    const bool noA = regen || h->dct;   // no stored matrix
+    h->use_q = !noA && !(prec == TVCS_PREC_FP32 && prod_supported(h->n));
+    if (noA) {
+        h->P = 1;   // these products leave A^T r whole
     } else if (h->use_q) {
         h->P = qprod_grid_clusters(prec, h->n, h->m);
         if (h->P == 0)
@@ -392,7 +451,7 @@ tvcs_status create_impl(tvcs_ctx* h, const float* A, uint64_t seed)
         return fail(TVCS_ERR_UNSUPPORTED, "no thread-block cluster of 8 or 16 fits for n = %d", h->n);
     const size_t nparts = 2 * (size_t)((N + 255) / 256 + 1024);
     // A: binary32 for the classic path and as the source of the split storages.
-    if (!regen) CKS(alloc((void**)&h->A, sizeof(float) * m * N));
+    if (!noA) CKS(alloc((void**)&h->A, sizeof(float) * m * N));
     CKS(alloc((void**)&h->f, sizeof(float) * m));
     CKS(alloc((void**)&h->r, sizeof(float) * m));
     CKS(alloc((void**)&h->ty, sizeof(float) * m));
@@ -434,7 +493,9 @@ tvcs_status create_impl(tvcs_ctx* h, const float* A, uint64_t seed)
     CK(cudaMemcpyAsync(h->tw, tw.data(), sizeof(float2) * h->n, cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(h->s2, s2.data(), sizeof(float) * h->n, cudaMemcpyHostToDevice, h->stream));
 
-    if (regen) {
+    if (h->dct) {
+        CKS(dct_init(h, dct_rows));
+    } else if (regen) {
         CKS(sync_and_check(h, "tvcs_create"));
         CKS(regen_init(h));
     } else if (A) {
@@ -444,7 +505,7 @@ tvcs_status create_impl(tvcs_ctx* h, const float* A, uint64_t seed)
         launch_gen_gauss(h->A, h->m, (int64_t)N, seed, scale, h->stream);
     }
     CKS(sync_and_check(h, "uploading A"));
-    if (h->use_q && !regen) {
+    if (h->use_q && !noA) {
         if (prec == TVCS_PREC_FP32) {
             h->P0 = reinterpret_cast<unsigned char*>(h->A);   // the plane is A itself
             h->A = nullptr;
@@ -572,6 +633,61 @@ tvcs_status tvcs_create(tvcs_handle* out, const float* A, uint64_t seed, int m, 
     h->opt = o;
     h->seed = seed;
     tvcs_status st = create_impl(h, A, seed);
+    if (st != TVCS_OK) {
+        std::string msg = g_last_error;
+        free_ctx(h);
+        g_last_error = msg;
+        return st;
+    }
+    *out = h;
+    return TVCS_OK;
+}
+
+tvcs_status tvcs_create_partial_dct(tvcs_handle* out, const int32_t* rows, int m, int n, double mu,
+                                    double beta, double tol, const tvcs_options* opt)
+{
+    if (!out) return fail(TVCS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!rows) return fail(TVCS_ERR_INVALID_ARG, "rows is NULL");
+    if (!dct_supported(n) || !tv_supported(n))
+        return fail(TVCS_ERR_INVALID_ARG, "n = %d not supported by the partial-DCT encoder "
+                                          "(16, 32, 48, 64, 96, 128)", n);
+    const long long N = (long long)n * n;
+    if (m < 1 || m > N) return fail(TVCS_ERR_INVALID_ARG, "m = %d outside [1, n*n]", m);
+    if (!(mu > 0.0) || !isfinite(mu)) return fail(TVCS_ERR_INVALID_ARG, "mu must be > 0");
+    if (!(beta > 0.0) || !isfinite(beta)) return fail(TVCS_ERR_INVALID_ARG, "beta must be > 0");
+    if (!(tol >= 0.0) || !isfinite(tol)) return fail(TVCS_ERR_INVALID_ARG, "tol must be >= 0");
+    {
+        std::vector<int32_t> sorted(rows, rows + m);
+        std::sort(sorted.begin(), sorted.end());
+        if (sorted[0] < 0 || sorted[m - 1] >= N)
+            return fail(TVCS_ERR_INVALID_ARG, "a coefficient index lies outside [0, n*n)");
+        for (int i = 1; i < m; ++i)
+            if (sorted[i] == sorted[i - 1])
+                return fail(TVCS_ERR_INVALID_ARG, "coefficient index %d appears twice", sorted[i]);
+    }
+    tvcs_options o;
+    tvcs_default_options(&o);
+    if (opt) o = *opt;
+    if (o.algo != TVCS_ALGO_IADM && o.algo != TVCS_ALGO_FTVCS)
+        return fail(TVCS_ERR_INVALID_ARG, "unknown algo %d", o.algo);
+    if (o.init < TVCS_INIT_ATF || o.init > TVCS_INIT_GIVEN)
+        return fail(TVCS_ERR_INVALID_ARG, "unknown init %d", o.init);
+    if (o.precision != TVCS_PREC_FP32 || o.a_mode != TVCS_A_STORED)
+        return fail(TVCS_ERR_INVALID_ARG, "the partial-DCT encoder computes in binary32 and stores "
+                                          "no matrix (precision FP32, a_mode STORED)");
+    if (!isfinite(o.tau)) return fail(TVCS_ERR_INVALID_ARG, "tau must be finite");
+    if (o.max_iter <= 0) o.max_iter = 500;
+    tvcs_ctx* h = new (std::nothrow) tvcs_ctx();
+    if (!h) return fail(TVCS_ERR_OOM, "host allocation failed");
+    h->m = m;
+    h->n = n;
+    h->N = n * n;
+    h->mu = mu;
+    h->beta = beta;
+    h->tol = tol;
+    h->opt = o;
+    tvcs_status st = create_impl(h, nullptr, 0, rows);
     if (st != TVCS_OK) {
         std::string msg = g_last_error;
         free_ctx(h);

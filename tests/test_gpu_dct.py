@@ -1,0 +1,111 @@
+"""The partial-DCT encoder (Sec. 3.2, reading C18) on the GPU against the FP64
+oracle through the C ABI: products per entry within 1e-5 of the |C| |x|
+bound, solves at fixed iteration counts within 1e-5 relative image error, the
+Sec. 3.2 workload to its tolerance within 1e-4."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tv(cuda_device):
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1001_1774_gb300 as tv
+    return tv
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def dct_handle(tv, rows, n, mu=500.0, beta=64.0, tau=1.9, max_iter=50, tol=0.0, algo=0):
+    opt = tv.tvcs_default_options()
+    opt.tau = tau
+    opt.max_iter = max_iter
+    opt.algo = algo
+    return tv.tvcs_create_partial_dct(rows, n, mu, beta, tol, opt)
+
+
+@pytest.mark.parametrize("n,ratio", [(16, 0.3), (32, 0.3), (48, 0.2), (64, 0.5), (96, 0.1),
+                                     (128, 0.3)])
+def test_dct_products_parity(tv, n, ratio):
+    m = synth.sampled_m(n, ratio)
+    rows = synth.dct_rows(n + 1, n, m)
+    rng = np.random.default_rng(n)
+    perm = rng.permutation(m)            # the caller's order need not be increasing
+    rows_c = rows[perm]
+    x = rng.standard_normal(n * n).astype(np.float32)
+    y = rng.standard_normal(m).astype(np.float32)
+    h = dct_handle(tv, rows_c, n)
+    r = np.empty(m, np.float32)
+    g = np.empty(n * n, np.float32)
+    tv.tvcs_apply(h, x, y, r, g)
+    rr = oracle.dct_Au(n, rows_c, x, y)
+    # |C| has entries <= sqrt(2/n): |(C X C^T)_k| <= (2/n) sum |x| bounds each term's scale
+    scale_r = (2.0 / n) * np.sum(np.abs(x)) + np.abs(y)
+    assert np.all(np.abs(r - rr) <= 1e-5 * scale_r)
+    gr = oracle.dct_At(n, rows_c, r.astype(np.float64))
+    scale_g = (2.0 / n) * np.sum(np.abs(r))
+    assert np.all(np.abs(g - gr) <= 1e-5 * scale_g)
+    assert tv.tvcs_get_tau(h) == pytest.approx(1.9)
+    tv.tvcs_destroy(h)
+
+
+def test_dct_power_iteration_gives_unit_lambda_max(tv):
+    n, m = 32, 300
+    rows = synth.dct_rows(3, n, m)
+    opt = tv.tvcs_default_options()
+    h = tv.tvcs_create_partial_dct(rows, n, 500.0, 64.0, 0.0, opt)
+    assert tv.tvcs_get_tau(h) == pytest.approx(1.0 / 1.01, rel=1e-5)   # A A^T = I
+    tv.tvcs_destroy(h)
+
+
+@pytest.mark.parametrize("algo", [0, 1])
+def test_dct_solve_fixed_iterations(tv, algo):
+    P = synth.make_dct_problem(32, 0.3, 13, 6, 500.0)
+    rows = P.extra["rows"]
+    h = dct_handle(tv, rows, 32, mu=P.mu, beta=P.beta, tau=1.9, max_iter=60, algo=algo)
+    u = np.empty(P.N, np.float32)
+    res = tv.tvcs_solve(h, P.f, u)
+    ref = oracle.solve_dct(rows, P.f, 32, P.mu, P.beta, 1.9, max_iter=60, algo=algo)
+    assert res.iters == 60
+    assert rel(u, ref.u) <= 1e-5
+    assert abs(res.objective - ref.info["objective"]) <= 1e-5 * ref.info["objective"]
+    tv.tvcs_destroy(h)
+
+
+def test_dct_rejects_bad_rows(tv):
+    opt = tv.tvcs_default_options()
+    with pytest.raises(tv.TvcsError):
+        tv.tvcs_create_partial_dct(np.array([3, 5, 3], np.int32), 16, 1.0, 1.0, 0.0, opt)
+    with pytest.raises(tv.TvcsError):
+        tv.tvcs_create_partial_dct(np.array([0, 256], np.int32), 16, 1.0, 1.0, 0.0, opt)
+    with pytest.raises(tv.TvcsError):
+        tv.tvcs_create_partial_dct(np.array([0, 1], np.int32), 192, 1.0, 1.0, 0.0, opt)
+
+
+def test_dct_workload_128_to_tolerance(tv):
+    # Sec. 3.2: 128 x 128, 30% of the DCT coefficients, sigma 0.001, tau 1.9, beta 2^6,
+    # stop at 5e-5; mu = 500 (a row of Table 1)
+    P = synth.workload_dct128()
+    rows = P.extra["rows"]
+    h = dct_handle(tv, rows, 128, mu=P.mu, beta=P.beta, tau=1.9, max_iter=P.max_iter, tol=P.tol)
+    u = torch.empty(P.N, dtype=torch.float32, device="cuda")
+    res = tv.tvcs_solve(h, torch.from_numpy(P.f).cuda(), u)
+    assert res.status == tv.TVCS_OK and res.stopped_by_tol == 1
+    full = oracle.solve_dct(rows, P.f, 128, P.mu, P.beta, 1.9, tol=P.tol, max_iter=P.max_iter)
+    assert abs(res.iters - full.info["iters"]) <= max(2, full.info["iters"] // 50)
+    same = oracle.solve_dct(rows, P.f, 128, P.mu, P.beta, 1.9, max_iter=res.iters)
+    assert rel(u.cpu().numpy(), same.u) <= 1e-4
+    assert abs(res.objective - same.info["objective"]) <= 1e-6 * same.info["objective"]
+    # the reconstruction error against the phantom is small at 30% sampling
+    assert rel(u.cpu().numpy(), P.ubar) < 0.2
+    tv.tvcs_destroy(h)
