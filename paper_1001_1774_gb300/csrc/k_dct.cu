@@ -6,15 +6,18 @@
 // image (the two matrix-vector products of eq. (line) for this encoder).
 //
 // One thread-block cluster of CL blocks; block q owns image rows (and
-// coefficient rows) [q R, (q+1) R), R = n / CL.  Per block:
+// coefficient rows) [q R, (q+1) R), R = n / CL (a multiple of 4).  Per block:
 //   1  Y = U C^T for its rows of u                       (row transform)
 //   2  Z = C Y_all for its coefficient rows, Y_all gathered from the cluster
 //   3  r_i = Z[rows_i] - f_i for its sampled coefficients, S = scatter(r)
 //   4  T = C^T S_all for its image rows, S_all gathered    (column transform back)
 //   5  G = T C for its rows                                (row transform back)
-// C lives in shared memory once per block with rows padded to n + 4 floats, so
-// that a warp reading a column of C four entries at a time (phase 1) and a
-// warp reading a row (phases 2-5) both hit distinct banks.
+// Every transform has the form out[i][c] = sum_j A[j][i] B[j][c] over the
+// block's R rows i: A is C, C^T or a transposed band (u, T) and B is C, C^T or
+// a gathered n x n matrix, all in shared memory.  A thread accumulates a 4 x 4
+// tile over one of KS slices of j (one float4 of A, broadcast across the warp,
+// and one of B per 16 FMAs); the KS partial tiles are summed afterwards.  C and
+// C^T are constants and are copied in before waiting on the preceding kernel.
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -31,41 +34,91 @@ constexpr int DCT_THREADS = 256;
 template <int NN, int CL>
 struct DctShape {
     static constexpr int R = NN / CL;
-    static constexpr int LD = NN + 4;              // padded row stride of C
-    static constexpr size_t O_C = 0;               // NN x LD
-    static constexpr size_t O_ALL = O_C + (size_t)NN * LD * 4;    // NN x NN gathered rows
-    static constexpr size_t O_U = O_ALL + (size_t)NN * NN * 4;    // R x NN each below
-    static constexpr size_t O_Y = O_U + (size_t)R * NN * 4;       // cluster-visible
-    static constexpr size_t O_S = O_Y + (size_t)R * NN * 4;       // cluster-visible
-    static constexpr size_t O_T = O_S + (size_t)R * NN * 4;
-    static constexpr size_t O_RED = O_T + (size_t)R * NN * 4;     // doubles
-    static constexpr size_t SMEM = O_RED + (32 + 2 * 16) * 8;
-    static_assert(NN % CL == 0 && NN % 4 == 0, "whole rows per block, float4 rows");
+    static constexpr int RG = R / 4, CG = NN / 4, TILES = RG * CG;
+    static constexpr int KS0 = DCT_THREADS / TILES;
+    static constexpr int KS = KS0 < CG ? KS0 : CG;    // slices of the summation index
+    static constexpr int JL = (NN + KS - 1) / KS;     // slice length
+    static constexpr size_t NSQ = (size_t)NN * NN * 4;
+    static constexpr size_t BAND = (size_t)R * NN * 4;
+    static constexpr size_t O_C = 0;                  // C, n x n
+    static constexpr size_t O_CT = O_C + NSQ;         // C^T, n x n
+    static constexpr size_t O_ALL = O_CT + NSQ;       // gathered n x n (Y_all, then S_all)
+    static constexpr size_t O_UT = O_ALL + NSQ;       // u band transposed (n x R), later T^T
+    static constexpr size_t O_Y = O_UT + BAND;        // cluster-visible
+    static constexpr size_t O_S = O_Y + BAND;         // cluster-visible
+    static constexpr size_t O_P = O_S + BAND;         // KS partial bands
+    static constexpr size_t O_RED = O_P + (size_t)KS * BAND;   // doubles
+    static constexpr size_t SMEM = O_RED + (32 + 16) * 8;
+    static_assert(NN % CL == 0 && R % 4 == 0 && CL <= 16, "whole 4-row groups per block");
+    static_assert(KS >= 1 && TILES * KS <= DCT_THREADS, "one tile slice per thread at most");
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
-// out[i][c] = sum_j left(i, j) right[j][c], i < R, c < NN; right rows at stride NN
-// (float4), left(i, j) a warp-uniform scalar per (i, j).  Each thread: one row i,
-// four columns.
-template <int NN, int R, typename Left>
-__device__ __forceinline__ void left_times_right(Left left, const float* right, float* out, int tid,
-                                                 int nthr)
+// P[ks][i][c] = sum over j in slice ks of A[j * lda + i] B[j * NN + c], i < R,
+// c < NN; one 4 x 4 tile per thread.
+template <int NN, int CL>
+__device__ __forceinline__ void tile_partials(const float* A, int lda, const float* B, float* P,
+                                              int tid)
 {
-    constexpr int C4 = NN / 4;
-    for (int o = tid; o < R * C4; o += nthr) {
-        const int i = o / C4, c4 = o - i * C4;
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4* rb = reinterpret_cast<const float4*>(right) + c4;
+    using S = DctShape<NN, CL>;
+    constexpr int CG = S::CG, RG = S::RG, R = S::R;
+    if (tid >= S::TILES * S::KS) return;
+    const int cg = tid % CG, rest = tid / CG, rg = rest % RG, ks = rest / RG;
+    const int j0 = ks * S::JL, j1 = min(NN, j0 + S::JL);
+    const float* ap = A + 4 * rg;
+    const float* bp = B + 4 * cg;
+    float acc[4][4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[t][v] = 0.f;
 #pragma unroll 4
-        for (int j = 0; j < NN; ++j) {
-            const float a = left(i, j);
-            const float4 b = rb[(size_t)j * C4];
-            acc.x = fmaf(a, b.x, acc.x);
-            acc.y = fmaf(a, b.y, acc.y);
-            acc.z = fmaf(a, b.z, acc.z);
-            acc.w = fmaf(a, b.w, acc.w);
+    for (int j = j0; j < j1; ++j) {
+        const float4 a = *reinterpret_cast<const float4*>(ap + (size_t)j * lda);
+        const float4 b = *reinterpret_cast<const float4*>(bp + (size_t)j * NN);
+        const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            acc[t][0] = fmaf(av[t], b.x, acc[t][0]);
+            acc[t][1] = fmaf(av[t], b.y, acc[t][1]);
+            acc[t][2] = fmaf(av[t], b.z, acc[t][2]);
+            acc[t][3] = fmaf(av[t], b.w, acc[t][3]);
         }
-        reinterpret_cast<float4*>(out)[o] = acc;
+    }
+    float* pp = P + ((size_t)ks * R + 4 * rg) * NN + 4 * cg;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+        *reinterpret_cast<float4*>(pp + (size_t)t * NN) =
+            make_float4(acc[t][0], acc[t][1], acc[t][2], acc[t][3]);
+}
+
+// Sum of the KS partial bands at float4 position o (row o / (NN/4)).
+template <int NN, int CL>
+__device__ __forceinline__ float4 partial_sum4(const float* P, int o)
+{
+    using S = DctShape<NN, CL>;
+    float4 t = reinterpret_cast<const float4*>(P)[o];
+#pragma unroll
+    for (int ks = 1; ks < S::KS; ++ks) {
+        const float4 v = reinterpret_cast<const float4*>(P + (size_t)ks * S::R * NN)[o];
+        t.x += v.x;
+        t.y += v.y;
+        t.z += v.z;
+        t.w += v.w;
+    }
+    return t;
+}
+
+// dst (n x n, this block's shared memory) = the R-row bands src of all blocks
+template <int NN, int CL>
+__device__ __forceinline__ void gather_bands(cg::cluster_group& cluster, float* src, float* dst,
+                                             int tid)
+{
+    constexpr int R = DctShape<NN, CL>::R, CPR = NN / 4;
+    for (int i = tid; i < NN * CPR; i += DCT_THREADS) {
+        const int row = i / CPR, c4 = i - row * CPR;
+        const float4* p = reinterpret_cast<const float4*>(cluster.map_shared_rank(src, row / R));
+        reinterpret_cast<float4*>(dst)[i] = p[(row % R) * CPR + c4];
     }
 }
 
@@ -80,21 +133,25 @@ k_dct_products(const float* __restrict__ Cg, const float* __restrict__ x,
                cudaGraphConditionalHandle cond, int set_cond)
 {
     using S = DctShape<NN, CL>;
-    constexpr int R = S::R, LD = S::LD;
+    constexpr int R = S::R, C4 = NN / 4;
     extern __shared__ __align__(16) unsigned char smem[];
     float* sC = reinterpret_cast<float*>(smem + S::O_C);
+    float* sCt = reinterpret_cast<float*>(smem + S::O_CT);
     float* sAll = reinterpret_cast<float*>(smem + S::O_ALL);
-    float* sU = reinterpret_cast<float*>(smem + S::O_U);
+    float* sUt = reinterpret_cast<float*>(smem + S::O_UT);
     float* sY = reinterpret_cast<float*>(smem + S::O_Y);
     float* sS = reinterpret_cast<float*>(smem + S::O_S);
-    float* sT = reinterpret_cast<float*>(smem + S::O_T);
+    float* sP = reinterpret_cast<float*>(smem + S::O_P);
     double* red = reinterpret_cast<double*>(smem + S::O_RED);   // [32]
     double* cred = red + 32;                                    // [CL] cluster partials
 
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int tid = threadIdx.x;
     const int r0 = rank * R;
+
+    // C and C^T (2 n^2 floats, constants) while the preceding kernel finishes
+    for (int i = tid; i < 2 * NN * C4; i += DCT_THREADS) cp_async16(sC + 4 * i, Cg + 4 * i);
 
     pdl_wait();
     if (mode == MODE_ITER) {
@@ -110,60 +167,50 @@ k_dct_products(const float* __restrict__ Cg, const float* __restrict__ x,
                 cudaGraphSetConditional(cond, (unsigned)cont);
             }
         }
-        if (skip) return;   // uniform across the cluster
+        if (skip) {   // uniform across the cluster; leave no copy in flight
+            cp_async_wait_all();
+            return;
+        }
     } else {
         pdl_release();
     }
 
-    // C (padded rows) and this block's rows of u
-    constexpr int CPR = NN / 4;
-    for (int i = tid; i < NN * CPR; i += nthr) {
-        const int k = i / CPR, c4 = i - k * CPR;
-        cp_async16(sC + k * LD + 4 * c4, Cg + (size_t)k * NN + 4 * c4);
+    // this block's rows of u, transposed: sUt[c][i] = u[r0 + i][c]
+    for (int i = tid; i < R * C4; i += DCT_THREADS) {
+        const int row = i / C4, c4 = i - row * C4;
+        const float4 v = reinterpret_cast<const float4*>(x + (size_t)(r0 + row) * NN)[c4];
+        sUt[(4 * c4 + 0) * R + row] = v.x;
+        sUt[(4 * c4 + 1) * R + row] = v.y;
+        sUt[(4 * c4 + 2) * R + row] = v.z;
+        sUt[(4 * c4 + 3) * R + row] = v.w;
     }
-    for (int i = tid; i < R * CPR; i += nthr) cp_async16(sU + 4 * i, x + (size_t)r0 * NN + 4 * i);
     cp_async_wait_all();
     __syncthreads();
 
-    // 1: Y[i][k] = sum_c U[i][c] C[k][c]; each thread one k, several rows, C read
-    //    down a column four entries at a time
-    for (int o = tid; o < R * NN; o += nthr) {
-        const int i = o / NN, k = o - i * NN;
-        const float4* cr = reinterpret_cast<const float4*>(sC + k * LD);
-        const float4* ur = reinterpret_cast<const float4*>(sU + i * NN);
-        float acc = 0.f;
-#pragma unroll 4
-        for (int c4 = 0; c4 < CPR; ++c4) {
-            const float4 a = ur[c4], b = cr[c4];
-            acc = fmaf(a.x, b.x, acc);
-            acc = fmaf(a.y, b.y, acc);
-            acc = fmaf(a.z, b.z, acc);
-            acc = fmaf(a.w, b.w, acc);
-        }
-        sY[o] = acc;
-    }
+    // 1: Y[i][k] = sum_c U[i][c] C[k][c] = sum_c Ut[c][i] Ct[c][k]
+    tile_partials<NN, CL>(sUt, R, sCt, sP, tid);
+    __syncthreads();
+    for (int o = tid; o < R * C4; o += DCT_THREADS)
+        reinterpret_cast<float4*>(sY)[o] = partial_sum4<NN, CL>(sP, o);
     cluster.sync();   // every block's rows of Y are complete
 
-    // 2: Z = C Y_all for coefficient rows r0 .. r0+R-1
-    for (int i = tid; i < NN * CPR; i += nthr) {
-        const int row = i / CPR, c4 = i - row * CPR;
-        const float4* src = reinterpret_cast<const float4*>(cluster.map_shared_rank(sY, row / R));
-        reinterpret_cast<float4*>(sAll)[i] = src[(row % R) * CPR + c4];
-    }
+    // 2: Z[i][c] = sum_k C[r0+i][k] Y[k][c] = sum_k Ct[k][r0+i] Y_all[k][c], left as partials
+    gather_bands<NN, CL>(cluster, sY, sAll, tid);
     __syncthreads();
-    left_times_right<NN, R>([&](int i, int j) { return sC[(r0 + i) * LD + j]; }, sAll, sT, tid,
-                            nthr);   // sT holds Z for now
+    tile_partials<NN, CL>(sCt + r0, NN, sAll, sP, tid);
+    for (int i = tid; i < R * NN; i += DCT_THREADS) sS[i] = 0.f;
     __syncthreads();
 
     // 3: residuals of this block's sampled coefficients, S = scatter(r)
-    for (int i = tid; i < R * NN; i += nthr) sS[i] = 0.f;
-    __syncthreads();
     double r2 = 0.0;
     const int e0 = rowptr[r0], e1 = rowptr[r0 + R];
-    for (int e = e0 + tid; e < e1; e += nthr) {
+    for (int e = e0 + tid; e < e1; e += DCT_THREADS) {
         const int idx = sidx[e] - r0 * NN;   // local position in the block's rows
         const int q = sperm[e];              // caller's order of the measurement
-        const float rv = y ? sT[idx] - y[q] : sT[idx];
+        float z = sP[idx];
+#pragma unroll
+        for (int ks = 1; ks < S::KS; ++ks) z += sP[(size_t)ks * R * NN + idx];
+        const float rv = y ? z - y[q] : z;
         r[q] = rv;
         sS[idx] = rv;
         r2 += (double)rv * (double)rv;
@@ -175,34 +222,26 @@ k_dct_products(const float* __restrict__ Cg, const float* __restrict__ x,
     }
     cluster.sync();   // every block's rows of S (and its ||r||^2 partial) are complete
 
-    // 4: T = C^T S_all for image rows r0 .. r0+R-1
-    for (int i = tid; i < NN * CPR; i += nthr) {
-        const int row = i / CPR, c4 = i - row * CPR;
-        const float4* src = reinterpret_cast<const float4*>(cluster.map_shared_rank(sS, row / R));
-        reinterpret_cast<float4*>(sAll)[i] = src[(row % R) * CPR + c4];
-    }
+    // 4: T[i][c] = sum_k C[k][r0+i] S_all[k][c]; stored transposed into sUt
+    gather_bands<NN, CL>(cluster, sS, sAll, tid);
     __syncthreads();
-    left_times_right<NN, R>([&](int i, int j) { return sC[j * LD + r0 + i]; }, sAll, sT, tid, nthr);
+    tile_partials<NN, CL>(sC + r0, NN, sAll, sP, tid);
+    __syncthreads();
+    for (int o = tid; o < R * C4; o += DCT_THREADS) {
+        const int row = o / C4, c4 = o - row * C4;
+        const float4 t = partial_sum4<NN, CL>(sP, o);
+        sUt[(4 * c4 + 0) * R + row] = t.x;
+        sUt[(4 * c4 + 1) * R + row] = t.y;
+        sUt[(4 * c4 + 2) * R + row] = t.z;
+        sUt[(4 * c4 + 3) * R + row] = t.w;
+    }
     __syncthreads();
 
-    // 5: G = T C for image rows r0 .. r0+R-1 (C's rows read at the padded stride)
-    {
-        constexpr int C4 = NN / 4;
-        for (int o = tid; o < R * C4; o += nthr) {
-            const int i = o / C4, c4 = o - i * C4;
-            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 4
-            for (int j = 0; j < NN; ++j) {
-                const float a = sT[i * NN + j];
-                const float4 b = reinterpret_cast<const float4*>(sC + j * LD)[c4];
-                acc.x = fmaf(a, b.x, acc.x);
-                acc.y = fmaf(a, b.y, acc.y);
-                acc.z = fmaf(a, b.z, acc.z);
-                acc.w = fmaf(a, b.w, acc.w);
-            }
-            reinterpret_cast<float4*>(g + (size_t)r0 * NN)[o] = acc;
-        }
-    }
+    // 5: G[i][c] = sum_j T[i][j] C[j][c] = sum_j Tt[j][i] C[j][c]
+    tile_partials<NN, CL>(sUt, R, sC, sP, tid);
+    __syncthreads();
+    for (int o = tid; o < R * C4; o += DCT_THREADS)
+        reinterpret_cast<float4*>(g + (size_t)r0 * NN)[o] = partial_sum4<NN, CL>(sP, o);
     if (rank == 0 && tid == 0) {
         double t = 0.0;
         for (int k = 0; k < CL; ++k) t += cred[k];
@@ -212,9 +251,9 @@ k_dct_products(const float* __restrict__ Cg, const float* __restrict__ x,
 }
 
 // ---------------------------------------------------------------------------
-// Host side.  Cluster of 16 blocks (8 for n = 16).
+// Host side.  Clusters of up to 16 blocks with 4 or 8 rows each.
 // ---------------------------------------------------------------------------
-#define TVCS_DCT_TABLE(X) X(16, 8) X(32, 16) X(48, 16) X(64, 16) X(96, 16) X(128, 16)
+#define TVCS_DCT_TABLE(X) X(16, 4) X(32, 8) X(48, 12) X(64, 16) X(96, 12) X(128, 16)
 
 template <int NN, int CL>
 static bool dct_configure_t()
@@ -225,6 +264,23 @@ static bool dct_configure_t()
         (CL > 8 && cudaFuncSetAttribute(k_dct_products<NN, CL>,
                                         cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
                        cudaSuccess)) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CL, 1, 1);
+    cfg.blockDim = dim3(DCT_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = S::SMEM;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, k_dct_products<NN, CL>, &cfg) != cudaSuccess ||
+        clusters < 1) {
         cudaGetLastError();
         return false;
     }
@@ -257,13 +313,15 @@ static void launch_dct_t(const DctArgs& a, cudaStream_t s)
     cfg.blockDim = dim3(DCT_THREADS, 1, 1);
     cfg.dynamicSmemBytes = DctShape<NN, CL>::SMEM;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = CL;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = a.pdl ? 2 : 1;
     cudaLaunchKernelEx(&cfg, k_dct_products<NN, CL>, a.C, a.x, a.y, a.sidx, a.sperm, a.rowptr, a.r,
                        a.g, a.ctrl, a.mode, (cudaGraphConditionalHandle)a.cond, a.set_cond);
 }

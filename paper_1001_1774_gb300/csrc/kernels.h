@@ -172,7 +172,7 @@ void launch_regen_reduce(const RegenProb* probs, int P, int maxN, int mode, cons
 // increasing index order (sidx) with their positions in the caller's order
 // (sperm); rowptr[k] = first sorted entry with index >= k n (n + 1 values).
 struct DctArgs {
-    const float* C;      // n x n orthonormal DCT-II matrix, binary32
+    const float* C;      // n x n orthonormal DCT-II matrix, then its transpose, binary32
     const float* x;      // n*n
     const float* y;      // m, nullable
     const int* sidx;
@@ -184,6 +184,7 @@ struct DctArgs {
     int mode;
     unsigned long long cond;
     int set_cond;
+    int pdl;             // launched as a programmatic dependent of the preceding kernel
 };
 bool dct_supported(int n);
 bool dct_configure(int n);   // kernel attributes (call once per device)

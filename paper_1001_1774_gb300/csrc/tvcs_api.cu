@@ -106,6 +106,7 @@ void products(tvcs_ctx* h, const float* x, const float* y, float* r, float* gpar
         d.mode = mode;
         d.cond = cond;
         d.set_cond = set_cond;
+        d.pdl = pdl;
         launch_dct_products(h->n, d, s);
         return;
     }
@@ -379,13 +380,15 @@ tvcs_status dct_init(tvcs_ctx* h, const int32_t* rows)
 {
     const int n = h->n, m = h->m;
     if (!dct_configure(n)) return fail(TVCS_ERR_UNSUPPORTED, "no partial-DCT kernel fits for n = %d", n);
-    std::vector<float> C((size_t)n * n);
+    std::vector<float> C(2 * (size_t)n * n);   // C, then C^T
     const double pi = 3.14159265358979323846;
     for (int k = 0; k < n; ++k) {
         const double a = k == 0 ? sqrt(1.0 / n) : sqrt(2.0 / n);
         for (int j = 0; j < n; ++j) {
             const long t = ((long)(2 * j + 1) * k) % (4L * n);
-            C[(size_t)k * n + j] = (float)(a * cos(2.0 * pi * (double)t / (4.0 * n)));
+            const float c = (float)(a * cos(2.0 * pi * (double)t / (4.0 * n)));
+            C[(size_t)k * n + j] = c;
+            C[(size_t)n * n + (size_t)j * n + k] = c;
         }
     }
     std::vector<std::pair<int, int>> e(m);
@@ -400,11 +403,11 @@ tvcs_status dct_init(tvcs_ctx* h, const int32_t* rows)
         while (i < m && sidx[i] < k * n) ++i;
         rowptr[k] = i;
     }
-    CKS(alloc((void**)&h->dctC, sizeof(float) * (size_t)n * n));
+    CKS(alloc((void**)&h->dctC, 2 * sizeof(float) * (size_t)n * n));
     CKS(alloc((void**)&h->dsidx, sizeof(int) * (size_t)m));
     CKS(alloc((void**)&h->dsperm, sizeof(int) * (size_t)m));
     CKS(alloc((void**)&h->drowptr, sizeof(int) * (size_t)(n + 1)));
-    CK(cudaMemcpy(h->dctC, C.data(), sizeof(float) * (size_t)n * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->dctC, C.data(), 2 * sizeof(float) * (size_t)n * n, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(h->dsidx, sidx.data(), sizeof(int) * (size_t)m, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(h->dsperm, sperm.data(), sizeof(int) * (size_t)m, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(h->drowptr, rowptr.data(), sizeof(int) * (size_t)(n + 1), cudaMemcpyHostToDevice));
