@@ -150,6 +150,18 @@ __device__ __forceinline__ void pdl_wait()
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// The two halves of a cluster barrier, executed by every thread of the cluster:
+// writes before arrive (shared, distributed shared, global) are visible after wait.
+__device__ __forceinline__ void cluster_arrive()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void cluster_wait()
+{
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void pdl_release()
 {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");

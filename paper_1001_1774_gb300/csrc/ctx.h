@@ -81,7 +81,7 @@ struct tvcs_ctx {
     uint64_t seed = 0;
     tvcs_regen* regen = nullptr;   // set for TVCS_A_REGENERATE
     bool dct = false;              // partial-DCT encoder (tvcs_create_partial_dct)
-    float* dctC = nullptr;         // n x n DCT matrix
+    float* dctC = nullptr;         // n x n DCT matrix, its transpose, 2 n x n scratch
     int *dsidx = nullptr, *dsperm = nullptr, *drowptr = nullptr;
     tvcs_uneven* uneven = nullptr; // uneven batch whose first handle is this one
 };

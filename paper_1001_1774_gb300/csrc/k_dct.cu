@@ -18,6 +18,9 @@
 // tile over one of KS slices of j (one float4 of A, broadcast across the warp,
 // and one of B per 16 FMAs); the KS partial tiles are summed afterwards.  C and
 // C^T are constants and are copied in before waiting on the preceding kernel.
+// The bands of Y and S are exchanged through global scratch (L2): each block
+// stores its band, and after a cluster barrier copies the whole matrix in,
+// which moves data faster than loads from the peers' shared memory.
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -44,8 +47,7 @@ struct DctShape {
     static constexpr size_t O_CT = O_C + NSQ;         // C^T, n x n
     static constexpr size_t O_ALL = O_CT + NSQ;       // gathered n x n (Y_all, then S_all)
     static constexpr size_t O_UT = O_ALL + NSQ;       // u band transposed (n x R), later T^T
-    static constexpr size_t O_Y = O_UT + BAND;        // cluster-visible
-    static constexpr size_t O_S = O_Y + BAND;         // cluster-visible
+    static constexpr size_t O_S = O_UT + BAND;        // S band
     static constexpr size_t O_P = O_S + BAND;         // KS partial bands
     static constexpr size_t O_RED = O_P + (size_t)KS * BAND;   // doubles
     static constexpr size_t SMEM = O_RED + (32 + 16) * 8;
@@ -109,16 +111,32 @@ __device__ __forceinline__ float4 partial_sum4(const float* P, int o)
     return t;
 }
 
-// dst (n x n, this block's shared memory) = the R-row bands src of all blocks
-template <int NN, int CL>
-__device__ __forceinline__ void gather_bands(cg::cluster_group& cluster, float* src, float* dst,
-                                             int tid)
+// dst (n x n, shared memory) = src (n x n, global), asynchronous 16-byte copies
+// that bypass L1 (the bands were written by other blocks in this launch).
+template <int NN>
+__device__ __forceinline__ void copy_matrix_async(const float* src, float* dst, int tid)
 {
-    constexpr int R = DctShape<NN, CL>::R, CPR = NN / 4;
-    for (int i = tid; i < NN * CPR; i += DCT_THREADS) {
-        const int row = i / CPR, c4 = i - row * CPR;
-        const float4* p = reinterpret_cast<const float4*>(cluster.map_shared_rank(src, row / R));
-        reinterpret_cast<float4*>(dst)[i] = p[(row % R) * CPR + c4];
+    for (int i = tid; i < NN * NN / 4; i += DCT_THREADS) cp_async16(dst + 4 * i, src + 4 * i);
+}
+
+// dst[c * R + 4 rg + t] = sum over slices of P[ks][4 rg + t][c]: the summed
+// band stored transposed (n x R), one column and four rows per thread.
+template <int NN, int CL>
+__device__ __forceinline__ void partial_sum_transposed(const float* P, float* dst, int tid)
+{
+    using S = DctShape<NN, CL>;
+    constexpr int R = S::R;
+    for (int o = tid; o < NN * S::RG; o += DCT_THREADS) {
+        const int c = o % NN, rg = o / NN;
+        float t[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float v = P[(size_t)(4 * rg + k) * NN + c];
+#pragma unroll
+            for (int ks = 1; ks < S::KS; ++ks) v += P[((size_t)ks * R + 4 * rg + k) * NN + c];
+            t[k] = v;
+        }
+        *reinterpret_cast<float4*>(dst + (size_t)c * R + 4 * rg) = make_float4(t[0], t[1], t[2], t[3]);
     }
 }
 
@@ -129,8 +147,8 @@ __global__ void __launch_bounds__(DCT_THREADS, 1)
 k_dct_products(const float* __restrict__ Cg, const float* __restrict__ x,
                const float* __restrict__ y, const int* __restrict__ sidx,
                const int* __restrict__ sperm, const int* __restrict__ rowptr,
-               float* __restrict__ r, float* __restrict__ g, Ctrl* __restrict__ ctrl, int mode,
-               cudaGraphConditionalHandle cond, int set_cond)
+               float* __restrict__ r, float* __restrict__ g, float* __restrict__ scratch,
+               Ctrl* __restrict__ ctrl, int mode, cudaGraphConditionalHandle cond, int set_cond)
 {
     using S = DctShape<NN, CL>;
     constexpr int R = S::R, C4 = NN / 4;
@@ -139,7 +157,6 @@ k_dct_products(const float* __restrict__ Cg, const float* __restrict__ x,
     float* sCt = reinterpret_cast<float*>(smem + S::O_CT);
     float* sAll = reinterpret_cast<float*>(smem + S::O_ALL);
     float* sUt = reinterpret_cast<float*>(smem + S::O_UT);
-    float* sY = reinterpret_cast<float*>(smem + S::O_Y);
     float* sS = reinterpret_cast<float*>(smem + S::O_S);
     float* sP = reinterpret_cast<float*>(smem + S::O_P);
     double* red = reinterpret_cast<double*>(smem + S::O_RED);   // [32]
@@ -147,6 +164,8 @@ k_dct_products(const float* __restrict__ Cg, const float* __restrict__ x,
 
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
+    float* Yg = scratch;                    // n x n, bands of Y
+    float* Sg = scratch + (size_t)NN * NN;  // n x n, bands of S
     const int tid = threadIdx.x;
     const int r0 = rank * R;
 
@@ -176,13 +195,11 @@ k_dct_products(const float* __restrict__ Cg, const float* __restrict__ x,
     }
 
     // this block's rows of u, transposed: sUt[c][i] = u[r0 + i][c]
-    for (int i = tid; i < R * C4; i += DCT_THREADS) {
-        const int row = i / C4, c4 = i - row * C4;
-        const float4 v = reinterpret_cast<const float4*>(x + (size_t)(r0 + row) * NN)[c4];
-        sUt[(4 * c4 + 0) * R + row] = v.x;
-        sUt[(4 * c4 + 1) * R + row] = v.y;
-        sUt[(4 * c4 + 2) * R + row] = v.z;
-        sUt[(4 * c4 + 3) * R + row] = v.w;
+    for (int o = tid; o < NN * S::RG; o += DCT_THREADS) {
+        const int c = o % NN, rg = o / NN;
+        const float* xr = x + (size_t)(r0 + 4 * rg) * NN + c;
+        *reinterpret_cast<float4*>(sUt + (size_t)c * R + 4 * rg) =
+            make_float4(xr[0], xr[NN], xr[2 * NN], xr[3 * NN]);
     }
     cp_async_wait_all();
     __syncthreads();
@@ -191,14 +208,16 @@ k_dct_products(const float* __restrict__ Cg, const float* __restrict__ x,
     tile_partials<NN, CL>(sUt, R, sCt, sP, tid);
     __syncthreads();
     for (int o = tid; o < R * C4; o += DCT_THREADS)
-        reinterpret_cast<float4*>(sY)[o] = partial_sum4<NN, CL>(sP, o);
-    cluster.sync();   // every block's rows of Y are complete
+        reinterpret_cast<float4*>(Yg + (size_t)r0 * NN)[o] = partial_sum4<NN, CL>(sP, o);
+    cluster_arrive();
+    for (int i = tid; i < R * NN; i += DCT_THREADS) sS[i] = 0.f;
+    cluster_wait();   // every block's rows of Y are in Yg
 
     // 2: Z[i][c] = sum_k C[r0+i][k] Y[k][c] = sum_k Ct[k][r0+i] Y_all[k][c], left as partials
-    gather_bands<NN, CL>(cluster, sY, sAll, tid);
+    copy_matrix_async<NN>(Yg, sAll, tid);
+    cp_async_wait_all();
     __syncthreads();
     tile_partials<NN, CL>(sCt + r0, NN, sAll, sP, tid);
-    for (int i = tid; i < R * NN; i += DCT_THREADS) sS[i] = 0.f;
     __syncthreads();
 
     // 3: residuals of this block's sampled coefficients, S = scatter(r)
@@ -215,26 +234,26 @@ k_dct_products(const float* __restrict__ Cg, const float* __restrict__ x,
         sS[idx] = rv;
         r2 += (double)rv * (double)rv;
     }
+    __syncthreads();
+    for (int o = tid; o < R * C4; o += DCT_THREADS)
+        reinterpret_cast<float4*>(Sg + (size_t)r0 * NN)[o] = reinterpret_cast<const float4*>(sS)[o];
+    cluster_arrive();
     const double br2 = block_sum(r2, red);
-    if (tid == 0) {
+    if (tid == 0) {   // read by block 0 after the last barrier
         double* dst = cluster.map_shared_rank(cred, 0);
         dst[rank] = br2;
     }
-    cluster.sync();   // every block's rows of S (and its ||r||^2 partial) are complete
+    cluster_wait();   // every block's rows of S are in Sg
 
     // 4: T[i][c] = sum_k C[k][r0+i] S_all[k][c]; stored transposed into sUt
-    gather_bands<NN, CL>(cluster, sS, sAll, tid);
+    copy_matrix_async<NN>(Sg, sAll, tid);
+    // the ||r||^2 partial is written; the matching wait is the last step
+    cluster_arrive();
+    cp_async_wait_all();
     __syncthreads();
     tile_partials<NN, CL>(sC + r0, NN, sAll, sP, tid);
     __syncthreads();
-    for (int o = tid; o < R * C4; o += DCT_THREADS) {
-        const int row = o / C4, c4 = o - row * C4;
-        const float4 t = partial_sum4<NN, CL>(sP, o);
-        sUt[(4 * c4 + 0) * R + row] = t.x;
-        sUt[(4 * c4 + 1) * R + row] = t.y;
-        sUt[(4 * c4 + 2) * R + row] = t.z;
-        sUt[(4 * c4 + 3) * R + row] = t.w;
-    }
+    partial_sum_transposed<NN, CL>(sP, sUt, tid);
     __syncthreads();
 
     // 5: G[i][c] = sum_j T[i][j] C[j][c] = sum_j Tt[j][i] C[j][c]
@@ -242,12 +261,12 @@ k_dct_products(const float* __restrict__ Cg, const float* __restrict__ x,
     __syncthreads();
     for (int o = tid; o < R * C4; o += DCT_THREADS)
         reinterpret_cast<float4*>(g + (size_t)r0 * NN)[o] = partial_sum4<NN, CL>(sP, o);
+    cluster_wait();   // every block's ||r||^2 partial is in block 0
     if (rank == 0 && tid == 0) {
         double t = 0.0;
         for (int k = 0; k < CL; ++k) t += cred[k];
         ctrl->r2 = t;
     }
-    cluster.sync();   // the peers' gathers from this block's shared memory are done
 }
 
 // ---------------------------------------------------------------------------
@@ -323,7 +342,7 @@ static void launch_dct_t(const DctArgs& a, cudaStream_t s)
     cfg.attrs = attr;
     cfg.numAttrs = a.pdl ? 2 : 1;
     cudaLaunchKernelEx(&cfg, k_dct_products<NN, CL>, a.C, a.x, a.y, a.sidx, a.sperm, a.rowptr, a.r,
-                       a.g, a.ctrl, a.mode, (cudaGraphConditionalHandle)a.cond, a.set_cond);
+                       a.g, a.scratch, a.ctrl, a.mode, (cudaGraphConditionalHandle)a.cond, a.set_cond);
 }
 
 void launch_dct_products(int n, const DctArgs& a, cudaStream_t s)

@@ -57,16 +57,6 @@ __host__ __device__ __forceinline__ int tile_rows_for(int W, int tile_cap)
     return rt;
 }
 
-__device__ __forceinline__ void cluster_arrive()
-{
-    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void cluster_wait()
-{
-    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
 // pre[p] = number of active chunks before problem p, pre[P] = T (all threads).
 __device__ int active_prefix(const RegenProb* __restrict__ probs, int P, int mode, int* pre,
                              int* scan)

@@ -180,6 +180,7 @@ struct DctArgs {
     const int* rowptr;
     float* r;            // m (caller's order)
     float* g;            // n*n
+    float* scratch;      // 2 n*n, exchange of the bands between the cluster's blocks
     Ctrl* ctrl;          // receives r2; MODE_ITER bookkeeping as the other product kernels
     int mode;
     unsigned long long cond;

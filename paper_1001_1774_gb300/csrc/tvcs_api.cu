@@ -95,6 +95,7 @@ void products(tvcs_ctx* h, const float* x, const float* y, float* r, float* gpar
     if (h->dct) {     // partial-DCT encoder; A^T r whole in g, else in gpart (P = 1)
         DctArgs d{};
         d.C = h->dctC;
+        d.scratch = h->dctC + 2 * (size_t)h->n * h->n;
         d.x = x;
         d.y = y;
         d.sidx = h->dsidx;
@@ -403,7 +404,7 @@ tvcs_status dct_init(tvcs_ctx* h, const int32_t* rows)
         while (i < m && sidx[i] < k * n) ++i;
         rowptr[k] = i;
     }
-    CKS(alloc((void**)&h->dctC, 2 * sizeof(float) * (size_t)n * n));
+    CKS(alloc((void**)&h->dctC, 4 * sizeof(float) * (size_t)n * n));   // C, C^T, 2 n^2 scratch
     CKS(alloc((void**)&h->dsidx, sizeof(int) * (size_t)m));
     CKS(alloc((void**)&h->dsperm, sizeof(int) * (size_t)m));
     CKS(alloc((void**)&h->drowptr, sizeof(int) * (size_t)(n + 1)));
