@@ -23,11 +23,14 @@
 namespace tvcs {
 
 // ctrls[b].r2 = sum over tiles of the fix-up's partials of ||r_b||^2.
-__global__ void k_batch_r2(const double* __restrict__ r2part, int tiles, Ctrl* __restrict__ ctrls)
+__global__ void k_batch_r2(const float2* __restrict__ r2part, int tiles, Ctrl* __restrict__ ctrls)
 {
-    __shared__ double red[32];
-    const double s = block_sum_array(r2part + (size_t)blockIdx.x * tiles, tiles, 1, red);
-    if (threadIdx.x == 0) ctrls[blockIdx.x].r2 = s;
+    __shared__ float2 red[32];
+    float2 s = make_float2(0.f, 0.f);
+    for (int i = threadIdx.x; i < tiles; i += blockDim.x)
+        s = ds_add(s, r2part[(size_t)blockIdx.x * tiles + i]);
+    s = block_sum_ds(s, red);
+    if (threadIdx.x == 0) ctrls[blockIdx.x].r2 = ds_value(s);
 }
 
 // Continue while any image runs and the loop bound holds.
@@ -110,7 +113,8 @@ void free_buffers(tvcs_batch* b)
     b->U = b->W = b->L = b->G = b->R = b->F = b->mu = nullptr;
     b->Uh = b->Ul = b->Rh = b->Rl = nullptr;
     b->ctrls = b->bctrl = b->hctrls = b->hbctrl = nullptr;
-    b->r2part = b->part = nullptr;
+    b->r2part = nullptr;
+    b->part = nullptr;
     b->ws = nullptr;
     b->tsb1 = b->ss1 = b->tsb2 = b->ss2 = nullptr;
     b->exec = nullptr;
@@ -215,7 +219,7 @@ tvcs_status ensure_batch(tvcs_ctx* h, int count)
         BCKS(balloc((void**)&b->Rl, sizeof(unsigned short) * B * b->mpad));
         BCKS(balloc((void**)&b->ctrls, sizeof(Ctrl) * B));
         BCKS(balloc((void**)&b->bctrl, sizeof(Ctrl)));
-        BCKS(balloc((void**)&b->r2part, sizeof(double) * B * b->p1.tiles_m));
+        BCKS(balloc((void**)&b->r2part, sizeof(float2) * B * b->p1.tiles_m));
         BCKS(balloc((void**)&b->part, sizeof(double) * B * 2 * ((N + 255) / 256)));
         BCK(cudaMallocHost((void**)&b->hctrls, sizeof(Ctrl) * B));
         BCK(cudaMallocHost((void**)&b->hbctrl, sizeof(Ctrl)));
@@ -451,7 +455,7 @@ tvcs_status solve_batch(tvcs_ctx* h, int count, const float* const* f, float* co
             r.iters = c.it;
             r.status = st;
             r.stopped_by_tol = c.stop_by_tol;
-            r.rel_change = c.relchg;
+            r.rel_change = ctrl_relchg(c);
             r.tv = c.tv;
             r.resid2 = c.r2;
             r.objective = c.tv + 0.5 * mus[i] * c.r2;

@@ -28,7 +28,6 @@ struct Ctrl {
     double tol;
     double du2;        // ||u^{k+1} - u^k||^2 of the last iteration
     double u2;         // ||u^k||^2 of the last iteration
-    double relchg;     // sqrt(du2/u2)
     double r2;         // ||A u - f||^2 at the current u
     double tv;         // sum_i ||D_i u||
     double kkt_p2;     // ||w - D u||^2
@@ -37,6 +36,12 @@ struct Ctrl {
     double vec2;       // ||g||^2 of the last gathered vector (power iteration)
     unsigned long long gbar;  // monotone arrival counter of the product kernel's grid barrier
 };
+
+// sqrt(du2 / u2), the relative change of eq. (stop) (host side).
+inline double ctrl_relchg(const Ctrl& c)
+{
+    return c.u2 > 0.0 ? sqrt(c.du2 / c.u2) : (c.du2 > 0.0 ? INFINITY : 0.0);
+}
 
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
 {
@@ -191,6 +196,78 @@ __device__ __forceinline__ double warp_sum(double v)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Sums of squares in binary32 double-single arithmetic: a value is the
+// unevaluated pair hi + lo.  ds_sq gives x^2 exactly (the FMA residual of the
+// rounded product), ds_add is Knuth's TwoSum followed by a fast
+// renormalisation, so a sum of non-negative terms keeps about 44 significant
+// bits.  Binary64 arithmetic runs at a small fraction of the binary32 rate on
+// this part, so reductions stay in binary32 and only ds_value converts.  The
+// _rn intrinsics keep the compiler from contracting the error terms into FMAs.
+__device__ __forceinline__ float2 ds_sq(float x)
+{
+    const float p = __fmul_rn(x, x);
+    return make_float2(p, __fmaf_rn(x, x, -p));
+}
+
+__device__ __forceinline__ float2 ds_add(float2 a, float2 b)
+{
+    const float s = __fadd_rn(a.x, b.x);
+    const float v = __fsub_rn(s, a.x);
+    const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, v)), __fsub_rn(b.x, v));
+    const float t = __fadd_rn(__fadd_rn(a.y, b.y), e);
+    const float h = __fadd_rn(s, t);
+    return make_float2(h, __fsub_rn(t, __fsub_rn(h, s)));
+}
+
+__device__ __forceinline__ double ds_value(float2 a) { return (double)a.x + (double)a.y; }
+
+__device__ __forceinline__ float2 warp_sum_ds(float2 v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float2 w = make_float2(__shfl_xor_sync(0xffffffffu, v.x, o),
+                                     __shfl_xor_sync(0xffffffffu, v.y, o));
+        v = ds_add(v, w);
+    }
+    return v;
+}
+
+// Block-wide double-single sums of two values per thread (one pair of
+// barriers); results valid in thread 0.  `scratch` holds >= 64 float2.
+__device__ __forceinline__ void block_sum_ds2(float2& a, float2& b, float2* scratch)
+{
+    a = warp_sum_ds(a);
+    b = warp_sum_ds(b);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        scratch[wid] = a;
+        scratch[32 + wid] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int i = 1; i < nw; ++i) {
+            a = ds_add(a, scratch[i]);
+            b = ds_add(b, scratch[32 + i]);
+        }
+    }
+}
+
+__device__ __forceinline__ float2 block_sum_ds(float2 a, float2* scratch)
+{
+    a = warp_sum_ds(a);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) scratch[wid] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int i = 1; i < nw; ++i) a = ds_add(a, scratch[i]);
+    }
+    return a;
 }
 
 __device__ __forceinline__ double warp_max(double v)

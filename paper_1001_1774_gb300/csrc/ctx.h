@@ -22,7 +22,8 @@ struct tvcs_batch {
     tvcs::Ctrl* hctrls = nullptr;        // pinned host mirror
     tvcs::Ctrl* bctrl = nullptr;         // loop control of the batch
     tvcs::Ctrl* hbctrl = nullptr;
-    double *r2part = nullptr, *part = nullptr;
+    float2* r2part = nullptr;   // double-single ||r||^2 partials
+    double* part = nullptr;
     float* ws = nullptr;           // stream-K partial tiles
     tvcs::GemmPlan p1, p2;               // R = A U - F (M = m, K = N) and G = A^T R (M = N, K = m)
     int *tsb1 = nullptr, *ss1 = nullptr, *tsb2 = nullptr, *ss2 = nullptr;
@@ -43,7 +44,7 @@ struct tvcs_regen {
     tvcs::RegenProb* dtab = nullptr;       // device entries
     std::vector<tvcs::RegenProb> htab;     // host copies, same order
     float* gslot = nullptr;
-    double* r2slot = nullptr;
+    float2* r2slot = nullptr;    // double-single ||r||^2 partials
     int* pre = nullptr;
 };
 struct tvcs_uneven;   // state of the uneven batch (regen.cu)
@@ -69,7 +70,8 @@ struct tvcs_ctx {
     float2* tw = nullptr;
     float* s2 = nullptr;
     float *gpart = nullptr, *gpart2 = nullptr;
-    double *r2part = nullptr, *part = nullptr;
+    float2* r2part = nullptr;   // double-single ||r||^2 partials
+    double* part = nullptr;
     tvcs::Ctrl* ctrl = nullptr;
     tvcs::Ctrl* hctrl = nullptr;  // pinned host mirror
     // loop graph

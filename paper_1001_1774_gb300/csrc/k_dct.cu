@@ -49,7 +49,7 @@ struct DctShape {
     static constexpr size_t O_UT = O_ALL + NSQ;       // u band transposed (n x R), later T^T
     static constexpr size_t O_S = O_UT + BAND;        // S band
     static constexpr size_t O_P = O_S + BAND;         // KS partial bands
-    static constexpr size_t O_RED = O_P + (size_t)KS * BAND;   // doubles
+    static constexpr size_t O_RED = O_P + (size_t)KS * BAND;   // float2
     static constexpr size_t SMEM = O_RED + (32 + 16) * 8;
     static_assert(NN % CL == 0 && R % 4 == 0 && CL <= 16, "whole 4-row groups per block");
     static_assert(KS >= 1 && TILES * KS <= DCT_THREADS, "one tile slice per thread at most");
@@ -159,8 +159,8 @@ k_dct_products(const float* __restrict__ Cg, const float* __restrict__ x,
     float* sUt = reinterpret_cast<float*>(smem + S::O_UT);
     float* sS = reinterpret_cast<float*>(smem + S::O_S);
     float* sP = reinterpret_cast<float*>(smem + S::O_P);
-    double* red = reinterpret_cast<double*>(smem + S::O_RED);   // [32]
-    double* cred = red + 32;                                    // [CL] cluster partials
+    float2* red = reinterpret_cast<float2*>(smem + S::O_RED);   // [32]
+    float2* cred = red + 32;                                    // [CL] cluster partials
 
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
@@ -169,8 +169,24 @@ k_dct_products(const float* __restrict__ Cg, const float* __restrict__ x,
     const int tid = threadIdx.x;
     const int r0 = rank * R;
 
-    // C and C^T (2 n^2 floats, constants) while the preceding kernel finishes
+    // C and C^T (2 n^2 floats), the sampled positions of this block's rows and
+    // their measurements: constants during a solve, fetched while the preceding
+    // kernel finishes
     for (int i = tid; i < 2 * NN * C4; i += DCT_THREADS) cp_async16(sC + 4 * i, Cg + 4 * i);
+    constexpr int EMAX = (R * NN + DCT_THREADS - 1) / DCT_THREADS;
+    const int e0 = rowptr[r0], e1 = rowptr[r0 + R];
+    int eidx[EMAX], eq[EMAX];
+    float ey[EMAX];
+#pragma unroll
+    for (int k = 0; k < EMAX; ++k) {
+        const int e = e0 + tid + k * DCT_THREADS;
+        eidx[k] = -1;
+        if (e < e1) {
+            eidx[k] = sidx[e] - r0 * NN;   // local position in the block's rows
+            eq[k] = sperm[e];              // caller's order of the measurement
+            ey[k] = y ? y[eq[k]] : 0.f;
+        }
+    }
 
     pdl_wait();
     if (mode == MODE_ITER) {
@@ -221,26 +237,27 @@ k_dct_products(const float* __restrict__ Cg, const float* __restrict__ x,
     __syncthreads();
 
     // 3: residuals of this block's sampled coefficients, S = scatter(r)
-    double r2 = 0.0;
-    const int e0 = rowptr[r0], e1 = rowptr[r0 + R];
-    for (int e = e0 + tid; e < e1; e += DCT_THREADS) {
-        const int idx = sidx[e] - r0 * NN;   // local position in the block's rows
-        const int q = sperm[e];              // caller's order of the measurement
-        float z = sP[idx];
+    float2 r2 = make_float2(0.f, 0.f);   // double-single ||r||^2
 #pragma unroll
-        for (int ks = 1; ks < S::KS; ++ks) z += sP[(size_t)ks * R * NN + idx];
-        const float rv = y ? z - y[q] : z;
-        r[q] = rv;
-        sS[idx] = rv;
-        r2 += (double)rv * (double)rv;
+    for (int k = 0; k < EMAX; ++k) {
+        const int idx = eidx[k];
+        if (idx >= 0) {
+            float z = sP[idx];
+#pragma unroll
+            for (int ks = 1; ks < S::KS; ++ks) z += sP[(size_t)ks * R * NN + idx];
+            const float rv = z - ey[k];
+            r[eq[k]] = rv;
+            sS[idx] = rv;
+            r2 = ds_add(r2, ds_sq(rv));
+        }
     }
     __syncthreads();
     for (int o = tid; o < R * C4; o += DCT_THREADS)
         reinterpret_cast<float4*>(Sg + (size_t)r0 * NN)[o] = reinterpret_cast<const float4*>(sS)[o];
     cluster_arrive();
-    const double br2 = block_sum(r2, red);
+    const float2 br2 = block_sum_ds(r2, red);
     if (tid == 0) {   // read by block 0 after the last barrier
-        double* dst = cluster.map_shared_rank(cred, 0);
+        float2* dst = cluster.map_shared_rank(cred, 0);
         dst[rank] = br2;
     }
     cluster_wait();   // every block's rows of S are in Sg
@@ -263,9 +280,9 @@ k_dct_products(const float* __restrict__ Cg, const float* __restrict__ x,
         reinterpret_cast<float4*>(g + (size_t)r0 * NN)[o] = partial_sum4<NN, CL>(sP, o);
     cluster_wait();   // every block's ||r||^2 partial is in block 0
     if (rank == 0 && tid == 0) {
-        double t = 0.0;
-        for (int k = 0; k < CL; ++k) t += cred[k];
-        ctrl->r2 = t;
+        float2 t = cred[0];
+        for (int k = 1; k < CL; ++k) t = ds_add(t, cred[k]);
+        ctrl->r2 = ds_value(t);
     }
 }
 

@@ -290,10 +290,10 @@ __global__ void __launch_bounds__(128) k_gemm_fixup(
     const float* __restrict__ ws, const int* __restrict__ tile_seg_begin,
     const int* __restrict__ seg_slot, int M, int count, const float* __restrict__ F, int ldf,
     float* __restrict__ out, int ldo, __nv_bfloat16* __restrict__ out_hi,
-    __nv_bfloat16* __restrict__ out_lo, int ldh, double* __restrict__ r2part, int tiles_m,
+    __nv_bfloat16* __restrict__ out_lo, int ldh, float2* __restrict__ r2part, int tiles_m,
     const Ctrl* __restrict__ ctrl, int check_skip)
 {
-    __shared__ double red[4][FX_B];
+    __shared__ float2 red[4][FX_B];
     if (check_skip && ctrl->skip) return;
     const int t = blockIdx.x, b0 = blockIdx.y * FX_B;
     const int row = t * GM_BM + threadIdx.x;
@@ -311,11 +311,11 @@ __global__ void __launch_bounds__(128) k_gemm_fixup(
             v[k][q] = (q < ns && b0 + k < count)
                           ? ws[((size_t)slot[q] * GM_BN + b0 + k) * GM_BM + threadIdx.x]
                           : 0.f;
-    double sq[FX_B];
+    float2 sq[FX_B];   // double-single squares
 #pragma unroll
     for (int k = 0; k < FX_B; ++k) {
         const int b = b0 + k;
-        sq[k] = 0.0;
+        sq[k] = make_float2(0.f, 0.f);
         if (b >= count) continue;
         float d = 0.f;   // the tile's segments in K order
 #pragma unroll
@@ -330,20 +330,21 @@ __global__ void __launch_bounds__(128) k_gemm_fixup(
                 out_hi[(size_t)b * ldh + row] = h;
                 out_lo[(size_t)b * ldh + row] = __float2bfloat16_rn(d - __bfloat162float(h));
             }
-            sq[k] = (double)d * (double)d;
+            sq[k] = ds_sq(d);
         }
     }
     if (r2part) {   // per image: the sum over the tile's rows (fixed order)
         const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
         for (int k = 0; k < FX_B; ++k) {
-            const double v = warp_sum(sq[k]);
+            const float2 v = warp_sum_ds(sq[k]);
             if (lane == 0) red[w][k] = v;
         }
         __syncthreads();
         if (threadIdx.x < FX_B && b0 + (int)threadIdx.x < count) {
             const int k = threadIdx.x;
-            r2part[(size_t)(b0 + k) * tiles_m + t] = ((red[0][k] + red[1][k]) + red[2][k]) + red[3][k];
+            r2part[(size_t)(b0 + k) * tiles_m + t] =
+                ds_add(ds_add(ds_add(red[0][k], red[1][k]), red[2][k]), red[3][k]);
         }
     }
 }
@@ -469,7 +470,7 @@ void launch_gemm(const CUtensorMap* xh, const CUtensorMap* xl, const CUtensorMap
 
 void launch_gemm_fixup(const float* ws, const int* tile_seg_begin, const int* seg_slot, int M,
                        int tiles_m, int count, const float* F, int ldf, float* out, int ldo,
-                       void* out_hi, void* out_lo, int ldh, double* r2part, const Ctrl* ctrl,
+                       void* out_hi, void* out_lo, int ldh, float2* r2part, const Ctrl* ctrl,
                        int check_skip, cudaStream_t s)
 {
     dim3 grid(tiles_m, (count + FX_B - 1) / FX_B);

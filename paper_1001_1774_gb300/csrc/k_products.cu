@@ -45,7 +45,7 @@ template <int V, int RL, int RS>
 __global__ void __maxnreg__(96)
     k_products(const float* __restrict__ A, int m, const float* __restrict__ x,
                const float* __restrict__ y, float* __restrict__ r, float* __restrict__ gpart,
-               float* __restrict__ g_out, double* __restrict__ r2part, Ctrl* __restrict__ ctrl,
+               float* __restrict__ g_out, float2* __restrict__ r2part, Ctrl* __restrict__ ctrl,
                int mode, cudaGraphConditionalHandle cond, int set_cond, long long budget)
 {
     using S = ProdShape<V, RL, RS>;
@@ -57,7 +57,7 @@ __global__ void __maxnreg__(96)
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + PROD_NST * S::STAGE_FLOATS * 4);
     uint64_t* empty = full + PROD_NST;
     float* red = reinterpret_cast<float*>(empty + PROD_NST);        // [2][RL][WPR]
-    double* dred = reinterpret_cast<double*>(red + 2 * RL * WPR);   // [32]
+    float2* dred = reinterpret_cast<float2*>(red + 2 * RL * WPR);   // [32]
     int* sflag = reinterpret_cast<int*>(dred + 32);                 // [4]
     float* sy = reinterpret_cast<float*>(sflag + 4);                // [YMAX]
 
@@ -133,7 +133,7 @@ __global__ void __maxnreg__(96)
         xu[v] = x4[ltid + v * TPR];
         acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    double r2 = 0.0;
+    float2 r2 = make_float2(0.f, 0.f);   // double-single ||r||^2 of this thread's rows
     bool ok = true;
     int step = 0;
     for (int s = 0; s < nst; ++s) {
@@ -176,7 +176,7 @@ __global__ void __maxnreg__(96)
                 const float ri = dot - yi;
                 if (ltid == 0) {
                     r[gi] = ri;
-                    r2 += (double)ri * (double)ri;
+                    r2 = ds_add(r2, ds_sq(ri));
                 }
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
@@ -231,12 +231,12 @@ __global__ void __maxnreg__(96)
             }
         }
     }
-    // binary64 ||r||^2: one value per row lane (held by ltid == 0)
+    // ||r||^2: one double-single value per row lane (held by ltid == 0)
     if (ltid == 0) dred[lane_row] = r2;
     named_barrier(1, PROD_CONS);
     if (tid == 0) {
-        double s = 0.0;
-        for (int l = 0; l < RL; ++l) s += dred[l];
+        float2 s = dred[0];
+        for (int l = 1; l < RL; ++l) s = ds_add(s, dred[l]);
         r2part[blockIdx.x] = s;
         // without the grid barrier below, the last block to arrive sums the partials
         sflag[0] = (g_out == nullptr && last_block_arrive(&ctrl->ticket_prod)) ? 1 : 0;
@@ -244,14 +244,14 @@ __global__ void __maxnreg__(96)
     named_barrier(1, PROD_CONS);
     // ||r||^2 = sum of the G partials with all consumer warps (G <= 512), fixed order
     auto sum_r2 = [&]() {
-        double v = tid < G ? __ldcg(r2part + tid) : 0.0;
-        v = warp_sum(v);
+        float2 v = tid < G ? __ldcg(r2part + tid) : make_float2(0.f, 0.f);
+        v = warp_sum_ds(v);
         if ((tid & 31) == 0) dred[tid >> 5] = v;
         named_barrier(1, PROD_CONS);
         if (tid == 0) {
-            double t = 0.0;
-            for (int w = 0; w < PROD_CONS / 32; ++w) t += dred[w];
-            ctrl->r2 = t;
+            float2 t = dred[0];
+            for (int w = 1; w < PROD_CONS / 32; ++w) t = ds_add(t, dred[w]);
+            ctrl->r2 = ds_value(t);
         }
     };
     if (sflag[0]) sum_r2();

@@ -58,7 +58,7 @@ struct QShape {
     static constexpr size_t O_BAR = NST * STAGE_BYTES;               // full[NST], empty[NST], xbar[4]
     static constexpr size_t O_RED = O_BAR + (2 * NST + 4) * 8;       // [2][CONS/32] floats
     static constexpr size_t O_XRED = O_RED + 2 * (CONS / 32) * 4;    // [4][CS] floats
-    static constexpr size_t O_DRED = ((O_XRED + 4 * CS * 4 + 15) / 16) * 16;   // [32] doubles
+    static constexpr size_t O_DRED = ((O_XRED + 4 * CS * 4 + 15) / 16) * 16;   // [32] float2
     static constexpr size_t O_Y = O_DRED + 32 * 8;                   // y of the rows
     static constexpr size_t O_S = O_Y + QPROD_YMAX * 4;              // row scales (FP8)
     static constexpr size_t SMEM = O_S + QPROD_YMAX * 4 + 16;
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(CONS + 32, 1)
     k_products_q(const unsigned char* __restrict__ P0, const unsigned char* __restrict__ P1,
                  const float* __restrict__ rscale, int m, const float* __restrict__ x,
                  const float* __restrict__ y, float* __restrict__ r, float* __restrict__ gpart,
-                 double* __restrict__ r2part, Ctrl* __restrict__ ctrl, int mode,
+                 float2* __restrict__ r2part, Ctrl* __restrict__ ctrl, int mode,
                  cudaGraphConditionalHandle cond, int set_cond, long long budget)
 {
     using S = QShape<PREC, V, CS, CONS, NST>;
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(CONS + 32, 1)
     uint64_t* xbar = empty + NST;                                   // [4]
     float* red = reinterpret_cast<float*>(smem + S::O_RED);         // [2][WARPS]
     float* xred = reinterpret_cast<float*>(smem + S::O_XRED);       // [4][CS]
-    double* dred = reinterpret_cast<double*>(smem + S::O_DRED);
+    float2* dred = reinterpret_cast<float2*>(smem + S::O_DRED);
     float* sy = reinterpret_cast<float*>(smem + S::O_Y);
     float* ss = reinterpret_cast<float*>(smem + S::O_S);
     int* sflag = reinterpret_cast<int*>(smem + S::O_S + QPROD_YMAX * 4);
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(CONS + 32, 1)
         xred_remote[k] = CS > 1 ? map_remote(smem_u32(xred), (uint32_t)k) : 0u;
         xbar_remote[k] = CS > 1 ? map_remote(smem_u32(xbar), (uint32_t)k) : 0u;
     }
-    double r2 = 0.0;
+    float2 r2 = make_float2(0.f, 0.f);   // double-single ||r||^2 (block 0, thread 0)
     bool ok = true;
     // This block's part of the dot product of row s (waits for the row's stage).
     auto part_of_row = [&](int s) -> float {
@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(CONS + 32, 1)
         const float ri = dot - yi;
         if (rank == 0 && tid == 0) {
             r[i0 + s] = ri;
-            r2 += (double)ri * (double)ri;
+            r2 = ds_add(r2, ds_sq(ri));
         }
         const int slot = s % NST;
         const unsigned char* sb = smem + (size_t)slot * S::STAGE_BYTES;
@@ -367,15 +367,15 @@ __global__ void __launch_bounds__(CONS + 32, 1)
     }
     named_barrier(1, CONS);
     if (sflag[0]) {
-        double v = 0.0;
-        for (int b = tid; b < G; b += CONS) v += r2part[b];
-        v = warp_sum(v);
+        float2 v = make_float2(0.f, 0.f);
+        for (int b = tid; b < G; b += CONS) v = ds_add(v, __ldcg(r2part + b));
+        v = warp_sum_ds(v);
         if ((tid & 31) == 0) dred[tid >> 5] = v;
         named_barrier(1, CONS);
         if (tid == 0) {
-            double t = 0.0;
-            for (int w = 0; w < WARPS; ++w) t += dred[w];
-            ctrl->r2 = t;
+            float2 t = dred[0];
+            for (int w = 1; w < WARPS; ++w) t = ds_add(t, dred[w]);
+            ctrl->r2 = ds_value(t);
         }
     }
     __syncwarp();

@@ -155,7 +155,7 @@ k_regen_products(const RegenProb* __restrict__ probs, int P, int mode, int wmax,
     int cend = min(m, row + RC);
     int head = c;
 
-    double r2acc = 0.0;
+    float2 r2acc = make_float2(0.f, 0.f);   // double-single ||r||^2 of the problem
     // exch + update of tile tm: partial dots from slot buffer sb, entries from tile buffer tb
     auto finish = [&](const TileMeta& tm, int sb, int tb) {
         cluster_wait();   // every block's partial dots of tile tm are visible
@@ -168,7 +168,7 @@ k_regen_products(const RegenProb* __restrict__ probs, int P, int mode, int wmax,
             rvec[sb * RG_RTMAX + tid] = rv;
             if (rank == 0) {
                 pp->r[i] = rv;
-                r2acc += (double)rv * (double)rv;
+                r2acc = ds_add(r2acc, ds_sq(rv));
             }
         }
         __syncthreads();
@@ -188,10 +188,10 @@ k_regen_products(const RegenProb* __restrict__ probs, int P, int mode, int wmax,
                 g4[q4] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
             if (rank == 0 && tid < 32) {   // r2acc lives in threads < 16 of block 0
-                const double v = warp_sum(r2acc);
+                const float2 v = warp_sum_ds(r2acc);
                 if (tid == 0) pp->r2slot[tm.head] = v;
             }
-            r2acc = 0.0;
+            r2acc = make_float2(0.f, 0.f);
         }
     };
 
@@ -344,9 +344,9 @@ k_regen_reduce(const RegenProb* __restrict__ probs, int P, int Q, const int* __r
         reinterpret_cast<float4*>(pr.g)[q4] = acc;
     }
     if (blockIdx.x == 0 && tid == 0 && pr.ctrl) {
-        double v = 0.0;
-        for (int h = 0; h < nh; ++h) v += pr.r2slot[heads[h]];
-        pr.ctrl->r2 = v;
+        float2 v = pr.r2slot[heads[0]];
+        for (int h = 1; h < nh; ++h) v = ds_add(v, pr.r2slot[heads[h]]);
+        pr.ctrl->r2 = ds_value(v);
     }
 }
 

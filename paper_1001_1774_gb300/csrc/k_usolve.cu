@@ -11,10 +11,11 @@
 // [k R, (k+1) R), R = n / C.  Phase A: w-step and right-hand side of the
 // owned rows (plus one recomputed halo row), forward row FFTs (two real rows
 // packed per complex transform), half spectrum kept in this block's shared
-// memory.  Phase B: the n/2+1 spectrum columns are split over the blocks;
-// each gathers its columns from the owners' shared memory (distributed shared
-// memory), transforms along the columns, divides by beta Lambda_pq + mu/tau,
-// transforms back and scatters the columns home.  Phase C: inverse row FFTs,
+// memory.  Phase B: the n/2+1 spectrum columns are split over the blocks; the
+// split at the end of phase A already stores each value into the shared memory
+// of its column's block (remote stores, which do not stall the issuing
+// thread), which transforms along the columns, divides by beta Lambda_pq +
+// mu/tau, transforms back and scatters the columns home.  Phase C: inverse row FFTs,
 // u update and norms.  Cluster barriers separate the phases, so the whole
 // u-solve is one launch and the spectrum never leaves the chip.
 //
@@ -32,6 +33,8 @@
 namespace cg = cooperative_groups;
 
 namespace tvcs {
+
+constexpr int US_THREADS = 512;
 
 template <int NN, int C>
 struct UsolveShape {
@@ -52,8 +55,9 @@ struct UsolveShape {
     static constexpr size_t O_WA = O_SPEC + ((R * Q * 8 + 15) / 16) * 16;
     static constexpr size_t O_WB = O_WA + WORK * 8;
     static constexpr size_t O_WL = O_WB + WORK * 8;            // w1, w2, l1, l2 of rows r0-1 .. r0+R-1
-    static constexpr size_t O_RED = O_WL + 4 * (R + 1) * NN * 4;
-    static constexpr size_t SMEM = O_RED + (32 + 2 * 16 + 2) * 8;
+    static constexpr size_t O_COL = O_WL + 4 * (R + 1) * NN * 4;   // QC columns, cluster-written
+    static constexpr size_t O_RED = O_COL + (size_t)COLFFT * 8;
+    static constexpr size_t SMEM = O_RED + (64 + 2 * 16) * 8;
     static_assert(NN % C == 0 && R % 2 == 0, "each block owns an even number of rows");
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
@@ -63,8 +67,28 @@ struct UsolveShape {
 // tau_img[b] when that is set too).  When u_hi is
 // set, the new u is also written as bfloat16 hi/lo planes (operand of the
 // batched products).
+// a4: the half spectra of the owned rows as in step_split (rows r0 + 2j and
+// r0 + 2j + 1 from packed transform j), each column q stored into the column
+// buffer of block q / QC: col[(q mod QC) NN + row].
 template <int NN, int C>
-__global__ void __launch_bounds__(256, 1) k_usolve_cluster(
+__device__ __forceinline__ void split_to_columns(cg::cluster_group& cluster, const float2* Z,
+                                                 int r0, float2* col, int tid, int nthr)
+{
+    using S = UsolveShape<NN, C>;
+    constexpr int Q = S::Q, QC = S::QC, R = S::R;
+    for (int i = tid; i < (R / 2) * Q; i += nthr) {
+        const int j = i / Q, q = i - j * Q;
+        const float2 a = Z[j * NN + q];
+        const float2 b = Z[j * NN + (NN - q) % NN];
+        const int owner = q / QC, f = q - owner * QC;
+        float2* dst = cluster.map_shared_rank(col, owner) + f * NN + r0 + 2 * j;
+        dst[0] = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+        dst[1] = make_float2(0.5f * (a.y + b.y), -0.5f * (a.x - b.x));
+    }
+}
+
+template <int NN, int C>
+__global__ void __launch_bounds__(US_THREADS, 1) k_usolve_cluster(
     float* __restrict__ u, float* __restrict__ wbuf, float* __restrict__ lbuf,
     const float* __restrict__ g, float* __restrict__ rhs_out, const float2* __restrict__ tw_g,
     const float* __restrict__ s2_g, float beta, float mu_over_tau, float mu,
@@ -101,8 +125,9 @@ __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
     float2* wa = reinterpret_cast<float2*>(smem + S::O_WA);
     float2* wb = reinterpret_cast<float2*>(smem + S::O_WB);
     float* swl = reinterpret_cast<float*>(smem + S::O_WL);       // [4][(R+1) NN]
-    double* red = reinterpret_cast<double*>(smem + S::O_RED);    // [32] block reduction
-    double* cred = red + 32;                                     // [C][2] cluster partials
+    float2* col = reinterpret_cast<float2*>(smem + S::O_COL);    // [QC][NN], cluster-written
+    float2* red = reinterpret_cast<float2*>(smem + S::O_RED);    // [64] block reduction
+    float2* cred = red + 64;                                     // [C][2] cluster partials
 
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
@@ -119,6 +144,9 @@ __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
             return;
         }
     }
+    // every block of the cluster has started before any distributed shared
+    // memory access (the wait sits just before the first one, the column split)
+    cluster_arrive();
     const int par = ctrl->wpar;
     const int pending = ctrl->pending;   // set by the previous u-solve (or the host)
     const float* wsrc = wbuf + (size_t)par * 2 * N;
@@ -163,40 +191,21 @@ __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
     step_sub_g<NN>(sg, R, r0, mu, wa, rhs_out, tid, nthr);
     __syncthreads();
     float2* Zr = fft_block<NN, false>(wa, wb, tw, R / 2, NN);
-    step_split<NN>(Zr, R, spec, Q, 1, tid, nthr);
-    cluster.sync();   // every block's half spectrum is complete
+    cluster_wait();
+    split_to_columns<NN, C>(cluster, Zr, r0, col, tid, nthr);
+    cluster.sync();   // every block's columns are complete
 
     // ---------------- phase B: columns ----------------
     const int q0 = rank * QC;
     const int ncol = max(0, min(QC, Q - q0));
-    {
-        // all remote loads first (independent, in registers), then the local stores
-        constexpr int GPT = (QC * NN + 255) / 256;
-        float2 v[GPT];
-#pragma unroll
-        for (int k = 0; k < GPT; ++k) {
-            const int i = tid + k * nthr;
-            if (i < ncol * NN) {
-                const int f = i % ncol, p = i / ncol;
-                const float2* own = cluster.map_shared_rank(spec, p / R);
-                v[k] = own[(p % R) * Q + q0 + f];
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < GPT; ++k) {
-            const int i = tid + k * nthr;
-            if (i < ncol * NN) wa[(i % ncol) * NN + i / ncol] = v[k];
-        }
-    }
-    __syncthreads();
-    float2* X = fft_block<NN, false>(wa, wb, tw, ncol, NN);
-    float2* other = (X == wa) ? wb : wa;
+    float2* X = fft_block<NN, false>(col, wb, tw, ncol, NN);
+    float2* other = (X == col) ? wb : col;
     for (int i = tid; i < ncol * NN; i += nthr) {
         const int f = i / NN, p = i - f * NN;
-        const float d = solve_divisor(s2, p, q0 + f, beta, mu_over_tau);
+        const float rd = 1.0f / solve_divisor(s2, p, q0 + f, beta, mu_over_tau);
         float2 v = X[i];
-        v.x = v.x / d;
-        v.y = v.y / d;
+        v.x *= rd;
+        v.y *= rd;
         X[i] = v;
     }
     __syncthreads();
@@ -212,24 +221,23 @@ __global__ void __launch_bounds__(256, 1) k_usolve_cluster(
     step_pack_inverse<NN>(spec, Q, 1, R, wa, tid, nthr);
     __syncthreads();
     float2* z = fft_block<NN, true>(wa, wb, tw, R / 2, NN);
-    // per-thread sums of a few squares in binary32, combined across threads in binary64
-    float du2f = 0.f, u2f = 0.f;
-    step_update<NN>(z, su + NN, R, r0, u, u_hi, u_lo, du2f, u2f, tid, nthr);
-    const double bdu = block_sum((double)du2f, red);
-    const double bu = block_sum((double)u2f, red);
+    // double-single sums of squares (fixed order per thread, warp and block)
+    float2 du2 = make_float2(0.f, 0.f), u2 = make_float2(0.f, 0.f);
+    step_update<NN>(z, su + NN, R, r0, u, u_hi, u_lo, du2, u2, tid, nthr);
+    block_sum_ds2(du2, u2, red);
     if (tid == 0) {
-        double* dst = cluster.map_shared_rank(cred, 0);
-        dst[2 * rank] = bdu;
-        dst[2 * rank + 1] = bu;
+        float2* dst = cluster.map_shared_rank(cred, 0);
+        dst[2 * rank] = du2;
+        dst[2 * rank + 1] = u2;
     }
     cluster.sync();   // partials delivered to block 0; every block has read wpar and done
     if (rank == 0 && tid == 0) {
-        double tdu = 0.0, tu = 0.0;
-        for (int k = 0; k < C; ++k) {
-            tdu += cred[2 * k];
-            tu += cred[2 * k + 1];
+        float2 tdu = cred[0], tu = cred[1];
+        for (int k = 1; k < C; ++k) {
+            tdu = ds_add(tdu, cred[2 * k]);
+            tu = ds_add(tu, cred[2 * k + 1]);
         }
-        step_stop(ctrl, par, mode, tdu, tu);
+        step_stop(ctrl, par, mode, ds_value(tdu), ds_value(tu));
     }
 }
 
@@ -259,7 +267,7 @@ static bool cluster_fits_t()
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
-    cfg.blockDim = dim3(256, 1, 1);
+    cfg.blockDim = dim3(US_THREADS, 1, 1);
     cfg.dynamicSmemBytes = S::SMEM;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -283,7 +291,7 @@ static void launch_usolve_t(const TvArgs& a, cudaStream_t s)
     using S = UsolveShape<NN, C>;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, a.nimg > 0 ? a.nimg : 1, 1);
-    cfg.blockDim = dim3(256, 1, 1);
+    cfg.blockDim = dim3(US_THREADS, 1, 1);
     cfg.dynamicSmemBytes = S::SMEM;
     cfg.stream = s;
     cudaLaunchAttribute attr[2];
@@ -300,7 +308,8 @@ static void launch_usolve_t(const TvArgs& a, cudaStream_t s)
                        a.tau, a.u_hi, a.u_lo);
 }
 
-// Cluster sizes available per n: {16, 8} where both give an even row count.
+// Cluster sizes available per n: {16, 8} where both give an even row count and
+// the shared memory fits (n = 192 needs 16).
 #define TVCS_USOLVE_TABLE(X) \
     X(16, 8)                 \
     X(32, 16) X(32, 8)       \
@@ -308,7 +317,7 @@ static void launch_usolve_t(const TvArgs& a, cudaStream_t s)
     X(64, 16) X(64, 8)       \
     X(96, 16) X(96, 8)       \
     X(128, 16) X(128, 8)     \
-    X(192, 16) X(192, 8)     \
+    X(192, 16)               \
     X(256, 16)
 
 bool usolve_cluster_fits(int n, int c)

@@ -50,7 +50,7 @@ struct ImgShape {
     static constexpr size_t A_END = A_WB + (size_t)(S / 2) * NN * 8;
     static constexpr size_t B_END = O_SCR + SPEC_BYTES;   // phase B: scratch = the second FFT buffer
     static constexpr size_t O_RED = A_END > B_END ? A_END : B_END;
-    static constexpr size_t SMEM = O_RED + 32 * 8;
+    static constexpr size_t SMEM = O_RED + 64 * 8;
     // phase C, inside the scratch region (the forward and inverse column FFTs
     // are 2 x stages ping-pong steps, so the solved spectrum ends in `spec`):
     // two u-row buffers, two FFT buffers
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(IMG_THREADS, 1) k_usolve_img(
     float* sy2 = reinterpret_cast<float*>(smem + SH::A_Y2);
     float2* wa = reinterpret_cast<float2*>(smem + SH::A_WA);
     float2* wb = reinterpret_cast<float2*>(smem + SH::A_WB);
-    double* red = reinterpret_cast<double*>(smem + SH::O_RED);
+    float2* red = reinterpret_cast<float2*>(smem + SH::O_RED);   // [64] block reduction
     const int tid = threadIdx.x, nthr = blockDim.x;
 
     if (mode == MODE_ITER) {
@@ -173,10 +173,10 @@ __global__ void __launch_bounds__(IMG_THREADS, 1) k_usolve_img(
     float2* X = fft_block<NN, false>(spec, scr, tw, Q, NN);
     for (int i = tid; i < Q * NN; i += nthr) {
         const int q = i / NN, p = i - q * NN;
-        const float d = solve_divisor(s2, p, q, beta, mu_over_tau);
+        const float rd = 1.0f / solve_divisor(s2, p, q, beta, mu_over_tau);
         float2 v = X[i];
-        v.x = v.x / d;
-        v.y = v.y / d;
+        v.x *= rd;
+        v.y *= rd;
         X[i] = v;
     }
     __syncthreads();
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(IMG_THREADS, 1) k_usolve_img(
     };
     load_u(0, ub0);
     cp_async_commit();
-    float du2f = 0.f, u2f = 0.f;
+    float2 du2 = make_float2(0.f, 0.f), u2 = make_float2(0.f, 0.f);
     for (int s = 0; s < SH::NSTRIPE; ++s) {
         float* cur = (s & 1) ? ub1 : ub0;
         if (s + 1 < SH::NSTRIPE) load_u(s + 1, (s & 1) ? ub0 : ub1);
@@ -203,12 +203,11 @@ __global__ void __launch_bounds__(IMG_THREADS, 1) k_usolve_img(
         step_pack_inverse<NN>(Y + r0, 1, NN, S, ca, tid, nthr);
         __syncthreads();
         float2* z = fft_block<NN, true>(ca, cb, tw, S / 2, NN);
-        step_update<NN>(z, cur, S, r0, u, u_hi, u_lo, du2f, u2f, tid, nthr);
+        step_update<NN>(z, cur, S, r0, u, u_hi, u_lo, du2, u2, tid, nthr);
         __syncthreads();
     }
-    const double bdu = block_sum((double)du2f, red);
-    const double bu = block_sum((double)u2f, red);
-    if (tid == 0) step_stop(ctrl, par, mode, bdu, bu);
+    block_sum_ds2(du2, u2, red);
+    if (tid == 0) step_stop(ctrl, par, mode, ds_value(du2), ds_value(u2));
 }
 
 // ---------------------------------------------------------------------------

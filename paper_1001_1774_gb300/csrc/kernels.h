@@ -61,7 +61,7 @@ struct ProdArgs {
     float* gpart;       // grid x N
     float* g_out;       // nullable: when set, the blocks meet at a grid barrier (cooperative
                         // launch) and reduce the partials into g_out = A^T r themselves
-    double* r2part;     // grid
+    float2* r2part;     // grid, double-single ||r||^2 partials
     Ctrl* ctrl;
     int mode;           // MODE_PLAIN or MODE_ITER
     unsigned long long cond;  // cudaGraphConditionalHandle (MODE_ITER inside the loop graph)
@@ -89,7 +89,7 @@ struct QProdArgs {
     const float* y;           // nullable
     float* r;
     float* gpart;             // clusters x N
-    double* r2part;           // clusters
+    float2* r2part;           // clusters, double-single ||r||^2 partials
     Ctrl* ctrl;
     int mode;
     unsigned long long cond;
@@ -118,7 +118,7 @@ void launch_gemm(const CUtensorMap* xh, const CUtensorMap* xl, const CUtensorMap
                  long long budget, cudaStream_t s);
 void launch_gemm_fixup(const float* ws, const int* tile_seg_begin, const int* seg_slot, int M,
                        int tiles_m, int count, const float* F, int ldf, float* out, int ldo,
-                       void* out_hi, void* out_lo, int ldh, double* r2part, const Ctrl* ctrl,
+                       void* out_hi, void* out_lo, int ldh, float2* r2part, const Ctrl* ctrl,
                        int check_skip, cudaStream_t s);
 void launch_split_rows(const float* v, int count, int len, int ld, void* hi, void* lo, int ldh,
                        cudaStream_t s);
@@ -138,7 +138,7 @@ struct RegenProb {
     float* r;            // m
     float* g;            // N, written by the reduction
     float* gslot;        // chunks x N partial slots
-    double* r2slot;      // chunks
+    float2* r2slot;      // chunks, double-single ||r||^2 partials
     Ctrl* ctrl;          // receives r2; with MODE_ITER, ctrl->skip marks a problem as inactive
     int m, N;
     int rows_per_chunk, chunks;

@@ -104,7 +104,7 @@ extern "C" tvcs_status tvcs_apply_noalloc(const float* A, int m, int n, const fl
     const int N = n * n;
     const int P = prod_grid(n, m, g_num_sms[dev]);
     const size_t b_gpart = round256((size_t)P * N * sizeof(float));
-    const size_t b_r2 = round256((size_t)P * sizeof(double));
+    const size_t b_r2 = round256((size_t)P * sizeof(float2));
     const size_t b_ctrl = round256(sizeof(Ctrl));
     if (b_gpart + b_r2 + b_ctrl > kScratchBytes)
         return set_last_error(TVCS_ERR_INVALID_ARG,
@@ -113,7 +113,7 @@ extern "C" tvcs_status tvcs_apply_noalloc(const float* A, int m, int n, const fl
                               m, n, b_gpart + b_r2 + b_ctrl, kScratchBytes);
     unsigned char* base = static_cast<unsigned char*>(g_scratch_ptr[dev]);
     float* gpart = reinterpret_cast<float*>(base);
-    double* r2part = reinterpret_cast<double*>(base + b_gpart);
+    float2* r2part = reinterpret_cast<float2*>(base + b_gpart);
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(base + b_gpart + b_r2);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 

@@ -63,7 +63,7 @@ struct tvcs_uneven {
     int P = 0, maxN = 0, init = 0;
     double beta = 0;
     float *R = nullptr, *F = nullptr, *zero = nullptr, *gslot = nullptr;
-    double* r2slot = nullptr;
+    float2* r2slot = nullptr;
     int* pre = nullptr;
     tvcs::RegenProb *dtab = nullptr, *dtab0 = nullptr;
     tvcs::RegenPlan plan;
@@ -168,7 +168,7 @@ Layout layout_for(const RegenPlan& plan, const std::vector<RegenProb>& probs, in
     return L;
 }
 
-void apply_layout(const Layout& L, float* gslot, double* r2slot, std::vector<RegenProb>* probs)
+void apply_layout(const Layout& L, float* gslot, float2* r2slot, std::vector<RegenProb>* probs)
 {
     for (size_t i = 0; i < probs->size(); ++i) {
         RegenProb& p = (*probs)[i];
@@ -182,7 +182,7 @@ void apply_layout(const Layout& L, float* gslot, double* r2slot, std::vector<Reg
 // Times each candidate plan on the problem set (one warm-up launch, one timed)
 // and returns the fastest.  gslot / r2slot must hold the largest layout.
 tvcs_status autotune(std::vector<RegenProb> probs, int maxN, int per_cluster, RegenProb* dtab,
-                     float* gslot, double* r2slot, int* pre, cudaStream_t s, RegenPlan* best)
+                     float* gslot, float2* r2slot, int* pre, cudaStream_t s, RegenPlan* best)
 {
     std::vector<RegenPlan> cands = candidates(maxN, (int)probs.size());
     if (cands.empty()) return set_last_error(TVCS_ERR_UNSUPPORTED, "no cluster of the regenerating product kernel fits");
@@ -289,7 +289,7 @@ tvcs_status regen_init(tvcs_ctx* h)
     const size_t gfl = max_layout_floats(one, h->N, 2, &rslots);
     if (gfl == 0) return set_last_error(TVCS_ERR_UNSUPPORTED, "no cluster of the regenerating product kernel fits");
     RCKS(ralloc((void**)&g->gslot, sizeof(float) * gfl));
-    RCKS(ralloc((void**)&g->r2slot, sizeof(double) * rslots));
+    RCKS(ralloc((void**)&g->r2slot, sizeof(float2) * rslots));
     RCKS(ralloc((void**)&g->pre, sizeof(int) * 4));
     RCKS(ralloc((void**)&g->dtab, sizeof(RegenProb) * kTab));
     RegenPlan plan;
@@ -511,7 +511,7 @@ tvcs_status build_uneven(const tvcs_handle* hs, int count, const double* mu, tvc
     const size_t gfl = max_layout_floats(probs, u->maxN, 16, &rslots);
     if (gfl == 0) return set_last_error(TVCS_ERR_UNSUPPORTED, "no cluster of the regenerating product kernel fits");
     RCKS(ralloc((void**)&u->gslot, sizeof(float) * gfl));
-    RCKS(ralloc((void**)&u->r2slot, sizeof(double) * rslots));
+    RCKS(ralloc((void**)&u->r2slot, sizeof(float2) * rslots));
     RCKS(autotune(probs, u->maxN, 16, u->dtab, u->gslot, u->r2slot, u->pre, s, &u->plan));
     Layout L = layout_for(u->plan, probs, 16);
     apply_layout(L, u->gslot, u->r2slot, &probs);
@@ -653,7 +653,7 @@ tvcs_status solve_uneven(const tvcs_handle* hs, int count, const float* const* f
             r.iters = c.it;
             r.status = st;
             r.stopped_by_tol = c.stop_by_tol;
-            r.rel_change = c.relchg;
+            r.rel_change = ctrl_relchg(c);
             r.tv = c.tv;
             r.resid2 = c.r2;
             r.objective = c.tv + 0.5 * sg.mu * c.r2;

@@ -336,7 +336,7 @@ tvcs_status run_loop(tvcs_ctx* h, int iters, double tol, tvcs_result* res)
         res->iters = c.it;
         res->status = st;
         res->stopped_by_tol = c.stop_by_tol;
-        res->rel_change = c.relchg;
+        res->rel_change = ctrl_relchg(c);
         res->tv = c.tv;
         res->resid2 = c.r2;
         res->objective = c.tv + 0.5 * h->mu * c.r2;
@@ -473,7 +473,7 @@ tvcs_status create_impl(tvcs_ctx* h, const float* A, uint64_t seed, const int32_
     CKS(alloc((void**)&h->s2, sizeof(float) * (size_t)h->n));
     CKS(alloc((void**)&h->gpart, sizeof(float) * N * (size_t)h->P));
     CKS(alloc((void**)&h->gpart2, sizeof(float) * N * (size_t)h->P));
-    CKS(alloc((void**)&h->r2part, sizeof(double) * (size_t)h->P));
+    CKS(alloc((void**)&h->r2part, sizeof(float2) * (size_t)h->P));
     CKS(alloc((void**)&h->part, sizeof(double) * nparts));
     CKS(alloc((void**)&h->ctrl, sizeof(Ctrl)));
     CK(cudaMallocHost((void**)&h->hctrl, sizeof(Ctrl)));

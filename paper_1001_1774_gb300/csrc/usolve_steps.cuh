@@ -178,14 +178,14 @@ __device__ __forceinline__ void step_pack_inverse(const float2* spec, int rs, in
 }
 
 // a4-a5: u <- u + d for the owned rows, d = z / n^2 from the packed inverse
-// transforms z; uold points at row r0 of the old u (row stride NN).  Adds the
-// thread's binary32 partial sums of d^2 and u_old^2 to du2f, u2f.  When u_hi
+// transforms z; uold points at row r0 of the old u (row stride NN).  Adds d^2
+// and u_old^2 to the thread's double-single sums du2, u2.  When u_hi
 // is set, the new u is also stored as bf16 hi/lo planes (round to nearest even
 // of u, then of the exact remainder).
 template <int NN>
 __device__ __forceinline__ void step_update(const float2* z, const float* uold, int R, int r0,
                                             float* u, unsigned short* u_hi, unsigned short* u_lo,
-                                            float& du2f, float& u2f, int tid, int nthr)
+                                            float2& du2, float2& u2, int tid, int nthr)
 {
     const float sc = 1.0f / (float)(NN * NN);
     for (int i = tid; i < (R / 2) * NN; i += nthr) {
@@ -196,8 +196,8 @@ __device__ __forceinline__ void step_update(const float2* z, const float* uold, 
             const int lr = 2 * j + h;
             const float d = (h == 0 ? v.x : v.y) * sc;
             const float o = uold[lr * NN + c];
-            du2f = fmaf(d, d, du2f);
-            u2f = fmaf(o, o, u2f);
+            du2 = ds_add(du2, ds_sq(d));
+            u2 = ds_add(u2, ds_sq(o));
             const float nw = o + d;
             u[(r0 + lr) * NN + c] = nw;
             if (u_hi) {
@@ -213,15 +213,15 @@ __device__ __forceinline__ void step_update(const float2* z, const float* uold, 
     }
 }
 
-// a5: eq. (stop) and the loop bookkeeping of one image, from the binary64 sums
-// of ||u^{k+1} - u^k||^2 and ||u^k||^2 (one thread).
+// a5: eq. (stop) and the loop bookkeeping of one image, from the sums
+// ||u^{k+1} - u^k||^2 and ||u^k||^2 (one thread; the host derives the relative
+// change from du2 and u2).
 __device__ __forceinline__ void step_stop(Ctrl* ctrl, int par, int mode, double tdu, double tu)
 {
     if (ctrl->algo == 0) ctrl->pending = 1;   // u moved: its multiplier update is due
     ctrl->wpar = par ^ 1;
     ctrl->du2 = tdu;
     ctrl->u2 = tu;
-    ctrl->relchg = tu > 0.0 ? sqrt(tdu / tu) : (tdu > 0.0 ? INFINITY : 0.0);
     if (mode == MODE_ITER) {
         const int it = ctrl->it + 1;
         ctrl->it = it;
