@@ -34,7 +34,7 @@ namespace cg = cooperative_groups;
 
 namespace tvcs {
 
-constexpr int US_THREADS = 512;
+constexpr int US_THREADS = 256;
 
 template <int NN, int C>
 struct UsolveShape {
