@@ -80,6 +80,10 @@ typedef struct {
                             regenerates A's entries from the seed given to tvcs_create (A must
                             be NULL and precision TVCS_PREC_FP32; the entries are the binary32
                             values the generator would store, so both modes apply the same A) */
+    int batch_compact;   /* 1 (default): in a shared-A batch (tvcs_solve_batched), an image that
+                            met eq. (stop) leaves the tensor-core GEMMs after its last iteration:
+                            the running images are packed into the leading columns and the GEMMs
+                            shrink with them; 0: every image keeps its column to the end */
 } tvcs_options;
 
 typedef struct {

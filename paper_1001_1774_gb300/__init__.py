@@ -45,7 +45,8 @@ class tvcs_options(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int), ("tau", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("precision", ctypes.c_int), ("init", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("power_iters", ctypes.c_int), ("timeout_cycles", ctypes.c_longlong),
-                ("host_loop", ctypes.c_int), ("a_mode", ctypes.c_int)]
+                ("host_loop", ctypes.c_int), ("a_mode", ctypes.c_int),
+                ("batch_compact", ctypes.c_int)]
 
 
 class tvcs_result(ctypes.Structure):

@@ -33,15 +33,38 @@ __global__ void k_batch_r2(const float2* __restrict__ r2part, int tiles, Ctrl* _
     if (threadIdx.x == 0) ctrls[blockIdx.x].r2 = ds_value(s);
 }
 
-// Continue while any image runs and the loop bound holds.
+// Continue while any image runs and the loop bound holds.  With slot tables
+// (count <= blockDim.x = 256): the running images, in image order, take slots
+// 0 .. nact-1 for the next iteration (a block-wide exclusive prefix sum of the
+// running flags); an image that stopped gets slot -1.
 __global__ void k_batch_cond(const Ctrl* __restrict__ ctrls, int count, Ctrl* __restrict__ bctrl,
-                             cudaGraphConditionalHandle cond, int set_cond)
+                             cudaGraphConditionalHandle cond, int set_cond,
+                             int* __restrict__ slot_img, int* __restrict__ img_slot)
 {
     __shared__ int any;
+    __shared__ int wtot[8];
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
     for (int b = threadIdx.x; b < count; b += blockDim.x)
         if (!ctrls[b].done && ctrls[b].error == ERR_NONE) atomicOr(&any, 1);
+    if (slot_img) {
+        const int b = threadIdx.x, lane = b & 31, w = b >> 5;
+        const bool run = b < count && !ctrls[b].done && ctrls[b].error == ERR_NONE;
+        const unsigned m = __ballot_sync(0xffffffffu, run);
+        if (lane == 0) wtot[w] = __popc(m);
+        __syncthreads();
+        int base = 0, total = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            if (k < w) base += wtot[k];
+            total += wtot[k];
+        }
+        const int slot = base + __popc(m & ((1u << lane) - 1u));
+        if (b < count) {
+            img_slot[b] = run ? slot : -1;
+            if (run) slot_img[slot] = b;
+        }
+        if (b == 0) bctrl->nact = total;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         const int lc = ++bctrl->loops;
@@ -52,9 +75,10 @@ __global__ void k_batch_cond(const Ctrl* __restrict__ ctrls, int count, Ctrl* __
 }
 
 void launch_batch_cond(const Ctrl* ctrls, int count, Ctrl* bctrl, unsigned long long cond,
-                       int set_cond, cudaStream_t s)
+                       int set_cond, cudaStream_t s, int* slot_img, int* img_slot)
 {
-    k_batch_cond<<<1, 256, 0, s>>>(ctrls, count, bctrl, (cudaGraphConditionalHandle)cond, set_cond);
+    k_batch_cond<<<1, 256, 0, s>>>(ctrls, count, bctrl, (cudaGraphConditionalHandle)cond, set_cond,
+                                   slot_img, img_slot);
 }
 
 // A_eff = hi + lo (exact in binary32) from the two bf16 planes.
@@ -103,7 +127,8 @@ tvcs_status balloc(void** p, size_t bytes)
 void free_buffers(tvcs_batch* b)
 {
     void* bufs[] = {b->U, b->W, b->L, b->G, b->R, b->F, b->mu, b->Uh, b->Ul, b->Rh, b->Rl,
-                    b->ctrls, b->bctrl, b->r2part, b->part, b->ws, b->tsb1, b->ss1, b->tsb2, b->ss2};
+                    b->ctrls, b->bctrl, b->r2part, b->part, b->ws, b->tsb1, b->ss1, b->tsb2, b->ss2,
+                    b->slot_img, b->img_slot};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (b->hctrls) cudaFreeHost(b->hctrls);
@@ -115,6 +140,7 @@ void free_buffers(tvcs_batch* b)
     b->ctrls = b->bctrl = b->hctrls = b->hbctrl = nullptr;
     b->r2part = nullptr;
     b->part = nullptr;
+    b->slot_img = b->img_slot = nullptr;
     b->ws = nullptr;
     b->tsb1 = b->ss1 = b->tsb2 = b->ss2 = nullptr;
     b->exec = nullptr;
@@ -141,10 +167,10 @@ tvcs_status make_maps(tvcs_ctx* h, int count)
               make_bf16_map(&b->mAl, h->P1, h->N, h->m, h->N, 128) &&
               make_bf16_map(&b->mAth, b->Ath, h->m, h->N, b->mpad, 128) &&
               make_bf16_map(&b->mAtl, b->Atl, h->m, h->N, b->mpad, 128) &&
-              make_bf16_map(&b->mUh, b->Uh, h->N, count, h->N, 256) &&
-              make_bf16_map(&b->mUl, b->Ul, h->N, count, h->N, 256) &&
-              make_bf16_map(&b->mRh, b->Rh, h->m, count, b->mpad, 256) &&
-              make_bf16_map(&b->mRl, b->Rl, h->m, count, b->mpad, 256);
+              make_bf16_map(&b->mUh, b->Uh, h->N, count, h->N, GEMM_Y_BOX) &&
+              make_bf16_map(&b->mUl, b->Ul, h->N, count, h->N, GEMM_Y_BOX) &&
+              make_bf16_map(&b->mRh, b->Rh, h->m, count, b->mpad, GEMM_Y_BOX) &&
+              make_bf16_map(&b->mRl, b->Rl, h->m, count, b->mpad, GEMM_Y_BOX);
     if (!ok) return set_last_error(TVCS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     return TVCS_OK;
 }
@@ -221,6 +247,8 @@ tvcs_status ensure_batch(tvcs_ctx* h, int count)
         BCKS(balloc((void**)&b->bctrl, sizeof(Ctrl)));
         BCKS(balloc((void**)&b->r2part, sizeof(float2) * B * b->p1.tiles_m));
         BCKS(balloc((void**)&b->part, sizeof(double) * B * 2 * ((N + 255) / 256)));
+        BCKS(balloc((void**)&b->slot_img, sizeof(int) * B));
+        BCKS(balloc((void**)&b->img_slot, sizeof(int) * B));
         BCK(cudaMallocHost((void**)&b->hctrls, sizeof(Ctrl) * B));
         BCK(cudaMallocHost((void**)&b->hbctrl, sizeof(Ctrl)));
         BCK(cudaMemsetAsync(b->Rh, 0, sizeof(unsigned short) * B * b->mpad, s));
@@ -238,20 +266,24 @@ tvcs_status ensure_batch(tvcs_ctx* h, int count)
 }
 
 // R = A U - F (R planes, ||r||^2 partials), then G = A^T R, for `count` images.
-void batch_products(tvcs_ctx* h, int count, bool subtract_f, cudaStream_t s)
+// compact: the GEMMs take the first bctrl->nact columns, column j being image
+// slot_img[j] (the U and R planes are stored in that column order).
+void batch_products(tvcs_ctx* h, int count, bool subtract_f, cudaStream_t s, bool compact = false)
 {
     tvcs_batch* b = h->batch;
     const long long budget = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : (1LL << 31);
-    launch_gemm(&b->mAh, &b->mAl, &b->mUh, &b->mUl, b->p1, b->ws, b->bctrl, 0, budget, s);
+    const int* nact = compact ? &b->bctrl->nact : nullptr;
+    const int* slot = compact ? b->slot_img : nullptr;
+    launch_gemm(&b->mAh, &b->mAl, &b->mUh, &b->mUl, b->p1, b->ws, b->bctrl, 0, budget, s, count, nact);
     launch_gemm_fixup(b->ws, b->tsb1, b->ss1, h->m, b->p1.tiles_m, count,
                       subtract_f ? b->F : nullptr, h->m, b->R, h->m, b->Rh, b->Rl, b->mpad,
-                      b->r2part, b->bctrl, 0, s);
-    launch_gemm(&b->mAth, &b->mAtl, &b->mRh, &b->mRl, b->p2, b->ws, b->bctrl, 0, budget, s);
+                      b->r2part, b->bctrl, 0, s, slot, nact);
+    launch_gemm(&b->mAth, &b->mAtl, &b->mRh, &b->mRl, b->p2, b->ws, b->bctrl, 0, budget, s, count, nact);
     launch_gemm_fixup(b->ws, b->tsb2, b->ss2, h->N, b->p2.tiles_m, count, nullptr, 0, b->G, h->N,
-                      nullptr, nullptr, 0, nullptr, b->bctrl, 0, s);
+                      nullptr, nullptr, 0, nullptr, b->bctrl, 0, s, slot, nact);
 }
 
-TvArgs batch_tv_args(tvcs_ctx* h, int count, int mode)
+TvArgs batch_tv_args(tvcs_ctx* h, int count, int mode, bool compact = false)
 {
     tvcs_batch* b = h->batch;
     TvArgs a{};
@@ -273,6 +305,7 @@ TvArgs batch_tv_args(tvcs_ctx* h, int count, int mode)
     a.tau = (float)h->tau;
     a.u_hi = b->Uh;
     a.u_lo = b->Ul;
+    a.img_slot = compact ? b->img_slot : nullptr;
     return a;
 }
 
@@ -301,10 +334,12 @@ tvcs_status build_batch_graph(tvcs_ctx* h, int count)
     cudaStream_t cs = h->cap_stream;
     BCK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
                                       cudaStreamCaptureModeThreadLocal));
-    TvArgs a = batch_tv_args(h, count, MODE_ITER);
+    const bool compact = h->opt.batch_compact != 0;
+    TvArgs a = batch_tv_args(h, count, MODE_ITER, compact);
     batch_usolve(h, a, cs);
-    batch_products(h, count, true, cs);
-    k_batch_cond<<<1, 256, 0, cs>>>(b->ctrls, count, b->bctrl, ch, 1);
+    batch_products(h, count, true, cs, compact);
+    launch_batch_cond(b->ctrls, count, b->bctrl, (unsigned long long)ch, 1, cs,
+                      compact ? b->slot_img : nullptr, compact ? b->img_slot : nullptr);
     cudaGraph_t captured = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &captured);
     if (e != cudaSuccess)
@@ -350,8 +385,8 @@ tvcs_status time_batch_stage(tvcs_ctx* h, int stage, int reps, double* ms)
     BCK(cudaEventRecord(h->ev0, s));
     for (int i = 0; i < reps; ++i) {
         if (stage == 3) {
-            launch_gemm(&b->mAh, &b->mAl, &b->mUh, &b->mUl, b->p1, b->ws, b->bctrl, 0, budget, s);
-            launch_gemm(&b->mAth, &b->mAtl, &b->mRh, &b->mRl, b->p2, b->ws, b->bctrl, 0, budget, s);
+            launch_gemm(&b->mAh, &b->mAl, &b->mUh, &b->mUl, b->p1, b->ws, b->bctrl, 0, budget, s, count);
+            launch_gemm(&b->mAth, &b->mAtl, &b->mRh, &b->mRl, b->p2, b->ws, b->bctrl, 0, budget, s, count);
         } else if (stage == 4) {
             launch_gemm_fixup(b->ws, b->tsb1, b->ss1, h->m, b->p1.tiles_m, count, b->F, h->m, b->R,
                               h->m, b->Rh, b->Rl, b->mpad, b->r2part, b->bctrl, 0, s);
@@ -407,6 +442,14 @@ tvcs_status solve_batch(tvcs_ctx* h, int count, const float* const* f, float* co
     BCK(cudaMemcpyAsync(b->ctrls, b->hctrls, sizeof(Ctrl) * count, cudaMemcpyHostToDevice, s));
     memset(b->hbctrl, 0, sizeof(Ctrl));
     b->hbctrl->loops_max = h->opt.max_iter + 2;
+    b->hbctrl->nact = count;   // every image starts in its own column (identity slots)
+    {
+        std::vector<int> ident(count);
+        for (int i = 0; i < count; ++i) ident[i] = i;
+        BCK(cudaMemcpyAsync(b->slot_img, ident.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s));
+        BCK(cudaMemcpyAsync(b->img_slot, ident.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s));
+        BCK(cudaStreamSynchronize(s));   // the host vector goes out of scope
+    }
     BCK(cudaMemcpyAsync(b->bctrl, b->hbctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
     // u^0 = A^T f (reading C3) or 0: G = A^T F through the second GEMM.
     if (h->opt.init == TVCS_INIT_ZERO) {
@@ -414,7 +457,7 @@ tvcs_status solve_batch(tvcs_ctx* h, int count, const float* const* f, float* co
     } else {
         launch_split_rows(b->F, count, h->m, h->m, b->Rh, b->Rl, b->mpad, s);
         const long long budget = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : (1LL << 31);
-        launch_gemm(&b->mAth, &b->mAtl, &b->mRh, &b->mRl, b->p2, b->ws, b->bctrl, 0, budget, s);
+        launch_gemm(&b->mAth, &b->mAtl, &b->mRh, &b->mRl, b->p2, b->ws, b->bctrl, 0, budget, s, count);
         launch_gemm_fixup(b->ws, b->tsb2, b->ss2, h->N, b->p2.tiles_m, count, nullptr, 0, b->U,
                           h->N, nullptr, nullptr, 0, nullptr, b->bctrl, 0, s);
     }

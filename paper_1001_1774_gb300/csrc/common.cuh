@@ -35,6 +35,7 @@ struct Ctrl {
     double lam_max;    // max_i ||lambda_i||
     double vec2;       // ||g||^2 of the last gathered vector (power iteration)
     unsigned long long gbar;  // monotone arrival counter of the product kernel's grid barrier
+    int nact;          // batch control block: images still iterating (the GEMMs' active columns)
 };
 
 // sqrt(du2 / u2), the relative change of eq. (stop) (host side).

@@ -27,6 +27,7 @@ struct tvcs_batch {
     float* ws = nullptr;           // stream-K partial tiles
     tvcs::GemmPlan p1, p2;               // R = A U - F (M = m, K = N) and G = A^T R (M = N, K = m)
     int *tsb1 = nullptr, *ss1 = nullptr, *tsb2 = nullptr, *ss2 = nullptr;
+    int *slot_img = nullptr, *img_slot = nullptr;   // compaction: column -> image, image -> column
     CUtensorMap mAh, mAl, mAth, mAtl, mUh, mUl, mRh, mRl;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;

@@ -42,6 +42,7 @@ constexpr int GM_BN = 256;
 constexpr int GM_NST = 2;
 constexpr uint32_t GM_A_BYTES = GM_BM * GM_BK * 2;            // 16 KB
 constexpr uint32_t GM_B_BYTES = GM_BN * GM_BK * 2;            // 32 KB
+constexpr uint32_t GM_YBOX_BYTES = GEMM_Y_BOX * GM_BK * 2;    // one 64-row box of a Y tile
 constexpr uint32_t GM_STAGE = 2 * GM_A_BYTES + 2 * GM_B_BYTES; // 96 KB
 constexpr uint32_t GM_TMEM_COLS = 2 * GM_BN;                  // two accumulators
 constexpr size_t GM_SMEM = 1024 + GM_NST * GM_STAGE + 256;
@@ -91,10 +92,11 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t smem_addr)
     return d;
 }
 
-// Instruction descriptor: BF16 x BF16 -> FP32, both K-major, M = 128, N = BN.
-__host__ __device__ constexpr uint32_t gemm_idesc()
+// Instruction descriptor: BF16 x BF16 -> FP32, both K-major, M = 128, N = nb
+// (a multiple of 16, at most BN).
+__host__ __device__ constexpr uint32_t gemm_idesc(int nb)
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GM_BN >> 3) << 17) |
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(nb >> 3) << 17) |
            ((uint32_t)(GM_BM >> 4) << 24);
 }
 
@@ -120,13 +122,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
 // ---------------------------------------------------------------------------
 // The GEMM.  tiles_m output tiles of 128 rows, kblocks K blocks of 64; block c
 // owns iterations [c W / G, (c+1) W / G) of W = tiles_m * kblocks.  Partial
-// tile (c, j) goes to ws + (c * smax + j) * BN * 128 as [column][row].
+// tile (c, j) goes to ws + (c * smax + j) * BN * 128 as [column][row].  Only
+// the first nb = roundup(min(ncols, *nact), 32) columns take part: the Y tile
+// is loaded as ceil(nb / 64) boxes of 64 rows, the MMAs run with N = nb and the
+// partial tiles get nb columns.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(192, 1)
     k_gemm_bf16x3(const __grid_constant__ CUtensorMap tXh, const __grid_constant__ CUtensorMap tXl,
                   const __grid_constant__ CUtensorMap tYh, const __grid_constant__ CUtensorMap tYl,
                   int tiles_m, int kblocks, float* __restrict__ ws, int smax,
-                  Ctrl* __restrict__ ctrl, int check_skip, long long budget)
+                  Ctrl* __restrict__ ctrl, int check_skip, long long budget,
+                  int ncols, const int* __restrict__ nact)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
@@ -138,6 +144,11 @@ __global__ void __launch_bounds__(192, 1)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(tempty + 2);
 
     if (check_skip && ctrl->skip) return;
+    int nb = min(ncols, GM_BN);   // columns of the MMAs and of the partial tiles
+    if (nact) nb = min(nb, *nact);
+    nb = min(GM_BN, max(32, (nb + 31) & ~31));
+    const int ybox = (nb + GEMM_Y_BOX - 1) / GEMM_Y_BOX;
+    const uint32_t stage_bytes = 2 * GM_A_BYTES + 2 * (uint32_t)ybox * GM_YBOX_BYTES;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long W = (long long)tiles_m * kblocks;
     const int G = gridDim.x;
@@ -180,11 +191,15 @@ __global__ void __launch_bounds__(192, 1)
                 }
                 const int t = (int)(w / kblocks), kb = (int)(w % kblocks);
                 unsigned char* st = smem + (size_t)s * GM_STAGE;
-                mbar_arrive_expect_tx(&full[s], GM_STAGE);
+                mbar_arrive_expect_tx(&full[s], stage_bytes);
                 tma_load_2d(st, &tXh, kb * GM_BK, t * GM_BM, &full[s]);
                 tma_load_2d(st + GM_A_BYTES, &tXl, kb * GM_BK, t * GM_BM, &full[s]);
-                tma_load_2d(st + 2 * GM_A_BYTES, &tYh, kb * GM_BK, 0, &full[s]);
-                tma_load_2d(st + 2 * GM_A_BYTES + GM_B_BYTES, &tYl, kb * GM_BK, 0, &full[s]);
+                for (int j = 0; j < ybox; ++j) {   // 64-row boxes, 1024-byte aligned
+                    tma_load_2d(st + 2 * GM_A_BYTES + j * GM_YBOX_BYTES, &tYh, kb * GM_BK,
+                                j * GEMM_Y_BOX, &full[s]);
+                    tma_load_2d(st + 2 * GM_A_BYTES + GM_B_BYTES + j * GM_YBOX_BYTES, &tYl,
+                                kb * GM_BK, j * GEMM_Y_BOX, &full[s]);
+                }
             }
             // leave no copy in flight
             const long long n_issued = it;
@@ -195,7 +210,7 @@ __global__ void __launch_bounds__(192, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            const uint32_t idesc = gemm_idesc();
+            const uint32_t idesc = gemm_idesc(nb);
             bool ok = true;
             long long it = 0;
             int seg = 0;
@@ -255,7 +270,7 @@ __global__ void __launch_bounds__(192, 1)
             }
             tc_fence_after();
             float* dst = ws + ((size_t)blockIdx.x * smax + seg) * (size_t)GM_BN * GM_BM;
-            for (int c0 = 0; c0 < GM_BN; c0 += 32) {
+            for (int c0 = 0; c0 < nb; c0 += 32) {
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * GM_BN + c0), v);
 #pragma unroll
@@ -280,8 +295,10 @@ __global__ void __launch_bounds__(192, 1)
 
 // ---------------------------------------------------------------------------
 // Fix-up: D = sum of a tile's partials (in K order), then the epilogue.
-// Block (t, j): rows [128 t, 128 t + 128) of the columns (images) 8 j .. 8 j + 7.
-// mode 1: R = D - F, R planes, ||r_b||^2 partial;  mode 2: G = D.
+// Block (t, j): rows [128 t, 128 t + 128) of the columns 8 j .. 8 j + 7; column c
+// belongs to image slot_img[c] (c itself when slot_img is null), and with nact
+// set only columns below *nact take part.
+// mode 1: R = D - F, R planes (column order), ||r_b||^2 partial;  mode 2: G = D.
 // ---------------------------------------------------------------------------
 constexpr int FX_B = 8;     // images per fix-up block
 constexpr int FX_SEG = 6;   // segments a tile usually has at most (more are added in a second pass)
@@ -291,11 +308,14 @@ __global__ void __launch_bounds__(128) k_gemm_fixup(
     const int* __restrict__ seg_slot, int M, int count, const float* __restrict__ F, int ldf,
     float* __restrict__ out, int ldo, __nv_bfloat16* __restrict__ out_hi,
     __nv_bfloat16* __restrict__ out_lo, int ldh, float2* __restrict__ r2part, int tiles_m,
-    const Ctrl* __restrict__ ctrl, int check_skip)
+    const Ctrl* __restrict__ ctrl, int check_skip, const int* __restrict__ slot_img,
+    const int* __restrict__ nact)
 {
     __shared__ float2 red[4][FX_B];
     if (check_skip && ctrl->skip) return;
     const int t = blockIdx.x, b0 = blockIdx.y * FX_B;
+    if (nact) count = min(count, *nact);
+    if (b0 >= count) return;   // uniform across the block
     const int row = t * GM_BM + threadIdx.x;
     const int s0 = tile_seg_begin[t], s1 = tile_seg_begin[t + 1];
     const int ns = s1 - s0;
@@ -311,24 +331,34 @@ __global__ void __launch_bounds__(128) k_gemm_fixup(
             v[k][q] = (q < ns && b0 + k < count)
                           ? ws[((size_t)slot[q] * GM_BN + b0 + k) * GM_BM + threadIdx.x]
                           : 0.f;
+    // the columns' images and their F entries, loaded with the partials
+    int img[FX_B];
+    float fv[FX_B];
+#pragma unroll
+    for (int k = 0; k < FX_B; ++k) {
+        const int c = b0 + k;
+        img[k] = c < count ? (slot_img ? __ldg(slot_img + c) : c) : 0;
+        fv[k] = (F && c < count && row < M) ? __ldg(F + (size_t)img[k] * ldf + row) : 0.f;
+    }
     float2 sq[FX_B];   // double-single squares
 #pragma unroll
     for (int k = 0; k < FX_B; ++k) {
-        const int b = b0 + k;
+        const int c = b0 + k;   // column
         sq[k] = make_float2(0.f, 0.f);
-        if (b >= count) continue;
+        if (c >= count) continue;
+        const int b = img[k];
         float d = 0.f;   // the tile's segments in K order
 #pragma unroll
         for (int q = 0; q < FX_SEG; ++q) d += v[k][q];
         for (int s = s0 + FX_SEG; s < s1; ++s)
-            d += ws[((size_t)seg_slot[s] * GM_BN + b) * GM_BM + threadIdx.x];
+            d += ws[((size_t)seg_slot[s] * GM_BN + c) * GM_BM + threadIdx.x];
         if (row < M) {
-            if (F) d -= F[(size_t)b * ldf + row];
+            d -= fv[k];
             out[(size_t)b * ldo + row] = d;
             if (out_hi) {
                 const __nv_bfloat16 h = __float2bfloat16_rn(d);
-                out_hi[(size_t)b * ldh + row] = h;
-                out_lo[(size_t)b * ldh + row] = __float2bfloat16_rn(d - __bfloat162float(h));
+                out_hi[(size_t)c * ldh + row] = h;
+                out_lo[(size_t)c * ldh + row] = __float2bfloat16_rn(d - __bfloat162float(h));
             }
             sq[k] = ds_sq(d);
         }
@@ -343,7 +373,8 @@ __global__ void __launch_bounds__(128) k_gemm_fixup(
         __syncthreads();
         if (threadIdx.x < FX_B && b0 + (int)threadIdx.x < count) {
             const int k = threadIdx.x;
-            r2part[(size_t)(b0 + k) * tiles_m + t] =
+            const int b = slot_img ? slot_img[b0 + k] : b0 + k;
+            r2part[(size_t)b * tiles_m + t] =
                 ds_add(ds_add(ds_add(red[0][k], red[1][k]), red[2][k]), red[3][k]);
         }
     }
@@ -462,22 +493,22 @@ cudaError_t gemm_configure()
 
 void launch_gemm(const CUtensorMap* xh, const CUtensorMap* xl, const CUtensorMap* yh,
                  const CUtensorMap* yl, const GemmPlan& p, float* ws, Ctrl* ctrl, int check_skip,
-                 long long budget, cudaStream_t s)
+                 long long budget, cudaStream_t s, int ncols, const int* nact)
 {
     k_gemm_bf16x3<<<p.grid, 192, GM_SMEM, s>>>(*xh, *xl, *yh, *yl, p.tiles_m, p.kblocks, ws,
-                                               p.smax, ctrl, check_skip, budget);
+                                               p.smax, ctrl, check_skip, budget, ncols, nact);
 }
 
 void launch_gemm_fixup(const float* ws, const int* tile_seg_begin, const int* seg_slot, int M,
                        int tiles_m, int count, const float* F, int ldf, float* out, int ldo,
                        void* out_hi, void* out_lo, int ldh, float2* r2part, const Ctrl* ctrl,
-                       int check_skip, cudaStream_t s)
+                       int check_skip, cudaStream_t s, const int* slot_img, const int* nact)
 {
     dim3 grid(tiles_m, (count + FX_B - 1) / FX_B);
     k_gemm_fixup<<<grid, 128, 0, s>>>(ws, tile_seg_begin, seg_slot, M, count, F, ldf, out, ldo,
                                       reinterpret_cast<__nv_bfloat16*>(out_hi),
                                       reinterpret_cast<__nv_bfloat16*>(out_lo), ldh, r2part,
-                                      tiles_m, ctrl, check_skip);
+                                      tiles_m, ctrl, check_skip, slot_img, nact);
 }
 
 void launch_split_rows(const float* v, int count, int len, int ld, void* hi, void* lo, int ldh,

@@ -66,7 +66,8 @@ struct UsolveShape {
 // control block ctrl + b and, when mu_img is set, mu = mu_img[b] (and tau =
 // tau_img[b] when that is set too).  When u_hi is
 // set, the new u is also written as bfloat16 hi/lo planes (operand of the
-// batched products).
+// batched products), at row img_slot[b] when img_slot is set (a compacted
+// batch; -1: the image has stopped and writes no planes), else at row b.
 // a4: the half spectra of the owned rows as in step_split (rows r0 + 2j and
 // r0 + 2j + 1 from packed transform j), each column q stored into the column
 // buffer of block q / QC: col[(q mod QC) NN + row].
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(US_THREADS, 1) k_usolve_cluster(
     const float* __restrict__ s2_g, float beta, float mu_over_tau, float mu,
     Ctrl* __restrict__ ctrl, int mode, const float* __restrict__ mu_img,
     const float* __restrict__ tau_img, float tau, unsigned short* __restrict__ u_hi,
-    unsigned short* __restrict__ u_lo)
+    unsigned short* __restrict__ u_lo, const int* __restrict__ img_slot)
 {
     using S = UsolveShape<NN, C>;
     constexpr int R = S::R, Q = S::Q, QC = S::QC, N = NN * NN;
@@ -106,8 +107,13 @@ __global__ void __launch_bounds__(US_THREADS, 1) k_usolve_cluster(
         g += (size_t)b * N;
         ctrl += b;
         if (u_hi) {
-            u_hi += (size_t)b * N;
-            u_lo += (size_t)b * N;
+            const int row = img_slot ? img_slot[b] : b;
+            if (row >= 0) {
+                u_hi += (size_t)row * N;
+                u_lo += (size_t)row * N;
+            } else {
+                u_hi = u_lo = nullptr;
+            }
         }
         if (mu_img) {
             mu = mu_img[b];
@@ -305,7 +311,7 @@ static void launch_usolve_t(const TvArgs& a, cudaStream_t s)
     cfg.numAttrs = a.pdl ? 2 : 1;
     cudaLaunchKernelEx(&cfg, k_usolve_cluster<NN, C>, a.u, a.w, a.lam, a.g, a.rhs_out, a.tw, a.s2,
                        a.beta, a.mu_over_tau, a.mu, a.ctrl, a.mode, a.mu_img, a.tau_img,
-                       a.tau, a.u_hi, a.u_lo);
+                       a.tau, a.u_hi, a.u_lo, a.img_slot);
 }
 
 // Cluster sizes available per n: {16, 8} where both give an even row count and

@@ -73,14 +73,16 @@ __device__ __forceinline__ void cp_async_wait_one()
 }  // namespace
 
 // Image b = blockIdx.x uses u + b N, w/lambda + 4 b N, g + b N, ctrl + b and,
-// when mu_img is set, mu_img[b] (and tau_img[b] when set).
+// when mu_img is set, mu_img[b] (and tau_img[b] when set); its bf16 planes go
+// to row img_slot[b] when img_slot is set (-1: stopped, no planes), else row b.
 template <int NN, int S>
 __global__ void __launch_bounds__(IMG_THREADS, 1) k_usolve_img(
     float* __restrict__ u, float* __restrict__ wbuf, float* __restrict__ lbuf,
     const float* __restrict__ g, const float2* __restrict__ tw_g, const float* __restrict__ s2_g,
     float beta, float mu_over_tau, float mu, Ctrl* __restrict__ ctrl, int mode,
     const float* __restrict__ mu_img, const float* __restrict__ tau_img, float tau,
-    unsigned short* __restrict__ u_hi, unsigned short* __restrict__ u_lo)
+    unsigned short* __restrict__ u_hi, unsigned short* __restrict__ u_lo,
+    const int* __restrict__ img_slot)
 {
     using SH = ImgShape<NN, S>;
     constexpr int N = NN * NN, Q = SH::Q, CPR = NN / 4, WL = (S + 1) * NN;
@@ -92,8 +94,13 @@ __global__ void __launch_bounds__(IMG_THREADS, 1) k_usolve_img(
         g += (size_t)b * N;
         ctrl += b;
         if (u_hi) {
-            u_hi += (size_t)b * N;
-            u_lo += (size_t)b * N;
+            const int row = img_slot ? img_slot[b] : b;
+            if (row >= 0) {
+                u_hi += (size_t)row * N;
+                u_lo += (size_t)row * N;
+            } else {
+                u_hi = u_lo = nullptr;
+            }
         }
         if (mu_img) {
             mu = mu_img[b];
@@ -241,7 +248,7 @@ void launch_usolve_img(int n, const TvArgs& a, cudaStream_t s)
     if (n == NN) {                                                                               \
         k_usolve_img<NN, S><<<a.nimg > 0 ? a.nimg : 1, IMG_THREADS, ImgShape<NN, S>::SMEM, s>>>( \
             a.u, a.w, a.lam, a.g, a.tw, a.s2, a.beta, a.mu_over_tau, a.mu, a.ctrl, a.mode,       \
-            a.mu_img, a.tau_img, a.tau, a.u_hi, a.u_lo);                                         \
+            a.mu_img, a.tau_img, a.tau, a.u_hi, a.u_lo, a.img_slot);                                         \
         return;                                                                                  \
     }
     TVCS_USOLVE_IMG_TABLE(X)

@@ -32,6 +32,7 @@ struct TvArgs {
     float tau;
     unsigned short* u_hi;       // nullable: bf16 hi/lo planes of the new u
     unsigned short* u_lo;
+    const int* img_slot;        // nullable: row of image b's planes (compacted batch), else b
     int pdl;                    // launch with a programmatic dependency on the preceding grid
 };
 
@@ -113,13 +114,21 @@ struct GemmPlan {
 void gemm_plan(int M, int K, int num_sms, GemmPlan* p);
 cudaError_t gemm_configure();
 bool make_bf16_map(CUtensorMap* map, const void* base, int inner, int rows, int ld, int box_rows);
+// The Y operand's tensor maps use boxes of GEMM_Y_BOX rows.  ncols: columns
+// (images) of Y; nact (nullable): the number of leading columns that take part,
+// read on the device.  The MMAs run with N = min(ncols, nact) rounded up to 32.
+constexpr int GEMM_Y_BOX = 64;
 void launch_gemm(const CUtensorMap* xh, const CUtensorMap* xl, const CUtensorMap* yh,
                  const CUtensorMap* yl, const GemmPlan& p, float* ws, Ctrl* ctrl, int check_skip,
-                 long long budget, cudaStream_t s);
+                 long long budget, cudaStream_t s, int ncols, const int* nact = nullptr);
+// Column j of the GEMM is image slot_img[j] (identity when slot_img is null) for
+// F, out and r2part; the bf16 planes out_hi/out_lo stay in column order.  With
+// nact set, only the first *nact columns are processed.
 void launch_gemm_fixup(const float* ws, const int* tile_seg_begin, const int* seg_slot, int M,
                        int tiles_m, int count, const float* F, int ldf, float* out, int ldo,
                        void* out_hi, void* out_lo, int ldh, float2* r2part, const Ctrl* ctrl,
-                       int check_skip, cudaStream_t s);
+                       int check_skip, cudaStream_t s, const int* slot_img = nullptr,
+                       const int* nact = nullptr);
 void launch_split_rows(const float* v, int count, int len, int ld, void* hi, void* lo, int ldh,
                        cudaStream_t s);
 void launch_transpose_split(const float* A, int m, int N, void* th, void* tl, int ldt,
@@ -193,8 +202,12 @@ void launch_dct_products(int n, const DctArgs& a, cudaStream_t s);
 
 // Loop condition of a batch: continue while any of ctrls[0..count) runs and
 // bctrl->loops stays below bctrl->loops_max (batch.cu).
+// With slot_img / img_slot set (count <= 256), also packs the running images
+// into the leading slots in image order: slot_img[0 .. nact), img_slot[b] (-1 for
+// an image that stopped), bctrl->nact.
 void launch_batch_cond(const Ctrl* ctrls, int count, Ctrl* bctrl, unsigned long long cond,
-                       int set_cond, cudaStream_t s);
+                       int set_cond, cudaStream_t s, int* slot_img = nullptr,
+                       int* img_slot = nullptr);
 
 // gather: out = scale * sum_p gpart[p], ctrl->vec2 = ||out||^2 (binary64)
 void launch_gather(const float* gpart, int P, int N, float scale, float* out, double* part,

@@ -588,6 +588,7 @@ void tvcs_default_options(tvcs_options* opt)
     opt->timeout_cycles = 0;
     opt->host_loop = 0;
     opt->a_mode = TVCS_A_STORED;
+    opt->batch_compact = 1;
 }
 
 const char* tvcs_last_error(void)

@@ -135,6 +135,40 @@ def test_batched_per_image_stop(tv):
     tv.tvcs_destroy(h)
 
 
+def test_batched_compaction_is_exact(tv):
+    # images stop at different iterations; with compaction the running images are packed
+    # into the GEMMs' leading columns and the GEMMs shrink (40 columns -> 64-wide MMAs ->
+    # 32-wide).  Every column is still a dot product over the same K in the same order,
+    # so the results are identical to the run that keeps every column.
+    A, ubars, F, mus, _ = synth.workload_shared_batch(count=40, n=32, ratio=0.3, seed=5, n_ellipses=6)
+    m, N = A.shape
+    tau = oracle.default_tau(A)
+    mus = [20.0 * 1.3 ** (b % 12) for b in range(40)]
+    out = {}
+    for compact in (1, 0):
+        opt = tv.tvcs_default_options()
+        opt.precision = tv.TVCS_PREC_BF16X2
+        opt.tau = tau
+        opt.max_iter = 3000
+        opt.batch_compact = compact
+        h = tv.tvcs_create(torch.from_numpy(A).cuda(), 0, m, 32, 1e3, 20.0, 1e-4, opt)
+        us = [np.empty(N, np.float32) for _ in range(40)]
+        res = tv.tvcs_solve_batched([h] * 40, [F[b] for b in range(40)], us, mus)
+        out[compact] = (us, res)
+        tv.tvcs_destroy(h)
+    (uc, rc), (uf, rf) = out[1], out[0]
+    iters = [r.iters for r in rc]
+    assert len(set(iters)) >= 6 and all(r.stopped_by_tol == 1 for r in rc)
+    assert iters == [r.iters for r in rf]
+    for b in range(40):
+        assert np.array_equal(uc[b], uf[b]), b
+        assert rc[b].objective == rf[b].objective
+    # and one of them against the oracle
+    ref = oracle.solve(A, F[7], 32, mus[7], 20.0, tau, tol=1e-4, max_iter=3000)
+    assert abs(rc[7].iters - ref.info["iters"]) <= max(2, ref.info["iters"] // 50)
+    assert rel(uc[7], ref.u) <= 1e-3
+
+
 def test_batched_workload_256_images_n128(tv):
     # 256 images of 128 x 128 sharing one 4915 x 16384 A (bf16 hi/lo), mu cycling over
     # {2e2, 5e2, 1e3, 2e3}, noise U[1e-3, 1e-2] RMS; a fixed 30 iterations, a sample
