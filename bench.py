@@ -707,8 +707,12 @@ def run_dct(args):
     ms = ev0.elapsed_time(ev1)
     u_gpu = u_dev.cpu().numpy()
     reps = 400
+    torch.cuda.nvtx.range_push("dct_products")
     prod_us = tv.tvcs_time_stage(h, 2, reps) * 1e3 / reps
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.nvtx.range_push("usolve")
     us_us = tv.tvcs_time_stage(h, 1, reps) * 1e3 / reps
+    torch.cuda.nvtx.range_pop()
     tv.tvcs_solve(h, f_dev, u_dev)               # a clean state after the stage timing
     f_host = torch.from_numpy(P.f).pin_memory()
     u_host = torch.empty(P.N, dtype=torch.float32).pin_memory()
@@ -735,7 +739,8 @@ def run_dct(args):
                         "peak": fp32_peak, "unit": "TFLOP/s",
                         "frac": flops / (prod_us * 1e-6) / 1e12 / fp32_peak, "traffic": None,
                         "kernel": "k_dct_products (one 16-block cluster)",
-                        "note": "latency-bound: 16.8 MFLOP per launch on 16 SMs",
+                        "note": "latency-bound: 16.8 MFLOP per launch on one 16-SM cluster "
+                                "(the peak is the whole GPU's; the cluster's 16 SMs have 8.5 TFLOP/s)",
                         "launch_us": prod_us,
                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"},
            "stage_us": {"dct_products": prod_us, "usolve_cluster": us_us},
