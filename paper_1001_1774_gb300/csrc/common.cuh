@@ -133,6 +133,13 @@ __device__ __forceinline__ uint64_t l2_policy_evict_first()
     return p;
 }
 
+__device__ __forceinline__ uint64_t l2_policy_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
 // Asynchronous 16-byte global -> shared copy (both addresses 16-byte aligned).
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
 {

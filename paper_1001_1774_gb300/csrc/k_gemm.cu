@@ -48,13 +48,16 @@ constexpr uint32_t GM_TMEM_COLS = 2 * GM_BN;                  // two accumulator
 constexpr size_t GM_SMEM = 1024 + GM_NST * GM_STAGE + 256;
 
 // ---- tcgen05 / TMA wrappers (PTX ISA: tcgen05 family, cp.async.bulk.tensor) ----
+// Tiled 2D TMA load with an L2 cache policy (createpolicy): the operand A streams
+// through once per GEMM (evict first), the small image operand is re-read by every
+// block (evict last), so that A does not push it, or the partial tiles, out of L2.
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
-                                            uint64_t* bar)
+                                            uint64_t* bar, uint64_t policy)
 {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        ".L2::cache_hint [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar)), "l"(policy)
         : "memory");
 }
 
@@ -182,6 +185,7 @@ __global__ void __launch_bounds__(192, 1)
             // ---------------- TMA producer ----------------
             bool ok = true;
             long long it = 0;
+            const uint64_t pol_x = l2_policy_evict_first(), pol_y = l2_policy_evict_last();
             for (long long w = w0; w < w1; ++w, ++it) {
                 const int s = (int)(it % GM_NST);
                 if (it >= GM_NST && !mbar_wait(&empty[s], (uint32_t)((it / GM_NST) - 1) & 1u, budget)) {
@@ -192,13 +196,13 @@ __global__ void __launch_bounds__(192, 1)
                 const int t = (int)(w / kblocks), kb = (int)(w % kblocks);
                 unsigned char* st = smem + (size_t)s * GM_STAGE;
                 mbar_arrive_expect_tx(&full[s], stage_bytes);
-                tma_load_2d(st, &tXh, kb * GM_BK, t * GM_BM, &full[s]);
-                tma_load_2d(st + GM_A_BYTES, &tXl, kb * GM_BK, t * GM_BM, &full[s]);
+                tma_load_2d(st, &tXh, kb * GM_BK, t * GM_BM, &full[s], pol_x);
+                tma_load_2d(st + GM_A_BYTES, &tXl, kb * GM_BK, t * GM_BM, &full[s], pol_x);
                 for (int j = 0; j < ybox; ++j) {   // 64-row boxes, 1024-byte aligned
                     tma_load_2d(st + 2 * GM_A_BYTES + j * GM_YBOX_BYTES, &tYh, kb * GM_BK,
-                                j * GEMM_Y_BOX, &full[s]);
+                                j * GEMM_Y_BOX, &full[s], pol_y);
                     tma_load_2d(st + 2 * GM_A_BYTES + GM_B_BYTES + j * GM_YBOX_BYTES, &tYl,
-                                kb * GM_BK, j * GEMM_Y_BOX, &full[s]);
+                                kb * GM_BK, j * GEMM_Y_BOX, &full[s], pol_y);
                 }
             }
             // leave no copy in flight

@@ -220,7 +220,7 @@ tvcs_status alloc(void** p, size_t bytes)
 
 // Runs the iteration body in a loop graph: K1 -> column pass -> inverse rows ->
 // products; the products kernel sets the WHILE condition from ctrl->done.
-constexpr int ITERS_PER_BODY = 4;
+constexpr int ITERS_PER_BODY = 16;
 
 tvcs_status build_graph(tvcs_ctx* h)
 {
