@@ -1,4 +1,4 @@
-// Shared-memory mixed-radix (4, 3, 2) Stockham FFT of compile-time length NN,
+// Shared-memory mixed-radix (8, 4, 3, 2) Stockham FFT of compile-time length NN,
 // used for the u-step of eq. (eqnorm11): the 2D DFT diagonalises D^T D under
 // periodic boundary (Sec. 2.1), so the u-solve is a forward 2D FFT, a divide
 // by beta*Lambda_pq + mu/tau and an inverse 2D FFT.
@@ -14,25 +14,42 @@
 
 namespace tvcs {
 
-// Radix of stage s for length n: all 4s first, then 3s, then 2s.
+// Radix of stage s for length n = 2^e 3^t: the fewest stages (e = 3a + 2b + c
+// with as many 8s as possible, a lone remainder 2 turned into 4 x 4 when an 8
+// can give way), in increasing radix order: 2s, 3s, 4s, 8s.  Small radices go
+// first, where a stage's outputs are scattered with stride R, so that the
+// eight-way scatter of a radix-8 stage happens only where its outputs are
+// contiguous (Ns large).
 __host__ __device__ constexpr int fft_radix(int n, int s)
 {
-    int m = n, st = 0;
-    while (m % 4 == 0 && m > 2) {
-        if (st == s) return 4;
-        m /= 4;
-        ++st;
+    int m = n, e = 0, t = 0;
+    while (m % 2 == 0) {
+        m /= 2;
+        ++e;
     }
     while (m % 3 == 0) {
-        if (st == s) return 3;
         m /= 3;
-        ++st;
+        ++t;
     }
-    while (m % 2 == 0) {
-        if (st == s) return 2;
-        m /= 2;
-        ++st;
+    if (m != 1) return 0;   // only 2^e 3^t
+    int n8 = e / 3, n4 = 0, n2 = 0;
+    if (e % 3 == 1) {
+        if (n8 > 0) {
+            --n8;
+            n4 = 2;
+        } else {
+            n2 = 1;
+        }
+    } else if (e % 3 == 2) {
+        n4 = 1;
     }
+    if (s < n2) return 2;
+    s -= n2;
+    if (s < t) return 3;
+    s -= t;
+    if (s < n4) return 4;
+    s -= n4;
+    if (s < n8) return 8;
     return 0;
 }
 
@@ -79,6 +96,27 @@ __device__ __forceinline__ void dft_small(float2* v)
         v[2] = csub(s02, s13);
         v[1] = cadd(d02, d13);
         v[3] = csub(d02, d13);
+    } else if constexpr (R == 8) {
+        // two 4-point transforms of the even and odd entries, joined with
+        // W8^k = exp(-+i pi k/4): 1, (1 -+ i)/sqrt 2, -+i, (-1 -+ i)/sqrt 2
+        float2 e[4] = {v[0], v[2], v[4], v[6]};
+        float2 o[4] = {v[1], v[3], v[5], v[7]};
+        dft_small<4, INV>(e);
+        dft_small<4, INV>(o);
+        const float h = 0.707106781186547524f;   // 1/sqrt 2
+        const float2 t1 = INV ? make_float2(h * (o[1].x - o[1].y), h * (o[1].x + o[1].y))
+                              : make_float2(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));
+        const float2 t2 = mul_mi<INV>(o[2]);
+        const float2 t3 = INV ? make_float2(-h * (o[3].x + o[3].y), h * (o[3].x - o[3].y))
+                              : make_float2(h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y));
+        v[0] = cadd(e[0], o[0]);
+        v[4] = csub(e[0], o[0]);
+        v[1] = cadd(e[1], t1);
+        v[5] = csub(e[1], t1);
+        v[2] = cadd(e[2], t2);
+        v[6] = csub(e[2], t2);
+        v[3] = cadd(e[3], t3);
+        v[7] = csub(e[3], t3);
     } else {  // R == 3: w = exp(-+2 pi i/3) = -1/2 -+ i sqrt(3)/2
         const float h = 0.866025403784438647f;  // sqrt(3)/2
         float2 a = v[0], b = v[1], c = v[2];
