@@ -40,7 +40,9 @@ template <int NN, int C>
 struct UsolveShape {
     static constexpr int R = NN / C;            // rows per block
     static constexpr int Q = NN / 2 + 1;        // half-spectrum columns
-    static constexpr int QC = (Q + C - 1) / C;  // columns per block in phase B
+    // Phase B works on n/2 column slots: slot 0 carries the two real columns
+    // q = 0 and q = n/2 as one complex column, slot q the column q (1 <= q < n/2).
+    static constexpr int QC = (NN / 2) / C;     // column slots per block in phase B
     static constexpr int ROWFFT = (R / 2) * NN; // complex elements of the packed row transforms
     static constexpr int COLFFT = QC * NN;
     static constexpr int WORK = ROWFFT > COLFFT ? ROWFFT : COLFFT;
@@ -59,6 +61,7 @@ struct UsolveShape {
     static constexpr size_t O_RED = O_COL + (size_t)COLFFT * 8;
     static constexpr size_t SMEM = O_RED + (64 + 2 * 16) * 8;
     static_assert(NN % C == 0 && R % 2 == 0, "each block owns an even number of rows");
+    static_assert((NN / 2) % C == 0, "whole column slots per block");
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
@@ -70,7 +73,9 @@ struct UsolveShape {
 // batch; -1: the image has stopped and writes no planes), else at row b.
 // a4: the half spectra of the owned rows as in step_split (rows r0 + 2j and
 // r0 + 2j + 1 from packed transform j), each column q stored into the column
-// buffer of block q / QC: col[(q mod QC) NN + row].
+// buffer of the block owning its slot: col[(slot mod QC) NN + row].  Columns
+// 0 and n/2 are real along the rows (row transforms of real rows at frequency
+// 0 and n/2) and share slot 0, as its real and imaginary parts.
 template <int NN, int C>
 __device__ __forceinline__ void split_to_columns(cg::cluster_group& cluster, const float2* Z,
                                                  int r0, float2* col, int tid, int nthr)
@@ -81,10 +86,17 @@ __device__ __forceinline__ void split_to_columns(cg::cluster_group& cluster, con
         const int j = i / Q, q = i - j * Q;
         const float2 a = Z[j * NN + q];
         const float2 b = Z[j * NN + (NN - q) % NN];
-        const int owner = q / QC, f = q - owner * QC;
+        const int slot = (2 * q == NN) ? 0 : q;
+        const int owner = slot / QC, f = slot - owner * QC;
         float2* dst = cluster.map_shared_rank(col, owner) + f * NN + r0 + 2 * j;
-        dst[0] = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
-        dst[1] = make_float2(0.5f * (a.y + b.y), -0.5f * (a.x - b.x));
+        if (q == 0 || 2 * q == NN) {   // real values: the x (q = 0) or y (q = n/2) part
+            float* d1 = reinterpret_cast<float*>(dst) + (q == 0 ? 0 : 1);
+            d1[0] = 0.5f * (a.x + b.x);
+            d1[2] = 0.5f * (a.y + b.y);
+        } else {
+            dst[0] = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+            dst[1] = make_float2(0.5f * (a.y + b.y), -0.5f * (a.x - b.x));
+        }
     }
 }
 
@@ -202,24 +214,51 @@ __global__ void __launch_bounds__(US_THREADS, 1) k_usolve_cluster(
     cluster.sync();   // every block's columns are complete
 
     // ---------------- phase B: columns ----------------
-    const int q0 = rank * QC;
-    const int ncol = max(0, min(QC, Q - q0));
+    const int q0 = rank * QC;   // first column slot of this block
+    constexpr int ncol = QC;
     float2* X = fft_block<NN, false>(col, wb, tw, ncol, NN);
     float2* other = (X == col) ? wb : col;
     for (int i = tid; i < ncol * NN; i += nthr) {
         const int f = i / NN, p = i - f * NN;
+        if (q0 + f == 0) continue;   // slot 0: below
         const float rd = 1.0f / solve_divisor(s2, p, q0 + f, beta, mu_over_tau);
         float2 v = X[i];
         v.x *= rd;
         v.y *= rd;
         X[i] = v;
     }
+    if (q0 == 0) {
+        // Slot 0 holds z = c0 + i cN of the real columns c0 (q = 0) and cN (q = n/2):
+        // C0_k = (Z_k + conj Z_{n-k}) / 2, CN_k = (Z_k - conj Z_{n-k}) / (2i), each divided
+        // by its own divisor (symmetric in k), recombined as Z_k = C0_k + i CN_k (and
+        // Z_{n-k} = conj C0_k + i conj CN_k), so that the inverse gives c0' + i cN'.
+        for (int k = tid; 2 * k <= NN; k += nthr) {
+            const int km = (NN - k) % NN;
+            const float2 zk = X[k], zm = X[km];
+            float2 c0 = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+            float2 cn = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+            const float r0 = 1.0f / solve_divisor(s2, k, 0, beta, mu_over_tau);
+            const float rn = 1.0f / solve_divisor(s2, k, NN / 2, beta, mu_over_tau);
+            c0.x *= r0;
+            c0.y *= r0;
+            cn.x *= rn;
+            cn.y *= rn;
+            X[k] = make_float2(c0.x - cn.y, c0.y + cn.x);
+            if (km != k) X[km] = make_float2(c0.x + cn.y, cn.x - c0.y);
+        }
+    }
     __syncthreads();
     float2* Y = fft_block<NN, true>(X, other, tw, ncol, NN);
     for (int i = tid; i < ncol * NN; i += nthr) {
         const int f = i % ncol, p = i / ncol;
-        float2* own = cluster.map_shared_rank(spec, p / R);
-        own[(p % R) * Q + q0 + f] = Y[f * NN + p];
+        float2* own = cluster.map_shared_rank(spec, p / R) + (p % R) * Q;
+        const float2 v = Y[f * NN + p];
+        if (q0 + f == 0) {   // back to the real columns 0 and n/2
+            own[0] = make_float2(v.x, 0.f);
+            own[NN / 2] = make_float2(v.y, 0.f);
+        } else {
+            own[q0 + f] = v;
+        }
     }
     cluster.sync();   // every column is home
 
