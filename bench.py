@@ -212,6 +212,11 @@ def traffic_from_profile():
         return None
 
 
+def batch_launch_iters(iters):
+    """The same for the shared-A batch, whose loop body holds 4 iterations."""
+    return -(-iters // 4) * 4
+
+
 def loop_launch_iters(iters):
     """Iterations whose kernels a single-image run launches: the loop graph's body
     holds 16 iterations, and the ones after the stopping iteration of the last
@@ -491,7 +496,7 @@ def run_batched(args):
            "e2e": {"value": B * args.steps / e2e_s, "unit": "image-iter/s",
                    "h2d_bytes_per_step": 4 * m * B / args.steps,
                    "d2h_bytes_per_step": 4 * N * B / args.steps},
-           "gpu_launches": 6 * args.steps + 8, "clocks": clocks, "tau": tau}
+           "gpu_launches": 6 * batch_launch_iters(args.steps) + 8, "clocks": clocks, "tau": tau}
     if not args.no_cpu_baseline:
         import oracle
         P = synth.Problem("batch_img0", 128, m, 1, mus[0], 10.0, 0.0, args.steps, 0.0, ubars[0], A,
@@ -856,7 +861,7 @@ def run_batched_tol(args):
                         "kernel": "k_gemm_bf16x3 (columns = running images); see --workload batch256"},
            "e2e": {"value": B / e2e_s, "unit": "recons/s", "h2d_bytes_per_step": 4 * m * B / its_a.max(),
                    "d2h_bytes_per_step": 4 * N * B / its_a.max()},
-           "gpu_launches": 6 * int(its_a.max()) + 8, "clocks": clocks, "tau": tau}
+           "gpu_launches": 6 * batch_launch_iters(int(its_a.max())) + 8, "clocks": clocks, "tau": tau}
     print(json.dumps(out), flush=True)
 
 def bf16_peak():

@@ -70,6 +70,7 @@ __global__ void k_batch_cond(const Ctrl* __restrict__ ctrls, int count, Ctrl* __
         const int lc = ++bctrl->loops;
         const int cont = (any && lc < bctrl->loops_max) ? 1 : 0;
         bctrl->done = !cont;
+        bctrl->skip = !cont;   // the GEMMs and fix-ups of later iterations in the body
         if (set_cond) cudaGraphSetConditional(cond, (unsigned)cont);
     }
 }
@@ -267,20 +268,25 @@ tvcs_status ensure_batch(tvcs_ctx* h, int count)
 
 // R = A U - F (R planes, ||r||^2 partials), then G = A^T R, for `count` images.
 // compact: the GEMMs take the first bctrl->nact columns, column j being image
-// slot_img[j] (the U and R planes are stored in that column order).
-void batch_products(tvcs_ctx* h, int count, bool subtract_f, cudaStream_t s, bool compact = false)
+// slot_img[j] (the U and R planes are stored in that column order).  in_loop:
+// the kernels return at once when bctrl->skip is set (every image has stopped).
+void batch_products(tvcs_ctx* h, int count, bool subtract_f, cudaStream_t s, bool compact = false,
+                    bool in_loop = false)
 {
     tvcs_batch* b = h->batch;
     const long long budget = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : (1LL << 31);
     const int* nact = compact ? &b->bctrl->nact : nullptr;
     const int* slot = compact ? b->slot_img : nullptr;
-    launch_gemm(&b->mAh, &b->mAl, &b->mUh, &b->mUl, b->p1, b->ws, b->bctrl, 0, budget, s, count, nact);
+    const int chk = in_loop ? 1 : 0;
+    launch_gemm(&b->mAh, &b->mAl, &b->mUh, &b->mUl, b->p1, b->ws, b->bctrl, chk, budget, s, count,
+                nact);
     launch_gemm_fixup(b->ws, b->tsb1, b->ss1, h->m, b->p1.tiles_m, count,
                       subtract_f ? b->F : nullptr, h->m, b->R, h->m, b->Rh, b->Rl, b->mpad,
-                      b->r2part, b->bctrl, 0, s, slot, nact);
-    launch_gemm(&b->mAth, &b->mAtl, &b->mRh, &b->mRl, b->p2, b->ws, b->bctrl, 0, budget, s, count, nact);
+                      b->r2part, b->bctrl, chk, s, slot, nact);
+    launch_gemm(&b->mAth, &b->mAtl, &b->mRh, &b->mRl, b->p2, b->ws, b->bctrl, chk, budget, s, count,
+                nact);
     launch_gemm_fixup(b->ws, b->tsb2, b->ss2, h->N, b->p2.tiles_m, count, nullptr, 0, b->G, h->N,
-                      nullptr, nullptr, 0, nullptr, b->bctrl, 0, s, slot, nact);
+                      nullptr, nullptr, 0, nullptr, b->bctrl, chk, s, slot, nact);
 }
 
 TvArgs batch_tv_args(tvcs_ctx* h, int count, int mode, bool compact = false)
@@ -317,6 +323,8 @@ void batch_usolve(tvcs_ctx* h, const TvArgs& a, cudaStream_t s)
         launch_usolve(h->n, h->batch->ucluster, a, s);
 }
 
+constexpr int BATCH_ITERS_PER_BODY = 4;
+
 tvcs_status build_batch_graph(tvcs_ctx* h, int count)
 {
     tvcs_batch* b = h->batch;
@@ -334,12 +342,18 @@ tvcs_status build_batch_graph(tvcs_ctx* h, int count)
     cudaStream_t cs = h->cap_stream;
     BCK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
                                       cudaStreamCaptureModeThreadLocal));
+    // BATCH_ITERS_PER_BODY iterations per body (each pass through the WHILE node
+    // costs several microseconds); once every image has stopped, the rest of the
+    // body is skipped (the u-solves per image, the GEMMs and fix-ups on bctrl->skip)
     const bool compact = h->opt.batch_compact != 0;
     TvArgs a = batch_tv_args(h, count, MODE_ITER, compact);
-    batch_usolve(h, a, cs);
-    batch_products(h, count, true, cs, compact);
-    launch_batch_cond(b->ctrls, count, b->bctrl, (unsigned long long)ch, 1, cs,
-                      compact ? b->slot_img : nullptr, compact ? b->img_slot : nullptr);
+    for (int k = 0; k < BATCH_ITERS_PER_BODY; ++k) {
+        batch_usolve(h, a, cs);
+        batch_products(h, count, true, cs, compact, true);
+        launch_batch_cond(b->ctrls, count, b->bctrl, (unsigned long long)ch,
+                          k + 1 == BATCH_ITERS_PER_BODY ? 1 : 0, cs,
+                          compact ? b->slot_img : nullptr, compact ? b->img_slot : nullptr);
+    }
     cudaGraph_t captured = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &captured);
     if (e != cudaSuccess)
