@@ -5,8 +5,10 @@
 // them, so each image stays on one SM and needs no cluster barrier.
 //
 // The block keeps the image's whole half spectrum in shared memory, column-
-// major (spec[q n + p], q = 0 .. n/2), so that phase B transforms all n/2+1
-// columns at once.  Phases A and C stream the image in stripes of S rows
+// major (spec[q (n+1) + p], q = 0 .. n/2: the column stride is padded by one
+// complex value so that a warp storing consecutive columns of one row, as the
+// split after the row transforms does, spreads over the banks), so that phase
+// B transforms all n/2+1 columns at once.  Phases A and C stream the image in stripes of S rows
 // through a two-deep ring of asynchronous 16-byte copies (the next stripe's
 // rows arrive while the current one is computed):
 //   A  per stripe: w-step, right-hand side, forward row FFTs (two real rows per
@@ -30,6 +32,7 @@ constexpr int IMG_THREADS = 512;
 template <int NN, int S>
 struct ImgShape {
     static constexpr int Q = NN / 2 + 1;
+    static constexpr int QS = NN + 1;               // column stride of the spectrum (complex)
     static constexpr int NSTRIPE = NN / S;
     static constexpr int IN_U = (S + 2) * NN;       // u rows r0-1 .. r0+S
     static constexpr int IN_G = S * NN;             // g rows r0 .. r0+S-1
@@ -37,8 +40,8 @@ struct ImgShape {
     static constexpr int IN = IN_U + IN_G + IN_WL;  // floats of one stripe's inputs
     static constexpr size_t O_TW = 0;
     static constexpr size_t O_S2 = O_TW + NN * 8;
-    static constexpr size_t O_SPEC = O_S2 + ((NN * 4 + 15) / 16) * 16;   // Q x NN complex
-    static constexpr size_t SPEC_BYTES = (size_t)Q * NN * 8;
+    static constexpr size_t O_SPEC = O_S2 + ((NN * 4 + 15) / 16) * 16;   // Q columns of QS complex
+    static constexpr size_t SPEC_BYTES = (((size_t)Q * QS * 8 + 15) / 16) * 16;
     static constexpr size_t O_SCR = O_SPEC + SPEC_BYTES;
     // phase A, inside the scratch region: two input buffers, y1, y2, two FFT buffers
     static constexpr size_t A_IN0 = O_SCR;
@@ -172,22 +175,22 @@ __global__ void __launch_bounds__(IMG_THREADS, 1) k_usolve_img(
         step_rhs<NN>(sy1, sy2, cur + SH::IN_U, S, r0, mu, wa, nullptr, tid, nthr);
         __syncthreads();
         float2* Z = fft_block<NN, false>(wa, wb, tw, S / 2, NN);
-        step_split<NN>(Z, S, spec + r0, 1, NN, tid, nthr);
+        step_split<NN>(Z, S, spec + r0, 1, SH::QS, tid, nthr);
         __syncthreads();       // the ring buffer, y and the FFT buffers are free again
     }
 
     // ---------------- phase B: all columns ----------------
-    float2* X = fft_block<NN, false>(spec, scr, tw, Q, NN);
+    float2* X = fft_block<NN, false>(spec, scr, tw, Q, SH::QS);
     for (int i = tid; i < Q * NN; i += nthr) {
         const int q = i / NN, p = i - q * NN;
         const float rd = 1.0f / solve_divisor(s2, p, q, beta, mu_over_tau);
-        float2 v = X[i];
+        float2 v = X[q * SH::QS + p];
         v.x *= rd;
         v.y *= rd;
-        X[i] = v;
+        X[q * SH::QS + p] = v;
     }
     __syncthreads();
-    const float2* Y = fft_block<NN, true>(X, X == spec ? scr : spec, tw, Q, NN);   // == spec
+    const float2* Y = fft_block<NN, true>(X, X == spec ? scr : spec, tw, Q, SH::QS);   // == spec
 
     // ---------------- phase C: stripes of S rows ----------------
     float* ub0 = reinterpret_cast<float*>(scr);
@@ -207,7 +210,7 @@ __global__ void __launch_bounds__(IMG_THREADS, 1) k_usolve_img(
         cp_async_wait_one();
         __syncthreads();
         const int r0 = s * S;
-        step_pack_inverse<NN>(Y + r0, 1, NN, S, ca, tid, nthr);
+        step_pack_inverse<NN>(Y + r0, 1, SH::QS, S, ca, tid, nthr);
         __syncthreads();
         float2* z = fft_block<NN, true>(ca, cb, tw, S / 2, NN);
         step_update<NN>(z, cur, S, r0, u, u_hi, u_lo, du2, u2, tid, nthr);
