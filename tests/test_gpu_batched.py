@@ -135,6 +135,23 @@ def test_batched_per_image_stop(tv):
     tv.tvcs_destroy(h)
 
 
+def test_batched_iteration_count_not_a_multiple_of_the_loop_body(tv):
+    # the loop graph holds 4 iterations per body: a run of 7 ends inside a body, and
+    # the GEMMs and fix-ups of the rest of the body must not change any image
+    A, ubars, F, mus, _ = synth.workload_shared_batch(count=5, n=32, ratio=0.3, seed=6, n_ellipses=6)
+    m, N = A.shape
+    tau = oracle.default_tau(A)
+    h = bf16_handle(tv, A, m, 32, mu=1e3, tau=tau, max_iter=7)
+    us = [np.empty(N, np.float32) for _ in range(5)]
+    res = tv.tvcs_solve_batched([h] * 5, [F[b] for b in range(5)], us, mus)
+    for b in range(5):
+        assert res[b].iters == 7
+        ref = oracle.solve(A, F[b], 32, mus[b], 10.0, tau, max_iter=7)
+        assert rel(us[b], ref.u) <= 1e-4, b
+        assert res[b].objective == pytest.approx(ref.info["objective"], rel=1e-4)
+    tv.tvcs_destroy(h)
+
+
 def test_batched_compaction_is_exact(tv):
     # images stop at different iterations; with compaction the running images are packed
     # into the GEMMs' leading columns and the GEMMs shrink (40 columns -> 64-wide MMAs ->

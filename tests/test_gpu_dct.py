@@ -59,6 +59,39 @@ def test_dct_products_parity(tv, n, ratio):
     tv.tvcs_destroy(h)
 
 
+@pytest.mark.parametrize("case", ["all", "one", "one_row"])
+def test_dct_products_edge_sets(tv, case):
+    # every coefficient (A is the whole orthonormal 2D DCT, so A^T A = I and
+    # g = x - A^T y), a single coefficient, and all samples in one coefficient row
+    # (every block but one of the cluster has no sampled entry)
+    n = 32
+    if case == "all":
+        rows = np.random.default_rng(1).permutation(n * n).astype(np.int32)
+    elif case == "one":
+        rows = np.array([n * n - 1], np.int32)
+    else:
+        rows = np.arange(5 * n, 6 * n, dtype=np.int32)[::-1].copy()
+    m = len(rows)
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal(n * n).astype(np.float32)
+    y = rng.standard_normal(m).astype(np.float32)
+    h = dct_handle(tv, rows, n)
+    r = np.empty(m, np.float32)
+    g = np.empty(n * n, np.float32)
+    tv.tvcs_apply(h, x, y, r, g)
+    rr = oracle.dct_Au(n, rows, x, y)
+    scale_r = (2.0 / n) * np.sum(np.abs(x)) + np.abs(y)
+    assert np.all(np.abs(r - rr) <= 1e-5 * scale_r)
+    gr = oracle.dct_At(n, rows, r.astype(np.float64))
+    assert np.all(np.abs(g - gr) <= 1e-5 * max((2.0 / n) * np.sum(np.abs(r)), 1e-30))
+    if case == "all":   # A^T A = I: g = x - A^T y, checked against the oracle's A^T alone
+        aty = oracle.dct_At(n, rows, y.astype(np.float64))
+        assert np.allclose(g, x - aty, rtol=0, atol=1e-5 * np.abs(x).max() * 4)
+    else:
+        assert np.isfinite(g).all()
+    tv.tvcs_destroy(h)
+
+
 def test_dct_power_iteration_gives_unit_lambda_max(tv):
     n, m = 32, 300
     rows = synth.dct_rows(3, n, m)
