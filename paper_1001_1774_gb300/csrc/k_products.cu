@@ -1,20 +1,22 @@
 // Rows a6-a7: r = A x - y and g = A^T r in ONE pass over A (Xiao & Yang,
 // eq. (line): g_k = A^T (A u^k - f); two products per iteration, Sec. 3.1).
 //
-// Each block owns a contiguous range of rows of A (row-major binary32).  A
-// producer warp streams the rows into a 3-stage shared-memory ring with bulk
-// asynchronous copies (TMA, non-tensor form, one mbarrier per stage; A is
-// read once per call, with an L2 evict-first hint).  Consumer threads own
-// fixed columns: for each row they form the dot product with x (warp
-// shuffles + one named barrier), compute r_i = dot - y_i, and fold r_i * A_i
-// into per-thread accumulators of A^T r.  Row i's data is used twice from
-// shared memory and read from HBM once, so the algorithmic traffic is one pass
-// over A.  Each block writes its partial A^T r (N floats); the next kernel sums
-// the P partials in a fixed order (deterministic).
+// Each block owns a contiguous range of rows of A (row-major binary32).  Thread
+// 0 streams the rows into a 3-stage shared-memory ring with bulk asynchronous
+// copies (TMA, non-tensor form, one mbarrier per stage; A is read once per
+// call, with an L2 evict-first hint), the first stages before the dependency
+// wait on the preceding kernel.  All 512 threads own fixed columns: for each
+// row they form the dot product with x (warp shuffles + one named barrier),
+// compute r_i = dot - y_i, and fold r_i * A_i into per-thread accumulators of
+// A^T r.  Row i's data is used twice from shared memory and read from HBM once,
+// so the algorithmic traffic is one pass over A.  Each block writes its partial
+// A^T r (N floats); with g_out set, a grid barrier (cooperative launch) follows
+// and every block sums its slice of the P partials in a fixed order
+// (deterministic), otherwise a later kernel does.
 //
-// Shapes: consumer threads = 512 in RL row lanes of TPR = 512/RL threads; a
-// thread holds V float4 columns of x and of the accumulator (N = 4*TPR*V).
-// RS rows per stage (<= 72 KB), 3 stages.
+// Shapes: 512 threads in RL row lanes of TPR = 512/RL threads; a thread holds V
+// float4 columns of x and of the accumulator (N = 4*TPR*V).  RS rows per stage,
+// 3 stages: one block per SM, and the grid leaves 16 SMs free for the u-solve.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -24,7 +26,7 @@ namespace tvcs {
 
 constexpr int PROD_CONS = 512;           // 16 warps; thread 0 also issues the TMA copies
 constexpr int PROD_THREADS = PROD_CONS;
-constexpr int PROD_NST = 2;
+constexpr int PROD_NST = 3;
 
 template <int V, int RL, int RS>
 struct ProdShape {
@@ -39,10 +41,11 @@ struct ProdShape {
     static_assert(TPR % 32 == 0, "row lanes must be whole warps");
 };
 
-// At most 96 registers a thread: 16 warps x 96 leave room in each of the SM's
-// four register files for a block of the u-solve beside a block of this kernel.
+// One block of 16 warps per SM (a three-stage ring of rows fills shared memory);
+// the grid leaves 16 SMs to the u-solve cluster of the same iteration, which
+// runs there while this kernel streams A.
 template <int V, int RL, int RS>
-__global__ void __maxnreg__(96)
+__global__ void __maxnreg__(128)
     k_products(const float* __restrict__ A, int m, const float* __restrict__ x,
                const float* __restrict__ y, float* __restrict__ r, float* __restrict__ gpart,
                float* __restrict__ g_out, float2* __restrict__ r2part, Ctrl* __restrict__ ctrl,
@@ -390,7 +393,8 @@ int prod_grid(int n, int m, int num_sms)
 {
     const int rl = prod_rl(n);
     int g = (m + rl - 1) / rl;
-    return g < num_sms ? g : num_sms;
+    const int cap = num_sms > 32 ? num_sms - 16 : num_sms;   // 16 SMs stay free for the u-solve cluster
+    return g < cap ? g : cap;
 }
 
 cudaError_t prod_configure(int n)
