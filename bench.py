@@ -227,9 +227,10 @@ def loop_launch_iters(iters):
 
 # ----------------------------------------------------------------------------- CPU oracle sample
 
-def oracle_sample(P, tau, budget_s=20.0, want_u=False, algo=0):
+def oracle_sample(P, tau, budget_s=20.0, want_u=False, algo=0, max_iters=None):
     """Times the FP64 oracle (as it stands) on this host: iterations/s measured on
-    a bounded number of iterations of the same workload."""
+    a bounded number of iterations of the same workload (at most max_iters, one
+    300-iteration reconstruction by default, fewer when the time budget is short)."""
     import numpy as np
     import oracle
     t0 = time.perf_counter()
@@ -238,7 +239,8 @@ def oracle_sample(P, tau, budget_s=20.0, want_u=False, algo=0):
     t0 = time.perf_counter()
     oracle.solve(P.A, P.f, P.n, P.mu, P.beta, tau, max_iter=2, algo=algo)
     per = max((time.perf_counter() - t0 - t_init) / 2, 1e-6)
-    iters = ITERS_PER_RECON if per * ITERS_PER_RECON <= budget_s else max(2, int(budget_s / per))
+    want = ITERS_PER_RECON if max_iters is None else max(1, max_iters)
+    iters = want if per * want <= budget_s else max(2, min(want, int(budget_s / per)))
     t0 = time.perf_counter()
     res = oracle.solve(P.A, P.f, P.n, P.mu, P.beta, tau, max_iter=iters, algo=algo)
     elapsed = time.perf_counter() - t0 - t_init
@@ -889,13 +891,15 @@ def run_reference(args):
     t0 = time.perf_counter()
     oracle.solve(P.A, P.f, P.n, P.mu, P.beta, tau, max_iter=min(args.warmup, 3))
     warm = time.perf_counter() - t0
-    cb = oracle_sample(P, tau, budget_s=budget, algo=1 if args.algo == "ftvcs" else 0)
+    # one step = one iteration, as in our arm; K steps when they fit the time budget
+    cb = oracle_sample(P, tau, budget_s=budget, algo=1 if args.algo == "ftvcs" else 0,
+                       max_iters=args.steps)
     A_bytes = P.m * P.N * 4
     value = cb["value"]
-    sample = ("%d of %d requested IADM iterations (FP64 C oracle, OpenMP), %.1f s"
-              % (cb["iters"], args.steps, cb["seconds"]))
+    sample = ("%d of %d requested %s iterations in one run (FP64 C oracle, OpenMP), %.1f s"
+              % (cb["iters"], args.steps, args.algo.upper(), cb["seconds"]))
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iter/s",
-           "n_gpus": ws, "steps": cb["iters"], "warmup": args.warmup,
+           "n_gpus": ws, "steps": cb["iters"], "requested_steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded phantom, Philox Gaussian A)",
            "config": workload_config(P, A_bytes, 0, args.algo),
