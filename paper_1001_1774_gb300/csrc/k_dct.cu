@@ -255,17 +255,17 @@ k_dct_products(const float* __restrict__ Cg, const float* __restrict__ x,
     for (int o = tid; o < R * C4; o += DCT_THREADS)
         reinterpret_cast<float4*>(Sg + (size_t)r0 * NN)[o] = reinterpret_cast<const float4*>(sS)[o];
     cluster_arrive();
+    cluster_wait();   // every block's rows of S are in Sg
+
+    // 4: T[i][c] = sum_k C[k][r0+i] S_all[k][c]; stored transposed into sUt.  The
+    // ||r||^2 partial goes to block 0 while the copy of S is in flight.
+    copy_matrix_async<NN>(Sg, sAll, tid);
     const float2 br2 = block_sum_ds(r2, red);
     if (tid == 0) {   // read by block 0 after the last barrier
         float2* dst = cluster.map_shared_rank(cred, 0);
         dst[rank] = br2;
     }
-    cluster_wait();   // every block's rows of S are in Sg
-
-    // 4: T[i][c] = sum_k C[k][r0+i] S_all[k][c]; stored transposed into sUt
-    copy_matrix_async<NN>(Sg, sAll, tid);
-    // the ||r||^2 partial is written; the matching wait is the last step
-    cluster_arrive();
+    cluster_arrive();   // the partial is written; the matching wait is the last step
     cp_async_wait_all();
     __syncthreads();
     tile_partials<NN, CL>(sC + r0, NN, sAll, sP, tid);
