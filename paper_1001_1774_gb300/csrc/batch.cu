@@ -91,13 +91,6 @@ __global__ void k_join_bf16x2(const unsigned short* __restrict__ hi, const unsig
         out[i] = __uint_as_float((unsigned)hi[i] << 16) + __uint_as_float((unsigned)lo[i] << 16);
 }
 
-__global__ void k_scale_copy(const float* __restrict__ in, float* __restrict__ out, long long n, float s)
-{
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        out[i] = s * in[i];
-}
-
 namespace {
 
 #define BCK(call)                                                                             \
