@@ -75,3 +75,12 @@ def test_reference_arm_prints_one_contract_line():
         assert k in d, k
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    # one step is one oracle iteration: K of them when they fit the time budget
+    assert d["steps"] == 5 and d["requested_steps"] == 5
+
+
+def test_launch_counts_include_the_skipped_tail_of_a_loop_body():
+    import bench
+    # single image: 16 iterations per loop body; shared-A batch: 4
+    assert [bench.loop_launch_iters(k) for k in (1, 16, 17, 300, 30000)] == [16, 16, 32, 304, 30000]
+    assert [bench.batch_launch_iters(k) for k in (1, 4, 7, 300)] == [4, 4, 8, 300]
