@@ -121,6 +121,24 @@ def test_printed_w_sign_does_not_reach_kkt_point():
     assert not np.isfinite(kd) or kd > 1e-2 or bad.info["lambda_align"] > 1e-2
 
 
+def test_warm_start_at_a_kkt_point_stays_there():
+    # The warm start of the beta-continuation (Sec. 3.1; u^0 and lambda^0 given, w^0 = 0):
+    # at a KKT point (u*, lambda*) of eq. (eqftvdcs) the first w-step returns w* = D u*
+    # (lambda* lies in the subdifferential at D u*), the u-step's right-hand side
+    # D^T (beta (w* - D u*) - lambda*) - mu A^T (A u* - f) vanishes by dual feasibility,
+    # and the multiplier update leaves lambda* unchanged: the iteration stays put.
+    P = _problem(8, 96, 20.0, 20.0)
+    tau = oracle.default_tau(P.A)
+    R = oracle.solve(P.A, P.f, 8, 20.0, 20.0, tau, max_iter=20000, tol=1e-15)
+    assert R.info["kkt_dual"] <= 1e-12
+    W = oracle.solve(P.A, P.f, 8, 20.0, 20.0, tau, max_iter=5, u0=R.u, lam0=R.lam)
+    assert np.max(np.abs(W.u - R.u)) <= 1e-12 * max(1.0, np.abs(R.u).max())
+    assert np.max(np.abs(W.lam - R.lam)) <= 1e-10
+    # and a warm start away from it does move
+    M = oracle.solve(P.A, P.f, 8, 20.0, 20.0, tau, max_iter=5, u0=R.u + 1e-3, lam0=R.lam)
+    assert np.max(np.abs(M.u - R.u)) > 1e-5
+
+
 def test_matches_independent_dual_solver_n8():
     # Full column rank (m = 96 >= N = 64): unique minimiser.
     P = _problem(8, 96, 20.0, 20.0)
