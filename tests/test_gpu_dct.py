@@ -142,3 +142,41 @@ def test_dct_workload_128_to_tolerance(tv):
     # the reconstruction error against the phantom is small at 30% sampling
     assert rel(u.cpu().numpy(), P.ubar) < 0.2
     tv.tvcs_destroy(h)
+
+
+@pytest.mark.parametrize("algo", [0, 1])
+def test_dct_beta_continuation_matches_oracle_stages(tv, algo):
+    # Sec. 3.1's continuation in beta (2^4 .. 2^7) with the partial-DCT encoder: each stage
+    # warm-started from the last stage's u (and lambda for IADM), w restarted at 0
+    P = synth.make_dct_problem(32, 0.3, 5, 6, 200.0)
+    rows = P.extra["rows"]
+    betas = [16.0, 32.0, 64.0, 128.0]
+    h = dct_handle(tv, rows, 32, mu=P.mu, beta=64.0, tau=1.9, max_iter=30, algo=algo)
+    u = np.empty(P.N, np.float32)
+    res = tv.tvcs_solve_continuation(h, P.f, u, betas)
+    assert len(res) == 4 and all(r.iters == 30 for r in res)
+    u0 = lam0 = None
+    for b in betas:
+        ref = oracle.solve_dct(rows, P.f, 32, P.mu, b, 1.9, max_iter=30, algo=algo, u0=u0,
+                               lam0=lam0 if algo == 0 else None)
+        u0, lam0 = ref.u, ref.lam
+    assert rel(u, ref.u) <= 1e-5
+    tv.tvcs_destroy(h)
+
+
+def test_dct_handles_in_a_batched_call_equal_single_solves(tv):
+    # several partial-DCT problems (different rows, data and mu) through
+    # tvcs_solve_batched: the same results as one solve per handle
+    probs = [synth.make_dct_problem(32, ratio, seed, 6, mu)
+             for ratio, seed, mu in ((0.3, 11, 100.0), (0.2, 12, 300.0), (0.5, 13, 50.0))]
+    hs = [dct_handle(tv, P.extra["rows"], 32, mu=P.mu, beta=64.0, tau=1.9, max_iter=40) for P in probs]
+    us = [np.empty(P.N, np.float32) for P in probs]
+    res = tv.tvcs_solve_batched(hs, [P.f for P in probs], us, [P.mu for P in probs])
+    for h, P, u, r in zip(hs, probs, us, res):
+        u1 = np.empty(P.N, np.float32)
+        r1 = tv.tvcs_solve(h, P.f, u1)
+        assert r.iters == r1.iters == 40
+        assert np.array_equal(u, u1)
+    for h in hs:
+        tv.tvcs_destroy(h)
+
