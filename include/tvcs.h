@@ -12,8 +12,11 @@
  * Solver: Algorithm 2 (IADM, Sec. 2.2) or Algorithm 1 (FTVCS, Sec. 2.1).  Each
  * iteration is one isotropic shrinkage, the products A*u and A^T*(A u - f),
  * and one FFT pair (Sec. 3.1).  All arithmetic runs in this library's CUDA
- * kernels; binary32 for the iterates, binary64 for the norms of the stopping
- * test, the objective and the optimality residuals.
+ * kernels: binary32 for the iterates; the sums of squares of every iteration
+ * (the norms of the stopping test, ||A u - f||^2) as binary32 double-single
+ * pairs (exact squares, compensated sums: about 44 significant bits), compared
+ * in binary64; binary64 for the objective and the optimality residuals at the
+ * end of a run.
  *
  * Conventions for every entry point:
  *  - Pointers to arrays may be host (pageable or pinned) or device pointers;
@@ -111,7 +114,9 @@ void tvcs_default_options(tvcs_options* opt);
  *          of the library's generator source, k_gen.cu).  A is copied (or generated) into device
  *          memory the handle owns, stored in opt->precision.
  *   m      number of measurements, 1 <= m <= 2^24
- *   n      image side: 4 <= n <= 256, n = 2^a 3^b, n even
+ *   n      image side: 16, 32, 48, 64, 96, 128, 192 or 256 with binary32 storage,
+ *          32, 64, 128, 192 or 256 with the bf16 and fp8 storages (other sides
+ *          return TVCS_ERR_INVALID_ARG)
  *   mu     > 0, beta > 0 (penalty of eq. (ALP)), tol >= 0 (eq. (stop); 0 disables)
  *   opt    nullable (defaults)
  * On success *out receives the handle (destroy with tvcs_destroy).
@@ -150,7 +155,8 @@ tvcs_status tvcs_solve(tvcs_handle h, const float* f, float* u, tvcs_result* res
  * the same handle created with precision TVCS_PREC_BF16X2 (and count <= 256),
  * all images iterate together: their u-steps run as one batched launch and
  * their products as tensor-core GEMMs (see tvcs_apply_batched); each image
- * stops on its own eq. (stop).  When every hs[i] was created with a_mode
+ * stops on its own eq. (stop), and with opt->batch_compact (the default) it
+ * then leaves the GEMMs, whose work shrinks with the images still running.  When every hs[i] was created with a_mode
  * TVCS_A_REGENERATE (count <= 1024, all on one device with equal algo, beta
  * and init, init TVCS_INIT_ATF or TVCS_INIT_ZERO; n, m, seed, mu, tau, tol and
  * max_iter may differ), all problems iterate together in one loop graph on
