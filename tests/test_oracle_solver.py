@@ -121,6 +121,43 @@ def test_printed_w_sign_does_not_reach_kkt_point():
     assert not np.isfinite(kd) or kd > 1e-2 or bad.info["lambda_align"] > 1e-2
 
 
+def test_kkt_report_matches_dense_definitions():
+    # The summary the oracle reports for a state (u, w, lambda), recomputed from the
+    # definitions with the explicit matrices D = (D1; D2) and A: TV = sum_i ||D_i u||,
+    # ||A u - f||^2, the objective of eq. (tv), the penalty objective of eq. (atv),
+    # ||w - D u||, ||D^T lambda + mu A^T (A u - f)||, max_i ||lambda_i|| and the
+    # largest ||lambda_i - w_i / ||w_i|||.
+    n, m, mu, beta = 6, 20, 3.0, 7.0
+    rng = np.random.default_rng(11)
+    A = (rng.standard_normal((m, n * n)) / np.sqrt(m)).astype(np.float32)
+    f = rng.standard_normal(m).astype(np.float32)
+    u = rng.standard_normal(n * n)
+    w = rng.standard_normal(2 * n * n)
+    w[5] = w[5 + n * n] = 0.0   # one w_i = 0 (no alignment term there)
+    lam = rng.standard_normal(2 * n * n)
+    D = diff_matrix(n)
+    N = n * n
+    A64 = A.astype(np.float64)
+    d = D @ u
+    r = A64 @ u - f.astype(np.float64)
+    e = w - d
+    got = oracle.kkt(A, f, n, mu, beta, u, w, lam)
+    tv = np.sum(np.hypot(d[:N], d[N:]))
+    assert got["tv"] == pytest.approx(tv, rel=1e-13)
+    assert got["resid2"] == pytest.approx(r @ r, rel=1e-13)
+    assert got["objective"] == pytest.approx(tv + 0.5 * mu * (r @ r), rel=1e-13)
+    atv = np.sum(np.hypot(w[:N], w[N:])) + 0.5 * beta * (e @ e) + 0.5 * mu * (r @ r)
+    assert got["atv"] == pytest.approx(atv, rel=1e-13)
+    assert got["kkt_primal"] == pytest.approx(np.linalg.norm(e), rel=1e-13)
+    dual = D.T @ lam + mu * (A64.T @ r)
+    assert got["kkt_dual"] == pytest.approx(np.linalg.norm(dual), rel=1e-12)
+    assert got["lambda_max_norm"] == pytest.approx(np.max(np.hypot(lam[:N], lam[N:])), rel=1e-14)
+    wn = np.hypot(w[:N], w[N:])
+    nz = wn > 0
+    al = np.hypot(lam[:N][nz] - w[:N][nz] / wn[nz], lam[N:][nz] - w[N:][nz] / wn[nz])
+    assert got["lambda_align"] == pytest.approx(np.max(al), rel=1e-13)
+
+
 def test_warm_start_at_a_kkt_point_stays_there():
     # The warm start of the beta-continuation (Sec. 3.1; u^0 and lambda^0 given, w^0 = 0):
     # at a KKT point (u*, lambda*) of eq. (eqftvdcs) the first w-step returns w* = D u*
