@@ -58,7 +58,9 @@ struct UsolveShape {
     static constexpr size_t O_WB = O_WA + WORK * 8;
     static constexpr size_t O_WL = O_WB + WORK * 8;            // w1, w2, l1, l2 of rows r0-1 .. r0+R-1
     static constexpr size_t O_COL = O_WL + 4 * (R + 1) * NN * 4;   // QC columns, cluster-written
-    static constexpr size_t O_RED = O_COL + (size_t)COLFFT * 8;
+    // reciprocal divisors of this block's column slots (and of column n/2 for slot 0)
+    static constexpr size_t O_RDIV = O_COL + (size_t)COLFFT * 8;
+    static constexpr size_t O_RED = O_RDIV + (size_t)(QC + 1) * NN * 4;
     static constexpr size_t SMEM = O_RED + (64 + 2 * 16) * 8;
     static_assert(NN % C == 0 && R % 2 == 0, "each block owns an even number of rows");
     static_assert((NN / 2) % C == 0, "whole column slots per block");
@@ -144,6 +146,7 @@ __global__ void __launch_bounds__(US_THREADS, 1) k_usolve_cluster(
     float2* wb = reinterpret_cast<float2*>(smem + S::O_WB);
     float* swl = reinterpret_cast<float*>(smem + S::O_WL);       // [4][(R+1) NN]
     float2* col = reinterpret_cast<float2*>(smem + S::O_COL);    // [QC][NN], cluster-written
+    float* rdiv = reinterpret_cast<float*>(smem + S::O_RDIV);   // [QC + 1][NN]
     float2* red = reinterpret_cast<float2*>(smem + S::O_RED);    // [64] block reduction
     float2* cred = red + 64;                                     // [C][2] cluster partials
 
@@ -198,7 +201,17 @@ __global__ void __launch_bounds__(US_THREADS, 1) k_usolve_cluster(
     cp_async_wait_all();
     __syncthreads();
     // a1-a3 up to D^T y need no g: under a programmatic dependent launch they run
-    // while the products finish
+    // while the products finish.  So do the reciprocals 1 / (beta Lambda_pq + mu/tau)
+    // of this block's column slots, which phase B only multiplies by: rdiv[f n + p]
+    // for slot q0 + f (column 0 for slot 0), rdiv[QC n + p] for column n/2.
+    {
+        const int q0r = rank * QC;
+        for (int i = tid; i < (QC + 1) * NN; i += nthr) {
+            const int f = i / NN, p = i - f * NN;
+            const int q = f < QC ? q0r + f : NN / 2;
+            rdiv[i] = 1.0f / solve_divisor(s2, p, q, beta, mu_over_tau);
+        }
+    }
     step_wshrink<NN>(su, swl, WL, R, r0, beta, pending, sy1, sy2, wdst, ldst, tid, nthr);
     __syncthreads();
     step_dty<NN>(sy1, sy2, R, wa, tid, nthr);
@@ -219,9 +232,9 @@ __global__ void __launch_bounds__(US_THREADS, 1) k_usolve_cluster(
     float2* X = fft_block<NN, false>(col, wb, tw, ncol, NN);
     float2* other = (X == col) ? wb : col;
     for (int i = tid; i < ncol * NN; i += nthr) {
-        const int f = i / NN, p = i - f * NN;
+        const int f = i / NN;
         if (q0 + f == 0) continue;   // slot 0: below
-        const float rd = 1.0f / solve_divisor(s2, p, q0 + f, beta, mu_over_tau);
+        const float rd = rdiv[i];
         float2 v = X[i];
         v.x *= rd;
         v.y *= rd;
@@ -237,8 +250,8 @@ __global__ void __launch_bounds__(US_THREADS, 1) k_usolve_cluster(
             const float2 zk = X[k], zm = X[km];
             float2 c0 = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
             float2 cn = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-            const float r0 = 1.0f / solve_divisor(s2, k, 0, beta, mu_over_tau);
-            const float rn = 1.0f / solve_divisor(s2, k, NN / 2, beta, mu_over_tau);
+            const float r0 = rdiv[k];
+            const float rn = rdiv[QC * NN + k];
             c0.x *= r0;
             c0.y *= r0;
             cn.x *= rn;
