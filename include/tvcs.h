@@ -151,7 +151,8 @@ tvcs_status tvcs_solve(tvcs_handle h, const float* f, float* u, tvcs_result* res
 /*
  * Solves `count` problems.  hs[i] are handles, f[i] (m_i values) and u[i]
  * (n_i*n_i values) host or device pointers; mu (nullable) overrides each
- * handle's mu; res (nullable) receives count summaries.  When every hs[i] is
+ * handle's mu (every mu[i] finite and > 0, else TVCS_ERR_INVALID_ARG before
+ * any handle is used); res (nullable) receives count summaries.  When every hs[i] is
  * the same handle created with precision TVCS_PREC_BF16X2 (and count <= 256),
  * all images iterate together: their u-steps run as one batched launch and
  * their products as tensor-core GEMMs (see tvcs_apply_batched); each image

@@ -780,7 +780,8 @@ tvcs_status tvcs_solve_batched(const tvcs_handle* hs, int count, const float* co
     if (!hs || !f || !u) return fail(TVCS_ERR_INVALID_ARG, "hs, f and u must be non-NULL");
     for (int i = 0; i < count; ++i) {
         if (!hs[i] || !f[i] || !u[i]) return fail(TVCS_ERR_INVALID_ARG, "entry %d is NULL", i);
-        if (mu && !(mu[i] > 0.0)) return fail(TVCS_ERR_INVALID_ARG, "mu[%d] must be > 0", i);
+        if (mu && (!(mu[i] > 0.0) || !isfinite(mu[i])))
+            return fail(TVCS_ERR_INVALID_ARG, "mu[%d] must be finite and > 0", i);
     }
     bool shared = hs[0]->opt.precision == TVCS_PREC_BF16X2 && count <= 256 && hs[0]->N % 128 == 0;
     for (int i = 1; i < count && shared; ++i) shared = hs[i] == hs[0];

@@ -79,4 +79,12 @@ def test_null_handle_and_batch_arguments(tv):
     assert "null handle" in tv.tvcs_last_error()
     assert lib.tvcs_solve_batched(None, -1, None, None, None, None) == tv.TVCS_ERR_INVALID_ARG
     assert lib.tvcs_solve_batched(None, 0, None, None, None, None) == tv.TVCS_OK
+    # per-problem mu overrides are checked before any handle is touched
+    buf = (ctypes.c_float * 4)()
+    hs = (ctypes.c_void_p * 1)(ctypes.addressof(buf))
+    fs = (ctypes.c_void_p * 1)(ctypes.addressof(buf))
+    for bad in (0.0, -1.0, float("nan"), float("inf")):
+        mus = (ctypes.c_double * 1)(bad)
+        assert lib.tvcs_solve_batched(hs, 1, fs, fs, mus, None) == tv.TVCS_ERR_INVALID_ARG
+        assert "mu[0]" in tv.tvcs_last_error()
     assert lib.tvcs_destroy(None) == tv.TVCS_OK
