@@ -135,6 +135,27 @@ def test_batched_per_image_stop(tv):
     tv.tvcs_destroy(h)
 
 
+def test_batched_zero_measurements_leave_after_one_iteration(tv):
+    # an image with f = 0 stops after its first iteration with u = 0 exactly (reading C5)
+    # and leaves the GEMMs; the other images run on and still match the oracle
+    A, ubars, F, mus, _ = synth.workload_shared_batch(count=5, n=32, ratio=0.3, seed=8, n_ellipses=6)
+    m, N = A.shape
+    tau = oracle.default_tau(A)
+    F = [F[b] for b in range(5)]
+    F[2] = np.zeros(m, np.float32)
+    h = bf16_handle(tv, A, m, 32, mu=1e3, beta=20.0, tau=tau, max_iter=3000, tol=1e-4)
+    us = [np.full(N, np.nan, np.float32) for _ in range(5)]
+    res = tv.tvcs_solve_batched([h] * 5, F, us, [50.0] * 5)
+    assert res[2].iters == 1 and res[2].stopped_by_tol == 1
+    assert not np.any(us[2]) and res[2].objective == 0.0
+    for b in (0, 1, 3, 4):
+        ref = oracle.solve(A, F[b], 32, 50.0, 20.0, tau, tol=1e-4, max_iter=3000)
+        assert res[b].iters > 1 and res[b].stopped_by_tol == 1
+        assert abs(res[b].iters - ref.info["iters"]) <= max(2, ref.info["iters"] // 50)
+        assert rel(us[b], ref.u) <= 1e-3
+    tv.tvcs_destroy(h)
+
+
 def test_batched_iteration_count_not_a_multiple_of_the_loop_body(tv):
     # the loop graph holds 4 iterations per body: a run of 7 ends inside a body, and
     # the GEMMs and fix-ups of the rest of the body must not change any image

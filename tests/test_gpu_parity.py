@@ -356,6 +356,50 @@ def test_workload_n128_300_iterations(tv):
     tv.tvcs_destroy(h)
 
 
+def test_workload_n128_is_positively_homogeneous(tv):
+    # At the full benchmark size, where the oracle is compared above: the problem
+    # (4 f, mu / 4, beta / 4) has the minimisers 4 u*, and every step of the iteration
+    # commutes with that scaling (the shrink threshold 1/beta, the divisor
+    # beta Lambda_pq + mu/tau, the terms beta w and mu g).  With a power of two every
+    # binary32 operation of the kernels commutes with it too, so the runs agree bit for bit.
+    P = synth.workload_n128()
+    tau = oracle.default_tau(P.A, 100)
+    A = torch.from_numpy(P.A).cuda()
+    us, objs = [], []
+    for c in (1.0, 4.0):
+        opt = tv.tvcs_default_options()
+        opt.tau = tau
+        opt.max_iter = 300
+        h = tv.tvcs_create(A, 0, P.m, P.n, P.mu / c, P.beta / c, 0.0, opt)
+        u = torch.empty(P.N, dtype=torch.float32, device="cuda")
+        res = tv.tvcs_solve(h, torch.from_numpy(c * P.f).cuda(), u)
+        assert res.iters == 300
+        us.append(u.cpu().numpy())
+        objs.append(res.objective)
+        tv.tvcs_destroy(h)
+    assert np.any(us[0])
+    assert np.array_equal(us[1], 4.0 * us[0])
+    assert objs[1] == pytest.approx(4.0 * objs[0], rel=1e-12)
+
+
+@pytest.mark.parametrize("algo", [0, 1])
+def test_zero_measurements_give_the_zero_image(tv, algo):
+    # f = 0: u = 0 is the minimiser, u^0 = A^T f = 0, and eq. (stop) with reading C5
+    # (||u^k|| = 0: stop once ||u^{k+1}|| = 0) ends the solve after one iteration, as in
+    # the oracle.
+    P = small_problem(32, 307)
+    tau = oracle.default_tau(P.A)
+    h = make_handle(tv, P, tau, algo=algo, max_iter=50, tol=1e-4)
+    f0 = np.zeros(P.m, np.float32)
+    u = np.full(P.N, np.nan, np.float32)
+    res = tv.tvcs_solve(h, f0, u)
+    ref = oracle.solve(P.A, f0, P.n, P.mu, P.beta, tau, tol=1e-4, max_iter=50, algo=algo)
+    assert ref.info["iters"] == 1
+    assert res.iters == 1 and res.stopped_by_tol == 1 and res.status == tv.TVCS_OK
+    assert not np.any(u) and res.objective == 0.0
+    tv.tvcs_destroy(h)
+
+
 def test_workload_n128_300_iterations_ftvcs(tv):
     # Algorithm 1 (FTVCS, lambda = 0) on the benchmark workload at full size.
     P = synth.workload_n128()

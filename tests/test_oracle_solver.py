@@ -206,6 +206,42 @@ def test_stop_rule_first_crossing():
     assert rc[-1] <= 2e-3 and np.all(rc[:-1] > 2e-3)
 
 
+@pytest.mark.parametrize("algo", [oracle.IADM, oracle.FTVCS])
+def test_zero_measurements_stop_at_the_zero_image(algo):
+    # With f = 0 the objective sum_i ||D_i u|| + (mu/2)||Au||^2 is >= 0 and vanishes at
+    # u = 0, a minimiser.  The back-projection A^T f is 0 and every step keeps u, w and
+    # lambda at 0, so eq. (stop) with reading C5 (||u^k|| = 0: stop once ||u^{k+1}|| = 0)
+    # ends the run after the first iteration.
+    P = _problem(16, 77, 1e3, 10.0)
+    tau = oracle.default_tau(P.A)
+    R = oracle.solve(P.A, np.zeros(P.m, np.float32), P.n, P.mu, P.beta, tau, tol=1e-4,
+                     max_iter=50, algo=algo)
+    assert R.info["iters"] == 1 and R.info["stopped_by_tol"] == 1
+    assert not np.any(R.u) and not np.any(R.w) and not np.any(R.lam)
+    assert R.info["objective"] == 0.0
+
+
+@pytest.mark.parametrize("algo", [oracle.IADM, oracle.FTVCS])
+def test_iteration_is_positively_homogeneous(algo):
+    # TV is positively homogeneous, so for c > 0 the problem (c f, mu / c, beta / c) has the
+    # minimisers c u* of (f, mu, beta), and each step of Algorithms 1-2 maps the iterates
+    # (u, w, lambda) of the first run to (c u, c w, lambda) of the second: the shrink
+    # threshold 1/beta, the u-step divisor beta Lambda_pq + mu/tau and the terms beta w and
+    # mu g of the right-hand side each scale so that the step commutes with c.  A term with
+    # the wrong power of beta or mu breaks that.  For c a power of two every binary64
+    # operation commutes with the scaling, so the two runs agree bit for bit.
+    P = _problem(16, 77, 1e3, 10.0)
+    tau = oracle.default_tau(P.A)
+    c = 4.0
+    R1 = oracle.solve(P.A, P.f, P.n, P.mu, P.beta, tau, max_iter=40, algo=algo)
+    R2 = oracle.solve(P.A, c * P.f, P.n, P.mu / c, P.beta / c, tau, max_iter=40, algo=algo)
+    assert np.any(R1.u)
+    assert np.array_equal(R2.u, c * R1.u)
+    assert np.array_equal(R2.w, c * R1.w)
+    assert np.array_equal(R2.lam, R1.lam)
+    assert R2.info["objective"] == c * R1.info["objective"]
+
+
 def test_iadm_objective_decreases_to_optimum_on_32x32():
     # Fig. 2 shows decreasing objective values; for IADM we check that the
     # objective approaches the optimal value (reading C13), and that IADM beats
