@@ -26,6 +26,9 @@
  *    call returns.
  *  - All device work is ordered on the handle's stream (tvcs_options.stream).
  *    Every call is synchronous: it returns after its device work finished.
+ *    The handle's stream does not wait for other streams: device arrays
+ *    written (or still read) by work on another stream must be complete when
+ *    the call is made, unless that stream is the handle's stream.
  *  - Errors: a negative tvcs_status, with a message for tvcs_last_error().
  *    No call aborts, throws or exits.  Arguments are validated before any
  *    device work, so invalid arguments never reach a kernel.

@@ -135,6 +135,24 @@ def _ptr(x, count: int | None = None, writable: bool = False):
     raise TypeError("unsupported array type %r" % type(x))
 
 
+def _ready(*arrays) -> None:
+    """The library orders its device work on the handle's stream, which does not
+    wait for other streams.  Before a call that reads or writes torch CUDA tensors,
+    finish the work queued on torch's current stream of each device involved (the
+    tensors' producers, and pending readers of output buffers): once per device."""
+    try:
+        import torch
+    except ImportError:
+        return
+    devs = set()
+    for a in arrays:
+        for x in (a if isinstance(a, (list, tuple)) else (a,)):
+            if isinstance(x, torch.Tensor) and x.is_cuda:
+                devs.add(x.device)
+    for d in devs:
+        torch.cuda.current_stream(d).synchronize()
+
+
 def tvcs_default_options() -> tvcs_options:
     o = tvcs_options()
     _lib.tvcs_default_options(ctypes.byref(o))
@@ -163,6 +181,7 @@ class Handle:
 def tvcs_create(A, seed: int, m: int, n: int, mu: float, beta: float, tol: float,
                 opt: tvcs_options | None = None) -> Handle:
     h = ctypes.c_void_p()
+    _ready(A)
     pa = _ptr(A, m * n * n) if A is not None else None
     _check(_lib.tvcs_create(ctypes.byref(h), pa, int(seed) & (2**64 - 1), int(m), int(n),
                             float(mu), float(beta), float(tol),
@@ -190,6 +209,7 @@ def tvcs_destroy(h: Handle) -> None:
 
 def tvcs_solve(h: Handle, f, u) -> tvcs_result:
     res = tvcs_result()
+    _ready(f, u)
     _check(_lib.tvcs_solve(h.ptr, _ptr(f, h.m), _ptr(u, h.N, True), ctypes.byref(res)))
     return res
 
@@ -197,6 +217,7 @@ def tvcs_solve(h: Handle, f, u) -> tvcs_result:
 def tvcs_solve_batched(hs, f_list, u_list, mu=None) -> list:
     count = len(hs)
     assert len(f_list) == count and len(u_list) == count
+    _ready(f_list, u_list)
     harr = (ctypes.c_void_p * count)(*[h.ptr.value for h in hs])
     farr = (ctypes.c_void_p * count)(*[_ptr(f, h.m).value for f, h in zip(f_list, hs)])
     uarr = (ctypes.c_void_p * count)(*[_ptr(u, h.N, True).value for u, h in zip(u_list, hs)])
@@ -211,6 +232,7 @@ def tvcs_solve_continuation(h: Handle, f, u, betas) -> list:
     n = len(betas)
     barr = (ctypes.c_double * n)(*[float(b) for b in betas])
     res = (tvcs_result * n)()
+    _ready(f, u)
     _check(_lib.tvcs_solve_continuation(h.ptr, _ptr(f, h.m), _ptr(u, h.N, True), barr, n, res))
     return list(res)
 
@@ -228,10 +250,12 @@ _STATE_SIZE = {TVCS_STATE_U: lambda h: h.N, TVCS_STATE_W: lambda h: 2 * h.N,
 
 
 def tvcs_get_state(h: Handle, which: int, dst) -> None:
+    _ready(dst)
     _check(_lib.tvcs_get_state(h.ptr, which, _ptr(dst, _STATE_SIZE[which](h), True)))
 
 
 def tvcs_set_state(h: Handle, which: int, src) -> None:
+    _ready(src)
     _check(_lib.tvcs_set_state(h.ptr, which, _ptr(src, _STATE_SIZE[which](h))))
 
 
@@ -252,6 +276,7 @@ def tvcs_time_stage(h: Handle, stage: int, reps: int) -> float:
 
 
 def tvcs_apply(h: Handle, x, y, r, g) -> None:
+    _ready(x, y, r, g)
     _check(_lib.tvcs_apply(h.ptr, _ptr(x, h.N), _ptr(y, h.m) if y is not None else None,
                            _ptr(r, h.m, True), _ptr(g, h.N, True)))
 
@@ -267,6 +292,7 @@ def tvcs_apply_noalloc(A, m: int, n: int, x, y, r, g, stream: int | None = None)
 
 def tvcs_apply_batched(h: Handle, count: int, X, Y, R, G) -> None:
     """R = A X - Y and G = A^T R for `count` images (rows of X, Y, R, G)."""
+    _ready(X, Y, R, G)
     _check(_lib.tvcs_apply_batched(h.ptr, int(count), _ptr(X, count * h.N),
                                    _ptr(Y, count * h.m) if Y is not None else None,
                                    _ptr(R, count * h.m, True), _ptr(G, count * h.N, True)))

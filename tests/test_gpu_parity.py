@@ -382,6 +382,28 @@ def test_workload_n128_is_positively_homogeneous(tv):
     assert objs[1] == pytest.approx(4.0 * objs[0], rel=1e-12)
 
 
+def test_binding_waits_for_the_torch_stream_that_wrote_f(tv):
+    # the handle's stream does not wait for torch's streams; the binding finishes the
+    # work queued on the current torch stream before the call, so an f whose copy sits
+    # behind a ~50 ms device delay on that stream is read complete
+    P = small_problem(32, 307)
+    tau = oracle.default_tau(P.A)
+    h = make_handle(tv, P, tau, max_iter=20)
+    u_ref = np.empty(P.N, np.float32)
+    tv.tvcs_solve(h, P.f, u_ref)
+    side = torch.cuda.Stream()
+    f_host = torch.from_numpy(P.f).pin_memory()
+    with torch.cuda.stream(side):
+        f = torch.zeros(P.m, dtype=torch.float32, device="cuda")
+        u = torch.full((P.N,), float("nan"), device="cuda")
+        torch.cuda._sleep(100_000_000)
+        f.copy_(f_host, non_blocking=True)
+        res = tv.tvcs_solve(h, f, u)
+    assert res.iters == 20
+    assert np.array_equal(u.cpu().numpy(), u_ref)
+    tv.tvcs_destroy(h)
+
+
 @pytest.mark.parametrize("algo", [0, 1])
 def test_zero_measurements_give_the_zero_image(tv, algo):
     # f = 0: u = 0 is the minimiser, u^0 = A^T f = 0, and eq. (stop) with reading C5
