@@ -5,7 +5,8 @@
 // 0 streams the rows into a 3-stage shared-memory ring with bulk asynchronous
 // copies (TMA, non-tensor form, one mbarrier per stage; A is read once per
 // call, with an L2 evict-first hint), the first stages before the dependency
-// wait on the preceding kernel.  All 512 threads own fixed columns: for each
+// wait on the preceding kernel, together with an L2 prefetch of the next 1 MB
+// of the block's rows.  All 512 threads own fixed columns: for each
 // row they form the dot product with x (warp shuffles + one named barrier),
 // compute r_i = dot - y_i, and fold r_i * A_i into per-thread accumulators of
 // A^T r.  Row i's data is used twice from shared memory and read from HBM once,
@@ -27,6 +28,9 @@ namespace tvcs {
 constexpr int PROD_CONS = 512;           // 16 warps; thread 0 also issues the TMA copies
 constexpr int PROD_THREADS = PROD_CONS;
 constexpr int PROD_NST = 3;
+// Rows of A prefetched into L2 per block before the dependency wait, beyond the
+// ring: 1 MB (16 rows at n = 128; 136 blocks then hold about L2's capacity).
+constexpr size_t PROD_PF_BYTES = 1024 * 1024;
 
 template <int V, int RL, int RS>
 struct ProdShape {
@@ -49,7 +53,7 @@ __global__ void __maxnreg__(128)
     k_products(const float* __restrict__ A, int m, const float* __restrict__ x,
                const float* __restrict__ y, float* __restrict__ r, float* __restrict__ gpart,
                float* __restrict__ g_out, float2* __restrict__ r2part, Ctrl* __restrict__ ctrl,
-               int mode, cudaGraphConditionalHandle cond, int set_cond, long long budget)
+               int mode, cudaGraphConditionalHandle cond, int set_cond, long long budget, int pf)
 {
     using S = ProdShape<V, RL, RS>;
     constexpr int N = S::N;
@@ -93,10 +97,20 @@ __global__ void __maxnreg__(128)
         tma_load_1d(stage + slot * S::STAGE_FLOATS, A + (size_t)(i0 + s * RS) * N, bytes,
                     &full[slot], pol);
     };
+    // The pf stages after the ring are prefetched into L2 before the wait as
+    // well (nothing waits for them): while the u-solve still runs, HBM streams
+    // more of A than the ring holds, and the ring's later copies find those
+    // rows in L2.  (Prefetching further ahead during the stream measured slower.)
+    auto prefetch = [&](int s) {
+        const int rows = min(RS, nrows - s * RS);
+        prefetch_l2_bulk(A + (size_t)(i0 + s * RS) * N, (uint32_t)rows * N * 4u);
+    };
     const int pre = min(PROD_NST, nst);
     int issued = 0;   // stages issued (thread 0)
-    if (tid == 0)
+    if (tid == 0) {
         for (; issued < pre; ++issued) issue(issued);
+        for (int s = pre; s < min(pre + pf, nst); ++s) prefetch(s);
+    }
     pdl_wait();   // x and the control block come from the preceding u-solve
     if (mode == MODE_ITER) {
         const int skip = ctrl->skip;
@@ -348,9 +362,10 @@ static void launch_prod_t(int grid, const ProdArgs& a, cudaStream_t s)
     }
     cfg.attrs = attr;
     cfg.numAttrs = na;
+    const int pf = (int)(PROD_PF_BYTES / (S::STAGE_FLOATS * 4));
     cudaLaunchKernelEx(&cfg, k_products<V, RL, RS>, a.A, a.m, a.x, a.y, a.r, a.gpart, a.g_out,
                        a.r2part, a.ctrl, a.mode, (cudaGraphConditionalHandle)a.cond, a.set_cond,
-                       a.budget);
+                       a.budget, pf);
 }
 
 template <int V, int RL, int RS>
