@@ -8,7 +8,7 @@
 //             nearest even); hi + lo is exact in binary32 and within 2^-16 |A|;
 //   FP8_BF16  A = s_i q + c, s_i = max_j |A_ij| / 448 per row, q = e4m3(A / s_i)
 //             (round to nearest even, saturating), c = bf16(A - s_i q).
-// Products accumulate in binary32; ||r||^2 in binary64.
+// Products accumulate in binary32; ||r||^2 as binary32 double-single pairs.
 //
 // A cluster of CS blocks shares each row: block k of the cluster owns columns
 // [k N/CS, (k+1) N/CS).  Each streams its column slice of the rows through a
@@ -195,12 +195,11 @@ __global__ void __launch_bounds__(CONS + 32, 1)
         if (tid == CONS) {
             const uint64_t pol = l2_policy_evict_first();
             const size_t col0 = (size_t)rank * NS;
-            bool ok = true;
+            int issued = 0;
             for (int s = 0; s < nrows; ++s) {
                 const int slot = s % NST;
                 if (s >= NST && !mbar_wait(&empty[slot], ((s / NST) - 1) & 1, budget)) {
                     set_error(ctrl, ERR_TIMEOUT);
-                    ok = false;
                     break;
                 }
                 const size_t row = (size_t)(i0 + s);
@@ -219,9 +218,12 @@ __global__ void __launch_bounds__(CONS + 32, 1)
                     tma_load_1d(dst + (size_t)NS, P1 + (row * N + col0) * 2, NS * 2u,
                                 &full[slot], pol);
                 }
+                ++issued;
             }
-            const int first = ok ? max(0, nrows - NST) : nrows;
-            for (int s = first; s < nrows; ++s) mbar_wait(&full[s % NST], (s / NST) & 1, budget);
+            // the last copy of every slot has landed before the block may leave (bounded),
+            // also when a wait gave up
+            for (int s = max(0, issued - NST); s < issued; ++s)
+                mbar_wait(&full[s % NST], (s / NST) & 1, budget);
         }
         __syncwarp();
         // stay for the final cluster barrier: no block leaves while peers may still write to it
