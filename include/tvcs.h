@@ -156,11 +156,15 @@ tvcs_status tvcs_solve(tvcs_handle h, const float* f, float* u, tvcs_result* res
  * (n_i*n_i values) host or device pointers; mu (nullable) overrides each
  * handle's mu (every mu[i] finite and > 0, else TVCS_ERR_INVALID_ARG before
  * any handle is used); res (nullable) receives count summaries.  When every hs[i] is
- * the same handle created with precision TVCS_PREC_BF16X2 (and count <= 256),
- * all images iterate together: their u-steps run as one batched launch and
- * their products as tensor-core GEMMs (see tvcs_apply_batched); each image
- * stops on its own eq. (stop), and with opt->batch_compact (the default) it
- * then leaves the GEMMs, whose work shrinks with the images still running.  When every hs[i] was created with a_mode
+ * the same handle created with precision TVCS_PREC_BF16X2, the images iterate
+ * together in groups of at most 256 (count > 256: ceil(count/256) groups of
+ * nearly equal size, one after another): a group's u-steps run as one batched
+ * launch and its products as tensor-core GEMMs (see tvcs_apply_batched); each
+ * image stops on its own eq. (stop), and with opt->batch_compact (the default)
+ * it then leaves the GEMMs, whose work shrinks with the images still running.
+ * An image that fails (TVCS_ERR_DIVERGED, TVCS_ERR_TIMEOUT) reports it in its
+ * result; the other images and groups still run, and the call returns that
+ * status.  When every hs[i] was created with a_mode
  * TVCS_A_REGENERATE (count <= 1024, all on one device with equal algo, beta
  * and init, init TVCS_INIT_ATF or TVCS_INIT_ZERO; n, m, seed, mu, tau, tol and
  * max_iter may differ), all problems iterate together in one loop graph on
@@ -244,13 +248,23 @@ tvcs_status tvcs_time_stage(tvcs_handle h, int stage, int reps, double* ms);
  * hi+lo splits of A and of the operands (X_hi A_hi + X_lo A_hi + X_hi A_lo,
  * binary32 accumulation).  X: count x n*n, Y: count x m (nullable), R: count x m,
  * G: count x n*n, image after image, host or device.  Requires a handle created
- * with precision TVCS_PREC_BF16X2, n*n a multiple of 128 and 1 <= count <= 256. */
+ * with precision TVCS_PREC_BF16X2, n*n a multiple of 128 and count >= 1 (more
+ * than 256 images run in groups of at most 256). */
 tvcs_status tvcs_apply_batched(tvcs_handle h, int count, const float* X, const float* Y,
                                float* R, float* G);
 
 /* Products alone on caller data: r = A x - y (y nullable: r = A x) and
  * g = A^T r, with the handle's stored A.  x: N, y: m, r: m, g: N. */
 tvcs_status tvcs_apply(tvcs_handle h, const float* x, const float* y, float* r, float* g);
+
+/* Test hook for the failure status TVCS_ERR_TIMEOUT (the paper has no
+ * counterpart).  With extra > 0, the grid barrier of the binary32 product kernel
+ * (n <= 128) waits for `extra` arrivals that never come: its bounded spin runs
+ * out after opt->timeout_cycles, every block records the timeout and returns,
+ * and the call (tvcs_apply, tvcs_solve, ...) returns TVCS_ERR_TIMEOUT with the
+ * handle still usable.  extra = 0 (the default) restores normal operation.
+ * Other storages and encoders return TVCS_ERR_UNSUPPORTED. */
+tvcs_status tvcs_test_hold_grid_barrier(tvcs_handle h, int extra);
 
 /* ---- Products without any device allocation -------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that
@@ -261,20 +275,24 @@ tvcs_status tvcs_apply(tvcs_handle h, const float* x, const float* y, float* r, 
  * r = A x - y (y nullable: r = A x) and g = A^T r as tvcs_apply, without a
  * handle and without allocating anything.
  *   A      m x n*n row-major binary32, device pointer; x: n*n, y: m (or NULL),
- *          r: m, g: n*n, all device pointers, owned by the caller
+ *          r: m, g: n*n, all device memory of the current device (or managed
+ *          memory), owned by the caller; host pointers and memory of another
+ *          GPU return TVCS_ERR_INVALID_ARG
  *   n      16, 32, 48, 64, 96 or 128; 1 <= m <= 2^24
  *   stream cudaStream_t (NULL: the legacy default stream); the call returns
- *          after its device work finished
+ *          after its device work finished.  It reads a status word back to the
+ *          host and synchronises the stream, so it cannot be recorded by a
+ *          stream capture: a capturing stream returns TVCS_ERR_INVALID_ARG
+ *          before any work.
  * Work memory: one file-scope device array of 12 MiB (per-block partial sums
  * of A^T r and a control block), which every GPU that loads the library holds
  * until the process exits.  Sizes whose partial sums do not fit return
  * TVCS_ERR_INVALID_ARG with a message naming the limit.  The first call on a
  * device performs one-time set-up on that device (it looks up the array's
- * device address and sets the kernels' shared-memory limit); make that first
- * call before any stream capture.  Every call on a device shares the same
- * array and clears the parts that must start at zero, so calls whose device
- * work overlaps (other host threads, other streams) race on it and must be
- * serialised by the caller. */
+ * device address and sets the kernels' shared-memory limit).  Every call on a
+ * device shares the same array and clears the parts that must start at zero,
+ * so calls whose device work overlaps (other host threads, other streams)
+ * race on it and must be serialised by the caller. */
 tvcs_status tvcs_apply_noalloc(const float* A, int m, int n, const float* x, const float* y,
                                float* r, float* g, void* stream);
 

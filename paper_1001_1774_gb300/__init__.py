@@ -38,7 +38,7 @@ EXPORTED = ["tvcs_default_options", "tvcs_create", "tvcs_create_partial_dct", "t
             "tvcs_solve_continuation",
             "tvcs_destroy", "tvcs_last_error", "tvcs_get_tau", "tvcs_get_state",
             "tvcs_set_state", "tvcs_iterate", "tvcs_run_stage", "tvcs_time_stage", "tvcs_apply",
-            "tvcs_apply_noalloc", "tvcs_apply_batched"]
+            "tvcs_apply_noalloc", "tvcs_apply_batched", "tvcs_test_hold_grid_barrier"]
 
 
 class tvcs_options(ctypes.Structure):
@@ -65,6 +65,7 @@ class TvcsError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__("tvcs status %d: %s" % (status, message))
         self.status = status
+        self.results = None   # per-problem summaries of a batched call that failed
 
 
 def _load() -> ctypes.CDLL:
@@ -93,6 +94,7 @@ def _load() -> ctypes.CDLL:
         "tvcs_apply": ([H, vp, vp, vp, vp], i),
         "tvcs_apply_noalloc": ([vp, i, i, vp, vp, vp, vp, vp], i),
         "tvcs_apply_batched": ([H, i, vp, vp, vp, vp], i),
+        "tvcs_test_hold_grid_barrier": ([H, i], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -223,7 +225,11 @@ def tvcs_solve_batched(hs, f_list, u_list, mu=None) -> list:
     uarr = (ctypes.c_void_p * count)(*[_ptr(u, h.N, True).value for u, h in zip(u_list, hs)])
     muarr = (ctypes.c_double * count)(*mu) if mu is not None else None
     res = (tvcs_result * count)()
-    _check(_lib.tvcs_solve_batched(harr, count, farr, uarr, muarr, res))
+    try:
+        _check(_lib.tvcs_solve_batched(harr, count, farr, uarr, muarr, res))
+    except TvcsError as e:
+        e.results = list(res)
+        raise
     return list(res)
 
 
@@ -283,8 +289,13 @@ def tvcs_apply(h: Handle, x, y, r, g) -> None:
 
 def tvcs_apply_noalloc(A, m: int, n: int, x, y, r, g, stream: int | None = None) -> None:
     """r = A x - y and g = A^T r from device tensors, allocating no device memory
-    (see include/tvcs.h for who needs this and its limits)."""
+    (see include/tvcs.h for who needs this and its limits).  stream: a raw
+    cudaStream_t; None runs on torch's current stream of the current device, so
+    the call is ordered after the work that produced the inputs there."""
     N = n * n
+    if stream is None:
+        import torch
+        stream = int(torch.cuda.current_stream().cuda_stream)
     _check(_lib.tvcs_apply_noalloc(_ptr(A, m * N), int(m), int(n), _ptr(x, N),
                                    _ptr(y, m) if y is not None else None, _ptr(r, m, True),
                                    _ptr(g, N, True), ctypes.c_void_p(stream or 0)))
@@ -296,6 +307,12 @@ def tvcs_apply_batched(h: Handle, count: int, X, Y, R, G) -> None:
     _check(_lib.tvcs_apply_batched(h.ptr, int(count), _ptr(X, count * h.N),
                                    _ptr(Y, count * h.m) if Y is not None else None,
                                    _ptr(R, count * h.m, True), _ptr(G, count * h.N, True)))
+
+
+def tvcs_test_hold_grid_barrier(h: Handle, extra: int) -> None:
+    """Timeout test hook: the product kernel's grid barrier waits for `extra`
+    arrivals that never come (0 restores normal operation)."""
+    _check(_lib.tvcs_test_hold_grid_barrier(h.ptr, int(extra)))
 
 
 def tvcs_last_error() -> str:

@@ -176,8 +176,8 @@ tvcs_status ensure_batch(tvcs_ctx* h, int count)
         return set_last_error(TVCS_ERR_UNSUPPORTED,
                               "the shared-A batched path needs A stored as bf16 hi+lo "
                               "(precision TVCS_PREC_BF16X2)");
-    if (count > 256)
-        return set_last_error(TVCS_ERR_INVALID_ARG, "at most 256 images per batched call");
+    if (count > BATCH_MAX)
+        return set_last_error(TVCS_ERR_INVALID_ARG, "at most %d images per batch", BATCH_MAX);
     if (h->N % 128 != 0)
         return set_last_error(TVCS_ERR_UNSUPPORTED, "batched path needs n*n a multiple of 128");
     if (!h->batch) {

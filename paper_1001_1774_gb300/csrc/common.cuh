@@ -114,6 +114,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
     return true;
 }
 
+// Bound of the waits that let a block's own asynchronous copies (or MMAs) land
+// after another wait gave up: never below 2^31 SM cycles (about a second), so
+// that a short timeout_cycles cannot make a block retire while its copies are
+// still writing to its shared memory.
+constexpr long long DRAIN_FLOOR_CYCLES = 1LL << 31;
+__device__ __forceinline__ long long drain_budget(long long budget)
+{
+    return budget > DRAIN_FLOOR_CYCLES ? budget : DRAIN_FLOOR_CYCLES;
+}
+
 // ---- bulk asynchronous copy global -> shared (TMA, non-tensor form) ----
 // Both addresses 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void tma_load_1d(void* dst_smem, const void* src_gmem, uint32_t bytes,

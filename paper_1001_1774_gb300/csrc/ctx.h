@@ -87,9 +87,13 @@ struct tvcs_ctx {
     float* dctC = nullptr;         // n x n DCT matrix, its transpose, 2 n x n scratch
     int *dsidx = nullptr, *dsperm = nullptr, *drowptr = nullptr;
     tvcs_uneven* uneven = nullptr; // uneven batch whose first handle is this one
+    int bar_extra = 0;             // timeout test hook (tvcs_test_hold_grid_barrier), else 0
 };
 
 namespace tvcs {
+// Images one shared-A batch holds (one thread per image in the batch condition
+// kernel's slot tables); larger calls run in groups.
+constexpr int BATCH_MAX = 256;
 tvcs_status set_last_error(tvcs_status s, const char* fmt, ...);
 void free_batch(tvcs_ctx* h);
 // Many images with the handle's A (all handles of a tvcs_solve_batched call equal).

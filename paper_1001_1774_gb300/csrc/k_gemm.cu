@@ -144,7 +144,8 @@ __global__ void __launch_bounds__(192, 1)
     uint64_t* empty = full + GM_NST;
     uint64_t* tfull = empty + GM_NST;    // [2] accumulator ready
     uint64_t* tempty = tfull + 2;        // [2] accumulator drained
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(tempty + 2);
+    uint64_t* mdrain = tempty + 2;       // the issuer's MMAs have finished (after a timeout)
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mdrain + 1);
 
     if (check_skip && ctrl->skip) return;
     int nb = min(ncols, GM_BN);   // columns of the MMAs and of the partial tiles
@@ -166,6 +167,7 @@ __global__ void __launch_bounds__(192, 1)
             mbar_init(&tfull[a], 1);
             mbar_init(&tempty[a], 4);
         }
+        mbar_init(mdrain, 1);
         fence_mbar_init();
     }
     if (warp == 1) {
@@ -208,7 +210,7 @@ __global__ void __launch_bounds__(192, 1)
             // leave no copy in flight
             const long long n_issued = it;
             for (long long j = (n_issued > GM_NST ? n_issued - GM_NST : 0); j < n_issued; ++j)
-                mbar_wait(&full[j % GM_NST], (uint32_t)(j / GM_NST) & 1u, budget);
+                mbar_wait(&full[j % GM_NST], (uint32_t)(j / GM_NST) & 1u, drain_budget(budget));
             (void)ok;
         }
     } else if (warp == 1) {
@@ -255,6 +257,10 @@ __global__ void __launch_bounds__(192, 1)
                 if (!ok) break;
                 tc_commit(&tfull[acc]);     // accumulator ready when all MMAs finish
                 ++seg;
+            }
+            if (!ok) {   // a wait gave up: the MMAs already issued finish before TMEM is freed
+                tc_commit(mdrain);
+                mbar_wait(mdrain, 0u, drain_budget(budget));
             }
         }
     } else {

@@ -53,7 +53,8 @@ __global__ void __maxnreg__(128)
     k_products(const float* __restrict__ A, int m, const float* __restrict__ x,
                const float* __restrict__ y, float* __restrict__ r, float* __restrict__ gpart,
                float* __restrict__ g_out, float2* __restrict__ r2part, Ctrl* __restrict__ ctrl,
-               int mode, cudaGraphConditionalHandle cond, int set_cond, long long budget, int pf)
+               int mode, cudaGraphConditionalHandle cond, int set_cond, long long budget, int pf,
+               int bar_extra)
 {
     using S = ProdShape<V, RL, RS>;
     constexpr int N = S::N;
@@ -128,7 +129,7 @@ __global__ void __maxnreg__(128)
         }
         if (skip) {   // leave no copy in flight
             if (tid == 0)
-                for (int s = 0; s < pre; ++s) mbar_wait(&full[s], 0u, budget);
+                for (int s = 0; s < pre; ++s) mbar_wait(&full[s], 0u, drain_budget(budget));
             return;
         }
     } else {
@@ -221,7 +222,7 @@ __global__ void __maxnreg__(128)
     }
     if (tid == 0 && !ok)   // a wait gave up: let the copies still in flight land (bounded)
         for (int s = max(0, issued - PROD_NST); s < issued; ++s)
-            mbar_wait(&full[s % PROD_NST], (s / PROD_NST) & 1, budget);
+            mbar_wait(&full[s % PROD_NST], (s / PROD_NST) & 1, drain_budget(budget));
 
     // ---------------- epilogue: partial A^T r and ||r||^2 ----------------
     named_barrier(1, PROD_CONS);   // every consumer is done with the stage ring
@@ -281,7 +282,10 @@ __global__ void __maxnreg__(128)
     if (tid == 0) {
         __threadfence();
         const unsigned long long t = atomicAdd(&ctrl->gbar, 1ull);
-        const unsigned long long target = (t / (unsigned long long)G + 1ull) * (unsigned long long)G;
+        // bar_extra (0 outside the timeout test) raises the target beyond what the
+        // grid's arrivals reach, so that only this bounded spin runs out
+        const unsigned long long target =
+            (t / (unsigned long long)G + 1ull) * (unsigned long long)G + (unsigned)bar_extra;
         const long long t0 = clock64();
         while (ld_acquire_u64(&ctrl->gbar) < target) {
             if (clock64() - t0 > budget) {
@@ -340,7 +344,7 @@ __global__ void __maxnreg__(128)
 // Shape table: n -> (V, RL, RS).  N = n^2 = 4 * (512/RL) * V.
 // ---------------------------------------------------------------------------
 template <int V, int RL, int RS>
-static void launch_prod_t(int grid, const ProdArgs& a, cudaStream_t s)
+static cudaError_t launch_prod_t(int grid, const ProdArgs& a, cudaStream_t s)
 {
     using S = ProdShape<V, RL, RS>;
     cudaLaunchConfig_t cfg = {};
@@ -363,9 +367,10 @@ static void launch_prod_t(int grid, const ProdArgs& a, cudaStream_t s)
     cfg.attrs = attr;
     cfg.numAttrs = na;
     const int pf = (int)(PROD_PF_BYTES / (S::STAGE_FLOATS * 4));
-    cudaLaunchKernelEx(&cfg, k_products<V, RL, RS>, a.A, a.m, a.x, a.y, a.r, a.gpart, a.g_out,
-                       a.r2part, a.ctrl, a.mode, (cudaGraphConditionalHandle)a.cond, a.set_cond,
-                       a.budget, pf);
+    return cudaLaunchKernelEx(&cfg, k_products<V, RL, RS>, a.A, a.m, a.x, a.y, a.r, a.gpart,
+                              a.g_out, a.r2part, a.ctrl, a.mode,
+                              (cudaGraphConditionalHandle)a.cond, a.set_cond, a.budget, pf,
+                              a.bar_extra);
 }
 
 template <int V, int RL, int RS>
@@ -422,13 +427,13 @@ cudaError_t prod_configure(int n)
     }
 }
 
-void launch_products(int n, int grid, const ProdArgs& a, cudaStream_t s)
+cudaError_t launch_products(int n, int grid, const ProdArgs& a, cudaStream_t s)
 {
     switch (n) {
-#define X(NN, V, RL, RS) case NN: launch_prod_t<V, RL, RS>(grid, a, s); break;
+#define X(NN, V, RL, RS) case NN: return launch_prod_t<V, RL, RS>(grid, a, s);
         TVCS_PROD_TABLE(X)
 #undef X
-        default: break;
+        default: return cudaErrorInvalidValue;
     }
 }
 
@@ -495,12 +500,16 @@ __global__ void __launch_bounds__(256) k_greduce(const float4* __restrict__ gpar
     }
 }
 
-void launch_greduce(const float* gpart, int P, int N, float* g, const Ctrl* ctrl, int mode,
-                    cudaStream_t s)
+cudaError_t launch_greduce(const float* gpart, int P, int N, float* g, const Ctrl* ctrl, int mode,
+                           cudaStream_t s)
 {
     const int N4 = N / 4;
-    k_greduce<<<(N4 + 31) / 32, 256, 0, s>>>(reinterpret_cast<const float4*>(gpart), P, N4,
-                                              reinterpret_cast<float4*>(g), ctrl, mode);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((N4 + 31) / 32, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.stream = s;
+    return cudaLaunchKernelEx(&cfg, k_greduce, reinterpret_cast<const float4*>(gpart), P, N4,
+                              reinterpret_cast<float4*>(g), ctrl, mode);
 }
 
 __global__ void k_normalize(const float* __restrict__ z, float* __restrict__ v, int N,

@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(CONS + 32, 1)
             // the last copy of every slot has landed before the block may leave (bounded),
             // also when a wait gave up
             for (int s = max(0, issued - NST); s < issued; ++s)
-                mbar_wait(&full[s % NST], (s / NST) & 1, budget);
+                mbar_wait(&full[s % NST], (s / NST) & 1, drain_budget(budget));
         }
         __syncwarp();
         // stay for the final cluster barrier: no block leaves while peers may still write to it

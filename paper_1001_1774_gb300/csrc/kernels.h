@@ -69,15 +69,18 @@ struct ProdArgs {
     int set_cond;
     long long budget;   // spin-wait bound, SM cycles
     int pdl;            // launch with a programmatic dependency on the preceding grid
+    int bar_extra;      // 0; > 0 only in the timeout test: the grid barrier's target is
+                        // raised by this many arrivals, which never come
 };
 
 bool prod_supported(int n);
 int prod_grid(int n, int m, int num_sms);   // number of blocks = number of partials P
 cudaError_t prod_configure(int n);          // opt-in shared memory size (call once per device)
-void launch_products(int n, int grid, const ProdArgs& a, cudaStream_t s);
+// Both return the launch's own status.
+cudaError_t launch_products(int n, int grid, const ProdArgs& a, cudaStream_t s);
 // g = sum_p gpart[p] (fixed order), wide grid; skipped when mode == MODE_ITER and ctrl->skip.
-void launch_greduce(const float* gpart, int P, int N, float* g, const Ctrl* ctrl, int mode,
-                    cudaStream_t s);
+cudaError_t launch_greduce(const float* gpart, int P, int N, float* g, const Ctrl* ctrl, int mode,
+                           cudaStream_t s);
 
 // Products with A in binary32 (n = 192, 256), bf16 hi+lo, or fp8 e4m3 + bf16
 // correction: clusters of CS blocks split each row's columns.

@@ -32,7 +32,7 @@ constexpr size_t kScratchBytes = 12u << 20;   // 12 MiB per device
 constexpr int kMaxDevices = 64;
 
 // Work memory of tvcs_apply_noalloc: per-block partial sums of A^T r, per-block
-// binary64 partials of ||r||^2 and a control block for the last-block ticket.
+// double-single partials of ||r||^2 and a control block for the last-block ticket.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_setup_mutex;
@@ -69,14 +69,18 @@ tvcs_status setup_device(int dev)
     return TVCS_OK;
 }
 
-bool is_device_pointer(const void* p)
+// True when p is device memory of device `dev` or managed memory (which any
+// device may access).  Device memory of another GPU is rejected: the kernels run
+// on `dev`, and without peer access a load from another GPU's memory faults.
+bool is_device_pointer_on(const void* p, int dev)
 {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -91,13 +95,31 @@ extern "C" tvcs_status tvcs_apply_noalloc(const float* A, int m, int n, const fl
     if (!prod_supported(n))
         return set_last_error(TVCS_ERR_INVALID_ARG,
                               "n = %d not supported (16, 32, 48, 64, 96, 128)", n);
-    if (!is_device_pointer(A) || !is_device_pointer(x) || !is_device_pointer(r) ||
-        !is_device_pointer(g) || (y && !is_device_pointer(y)))
-        return set_last_error(TVCS_ERR_INVALID_ARG, "all arrays must be device pointers");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // The call reads an error word back to the host and synchronises the stream,
+    // neither of which a stream capture can record: reject a capturing stream
+    // (or a legacy-stream call while another capture forbids it) before any work.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_last_error(TVCS_ERR_INVALID_ARG,
+                              "tvcs_apply_noalloc cannot run while a stream capture is active "
+                              "(cudaStreamIsCapturing: %s)", cudaGetErrorString(e));
+    }
+    if (cap != cudaStreamCaptureStatusNone)
+        return set_last_error(TVCS_ERR_INVALID_ARG,
+                              "tvcs_apply_noalloc cannot be captured into a CUDA graph "
+                              "(the stream is capturing)");
     int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return set_last_error(TVCS_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (!is_device_pointer_on(A, dev) || !is_device_pointer_on(x, dev) ||
+        !is_device_pointer_on(r, dev) || !is_device_pointer_on(g, dev) ||
+        (y && !is_device_pointer_on(y, dev)))
+        return set_last_error(TVCS_ERR_INVALID_ARG,
+                              "all arrays must be device memory of the current device (%d)", dev);
     tvcs_status st = setup_device(dev);
     if (st != TVCS_OK) return st;
 
@@ -115,7 +137,6 @@ extern "C" tvcs_status tvcs_apply_noalloc(const float* A, int m, int n, const fl
     float* gpart = reinterpret_cast<float*>(base);
     float2* r2part = reinterpret_cast<float2*>(base + b_gpart);
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(base + b_gpart + b_r2);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
 
     // The array keeps the previous call's contents: the control block (tickets,
     // error word) must start at zero; the partials are fully overwritten.
@@ -133,12 +154,17 @@ extern "C" tvcs_status tvcs_apply_noalloc(const float* A, int m, int n, const fl
     a.ctrl = ctrl;
     a.mode = MODE_PLAIN;
     a.budget = 1LL << 31;
-    launch_products(n, P, a, s);
-    launch_greduce(gpart, P, N, g, ctrl, MODE_PLAIN, s);
+    // Launch failures are this call's own: each launcher returns its launch status.
+    e = launch_products(n, P, a, s);
+    if (e == cudaSuccess) e = launch_greduce(gpart, P, N, g, ctrl, MODE_PLAIN, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_last_error(TVCS_ERR_CUDA, "tvcs_apply_noalloc: launch failed: %s",
+                              cudaGetErrorString(e));
+    }
     int err_word = 0;
     e = cudaMemcpyAsync(&err_word, &ctrl->error, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess)
         return set_last_error(TVCS_ERR_CUDA, "tvcs_apply_noalloc: %s", cudaGetErrorString(e));
     if (err_word == ERR_TIMEOUT)

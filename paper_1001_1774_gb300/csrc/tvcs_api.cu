@@ -146,6 +146,7 @@ void products(tvcs_ctx* h, const float* x, const float* y, float* r, float* gpar
     a.g_out = g;
     a.budget = budget_of(h);
     a.pdl = pdl;
+    a.bar_extra = h->bar_extra;
     launch_products(h->n, h->P, a, s);
 }
 
@@ -783,11 +784,33 @@ tvcs_status tvcs_solve_batched(const tvcs_handle* hs, int count, const float* co
         if (mu && (!(mu[i] > 0.0) || !isfinite(mu[i])))
             return fail(TVCS_ERR_INVALID_ARG, "mu[%d] must be finite and > 0", i);
     }
-    bool shared = hs[0]->opt.precision == TVCS_PREC_BF16X2 && count <= 256 && hs[0]->N % 128 == 0;
+    bool shared = hs[0]->opt.precision == TVCS_PREC_BF16X2 && hs[0]->N % 128 == 0;
     for (int i = 1; i < count && shared; ++i) shared = hs[i] == hs[0];
     if (shared) {
         CKS(check_handle(hs[0]));
-        return solve_batch(hs[0], count, f, u, mu, res);
+        if (count <= BATCH_MAX) return solve_batch(hs[0], count, f, u, mu, res);
+        // More images than one batch holds: groups of nearly equal size (the larger
+        // ones first, so that the loop graph is rebuilt at most once), each through
+        // the same tensor-core path.  A group whose images report a per-image
+        // failure does not stop the later groups.
+        const int groups = (count + BATCH_MAX - 1) / BATCH_MAX;
+        const int base = count / groups, extra = count % groups;
+        tvcs_status worst = TVCS_OK, err = TVCS_OK;
+        for (int gi = 0, off = 0; gi < groups; ++gi) {
+            const int c = base + (gi < extra ? 1 : 0);
+            tvcs_status st = solve_batch(hs[0], c, f + off, u + off, mu ? mu + off : nullptr,
+                                         res ? res + off : nullptr);
+            if (st == TVCS_ERR_DIVERGED || st == TVCS_ERR_TIMEOUT) {
+                if (err == TVCS_OK) err = st;
+            } else if (st < 0) {
+                return st;
+            } else if (st > worst) {
+                worst = st;
+            }
+            off += c;
+        }
+        if (err < 0) return fail(err, "an image of the batch failed (see its result)");
+        return worst;
     }
     if (uneven_eligible(hs, count)) {
         CKS(check_handle(hs[0]));
@@ -920,7 +943,31 @@ tvcs_status tvcs_apply_batched(tvcs_handle h, int count, const float* X, const f
     CKS(check_handle(h));
     if (count < 1) return fail(TVCS_ERR_INVALID_ARG, "count must be >= 1");
     if (!X || !R || !G) return fail(TVCS_ERR_INVALID_ARG, "X, R and G must be non-NULL");
-    return apply_batch(h, count, X, Y, R, G);
+    // groups of at most BATCH_MAX images (nearly equal sizes, the larger first)
+    const int groups = (count + BATCH_MAX - 1) / BATCH_MAX;
+    const int base = count / groups, extra = count % groups;
+    const size_t N = (size_t)h->N, m = (size_t)h->m;
+    for (int gi = 0, off = 0; gi < groups; ++gi) {
+        const int c = base + (gi < extra ? 1 : 0);
+        CKS(apply_batch(h, c, X + off * N, Y ? Y + off * m : nullptr, R + off * m, G + off * N));
+        off += c;
+    }
+    return TVCS_OK;
+}
+
+tvcs_status tvcs_test_hold_grid_barrier(tvcs_handle h, int extra)
+{
+    CKS(check_handle(h));
+    if (extra < 0) return fail(TVCS_ERR_INVALID_ARG, "extra must be >= 0");
+    if (h->use_q || h->regen || h->dct)
+        return fail(TVCS_ERR_UNSUPPORTED, "the hook acts on the binary32 product kernel (n <= 128)");
+    if (h->bar_extra != extra) {
+        h->bar_extra = extra;
+        // the loop graph captured the old value
+        if (h->exec) { cudaGraphExecDestroy(h->exec); h->exec = nullptr; }
+        if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+    }
+    return TVCS_OK;
 }
 
 tvcs_status tvcs_apply(tvcs_handle h, const float* x, const float* y, float* r, float* g)

@@ -227,3 +227,36 @@ def test_batched_workload_256_images_n128(tv):
         print("image %d mu %.0f rel err %.2e" % (b, mus[b], err))
         assert err <= 1e-4
     tv.tvcs_destroy(h)
+
+
+def test_batched_more_than_256_images_run_in_groups(tv):
+    # 300 images: two groups of 150 through the same tensor-core path.  An image's
+    # column is independent of the others, so every image equals its result in a
+    # call that holds only its own group; a sample matches the FP64 oracle.
+    A, ubars, F, mus, _ = synth.workload_shared_batch(count=300, n=32, ratio=0.3, seed=12, n_ellipses=6)
+    m, N = A.shape
+    tau = oracle.default_tau(A)
+    iters = 30
+    h = bf16_handle(tv, A, m, 32, mu=1e3, tau=tau, max_iter=iters)
+    Fd = torch.from_numpy(F).cuda()
+    U = torch.empty((300, N), dtype=torch.float32, device="cuda")
+    res = tv.tvcs_solve_batched([h] * 300, [Fd[b] for b in range(300)], [U[b] for b in range(300)], mus)
+    assert all(r.iters == iters for r in res)
+    U2 = torch.empty((150, N), dtype=torch.float32, device="cuda")
+    tv.tvcs_solve_batched([h] * 150, [Fd[150 + b] for b in range(150)], [U2[b] for b in range(150)],
+                          mus[150:])
+    Uh, U2h = U.cpu().numpy(), U2.cpu().numpy()
+    assert np.array_equal(Uh[150:], U2h)
+    for b in (0, 149, 150, 299):
+        ref = oracle.solve(A, F[b], 32, mus[b], 10.0, tau, max_iter=iters)
+        assert rel(Uh[b], ref.u) <= 1e-4, b
+    # the products entry point groups the same way
+    X = np.ascontiguousarray(Uh[:260])
+    R = np.empty((260, m), np.float32)
+    G = np.empty((260, N), np.float32)
+    tv.tvcs_apply_batched(h, 260, X, F[:260], R, G)
+    R1 = np.empty((130, m), np.float32)
+    G1 = np.empty((130, N), np.float32)
+    tv.tvcs_apply_batched(h, 130, np.ascontiguousarray(X[130:]), np.ascontiguousarray(F[130:260]), R1, G1)
+    assert np.array_equal(R[130:], R1) and np.array_equal(G[130:], G1)
+    tv.tvcs_destroy(h)
