@@ -46,6 +46,8 @@ def parse_args():
     ap.add_argument("--ref-budget", type=float, default=60.0,
                     help="seconds of oracle iterations the reference arm times")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sub-records", action="store_true",
+                    help="skip the short batch256 and n256 segments of the default line")
     ap.add_argument("--workload", choices=["n128", "n32", "n256", "batch256", "batch256tol", "uneven64",
                                            "dct128"],
                     default="n128",
@@ -217,12 +219,20 @@ def batch_launch_iters(iters):
     return -(-iters // 4) * 4
 
 
-def loop_launch_iters(iters):
-    """Iterations whose kernels a single-image run launches: the loop graph's body
-    holds 16 iterations, and the ones after the stopping iteration of the last
-    body launch and skip their work."""
+def loop_launch_iters(iters, max_iter=None):
+    """Iterations whose kernels a single-image run launches: the run's first
+    16 * (max_iter // 16) iterations go through a WHILE graph of 16-iteration
+    bodies and the remaining max_iter % 16 through a graph of their own.  A
+    fixed-count run (max_iter = iters) launches exactly its iterations; a run
+    that stopped by tol after `iters` also launches the rest of its last body
+    and the final graph, whose iterations skip their work."""
+    if max_iter is None or iters >= max_iter:
+        return iters if max_iter is None else max_iter
     body = 16
-    return -(-iters // body) * body
+    nb, rest = max_iter // body, max_iter % body
+    if iters <= nb * body:
+        return -(-iters // body) * body + rest
+    return max_iter
 
 
 # ----------------------------------------------------------------------------- CPU oracle sample
@@ -249,6 +259,25 @@ def oracle_sample(P, tau, budget_s=20.0, want_u=False, algo=0, max_iters=None):
 
 
 # ----------------------------------------------------------------------------- our arm
+
+def sub_records(tv, args, stream, main):
+    """The other configurations of the benchmark, short: the 256-image shared-A
+    batch (tensor-core GEMMs) and the 256 x 256 image with A stored as binary32,
+    bf16 hi+lo and fp8 + bf16 correction (product kernels against HBM)."""
+    steps = 20
+    out = {}
+    b = batch_segment(tv, steps, 3, stream, want_parity=not args.no_cpu_baseline)
+    for k in ("_A", "_F", "_mus"):
+        b.pop(k)
+    single_recons = main["recons_per_s"]
+    b["vs_single_image_fp32"] = {"recons_per_s_single": single_recons,
+                                 "ratio": b["recons_per_s"] / single_recons}
+    out["batch256"] = b
+    for p in (0, 1, 2):
+        out["n256_" + STORAGE[p][0]] = n256_segment(tv, p, steps, stream)
+    return out
+
+
 
 def run_ours(args):
     import numpy as np
@@ -388,6 +417,19 @@ def run_ours(args):
                 err = float(np.linalg.norm(u_gpu - ref) / np.linalg.norm(ref))
                 out["parity_vs_oracle"] = {"rel_image_err": err, "iters": ITERS_PER_RECON,
                                            "ok": err <= 1e-4}
+            # the same oracle on one core (a bounded sample of the same workload)
+            import oracle
+            nthr = oracle.num_threads()
+            oracle.set_num_threads(1)
+            try:
+                cb1 = oracle_sample(P, tau, budget_s=8.0, algo=1 if args.algo == "ftvcs" else 0)
+            finally:
+                oracle.set_num_threads(nthr)
+            out["cpu_baseline"]["one_thread"] = {
+                "value": cb1["value"], "unit": "iter/s", "cores": 1,
+                "sample": "%d iterations of the same workload, %.1f s" % (cb1["iters"], cb1["seconds"])}
+        if ws == 1 and args.workload == "n128" and not args.no_sub_records:
+            out["sub_records"] = sub_records(tv, args, stream, out)
     tv.tvcs_destroy(h)
     if ws > 1:
         dist.barrier()
@@ -400,27 +442,66 @@ def ctypes_stream(stream) -> int:
     return int(stream.cuda_stream)
 
 
-# ----------------------------------------------------------------------------- batched arm
+# ----------------------------------------------------------------------------- sub-records
 
-def run_batched(args):
-    """256 images of 128 x 128 sharing one 4915 x 16384 A stored as bf16 hi/lo; a
-    step is one iteration of all 256 images (u-steps as one batched launch, the
-    products as two tcgen05 BF16x3 GEMMs)."""
+def n256_segment(tv, precision, steps, stream):
+    """The 256 x 256 single-image workload (m = 13107, A generated on the device
+    from its seed and stored per `precision`): the product kernel's time against
+    its algorithmic bytes, and `steps` iterations of the loop."""
+    import torch
+    import synth
+    sp = workload_spec("n256", 0)
+    P = synth.make_problem(sp["n"], sp["ratio"], sp["seed"], sp["n_ellipses"], sp["mu"], sp["beta"],
+                           0.0, steps, sp["noise_c"], materialise=False)
+    opt = tv.tvcs_default_options()
+    opt.precision = precision
+    opt.max_iter = steps
+    opt.stream = ctypes_stream(stream)
+    h = tv.tvcs_create(None, P.seed, P.m, P.n, P.mu, P.beta, 0.0, opt)
+    with torch.cuda.stream(stream):
+        f = torch.from_numpy(P.f).cuda()
+        u = torch.empty(P.N, dtype=torch.float32, device="cuda")
+    stream.synchronize()
+    tv.tvcs_solve(h, f, u)                       # state, loop graphs
+    tv.tvcs_iterate(h, 3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    tv.tvcs_iterate(h, steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    reps = 20
+    prod_us = tv.tvcs_time_stage(h, 2, reps) * 1e3 / reps
+    tv.tvcs_destroy(h)
+    peak, peak_src = hbm_peak()
+    A_bytes = P.m * P.N * STORAGE[precision][1] + (4 * P.m if precision == 2 else 0)
+    alg = A_bytes + 4 * (P.N + 2 * P.m)
+    achieved = alg / (prod_us * 1e-6) / 1e9
+    return {"workload": "n256_m13107_%s_single_image" % STORAGE[precision][0],
+            "value": steps / (ms / 1e3), "unit": "iter/s", "steps": steps,
+            "recons_per_s": steps / (ms / 1e3) / ITERS_PER_RECON,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "kernel": "k_products_q<%d>" % precision,
+                         "algorithmic_bytes_per_launch": alg, "launch_us": prod_us,
+                         "peak_source": peak_src}}
+
+
+def batch_segment(tv, steps, warmup, stream, want_parity=True):
+    """256 images of 128 x 128 sharing one 4915 x 16384 A (bf16 hi/lo): `steps`
+    batched iterations; the GEMM pair's time against the bf16 peak; image 0
+    against the FP64 oracle after the same iterations."""
     import numpy as np
     import torch
-
     import synth
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_1001_1774_gb300 as tv
     B = 256
     A, ubars, F, mus, _ = synth.workload_shared_batch(count=B, n=128, ratio=0.3, seed=1)
     m, N = A.shape
-    stream = torch.cuda.Stream()
     opt = tv.tvcs_default_options()
     opt.precision = tv.TVCS_PREC_BF16X2
     opt.stream = ctypes_stream(stream)
-    opt.max_iter = max(args.warmup, 3)
+    opt.max_iter = max(warmup, 3)
     with torch.cuda.stream(stream):
         A_dev = torch.from_numpy(A).cuda()
         F_dev = torch.from_numpy(F).cuda()
@@ -431,22 +512,20 @@ def run_batched(args):
     tau = tv.tvcs_get_tau(h)
     fl = [F_dev[b] for b in range(B)]
     ul = [U_dev[b] for b in range(B)]
-    tv.tvcs_solve_batched([h] * B, fl, ul, mus)      # warm-up: builds A^T, plans, the graph
-    # the timed run: args.steps iterations of all images (tol 0: fixed count)
-    h2_opt = opt
+    tv.tvcs_solve_batched([h] * B, fl, ul, mus)      # warm-up: A^T, plans, loop graph
     tv.tvcs_destroy(h)
-    h2_opt.max_iter = args.steps
-    h2_opt.tau = tau
+    opt.max_iter = steps
+    opt.tau = tau
     with torch.cuda.stream(stream):
         A_dev = torch.from_numpy(A).cuda()
     stream.synchronize()
-    h = tv.tvcs_create(A_dev, 0, m, 128, 1e3, 10.0, 0.0, h2_opt)
+    h = tv.tvcs_create(A_dev, 0, m, 128, 1e3, 10.0, 0.0, opt)
     del A_dev
-    tv.tvcs_solve_batched([h] * B, fl, ul, mus)      # builds the state and the loop graph
-    sampler = ClockSampler(0)
+    tv.tvcs_solve_batched([h] * B, fl, ul, mus)      # state and the loop graph of this count
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    sampler = ClockSampler(0)
     sampler.start()
     time.sleep(0.2)
     ev0.record(stream)
@@ -455,63 +534,83 @@ def run_batched(args):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
-    assert all(r.iters == args.steps for r in res)
+    assert all(r.iters == steps for r in res)
     loop_ms = res[0].ms
-    reps = 50
-    torch.cuda.nvtx.range_push("stage3")
+    reps = 20
     gemm_us = tv.tvcs_time_stage(h, 3, reps) * 1e3 / reps
-    torch.cuda.nvtx.range_pop()
-    torch.cuda.nvtx.range_push("stage4")
     fix_us = tv.tvcs_time_stage(h, 4, reps) * 1e3 / reps
-    torch.cuda.nvtx.range_pop()
-    torch.cuda.nvtx.range_push("stage5")
     us_us = tv.tvcs_time_stage(h, 5, reps) * 1e3 / reps
-    torch.cuda.nvtx.range_pop()
+    U0 = U_dev[0].cpu().numpy()
     # end to end with pinned host buffers (f in, images out inside the timed call)
     F_host = torch.from_numpy(F).pin_memory()
     U_host = torch.empty((B, N), dtype=torch.float32).pin_memory()
     t0 = time.perf_counter()
     tv.tvcs_solve_batched([h] * B, [F_host[b] for b in range(B)], [U_host[b] for b in range(B)], mus)
     e2e_s = time.perf_counter() - t0
-    U_gpu = U_host.numpy().copy()
     tv.tvcs_destroy(h)
-
-    flops_gemm_pair = 2 * 3 * 2.0 * m * N * B        # two GEMMs, three bf16 terms each
+    flops = 2 * 3 * 2.0 * m * N * B                  # two GEMMs, three bf16 terms each
     peak = bf16_peak()
-    value = B * args.steps / (ms / 1e3)
-    out = {"metric": METRIC, "value": value, "unit": "image-iter/s", "n_gpus": 1,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3->f32",
-           "data": "synthetic (seeded phantoms, Philox Gaussian A)",
-           "recons_per_s": value / ITERS_PER_RECON,
-           "config": {"workload": "batch256_n128_m4915_bf16x2_shared_A", "images": B, "n": 128,
-                      "m": m, "mu": "cycling 2e2, 5e2, 1e3, 2e3", "iters_per_recon": ITERS_PER_RECON,
-                      "l2": "inputs larger than L2 (A and A^T bf16 hi/lo = 644 MB); no flush"},
-           "roofline": {"bound": "tensor", "achieved": flops_gemm_pair / (gemm_us * 1e-6) / 1e12,
-                        "peak": peak[0], "unit": "TFLOP/s",
-                        "frac": flops_gemm_pair / (gemm_us * 1e-6) / 1e12 / peak[0], "traffic": None,
-                        "kernel": "k_gemm_bf16x3 (R = A U and G = A^T R, 3 bf16 MMAs per product)",
-                        "flops_per_iteration": flops_gemm_pair, "launch_pair_us": gemm_us,
+    tf = flops / (gemm_us * 1e-6) / 1e12
+    value = B * steps / (ms / 1e3)
+    out = {"workload": "batch256_n128_m4915_bf16x2_shared_A", "value": value,
+           "unit": "image-iter/s", "steps": steps, "recons_per_s": value / ITERS_PER_RECON,
+           "ms_per_step": ms / steps,
+           "roofline": {"bound": "tensor", "achieved": tf, "peak": peak[0], "unit": "TFLOP/s",
+                        "frac": tf / peak[0], "kernel": "k_gemm_bf16x3 pair (R = A U, G = A^T R)",
+                        "flops_per_iteration": flops, "launch_pair_us": gemm_us,
                         "peak_source": peak[1]},
            "stage_us": {"gemm_pair": gemm_us, "fixups": fix_us, "usolve_batched": us_us,
-                        "loop_per_iteration": loop_ms * 1e3 / args.steps},
-           "e2e": {"value": B * args.steps / e2e_s, "unit": "image-iter/s",
-                   "h2d_bytes_per_step": 4 * m * B / args.steps,
-                   "d2h_bytes_per_step": 4 * N * B / args.steps},
-           "gpu_launches": 6 * batch_launch_iters(args.steps) + 8, "clocks": clocks, "tau": tau}
-    if not args.no_cpu_baseline:
+                        "loop_per_iteration": loop_ms * 1e3 / steps},
+           "e2e": {"value": B * steps / e2e_s, "unit": "image-iter/s",
+                   "h2d_bytes_per_step": 4 * m * B / steps, "d2h_bytes_per_step": 4 * N * B / steps},
+           "gpu_launches": 6 * batch_launch_iters(steps) + 8, "clocks": clocks, "tau": tau,
+           "_A": A, "_F": F, "_mus": mus}
+    if want_parity:
         import oracle
-        P = synth.Problem("batch_img0", 128, m, 1, mus[0], 10.0, 0.0, args.steps, 0.0, ubars[0], A,
+        ref = oracle.solve(A, F[0], 128, mus[0], 10.0, tau, max_iter=steps)
+        err = float(np.linalg.norm(U0 - ref.u.ravel()) / np.linalg.norm(ref.u))
+        out["parity_vs_oracle"] = {"rel_image_err": err, "image": 0, "iters": steps,
+                                   "ok": err <= 1e-4}
+    return out
+
+
+# ----------------------------------------------------------------------------- batched arm
+
+def run_batched(args):
+    """256 images of 128 x 128 sharing one 4915 x 16384 A stored as bf16 hi/lo; a
+    step is one iteration of all 256 images (u-steps as one batched launch, the
+    products as two tcgen05 BF16x3 GEMMs)."""
+    import torch
+
+    import synth
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1001_1774_gb300 as tv
+    stream = torch.cuda.Stream()
+    b = batch_segment(tv, args.steps, args.warmup, stream,
+                      want_parity=not args.no_cpu_baseline and args.steps <= ITERS_PER_RECON)
+    A, F, mus = b.pop("_A"), b.pop("_F"), b.pop("_mus")
+    m, N = A.shape
+    out = {"metric": METRIC, "value": b["value"], "unit": "image-iter/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": b["ms_per_step"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3->f32",
+           "data": "synthetic (seeded phantoms, Philox Gaussian A)",
+           "recons_per_s": b["recons_per_s"],
+           "config": {"workload": b["workload"], "images": 256, "n": 128,
+                      "m": m, "mu": "cycling 2e2, 5e2, 1e3, 2e3", "iters_per_recon": ITERS_PER_RECON,
+                      "l2": "inputs larger than L2 (A and A^T bf16 hi/lo = 644 MB); no flush"}}
+    for k in ("roofline", "stage_us", "e2e", "gpu_launches", "clocks", "tau", "parity_vs_oracle"):
+        if k in b:
+            out[k] = b[k]
+    out["roofline"]["traffic"] = None
+    if not args.no_cpu_baseline:
+        P = synth.Problem("batch_img0", 128, m, 1, mus[0], 10.0, 0.0, args.steps, 0.0, None, A,
                           F[0])
-        cb = oracle_sample(P, tau, budget_s=20.0, want_u=True)
+        cb = oracle_sample(P, b["tau"], budget_s=20.0)
         out["cpu_baseline"] = {"value": cb["value"], "unit": "image-iter/s", "cores": cb["cores"],
                                "kind": "oracle",
                                "sample": "%d IADM iterations of image 0 (FP64 C oracle, OpenMP), "
                                          "%.1f s" % (cb["iters"], cb["seconds"])}
-        if cb["iters"] == min(args.steps, ITERS_PER_RECON) and args.steps <= ITERS_PER_RECON:
-            err = float(np.linalg.norm(U_gpu[0] - cb["u"].ravel()) / np.linalg.norm(cb["u"]))
-            out["parity_vs_oracle"] = {"rel_image_err": err, "image": 0, "iters": args.steps,
-                                       "ok": err <= 1e-4}
     print(json.dumps(out), flush=True)
 
 
@@ -761,7 +860,7 @@ def run_dct(args):
            "stage_us": {"dct_products": prod_us, "usolve_cluster": us_us},
            "e2e": {"value": r_e.iters / e2e_s, "unit": "iter/s",
                    "h2d_bytes_per_step": 4 * P.m / r_e.iters, "d2h_bytes_per_step": 4 * P.N / r_e.iters},
-           "gpu_launches": nrec * (2 * loop_launch_iters(res.iters) + 2),
+           "gpu_launches": nrec * (2 * loop_launch_iters(res.iters, P.max_iter) + 2),
            "relative_error_vs_phantom": float(np.linalg.norm(u_gpu - ub) / np.linalg.norm(ub)),
            "clocks": clocks}
     if not args.no_cpu_baseline:

@@ -79,6 +79,7 @@ def _load():
                 "oracle_kkt": ([ctypes.POINTER(_Params), vp, vp, vp, vp, vp,
                                 ctypes.POINTER(_Info)], None),
                 "oracle_num_threads": ([], i),
+                "oracle_set_num_threads": ([i], None),
                 "oracle_dct2": ([i, i, vp, vp], None),
                 "oracle_dct_Au": ([i, i, vp, vp, vp, vp], None),
                 "oracle_dct_At": ([i, i, vp, vp, vp], None),
@@ -108,6 +109,11 @@ def _f32(x):
 
 def num_threads() -> int:
     return int(_load().oracle_num_threads())
+
+
+def set_num_threads(k: int) -> None:
+    """Threads of the oracle's parallel loops from now on (results do not depend on it)."""
+    _load().oracle_set_num_threads(int(k))
 
 
 def D(u: np.ndarray):

@@ -28,6 +28,17 @@ int oracle_num_threads(void)
 #endif
 }
 
+/* Threads of the parallel loops from now on (k >= 1); used to time the oracle
+ * on one core beside all cores.  Results do not depend on it. */
+void oracle_set_num_threads(int k)
+{
+#ifdef _OPENMP
+    if (k >= 1) omp_set_num_threads(k);
+#else
+    (void)k;
+#endif
+}
+
 /* Sec. 1.4 and eq. (tv): D_i in R^{2 x n^2} stacks row i of D^(1) and D^(2). */
 void oracle_D(int n, const double* u, double* d1, double* d2)
 {

@@ -130,6 +130,7 @@ void oracle_kkt_dct(const oracle_params* p, const int32_t* rows, const float* f,
 
 /* Number of OpenMP threads the oracle uses. */
 int oracle_num_threads(void);
+void oracle_set_num_threads(int k);
 
 #ifdef __cplusplus
 }

@@ -419,11 +419,16 @@ tvcs_status apply_batch(tvcs_ctx* h, int count, const float* X, const float* Y, 
     const size_t N = h->N, m = h->m;
     BCK(cudaMemcpyAsync(b->U, X, sizeof(float) * count * N, cudaMemcpyDefault, s));
     if (Y) BCK(cudaMemcpyAsync(b->F, Y, sizeof(float) * count * m, cudaMemcpyDefault, s));
+    BCK(cudaMemsetAsync(&b->bctrl->error, 0, sizeof(int), s));   // bounded waits report here
     launch_split_rows(b->U, count, h->N, h->N, b->Uh, b->Ul, h->N, s);
     batch_products(h, count, Y != nullptr, s);
     BCK(cudaMemcpyAsync(R, b->R, sizeof(float) * count * m, cudaMemcpyDefault, s));
     BCK(cudaMemcpyAsync(G, b->G, sizeof(float) * count * N, cudaMemcpyDefault, s));
-    return sync_check(h, "batched products");
+    BCK(cudaMemcpyAsync(b->hbctrl, b->bctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    BCKS(sync_check(h, "batched products"));
+    if (b->hbctrl->error == ERR_TIMEOUT)
+        return set_last_error(TVCS_ERR_TIMEOUT, "a bounded device wait gave up");
+    return TVCS_OK;
 }
 
 tvcs_status solve_batch(tvcs_ctx* h, int count, const float* const* f, float* const* u,

@@ -75,9 +75,11 @@ struct tvcs_ctx {
     double* part = nullptr;
     tvcs::Ctrl* ctrl = nullptr;
     tvcs::Ctrl* hctrl = nullptr;  // pinned host mirror
-    // loop graph
+    // loop graph (a WHILE node over bodies of 16 iterations) and the graphs of
+    // 1..15 iterations that end a run whose length is not a multiple of 16
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    cudaGraphExec_t tail[16] = {};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool state_ready = false;
     tvcs_batch* batch = nullptr;

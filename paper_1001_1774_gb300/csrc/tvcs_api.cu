@@ -185,6 +185,16 @@ tvcs_status write_ctrl(tvcs_ctx* h)
     return TVCS_OK;
 }
 
+// The loop graphs capture launch arguments (beta, mu, test hooks): destroyed
+// whenever one of them changes, rebuilt on the next run.
+void drop_loop_graphs(tvcs_ctx* h)
+{
+    if (h->exec) { cudaGraphExecDestroy(h->exec); h->exec = nullptr; }
+    if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+    for (cudaGraphExec_t& t : h->tail)
+        if (t) { cudaGraphExecDestroy(t); t = nullptr; }
+}
+
 void free_ctx(tvcs_ctx* h)
 {
     if (!h) return;
@@ -192,8 +202,7 @@ void free_ctx(tvcs_ctx* h)
     if (h->stream) cudaStreamSynchronize(h->stream);
     free_batch(h);
     free_regen(h);
-    if (h->exec) cudaGraphExecDestroy(h->exec);
-    if (h->graph) cudaGraphDestroy(h->graph);
+    drop_loop_graphs(h);
     void* bufs[] = {h->A, h->f, h->u, h->w, h->lam, h->g, h->r, h->rhs, h->zeroN, h->tx, h->ty,
                     h->tr, h->tg, h->spec, h->tw, h->s2, h->gpart, h->gpart2, h->r2part, h->part,
                     h->ctrl, h->P0, h->P1, h->rscale, h->dctC, h->dsidx, h->dsperm, h->drowptr};
@@ -251,6 +260,27 @@ tvcs_status build_graph(tvcs_ctx* h)
     return TVCS_OK;
 }
 
+// A plain graph of `iters` (1..15) iterations: the end of a run whose length is
+// not a multiple of the loop body, so that a run launches exactly its iterations.
+tvcs_status build_tail(tvcs_ctx* h, int iters)
+{
+    if (h->tail[iters]) return TVCS_OK;
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < iters; ++k) launch_iteration(h, 0ull, 0, h->cap_stream, k > 0);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (e != cudaSuccess) return fail(TVCS_ERR_CUDA, "capture of the run's last iterations: %s",
+                                      cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&h->tail[iters], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->tail[iters] = nullptr;
+        return fail(TVCS_ERR_CUDA, "instantiating the run's last iterations: %s",
+                    cudaGetErrorString(e));
+    }
+    return TVCS_OK;
+}
+
 // (Re)computes r = A u - f and the partials of g = A^T r for the current u.
 void refresh_products(tvcs_ctx* h)
 {
@@ -293,7 +323,12 @@ tvcs_status init_state(tvcs_ctx* h, int init)
 // Runs up to `iters` iterations from the current state; tol > 0 enables eq. (stop).
 tvcs_status run_loop(tvcs_ctx* h, int iters, double tol, tvcs_result* res)
 {
-    if (!h->opt.host_loop) CKS(build_graph(h));
+    // whole loop bodies in the WHILE graph, the remainder in a graph of its own
+    const int nbody = iters / ITERS_PER_BODY, rest = iters % ITERS_PER_BODY;
+    if (!h->opt.host_loop) {
+        if (nbody > 0) CKS(build_graph(h));
+        if (rest > 0) CKS(build_tail(h, rest));
+    }
     CKS(read_ctrl(h));
     Ctrl& c = *h->hctrl;
     c.it = 0;
@@ -302,7 +337,7 @@ tvcs_status run_loop(tvcs_ctx* h, int iters, double tol, tvcs_result* res)
     c.skip = 0;
     c.stop_by_tol = 0;
     c.loops = 0;
-    c.loops_max = iters + 2;
+    c.loops_max = nbody;   // bodies of the WHILE graph (each ends by checking this bound)
     c.tol = tol;
     c.error = 0;
     c.algo = h->opt.algo;
@@ -315,7 +350,8 @@ tvcs_status run_loop(tvcs_ctx* h, int iters, double tol, tvcs_result* res)
             // profilers that cannot look inside graphs with conditional nodes).
             for (int k = 0; k < iters; ++k) launch_iteration(h, 0ull, 0, h->stream, false);
         } else {
-            CK(cudaGraphLaunch(h->exec, h->stream));
+            if (nbody > 0) CK(cudaGraphLaunch(h->exec, h->stream));
+            if (rest > 0) CK(cudaGraphLaunch(h->tail[rest], h->stream));
         }
     }
     CK(cudaEventRecord(h->ev1, h->stream));
@@ -742,10 +778,7 @@ tvcs_status tvcs_solve_continuation(tvcs_handle h, const float* f, float* u, con
         if (!(betas[k] > 0.0) || !isfinite(betas[k]))
             return fail(TVCS_ERR_INVALID_ARG, "betas[%d] must be > 0", k);
     const double beta0 = h->beta;
-    auto drop_graph = [&]() {   // beta is a launch argument captured in the loop graph
-        if (h->exec) { cudaGraphExecDestroy(h->exec); h->exec = nullptr; }
-        if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
-    };
+    auto drop_graph = [&]() { drop_loop_graphs(h); };   // beta is captured in the loop graphs
     CKS(copy_in(h, h->f, f, (size_t)h->m));
     tvcs_status worst = TVCS_OK;
     for (int k = 0; k < nbeta; ++k) {
@@ -823,14 +856,12 @@ tvcs_status tvcs_solve_batched(const tvcs_handle* hs, int count, const float* co
         if (mu && mu[i] != h->mu) {
             // mu is baked into the loop graph: rebuild it for this problem.
             h->mu = mu[i];
-            if (h->exec) { cudaGraphExecDestroy(h->exec); h->exec = nullptr; }
-            if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+            drop_loop_graphs(h);
         }
         tvcs_status st = tvcs_solve(h, f[i], u[i], res ? &res[i] : nullptr);
         if (h->mu != mu0) {
             h->mu = mu0;
-            if (h->exec) { cudaGraphExecDestroy(h->exec); h->exec = nullptr; }
-            if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+            drop_loop_graphs(h);
         }
         if (st < 0) return st;
         if (st > worst) worst = st;
@@ -963,9 +994,7 @@ tvcs_status tvcs_test_hold_grid_barrier(tvcs_handle h, int extra)
         return fail(TVCS_ERR_UNSUPPORTED, "the hook acts on the binary32 product kernel (n <= 128)");
     if (h->bar_extra != extra) {
         h->bar_extra = extra;
-        // the loop graph captured the old value
-        if (h->exec) { cudaGraphExecDestroy(h->exec); h->exec = nullptr; }
-        if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+        drop_loop_graphs(h);   // the loop graphs captured the old value
     }
     return TVCS_OK;
 }
@@ -976,11 +1005,16 @@ tvcs_status tvcs_apply(tvcs_handle h, const float* x, const float* y, float* r, 
     if (!x || !r || !g) return fail(TVCS_ERR_INVALID_ARG, "x, r and g must be non-NULL");
     CKS(copy_in(h, h->tx, x, (size_t)h->N));
     if (y) CKS(copy_in(h, h->ty, y, (size_t)h->m));
+    // the kernels record a bounded wait that gave up in the control block's error word
+    CK(cudaMemsetAsync(&h->ctrl->error, 0, sizeof(int), h->stream));
     products(h, h->tx, y ? h->ty : nullptr, h->tr, h->gpart2, h->tg, MODE_PLAIN, 0ull, 0,
              h->stream);
     CKS(copy_out(h, r, h->tr, (size_t)h->m));
     CKS(copy_out(h, g, h->tg, (size_t)h->N));
-    return sync_and_check(h, "tvcs_apply");
+    CKS(read_ctrl(h));
+    if (h->hctrl->error == ERR_TIMEOUT)
+        return fail(TVCS_ERR_TIMEOUT, "a bounded device wait gave up");
+    return TVCS_OK;
 }
 
 }  // extern "C"

@@ -82,5 +82,9 @@ def test_reference_arm_prints_one_contract_line():
 def test_launch_counts_include_the_skipped_tail_of_a_loop_body():
     import bench
     # single image: 16 iterations per loop body; shared-A batch: 4
-    assert [bench.loop_launch_iters(k) for k in (1, 16, 17, 300, 30000)] == [16, 16, 32, 304, 30000]
+    # fixed-count runs launch exactly their iterations; a run stopped by tol at k of
+    # max_iter = 5000 (312 bodies + 8) launches the rest of its body and the last 8
+    assert [bench.loop_launch_iters(k) for k in (1, 16, 17, 300, 30000)] == [1, 16, 17, 300, 30000]
+    assert [bench.loop_launch_iters(k, 5000) for k in (1, 16, 17, 2403, 4995, 5000)] == \
+        [24, 24, 40, 2424, 5000, 5000]
     assert [bench.batch_launch_iters(k) for k in (1, 4, 7, 300)] == [4, 4, 8, 300]
