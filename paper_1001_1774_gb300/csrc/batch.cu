@@ -356,6 +356,27 @@ tvcs_status build_batch_graph(tvcs_ctx* h, int count)
     return TVCS_OK;
 }
 
+// True when p[i] = p[0] + i * len for every i and the whole range lies in one
+// allocation (pageable host memory, or one device / pinned allocation), so that
+// one copy can move all images.
+template <typename T>
+bool contiguous(T* const* p, int count, size_t len)
+{
+    for (int i = 1; i < count; ++i)
+        if (p[i] != p[0] + (size_t)i * len) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p[0]) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeUnregistered) return true;
+    CUdeviceptr base = 0;
+    size_t size = 0;
+    const CUdeviceptr a = (CUdeviceptr)(uintptr_t)p[0];
+    if (cuMemGetAddressRange(&base, &size, a) != CUDA_SUCCESS) return false;
+    return a + (CUdeviceptr)(sizeof(T) * len * (size_t)count) <= base + size;
+}
+
 tvcs_status sync_check(tvcs_ctx* h, const char* what)
 {
     cudaError_t e = cudaStreamSynchronize(h->stream);
@@ -438,8 +459,12 @@ tvcs_status solve_batch(tvcs_ctx* h, int count, const float* const* f, float* co
     tvcs_batch* b = h->batch;
     cudaStream_t s = h->stream;
     const size_t N = h->N, m = h->m;
-    for (int i = 0; i < count; ++i)
-        BCK(cudaMemcpyAsync(b->F + i * m, f[i], sizeof(float) * m, cudaMemcpyDefault, s));
+    if (contiguous(f, count, m)) {   // one copy when the caller's arrays are back to back
+        BCK(cudaMemcpyAsync(b->F, f[0], sizeof(float) * m * count, cudaMemcpyDefault, s));
+    } else {
+        for (int i = 0; i < count; ++i)
+            BCK(cudaMemcpyAsync(b->F + i * m, f[i], sizeof(float) * m, cudaMemcpyDefault, s));
+    }
     std::vector<float> mus(count);
     for (int i = 0; i < count; ++i) mus[i] = (float)(mu ? mu[i] : h->mu);
     BCK(cudaMemcpyAsync(b->mu, mus.data(), sizeof(float) * count, cudaMemcpyHostToDevice, s));
@@ -484,8 +509,12 @@ tvcs_status solve_batch(tvcs_ctx* h, int count, const float* const* f, float* co
     TvArgs a = batch_tv_args(h, count, MODE_PLAIN);
     launch_tv(h->n, a, 4, s);
     launch_tv(h->n, a, 5, s);
-    for (int i = 0; i < count; ++i)
-        BCK(cudaMemcpyAsync(u[i], b->U + i * N, sizeof(float) * N, cudaMemcpyDefault, s));
+    if (contiguous(u, count, N)) {
+        BCK(cudaMemcpyAsync(u[0], b->U, sizeof(float) * N * count, cudaMemcpyDefault, s));
+    } else {
+        for (int i = 0; i < count; ++i)
+            BCK(cudaMemcpyAsync(u[i], b->U + i * N, sizeof(float) * N, cudaMemcpyDefault, s));
+    }
     BCK(cudaMemcpyAsync(b->hctrls, b->ctrls, sizeof(Ctrl) * count, cudaMemcpyDeviceToHost, s));
     BCK(cudaMemcpyAsync(b->hbctrl, b->bctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     BCKS(sync_check(h, "batched solve"));

@@ -526,6 +526,28 @@ __global__ void k_fill(float* __restrict__ v, int N, float value)
     if (i < N) v[i] = value;
 }
 
+// Start of a run: the loop bookkeeping of the control block, set on the device
+// (no host round trip before the loop); the other fields keep their values.
+__global__ void k_run_begin(Ctrl* __restrict__ c, int max_iter, int loops_max, double tol, int algo)
+{
+    c->it = 0;
+    c->max_iter = max_iter;
+    c->done = 0;
+    c->skip = 0;
+    c->stop_by_tol = 0;
+    c->loops = 0;
+    c->loops_max = loops_max;
+    c->tol = tol;
+    c->error = 0;
+    c->algo = algo;
+    c->ticket_fft = c->ticket_prod = c->ticket_fin = c->ticket_w = c->ticket_gather = 0u;
+}
+
+void launch_run_begin(Ctrl* c, int max_iter, int loops_max, double tol, int algo, cudaStream_t s)
+{
+    k_run_begin<<<1, 1, 0, s>>>(c, max_iter, loops_max, tol, algo);
+}
+
 void launch_gather(const float* gpart, int P, int N, float scale, float* out, double* part,
                    Ctrl* ctrl, cudaStream_t s)
 {

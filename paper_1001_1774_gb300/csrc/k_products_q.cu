@@ -55,8 +55,8 @@ struct QShape {
     static constexpr int N = NS * CS;
     static constexpr int THREADS = CONS + 32;
     static constexpr size_t STAGE_BYTES = (size_t)NS * QPrec<PREC>::PLANE_BYTES_NUM;
-    static constexpr size_t O_BAR = NST * STAGE_BYTES;               // full[NST], empty[NST], xbar[4]
-    static constexpr size_t O_RED = O_BAR + (2 * NST + 4) * 8;       // [2][CONS/32] floats
+    static constexpr size_t O_BAR = NST * STAGE_BYTES;   // full[NST], empty[NST], xbar[4], partbar[2]
+    static constexpr size_t O_RED = O_BAR + (2 * NST + 6) * 8;       // [2][CONS/32] floats
     static constexpr size_t O_XRED = O_RED + 2 * (CONS / 32) * 4;    // [4][CS] floats
     static constexpr size_t O_DRED = ((O_XRED + 4 * CS * 4 + 15) / 16) * 16;   // [32] float2
     static constexpr size_t O_Y = O_DRED + 32 * 8;                   // y of the rows
@@ -114,29 +114,6 @@ __device__ __forceinline__ void cluster_sync_all()
 __device__ __forceinline__ float bf16_lo_f(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi_f(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
 
-// Decodes column chunk `ch` (4 consecutive columns) of the row slice at `sb`.
-template <int PREC, int NS>
-__device__ __forceinline__ float4 decode_chunk(const unsigned char* sb, int ch, float scale)
-{
-    if constexpr (PREC == 0) {
-        return reinterpret_cast<const float4*>(sb)[ch];
-    } else if constexpr (PREC == 1) {
-        const uint2 h = reinterpret_cast<const uint2*>(sb)[ch];
-        const uint2 l = reinterpret_cast<const uint2*>(sb + (size_t)NS * 2)[ch];
-        return make_float4(bf16_lo_f(h.x) + bf16_lo_f(l.x), bf16_hi_f(h.x) + bf16_hi_f(l.x),
-                           bf16_lo_f(h.y) + bf16_lo_f(l.y), bf16_hi_f(h.y) + bf16_hi_f(l.y));
-    } else {
-        const uint32_t q = reinterpret_cast<const uint32_t*>(sb)[ch];
-        const uint2 c = reinterpret_cast<const uint2*>(sb + (size_t)NS)[ch];
-        __nv_fp8x2_storage_t q01 = (__nv_fp8x2_storage_t)(q & 0xffffu);
-        __nv_fp8x2_storage_t q23 = (__nv_fp8x2_storage_t)(q >> 16);
-        const float2 a01 = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(q01, __NV_E4M3)));
-        const float2 a23 = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(q23, __NV_E4M3)));
-        return make_float4(fmaf(scale, a01.x, bf16_lo_f(c.x)), fmaf(scale, a01.y, bf16_hi_f(c.x)),
-                           fmaf(scale, a23.x, bf16_lo_f(c.y)), fmaf(scale, a23.y, bf16_hi_f(c.y)));
-    }
-}
-
 template <int PREC, int V, int CS, int CONS, int NST>
 __global__ void __launch_bounds__(CONS + 32, 1)
     k_products_q(const unsigned char* __restrict__ P0, const unsigned char* __restrict__ P1,
@@ -151,6 +128,7 @@ __global__ void __launch_bounds__(CONS + 32, 1)
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::O_BAR);
     uint64_t* empty = full + NST;
     uint64_t* xbar = empty + NST;                                   // [4]
+    uint64_t* partbar = xbar + 4;                                   // [2]
     float* red = reinterpret_cast<float*>(smem + S::O_RED);         // [2][WARPS]
     float* xred = reinterpret_cast<float*>(smem + S::O_XRED);       // [4][CS]
     float2* dred = reinterpret_cast<float2*>(smem + S::O_DRED);
@@ -185,6 +163,7 @@ __global__ void __launch_bounds__(CONS + 32, 1)
             mbar_init(&empty[s], WARPS);
         }
         for (int b = 0; b < 4; ++b) mbar_init(&xbar[b], CS);
+        for (int b = 0; b < 2; ++b) mbar_init(&partbar[b], WARPS);
         fence_mbar_init();
     }
     __syncthreads();
@@ -232,6 +211,7 @@ __global__ void __launch_bounds__(CONS + 32, 1)
     }
 
     // ---------------- consumers ----------------
+    const int lane = tid & 31, warp = tid >> 5;
     const bool y_in_smem = (y != nullptr) && nrows <= QPROD_YMAX;
     const bool s_in_smem = (PREC == 2) && nrows <= QPROD_YMAX;
     if (y_in_smem)
@@ -246,75 +226,126 @@ __global__ void __launch_bounds__(CONS + 32, 1)
         acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     named_barrier(1, CONS);
-    uint32_t xred_remote[CS];
-    uint32_t xbar_remote[CS];
-#pragma unroll
-    for (int k = 0; k < CS; ++k) {
-        xred_remote[k] = CS > 1 ? map_remote(smem_u32(xred), (uint32_t)k) : 0u;
-        xbar_remote[k] = CS > 1 ? map_remote(smem_u32(xbar), (uint32_t)k) : 0u;
+    uint32_t xred_remote = 0u, xbar_remote = 0u;   // peer `tid` (tid < CS) of the cluster
+    if (CS > 1 && tid < CS) {
+        xred_remote = map_remote(smem_u32(xred), (uint32_t)tid);
+        xbar_remote = map_remote(smem_u32(xbar), (uint32_t)tid);
     }
     float2 r2 = make_float2(0.f, 0.f);   // double-single ||r||^2 (block 0, thread 0)
     bool ok = true;
-    // This block's part of the dot product of row s (waits for the row's stage).
-    auto part_of_row = [&](int s) -> float {
+    auto row_scale = [&](int s) -> float {
+        if constexpr (PREC == 2) return s_in_smem ? ss[s] : rscale[i0 + s];
+        return 1.0f;
+    };
+    // Row s, first use: this warp's part of the block's dot product over its column
+    // slice; lane 0 stores it in red[s & 1] and arrives on partbar[s & 1].  No
+    // block-wide barrier: only the threads that send the block's part wait for
+    // all warps (the warps otherwise run apart by up to the exchange's bound).
+    auto warp_part = [&](int s) {
         const int slot = s % NST;
         if (ok && !mbar_wait(&full[slot], (s / NST) & 1, budget)) {
             set_error(ctrl, ERR_TIMEOUT);
             ok = false;
         }
         const unsigned char* sb = smem + (size_t)slot * S::STAGE_BYTES;
-        float scale = 1.0f;
-        if constexpr (PREC == 2) scale = s_in_smem ? ss[s] : rscale[i0 + s];
-        float d = 0.f;
+        float d0 = 0.f, d1 = 0.f;
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            const float4 a = decode_chunk<PREC, NS>(sb, tid + v * CONS, scale);
-            d = fmaf(a.x, xu[v].x, d);
-            d = fmaf(a.y, xu[v].y, d);
-            d = fmaf(a.z, xu[v].z, d);
-            d = fmaf(a.w, xu[v].w, d);
+            const int ch = tid + v * CONS;
+            if constexpr (PREC == 0) {
+                const float4 a = reinterpret_cast<const float4*>(sb)[ch];
+                d0 = fmaf(a.x, xu[v].x, d0);
+                d1 = fmaf(a.y, xu[v].y, d1);
+                d0 = fmaf(a.z, xu[v].z, d0);
+                d1 = fmaf(a.w, xu[v].w, d1);
+            } else if constexpr (PREC == 1) {   // hi + lo, each product exact-free of a join
+                const uint2 h = reinterpret_cast<const uint2*>(sb)[ch];
+                const uint2 l = reinterpret_cast<const uint2*>(sb + (size_t)NS * 2)[ch];
+                d0 = fmaf(bf16_lo_f(h.x), xu[v].x, d0);
+                d1 = fmaf(bf16_lo_f(l.x), xu[v].x, d1);
+                d0 = fmaf(bf16_hi_f(h.x), xu[v].y, d0);
+                d1 = fmaf(bf16_hi_f(l.x), xu[v].y, d1);
+                d0 = fmaf(bf16_lo_f(h.y), xu[v].z, d0);
+                d1 = fmaf(bf16_lo_f(l.y), xu[v].z, d1);
+                d0 = fmaf(bf16_hi_f(h.y), xu[v].w, d0);
+                d1 = fmaf(bf16_hi_f(l.y), xu[v].w, d1);
+            } else {   // s q + c: the e4m3 part (d0, scaled once per row) and the correction (d1)
+                const uint32_t q = reinterpret_cast<const uint32_t*>(sb)[ch];
+                const uint2 c = reinterpret_cast<const uint2*>(sb + (size_t)NS)[ch];
+                const float2 a01 = __half22float2(__half2(
+                    __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(q & 0xffffu), __NV_E4M3)));
+                const float2 a23 = __half22float2(__half2(
+                    __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(q >> 16), __NV_E4M3)));
+                d0 = fmaf(a01.x, xu[v].x, d0);
+                d1 = fmaf(bf16_lo_f(c.x), xu[v].x, d1);
+                d0 = fmaf(a01.y, xu[v].y, d0);
+                d1 = fmaf(bf16_hi_f(c.x), xu[v].y, d1);
+                d0 = fmaf(a23.x, xu[v].z, d0);
+                d1 = fmaf(bf16_lo_f(c.y), xu[v].z, d1);
+                d0 = fmaf(a23.y, xu[v].w, d0);
+                d1 = fmaf(bf16_hi_f(c.y), xu[v].w, d1);
+            }
         }
+        float d;
+        if constexpr (PREC == 2)
+            d = fmaf(row_scale(s), d0, d1);
+        else
+            d = d0 + d1;
         d = warp_sum(d);
-        float* rb = red + (s & 1) * WARPS;
-        if ((tid & 31) == 0) rb[tid >> 5] = d;
-        named_barrier(1, CONS);
-        float part = 0.f;
-#pragma unroll
-        for (int w = 0; w < WARPS; ++w) part += rb[w];
-        return part;
+        if (lane == 0) {
+            red[(s & 1) * WARPS + warp] = d;
+            mbar_arrive(&partbar[s & 1]);
+        }
     };
-    // Sends the part of row s to every block of the cluster (slot s mod 4).
-    auto send_part = [&](int s, float part) {
-        if constexpr (CS > 1) {
+    // The block's part of row s, summed in warp order by the sending threads
+    // (tid < CS: thread k sends to block k of the cluster; slot s mod 4).
+    auto send_part = [&](int s) {
+        if (tid < CS) {
+            if (ok && !mbar_wait(&partbar[s & 1], (uint32_t)((s >> 1) & 1), budget)) {
+                set_error(ctrl, ERR_TIMEOUT);
+                ok = false;
+            }
+            const float* rb = red + (s & 1) * WARPS;
+            float part = 0.f;
+#pragma unroll
+            for (int w = 0; w < WARPS; ++w) part += rb[w];
             const int b = s & 3;
-            if (tid < CS) {
-                st_remote_f32(xred_remote[tid] + (uint32_t)((b * CS + rank) * 4), part);
-                mbar_arrive_remote(xbar_remote[tid] + (uint32_t)(b * 8));
+            if constexpr (CS > 1) {
+                st_remote_f32(xred_remote + (uint32_t)((b * CS + rank) * 4), part);
+                mbar_arrive_remote(xbar_remote + (uint32_t)(b * 8));
+            } else {
+                xred[b] = part;
+                mbar_arrive(&xbar[b]);
             }
         }
     };
     // Software pipeline: the part of row s+1 is computed and sent before the
-    // cluster's parts of row s are awaited, hiding the exchange latency.  A
-    // peer writes slot s mod 4 for row s+4 only after receiving this block's
-    // part of row s+2, which is sent after this block has read row s: four
-    // slots make the reuse safe.
-    float part_next = nrows > 0 ? part_of_row(0) : 0.f;
-    if (nrows > 0) send_part(0, part_next);
+    // cluster's parts of row s are awaited, hiding the exchange latency.  Slot
+    // reuse: a peer writes slot s mod 4 for row s+4 only after it has received
+    // this block's part of row s+2, which this block sends only once all of its
+    // warps have passed row s; the red[] and partbar[] pairs are reused two rows
+    // later under the same argument.
+    if (nrows > 0) {
+        warp_part(0);
+        send_part(0);
+    }
     for (int s = 0; s < nrows; ++s) {
-        const float part_s = part_next;
         if (s + 1 < nrows) {
-            part_next = part_of_row(s + 1);
-            send_part(s + 1, part_next);
+            warp_part(s + 1);
+            send_part(s + 1);
         }
-        float dot;
-        if constexpr (CS == 1) {
-            dot = part_s;
-        } else {
-            const int b = s & 3;
-            const uint32_t phase = (uint32_t)((s >> 2) & 1);
-            if (ok && !mbar_try_wait_cluster(&xbar[b], phase)) {
+        const int b = s & 3;
+        const uint32_t phase = (uint32_t)((s >> 2) & 1);
+        if (ok) {
+            bool got;
+            if constexpr (CS > 1) got = mbar_try_wait_cluster(&xbar[b], phase);
+            else got = mbar_try_wait(&xbar[b], phase);
+            if (!got) {
                 const long long t0 = clock64();
-                while (!mbar_try_wait_cluster(&xbar[b], phase)) {
+                for (;;) {
+                    if constexpr (CS > 1) got = mbar_try_wait_cluster(&xbar[b], phase);
+                    else got = mbar_try_wait(&xbar[b], phase);
+                    if (got) break;
                     if (clock64() - t0 > budget) {
                         set_error(ctrl, ERR_TIMEOUT);
                         ok = false;
@@ -322,10 +353,10 @@ __global__ void __launch_bounds__(CONS + 32, 1)
                     }
                 }
             }
-            dot = 0.f;
-#pragma unroll
-            for (int k = 0; k < CS; ++k) dot += xred[b * CS + k];
         }
+        float dot = 0.f;
+#pragma unroll
+        for (int k = 0; k < CS; ++k) dot += xred[b * CS + k];
         float yi = 0.f;
         if (y != nullptr) yi = y_in_smem ? sy[s] : y[i0 + s];
         const float ri = dot - yi;
@@ -335,19 +366,41 @@ __global__ void __launch_bounds__(CONS + 32, 1)
         }
         const int slot = s % NST;
         const unsigned char* sb = smem + (size_t)slot * S::STAGE_BYTES;
-        float scale = 1.0f;
-        if constexpr (PREC == 2) scale = s_in_smem ? ss[s] : rscale[i0 + s];
+        // Second use of row s: acc += r_i A_i over this block's columns.
+        float rs = ri;
+        if constexpr (PREC == 2) rs = ri * row_scale(s);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            const float4 a = decode_chunk<PREC, NS>(sb, tid + v * CONS, scale);
-            acc[v].x = fmaf(ri, a.x, acc[v].x);
-            acc[v].y = fmaf(ri, a.y, acc[v].y);
-            acc[v].z = fmaf(ri, a.z, acc[v].z);
-            acc[v].w = fmaf(ri, a.w, acc[v].w);
+            const int ch = tid + v * CONS;
+            if constexpr (PREC == 0) {
+                const float4 a = reinterpret_cast<const float4*>(sb)[ch];
+                acc[v].x = fmaf(ri, a.x, acc[v].x);
+                acc[v].y = fmaf(ri, a.y, acc[v].y);
+                acc[v].z = fmaf(ri, a.z, acc[v].z);
+                acc[v].w = fmaf(ri, a.w, acc[v].w);
+            } else if constexpr (PREC == 1) {
+                const uint2 h = reinterpret_cast<const uint2*>(sb)[ch];
+                const uint2 l = reinterpret_cast<const uint2*>(sb + (size_t)NS * 2)[ch];
+                acc[v].x = fmaf(ri, bf16_lo_f(h.x) + bf16_lo_f(l.x), acc[v].x);
+                acc[v].y = fmaf(ri, bf16_hi_f(h.x) + bf16_hi_f(l.x), acc[v].y);
+                acc[v].z = fmaf(ri, bf16_lo_f(h.y) + bf16_lo_f(l.y), acc[v].z);
+                acc[v].w = fmaf(ri, bf16_hi_f(h.y) + bf16_hi_f(l.y), acc[v].w);
+            } else {   // (r_i s_i) q + r_i c
+                const uint32_t q = reinterpret_cast<const uint32_t*>(sb)[ch];
+                const uint2 c = reinterpret_cast<const uint2*>(sb + (size_t)NS)[ch];
+                const float2 a01 = __half22float2(__half2(
+                    __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(q & 0xffffu), __NV_E4M3)));
+                const float2 a23 = __half22float2(__half2(
+                    __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(q >> 16), __NV_E4M3)));
+                acc[v].x = fmaf(ri, bf16_lo_f(c.x), fmaf(rs, a01.x, acc[v].x));
+                acc[v].y = fmaf(ri, bf16_hi_f(c.x), fmaf(rs, a01.y, acc[v].y));
+                acc[v].z = fmaf(ri, bf16_lo_f(c.y), fmaf(rs, a23.x, acc[v].z));
+                acc[v].w = fmaf(ri, bf16_hi_f(c.y), fmaf(rs, a23.y, acc[v].w));
+            }
         }
         // this warp is done with row s: release its slot to the producer
         __syncwarp();
-        if ((tid & 31) == 0) mbar_arrive(&empty[slot]);
+        if (lane == 0) mbar_arrive(&empty[slot]);
     }
 
     // ---------------- epilogue ----------------

@@ -218,6 +218,9 @@ void launch_gather(const float* gpart, int P, int N, float scale, float* out, do
 // v = z / sqrt(ctrl->vec2)
 void launch_normalize(const float* z, float* v, int N, const Ctrl* ctrl, cudaStream_t s);
 void launch_fill(float* v, int N, float value, cudaStream_t s);
+// it, max_iter, done, skip, stop_by_tol, loops, loops_max, tol, error, algo and the
+// tickets of a control block for a new run
+void launch_run_begin(Ctrl* c, int max_iter, int loops_max, double tol, int algo, cudaStream_t s);
 
 // Gaussian encoding matrix rows from the counter-based generator.
 void launch_gen_gauss(float* A, int m, int64_t N, uint64_t seed, float scale, cudaStream_t s);

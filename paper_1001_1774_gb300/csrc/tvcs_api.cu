@@ -329,20 +329,9 @@ tvcs_status run_loop(tvcs_ctx* h, int iters, double tol, tvcs_result* res)
         if (nbody > 0) CKS(build_graph(h));
         if (rest > 0) CKS(build_tail(h, rest));
     }
-    CKS(read_ctrl(h));
     Ctrl& c = *h->hctrl;
-    c.it = 0;
-    c.max_iter = iters;
-    c.done = 0;
-    c.skip = 0;
-    c.stop_by_tol = 0;
-    c.loops = 0;
-    c.loops_max = nbody;   // bodies of the WHILE graph (each ends by checking this bound)
-    c.tol = tol;
-    c.error = 0;
-    c.algo = h->opt.algo;
-    c.ticket_fft = c.ticket_prod = c.ticket_fin = c.ticket_w = c.ticket_gather = 0;
-    CKS(write_ctrl(h));
+    // loops_max: bodies of the WHILE graph (each ends by checking this bound)
+    launch_run_begin(h->ctrl, iters, nbody, tol, h->opt.algo, h->stream);
     CK(cudaEventRecord(h->ev0, h->stream));
     if (iters > 0) {
         if (h->opt.host_loop) {
