@@ -53,7 +53,7 @@ template <int PREC, int V, int CS, int CONS, int NST>
 struct QShape {
     static constexpr int NS = 4 * CONS * V;        // columns per block (the slice)
     static constexpr int N = NS * CS;
-    static constexpr int THREADS = CONS + 32;
+    static constexpr int THREADS = CONS + 64;   // consumers, the producer warp, the exchange warp
     static constexpr size_t STAGE_BYTES = (size_t)NS * QPrec<PREC>::PLANE_BYTES_NUM;
     static constexpr size_t O_BAR = NST * STAGE_BYTES;   // full[NST], empty[NST], xbar[4], partbar[2]
     static constexpr size_t O_RED = O_BAR + (2 * NST + 6) * 8;       // [2][CONS/32] floats
@@ -115,7 +115,7 @@ __device__ __forceinline__ float bf16_lo_f(uint32_t w) { return __uint_as_float(
 __device__ __forceinline__ float bf16_hi_f(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
 
 template <int PREC, int V, int CS, int CONS, int NST>
-__global__ void __launch_bounds__(CONS + 32, 1)
+__global__ void __launch_bounds__(CONS + 64, 1)
     k_products_q(const unsigned char* __restrict__ P0, const unsigned char* __restrict__ P1,
                  const float* __restrict__ rscale, int m, const float* __restrict__ x,
                  const float* __restrict__ y, float* __restrict__ r, float* __restrict__ gpart,
@@ -169,6 +169,40 @@ __global__ void __launch_bounds__(CONS + 32, 1)
     __syncthreads();
     if constexpr (CS > 1) cluster_sync_all();   // peers' barriers exist before any remote arrival
 
+    if (tid >= CONS + 32) {
+        // ---------------- exchange warp: the block's part of every row to the cluster ----
+        // The warps' parts of row s (red[s & 1], complete when partbar[s & 1] completes)
+        // are read by lanes 0 .. WARPS-1 and added by a fixed shuffle tree; lane k < CS
+        // then stores the sum into block k's slot s mod 4 and arrives on its barrier.  All
+        // reads of red[] for row s precede every send of row s, so the consumers, which
+        // reuse red[s & 1] for row s+2 only after this block's own part of row s reached
+        // them, never overwrite a part that is still to be read.
+        const int lane = tid & 31;
+        const uint32_t xr = CS > 1 ? map_remote(smem_u32(xred), (uint32_t)(lane % CS)) : 0u;
+        const uint32_t xb = CS > 1 ? map_remote(smem_u32(xbar), (uint32_t)(lane % CS)) : 0u;
+        bool eok = true;
+        for (int s = 0; s < nrows; ++s) {
+            if (eok && !mbar_wait(&partbar[s & 1], (uint32_t)((s >> 1) & 1), budget)) {
+                set_error(ctrl, ERR_TIMEOUT);
+                eok = false;
+            }
+            float part = lane < WARPS ? red[(s & 1) * WARPS + lane] : 0.f;
+            part = warp_sum(part);
+            const int b = s & 3;
+            if (lane < CS) {
+                if constexpr (CS > 1) {
+                    st_remote_f32(xr + (uint32_t)((b * CS + rank) * 4), part);
+                    mbar_arrive_remote(xb + (uint32_t)(b * 8));
+                } else {
+                    xred[b] = part;
+                    mbar_arrive(&xbar[b]);
+                }
+            }
+            __syncwarp();
+        }
+        if constexpr (CS > 1) cluster_sync_all();
+        return;
+    }
     if (tid >= CONS) {
         // ---------------- producer warp: row slices into the ring ----------------
         if (tid == CONS) {
@@ -226,11 +260,6 @@ __global__ void __launch_bounds__(CONS + 32, 1)
         acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     named_barrier(1, CONS);
-    uint32_t xred_remote = 0u, xbar_remote = 0u;   // peer `tid` (tid < CS) of the cluster
-    if (CS > 1 && tid < CS) {
-        xred_remote = map_remote(smem_u32(xred), (uint32_t)tid);
-        xbar_remote = map_remote(smem_u32(xbar), (uint32_t)tid);
-    }
     float2 r2 = make_float2(0.f, 0.f);   // double-single ||r||^2 (block 0, thread 0)
     bool ok = true;
     auto row_scale = [&](int s) -> float {
@@ -239,8 +268,8 @@ __global__ void __launch_bounds__(CONS + 32, 1)
     };
     // Row s, first use: this warp's part of the block's dot product over its column
     // slice; lane 0 stores it in red[s & 1] and arrives on partbar[s & 1].  No
-    // block-wide barrier: only the threads that send the block's part wait for
-    // all warps (the warps otherwise run apart by up to the exchange's bound).
+    // block-wide barrier: only the exchange warp waits for all warps (the consumer
+    // warps otherwise run apart by up to the exchange's bound).
     auto warp_part = [&](int s) {
         const int slot = s % NST;
         if (ok && !mbar_wait(&full[slot], (s / NST) & 1, budget)) {
@@ -297,43 +326,15 @@ __global__ void __launch_bounds__(CONS + 32, 1)
             mbar_arrive(&partbar[s & 1]);
         }
     };
-    // The block's part of row s, summed in warp order by the sending threads
-    // (tid < CS: thread k sends to block k of the cluster; slot s mod 4).
-    auto send_part = [&](int s) {
-        if (tid < CS) {
-            if (ok && !mbar_wait(&partbar[s & 1], (uint32_t)((s >> 1) & 1), budget)) {
-                set_error(ctrl, ERR_TIMEOUT);
-                ok = false;
-            }
-            const float* rb = red + (s & 1) * WARPS;
-            float part = 0.f;
-#pragma unroll
-            for (int w = 0; w < WARPS; ++w) part += rb[w];
-            const int b = s & 3;
-            if constexpr (CS > 1) {
-                st_remote_f32(xred_remote + (uint32_t)((b * CS + rank) * 4), part);
-                mbar_arrive_remote(xbar_remote + (uint32_t)(b * 8));
-            } else {
-                xred[b] = part;
-                mbar_arrive(&xbar[b]);
-            }
-        }
-    };
-    // Software pipeline: the part of row s+1 is computed and sent before the
-    // cluster's parts of row s are awaited, hiding the exchange latency.  Slot
-    // reuse: a peer writes slot s mod 4 for row s+4 only after it has received
-    // this block's part of row s+2, which this block sends only once all of its
-    // warps have passed row s; the red[] and partbar[] pairs are reused two rows
-    // later under the same argument.
-    if (nrows > 0) {
-        warp_part(0);
-        send_part(0);
-    }
+    // Software pipeline: the part of row s+1 is computed (and sent by the exchange
+    // warp) before the cluster's parts of row s are awaited, hiding the exchange
+    // latency.  Slot reuse: a peer writes slot s mod 4 for row s+4 only after it
+    // has received this block's part of row s+2, which is sent only once all of
+    // this block's warps have passed row s; the red[] and partbar[] pairs are
+    // reused two rows later under the same argument.
+    if (nrows > 0) warp_part(0);
     for (int s = 0; s < nrows; ++s) {
-        if (s + 1 < nrows) {
-            warp_part(s + 1);
-            send_part(s + 1);
-        }
+        if (s + 1 < nrows) warp_part(s + 1);
         const int b = s & 3;
         const uint32_t phase = (uint32_t)((s >> 2) & 1);
         if (ok) {
