@@ -22,17 +22,6 @@
 
 namespace tvcs {
 
-// ctrls[b].r2 = sum over tiles of the fix-up's partials of ||r_b||^2.
-__global__ void k_batch_r2(const float2* __restrict__ r2part, int tiles, Ctrl* __restrict__ ctrls)
-{
-    __shared__ float2 red[32];
-    float2 s = make_float2(0.f, 0.f);
-    for (int i = threadIdx.x; i < tiles; i += blockDim.x)
-        s = ds_add(s, r2part[(size_t)blockIdx.x * tiles + i]);
-    s = block_sum_ds(s, red);
-    if (threadIdx.x == 0) ctrls[blockIdx.x].r2 = ds_value(s);
-}
-
 // Continue while any image runs and the loop bound holds.  With slot tables
 // (count <= blockDim.x = 256): the running images, in image order, take slots
 // 0 .. nact-1 for the next iteration (a block-wide exclusive prefix sum of the
@@ -80,6 +69,118 @@ void launch_batch_cond(const Ctrl* ctrls, int count, Ctrl* bctrl, unsigned long 
 {
     k_batch_cond<<<1, 256, 0, s>>>(ctrls, count, bctrl, (cudaGraphConditionalHandle)cond, set_cond,
                                    slot_img, img_slot);
+}
+
+// End-of-run residual of every image, r_b = A_eff u_b - f_b with A_eff = hi + lo
+// (the stored matrix, exact in binary32), on the CUDA cores in binary32 with a
+// three-level sum: 32 products from zero, 16 such chunks, then the running total
+// (the tensor-core products keep 16 bits of u and add in one long binary32 chain,
+// which is accurate for the iteration but not for ||r||^2 of a converged image).
+// Block: 64 rows x 64 images, 256 threads of 4 x 4 outputs; K in chunks of 32.
+constexpr int RS_BM = 64, RS_BB = 64, RS_BK = 32;
+
+__global__ void __launch_bounds__(256)
+    k_batch_resid(const unsigned short* __restrict__ hi, const unsigned short* __restrict__ lo,
+                  int m, int N, const float* __restrict__ U, const float* __restrict__ F,
+                  int count, float* __restrict__ R)
+{
+    __shared__ float As[RS_BK][RS_BM + 4];
+    __shared__ float Us[RS_BK][RS_BB + 4];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;              // images tx*4.., rows ty*4..
+    const int i0 = blockIdx.x * RS_BM, b0 = blockIdx.y * RS_BB;
+    float c[4][4], l1[4][4], l2[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) l1[a][b] = l2[a][b] = 0.f;
+    const int lr = tid >> 2, lg = (tid & 3) * 8;         // loader: row / image lr, columns lg..lg+7
+    int chunk = 0;
+    for (int k0 = 0; k0 < N; k0 += RS_BK, ++chunk) {
+        {   // A_eff tile (transposed) and U tile (transposed)
+            const int i = i0 + lr;
+            float av[8];
+            if (i < m) {
+                const uint4 h = *reinterpret_cast<const uint4*>(hi + (size_t)i * N + k0 + lg);
+                const uint4 l = *reinterpret_cast<const uint4*>(lo + (size_t)i * N + k0 + lg);
+                const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    av[2 * q] = __uint_as_float(hw[q] << 16) + __uint_as_float(lw[q] << 16);
+                    av[2 * q + 1] = __uint_as_float(hw[q] & 0xffff0000u) +
+                                    __uint_as_float(lw[q] & 0xffff0000u);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) av[q] = 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) As[lg + q][lr] = av[q];
+            const int b = b0 + lr;
+            float uv[8];
+            if (b < count) {
+                const float4 u0 = *reinterpret_cast<const float4*>(U + (size_t)b * N + k0 + lg);
+                const float4 u1 = *reinterpret_cast<const float4*>(U + (size_t)b * N + k0 + lg + 4);
+                uv[0] = u0.x; uv[1] = u0.y; uv[2] = u0.z; uv[3] = u0.w;
+                uv[4] = u1.x; uv[5] = u1.y; uv[6] = u1.z; uv[7] = u1.w;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) uv[q] = 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) Us[lg + q][lr] = uv[q];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) c[a][b] = 0.f;
+#pragma unroll 8
+        for (int k = 0; k < RS_BK; ++k) {
+            const float4 a4 = *reinterpret_cast<const float4*>(&As[k][ty * 4]);
+            const float4 u4 = *reinterpret_cast<const float4*>(&Us[k][tx * 4]);
+            const float av[4] = {a4.x, a4.y, a4.z, a4.w}, uv[4] = {u4.x, u4.y, u4.z, u4.w};
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) c[a][b] = fmaf(av[a], uv[b], c[a][b]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) l1[a][b] += c[a][b];
+        if ((chunk & 15) == 15) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    l2[a][b] += l1[a][b];
+                    l1[a][b] = 0.f;
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int i = i0 + ty * 4 + a;
+        if (i >= m) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int img = b0 + tx * 4 + b;
+            if (img < count) R[(size_t)img * m + i] = (l2[a][b] + l1[a][b]) - F[(size_t)img * m + i];
+        }
+    }
+}
+
+// ctrls[b].r2 = ||R_b||^2 (double-single, fixed order), one block per image.
+__global__ void k_batch_resid_r2(const float* __restrict__ R, int m, Ctrl* __restrict__ ctrls)
+{
+    __shared__ float2 red[32];
+    float2 s = make_float2(0.f, 0.f);
+    const float* r = R + (size_t)blockIdx.x * m;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) s = ds_add(s, ds_sq(r[i]));
+    s = block_sum_ds(s, red);
+    if (threadIdx.x == 0) ctrls[blockIdx.x].r2 = ds_value(s);
 }
 
 // A_eff = hi + lo (exact in binary32) from the two bf16 planes.
@@ -504,8 +605,12 @@ tvcs_status solve_batch(tvcs_ctx* h, int count, const float* const* f, float* co
     BCK(cudaEventRecord(h->ev0, s));
     if (h->opt.max_iter > 0) BCK(cudaGraphLaunch(b->exec, s));
     BCK(cudaEventRecord(h->ev1, s));
-    // end of run, per image: ||r||^2, final multiplier update, objective, residuals
-    k_batch_r2<<<count, 128, 0, s>>>(b->r2part, b->p1.tiles_m, b->ctrls);
+    // end of run, per image: ||r||^2 of the image's own residual recomputed on the CUDA
+    // cores, final multiplier update, objective, residuals
+    k_batch_resid<<<dim3((h->m + RS_BM - 1) / RS_BM, (count + RS_BB - 1) / RS_BB), 256, 0, s>>>(
+        reinterpret_cast<const unsigned short*>(h->P0), reinterpret_cast<const unsigned short*>(h->P1),
+        h->m, h->N, b->U, b->F, count, b->R);
+    k_batch_resid_r2<<<count, 256, 0, s>>>(b->R, h->m, b->ctrls);
     TvArgs a = batch_tv_args(h, count, MODE_PLAIN);
     launch_tv(h->n, a, 4, s);
     launch_tv(h->n, a, 5, s);

@@ -136,6 +136,20 @@ __device__ __forceinline__ void tma_load_1d(void* dst_smem, const void* src_gmem
         : "memory");
 }
 
+// The same copy issued as `pieces` bulk copies of nearly equal size (each a
+// multiple of 16 bytes; bytes must be one), completing on the same barrier.
+__device__ __forceinline__ void tma_load_1d_split(void* dst_smem, const void* src_gmem,
+                                                  uint32_t bytes, uint64_t* bar, uint64_t policy,
+                                                  int pieces)
+{
+    const uint32_t piece = ((bytes / (uint32_t)pieces) + 15u) & ~15u;
+    for (uint32_t off = 0; off < bytes; off += piece) {
+        const uint32_t len = bytes - off < piece ? bytes - off : piece;
+        tma_load_1d(static_cast<unsigned char*>(dst_smem) + off,
+                    static_cast<const unsigned char*>(src_gmem) + off, len, bar, policy);
+    }
+}
+
 // ---- bulk prefetch global -> L2 (no completion to wait for) ----
 // src 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void prefetch_l2_bulk(const void* src_gmem, uint32_t bytes)

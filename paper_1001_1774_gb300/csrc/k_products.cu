@@ -31,6 +31,8 @@ constexpr int PROD_NST = 3;
 // Rows of A prefetched into L2 per block before the dependency wait, beyond the
 // ring: 1 MB (16 rows at n = 128; 136 blocks then hold about L2's capacity).
 constexpr size_t PROD_PF_BYTES = 1024 * 1024;
+// Bulk copies per stage of the ring.
+constexpr int PROD_TMA_PIECES = 1;
 
 template <int V, int RL, int RS>
 struct ProdShape {
@@ -95,8 +97,8 @@ __global__ void __maxnreg__(128)
         const int rows = min(RS, nrows - s * RS);
         const uint32_t bytes = (uint32_t)rows * N * 4u;
         mbar_arrive_expect_tx(&full[slot], bytes);
-        tma_load_1d(stage + slot * S::STAGE_FLOATS, A + (size_t)(i0 + s * RS) * N, bytes,
-                    &full[slot], pol);
+        tma_load_1d_split(stage + slot * S::STAGE_FLOATS, A + (size_t)(i0 + s * RS) * N, bytes,
+                          &full[slot], pol, PROD_TMA_PIECES);
     };
     // The pf stages after the ring are prefetched into L2 before the wait as
     // well (nothing waits for them): while the u-solve still runs, HBM streams

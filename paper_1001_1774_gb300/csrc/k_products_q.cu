@@ -32,6 +32,8 @@
 namespace tvcs {
 
 constexpr int QPROD_YMAX = 1024;
+// Bulk copies per storage plane and stage (the binary32 plane, twice the bytes, takes twice as many).
+constexpr int QPROD_TMA_PIECES = 1;
 
 template <int PREC>
 struct QPrec;
@@ -219,17 +221,20 @@ __global__ void __launch_bounds__(CONS + 64, 1)
                 unsigned char* dst = smem + (size_t)slot * S::STAGE_BYTES;
                 if constexpr (PREC == 0) {
                     mbar_arrive_expect_tx(&full[slot], NS * 4u);
-                    tma_load_1d(dst, P0 + (row * N + col0) * 4, NS * 4u, &full[slot], pol);
+                    tma_load_1d_split(dst, P0 + (row * N + col0) * 4, NS * 4u, &full[slot], pol,
+                                      QPROD_TMA_PIECES * 2);
                 } else if constexpr (PREC == 1) {
                     mbar_arrive_expect_tx(&full[slot], NS * 4u);
-                    tma_load_1d(dst, P0 + (row * N + col0) * 2, NS * 2u, &full[slot], pol);
-                    tma_load_1d(dst + (size_t)NS * 2, P1 + (row * N + col0) * 2, NS * 2u,
-                                &full[slot], pol);
+                    tma_load_1d_split(dst, P0 + (row * N + col0) * 2, NS * 2u, &full[slot], pol,
+                                      QPROD_TMA_PIECES);
+                    tma_load_1d_split(dst + (size_t)NS * 2, P1 + (row * N + col0) * 2, NS * 2u,
+                                      &full[slot], pol, QPROD_TMA_PIECES);
                 } else {
                     mbar_arrive_expect_tx(&full[slot], NS * 3u);
-                    tma_load_1d(dst, P0 + (row * N + col0), NS * 1u, &full[slot], pol);
-                    tma_load_1d(dst + (size_t)NS, P1 + (row * N + col0) * 2, NS * 2u,
-                                &full[slot], pol);
+                    tma_load_1d_split(dst, P0 + (row * N + col0), NS * 1u, &full[slot], pol,
+                                      QPROD_TMA_PIECES);
+                    tma_load_1d_split(dst + (size_t)NS, P1 + (row * N + col0) * 2, NS * 2u,
+                                      &full[slot], pol, QPROD_TMA_PIECES);
                 }
                 ++issued;
             }

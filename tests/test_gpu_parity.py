@@ -212,6 +212,41 @@ def test_convergence_parity_fast_setting(tv):
     tv.tvcs_destroy(h)
 
 
+def objective_exact(A, f, u, mu):
+    """Phi(u) of eq. (tv) for a binary32 image, evaluated in binary64 (the oracle's TV)."""
+    u = np.asarray(u, dtype=np.float64)
+    n = int(round(np.sqrt(u.size)))
+    r = A.astype(np.float64) @ u.ravel() - f.astype(np.float64)
+    return oracle.tv(u.reshape(n, n)) + 0.5 * mu * float(r @ r)
+
+
+def test_workload_n32_converges_to_tol(tv):
+    # The n=32, m=307 workload (mu=1e3, beta=10, tol 1e-4) with an iteration cap large
+    # enough for eq. (stop) to end the run (the oracle needs about 4.4K iterations):
+    # the stop iteration within one of the oracle's, the image within 1e-4 and the
+    # objective within 1e-6 of the oracle's converged run (Thm 4: the iterates
+    # converge to a KKT point, so the two runs meet at the same solution).
+    P = synth.workload_n32()
+    tau = oracle.default_tau(P.A)
+    cap = 20000
+    h = make_handle(tv, P, tau, max_iter=cap, tol=P.tol)
+    u = np.empty(P.N, np.float32)
+    res = tv.tvcs_solve(h, P.f, u)
+    ref = oracle.solve(P.A, P.f, P.n, P.mu, P.beta, tau, tol=P.tol, max_iter=cap)
+    assert res.status == tv.TVCS_OK and res.stopped_by_tol == 1
+    assert ref.info["iters"] < cap
+    assert abs(res.iters - ref.info["iters"]) <= 1
+    same = ref if res.iters == ref.info["iters"] else oracle.solve(
+        P.A, P.f, P.n, P.mu, P.beta, tau, max_iter=res.iters)
+    assert rel(u, same.u) <= 1e-4 and rel(u, ref.u) <= 1e-4
+    obj = same.info["objective"]
+    assert abs(res.objective - obj) <= 1e-6 * obj                      # reported by the GPU
+    assert abs(objective_exact(P.A, P.f, u, P.mu) - obj) <= 1e-6 * obj  # of the GPU's image
+    print("n32 to tol: %d iterations, image %.2e, objective %.2e" %
+          (res.iters, rel(u, same.u), abs(res.objective - obj) / obj))
+    tv.tvcs_destroy(h)
+
+
 def test_workload_n32_to_500_iterations(tv):
     # n=32, m=307, mu=1e3, beta=10, tol 1e-4, <= 500 iterations.
     P = synth.workload_n32()
