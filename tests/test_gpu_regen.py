@@ -271,3 +271,38 @@ def test_uneven_workload_64_problems_sampled(tv):
     assert checked >= 3
     for h in hs:
         tv.tvcs_destroy(h)
+
+
+def test_uneven_workload_64_problems_every_side_fixed_iterations(tv):
+    # The whole 64-problem batch (A regenerated in the kernel) for a fixed 20
+    # iterations; a seeded sample covering every image side (64, 96, 128, 192) and
+    # every sampling ratio of the larger sides is compared with the FP64 oracle at
+    # 1e-5 (the oracle regenerates each sampled A on the host).
+    probs = synth.workload_uneven(64, materialise=False)
+    iters = 20
+    hs, taus = [], []
+    for P in probs:
+        h = regen_handle(tv, P.seed, P.m, P.n, P.mu, P.beta, 0.0, max_iter=iters, tol=0.0)
+        hs.append(h)
+        taus.append(tv.tvcs_get_tau(h))
+    us = [np.empty(P.N, np.float32) for P in probs]
+    res = tv.tvcs_solve_batched(hs, [P.f for P in probs], us)
+    assert all(r.iters == iters for r in res)
+    sample = {3: (64, 0.5), 28: (96, 0.1), 6: (96, 0.3), 18: (96, 0.5), 15: (128, 0.1),
+              22: (128, 0.2), 12: (128, 0.5), 5: (192, 0.1), 58: (192, 0.3), 23: (192, 0.5)}
+    seen = set()
+    for k, P in enumerate(probs):
+        if P.seed not in sample:
+            continue
+        assert (P.n, round(P.m / P.N, 1)) == sample[P.seed]
+        A = synth.gaussian_matrix(P.seed, P.m, P.N)
+        ref = oracle.solve(A, P.f, P.n, P.mu, P.beta, taus[k], max_iter=iters)
+        del A
+        err = rel(us[k], ref.u)
+        print("seed %d n %d m %d: rel image err %.2e" % (P.seed, P.n, P.m, err))
+        assert err <= 1e-5, (P.seed, P.n, P.m, err)
+        assert abs(res[k].objective - ref.info["objective"]) <= 1e-5 * ref.info["objective"]
+        seen.add(P.n)
+    assert seen == {64, 96, 128, 192}
+    for h in hs:
+        tv.tvcs_destroy(h)
