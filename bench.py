@@ -49,7 +49,7 @@ def parse_args():
     ap.add_argument("--no-sub-records", action="store_true",
                     help="skip the short batch256 and n256 segments of the default line")
     ap.add_argument("--workload", choices=["n128", "n32", "n256", "batch256", "batch256tol", "uneven64",
-                                           "dct128"],
+                                           "dct128", "products"],
                     default="n128",
                     help="n128: 128x128, m=4915, binary32 A (the benchmark workload); "
                          "n32: 32x32, m=307, to tol 1e-4; "
@@ -57,7 +57,11 @@ def parse_args():
                          "batch256: 256 images of 128x128 sharing one A (bf16 hi/lo); "
                          "uneven64: 64 problems of n in {64..192}, A regenerated in the kernel; "
                          "dct128: 128x128 with the partial-DCT encoder of Sec. 3.2, to tol 5e-5; "
-                         "batch256tol: the batch256 images, each to its own tol 1e-4 (compaction)")
+                         "batch256tol: the batch256 images, each to its own tol 1e-4 (compaction); "
+                         "products: the product kernel alone for --n, --m, --precision (A generated "
+                         "on the device), --steps back-to-back launches (for profiler captures)")
+    ap.add_argument("--n", type=int, default=256, help="image side of --workload products")
+    ap.add_argument("--m", type=int, default=13107, help="measurements of --workload products")
     ap.add_argument("--algo", choices=["iadm", "ftvcs"], default="iadm",
                     help="Algorithm 2 (IADM, default) or Algorithm 1 (FTVCS: lambda = 0, the penalty model)")
     ap.add_argument("--precision", type=int, default=0,
@@ -1014,6 +1018,38 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_products(args):
+    """The product kernel alone (rows a6-a7): A (m x n^2) generated on the device from
+    seed 7 and stored per --precision, u and f set, then --steps back-to-back product
+    launches timed with CUDA events.  The two launches that setting u and f makes
+    come first (profiler captures skip them)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1001_1774_gb300 as tv
+    n, m, prec = args.n, args.m, args.precision
+    N = n * n
+    opt = tv.tvcs_default_options()
+    opt.precision = prec
+    opt.tau = 0.1
+    opt.host_loop = 1
+    h = tv.tvcs_create(None, 7, m, n, 500.0, 10.0, 0.0, opt)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    u = torch.rand(N, device="cuda", generator=g)
+    f = torch.randn(m, device="cuda", generator=g)
+    tv.tvcs_set_state(h, tv.TVCS_STATE_F, f)
+    tv.tvcs_set_state(h, tv.TVCS_STATE_U, u)
+    ms = tv.tvcs_time_stage(h, 2, args.steps)
+    tv.tvcs_destroy(h)
+    bpe = STORAGE[prec][1]
+    alg = m * N * bpe + (4 * m if prec == 2 else 0) + 4 * (N + 2 * m)
+    us = ms * 1e3 / args.steps
+    peak, src = hbm_peak()
+    print(json.dumps({"workload": "products_n%d_m%d_%s" % (n, m, STORAGE[prec][0]), "launches": args.steps,
+                      "us_per_launch": us, "algorithmic_bytes": alg, "GB_s": alg / us / 1e3,
+                      "frac_of_hbm": alg / us / 1e3 / peak, "peak_source": src}), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -1026,6 +1062,8 @@ def main():
         run_dct(args)
     elif args.workload == "batch256tol":
         run_batched_tol(args)
+    elif args.workload == "products":
+        run_products(args)
     else:
         run_ours(args)
 
