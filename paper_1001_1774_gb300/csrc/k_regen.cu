@@ -5,16 +5,20 @@
 // products read no byte of A from memory (the two matrix-vector products of
 // eq. (line), Sec. 2.1, with A given by its seed).
 //
-// A cluster of CS blocks splits each row's N columns into CS slices of
-// W = N / CS; block `rank` reads x's slice through the read-only cache and
-// accumulates its slice of A^T r in shared memory.  A tile is up to 16 consecutive rows.  Per tile:
-//   gen     each thread generates four-element groups (one Philox block each)
-//           of one row, stores them in the tile buffer and accumulates the
-//           row's dot product with x;
-//   exch    every block reads the per-row partial dots of all blocks of its
-//           cluster (distributed shared memory) and adds them in rank order,
-//           so all blocks hold the same r_i;
-//   update  g_slice += A_tile^T r_tile from the tile buffer.
+// A cluster of CS blocks (4, 8 or 16) splits each row's N columns into CS slices
+// of W = N / CS; block `rank` reads x's slice through the read-only cache and
+// accumulates its slice of A^T r in shared memory.  A tile is up to 16
+// consecutive rows.  Per tile:
+//   gen     the warps take (row, segment) items: a segment is one sixteenth of
+//           a row (N / 16 columns, so a block owns 16 / CS of them); lane L
+//           generates the four-element groups L, L+32, L+64, ... of the segment
+//           (one Philox block each, two in flight), stores them in the tile
+//           buffer and adds them into its dot product with x in that order; a
+//           fixed shuffle tree adds the 32 lanes;
+//   exch    every block reads the 16 segment dots of each row from the blocks of
+//           its cluster (distributed shared memory) and adds them in segment
+//           order, so all blocks hold the same r_i;
+//   update  g_slice += A_tile^T r_tile from the tile buffer, row after row.
 // With two tile buffers, split cluster barriers (arrive after the partial
 // dots of tile t, wait before reading them) let the generation of tile t+1
 // run while the exchange of tile t completes; with one, the shared memory
@@ -22,12 +26,14 @@
 // element of A is generated once per launch.
 //
 // Many problems (own m, N, seed, x, y) share one launch.  Problem p's rows are
-// cut into `chunks` chunks; the chunks of the active problems are numbered in
+// cut into chunks of a fixed number of rows (about 2^22 entries, independent
+// of the launch shape); the chunks of the active problems are numbered in
 // problem order (T in all) and cluster q takes chunks [q T / Q, (q+1) T / Q).
-// A run of consecutive chunks of one problem inside a cluster's range sums
-// into one slice, stored at the end of the run in the slot of the run's first
-// chunk.  k_regen_reduce finds the same run heads from (T, Q) and adds the
-// slots in chunk order: the result does not depend on timing.
+// Every chunk stores its slice of A^T r and its ||r||^2 (added row after row)
+// in a slot of its own; k_regen_reduce adds a problem's slots in chunk order.
+// So every sum has an order fixed by the problem alone: the results do not
+// depend on the cluster size, tile height, kernel variant or number of clusters
+// the tuner picks, nor on which other problems share the launch.
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -42,7 +48,9 @@ namespace {
 
 constexpr int RG_THREADS = 256;
 constexpr int RG_RTMAX = 16;                 // rows per tile at most
-constexpr int RG_NWMAX = RG_THREADS / 32;    // warps sharing one row at most
+constexpr int RG_NWARP = RG_THREADS / 32;
+constexpr int RG_NSEG = 16;                  // segments of a row (fixed summation order)
+constexpr int RG_SEGMAX = 4;                 // segments of a row per block (cluster size >= 4)
 constexpr int RG_QMAX = 1024;                // clusters per launch at most
 
 __host__ __device__ __forceinline__ int range_start(int q, int T, int Q)
@@ -96,7 +104,7 @@ __device__ int active_prefix(const RegenProb* __restrict__ probs, int P, int mod
 }
 
 struct TileMeta {
-    int p, i0, nr, rt, W, head, last;   // last: the run of the slice ends with this tile
+    int p, i0, nr, rt, W, chunk, last;   // last: the tile ends its chunk
 };
 
 __device__ __forceinline__ void fma4(float4& acc, const float4& a, float s)
@@ -123,16 +131,16 @@ k_regen_products(const RegenProb* __restrict__ probs, int P, int mode, int wmax,
     int* scan = pre + pcap + 4;                                 // RG_THREADS
     float* gs = reinterpret_cast<float*>(scan + RG_THREADS);    // A^T r slice, wmax
     float* tile = gs + wmax;                                    // NBUF x tile_cap
-    float* wpart = tile + NBUF * tile_cap;                      // 2 x RTMAX x NWMAX
-    float* slotv = wpart + 2 * RG_RTMAX * RG_NWMAX;             // 2 x RTMAX, read by the peers
-    float* rvec = slotv + 2 * RG_RTMAX;                         // 2 x RTMAX
+    float* slotv = tile + NBUF * tile_cap;                      // 2 x RTMAX x SEGMAX, read by peers
+    float* rvec = slotv + 2 * RG_RTMAX * RG_SEGMAX;             // 2 x RTMAX
 
     cg::cluster_group cluster = cg::this_cluster();
     const int CS = (int)cluster.num_blocks();
     const int rank = (int)cluster.block_rank();
     const int Q = gridDim.x / CS;
     const int cq = blockIdx.x / CS;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int segs = RG_NSEG / CS;   // segments of a row this block owns
 
     const int T = active_prefix(probs, P, mode, pre, scan);
     if (blockIdx.x == 0)
@@ -153,25 +161,26 @@ k_regen_products(const RegenProb* __restrict__ probs, int P, int mode, int wmax,
     int rt = tile_rows_for(W, tile_cap);
     int row = c * RC;
     int cend = min(m, row + RC);
-    int head = c;
 
-    float2 r2acc = make_float2(0.f, 0.f);   // double-single ||r||^2 of the problem
+    float2 r2acc = make_float2(0.f, 0.f);   // double-single ||r||^2 of the chunk (block 0, thread 0)
     // exch + update of tile tm: partial dots from slot buffer sb, entries from tile buffer tb
     auto finish = [&](const TileMeta& tm, int sb, int tb) {
-        cluster_wait();   // every block's partial dots of tile tm are visible
+        cluster_wait();   // every block's segment dots of tile tm are visible
         const RegenProb* pp = probs + tm.p;
         if (tid < tm.nr) {
-            float s = 0.f;
-            for (int k = 0; k < CS; ++k) s += cluster.map_shared_rank(slotv, k)[sb * RG_RTMAX + tid];
+            float s = 0.f;   // segments 0 .. 15 in order: block k holds k segs .. (k+1) segs - 1
+            for (int k = 0; k < CS; ++k) {
+                const float* pv = cluster.map_shared_rank(slotv, k) + (sb * RG_RTMAX + tid) * RG_SEGMAX;
+                for (int q = 0; q < segs; ++q) s += pv[q];
+            }
             const int i = tm.i0 + tid;
             const float rv = pp->y ? s - pp->y[i] : s;
             rvec[sb * RG_RTMAX + tid] = rv;
-            if (rank == 0) {
-                pp->r[i] = rv;
-                r2acc = ds_add(r2acc, ds_sq(rv));
-            }
+            if (rank == 0) pp->r[i] = rv;
         }
         __syncthreads();
+        if (rank == 0 && tid == 0)   // ||r||^2 of the chunk, row after row
+            for (int rr = 0; rr < tm.nr; ++rr) r2acc = ds_add(r2acc, ds_sq(rvec[sb * RG_RTMAX + rr]));
         const float4* tbuf = reinterpret_cast<const float4*>(tile + tb * tile_cap);
         float4* g4 = reinterpret_cast<float4*>(gs);
         const int G = tm.W / 4;
@@ -180,18 +189,17 @@ k_regen_products(const RegenProb* __restrict__ probs, int P, int mode, int wmax,
             for (int rr = 0; rr < tm.nr; ++rr) fma4(acc, tbuf[rr * G + q4], rvec[sb * RG_RTMAX + rr]);
             g4[q4] = acc;
         }
-        if (tm.last) {   // each thread stores and clears the groups it accumulated
-            float4* dst = reinterpret_cast<float4*>(pp->gslot + (size_t)tm.head * pp->N +
+        if (tm.last) {   // the chunk ends: each thread stores and clears the groups it accumulated
+            float4* dst = reinterpret_cast<float4*>(pp->gslot + (size_t)tm.chunk * pp->N +
                                                     (size_t)rank * tm.W);
             for (int q4 = tid; q4 < G; q4 += RG_THREADS) {
                 dst[q4] = g4[q4];
                 g4[q4] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            if (rank == 0 && tid < 32) {   // r2acc lives in threads < 16 of block 0
-                const float2 v = warp_sum_ds(r2acc);
-                if (tid == 0) pp->r2slot[tm.head] = v;
+            if (rank == 0 && tid == 0) {
+                pp->r2slot[tm.chunk] = r2acc;
+                r2acc = make_float2(0.f, 0.f);
             }
-            r2acc = make_float2(0.f, 0.f);
         }
     };
 
@@ -208,22 +216,25 @@ k_regen_products(const RegenProb* __restrict__ probs, int P, int mode, int wmax,
             cur.nr = min(rt, cend - row);
             cur.rt = rt;
             cur.W = W;
-            cur.head = head;
-            // gen: rows of the tile, tpr threads per row
+            cur.chunk = c;
+            // gen: (row, segment) items over the warps
             {
-                const int tpr = RG_THREADS / rt;
-                const int rr = tid / tpr, lane = tid - rr * tpr;
-                const int G = W / 4;
-                float dot = 0.f;
-                if (rr < cur.nr) {
+                const int Gs = N / (4 * RG_NSEG);   // groups of a segment
+                const int G = W / 4;                // groups of the block's slice of a row
+                float4* tbase = reinterpret_cast<float4*>(tile + tb * tile_cap);
+                const float4* xbase = reinterpret_cast<const float4*>(pr->x + (size_t)rank * W);
+                const float scale = pr->scale;
+                const unsigned long long seed = pr->seed;
+                for (int it = warp; it < cur.nr * segs; it += RG_NWARP) {
+                    const int rr = it / segs, sl = it - rr * segs;
                     const unsigned long long i = (unsigned long long)(cur.i0 + rr);
+                    const int g0 = sl * Gs;
                     const unsigned long long b0 =
-                        (i * (unsigned long long)N + (unsigned long long)rank * W) >> 2;
-                    float4* trow = reinterpret_cast<float4*>(tile + tb * tile_cap) + rr * G;
+                        ((i * (unsigned long long)N + (unsigned long long)rank * W) >> 2) + g0;
+                    float4* trow = tbase + rr * G + g0;
                     // x slice through the read-only path: L1 keeps it across the tile's rows
-                    const float4* x4 = reinterpret_cast<const float4*>(pr->x + (size_t)rank * W);
-                    const float scale = pr->scale;
-                    const unsigned long long seed = pr->seed;
+                    const float4* x4 = xbase + g0;
+                    float dot = 0.f;
                     auto emit = [&](int q, const float4& z) {
                         float4 a;
                         a.x = __fmul_rn(z.x, scale);
@@ -237,23 +248,23 @@ k_regen_products(const RegenProb* __restrict__ probs, int P, int mode, int wmax,
                         dot = fmaf(a.z, xv.z, dot);
                         dot = fmaf(a.w, xv.w, dot);
                     };
-                    // two independent Philox blocks in flight per thread (latency hiding)
-                    int q4 = lane;
-                    for (; q4 + tpr < G; q4 += 2 * tpr) {
-                        const float4 z0 = gen_normals4(seed, 0u, b0 + q4);
-                        const float4 z1 = gen_normals4(seed, 0u, b0 + q4 + tpr);
-                        emit(q4, z0);
-                        emit(q4 + tpr, z1);
+                    // groups lane, lane+32, lane+64, ... in this order, two Philox blocks in flight
+                    int q = lane;
+                    for (; q + 32 < Gs; q += 64) {
+                        const float4 z0 = gen_normals4(seed, 0u, b0 + q);
+                        const float4 z1 = gen_normals4(seed, 0u, b0 + q + 32);
+                        emit(q, z0);
+                        emit(q + 32, z1);
                     }
-                    if (q4 < G) emit(q4, gen_normals4(seed, 0u, b0 + q4));
+                    if (q < Gs) emit(q, gen_normals4(seed, 0u, b0 + q));
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
+                    if (lane == 0) slotv[(sb * RG_RTMAX + rr) * RG_SEGMAX + sl] = dot;
                 }
-                const int wl = tpr < 32 ? tpr : 32;
-                for (int off = wl >> 1; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
-                if (rr < cur.nr && (lane & (wl - 1)) == 0)
-                    wpart[(sb * RG_RTMAX + rr) * RG_NWMAX + (lane >> 5)] = dot;
             }
             // advance the cursor
             row += cur.nr;
+            cur.last = row >= cend ? 1 : 0;
             if (row >= cend) {
                 ++j;
                 if (j < j1) {
@@ -268,23 +279,15 @@ k_regen_products(const RegenProb* __restrict__ probs, int P, int mode, int wmax,
                         RC = pr->rows_per_chunk;
                         W = N / CS;
                         rt = tile_rows_for(W, tile_cap);
-                        head = c;
                     }
                     row = c * RC;
                     cend = min(m, row + RC);
                 }
             }
-            cur.last = (j >= j1 || p != cur.p) ? 1 : 0;
         }
         if (NBUF == 2 && have_prev) finish(prev, sb ^ 1, tb ^ 1);
         if (!have_cur) break;
-        __syncthreads();   // partial dots of this tile complete; the other tile buffer is free
-        if (tid < cur.nr) {
-            const int nw = (RG_THREADS / cur.rt) / 32;
-            float s = 0.f;
-            for (int w = 0; w < (nw > 0 ? nw : 1); ++w) s += wpart[(sb * RG_RTMAX + tid) * RG_NWMAX + w];
-            slotv[sb * RG_RTMAX + tid] = s;
-        }
+        __syncthreads();   // segment dots of this tile complete; the other tile buffer is free
         cluster_arrive();
         if (NBUF == 1) {
             finish(cur, sb, 0);
@@ -299,14 +302,12 @@ k_regen_products(const RegenProb* __restrict__ probs, int P, int mode, int wmax,
     cluster_wait();
 }
 
-// g = sum of the run slots (chunk order), ctrl->r2 = sum of the run r2 slots.
+// g = sum of the chunk slots in chunk order, ctrl->r2 = sum of the chunk r2 slots.
 // Grid (ceil(maxN / 1024), P), 256 threads, one float4 per thread.
 __global__ void __launch_bounds__(256)
-k_regen_reduce(const RegenProb* __restrict__ probs, int P, int Q, const int* __restrict__ pre,
+k_regen_reduce(const RegenProb* __restrict__ probs, int P, const int* __restrict__ pre,
                cudaGraphConditionalHandle cond, int set_cond)
 {
-    __shared__ int heads[RG_QMAX + 1];
-    __shared__ int nh;
     const int p = blockIdx.y;
     const int tid = threadIdx.x;
     const RegenProb& pr = probs[p];
@@ -316,26 +317,15 @@ k_regen_reduce(const RegenProb* __restrict__ probs, int P, int Q, const int* __r
         const int cont = (!c->done && c->error == ERR_NONE && lc < c->loops_max) ? 1 : 0;
         cudaGraphSetConditional(cond, (unsigned)cont);
     }
-    const int s = pre[p], K = pre[p + 1] - s;
+    const int K = pre[p + 1] - pre[p];
     if (K == 0) return;   // inactive in this launch
-    const int T = pre[P];
-    if (tid == 0) {
-        int n = 0;
-        heads[n++] = 0;
-        for (int q = 1; q < Q; ++q) {
-            const int st = range_start(q, T, Q);
-            if (st > s && st < s + K && st - s != heads[n - 1]) heads[n++] = st - s;
-        }
-        nh = n;
-    }
-    __syncthreads();
     const int n4 = pr.N / 4;
     const int q4 = blockIdx.x * blockDim.x + tid;
     if (q4 < n4) {
         const float4* slot = reinterpret_cast<const float4*>(pr.gslot);
-        float4 acc = slot[(size_t)heads[0] * n4 + q4];
-        for (int h = 1; h < nh; ++h) {
-            const float4 v = slot[(size_t)heads[h] * n4 + q4];
+        float4 acc = slot[q4];
+        for (int h = 1; h < K; ++h) {
+            const float4 v = slot[(size_t)h * n4 + q4];
             acc.x += v.x;
             acc.y += v.y;
             acc.z += v.z;
@@ -344,8 +334,8 @@ k_regen_reduce(const RegenProb* __restrict__ probs, int P, int Q, const int* __r
         reinterpret_cast<float4*>(pr.g)[q4] = acc;
     }
     if (blockIdx.x == 0 && tid == 0 && pr.ctrl) {
-        float2 v = pr.r2slot[heads[0]];
-        for (int h = 1; h < nh; ++h) v = ds_add(v, pr.r2slot[heads[h]]);
+        float2 v = pr.r2slot[0];
+        for (int h = 1; h < K; ++h) v = ds_add(v, pr.r2slot[h]);
         pr.ctrl->r2 = ds_value(v);
     }
 }
@@ -353,8 +343,8 @@ k_regen_reduce(const RegenProb* __restrict__ probs, int P, int Q, const int* __r
 static size_t regen_smem(int wmax, int tile_cap, int nbuf, int pcap)
 {
     return sizeof(int) * ((size_t)pcap + 4 + RG_THREADS) +
-           sizeof(float) * ((size_t)wmax + (size_t)nbuf * tile_cap + 2 * RG_RTMAX * RG_NWMAX +
-                            4 * RG_RTMAX);
+           sizeof(float) * ((size_t)wmax + (size_t)nbuf * tile_cap + 2 * RG_RTMAX * RG_SEGMAX +
+                            2 * RG_RTMAX);
 }
 
 int regen_tile_rows(const RegenPlan& plan, int N)
@@ -396,7 +386,8 @@ static bool configure_t(RegenPlan* plan, int optin)
 bool regen_configure(RegenPlan* plan)
 {
     plan->clusters = 0;
-    if (plan->cs < 1 || plan->cs > 16 || plan->wmax <= 0 || plan->wmax % 4 != 0 ||
+    if ((plan->cs != 4 && plan->cs != 8 && plan->cs != 16) || plan->wmax <= 0 ||
+        plan->wmax % 4 != 0 || tile_rows_for(plan->wmax, plan->tile_cap) < plan->cs / 2 ||
         plan->tile_cap < plan->wmax || plan->tile_cap % 4 != 0 ||
         plan->minb < 2 || plan->minb > 4 || (plan->nbuf != 1 && plan->nbuf != 2) ||
         plan->pcap < 1 || plan->pcap > REGEN_PMAX)
@@ -444,9 +435,9 @@ void launch_regen_reduce(const RegenProb* probs, int P, int maxN, int mode, cons
                          const int* pre, unsigned long long cond, int set_cond, cudaStream_t s)
 {
     (void)mode;
+    (void)plan;
     const dim3 grid((maxN / 4 + 255) / 256, P);
-    k_regen_reduce<<<grid, 256, 0, s>>>(probs, P, plan.clusters, pre,
-                                        (cudaGraphConditionalHandle)cond, set_cond);
+    k_regen_reduce<<<grid, 256, 0, s>>>(probs, P, pre, (cudaGraphConditionalHandle)cond, set_cond);
 }
 
 }  // namespace tvcs

@@ -15,9 +15,11 @@
 // Problems that met eq. (stop) drop out of the product launch's work list.
 //
 // Tiles are chosen by measurement: every candidate of cluster size (4, 8, 16),
-// tile height (1, 2, 4, 8 rows of the largest problem) and kernel variant
-// (registers for 2, 3 or 4 blocks per SM; one or two tile buffers) is timed on
-// the actual problem set and the fastest is kept.
+// tile height (1, 2, 4, 8 rows of the largest problem, at least half the
+// cluster size) and kernel variant (registers for 2, 3 or 4 blocks per SM; one
+// or two tile buffers) is timed on the actual problem set and the fastest is
+// kept.  Every candidate adds in the same order (fixed row segments and
+// chunks), so the choice changes the time, not the results.
 #include <algorithm>
 #include <utility>
 #include <cuda_runtime.h>
@@ -111,14 +113,15 @@ tvcs_status ralloc(void** p, size_t bytes)
     return TVCS_OK;
 }
 
-// Rows per chunk so that a chunk holds about `target` entries of A, rounded up
-// to whole tiles.
-void chunking(const RegenPlan& plan, int m, int N, double target, int* rpc, int* chunks)
+// Rows per chunk: about 2^22 entries of A, fixed by the problem's row length
+// alone, so that the chunk slots (and with them the order of every sum of A^T r
+// and ||r||^2) do not depend on the launch shape.
+constexpr double kChunkEntries = 4194304.0;
+
+void chunking(int m, int N, int* rpc, int* chunks)
 {
-    const int rt = regen_tile_rows(plan, N);
-    long long rows = (long long)(target / N);
+    long long rows = (long long)ceil(kChunkEntries / N);
     if (rows < 1) rows = 1;
-    rows = (rows + rt - 1) / rt * rt;
     if (rows > m) rows = m;
     *rpc = (int)rows;
     *chunks = (int)((m + rows - 1) / rows);
@@ -151,15 +154,12 @@ struct Layout {
     size_t gfloats = 0, rslots = 0;
 };
 
-Layout layout_for(const RegenPlan& plan, const std::vector<RegenProb>& probs, int per_cluster)
+Layout layout_for(const std::vector<RegenProb>& probs)
 {
     Layout L;
-    double total = 0.0;
-    for (const RegenProb& p : probs) total += (double)p.m * p.N;
-    const double target = total / ((double)plan.clusters * per_cluster);
     for (const RegenProb& p : probs) {
         int rpc = 0, ch = 0;
-        chunking(plan, p.m, p.N, target, &rpc, &ch);
+        chunking(p.m, p.N, &rpc, &ch);
         L.rpc.push_back(rpc);
         L.chunks.push_back(ch);
         L.gofs.push_back(L.gfloats);
@@ -182,9 +182,10 @@ void apply_layout(const Layout& L, float* gslot, float2* r2slot, std::vector<Reg
 }
 
 // Times each candidate plan on the problem set (one warm-up launch, one timed)
-// and returns the fastest.  gslot / r2slot must hold the largest layout.
-tvcs_status autotune(std::vector<RegenProb> probs, int maxN, int per_cluster, RegenProb* dtab,
-                     float* gslot, float2* r2slot, int* pre, cudaStream_t s, RegenPlan* best)
+// and returns the fastest.  The chunk layout is the same for every plan (and so
+// are the results); gslot / r2slot hold it.
+tvcs_status autotune(std::vector<RegenProb> probs, int maxN, RegenProb* dtab, float* gslot,
+                     float2* r2slot, int* pre, cudaStream_t s, RegenPlan* best)
 {
     std::vector<RegenPlan> cands = candidates(maxN, (int)probs.size());
     if (cands.empty()) return set_last_error(TVCS_ERR_UNSUPPORTED, "no cluster of the regenerating product kernel fits");
@@ -193,10 +194,9 @@ tvcs_status autotune(std::vector<RegenProb> probs, int maxN, int per_cluster, Re
     RCK(cudaEventCreate(&e1));
     const int P = (int)probs.size();
     // one timed launch (after one untimed) per candidate; the reps-launch minimum
+    apply_layout(layout_for(probs), gslot, r2slot, &probs);
+    RCK(cudaMemcpyAsync(dtab, probs.data(), sizeof(RegenProb) * P, cudaMemcpyHostToDevice, s));
     auto time_plan = [&](const RegenPlan& c, int reps, float* out) -> tvcs_status {
-        Layout L = layout_for(c, probs, per_cluster);
-        apply_layout(L, gslot, r2slot, &probs);
-        RCK(cudaMemcpyAsync(dtab, probs.data(), sizeof(RegenProb) * P, cudaMemcpyHostToDevice, s));
         launch_regen(dtab, P, MODE_PLAIN, c, pre, s);
         launch_regen_reduce(dtab, P, maxN, MODE_PLAIN, c, pre, 0ull, 0, s);
         float best = -1.f;
@@ -251,19 +251,6 @@ tvcs_status autotune(std::vector<RegenProb> probs, int maxN, int per_cluster, Re
     return TVCS_OK;
 }
 
-size_t max_layout_floats(const std::vector<RegenProb>& probs, int maxN, int per_cluster,
-                         size_t* rslots)
-{
-    size_t g = 0, r = 0;
-    for (RegenPlan c : candidates(maxN, (int)probs.size())) {
-        Layout L = layout_for(c, probs, per_cluster);
-        if (L.gfloats > g) g = L.gfloats;
-        if (L.rslots > r) r = L.rslots;
-    }
-    *rslots = r;
-    return g;
-}
-
 std::mutex g_plan_mutex;
 std::map<std::tuple<int, int, int>, RegenPlan> g_plans;   // (device, N, m) -> tuned plan
 
@@ -312,11 +299,11 @@ tvcs_status regen_init(tvcs_ctx* h)
     base.r = h->tr;
     base.g = h->tg;
     std::vector<RegenProb> one(1, base);
-    size_t rslots = 0;
-    const size_t gfl = max_layout_floats(one, h->N, 2, &rslots);
-    if (gfl == 0) return set_last_error(TVCS_ERR_UNSUPPORTED, "no cluster of the regenerating product kernel fits");
-    RCKS(ralloc((void**)&g->gslot, sizeof(float) * gfl));
-    RCKS(ralloc((void**)&g->r2slot, sizeof(float2) * rslots));
+    const Layout L0 = layout_for(one);
+    if (candidates(h->N, 1).empty())
+        return set_last_error(TVCS_ERR_UNSUPPORTED, "no cluster of the regenerating product kernel fits");
+    RCKS(ralloc((void**)&g->gslot, sizeof(float) * L0.gfloats));
+    RCKS(ralloc((void**)&g->r2slot, sizeof(float2) * L0.rslots));
     RCKS(ralloc((void**)&g->pre, sizeof(int) * 4));
     RCKS(ralloc((void**)&g->dtab, sizeof(RegenProb) * kTab));
     RegenPlan plan;
@@ -333,13 +320,12 @@ tvcs_status regen_init(tvcs_ctx* h)
         regen_configure(&plan);
     } else {
         launch_fill(h->tx, h->N, (float)(1.0 / sqrt((double)h->N)), h->stream);
-        RCKS(autotune(one, h->N, 2, g->dtab, g->gslot, g->r2slot, g->pre, h->stream, &plan));
+        RCKS(autotune(one, h->N, g->dtab, g->gslot, g->r2slot, g->pre, h->stream, &plan));
         std::lock_guard<std::mutex> lk(g_plan_mutex);
         g_plans[{h->dev, h->N, h->m}] = plan;
     }
     g->plan = plan;
-    Layout L = layout_for(plan, one, 2);
-    apply_layout(L, g->gslot, g->r2slot, &one);
+    apply_layout(L0, g->gslot, g->r2slot, &one);
     g->htab.clear();
     g->htab.push_back(one[0]);
     RCK(cudaMemcpy(g->dtab, &one[0], sizeof(RegenProb), cudaMemcpyHostToDevice));
@@ -534,13 +520,10 @@ tvcs_status build_uneven(const tvcs_handle* hs, int count, const double* mu, tvc
             p.ctrl = u->ctrls + k;
             u->elems += (long long)h->m * c.N;
         }
-    size_t rslots = 0;
-    const size_t gfl = max_layout_floats(probs, u->maxN, 16, &rslots);
-    if (gfl == 0) return set_last_error(TVCS_ERR_UNSUPPORTED, "no cluster of the regenerating product kernel fits");
-    RCKS(ralloc((void**)&u->gslot, sizeof(float) * gfl));
-    RCKS(ralloc((void**)&u->r2slot, sizeof(float2) * rslots));
-    RCKS(autotune(probs, u->maxN, 16, u->dtab, u->gslot, u->r2slot, u->pre, s, &u->plan));
-    Layout L = layout_for(u->plan, probs, 16);
+    const Layout L = layout_for(probs);
+    RCKS(ralloc((void**)&u->gslot, sizeof(float) * L.gfloats));
+    RCKS(ralloc((void**)&u->r2slot, sizeof(float2) * L.rslots));
+    RCKS(autotune(probs, u->maxN, u->dtab, u->gslot, u->r2slot, u->pre, s, &u->plan));
     apply_layout(L, u->gslot, u->r2slot, &probs);
     RCK(cudaMemcpy(u->dtab, probs.data(), sizeof(RegenProb) * count, cudaMemcpyHostToDevice));
     for (RegenProb& p : probs) p.x = u->zero;   // start point: A^T (0 - f)

@@ -306,3 +306,38 @@ def test_uneven_workload_64_problems_every_side_fixed_iterations(tv):
     assert seen == {64, 96, 128, 192}
     for h in hs:
         tv.tvcs_destroy(h)
+
+
+def test_uneven_results_do_not_depend_on_the_batch_or_the_tuned_plan(tv):
+    # The regenerating products add every sum in an order fixed by the problem
+    # alone (row segments, chunk slots), whatever launch shape the tuner picks for
+    # a problem set.  A problem solved in three different batches (each tuned on
+    # its own: different widest rows, tile heights and chunk-to-cluster
+    # assignments) gives bit-identical images and summaries.
+    probs = uneven_problems(SHAPES, first_seed=101)
+    extra = uneven_problems([(96, 0.2), (128, 0.1)], first_seed=151)
+    hs = [regen_handle(tv, P.seed, P.m, P.n, P.mu, P.beta, 0.1, max_iter=25) for P in probs]
+    hx = [regen_handle(tv, P.seed, P.m, P.n, P.mu, P.beta, 0.1, max_iter=25) for P in extra]
+    u_all = [np.empty(P.N, np.float32) for P in probs]
+    r_all = tv.tvcs_solve_batched(hs, [P.f for P in probs], u_all)
+    # the first three problems next to two larger ones (wider rows: other tiles)
+    sub = [0, 1, 2]
+    u_sub = [np.empty(probs[k].N, np.float32) for k in sub] + [np.empty(P.N, np.float32) for P in extra]
+    r_sub = tv.tvcs_solve_batched([hs[k] for k in sub] + hx, [probs[k].f for k in sub] + [P.f for P in extra],
+                                  u_sub)
+    for j, k in enumerate(sub):
+        assert np.array_equal(u_sub[j], u_all[k]), k
+        assert r_sub[j].objective == r_all[k].objective and r_sub[j].resid2 == r_all[k].resid2
+    # one problem alone
+    for k in (3, 6):
+        u1 = np.empty(probs[k].N, np.float32)
+        r1 = tv.tvcs_solve_batched([hs[k]], [probs[k].f], [u1])
+        assert np.array_equal(u1, u_all[k]), k
+        assert r1[0].objective == r_all[k].objective
+    # and the batch against the oracle, so that the equal results are also right
+    for k in (0, 6):
+        P = probs[k]
+        ref = oracle.solve(P.A, P.f, P.n, P.mu, P.beta, 0.1, max_iter=25)
+        assert rel(u_all[k], ref.u) <= 1e-5
+    for h in hs + hx:
+        tv.tvcs_destroy(h)
