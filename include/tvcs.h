@@ -90,6 +90,14 @@ typedef struct {
                             met eq. (stop) leaves the tensor-core GEMMs after its last iteration:
                             the running images are packed into the leading columns and the GEMMs
                             shrink with them; 0: every image keeps its column to the end */
+    int autotune;        /* 1 (default): launch shapes are picked by timing candidates on the
+                            device and cached per device and problem size -- the shared-A batch's
+                            two GEMMs (number of persistent blocks, hence the stream-K split) at
+                            the first batched call, and the regenerating products (cluster size,
+                            tile height, kernel variant) at tvcs_create; 0: the default shapes
+                            (one GEMM block per SM; the first regenerating candidate).  A GEMM
+                            shape changes the grouping of its K sums (results agree to binary32
+                            rounding); a regenerating shape changes no result. */
 } tvcs_options;
 
 typedef struct {

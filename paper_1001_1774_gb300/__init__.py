@@ -46,7 +46,7 @@ class tvcs_options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("init", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("power_iters", ctypes.c_int), ("timeout_cycles", ctypes.c_longlong),
                 ("host_loop", ctypes.c_int), ("a_mode", ctypes.c_int),
-                ("batch_compact", ctypes.c_int)]
+                ("batch_compact", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class tvcs_result(ctypes.Structure):

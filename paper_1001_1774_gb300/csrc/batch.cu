@@ -13,7 +13,11 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -243,6 +247,35 @@ void free_buffers(tvcs_batch* b)
     b->cap = 0;
 }
 
+// True when p[i] = p[0] + i * len for every i and the whole range lies in one
+// allocation (pageable host memory, or one device / pinned allocation), so that
+// one copy can move all images.
+template <typename T>
+bool contiguous(T* const* p, int count, size_t len)
+{
+    for (int i = 1; i < count; ++i)
+        if (p[i] != p[0] + (size_t)i * len) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p[0]) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeUnregistered) return true;
+    CUdeviceptr base = 0;
+    size_t size = 0;
+    const CUdeviceptr a = (CUdeviceptr)(uintptr_t)p[0];
+    if (cuMemGetAddressRange(&base, &size, a) != CUDA_SUCCESS) return false;
+    return a + (CUdeviceptr)(sizeof(T) * len * (size_t)count) <= base + size;
+}
+
+tvcs_status sync_check(tvcs_ctx* h, const char* what)
+{
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return set_last_error(TVCS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return TVCS_OK;
+}
+
 tvcs_status upload_plan(const GemmPlan& p, int** tsb, int** ss, cudaStream_t s)
 {
     BCKS(balloc((void**)tsb, sizeof(int) * p.tile_seg_begin.size()));
@@ -267,6 +300,98 @@ tvcs_status make_maps(tvcs_ctx* h, int count)
               make_bf16_map(&b->mRh, b->Rh, h->m, count, b->mpad, GEMM_Y_BOX) &&
               make_bf16_map(&b->mRl, b->Rl, h->m, count, b->mpad, GEMM_Y_BOX);
     if (!ok) return set_last_error(TVCS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    return TVCS_OK;
+}
+
+// Numbers of persistent blocks the GEMM tuner tries: all SMs, 7/8, 3/4 and 1/2 of them.
+std::vector<int> gemm_grid_candidates(int num_sms)
+{
+    return {num_sms, num_sms * 7 / 8, num_sms * 3 / 4, num_sms / 2};
+}
+
+std::mutex g_gemm_tune_mutex;
+std::map<std::tuple<int, int, int>, std::pair<int, int>> g_gemm_grids;   // (device, m, N) -> grids
+
+// Picks the number of persistent blocks of each GEMM (and with it the stream-K
+// split of its tiles x K-blocks) by timing every candidate, GEMM and fix-up
+// together, over five launches each (median), on the handle's own operands;
+// cached per device and (m, n).  opt.autotune = 0 keeps one block per SM.  A
+// different split regroups the K sums of a tile, so results agree to binary32
+// rounding with the default shape, not bitwise.
+tvcs_status tune_gemms(tvcs_ctx* h, int count)
+{
+    tvcs_batch* b = h->batch;
+    cudaStream_t s = h->stream;
+    int g1 = h->num_sms, g2 = h->num_sms;
+    if (h->opt.autotune) {
+        bool cached = false;
+        {
+            std::lock_guard<std::mutex> lk(g_gemm_tune_mutex);
+            auto it = g_gemm_grids.find({h->dev, h->m, h->N});
+            if (it != g_gemm_grids.end()) {
+                g1 = it->second.first;
+                g2 = it->second.second;
+                cached = true;
+            }
+        }
+        if (!cached) {
+            const long long budget = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : (1LL << 31);
+            for (int which = 0; which < 2; ++which) {
+                const int M = which == 0 ? h->m : h->N, K = which == 0 ? h->N : h->m;
+                float best = -1.f;
+                for (int g : gemm_grid_candidates(h->num_sms)) {
+                    GemmPlan p;
+                    gemm_plan(M, K, g, &p);
+                    int *tsb = nullptr, *ss = nullptr;
+                    BCKS(upload_plan(p, &tsb, &ss, s));
+                    float t[5];
+                    for (int rep = -1; rep < 5; ++rep) {
+                        if (rep >= 0) BCK(cudaEventRecord(h->ev0, s));
+                        if (which == 0) {
+                            launch_gemm(&b->mAh, &b->mAl, &b->mUh, &b->mUl, p, b->ws, b->bctrl, 0,
+                                        budget, s, count);
+                            launch_gemm_fixup(b->ws, tsb, ss, h->m, p.tiles_m, count, b->F, h->m,
+                                              b->R, h->m, b->Rh, b->Rl, b->mpad, b->r2part, b->bctrl,
+                                              0, s);
+                        } else {
+                            launch_gemm(&b->mAth, &b->mAtl, &b->mRh, &b->mRl, p, b->ws, b->bctrl, 0,
+                                        budget, s, count);
+                            launch_gemm_fixup(b->ws, tsb, ss, h->N, p.tiles_m, count, nullptr, 0,
+                                              b->G, h->N, nullptr, nullptr, 0, nullptr, b->bctrl, 0,
+                                              s);
+                        }
+                        if (rep >= 0) {
+                            BCK(cudaEventRecord(h->ev1, s));
+                            BCK(cudaEventSynchronize(h->ev1));
+                            BCK(cudaEventElapsedTime(&t[rep], h->ev0, h->ev1));
+                        }
+                    }
+                    BCKS(sync_check(h, "tuning the batched GEMMs"));
+                    cudaFree(tsb);
+                    cudaFree(ss);
+                    std::sort(t, t + 5);
+                    if (best < 0.f || t[2] < best) {
+                        best = t[2];
+                        (which == 0 ? g1 : g2) = g;
+                    }
+                }
+            }
+            std::lock_guard<std::mutex> lk(g_gemm_tune_mutex);
+            g_gemm_grids[{h->dev, h->m, h->N}] = {g1, g2};
+        }
+    }
+    if (g1 != b->p1.grid || g2 != b->p2.grid) {
+        cudaFree(b->tsb1);
+        cudaFree(b->ss1);
+        cudaFree(b->tsb2);
+        cudaFree(b->ss2);
+        b->tsb1 = b->ss1 = b->tsb2 = b->ss2 = nullptr;
+        gemm_plan(h->m, h->N, g1, &b->p1);
+        gemm_plan(h->N, h->m, g2, &b->p2);
+        BCKS(upload_plan(b->p1, &b->tsb1, &b->ss1, s));
+        BCKS(upload_plan(b->p2, &b->tsb2, &b->ss2, s));
+        BCKS(sync_check(h, "uploading the tuned GEMM plans"));
+    }
     return TVCS_OK;
 }
 
@@ -325,7 +450,14 @@ tvcs_status ensure_batch(tvcs_ctx* h, int count)
         gemm_plan(h->N, h->m, h->num_sms, &b->p2);
         BCKS(upload_plan(b->p1, &b->tsb1, &b->ss1, s));
         BCKS(upload_plan(b->p2, &b->tsb2, &b->ss2, s));
-        const size_t wsf = b->p1.ws_floats > b->p2.ws_floats ? b->p1.ws_floats : b->p2.ws_floats;
+        // the workspace holds the partial tiles of every candidate shape the tuner may pick
+        size_t wsf = 0;
+        for (int g : gemm_grid_candidates(h->num_sms)) {
+            GemmPlan q1, q2;
+            gemm_plan(h->m, h->N, g, &q1);
+            gemm_plan(h->N, h->m, g, &q2);
+            wsf = std::max(wsf, std::max(q1.ws_floats, q2.ws_floats));
+        }
         BCKS(balloc((void**)&b->ws, sizeof(float) * wsf));
         BCKS(balloc((void**)&b->U, sizeof(float) * B * N));
         BCKS(balloc((void**)&b->G, sizeof(float) * B * N));
@@ -348,7 +480,11 @@ tvcs_status ensure_batch(tvcs_ctx* h, int count)
         BCK(cudaMallocHost((void**)&b->hbctrl, sizeof(Ctrl)));
         BCK(cudaMemsetAsync(b->Rh, 0, sizeof(unsigned short) * B * b->mpad, s));
         BCK(cudaMemsetAsync(b->Rl, 0, sizeof(unsigned short) * B * b->mpad, s));
+        BCK(cudaMemsetAsync(b->Uh, 0, sizeof(unsigned short) * B * N, s));
+        BCK(cudaMemsetAsync(b->Ul, 0, sizeof(unsigned short) * B * N, s));
+        BCK(cudaMemsetAsync(b->F, 0, sizeof(float) * B * m, s));
         b->cap = count;
+        b->tuned = false;
     }
     if (b->exec && b->graph_count != count) {   // the loop graph's launch shapes depend on count
         cudaGraphExecDestroy(b->exec);
@@ -357,7 +493,12 @@ tvcs_status ensure_batch(tvcs_ctx* h, int count)
         b->graph = nullptr;
     }
     b->last_count = count;
-    return make_maps(h, count);
+    BCKS(make_maps(h, count));
+    if (!b->tuned) {
+        BCKS(tune_gemms(h, count));
+        b->tuned = true;
+    }
+    return TVCS_OK;
 }
 
 // R = A U - F (R planes, ||r||^2 partials), then G = A^T R, for `count` images.
@@ -454,35 +595,6 @@ tvcs_status build_batch_graph(tvcs_ctx* h, int count)
         return set_last_error(TVCS_ERR_CUDA, "capture of the batched loop: %s", cudaGetErrorString(e));
     BCK(cudaGraphInstantiate(&b->exec, b->graph, 0));
     b->graph_count = count;
-    return TVCS_OK;
-}
-
-// True when p[i] = p[0] + i * len for every i and the whole range lies in one
-// allocation (pageable host memory, or one device / pinned allocation), so that
-// one copy can move all images.
-template <typename T>
-bool contiguous(T* const* p, int count, size_t len)
-{
-    for (int i = 1; i < count; ++i)
-        if (p[i] != p[0] + (size_t)i * len) return false;
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p[0]) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    if (at.type == cudaMemoryTypeUnregistered) return true;
-    CUdeviceptr base = 0;
-    size_t size = 0;
-    const CUdeviceptr a = (CUdeviceptr)(uintptr_t)p[0];
-    if (cuMemGetAddressRange(&base, &size, a) != CUDA_SUCCESS) return false;
-    return a + (CUdeviceptr)(sizeof(T) * len * (size_t)count) <= base + size;
-}
-
-tvcs_status sync_check(tvcs_ctx* h, const char* what)
-{
-    cudaError_t e = cudaStreamSynchronize(h->stream);
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) return set_last_error(TVCS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
     return TVCS_OK;
 }
 

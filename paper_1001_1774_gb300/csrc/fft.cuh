@@ -11,6 +11,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 namespace tvcs {
 
@@ -161,6 +162,17 @@ __device__ __forceinline__ void fft_stage(const float2* __restrict__ src, float2
         dft_small<R, INV>(v);
         float2* d = dst + f * dist;
         const int base = (j / NS) * NS * R + k;
+        if constexpr (NS == 1 && R % 2 == 0) {
+            // the R outputs are contiguous: 16-byte stores (a warp then writes whole
+            // 128-byte lines instead of R-way conflicting 8-byte stores) where the
+            // address is 16-byte aligned
+            if ((reinterpret_cast<uintptr_t>(d + base) & 15u) == 0) {
+                float4* d4 = reinterpret_cast<float4*>(d + base);
+#pragma unroll
+                for (int r = 0; r < R; r += 2) d4[r / 2] = make_float4(v[r].x, v[r].y, v[r + 1].x, v[r + 1].y);
+                continue;
+            }
+        }
 #pragma unroll
         for (int r = 0; r < R; ++r) d[base + r * NS] = v[r];
     }

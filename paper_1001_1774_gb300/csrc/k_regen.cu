@@ -26,9 +26,11 @@
 // element of A is generated once per launch.
 //
 // Many problems (own m, N, seed, x, y) share one launch.  Problem p's rows are
-// cut into chunks of a fixed number of rows (about 2^22 entries, independent
-// of the launch shape); the chunks of the active problems are numbered in
-// problem order (T in all) and cluster q takes chunks [q T / Q, (q+1) T / Q).
+// cut into chunks of a fixed number of rows (about 2^21 entries, and at least
+// 16 chunks when the problem has the rows: fixed by the problem, not by the
+// launch shape); the chunks of the active problems are numbered in problem
+// order, and cluster q of Q takes the chunks that start in the q-th of Q equal
+// shares of the active problems' entries.
 // Every chunk stores its slice of A^T r and its ||r||^2 (added row after row)
 // in a slot of its own; k_regen_reduce adds a problem's slots in chunk order.
 // So every sum has an order fixed by the problem alone: the results do not
@@ -53,11 +55,6 @@ constexpr int RG_NSEG = 16;                  // segments of a row (fixed summati
 constexpr int RG_SEGMAX = 4;                 // segments of a row per block (cluster size >= 4)
 constexpr int RG_QMAX = 1024;                // clusters per launch at most
 
-__host__ __device__ __forceinline__ int range_start(int q, int T, int Q)
-{
-    return (int)(((long long)q * T) / Q);
-}
-
 __host__ __device__ __forceinline__ int tile_rows_for(int W, int tile_cap)
 {
     int rt = RG_RTMAX;
@@ -65,42 +62,79 @@ __host__ __device__ __forceinline__ int tile_rows_for(int W, int tile_cap)
     return rt;
 }
 
-// pre[p] = number of active chunks before problem p, pre[P] = T (all threads).
+// pre[p] = number of active chunks before problem p, pre[P] = T; prew[p] = entries
+// of A of the active problems before p, prew[P] = E (all threads).
 __device__ int active_prefix(const RegenProb* __restrict__ probs, int P, int mode, int* pre,
-                             int* scan)
+                             int* scan, long long* prew, long long* wscan)
 {
     const int tid = threadIdx.x;
     int cnt[4];
+    long long wk[4];
     int local = 0;
+    long long wlocal = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int p = tid * 4 + k;
         int c = 0;
+        long long w = 0;
         if (p < P) {
             c = probs[p].chunks;
             if (mode == MODE_ITER && probs[p].ctrl && probs[p].ctrl->skip) c = 0;
+            if (c > 0) w = (long long)probs[p].m * probs[p].N;
         }
         cnt[k] = c;
+        wk[k] = w;
         local += c;
+        wlocal += w;
     }
     scan[tid] = local;
+    wscan[tid] = wlocal;
     __syncthreads();
     for (int off = 1; off < RG_THREADS; off <<= 1) {
         const int v = tid >= off ? scan[tid - off] : 0;
+        const long long wv = tid >= off ? wscan[tid - off] : 0;
         __syncthreads();
         scan[tid] += v;
+        wscan[tid] += wv;
         __syncthreads();
     }
     int run = scan[tid] - local;
+    long long wrun = wscan[tid] - wlocal;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int p = tid * 4 + k;
-        if (p < P) pre[p] = run;
+        if (p < P) {
+            pre[p] = run;
+            prew[p] = wrun;
+        }
         run += cnt[k];
+        wrun += wk[k];
     }
-    if (tid == RG_THREADS - 1) pre[P] = scan[tid];
+    if (tid == RG_THREADS - 1) {
+        pre[P] = scan[tid];
+        prew[P] = wscan[tid];
+    }
     __syncthreads();
     return pre[P];
+}
+
+// The first active chunk whose first entry lies at or after work offset t (T when
+// t is at or past the end).  Cluster q takes the chunks starting in
+// [q E / Q, (q+1) E / Q): ranges of equal work, whatever the chunk sizes.
+__device__ int chunk_at_work(const RegenProb* __restrict__ probs, int P, const int* pre,
+                             const long long* prew, long long t)
+{
+    if (t >= prew[P]) return pre[P];
+    int lo = 0, hi = P - 1;   // the problem p with prew[p] <= t < prew[p+1]
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prew[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const int p = lo;
+    const long long cw = (long long)probs[p].rows_per_chunk * probs[p].N;
+    const long long k = (t - prew[p] + cw - 1) / cw;
+    return pre[p] + (int)k;
 }
 
 struct TileMeta {
@@ -129,9 +163,12 @@ k_regen_products(const RegenProb* __restrict__ probs, int P, int mode, int wmax,
     extern __shared__ __align__(16) unsigned char smem[];
     int* pre = reinterpret_cast<int*>(smem);                    // pcap + 4 (pcap >= P, multiple of 4)
     int* scan = pre + pcap + 4;                                 // RG_THREADS
-    float* gs = reinterpret_cast<float*>(scan + RG_THREADS);    // A^T r slice, wmax
+    long long* prew = reinterpret_cast<long long*>(scan + RG_THREADS);   // pcap + 4
+    long long* wscan = prew + pcap + 4;                         // RG_THREADS
+    float* gs = reinterpret_cast<float*>(wscan + RG_THREADS);   // A^T r slice, wmax
     float* tile = gs + wmax;                                    // NBUF x tile_cap
-    float* slotv = tile + NBUF * tile_cap;                      // 2 x RTMAX x SEGMAX, read by peers
+    float* wpart = tile + NBUF * tile_cap;                      // 2 x RTMAX x SEGMAX, this block's
+    float* slotv = wpart + 2 * RG_RTMAX * RG_SEGMAX;            // the same, read by the peers
     float* rvec = slotv + 2 * RG_RTMAX * RG_SEGMAX;             // 2 x RTMAX
 
     cg::cluster_group cluster = cg::this_cluster();
@@ -142,11 +179,12 @@ k_regen_products(const RegenProb* __restrict__ probs, int P, int mode, int wmax,
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int segs = RG_NSEG / CS;   // segments of a row this block owns
 
-    const int T = active_prefix(probs, P, mode, pre, scan);
+    active_prefix(probs, P, mode, pre, scan, prew, wscan);
     if (blockIdx.x == 0)
         for (int p = tid; p <= P; p += RG_THREADS) pre_out[p] = pre[p];
-    int j = range_start(cq, T, Q);
-    const int j1 = range_start(cq + 1, T, Q);
+    const long long E = prew[P];
+    int j = chunk_at_work(probs, P, pre, prew, (long long)cq * E / Q);
+    const int j1 = chunk_at_work(probs, P, pre, prew, (long long)(cq + 1) * E / Q);
     if (j >= j1) return;   // the whole cluster has no chunk
 
     for (int i = tid; i < wmax; i += RG_THREADS) gs[i] = 0.f;
@@ -259,7 +297,7 @@ k_regen_products(const RegenProb* __restrict__ probs, int P, int mode, int wmax,
                     if (q < Gs) emit(q, gen_normals4(seed, 0u, b0 + q));
 #pragma unroll
                     for (int off = 16; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
-                    if (lane == 0) slotv[(sb * RG_RTMAX + rr) * RG_SEGMAX + sl] = dot;
+                    if (lane == 0) wpart[(sb * RG_RTMAX + rr) * RG_SEGMAX + sl] = dot;
                 }
             }
             // advance the cursor
@@ -288,6 +326,12 @@ k_regen_products(const RegenProb* __restrict__ probs, int P, int mode, int wmax,
         if (NBUF == 2 && have_prev) finish(prev, sb ^ 1, tb ^ 1);
         if (!have_cur) break;
         __syncthreads();   // segment dots of this tile complete; the other tile buffer is free
+        // Published only now: the peers read slotv[sb] of tile t-2 until they arrive
+        // for tile t-1, which finish(prev) above has waited for.
+        if (tid < cur.nr * segs) {
+            const int rr = tid / segs, sl = tid - rr * segs;
+            slotv[(sb * RG_RTMAX + rr) * RG_SEGMAX + sl] = wpart[(sb * RG_RTMAX + rr) * RG_SEGMAX + sl];
+        }
         cluster_arrive();
         if (NBUF == 1) {
             finish(cur, sb, 0);
@@ -343,7 +387,8 @@ k_regen_reduce(const RegenProb* __restrict__ probs, int P, const int* __restrict
 static size_t regen_smem(int wmax, int tile_cap, int nbuf, int pcap)
 {
     return sizeof(int) * ((size_t)pcap + 4 + RG_THREADS) +
-           sizeof(float) * ((size_t)wmax + (size_t)nbuf * tile_cap + 2 * RG_RTMAX * RG_SEGMAX +
+           sizeof(long long) * ((size_t)pcap + 4 + RG_THREADS) +
+           sizeof(float) * ((size_t)wmax + (size_t)nbuf * tile_cap + 4 * RG_RTMAX * RG_SEGMAX +
                             2 * RG_RTMAX);
 }
 

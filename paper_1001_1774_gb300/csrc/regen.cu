@@ -113,16 +113,19 @@ tvcs_status ralloc(void** p, size_t bytes)
     return TVCS_OK;
 }
 
-// Rows per chunk: about 2^22 entries of A, fixed by the problem's row length
-// alone, so that the chunk slots (and with them the order of every sum of A^T r
-// and ||r||^2) do not depend on the launch shape.
-constexpr double kChunkEntries = 4194304.0;
+// Rows per chunk: about 2^21 entries of A, and at most m/16 rows so that a small
+// problem still spreads over 16 clusters; fixed by the problem alone, so that
+// the chunk slots (and with them the order of every sum of A^T r and ||r||^2)
+// do not depend on the launch shape.  The kernel balances the clusters by
+// entries, so chunks of different problems may differ in size.
+constexpr long long kChunkEntries = 1LL << 21;
 
 void chunking(int m, int N, int* rpc, int* chunks)
 {
-    long long rows = (long long)ceil(kChunkEntries / N);
+    long long rows = (kChunkEntries + N - 1) / N;
+    const long long cap = (m + 15) / 16;
+    if (rows > cap) rows = cap;
     if (rows < 1) rows = 1;
-    if (rows > m) rows = m;
     *rpc = (int)rows;
     *chunks = (int)((m + rows - 1) / rows);
 }
@@ -185,10 +188,15 @@ void apply_layout(const Layout& L, float* gslot, float2* r2slot, std::vector<Reg
 // and returns the fastest.  The chunk layout is the same for every plan (and so
 // are the results); gslot / r2slot hold it.
 tvcs_status autotune(std::vector<RegenProb> probs, int maxN, RegenProb* dtab, float* gslot,
-                     float2* r2slot, int* pre, cudaStream_t s, RegenPlan* best)
+                     float2* r2slot, int* pre, cudaStream_t s, RegenPlan* best, bool timed = true)
 {
     std::vector<RegenPlan> cands = candidates(maxN, (int)probs.size());
     if (cands.empty()) return set_last_error(TVCS_ERR_UNSUPPORTED, "no cluster of the regenerating product kernel fits");
+    if (!timed) {   // the first candidate, untimed
+        *best = cands[0];
+        regen_configure(best);
+        return TVCS_OK;
+    }
     cudaEvent_t e0, e1;
     RCK(cudaEventCreate(&e0));
     RCK(cudaEventCreate(&e1));
@@ -308,7 +316,7 @@ tvcs_status regen_init(tvcs_ctx* h)
     RCKS(ralloc((void**)&g->dtab, sizeof(RegenProb) * kTab));
     RegenPlan plan;
     bool cached = false;
-    {
+    if (h->opt.autotune) {
         std::lock_guard<std::mutex> lk(g_plan_mutex);
         auto it = g_plans.find({h->dev, h->N, h->m});
         if (it != g_plans.end()) {
@@ -320,9 +328,12 @@ tvcs_status regen_init(tvcs_ctx* h)
         regen_configure(&plan);
     } else {
         launch_fill(h->tx, h->N, (float)(1.0 / sqrt((double)h->N)), h->stream);
-        RCKS(autotune(one, h->N, g->dtab, g->gslot, g->r2slot, g->pre, h->stream, &plan));
-        std::lock_guard<std::mutex> lk(g_plan_mutex);
-        g_plans[{h->dev, h->N, h->m}] = plan;
+        RCKS(autotune(one, h->N, g->dtab, g->gslot, g->r2slot, g->pre, h->stream, &plan,
+                      h->opt.autotune != 0));
+        if (h->opt.autotune) {
+            std::lock_guard<std::mutex> lk(g_plan_mutex);
+            g_plans[{h->dev, h->N, h->m}] = plan;
+        }
     }
     g->plan = plan;
     apply_layout(L0, g->gslot, g->r2slot, &one);
@@ -523,7 +534,8 @@ tvcs_status build_uneven(const tvcs_handle* hs, int count, const double* mu, tvc
     const Layout L = layout_for(probs);
     RCKS(ralloc((void**)&u->gslot, sizeof(float) * L.gfloats));
     RCKS(ralloc((void**)&u->r2slot, sizeof(float2) * L.rslots));
-    RCKS(autotune(probs, u->maxN, u->dtab, u->gslot, u->r2slot, u->pre, s, &u->plan));
+    RCKS(autotune(probs, u->maxN, u->dtab, u->gslot, u->r2slot, u->pre, s, &u->plan,
+                  h0->opt.autotune != 0));
     apply_layout(L, u->gslot, u->r2slot, &probs);
     RCK(cudaMemcpy(u->dtab, probs.data(), sizeof(RegenProb) * count, cudaMemcpyHostToDevice));
     for (RegenProb& p : probs) p.x = u->zero;   // start point: A^T (0 - f)

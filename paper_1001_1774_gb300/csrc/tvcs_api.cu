@@ -615,6 +615,7 @@ void tvcs_default_options(tvcs_options* opt)
     opt->host_loop = 0;
     opt->a_mode = TVCS_A_STORED;
     opt->batch_compact = 1;
+    opt->autotune = 1;
 }
 
 const char* tvcs_last_error(void)

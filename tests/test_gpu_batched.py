@@ -301,3 +301,37 @@ def test_batched_more_than_256_images_run_in_groups(tv):
     tv.tvcs_apply_batched(h, 130, np.ascontiguousarray(X[130:]), np.ascontiguousarray(F[130:260]), R1, G1)
     assert np.array_equal(R[130:], R1) and np.array_equal(G[130:], G1)
     tv.tvcs_destroy(h)
+
+
+def test_gemm_autotune_agrees_with_the_default_shape(tv):
+    # The tuner picks each GEMM's number of persistent blocks by timing; a different
+    # stream-K split regroups the K sums of a tile, so the products agree with the
+    # default shape (one block per SM) to binary32 rounding of the sums, 1e-6 of the
+    # absolute sums, and solves to 1e-6.
+    n, m, count = 64, 1229, 48
+    N = n * n
+    A = synth.gaussian_matrix(77, m, N)
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((count, N)).astype(np.float32)
+    Y = rng.standard_normal((count, m)).astype(np.float32)
+    out = {}
+    for tune in (1, 0):
+        opt = tv.tvcs_default_options()
+        opt.precision = tv.TVCS_PREC_BF16X2
+        opt.tau = 0.1
+        opt.max_iter = 20
+        opt.autotune = tune
+        h = tv.tvcs_create(torch.from_numpy(A).cuda(), 0, m, n, 1e3, 10.0, 0.0, opt)
+        R = np.empty((count, m), np.float32)
+        G = np.empty((count, N), np.float32)
+        tv.tvcs_apply_batched(h, count, X, Y, R, G)
+        us = [np.empty(N, np.float32) for _ in range(count)]
+        tv.tvcs_solve_batched([h] * count, [np.ascontiguousarray(Y[b]) for b in range(count)], us)
+        out[tune] = (R, G, us)
+        tv.tvcs_destroy(h)
+    (R1, G1, u1), (R0, G0, u0) = out[1], out[0]
+    A64 = np.abs(A.astype(np.float64))
+    assert np.all(np.abs(R1.astype(np.float64) - R0) <= 1e-6 * (np.abs(X.astype(np.float64)) @ A64.T) + 1e-30)
+    assert np.all(np.abs(G1.astype(np.float64) - G0) <= 1e-6 * (np.abs(R0.astype(np.float64)) @ A64) + 1e-30)
+    for b in range(count):
+        assert rel(u1[b], u0[b]) <= 1e-6, b

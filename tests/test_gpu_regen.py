@@ -341,3 +341,30 @@ def test_uneven_results_do_not_depend_on_the_batch_or_the_tuned_plan(tv):
         assert rel(u_all[k], ref.u) <= 1e-5
     for h in hs + hx:
         tv.tvcs_destroy(h)
+
+
+def test_regen_autotune_off_gives_the_same_results(tv):
+    # With autotune off the first candidate shape runs untimed; the regenerating
+    # products add in a fixed order, so single solves and an uneven batch give
+    # bit-identical results either way.
+    probs = uneven_problems(SHAPES[:4], first_seed=171)
+    res = {}
+    for tune in (1, 0):
+        hs = []
+        for P in probs:
+            opt = tv.tvcs_default_options()
+            opt.tau = 0.1
+            opt.max_iter = 15
+            opt.a_mode = tv.TVCS_A_REGENERATE
+            opt.autotune = tune
+            hs.append(tv.tvcs_create(None, P.seed, P.m, P.n, P.mu, P.beta, 0.0, opt))
+        us = [np.empty(P.N, np.float32) for P in probs]
+        tv.tvcs_solve_batched(hs, [P.f for P in probs], us)
+        u0 = np.empty(probs[0].N, np.float32)
+        tv.tvcs_solve(hs[0], probs[0].f, u0)
+        res[tune] = (us, u0)
+        for h in hs:
+            tv.tvcs_destroy(h)
+    for a, b in zip(res[1][0], res[0][0]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(res[1][1], res[0][1])
