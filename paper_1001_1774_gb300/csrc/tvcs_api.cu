@@ -232,6 +232,11 @@ tvcs_status alloc(void** p, size_t bytes)
 // products; the products kernel sets the WHILE condition from ctrl->done.
 constexpr int ITERS_PER_BODY = 16;
 
+tvcs_status build_tail(tvcs_ctx* h, int iters);
+
+// The WHILE graph and the graphs of 1 .. 15 iterations that end runs whose
+// length is not a multiple of the body, all built (and uploaded to the device)
+// at once, so that no later call pays for a capture or a first-launch upload.
 tvcs_status build_graph(tvcs_ctx* h)
 {
     if (h->exec) return TVCS_OK;
@@ -257,6 +262,8 @@ tvcs_status build_graph(tvcs_ctx* h)
     cudaError_t e = cudaStreamEndCapture(h->cap_stream, &captured);
     if (e != cudaSuccess) return fail(TVCS_ERR_CUDA, "capture of the loop body: %s", cudaGetErrorString(e));
     CK(cudaGraphInstantiate(&h->exec, h->graph, 0));
+    CK(cudaGraphUpload(h->exec, h->stream));
+    for (int r = 1; r < ITERS_PER_BODY; ++r) CKS(build_tail(h, r));
     return TVCS_OK;
 }
 
@@ -278,6 +285,7 @@ tvcs_status build_tail(tvcs_ctx* h, int iters)
         return fail(TVCS_ERR_CUDA, "instantiating the run's last iterations: %s",
                     cudaGetErrorString(e));
     }
+    CK(cudaGraphUpload(h->tail[iters], h->stream));
     return TVCS_OK;
 }
 
@@ -325,10 +333,7 @@ tvcs_status run_loop(tvcs_ctx* h, int iters, double tol, tvcs_result* res)
 {
     // whole loop bodies in the WHILE graph, the remainder in a graph of its own
     const int nbody = iters / ITERS_PER_BODY, rest = iters % ITERS_PER_BODY;
-    if (!h->opt.host_loop) {
-        if (nbody > 0) CKS(build_graph(h));
-        if (rest > 0) CKS(build_tail(h, rest));
-    }
+    if (!h->opt.host_loop) CKS(build_graph(h));
     Ctrl& c = *h->hctrl;
     // loops_max: bodies of the WHILE graph (each ends by checking this bound)
     launch_run_begin(h->ctrl, iters, nbody, tol, h->opt.algo, h->stream);
