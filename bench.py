@@ -60,6 +60,8 @@ def parse_args():
                          "batch256tol: the batch256 images, each to its own tol 1e-4 (compaction); "
                          "products: the product kernel alone for --n, --m, --precision (A generated "
                          "on the device), --steps back-to-back launches (for profiler captures)")
+    ap.add_argument("--images", type=int, default=256,
+                    help="images of --workload batch256 (more than 256 run in groups of at most 256)")
     ap.add_argument("--n", type=int, default=256, help="image side of --workload products")
     ap.add_argument("--m", type=int, default=13107, help="measurements of --workload products")
     ap.add_argument("--algo", choices=["iadm", "ftvcs"], default="iadm",
@@ -496,14 +498,14 @@ def n256_segment(tv, precision, steps, stream):
                          "peak_source": peak_src}}
 
 
-def batch_segment(tv, steps, warmup, stream, want_parity=True):
-    """256 images of 128 x 128 sharing one 4915 x 16384 A (bf16 hi/lo): `steps`
-    batched iterations; the GEMM pair's time against the bf16 peak; image 0
-    against the FP64 oracle after the same iterations."""
+def batch_segment(tv, steps, warmup, stream, want_parity=True, images=256):
+    """`images` (256 by default) images of 128 x 128 sharing one 4915 x 16384 A (bf16
+    hi/lo): `steps` batched iterations; the GEMM pair's time against the bf16 peak;
+    image 0 against the FP64 oracle after the same iterations."""
     import numpy as np
     import torch
     import synth
-    B = 256
+    B = images
     A, ubars, F, mus, _ = synth.workload_shared_batch(count=B, n=128, ratio=0.3, seed=1)
     m, N = A.shape
     opt = tv.tvcs_default_options()
@@ -556,11 +558,15 @@ def batch_segment(tv, steps, warmup, stream, want_parity=True):
     tv.tvcs_solve_batched([h] * B, [F_host[b] for b in range(B)], [U_host[b] for b in range(B)], mus)
     e2e_s = time.perf_counter() - t0
     tv.tvcs_destroy(h)
-    flops = 2 * 3 * 2.0 * m * N * B                  # two GEMMs, three bf16 terms each
+    # more than 256 images run in groups of nearly equal size, the smaller ones last:
+    # the stage timings above are of the last group
+    groups = -(-B // 256)
+    last = B // groups
+    flops = 2 * 3 * 2.0 * m * N * last               # two GEMMs, three bf16 terms each
     peak = bf16_peak()
     tf = flops / (gemm_us * 1e-6) / 1e12
     value = B * steps / (ms / 1e3)
-    out = {"workload": "batch256_n128_m4915_bf16x2_shared_A", "value": value,
+    out = {"workload": "batch%d_n128_m4915_bf16x2_shared_A" % B, "value": value,
            "unit": "image-iter/s", "steps": steps, "recons_per_s": value / ITERS_PER_RECON,
            "ms_per_step": ms / steps,
            "roofline": {"bound": "tensor", "achieved": tf, "peak": peak[0], "unit": "TFLOP/s",
@@ -571,8 +577,8 @@ def batch_segment(tv, steps, warmup, stream, want_parity=True):
                         "loop_per_iteration": loop_ms * 1e3 / steps},
            "e2e": {"value": B * steps / e2e_s, "unit": "image-iter/s",
                    "h2d_bytes_per_step": 4 * m * B / steps, "d2h_bytes_per_step": 4 * N * B / steps},
-           "gpu_launches": 6 * batch_launch_iters(steps) + 8, "clocks": clocks, "tau": tau,
-           "_A": A, "_F": F, "_mus": mus}
+           "gpu_launches": groups * (6 * batch_launch_iters(steps) + 8), "clocks": clocks, "tau": tau,
+           "groups": groups, "_A": A, "_F": F, "_mus": mus}
     if want_parity:
         import oracle
         ref = oracle.solve(A, F[0], 128, mus[0], 10.0, tau, max_iter=steps)
@@ -596,7 +602,8 @@ def run_batched(args):
     import paper_1001_1774_gb300 as tv
     stream = torch.cuda.Stream()
     b = batch_segment(tv, args.steps, args.warmup, stream,
-                      want_parity=not args.no_cpu_baseline and args.steps <= ITERS_PER_RECON)
+                      want_parity=not args.no_cpu_baseline and args.steps <= ITERS_PER_RECON,
+                      images=args.images)
     A, F, mus = b.pop("_A"), b.pop("_F"), b.pop("_mus")
     m, N = A.shape
     out = {"metric": METRIC, "value": b["value"], "unit": "image-iter/s", "n_gpus": 1,
@@ -604,7 +611,7 @@ def run_batched(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3->f32",
            "data": "synthetic (seeded phantoms, Philox Gaussian A)",
            "recons_per_s": b["recons_per_s"],
-           "config": {"workload": b["workload"], "images": 256, "n": 128,
+           "config": {"workload": b["workload"], "images": args.images, "n": 128,
                       "m": m, "mu": "cycling 2e2, 5e2, 1e3, 2e3", "iters_per_recon": ITERS_PER_RECON,
                       "l2": "inputs larger than L2 (A and A^T bf16 hi/lo = 644 MB); no flush"}}
     for k in ("roofline", "stage_us", "e2e", "gpu_launches", "clocks", "tau", "parity_vs_oracle"):

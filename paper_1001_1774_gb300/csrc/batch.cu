@@ -261,10 +261,25 @@ bool contiguous(T* const* p, int count, size_t len)
         return false;
     }
     if (at.type == cudaMemoryTypeUnregistered) return true;
+    // the driver's address-range query, looked up at run time (the library links no
+    // driver symbol, so that it loads where no driver is installed)
+    typedef CUresult (*RangeFn)(CUdeviceptr*, size_t*, CUdeviceptr);
+    static RangeFn range_fn = nullptr;
+    if (!range_fn) {
+        void* fp = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &fp, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fp) {
+            cudaGetLastError();
+            return false;
+        }
+        range_fn = reinterpret_cast<RangeFn>(fp);
+    }
     CUdeviceptr base = 0;
     size_t size = 0;
     const CUdeviceptr a = (CUdeviceptr)(uintptr_t)p[0];
-    if (cuMemGetAddressRange(&base, &size, a) != CUDA_SUCCESS) return false;
+    if (range_fn(&base, &size, a) != CUDA_SUCCESS) return false;
     return a + (CUdeviceptr)(sizeof(T) * len * (size_t)count) <= base + size;
 }
 

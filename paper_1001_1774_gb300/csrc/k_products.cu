@@ -33,6 +33,9 @@ constexpr int PROD_NST = 3;
 constexpr size_t PROD_PF_BYTES = 1024 * 1024;
 // Bulk copies per stage of the ring.
 constexpr int PROD_TMA_PIECES = 1;
+// Stages ahead of each refill that are also prefetched into L2 while streaming
+// (0: only the pre-wait prefetch).
+constexpr int PROD_PF_STREAM = 0;
 
 template <int V, int RL, int RS>
 struct ProdShape {
@@ -219,6 +222,10 @@ __global__ void __maxnreg__(128)
             if (ok) {
                 issue(s + PROD_NST);
                 ++issued;
+                // while streaming, prefetch into L2 the stage PROD_PF_STREAM stages past
+                // the one just issued
+                if (PROD_PF_STREAM > 0 && s + PROD_NST + PROD_PF_STREAM < nst)
+                    prefetch(s + PROD_NST + PROD_PF_STREAM);
             }
         }
     }
