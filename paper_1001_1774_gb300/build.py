@@ -20,7 +20,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtvcs.so")
 SOURCES = ["tvcs_api.cu", "k_usolve.cu", "k_tv.cu", "k_products.cu", "k_products_q.cu",
            "k_gemm.cu", "batch.cu", "k_gen.cu", "noalloc.cu", "k_regen.cu", "regen.cu",
-           "k_usolve_img.cu", "k_dct.cu"]
+           "k_usolve_img.cu", "k_usolve_reg.cu", "k_dct.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

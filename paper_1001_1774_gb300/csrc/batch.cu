@@ -432,6 +432,7 @@ tvcs_status ensure_batch(tvcs_ctx* h, int count)
         // Many images in flight: one block per image where n allows it, else
         // 8-block clusters (they pack the SMs more densely than 16).
         b->uimg = usolve_img_configure(h->n);
+        b->ureg = h->n == 128 && usolve_reg_configure();
         b->ucluster = usolve_cluster_fits(h->n, 8) ? 8 : h->ucluster;
         usolve_cluster_fits(h->n, b->ucluster);   // kernel attributes of the chosen size
     }
@@ -567,7 +568,9 @@ TvArgs batch_tv_args(tvcs_ctx* h, int count, int mode, bool compact = false)
 
 void batch_usolve(tvcs_ctx* h, const TvArgs& a, cudaStream_t s)
 {
-    if (h->batch->uimg)
+    if (h->batch->ureg)
+        launch_usolve_reg128(a, s);
+    else if (h->batch->uimg)
         launch_usolve_img(h->n, a, s);
     else
         launch_usolve(h->n, h->batch->ucluster, a, s);

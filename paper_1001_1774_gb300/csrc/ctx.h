@@ -35,6 +35,7 @@ struct tvcs_batch {
     int last_count = 0;            // images of the last batched call
     int ucluster = 0;              // cluster size of the batched u-solve
     bool uimg = false;             // the u-solve runs one block per image (k_usolve_img)
+    bool ureg = false;             // n = 128: one block per image, transforms in registers (k_usolve_reg.cu)
     bool tuned = false;            // the GEMM launch shapes have been picked for these buffers
 };
 

@@ -1,0 +1,413 @@
+// Rows a1-a5 of one IADM/FTVCS iteration for many 128 x 128 images at once, one
+// block per image, with every 128-point transform held in the registers of one
+// warp (Xiao & Yang, Sec. 2.1-2.2: the w-step of eq. (iadmw) with reading C1 and
+// the shrink of eq. (shrink), the right-hand side of eq. (eqnorm11) times beta
+// in increment form, the FFT solve with the eigenvalues of D^T D, the stop
+// norms of eq. (stop)).  The same arithmetic as usolve_steps.cuh, laid out so
+// that no phase needs a block barrier: a warp owns whole rows (phases A and C)
+// or whole columns (phase B) of the image.
+//
+// 128-point DFT in one warp.  Lane l holds x[l + 32 j], j = 0..3.  With
+// c = l + 32 j and k = k1 + 4 k2 (k1 = 0..3, k2 = 0..31),
+//     X[k1 + 4 k2] = sum_l W32^(l k2) * [ W128^(l k1) * sum_j x[l + 32 j] W4^(j k1) ],
+// so a radix-4 DFT in registers, a twiddle, and for each k1 a 32-point DFT
+// across the lanes (five radix-2 butterfly stages through shuffles, decimation
+// in frequency: lane l ends with k2 = bitrev5(l)).  The inverse runs the mirror
+// image (decimation in time from that order, twiddle, inverse radix-4), so a
+// forward transform followed by its inverse needs no reordering.
+//
+// Phases (8 warps):
+//   A  per pair of rows (r0, r0+1): the multiplier update and shrink of rows
+//      r0-1 .. r0+1 from u, w, lambda in global memory (L2), the right-hand
+//      side of the pair packed into one complex row, its forward transform, and
+//      the split into the two rows' half spectra, stored column-major in shared
+//      memory (the spectrum of the image never leaves the SM);
+//   B  per column q = 0..64: forward transform, divide by beta Lambda_pq + mu/tau,
+//      inverse transform, in registers;
+//   C  per pair of rows: the packed inverse row transform (through the same
+//      forward code on the conjugate), u += d, bf16 planes, double-single norms;
+// then the block's sums and eq. (stop).  Shared memory: the half spectrum
+// (65 columns of 129 complex values) and one 128-value exchange row per warp:
+// 75 KB, three images per SM.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "usolve_steps.cuh"
+
+namespace tvcs {
+
+namespace {
+
+constexpr int RG_NN = 128;
+constexpr int RG_N = RG_NN * RG_NN;
+constexpr int RG_Q = RG_NN / 2 + 1;      // columns of the half spectrum
+constexpr int RG_QS = RG_NN + 1;         // column stride (complex)
+constexpr int RG_WARPS = 8;
+constexpr int RG_T = RG_WARPS * 32;
+constexpr int RG_XS = RG_NN + RG_NN / 16;   // exchange row of a warp, one pad per 16 values
+constexpr size_t RG_SMEM = ((size_t)RG_Q * RG_QS * 8 + 15) / 16 * 16 + (size_t)RG_WARPS * RG_XS * 8 + 64 * 8;
+
+__device__ __forceinline__ int bitrev5(int l) { return (int)(__brev((unsigned)l) >> 27); }
+
+// padded position of value c in a warp's exchange row (conflict-free for the
+// natural and the bit-reversed orders used here)
+__device__ __forceinline__ int xpos(int c) { return c + (c >> 4); }
+
+__device__ __forceinline__ float2 shfl_xor2(float2 v, int m)
+{
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+
+// Per-lane twiddles: the in-lane W128^(l k1) (k1 = 1..3) and, for each lane
+// stage s (half h = 16 >> s), W_{2h}^(l mod h) on the lanes that take the
+// difference (l & h).  Forward values (exp(-2 pi i t / n)); the inverse uses
+// their conjugates.
+struct LaneTw {
+    float2 w1[3];
+    float2 ws[5];
+};
+
+__device__ __forceinline__ LaneTw lane_twiddles(const float2* __restrict__ tw128, int l)
+{
+    LaneTw t;
+#pragma unroll
+    for (int k1 = 1; k1 < 4; ++k1) {
+        const float2 c = tw128[(l * k1) & (RG_NN - 1)];   // (cos, sin)(2 pi t / 128)
+        t.w1[k1 - 1] = make_float2(c.x, -c.y);
+    }
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int h = 16 >> s;
+        const int e = (l & (h - 1)) * (16 / h);            // exponent of W32
+        const float2 c = tw128[(4 * e) & (RG_NN - 1)];
+        t.ws[s] = make_float2(c.x, -c.y);
+    }
+    return t;
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b)   // a * conj(b)
+{
+    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+
+// Forward: v[j] = x[l + 32 j] in, v[k1] = X[k1 + 4 bitrev5(l)] out.
+__device__ __forceinline__ void fft128_fwd(float2 v[4], const LaneTw& t, int l)
+{
+    {   // radix 4 over j, W4 = -i
+        const float2 s02 = make_float2(v[0].x + v[2].x, v[0].y + v[2].y);
+        const float2 d02 = make_float2(v[0].x - v[2].x, v[0].y - v[2].y);
+        const float2 s13 = make_float2(v[1].x + v[3].x, v[1].y + v[3].y);
+        const float2 d13 = make_float2(v[1].y - v[3].y, v[3].x - v[1].x);   // -i (v1 - v3)
+        v[0] = make_float2(s02.x + s13.x, s02.y + s13.y);
+        v[2] = make_float2(s02.x - s13.x, s02.y - s13.y);
+        v[1] = make_float2(d02.x + d13.x, d02.y + d13.y);
+        v[3] = make_float2(d02.x - d13.x, d02.y - d13.y);
+    }
+#pragma unroll
+    for (int k1 = 1; k1 < 4; ++k1) v[k1] = cmulf(v[k1], t.w1[k1 - 1]);
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {   // decimation in frequency across the lanes
+        const int h = 16 >> s;
+        const bool lower = (l & h) != 0;
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            const float2 p = shfl_xor2(v[k1], h);
+            if (!lower) {
+                v[k1] = make_float2(v[k1].x + p.x, v[k1].y + p.y);
+            } else {
+                v[k1] = cmulf(make_float2(p.x - v[k1].x, p.y - v[k1].y), t.ws[s]);
+            }
+        }
+    }
+}
+
+// Inverse (unnormalised): v[k1] = X[k1 + 4 bitrev5(l)] in, v[j] = x[l + 32 j] out.
+__device__ __forceinline__ void fft128_inv(float2 v[4], const LaneTw& t, int l)
+{
+#pragma unroll
+    for (int s = 4; s >= 0; --s) {   // decimation in time across the lanes
+        const int h = 16 >> s;
+        const bool lower = (l & h) != 0;
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            const float2 own = lower ? cmulc(v[k1], t.ws[s]) : v[k1];
+            const float2 p = shfl_xor2(own, h);
+            v[k1] = lower ? make_float2(p.x - own.x, p.y - own.y)
+                          : make_float2(own.x + p.x, own.y + p.y);
+        }
+    }
+#pragma unroll
+    for (int k1 = 1; k1 < 4; ++k1) v[k1] = cmulc(v[k1], t.w1[k1 - 1]);
+    {   // inverse radix 4, W4^-1 = +i
+        const float2 s02 = make_float2(v[0].x + v[2].x, v[0].y + v[2].y);
+        const float2 d02 = make_float2(v[0].x - v[2].x, v[0].y - v[2].y);
+        const float2 s13 = make_float2(v[1].x + v[3].x, v[1].y + v[3].y);
+        const float2 d13 = make_float2(v[3].y - v[1].y, v[1].x - v[3].x);   // +i (v1 - v3)
+        v[0] = make_float2(s02.x + s13.x, s02.y + s13.y);
+        v[2] = make_float2(s02.x - s13.x, s02.y - s13.y);
+        v[1] = make_float2(d02.x + d13.x, d02.y + d13.y);
+        v[3] = make_float2(d02.x - d13.x, d02.y - d13.y);
+    }
+}
+
+// The value of lane l-1 (lane 0: lane 31's value of the previous j; column c-1).
+__device__ __forceinline__ void shift_left_cols(const float v[4], float out[4], int l)
+{
+    float s[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s[j] = __shfl_sync(0xffffffffu, v[j], (l + 31) & 31);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out[j] = (l == 0) ? s[(j + 3) & 3] : s[j];
+}
+
+// The value of lane l+1 (lane 31: lane 0's value of the next j; column c+1).
+__device__ __forceinline__ void shift_right_cols(const float v[4], float out[4], int l)
+{
+    float s[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s[j] = __shfl_sync(0xffffffffu, v[j], (l + 1) & 31);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out[j] = (l == 31) ? s[(j + 1) & 3] : s[j];
+}
+
+}  // namespace
+
+// Image b = blockIdx.x, with the conventions of k_usolve_img (per-image mu and
+// tau, control block, bf16 planes at row img_slot[b]).
+__global__ void __launch_bounds__(RG_T, 3) k_usolve_reg128(
+    float* __restrict__ u, float* __restrict__ wbuf, float* __restrict__ lbuf,
+    const float* __restrict__ g, const float2* __restrict__ tw_g, const float* __restrict__ s2_g,
+    float beta, float mu_over_tau, float mu, Ctrl* __restrict__ ctrl, int mode,
+    const float* __restrict__ mu_img, const float* __restrict__ tau_img, float tau,
+    unsigned short* __restrict__ u_hi, unsigned short* __restrict__ u_lo,
+    const int* __restrict__ img_slot)
+{
+    constexpr int NN = RG_NN, N = RG_N;
+    {
+        const int b = blockIdx.x;
+        u += (size_t)b * N;
+        wbuf += (size_t)b * 4 * N;
+        lbuf += (size_t)b * 4 * N;
+        g += (size_t)b * N;
+        ctrl += b;
+        if (u_hi) {
+            const int row = img_slot ? img_slot[b] : b;
+            if (row >= 0) {
+                u_hi += (size_t)row * N;
+                u_lo += (size_t)row * N;
+            } else {
+                u_hi = u_lo = nullptr;
+            }
+        }
+        if (mu_img) {
+            mu = mu_img[b];
+            mu_over_tau = mu / (tau_img ? tau_img[b] : tau);
+        }
+    }
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* spec = reinterpret_cast<float2*>(smem);                     // spec[q QS + p]
+    float2* xrow_all = reinterpret_cast<float2*>(smem + ((size_t)RG_Q * RG_QS * 8 + 15) / 16 * 16);
+    float2* red = xrow_all + RG_WARPS * RG_XS;                          // [64]
+    const int tid = threadIdx.x, l = tid & 31, warp = tid >> 5;
+    float2* xrow = xrow_all + warp * RG_XS;
+
+    if (mode == MODE_ITER) {
+        const int done = ctrl->done;   // stable during this kernel
+        if (tid == 0) ctrl->skip = done;
+        if (done) return;              // uniform across the block
+    }
+    const int pending = ctrl->pending;
+    const int par = ctrl->wpar;
+    const float* wsrc = wbuf + (size_t)par * 2 * N;
+    const float* lsrc = lbuf + (size_t)par * 2 * N;
+    float* wdst = wbuf + (size_t)(par ^ 1) * 2 * N;
+    float* ldst = lbuf + (size_t)(par ^ 1) * 2 * N;
+    const LaneTw tw = lane_twiddles(tw_g, l);
+    const float inv_beta = 1.0f / beta;
+
+    // ---------------- phase A: pairs of rows ----------------
+    for (int pr = warp; pr < NN / 2; pr += RG_WARPS) {
+        const int r0 = 2 * pr;
+        float uu[4][4];   // u rows r0-1 .. r0+2 at columns l + 32 j
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int row = (r0 - 1 + t + NN) & (NN - 1);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) uu[t][j] = u[row * NN + l + 32 * j];
+        }
+        float y1[2][4], y2[3][4];   // y1 of rows r0, r0+1; y2 of rows r0-1 .. r0+1
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {   // rows r0-1+t: multiplier update, shrink, y
+            const int row = (r0 - 1 + t + NN) & (NN - 1);
+            float up[4];
+            shift_right_cols(uu[t], up, l);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int gi = row * NN + l + 32 * j;
+                const float uc = uu[t][j];
+                const float d1 = up[j] - uc;
+                const float d2 = uu[t + 1][j] - uc;
+                float l1 = lsrc[gi], l2 = lsrc[N + gi];
+                if (pending) {   // eq. (udlamb) for the previous iteration
+                    l1 -= beta * (wsrc[gi] - d1);
+                    l2 -= beta * (wsrc[N + gi] - d2);
+                }
+                const float z1 = d1 + l1 * inv_beta, z2 = d2 + l2 * inv_beta;
+                const float nz = sqrtf(z1 * z1 + z2 * z2);
+                float w1 = 0.0f, w2 = 0.0f;
+                if (nz > inv_beta) {
+                    const float sc = (nz - inv_beta) / nz;
+                    w1 = sc * z1;
+                    w2 = sc * z2;
+                }
+                y2[t][j] = beta * (w2 - d2) - l2;
+                if (t >= 1) {
+                    y1[t - 1][j] = beta * (w1 - d1) - l1;
+                    wdst[gi] = w1;
+                    wdst[N + gi] = w2;
+                    ldst[gi] = l1;
+                    ldst[N + gi] = l2;
+                }
+            }
+        }
+        // right-hand side of rows r0, r0+1 packed: z = rhs[r0] + i rhs[r0+1]
+        float2 v[4];
+        float ym[2][4];
+        shift_left_cols(y1[0], ym[0], l);
+        shift_left_cols(y1[1], ym[1], l);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float rr[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float dty = ym[h][j] - y1[h][j] + y2[h][j] - y2[h + 1][j];
+                rr[h] = dty - mu * g[(r0 + h) * NN + l + 32 * j];
+            }
+            v[j] = make_float2(rr[0], rr[1]);
+        }
+        fft128_fwd(v, tw, l);
+        // exchange row: Z[k] at its padded position, then the split of the pair
+        const int br = bitrev5(l);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) xrow[xpos(k1 + 4 * br)] = v[k1];
+        __syncwarp();
+        for (int q = l; q < RG_Q; q += 32) {
+            const float2 a = xrow[xpos(q)];
+            const float2 bb = xrow[xpos((NN - q) & (NN - 1))];
+            spec[q * RG_QS + r0] = make_float2(0.5f * (a.x + bb.x), 0.5f * (a.y - bb.y));
+            spec[q * RG_QS + r0 + 1] = make_float2(0.5f * (a.y + bb.y), -0.5f * (a.x - bb.x));
+        }
+        __syncwarp();   // the exchange row is free for the next pair
+    }
+    __syncthreads();
+
+    // ---------------- phase B: columns ----------------
+    float s2p[4];   // s2 of the rows p = k1 + 4 bitrev5(l) this lane holds after a forward transform
+    {
+        const int br = bitrev5(l);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) s2p[k1] = s2_g[k1 + 4 * br];
+    }
+    for (int q = warp; q < RG_Q; q += RG_WARPS) {
+        float2* col = spec + q * RG_QS;
+        float2 v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = col[l + 32 * j];
+        fft128_fwd(v, tw, l);
+        const float s2q = s2_g[q];
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            const float rd = 1.0f / (beta * (s2p[k1] + s2q) + mu_over_tau);
+            v[k1].x *= rd;
+            v[k1].y *= rd;
+        }
+        fft128_inv(v, tw, l);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) col[l + 32 * j] = v[j];
+    }
+    __syncthreads();
+
+    // ---------------- phase C: pairs of rows ----------------
+    const float sc = 1.0f / (float)N;
+    float2 du2 = make_float2(0.f, 0.f), u2 = make_float2(0.f, 0.f);
+    for (int pr = warp; pr < NN / 2; pr += RG_WARPS) {
+        const int r0 = 2 * pr;
+        // packed inverse input Z[q] = X[q] + i Y[q] (q >= 65 by conjugate symmetry);
+        // transformed with the forward code on conj(Z): x = conj(F(conj Z))
+        float2 v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int q = l + 32 * j;
+            const bool lo = q < RG_Q;
+            const int qq = lo ? q : NN - q;
+            float2 X = spec[qq * RG_QS + r0];
+            float2 Y = spec[qq * RG_QS + r0 + 1];
+            if (qq == 0 || 2 * qq == NN) {   // exactly real bins
+                X.y = 0.f;
+                Y.y = 0.f;
+            }
+            if (!lo) {
+                X.y = -X.y;
+                Y.y = -Y.y;
+            }
+            v[j] = make_float2(X.x - Y.y, -(X.y + Y.x));   // conj(X + i Y)
+        }
+        fft128_fwd(v, tw, l);
+        const int br = bitrev5(l);
+        // conj of the result, through the exchange row into natural column order
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) xrow[xpos(k1 + 4 * br)] = make_float2(v[k1].x, -v[k1].y);
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = l + 32 * j;
+            const float2 z = xrow[xpos(c)];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int gi = (r0 + h) * NN + c;
+                const float d = (h == 0 ? z.x : z.y) * sc;
+                const float o = u[gi];
+                du2 = ds_add(du2, ds_sq(d));
+                u2 = ds_add(u2, ds_sq(o));
+                const float nw = o + d;
+                u[gi] = nw;
+                if (u_hi) {
+                    const unsigned int bits = __float_as_uint(nw);
+                    const unsigned int hb = (bits + 0x7fffu + ((bits >> 16) & 1u)) & 0xffff0000u;
+                    const float rem = nw - __uint_as_float(hb);
+                    const unsigned int rb = __float_as_uint(rem);
+                    const unsigned int lb = (rb + 0x7fffu + ((rb >> 16) & 1u)) & 0xffff0000u;
+                    u_hi[gi] = (unsigned short)(hb >> 16);
+                    u_lo[gi] = (unsigned short)(lb >> 16);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    block_sum_ds2(du2, u2, red);
+    if (tid == 0) step_stop(ctrl, par, mode, ds_value(du2), ds_value(u2));
+}
+
+bool usolve_reg_configure()
+{
+    if (cudaFuncSetAttribute(k_usolve_reg128, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)RG_SMEM) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+void launch_usolve_reg128(const TvArgs& a, cudaStream_t s)
+{
+    k_usolve_reg128<<<a.nimg > 0 ? a.nimg : 1, RG_T, RG_SMEM, s>>>(
+        a.u, a.w, a.lam, a.g, a.tw, a.s2, a.beta, a.mu_over_tau, a.mu, a.ctrl, a.mode, a.mu_img,
+        a.tau_img, a.tau, a.u_hi, a.u_lo, a.img_slot);
+}
+
+}  // namespace tvcs

@@ -51,6 +51,10 @@ void launch_usolve(int n, int cluster, const TvArgs& a, cudaStream_t s);
 // usolve_img_configure sets the kernel attributes, false if n has no variant.
 bool usolve_img_configure(int n);
 void launch_usolve_img(int n, const TvArgs& a, cudaStream_t s);
+// The same rows for batches of 128 x 128 images with the 128-point transforms in
+// the registers of one warp (k_usolve_reg.cu): no block barrier inside a phase.
+bool usolve_reg_configure();
+void launch_usolve_reg128(const TvArgs& a, cudaStream_t s);
 
 // Fused single-pass products r = A x - y, gpart = per-block partials of A^T r.
 struct ProdArgs {

@@ -336,3 +336,30 @@ def test_gemm_autotune_agrees_with_the_default_shape(tv):
     assert np.all(np.abs(G1.astype(np.float64) - G0) <= 1e-6 * (np.abs(R0.astype(np.float64)) @ A64) + 1e-30)
     for b in range(count):
         assert rel(u1[b], u0[b]) <= 1e-5, b
+
+
+def test_batched_n128_u_solve_in_registers(tv):
+    # 128 x 128 images take the u-solve whose 128-point transforms stay in the
+    # registers of one warp: 6 images for 40 iterations against the FP64 oracle,
+    # and image 2 against the single-image solve on the same bf16 hi+lo storage
+    # (binary32 u-step on a thread-block cluster).
+    A, ubars, F, mus, _ = synth.workload_shared_batch(count=6, n=128, ratio=0.3, seed=17, n_ellipses=8)
+    m, N = A.shape
+    tau = oracle.default_tau(A, 30)
+    iters = 40
+    h = bf16_handle(tv, A, m, 128, mu=1e3, tau=tau, max_iter=iters)
+    us = [np.empty(N, np.float32) for _ in range(6)]
+    res = tv.tvcs_solve_batched([h] * 6, [F[b] for b in range(6)], us, mus)
+    for b in range(6):
+        assert res[b].iters == iters
+        ref = oracle.solve(A, F[b], 128, mus[b], 10.0, tau, max_iter=iters)
+        err = rel(us[b], ref.u)
+        print("n128 image %d: %.2e" % (b, err))
+        assert err <= 1e-4, (b, err)
+        assert res[b].objective == pytest.approx(ref.info["objective"], rel=1e-4)
+    h1 = bf16_handle(tv, A, m, 128, mu=mus[2], tau=tau, max_iter=iters)
+    u1 = np.empty(N, np.float32)
+    tv.tvcs_solve(h1, F[2], u1)
+    assert rel(us[2], u1) <= 1e-4
+    tv.tvcs_destroy(h)
+    tv.tvcs_destroy(h1)
