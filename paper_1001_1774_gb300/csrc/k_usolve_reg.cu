@@ -17,18 +17,20 @@
 // forward transform followed by its inverse needs no reordering.
 //
 // Phases (8 warps):
-//   A  per pair of rows (r0, r0+1): the multiplier update and shrink of rows
-//      r0-1 .. r0+1 from u, w, lambda in global memory (L2), the right-hand
-//      side of the pair packed into one complex row, its forward transform, and
-//      the split into the two rows' half spectra, stored column-major in shared
-//      memory (the spectrum of the image never leaves the SM);
+//   A  per pair of rows (r0, r0+1), each warp down a stripe of 16 rows: the
+//      multiplier update and shrink of the two rows from u, w, lambda in global
+//      memory (L2), the right-hand side of the pair packed into one complex row,
+//      its forward transform, and the split into the two rows' half spectra,
+//      stored column-major in shared memory (the spectrum of the image never
+//      leaves the SM);
 //   B  per column q = 0..64: forward transform, divide by beta Lambda_pq + mu/tau,
 //      inverse transform, in registers;
 //   C  per pair of rows: the packed inverse row transform (through the same
 //      forward code on the conjugate), u += d, bf16 planes, double-single norms;
 // then the block's sums and eq. (stop).  Shared memory: the half spectrum
 // (65 columns of 129 complex values) and one 128-value exchange row per warp:
-// 75 KB, three images per SM.
+// 75 KB; two images per SM (256 images in one wave), with the registers of
+// that occupancy holding the next pair's loads while a pair is transformed.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -175,11 +177,74 @@ __device__ __forceinline__ void shift_right_cols(const float v[4], float out[4],
     for (int j = 0; j < 4; ++j) out[j] = (l == 31) ? s[(j + 1) & 3] : s[j];
 }
 
+// Multiplier update of eq. (udlamb) (when an iteration is pending), shrink of
+// eq. (shrink) and y = beta (w - Du) - lambda for one row held as columns
+// l + 32 j: uc is the row, ud the row below it (periodic), l1/l2 the
+// multipliers (updated in place), wo1/wo2 the previous w (read when pending).
+__device__ __forceinline__ void shrink_row(const float (&uc)[4], const float (&ud)[4], float (&l1)[4],
+                                           float (&l2)[4], const float (&wo1)[4], const float (&wo2)[4],
+                                           int pending, float beta, float inv_beta, int l,
+                                           float (&y1)[4], float (&y2)[4], float (&w1)[4], float (&w2)[4])
+{
+    float up[4];
+    shift_right_cols(uc, up, l);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float d1 = up[j] - uc[j];
+        const float d2 = ud[j] - uc[j];
+        if (pending) {
+            l1[j] -= beta * (wo1[j] - d1);
+            l2[j] -= beta * (wo2[j] - d2);
+        }
+        const float z1 = d1 + l1[j] * inv_beta, z2 = d2 + l2[j] * inv_beta;
+        const float nz = sqrtf(z1 * z1 + z2 * z2);
+        float a1 = 0.0f, a2 = 0.0f;
+        if (nz > inv_beta) {
+            const float sc = (nz - inv_beta) / nz;
+            a1 = sc * z1;
+            a2 = sc * z2;
+        }
+        w1[j] = a1;
+        w2[j] = a2;
+        y1[j] = beta * (a1 - d1) - l1[j];
+        y2[j] = beta * (a2 - d2) - l2[j];
+    }
+}
+
+// What the pair of rows (r0, r0 + 1) reads besides the carried row r0 of u:
+// u rows r0 + 1, r0 + 2 (periodic), the multipliers, w (when pending) and g
+// of rows r0, r0 + 1.
+struct PairIn {
+    float u[2][4];
+    float l1[2][4], l2[2][4], w1[2][4], w2[2][4];
+    float g[2][4];
+};
+
+__device__ __forceinline__ void load_pair(PairIn& in, const float* __restrict__ u,
+                                          const float* __restrict__ lsrc, const float* __restrict__ wsrc,
+                                          const float* __restrict__ g, int r0, int l, int pending)
+{
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = l + 32 * j;
+            const int gi = (r0 + h) * RG_NN + c;
+            in.u[h][j] = u[((r0 + 1 + h) & (RG_NN - 1)) * RG_NN + c];
+            in.l1[h][j] = lsrc[gi];
+            in.l2[h][j] = lsrc[RG_N + gi];
+            in.w1[h][j] = pending ? wsrc[gi] : 0.0f;
+            in.w2[h][j] = pending ? wsrc[RG_N + gi] : 0.0f;
+            in.g[h][j] = g[gi];
+        }
+    }
+}
+
 }  // namespace
 
 // Image b = blockIdx.x, with the conventions of k_usolve_img (per-image mu and
 // tau, control block, bf16 planes at row img_slot[b]).
-__global__ void __launch_bounds__(RG_T, 3) k_usolve_reg128(
+__global__ void __launch_bounds__(RG_T, 2) k_usolve_reg128(
     float* __restrict__ u, float* __restrict__ wbuf, float* __restrict__ lbuf,
     const float* __restrict__ g, const float2* __restrict__ tw_g, const float* __restrict__ s2_g,
     float beta, float mu_over_tau, float mu, Ctrl* __restrict__ ctrl, int mode,
@@ -231,48 +296,51 @@ __global__ void __launch_bounds__(RG_T, 3) k_usolve_reg128(
     const float inv_beta = 1.0f / beta;
 
     // ---------------- phase A: pairs of rows ----------------
-    for (int pr = warp; pr < NN / 2; pr += RG_WARPS) {
-        const int r0 = 2 * pr;
-        float uu[4][4];   // u rows r0-1 .. r0+2 at columns l + 32 j
+    // Warp w owns the stripe of rows 16 w .. 16 w + 15 (eight pairs), so that
+    // each pair shares its upper u row and the y2 row above it with the pair
+    // before: one shrink per row, plus one for the row above the stripe.  The
+    // loads of the next pair are issued before the transform of the current
+    // one, which hides their latency.
+    constexpr int PPW = NN / 2 / RG_WARPS;
+    const int R0 = warp * 2 * PPW;
+    float ucur[4], y2prev[4];   // u row r0 and y2 of row r0 - 1
+    {
+        const int rp = (R0 - 1 + NN) & (NN - 1);
+        float ur[4], lr1[4], lr2[4], wr1[4], wr2[4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int row = (r0 - 1 + t + NN) & (NN - 1);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) uu[t][j] = u[row * NN + l + 32 * j];
+        for (int j = 0; j < 4; ++j) {
+            const int gi = rp * NN + l + 32 * j;
+            ur[j] = u[gi];
+            ucur[j] = u[R0 * NN + l + 32 * j];
+            lr1[j] = lsrc[gi];
+            lr2[j] = lsrc[N + gi];
+            wr1[j] = pending ? wsrc[gi] : 0.0f;
+            wr2[j] = pending ? wsrc[N + gi] : 0.0f;
         }
-        float y1[2][4], y2[3][4];   // y1 of rows r0, r0+1; y2 of rows r0-1 .. r0+1
+        float y1d[4], w1d[4], w2d[4];
+        shrink_row(ur, ucur, lr1, lr2, wr1, wr2, pending, beta, inv_beta, l, y1d, y2prev, w1d, w2d);
+    }
+    PairIn cur;
+    load_pair(cur, u, lsrc, wsrc, g, R0, l, pending);
+#pragma unroll 1
+    for (int k = 0; k < PPW; ++k) {
+        const int r0 = R0 + 2 * k;
+        float y1[2][4], y2[2][4], w1[4], w2[4];
 #pragma unroll
-        for (int t = 0; t < 3; ++t) {   // rows r0-1+t: multiplier update, shrink, y
-            const int row = (r0 - 1 + t + NN) & (NN - 1);
-            float up[4];
-            shift_right_cols(uu[t], up, l);
+        for (int h = 0; h < 2; ++h) {   // rows r0 + h: multiplier update, shrink, y
+            if (h == 0)
+                shrink_row(ucur, cur.u[0], cur.l1[0], cur.l2[0], cur.w1[0], cur.w2[0], pending, beta,
+                           inv_beta, l, y1[0], y2[0], w1, w2);
+            else
+                shrink_row(cur.u[0], cur.u[1], cur.l1[1], cur.l2[1], cur.w1[1], cur.w2[1], pending, beta,
+                           inv_beta, l, y1[1], y2[1], w1, w2);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int gi = row * NN + l + 32 * j;
-                const float uc = uu[t][j];
-                const float d1 = up[j] - uc;
-                const float d2 = uu[t + 1][j] - uc;
-                float l1 = lsrc[gi], l2 = lsrc[N + gi];
-                if (pending) {   // eq. (udlamb) for the previous iteration
-                    l1 -= beta * (wsrc[gi] - d1);
-                    l2 -= beta * (wsrc[N + gi] - d2);
-                }
-                const float z1 = d1 + l1 * inv_beta, z2 = d2 + l2 * inv_beta;
-                const float nz = sqrtf(z1 * z1 + z2 * z2);
-                float w1 = 0.0f, w2 = 0.0f;
-                if (nz > inv_beta) {
-                    const float sc = (nz - inv_beta) / nz;
-                    w1 = sc * z1;
-                    w2 = sc * z2;
-                }
-                y2[t][j] = beta * (w2 - d2) - l2;
-                if (t >= 1) {
-                    y1[t - 1][j] = beta * (w1 - d1) - l1;
-                    wdst[gi] = w1;
-                    wdst[N + gi] = w2;
-                    ldst[gi] = l1;
-                    ldst[N + gi] = l2;
-                }
+                const int gi = (r0 + h) * NN + l + 32 * j;
+                wdst[gi] = w1[j];
+                wdst[N + gi] = w2[j];
+                ldst[gi] = cur.l1[h][j];
+                ldst[N + gi] = cur.l2[h][j];
             }
         }
         // right-hand side of rows r0, r0+1 packed: z = rhs[r0] + i rhs[r0+1]
@@ -282,14 +350,16 @@ __global__ void __launch_bounds__(RG_T, 3) k_usolve_reg128(
         shift_left_cols(y1[1], ym[1], l);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            float rr[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const float dty = ym[h][j] - y1[h][j] + y2[h][j] - y2[h + 1][j];
-                rr[h] = dty - mu * g[(r0 + h) * NN + l + 32 * j];
-            }
-            v[j] = make_float2(rr[0], rr[1]);
+            const float rr0 = ym[0][j] - y1[0][j] + y2prev[j] - y2[0][j] - mu * cur.g[0][j];
+            const float rr1 = ym[1][j] - y1[1][j] + y2[0][j] - y2[1][j] - mu * cur.g[1][j];
+            v[j] = make_float2(rr0, rr1);
         }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            ucur[j] = cur.u[1][j];
+            y2prev[j] = y2[1][j];
+        }
+        if (k + 1 < PPW) load_pair(cur, u, lsrc, wsrc, g, r0 + 2, l, pending);
         fft128_fwd(v, tw, l);
         // exchange row: Z[k] at its padded position, then the split of the pair
         const int br = bitrev5(l);
@@ -337,6 +407,11 @@ __global__ void __launch_bounds__(RG_T, 3) k_usolve_reg128(
     float2 du2 = make_float2(0.f, 0.f), u2 = make_float2(0.f, 0.f);
     for (int pr = warp; pr < NN / 2; pr += RG_WARPS) {
         const int r0 = 2 * pr;
+        float uo[2][4];   // u of the pair, loaded before the transform that hides the latency
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) uo[h][j] = u[(r0 + h) * NN + l + 32 * j];
         // packed inverse input Z[q] = X[q] + i Y[q] (q >= 65 by conjugate symmetry);
         // transformed with the forward code on conj(Z): x = conj(F(conj Z))
         float2 v[4];
@@ -371,7 +446,7 @@ __global__ void __launch_bounds__(RG_T, 3) k_usolve_reg128(
             for (int h = 0; h < 2; ++h) {
                 const int gi = (r0 + h) * NN + c;
                 const float d = (h == 0 ? z.x : z.y) * sc;
-                const float o = u[gi];
+                const float o = uo[h][j];
                 du2 = ds_add(du2, ds_sq(d));
                 u2 = ds_add(u2, ds_sq(o));
                 const float nw = o + d;
