@@ -274,6 +274,18 @@ tvcs_status tvcs_apply(tvcs_handle h, const float* x, const float* y, float* r, 
  * Other storages and encoders return TVCS_ERR_UNSUPPORTED. */
 tvcs_status tvcs_test_hold_grid_barrier(tvcs_handle h, int extra);
 
+/* Test hook for the launch shape of the two batched GEMMs (R = A U - F and
+ * G = A^T R; the paper has no counterpart): grid1/grid2 persistent blocks, on
+ * single blocks (pair 0, grid <= SM count) or on clusters of two blocks that
+ * share each 256-row tile (pair 1, grid even, grid/2 <= the clusters that fit).
+ * grid1 = grid2 = 0 returns the choice to the tuner (opt->autotune) or to one
+ * block per SM.  Takes effect at the next batched call, which re-plans the
+ * stream-K split and rebuilds the batch buffers.  Results of different shapes
+ * agree to binary32 rounding (a tile's K sums are grouped differently), not
+ * bitwise.  TVCS_ERR_INVALID_ARG for a malformed shape, TVCS_ERR_UNSUPPORTED
+ * for more pairs than fit. */
+tvcs_status tvcs_test_gemm_shape(tvcs_handle h, int grid1, int pair1, int grid2, int pair2);
+
 /* ---- Products without any device allocation -------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that
  * cannot call cudaMalloc when they need the products -- applications that

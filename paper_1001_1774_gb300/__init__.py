@@ -38,7 +38,8 @@ EXPORTED = ["tvcs_default_options", "tvcs_create", "tvcs_create_partial_dct", "t
             "tvcs_solve_continuation",
             "tvcs_destroy", "tvcs_last_error", "tvcs_get_tau", "tvcs_get_state",
             "tvcs_set_state", "tvcs_iterate", "tvcs_run_stage", "tvcs_time_stage", "tvcs_apply",
-            "tvcs_apply_noalloc", "tvcs_apply_batched", "tvcs_test_hold_grid_barrier"]
+            "tvcs_apply_noalloc", "tvcs_apply_batched", "tvcs_test_hold_grid_barrier",
+            "tvcs_test_gemm_shape"]
 
 
 class tvcs_options(ctypes.Structure):
@@ -95,6 +96,7 @@ def _load() -> ctypes.CDLL:
         "tvcs_apply_noalloc": ([vp, i, i, vp, vp, vp, vp, vp], i),
         "tvcs_apply_batched": ([H, i, vp, vp, vp, vp], i),
         "tvcs_test_hold_grid_barrier": ([H, i], i),
+        "tvcs_test_gemm_shape": ([H, i, i, i, i], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -313,6 +315,12 @@ def tvcs_test_hold_grid_barrier(h: Handle, extra: int) -> None:
     """Timeout test hook: the product kernel's grid barrier waits for `extra`
     arrivals that never come (0 restores normal operation)."""
     _check(_lib.tvcs_test_hold_grid_barrier(h.ptr, int(extra)))
+
+
+def tvcs_test_gemm_shape(h: Handle, grid1: int, pair1: int, grid2: int, pair2: int) -> None:
+    """Test hook: launch shape of the two batched GEMMs (blocks, and 1 for CTA
+    pairs); grid1 = grid2 = 0 returns the choice to the tuner."""
+    _check(_lib.tvcs_test_gemm_shape(h.ptr, int(grid1), int(pair1), int(grid2), int(pair2)))
 
 
 def tvcs_last_error() -> str:

@@ -187,15 +187,6 @@ __global__ void k_batch_resid_r2(const float* __restrict__ R, int m, Ctrl* __res
     if (threadIdx.x == 0) ctrls[blockIdx.x].r2 = ds_value(s);
 }
 
-// A_eff = hi + lo (exact in binary32) from the two bf16 planes.
-__global__ void k_join_bf16x2(const unsigned short* __restrict__ hi, const unsigned short* __restrict__ lo,
-                              float* __restrict__ out, long long count)
-{
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
-         i += (long long)gridDim.x * blockDim.x)
-        out[i] = __uint_as_float((unsigned)hi[i] << 16) + __uint_as_float((unsigned)lo[i] << 16);
-}
-
 namespace {
 
 #define BCK(call)                                                                             \
@@ -306,10 +297,12 @@ tvcs_status upload_plan(const GemmPlan& p, int** tsb, int** ss, cudaStream_t s)
 tvcs_status make_maps(tvcs_ctx* h, int count)
 {
     tvcs_batch* b = h->batch;
-    bool ok = make_bf16_map(&b->mAh, h->P0, h->N, h->m, h->N, 128) &&
-              make_bf16_map(&b->mAl, h->P1, h->N, h->m, h->N, 128) &&
-              make_bf16_map(&b->mAth, b->Ath, h->m, h->N, b->mpad, 128) &&
-              make_bf16_map(&b->mAtl, b->Atl, h->m, h->N, b->mpad, 128) &&
+    // the X operands in their tile-contiguous planes: rows of 64 values, boxes of 128 rows
+    const int rows1 = b->tiles1 * b->kb1 * 128, rows2 = b->tiles2 * b->kb2 * 128;
+    bool ok = make_bf16_map(&b->mAh, b->Tah, 64, rows1, 64, 128) &&
+              make_bf16_map(&b->mAl, b->Tal, 64, rows1, 64, 128) &&
+              make_bf16_map(&b->mAth, b->Tth, 64, rows2, 64, 128) &&
+              make_bf16_map(&b->mAtl, b->Ttl, 64, rows2, 64, 128) &&
               make_bf16_map(&b->mUh, b->Uh, h->N, count, h->N, GEMM_Y_BOX) &&
               make_bf16_map(&b->mUl, b->Ul, h->N, count, h->N, GEMM_Y_BOX) &&
               make_bf16_map(&b->mRh, b->Rh, h->m, count, b->mpad, GEMM_Y_BOX) &&
@@ -318,32 +311,48 @@ tvcs_status make_maps(tvcs_ctx* h, int count)
     return TVCS_OK;
 }
 
-// Numbers of persistent blocks the GEMM tuner tries: all SMs, 7/8, 3/4 and 1/2 of them.
-std::vector<int> gemm_grid_candidates(int num_sms)
+// Launch shapes the GEMM tuner tries: one block per SM and 7/8, 3/4, 1/2 of
+// that, on single blocks and (where the device holds clusters of two of them)
+// on CTA pairs.
+struct GemmShape {
+    int grid = 0, pair = 0;
+};
+
+std::vector<GemmShape> gemm_shape_candidates(int num_sms, int pair_clusters)
 {
-    return {num_sms, num_sms * 7 / 8, num_sms * 3 / 4, num_sms / 2};
+    std::vector<GemmShape> v;
+    for (int g : {num_sms, num_sms * 7 / 8, num_sms * 3 / 4, num_sms / 2}) v.push_back({g, 0});
+    const int pc = std::min(pair_clusters, num_sms / 2);
+    if (pc > 0)
+        for (int c : {pc, pc * 7 / 8, pc * 3 / 4, pc / 2})
+            if (c > 0) v.push_back({2 * c, 1});
+    return v;
 }
 
 std::mutex g_gemm_tune_mutex;
-std::map<std::tuple<int, int, int>, std::pair<int, int>> g_gemm_grids;   // (device, m, N) -> grids
+std::map<std::tuple<int, int, int>, std::pair<GemmShape, GemmShape>> g_gemm_shapes;   // (device, m, N)
 
-// Picks the number of persistent blocks of each GEMM (and with it the stream-K
-// split of its tiles x K-blocks) by timing every candidate, GEMM and fix-up
-// together, over five launches each (median), on the handle's own operands;
-// cached per device and (m, n).  opt.autotune = 0 keeps one block per SM.  A
+// Picks the launch shape of each GEMM (persistent blocks or pairs, and with it
+// the stream-K split of its tiles x K-blocks) by timing every candidate, GEMM
+// and fix-up together, over five launches each (median), on the handle's own
+// operands; cached per device and (m, n).  opt.autotune = 0 keeps one block
+// per SM; a shape set through tvcs_test_gemm_shape takes precedence.  A
 // different split regroups the K sums of a tile, so results agree to binary32
 // rounding with the default shape, not bitwise.
 tvcs_status tune_gemms(tvcs_ctx* h, int count)
 {
     tvcs_batch* b = h->batch;
     cudaStream_t s = h->stream;
-    int g1 = h->num_sms, g2 = h->num_sms;
-    if (h->opt.autotune) {
+    GemmShape g1{h->num_sms, 0}, g2{h->num_sms, 0};
+    if (h->gemm_force[0] > 0) {
+        g1 = {h->gemm_force[0], h->gemm_force[1]};
+        g2 = {h->gemm_force[2], h->gemm_force[3]};
+    } else if (h->opt.autotune) {
         bool cached = false;
         {
             std::lock_guard<std::mutex> lk(g_gemm_tune_mutex);
-            auto it = g_gemm_grids.find({h->dev, h->m, h->N});
-            if (it != g_gemm_grids.end()) {
+            auto it = g_gemm_shapes.find({h->dev, h->m, h->N});
+            if (it != g_gemm_shapes.end()) {
                 g1 = it->second.first;
                 g2 = it->second.second;
                 cached = true;
@@ -354,9 +363,9 @@ tvcs_status tune_gemms(tvcs_ctx* h, int count)
             for (int which = 0; which < 2; ++which) {
                 const int M = which == 0 ? h->m : h->N, K = which == 0 ? h->N : h->m;
                 float best = -1.f;
-                for (int g : gemm_grid_candidates(h->num_sms)) {
+                for (GemmShape g : gemm_shape_candidates(h->num_sms, b->pair_clusters)) {
                     GemmPlan p;
-                    gemm_plan(M, K, g, &p);
+                    gemm_plan(M, K, g.grid, &p, g.pair != 0);
                     int *tsb = nullptr, *ss = nullptr;
                     BCKS(upload_plan(p, &tsb, &ss, s));
                     float t[5];
@@ -392,17 +401,21 @@ tvcs_status tune_gemms(tvcs_ctx* h, int count)
                 }
             }
             std::lock_guard<std::mutex> lk(g_gemm_tune_mutex);
-            g_gemm_grids[{h->dev, h->m, h->N}] = {g1, g2};
+            g_gemm_shapes[{h->dev, h->m, h->N}] = {g1, g2};
         }
     }
-    if (g1 != b->p1.grid || g2 != b->p2.grid) {
+    GemmPlan q1, q2;
+    gemm_plan(h->m, h->N, g1.grid, &q1, g1.pair != 0);
+    gemm_plan(h->N, h->m, g2.grid, &q2, g2.pair != 0);
+    if (q1.grid != b->p1.grid || q1.pair != b->p1.pair || q2.grid != b->p2.grid ||
+        q2.pair != b->p2.pair) {
         cudaFree(b->tsb1);
         cudaFree(b->ss1);
         cudaFree(b->tsb2);
         cudaFree(b->ss2);
         b->tsb1 = b->ss1 = b->tsb2 = b->ss2 = nullptr;
-        gemm_plan(h->m, h->N, g1, &b->p1);
-        gemm_plan(h->N, h->m, g2, &b->p2);
+        b->p1 = q1;
+        b->p2 = q2;
         BCKS(upload_plan(b->p1, &b->tsb1, &b->ss1, s));
         BCKS(upload_plan(b->p2, &b->tsb2, &b->ss2, s));
         BCKS(sync_check(h, "uploading the tuned GEMM plans"));
@@ -436,31 +449,32 @@ tvcs_status ensure_batch(tvcs_ctx* h, int count)
         b->ucluster = usolve_cluster_fits(h->n, 8) ? 8 : h->ucluster;
         usolve_cluster_fits(h->n, b->ucluster);   // kernel attributes of the chosen size
     }
-    if (!b->Ath) {
+    if (!b->Tah) {
+        // A and A^T as tile-contiguous hi/lo planes (each GEMM tile of the X operand is
+        // one contiguous 16 KB block in HBM)
         b->mpad = (int)((m + 7) / 8 * 8);
         BCK(gemm_configure());
-        BCKS(balloc((void**)&b->Ath, sizeof(unsigned short) * N * b->mpad));
-        BCKS(balloc((void**)&b->Atl, sizeof(unsigned short) * N * b->mpad));
-        float* tmp = nullptr;
-        BCKS(balloc((void**)&tmp, sizeof(float) * m * N));
-        k_join_bf16x2<<<152 * 8, 256, 0, s>>>(reinterpret_cast<const unsigned short*>(h->P0),
-                                              reinterpret_cast<const unsigned short*>(h->P1), tmp,
-                                              (long long)(m * N));
-        launch_transpose_split(tmp, h->m, h->N, b->Ath, b->Atl, b->mpad, s);
+        b->pair_clusters = gemm_pair_max_clusters(h->num_sms);
+        b->tiles1 = (int)((m + 127) / 128);
+        b->kb1 = (int)((N + 63) / 64);
+        b->tiles2 = (int)((N + 127) / 128);
+        b->kb2 = (int)((m + 63) / 64);
+        const size_t e1 = (size_t)b->tiles1 * b->kb1 * 128 * 64, e2 = (size_t)b->tiles2 * b->kb2 * 128 * 64;
+        BCKS(balloc((void**)&b->Tah, sizeof(unsigned short) * e1));
+        BCKS(balloc((void**)&b->Tal, sizeof(unsigned short) * e1));
+        BCKS(balloc((void**)&b->Tth, sizeof(unsigned short) * e2));
+        BCKS(balloc((void**)&b->Ttl, sizeof(unsigned short) * e2));
+        launch_tile_planes(h->P0, h->P1, h->m, h->N, 0, b->Tah, b->Tal, b->tiles1, b->kb1, s);
+        launch_tile_planes(h->P0, h->P1, h->m, h->N, 1, b->Tth, b->Ttl, b->tiles2, b->kb2, s);
         cudaError_t e = cudaStreamSynchronize(s);
-        cudaFree(tmp);
+        if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess)
-            return set_last_error(TVCS_ERR_CUDA, "building A^T: %s", cudaGetErrorString(e));
+            return set_last_error(TVCS_ERR_CUDA, "building the tiled planes of A and A^T: %s",
+                                  cudaGetErrorString(e));
     }
     if (b->cap < count) {
-        // keep A^T, replace the per-image buffers
-        unsigned short *ath = b->Ath, *atl = b->Atl;
-        const int mpad = b->mpad;
-        b->Ath = b->Atl = nullptr;
+        // keep the tiled planes of A and A^T, replace the per-image buffers
         free_buffers(b);
-        b->Ath = ath;
-        b->Atl = atl;
-        b->mpad = mpad;
         const size_t B = (size_t)count;
         gemm_plan(h->m, h->N, h->num_sms, &b->p1);
         gemm_plan(h->N, h->m, h->num_sms, &b->p2);
@@ -468,10 +482,15 @@ tvcs_status ensure_batch(tvcs_ctx* h, int count)
         BCKS(upload_plan(b->p2, &b->tsb2, &b->ss2, s));
         // the workspace holds the partial tiles of every candidate shape the tuner may pick
         size_t wsf = 0;
-        for (int g : gemm_grid_candidates(h->num_sms)) {
+        std::vector<GemmShape> shapes = gemm_shape_candidates(h->num_sms, b->pair_clusters);
+        if (h->gemm_force[0] > 0) {
+            shapes.push_back({h->gemm_force[0], h->gemm_force[1]});
+            shapes.push_back({h->gemm_force[2], h->gemm_force[3]});
+        }
+        for (GemmShape g : shapes) {
             GemmPlan q1, q2;
-            gemm_plan(h->m, h->N, g, &q1);
-            gemm_plan(h->N, h->m, g, &q2);
+            gemm_plan(h->m, h->N, g.grid, &q1, g.pair != 0);
+            gemm_plan(h->N, h->m, g.grid, &q2, g.pair != 0);
             wsf = std::max(wsf, std::max(q1.ws_floats, q2.ws_floats));
         }
         BCKS(balloc((void**)&b->ws, sizeof(float) * wsf));
@@ -623,8 +642,8 @@ void free_batch(tvcs_ctx* h)
     if (!h || !h->batch) return;
     tvcs_batch* b = h->batch;
     free_buffers(b);
-    if (b->Ath) cudaFree(b->Ath);
-    if (b->Atl) cudaFree(b->Atl);
+    for (void* p : {(void*)b->Tah, (void*)b->Tal, (void*)b->Tth, (void*)b->Ttl})
+        if (p) cudaFree(p);
     delete b;
     h->batch = nullptr;
 }

@@ -14,7 +14,10 @@
 struct tvcs_batch {
     int cap = 0;                   // images the buffers hold
     int mpad = 0;                  // m rounded up to a multiple of 8 (bf16 row pitch)
-    unsigned short *Ath = nullptr, *Atl = nullptr;   // A^T as bf16 hi/lo planes, N x mpad
+    // the GEMMs' X operands, A (m x N) and A^T (N x m), as tile-contiguous bf16 hi/lo
+    // planes: tiles x kb tiles of 128 x 64 values, 16 KB each (launch_tile_planes)
+    unsigned short *Tah = nullptr, *Tal = nullptr, *Tth = nullptr, *Ttl = nullptr;
+    int tiles1 = 0, kb1 = 0, tiles2 = 0, kb2 = 0;
     float *U = nullptr, *W = nullptr, *L = nullptr, *G = nullptr, *R = nullptr, *F = nullptr;
     float* mu = nullptr;           // per-image mu
     unsigned short *Uh = nullptr, *Ul = nullptr, *Rh = nullptr, *Rl = nullptr;
@@ -37,6 +40,7 @@ struct tvcs_batch {
     bool uimg = false;             // the u-solve runs one block per image (k_usolve_img)
     bool ureg = false;             // n = 128: one block per image, transforms in registers (k_usolve_reg.cu)
     bool tuned = false;            // the GEMM launch shapes have been picked for these buffers
+    int pair_clusters = 0;         // clusters of two GEMM blocks resident at once (0: no pair kernel)
 };
 
 // Products with A regenerated in the kernel (handles created with
@@ -92,6 +96,7 @@ struct tvcs_ctx {
     int *dsidx = nullptr, *dsperm = nullptr, *drowptr = nullptr;
     tvcs_uneven* uneven = nullptr; // uneven batch whose first handle is this one
     int bar_extra = 0;             // timeout test hook (tvcs_test_hold_grid_barrier), else 0
+    int gemm_force[4] = {0, 0, 0, 0};   // tvcs_test_gemm_shape: grid, pair of each batched GEMM (0: tuner)
 };
 
 namespace tvcs {

@@ -3,7 +3,10 @@
 //     R = A U - F        (m x B,  K = n^2)
 //     G = A^T R          (n^2 x B, K = m)
 // with U = [u_1 ... u_B], F = [f_1 ... f_B].  Both run as K-major ("TN") GEMMs
-// D = X Y^T because A is stored twice, as A (m x n^2) and as A^T (n^2 x m).
+// D = X Y^T with the operand X = A (m x n^2) or A^T (n^2 x m) held in
+// tile-contiguous planes (k_tile_planes): each 128 x 64 tile of X is one
+// contiguous 16 KB block, so that a TMA load reads whole DRAM pages instead of
+// 128 pieces of 128 bytes a row pitch apart.
 //
 // Precision: every operand is split into bfloat16 hi + lo planes (hi =
 // bf16(v), lo = bf16(v - hi), round to nearest even) and
@@ -24,7 +27,8 @@
 // drains).  Each (block, segment) writes a partial tile; a fix-up kernel adds
 // the partials of every tile in K order (deterministic) and applies the
 // epilogue.  Every wait is bounded; on a timeout the kernel records the error,
-// lets its copies land and frees its tensor memory.
+// lets its copies land and frees its tensor memory.  k_gemm_bf16x3_pair runs the
+// same GEMM on clusters of two blocks (tcgen05 cta_group::2, 256-row tiles).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -198,8 +202,9 @@ __global__ void __launch_bounds__(192, 1)
                 const int t = (int)(w / kblocks), kb = (int)(w % kblocks);
                 unsigned char* st = smem + (size_t)s * GM_STAGE;
                 mbar_arrive_expect_tx(&full[s], stage_bytes);
-                tma_load_2d(st, &tXh, kb * GM_BK, t * GM_BM, &full[s], pol_x);
-                tma_load_2d(st + GM_A_BYTES, &tXl, kb * GM_BK, t * GM_BM, &full[s], pol_x);
+                const int xrow = (t * kblocks + kb) * GM_BM;   // tile-contiguous X (k_tile_planes)
+                tma_load_2d(st, &tXh, 0, xrow, &full[s], pol_x);
+                tma_load_2d(st + GM_A_BYTES, &tXl, 0, xrow, &full[s], pol_x);
                 for (int j = 0; j < ybox; ++j) {   // 64-row boxes, 1024-byte aligned
                     tma_load_2d(st + 2 * GM_A_BYTES + j * GM_YBOX_BYTES, &tYh, kb * GM_BK,
                                 j * GEMM_Y_BOX, &full[s], pol_y);
@@ -298,6 +303,312 @@ __global__ void __launch_bounds__(192, 1)
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(GM_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The same GEMM on CTA pairs (cta_group::2): a cluster of two blocks computes a
+// 256 x BN tile with M = 256 MMAs issued by the even block.  Each block holds
+// its 128 rows of the X tile and half of the Y tile (rows [rank nb/2, (rank+1)
+// nb/2) of the nb running columns); the MMA reads the X half of each block and
+// both Y halves, and writes each block's 128 rows of the accumulator into that
+// block's tensor memory.  Per block and K block the ring then holds 64 KB (three
+// stages) and the MMAs read 96 KB of shared memory instead of 144 KB, the Y
+// operand is fetched once per pair, and the two blocks' epilogues drain their
+// own halves.
+//   Barriers: the odd block's producer fills its own stage and, once its
+// copies have landed, its warp 1 arrives on the even block's "full" barrier
+// (remote arrival), so the even block's MMAs start when both halves are in.
+// The MMA commits arrive on the "empty" and "accumulator ready" barriers of
+// both blocks (multicast); the odd block's epilogue warps arrive on the even
+// block's "accumulator drained" barrier.  Stream-K over pairs: pair p owns
+// iterations [p W / P, (p+1) W / P) of W = tiles x kblocks (256-row tiles);
+// block c of the grid writes its partial tiles to ws + (c smax + j) BN 128, the
+// 128-row half tile 2 t + rank of the pair's tile t.
+// ---------------------------------------------------------------------------
+constexpr int GP_NST = 3;
+constexpr uint32_t GP_YH_BYTES = (GM_BN / 2) * GM_BK * 2;           // 16 KB: half a Y tile
+constexpr uint32_t GP_STAGE = 2 * GM_A_BYTES + 2 * GP_YH_BYTES;     // 64 KB
+constexpr size_t GP_SMEM = 1024 + GP_NST * GP_STAGE + 256;
+
+__device__ __forceinline__ void tc_mma_pair(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrive on the barrier at the same shared-memory offset in every block of the
+// cluster named in cta_mask once the MMAs issued so far have finished.
+__device__ __forceinline__ void tc_commit_pair(uint64_t* bar, uint16_t cta_mask)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 "
+        "[%0], %1;" ::"r"(smem_u32(bar)),
+        "h"(cta_mask)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t gemm_cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t gemm_map_peer(const void* local, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(local)), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void gemm_arrive_remote(uint32_t addr)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr)
+                 : "memory");
+}
+
+// Bounded wait with cluster-scope acquire: the phase may have been completed by
+// the other block of the pair (its arrival or an MMA commit it issued).
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity, long long budget)
+{
+    auto try_once = [&]() {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        return ok != 0;
+    };
+    if (try_once()) return true;
+    const long long t0 = clock64();
+    while (!try_once()) {
+        if (clock64() - t0 > budget) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void gemm_cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                     : "memory");
+}
+
+// Instruction descriptor of the pair's MMA: M = 256 (128 rows in each block).
+__host__ __device__ constexpr uint32_t gemm_idesc_pair(int nb)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(nb >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
+    k_gemm_bf16x3_pair(const __grid_constant__ CUtensorMap tXh, const __grid_constant__ CUtensorMap tXl,
+                       const __grid_constant__ CUtensorMap tYh, const __grid_constant__ CUtensorMap tYl,
+                       int tiles, int kblocks, float* __restrict__ ws, int smax,
+                       Ctrl* __restrict__ ctrl, int check_skip, long long budget, int ncols,
+                       const int* __restrict__ nact)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + GP_NST * GP_STAGE);
+    uint64_t* empty = full + GP_NST;
+    uint64_t* tfull = empty + GP_NST;    // [2] accumulator ready
+    uint64_t* tempty = tfull + 2;        // [2] accumulator drained (both blocks; used on the even one)
+    uint64_t* mdrain = tempty + 2;       // the issuer's MMAs have finished (after a timeout)
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mdrain + 1);
+
+    if (check_skip && ctrl->skip) return;   // the same for every block of the grid
+    int nb = min(ncols, GM_BN);
+    if (nact) nb = min(nb, *nact);
+    nb = min(GM_BN, max(32, (nb + 31) & ~31));
+    const int nbh = nb / 2;                                 // Y rows held by each block
+    const int ybox = (nbh + GEMM_Y_BOX - 1) / GEMM_Y_BOX;
+    const uint32_t stage_bytes = 2 * GM_A_BYTES + 2 * (uint32_t)ybox * GM_YBOX_BYTES;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t rank = gemm_cluster_rank();
+    const bool lead = rank == 0;
+    const long long W = (long long)tiles * kblocks;
+    const int P = gridDim.x >> 1, pair = blockIdx.x >> 1;
+    const long long w0 = W * pair / P, w1 = W * (pair + 1) / P;
+
+    if (tid == 0) {
+        for (int s = 0; s < GP_NST; ++s) {
+            mbar_init(&full[s], lead ? 2 : 1);   // own copies (+ the odd block's arrival)
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], 8);
+        }
+        mbar_init(mdrain, 1);
+        fence_mbar_init();
+    }
+    if (warp == 1) {   // one warp of each block of the pair, together
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tslot)),
+                     "r"(GM_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    gemm_cluster_sync();   // both blocks' barriers exist before any remote arrival
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer (both blocks) ----------------
+            bool ok = true;
+            long long it = 0;
+            const uint64_t pol_x = l2_policy_evict_first(), pol_y = l2_policy_evict_last();
+            for (long long w = w0; w < w1; ++w, ++it) {
+                const int s = (int)(it % GP_NST);
+                if (it >= GP_NST &&
+                    !mbar_wait_cluster(&empty[s], (uint32_t)((it / GP_NST) - 1) & 1u, budget)) {
+                    set_error(ctrl, ERR_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+                const int t = (int)(w / kblocks), kb = (int)(w % kblocks);
+                unsigned char* st = smem + (size_t)s * GP_STAGE;
+                mbar_arrive_expect_tx(&full[s], stage_bytes);
+                // 128-row tile 2 t + rank of the tile-contiguous X (past the last one: zeros)
+                const int xrow = ((2 * t + (int)rank) * kblocks + kb) * GM_BM;
+                tma_load_2d(st, &tXh, 0, xrow, &full[s], pol_x);
+                tma_load_2d(st + GM_A_BYTES, &tXl, 0, xrow, &full[s], pol_x);
+                for (int j = 0; j < ybox; ++j) {   // 64-row boxes, 1024-byte aligned
+                    const int yrow = (int)rank * nbh + j * GEMM_Y_BOX;
+                    tma_load_2d(st + 2 * GM_A_BYTES + j * GM_YBOX_BYTES, &tYh, kb * GM_BK, yrow,
+                                &full[s], pol_y);
+                    tma_load_2d(st + 2 * GM_A_BYTES + GP_YH_BYTES + j * GM_YBOX_BYTES, &tYl,
+                                kb * GM_BK, yrow, &full[s], pol_y);
+                }
+            }
+            // leave no copy in flight; on the even block a stage's phase also
+            // needs the odd block's arrival, hence the drain bound
+            const long long n_issued = it;
+            for (long long j = (n_issued > GP_NST ? n_issued - GP_NST : 0); j < n_issued; ++j)
+                mbar_wait_cluster(&full[j % GP_NST], (uint32_t)(j / GP_NST) & 1u, drain_budget(budget));
+            // and no MMA-commit arrival still on its way to this block's barriers
+            if (ok)
+                for (long long j = (n_issued > GP_NST ? n_issued - GP_NST : 0); j < n_issued; ++j)
+                    mbar_wait_cluster(&empty[j % GP_NST], (uint32_t)(j / GP_NST) & 1u,
+                                      drain_budget(budget));
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && lead) {
+            // ---------------- MMA issuer (even block) ----------------
+            const uint32_t idesc = gemm_idesc_pair(nb);
+            bool ok = true;
+            long long it = 0;
+            int seg = 0;
+            long long w = w0;
+            while (w < w1 && ok) {
+                const int t = (int)(w / kblocks);
+                const long long wend = min(w1, (long long)(t + 1) * kblocks);
+                const int acc = seg & 1;
+                if (seg >= 2 &&
+                    !mbar_wait_cluster(&tempty[acc], (uint32_t)((seg >> 1) - 1) & 1u, budget)) {
+                    set_error(ctrl, ERR_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dt = tmem + (uint32_t)(acc * GM_BN);
+                bool first = true;
+                for (; w < wend; ++w, ++it) {
+                    const int s = (int)(it % GP_NST);
+                    if (!mbar_wait_cluster(&full[s], (uint32_t)(it / GP_NST) & 1u, budget)) {
+                        set_error(ctrl, ERR_TIMEOUT);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t base = smem_u32(smem + (size_t)s * GP_STAGE);
+                    const uint32_t xh = base, xl = base + GM_A_BYTES;
+                    const uint32_t yh = base + 2 * GM_A_BYTES, yl = yh + GP_YH_BYTES;
+#pragma unroll
+                    for (int k = 0; k < GM_BK / 16; ++k) {
+                        const uint32_t off = k * 32;   // 16 bf16 along K
+                        tc_mma_pair(dt, sw128_desc(xh + off), sw128_desc(yh + off), idesc, first ? 0u : 1u);
+                        first = false;
+                        tc_mma_pair(dt, sw128_desc(xh + off), sw128_desc(yl + off), idesc, 1u);
+                        tc_mma_pair(dt, sw128_desc(xl + off), sw128_desc(yh + off), idesc, 1u);
+                    }
+                    tc_commit_pair(&empty[s], 3);   // frees the stage in both blocks
+                }
+                if (!ok) break;
+                tc_commit_pair(&tfull[acc], 3);     // both halves of the accumulator ready
+                ++seg;
+            }
+            if (!ok) {   // a wait gave up: the MMAs already issued finish before TMEM is freed
+                tc_commit_pair(mdrain, 1);
+                mbar_wait(mdrain, 0u, drain_budget(budget));
+            }
+        } else if (lane == 0) {
+            // ------- odd block: tell the even block when each stage has landed -------
+            const uint32_t lead_full = gemm_map_peer(full, 0);
+            long long it = 0;
+            for (long long w = w0; w < w1; ++w, ++it) {
+                const int s = (int)(it % GP_NST);
+                if (!mbar_wait_cluster(&full[s], (uint32_t)(it / GP_NST) & 1u, budget)) {
+                    set_error(ctrl, ERR_TIMEOUT);
+                    break;
+                }
+                gemm_arrive_remote(lead_full + (uint32_t)(s * 8));
+            }
+        }
+    } else {
+        // ---------------- epilogue warps 2..5 (both blocks): TMEM -> workspace ----------------
+        const int q = warp & 3;               // TMEM lane quarter this warp may access
+        const uint32_t lead_tempty = gemm_map_peer(tempty, 0);
+        int seg = 0;
+        long long w = w0;
+        while (w < w1) {
+            const int t = (int)(w / kblocks);
+            const long long wend = min(w1, (long long)(t + 1) * kblocks);
+            const int acc = seg & 1;
+            if (!mbar_wait_cluster(&tfull[acc], (uint32_t)(seg >> 1) & 1u, budget)) {
+                set_error(ctrl, ERR_TIMEOUT);
+                break;
+            }
+            tc_fence_after();
+            float* dst = ws + ((size_t)blockIdx.x * smax + seg) * (size_t)GM_BN * GM_BM;
+            for (int c0 = 0; c0 < nb; c0 += 32) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * GM_BN + c0), v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) dst[(size_t)(c0 + j) * GM_BM + q * 32 + lane] = v[j];
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                if (lead)
+                    mbar_arrive(&tempty[acc]);
+                else
+                    gemm_arrive_remote(lead_tempty + (uint32_t)(acc * 8));
+            }
+            w = wend;
+            ++seg;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    gemm_cluster_sync();   // neither block leaves while the pair's MMAs or arrivals may touch it
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(GM_TMEM_COLS)
                      : "memory");
     }
@@ -403,25 +714,44 @@ __global__ void k_split_rows(const float* __restrict__ v, int len, int ld,
     }
 }
 
-// A (m x N binary32) -> A^T hi/lo planes (N x ldt bf16), 32 x 32 tiles.
-__global__ void k_transpose_split(const float* __restrict__ A, int m, int N,
-                                  __nv_bfloat16* __restrict__ th, __nv_bfloat16* __restrict__ tl,
-                                  int ldt)
+// Tile-contiguous bf16 planes of the operand X of a batched GEMM: X = A
+// (trans = 0, m x N) or X = A^T (trans = 1, N x m), both from A's hi and lo
+// planes (m x N, row-major).  Tile (t, kb) of X -- rows [128 t, 128 t + 128),
+// columns [64 kb, 64 kb + 64) -- is stored as 128 rows of 64 values (16 KB, one
+// TMA box read from contiguous memory) at tile index t * kblocks + kb; entries
+// past X's edge are zero.  One block per tile.
+__global__ void __launch_bounds__(256) k_tile_planes(const unsigned short* __restrict__ Ph,
+                                                     const unsigned short* __restrict__ Pl, int m,
+                                                     int N, int trans, unsigned short* __restrict__ Th,
+                                                     unsigned short* __restrict__ Tl, int kblocks)
 {
-    __shared__ float tile[32][33];
-    const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const int i = i0 + k, j = j0 + threadIdx.x;
-        tile[k][threadIdx.x] = (i < m && j < N) ? A[(size_t)i * N + j] : 0.f;
-    }
-    __syncthreads();
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const int j = j0 + k, i = i0 + threadIdx.x;
-        if (j < N && i < ldt) {
-            const float x = i < m ? tile[threadIdx.x][k] : 0.f;
-            const __nv_bfloat16 h = __float2bfloat16_rn(x);
-            th[(size_t)j * ldt + i] = h;
-            tl[(size_t)j * ldt + i] = __float2bfloat16_rn(x - __bfloat162float(h));
+    __shared__ unsigned short sh[2][GM_BK][GM_BM + 2];   // [plane][column of X][row of X]
+    const int tile = blockIdx.x;
+    const int t = tile / kblocks, kb = tile - t * kblocks;
+    const size_t out = (size_t)tile * GM_BM * GM_BK;
+    if (!trans) {   // X row 128 t + r is A row 128 t + r: 128-byte pieces, copied as they are
+        for (int i = threadIdx.x; i < GM_BM * GM_BK; i += blockDim.x) {
+            const int r = i / GM_BK, c = i - r * GM_BK;
+            const int R = t * GM_BM + r, C = kb * GM_BK + c;
+            const bool in = R < m && C < N;
+            const size_t src = (size_t)R * N + C;
+            Th[out + i] = in ? Ph[src] : (unsigned short)0;
+            Tl[out + i] = in ? Pl[src] : (unsigned short)0;
+        }
+    } else {        // X[128 t + r][64 kb + c] = A[64 kb + c][128 t + r]: through shared memory
+        for (int i = threadIdx.x; i < GM_BK * GM_BM; i += blockDim.x) {
+            const int c = i / GM_BM, r = i - c * GM_BM;
+            const int R = kb * GM_BK + c, C = t * GM_BM + r;   // A's row and column
+            const bool in = R < m && C < N;
+            const size_t src = (size_t)R * N + C;
+            sh[0][c][r] = in ? Ph[src] : (unsigned short)0;
+            sh[1][c][r] = in ? Pl[src] : (unsigned short)0;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < GM_BM * GM_BK; i += blockDim.x) {
+            const int r = i / GM_BK, c = i - r * GM_BK;
+            Th[out + i] = sh[0][c][r];
+            Tl[out + i] = sh[1][c][r];
         }
     }
 }
@@ -463,22 +793,32 @@ bool make_bf16_map(CUtensorMap* map, const void* base, int inner, int rows, int 
            CUDA_SUCCESS;
 }
 
-void gemm_plan(int M, int K, int num_sms, GemmPlan* p)
+void gemm_plan(int M, int K, int grid, GemmPlan* p, bool pair)
 {
+    p->pair = pair ? 1 : 0;
     p->tiles_m = (M + GM_BM - 1) / GM_BM;
+    p->tiles = pair ? (M + 2 * GM_BM - 1) / (2 * GM_BM) : p->tiles_m;
     p->kblocks = (K + GM_BK - 1) / GM_BK;
-    const long long W = (long long)p->tiles_m * p->kblocks;
-    p->grid = (int)(W < num_sms ? W : num_sms);
-    // segments of each block and, per tile, its (block, segment) slots in K order
-    std::vector<std::vector<int>> per_tile(p->tiles_m);
+    const long long W = (long long)p->tiles * p->kblocks;
+    long long units = pair ? grid / 2 : grid;   // blocks, or pairs of blocks
+    if (units > W) units = W;
+    if (units < 1) units = 1;
+    p->grid = (int)(pair ? 2 * units : units);
+    // segments of each unit and, per 128-row tile, its (block, segment) slots in K order
+    std::vector<std::vector<long long>> per_tile(p->tiles_m);
     int smax = 1;
-    for (int c = 0; c < p->grid; ++c) {
-        const long long w0 = W * c / p->grid, w1 = W * (c + 1) / p->grid;
+    for (long long c = 0; c < units; ++c) {
+        const long long w0 = W * c / units, w1 = W * (c + 1) / units;
         int j = 0;
         long long w = w0;
         while (w < w1) {
             const int t = (int)(w / p->kblocks);
-            per_tile[t].push_back(c * 1000000 + j);   // decoded below once smax is known
+            if (pair) {   // the even block holds rows [0, 128) of the pair's tile, the odd one the rest
+                per_tile[2 * t].push_back((2 * c) * 1000000 + j);
+                if (2 * t + 1 < p->tiles_m) per_tile[2 * t + 1].push_back((2 * c + 1) * 1000000 + j);
+            } else {
+                per_tile[t].push_back(c * 1000000 + j);
+            }
             w = std::min(w1, (long long)(t + 1) * p->kblocks);
             ++j;
         }
@@ -489,7 +829,8 @@ void gemm_plan(int M, int K, int num_sms, GemmPlan* p)
     p->seg_slot.clear();
     for (int t = 0; t < p->tiles_m; ++t) {
         p->tile_seg_begin[t] = (int)p->seg_slot.size();
-        for (int code : per_tile[t]) p->seg_slot.push_back((code / 1000000) * smax + code % 1000000);
+        for (long long code : per_tile[t])
+            p->seg_slot.push_back((int)((code / 1000000) * smax + code % 1000000));
     }
     p->tile_seg_begin[p->tiles_m] = (int)p->seg_slot.size();
     p->ws_floats = (size_t)p->grid * smax * GM_BN * GM_BM;
@@ -497,16 +838,37 @@ void gemm_plan(int M, int K, int num_sms, GemmPlan* p)
 
 cudaError_t gemm_configure()
 {
-    return cudaFuncSetAttribute(k_gemm_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)GM_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)GM_SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_gemm_bf16x3_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)GP_SMEM);
+}
+
+int gemm_pair_max_clusters(int num_sms)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(num_sms & ~1), 1, 1);
+    cfg.blockDim = dim3(192, 1, 1);
+    cfg.dynamicSmemBytes = GP_SMEM;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, (const void*)k_gemm_bf16x3_pair, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
 }
 
 void launch_gemm(const CUtensorMap* xh, const CUtensorMap* xl, const CUtensorMap* yh,
                  const CUtensorMap* yl, const GemmPlan& p, float* ws, Ctrl* ctrl, int check_skip,
                  long long budget, cudaStream_t s, int ncols, const int* nact)
 {
-    k_gemm_bf16x3<<<p.grid, 192, GM_SMEM, s>>>(*xh, *xl, *yh, *yl, p.tiles_m, p.kblocks, ws,
-                                               p.smax, ctrl, check_skip, budget, ncols, nact);
+    if (p.pair)
+        k_gemm_bf16x3_pair<<<p.grid, 192, GP_SMEM, s>>>(*xh, *xl, *yh, *yl, p.tiles, p.kblocks, ws,
+                                                        p.smax, ctrl, check_skip, budget, ncols, nact);
+    else
+        k_gemm_bf16x3<<<p.grid, 192, GM_SMEM, s>>>(*xh, *xl, *yh, *yl, p.tiles, p.kblocks, ws,
+                                                   p.smax, ctrl, check_skip, budget, ncols, nact);
 }
 
 void launch_gemm_fixup(const float* ws, const int* tile_seg_begin, const int* seg_slot, int M,
@@ -529,12 +891,12 @@ void launch_split_rows(const float* v, int count, int len, int ld, void* hi, voi
                                       reinterpret_cast<__nv_bfloat16*>(lo), ldh);
 }
 
-void launch_transpose_split(const float* A, int m, int N, void* th, void* tl, int ldt,
-                            cudaStream_t s)
+void launch_tile_planes(const void* Ph, const void* Pl, int m, int N, int trans, void* Th,
+                        void* Tl, int tiles_m, int kblocks, cudaStream_t s)
 {
-    dim3 grid((N + 31) / 32, (ldt + 31) / 32);
-    k_transpose_split<<<grid, dim3(32, 8), 0, s>>>(A, m, N, reinterpret_cast<__nv_bfloat16*>(th),
-                                                   reinterpret_cast<__nv_bfloat16*>(tl), ldt);
+    k_tile_planes<<<tiles_m * kblocks, 256, 0, s>>>(
+        static_cast<const unsigned short*>(Ph), static_cast<const unsigned short*>(Pl), m, N, trans,
+        static_cast<unsigned short*>(Th), static_cast<unsigned short*>(Tl), kblocks);
 }
 
 }  // namespace tvcs

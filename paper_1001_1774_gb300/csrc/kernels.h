@@ -113,13 +113,20 @@ void launch_quant_fp8(const float* A, int m, int N, void* q, void* c, float* sca
 
 // Batched products as tcgen05 BF16x3 GEMMs with stream-K scheduling (k_gemm.cu).
 struct GemmPlan {
-    int tiles_m = 0, kblocks = 0, grid = 0, smax = 1;
+    int tiles_m = 0, kblocks = 0, grid = 0, smax = 1;   // tiles_m: 128-row tiles of the fix-up
+    int pair = 0;    // 1: CTA pairs (k_gemm_bf16x3_pair) on 256-row tiles
+    int tiles = 0;   // the kernel's tiles (128 or 256 rows)
     std::vector<int> tile_seg_begin;   // tiles_m + 1 offsets into seg_slot
     std::vector<int> seg_slot;         // workspace slot of each segment, per tile in K order
     size_t ws_floats = 0;
 };
-void gemm_plan(int M, int K, int num_sms, GemmPlan* p);
+// grid: blocks of the launch (pair: rounded down to whole pairs); every plan
+// covers W = tiles x kblocks with at most W units (blocks or pairs).
+void gemm_plan(int M, int K, int grid, GemmPlan* p, bool pair = false);
 cudaError_t gemm_configure();
+// Clusters of two GEMM blocks that fit on the device at once (0: the pair
+// kernel cannot run).
+int gemm_pair_max_clusters(int num_sms);
 bool make_bf16_map(CUtensorMap* map, const void* base, int inner, int rows, int ld, int box_rows);
 // The Y operand's tensor maps use boxes of GEMM_Y_BOX rows.  ncols: columns
 // (images) of Y; nact (nullable): the number of leading columns that take part,
@@ -138,8 +145,11 @@ void launch_gemm_fixup(const float* ws, const int* tile_seg_begin, const int* se
                        const int* nact = nullptr);
 void launch_split_rows(const float* v, int count, int len, int ld, void* hi, void* lo, int ldh,
                        cudaStream_t s);
-void launch_transpose_split(const float* A, int m, int N, void* th, void* tl, int ldt,
-                            cudaStream_t s);
+// Tile-contiguous hi/lo planes of X = A (trans 0) or A^T (trans 1) for the
+// batched GEMMs, from A's planes Ph/Pl (m x N): tiles_m x kblocks tiles of
+// 128 x 64, tile (t, kb) at index t * kblocks + kb (k_gemm.cu).
+void launch_tile_planes(const void* Ph, const void* Pl, int m, int N, int trans, void* Th,
+                        void* Tl, int tiles_m, int kblocks, cudaStream_t s);
 
 // Products with A regenerated inside the kernel (k_regen.cu): r = A x - y and
 // g = A^T r for many problems of different sizes in one persistent launch.

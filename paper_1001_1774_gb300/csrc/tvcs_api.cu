@@ -994,6 +994,37 @@ tvcs_status tvcs_test_hold_grid_barrier(tvcs_handle h, int extra)
     return TVCS_OK;
 }
 
+tvcs_status tvcs_test_gemm_shape(tvcs_handle h, int grid1, int pair1, int grid2, int pair2)
+{
+    CKS(check_handle(h));
+    if (grid1 < 0 || grid2 < 0 || (grid1 == 0) != (grid2 == 0))
+        return fail(TVCS_ERR_INVALID_ARG, "grids must both be > 0, or both 0 (the tuner decides)");
+    if (grid1 > 0) {
+        CK(tvcs::gemm_configure());
+        const int pc = std::min(tvcs::gemm_pair_max_clusters(h->num_sms), h->num_sms / 2);
+        const int grid[2] = {grid1, grid2}, pair[2] = {pair1, pair2};
+        for (int i = 0; i < 2; ++i) {
+            if (pair[i] != 0 && pair[i] != 1) return fail(TVCS_ERR_INVALID_ARG, "pair must be 0 or 1");
+            if (pair[i] && grid[i] % 2 != 0)
+                return fail(TVCS_ERR_INVALID_ARG, "a grid of pairs is an even number of blocks");
+            if (pair[i] && grid[i] / 2 > pc)
+                return fail(TVCS_ERR_UNSUPPORTED, "%d pairs requested, %d fit on the device", grid[i] / 2,
+                            pc);
+            if (!pair[i] && grid[i] > h->num_sms)
+                return fail(TVCS_ERR_INVALID_ARG, "at most %d persistent blocks", h->num_sms);
+        }
+    }
+    h->gemm_force[0] = grid1;
+    h->gemm_force[1] = grid1 > 0 ? pair1 : 0;
+    h->gemm_force[2] = grid2;
+    h->gemm_force[3] = grid2 > 0 ? pair2 : 0;
+    if (h->batch) {   // the next batched call re-plans and resizes the workspace
+        h->batch->tuned = false;
+        h->batch->cap = 0;
+    }
+    return TVCS_OK;
+}
+
 tvcs_status tvcs_apply(tvcs_handle h, const float* x, const float* y, float* r, float* g)
 {
     CKS(check_handle(h));

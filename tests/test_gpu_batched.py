@@ -75,18 +75,10 @@ def bf16_handle(tv, A, m, n, mu=1.0, beta=10.0, tau=0.1, max_iter=50, tol=0.0):
     return tv.tvcs_create(torch.from_numpy(A).cuda(), 0, m, n, mu, beta, tol, opt)
 
 
-@pytest.mark.parametrize("n,m,count", [(32, 307, 1), (32, 307, 7), (32, 300, 256), (64, 1229, 40),
-                                       (128, 4915, 64)])
-def test_batched_products(tv, n, m, count):
-    N = n * n
-    A = synth.gaussian_matrix(70 + n, m, N)
-    rng = np.random.default_rng(count + n)
-    X = rng.standard_normal((count, N)).astype(np.float32)
-    Y = rng.standard_normal((count, m)).astype(np.float32)
-    h = bf16_handle(tv, A, m, n)
-    R = np.empty((count, m), np.float32)
-    G = np.empty((count, N), np.float32)
-    tv.tvcs_apply_batched(h, count, X, Y, R, G)
+def check_batched_products(A, X, Y, R, G, rng):
+    """R = A X - Y and G = A^T R against the split products formed in binary64."""
+    count, N = X.shape
+    m = A.shape[0]
     Ah, Al = quant_ref.split_bf16x2(A)
     Xh, Xl = quant_ref.split_bf16x2(X)
     # rows of A checked: all for small m, a seeded sample for the full-size case
@@ -102,7 +94,106 @@ def test_batched_products(tv, n, m, count):
     Gref = bf16x3(Th[cols], Tl[cols], Rh, Rl).T
     gscale = np.abs(Aeff.T[cols].astype(np.float64)) @ np.abs(R.astype(np.float64)).T
     assert np.all(np.abs(G[:, cols].astype(np.float64) - Gref) <= 1e-5 * gscale.T + 1e-30)
+
+
+@pytest.mark.parametrize("n,m,count", [(32, 307, 1), (32, 307, 7), (32, 300, 256), (64, 1229, 40),
+                                       (128, 4915, 64)])
+def test_batched_products(tv, n, m, count):
+    N = n * n
+    A = synth.gaussian_matrix(70 + n, m, N)
+    rng = np.random.default_rng(count + n)
+    X = rng.standard_normal((count, N)).astype(np.float32)
+    Y = rng.standard_normal((count, m)).astype(np.float32)
+    h = bf16_handle(tv, A, m, n)
+    R = np.empty((count, m), np.float32)
+    G = np.empty((count, N), np.float32)
+    tv.tvcs_apply_batched(h, count, X, Y, R, G)
+    check_batched_products(A, X, Y, R, G, rng)
     tv.tvcs_destroy(h)
+
+
+def set_pair_shape(tv, h, pairs):
+    """Both GEMMs on CTA pairs: the first of `pairs` (pairs of blocks) that fits."""
+    for p in pairs:
+        try:
+            tv.tvcs_test_gemm_shape(h, 2 * p, 1, 2 * p, 1)
+            return p
+        except tv.TvcsError as e:
+            assert e.status == tv.TVCS_ERR_UNSUPPORTED
+    pytest.fail("no pair shape fits")
+
+
+# M = m rows in 256-row pair tiles: m = 307 leaves the odd block of the last
+# tile wholly past the matrix; 40 and 200 images give each block of a pair
+# 32 and 112 of the running columns (a 64-row box that reaches into the other
+# block's half or past the images); one to three pairs walk several tiles each,
+# so both accumulators are reused; n = 128 is the full-size operand.
+@pytest.mark.parametrize("n,m,count,pairs", [(32, 307, 7, (76, 72, 64)), (32, 307, 7, (1,)),
+                                             (64, 1229, 40, (76, 72, 64)), (64, 1229, 200, (3,)),
+                                             (128, 4915, 256, (76, 72, 64))])
+def test_gemm_on_cta_pairs(tv, n, m, count, pairs):
+    # The GEMMs on clusters of two blocks that share each 256-row tile
+    # (tcgen05 cta_group::2): the same checks as the single-block kernel against
+    # the split products in binary64 (1e-5 of the absolute sums), and agreement with
+    # the single-block shape within the same bound: a different stream-K split
+    # regroups binary32 sums of up to K = m or n^2 terms (whole-K tiles against
+    # tiles split over several blocks), which is not bitwise.
+    N = n * n
+    A = synth.gaussian_matrix(90 + n, m, N)
+    rng = np.random.default_rng(count + 3 * n)
+    X = rng.standard_normal((count, N)).astype(np.float32)
+    Y = rng.standard_normal((count, m)).astype(np.float32)
+    out = []
+    for pair in (1, 0):
+        h = bf16_handle(tv, A, m, n)
+        if pair:
+            p = set_pair_shape(tv, h, pairs)
+            print("pairs", p)
+        else:
+            tv.tvcs_test_gemm_shape(h, 152 if n > 32 else 64, 0, 152 if n > 32 else 64, 0)
+        R = np.empty((count, m), np.float32)
+        G = np.empty((count, N), np.float32)
+        tv.tvcs_apply_batched(h, count, X, Y, R, G)
+        out.append((R, G))
+        tv.tvcs_destroy(h)
+    (R1, G1), (R0, G0) = out
+    check_batched_products(A, X, Y, R1, G1, rng)
+    A64 = np.abs(A.astype(np.float64))
+    dr = np.max(np.abs(R1.astype(np.float64) - R0) / (np.abs(X.astype(np.float64)) @ A64.T + 1e-30))
+    dg = np.max(np.abs(G1.astype(np.float64) - G0) / (np.abs(R0.astype(np.float64)) @ A64 + 1e-30))
+    print("pair vs single shape, of the absolute sums: R %.2e, G %.2e" % (dr, dg))
+    assert dr <= 1e-5 and dg <= 1e-5
+
+
+def test_gemm_pair_shape_solves_and_rejects_bad_shapes(tv):
+    # 20-iteration batched solves with both GEMMs on CTA pairs agree with the
+    # single-block shape to the parity tolerance 1e-5; malformed shapes are refused.
+    n, m, count = 64, 1229, 48
+    N = n * n
+    A = synth.gaussian_matrix(78, m, N)
+    rng = np.random.default_rng(9)
+    F = rng.standard_normal((count, m)).astype(np.float32)
+    res = []
+    for pair in (1, 0):
+        h = bf16_handle(tv, A, m, n, mu=1e3, max_iter=20)
+        if pair:
+            set_pair_shape(tv, h, (76, 72, 64))
+        else:
+            tv.tvcs_test_gemm_shape(h, 152, 0, 152, 0)
+        us = [np.empty(N, np.float32) for _ in range(count)]
+        tv.tvcs_solve_batched([h] * count, [np.ascontiguousarray(F[b]) for b in range(count)], us)
+        res.append(us)
+        if pair:
+            for bad in ((3, 1, 4, 1), (4, 2, 4, 1), (-1, 0, 4, 0), (4, 0, 0, 0), (100000, 0, 4, 0)):
+                with pytest.raises(tv.TvcsError) as ei:
+                    tv.tvcs_test_gemm_shape(h, *bad)
+                assert ei.value.status == tv.TVCS_ERR_INVALID_ARG, bad
+            with pytest.raises(tv.TvcsError) as ei:
+                tv.tvcs_test_gemm_shape(h, 2 * 100000, 1, 4, 0)
+            assert ei.value.status in (tv.TVCS_ERR_UNSUPPORTED, tv.TVCS_ERR_INVALID_ARG)
+        tv.tvcs_destroy(h)
+    for b in range(count):
+        assert rel(res[0][b], res[1][b]) <= 1e-5, b
 
 
 def test_batched_solve_matches_oracle_and_single_image(tv):
