@@ -61,7 +61,7 @@ def parse_args():
                          "products: the product kernel alone for --n, --m, --precision (A generated "
                          "on the device), --steps back-to-back launches (for profiler captures)")
     ap.add_argument("--images", type=int, default=256,
-                    help="images of --workload batch256 (more than 256 run in groups of at most 256)")
+                    help="images of --workload batch256 (one group up to 512; more run in groups of at most 512)")
     ap.add_argument("--n", type=int, default=256, help="image side of --workload products")
     ap.add_argument("--m", type=int, default=13107, help="measurements of --workload products")
     ap.add_argument("--algo", choices=["iadm", "ftvcs"], default="iadm",
@@ -558,9 +558,9 @@ def batch_segment(tv, steps, warmup, stream, want_parity=True, images=256):
     tv.tvcs_solve_batched([h] * B, [F_host[b] for b in range(B)], [U_host[b] for b in range(B)], mus)
     e2e_s = time.perf_counter() - t0
     tv.tvcs_destroy(h)
-    # more than 256 images run in groups of nearly equal size, the smaller ones last:
+    # more than 512 images run in groups of nearly equal size, the smaller ones last:
     # the stage timings above are of the last group
-    groups = -(-B // 256)
+    groups = -(-B // 512)
     last = B // groups
     flops = 2 * 3 * 2.0 * m * N * last               # two GEMMs, three bf16 terms each
     peak = bf16_peak()

@@ -256,8 +256,9 @@ tvcs_status tvcs_time_stage(tvcs_handle h, int stage, int reps, double* ms);
  * hi+lo splits of A and of the operands (X_hi A_hi + X_lo A_hi + X_hi A_lo,
  * binary32 accumulation).  X: count x n*n, Y: count x m (nullable), R: count x m,
  * G: count x n*n, image after image, host or device.  Requires a handle created
- * with precision TVCS_PREC_BF16X2, n*n a multiple of 128 and count >= 1 (more
- * than 256 images run in groups of at most 256). */
+ * with precision TVCS_PREC_BF16X2, n*n a multiple of 128 and count >= 1 (groups
+ * as in tvcs_solve_batched: at most 512 images each, 256 where clusters of two
+ * GEMM blocks cannot run). */
 tvcs_status tvcs_apply_batched(tvcs_handle h, int count, const float* X, const float* Y,
                                float* R, float* G);
 
@@ -279,7 +280,9 @@ tvcs_status tvcs_test_hold_grid_barrier(tvcs_handle h, int extra);
  * single blocks (pair 0, grid <= SM count) or on clusters of two blocks that
  * share each 256-row tile (pair 1, grid even, grid/2 <= the clusters that fit).
  * grid1 = grid2 = 0 returns the choice to the tuner (opt->autotune) or to one
- * block per SM.  Takes effect at the next batched call, which re-plans the
+ * block per SM.  Above 256 images a batch needs pair = 1 (two N tiles of 256
+ * columns per tile of A), else the batched call returns TVCS_ERR_INVALID_ARG.
+ * Takes effect at the next batched call, which re-plans the
  * stream-K split and rebuilds the batch buffers.  Results of different shapes
  * agree to binary32 rounding (a tile's K sums are grouped differently), not
  * bitwise.  TVCS_ERR_INVALID_ARG for a malformed shape, TVCS_ERR_UNSUPPORTED

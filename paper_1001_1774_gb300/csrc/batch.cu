@@ -27,7 +27,7 @@
 namespace tvcs {
 
 // Continue while any image runs and the loop bound holds.  With slot tables
-// (count <= blockDim.x = 256): the running images, in image order, take slots
+// (count <= blockDim.x = BATCH_MAX): the running images, in image order, take slots
 // 0 .. nact-1 for the next iteration (a block-wide exclusive prefix sum of the
 // running flags); an image that stopped gets slot -1.
 __global__ void k_batch_cond(const Ctrl* __restrict__ ctrls, int count, Ctrl* __restrict__ bctrl,
@@ -35,7 +35,7 @@ __global__ void k_batch_cond(const Ctrl* __restrict__ ctrls, int count, Ctrl* __
                              int* __restrict__ slot_img, int* __restrict__ img_slot)
 {
     __shared__ int any;
-    __shared__ int wtot[8];
+    __shared__ int wtot[BATCH_MAX / 32];
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
     for (int b = threadIdx.x; b < count; b += blockDim.x)
@@ -71,8 +71,8 @@ __global__ void k_batch_cond(const Ctrl* __restrict__ ctrls, int count, Ctrl* __
 void launch_batch_cond(const Ctrl* ctrls, int count, Ctrl* bctrl, unsigned long long cond,
                        int set_cond, cudaStream_t s, int* slot_img, int* img_slot)
 {
-    k_batch_cond<<<1, 256, 0, s>>>(ctrls, count, bctrl, (cudaGraphConditionalHandle)cond, set_cond,
-                                   slot_img, img_slot);
+    k_batch_cond<<<1, BATCH_MAX, 0, s>>>(ctrls, count, bctrl, (cudaGraphConditionalHandle)cond,
+                                         set_cond, slot_img, img_slot);
 }
 
 // End-of-run residual of every image, r_b = A_eff u_b - f_b with A_eff = hi + lo
@@ -311,6 +311,9 @@ tvcs_status make_maps(tvcs_ctx* h, int count)
     return TVCS_OK;
 }
 
+// N tiles of 256 images per X tile of the GEMMs: two above 256 images.
+int gemm_nt(int count) { return count > 256 ? 2 : 1; }
+
 // Launch shapes the GEMM tuner tries: one block per SM and 7/8, 3/4, 1/2 of
 // that, on single blocks and (where the device holds clusters of two of them)
 // on CTA pairs.
@@ -318,10 +321,11 @@ struct GemmShape {
     int grid = 0, pair = 0;
 };
 
-std::vector<GemmShape> gemm_shape_candidates(int num_sms, int pair_clusters)
+std::vector<GemmShape> gemm_shape_candidates(int num_sms, int pair_clusters, int nt)
 {
     std::vector<GemmShape> v;
-    for (int g : {num_sms, num_sms * 7 / 8, num_sms * 3 / 4, num_sms / 2}) v.push_back({g, 0});
+    if (nt == 1)   // the single-block kernel takes at most 256 images
+        for (int g : {num_sms, num_sms * 7 / 8, num_sms * 3 / 4, num_sms / 2}) v.push_back({g, 0});
     const int pc = std::min(pair_clusters, num_sms / 2);
     if (pc > 0)
         for (int c : {pc, pc * 7 / 8, pc * 3 / 4, pc / 2})
@@ -330,7 +334,7 @@ std::vector<GemmShape> gemm_shape_candidates(int num_sms, int pair_clusters)
 }
 
 std::mutex g_gemm_tune_mutex;
-std::map<std::tuple<int, int, int>, std::pair<GemmShape, GemmShape>> g_gemm_shapes;   // (device, m, N)
+std::map<std::tuple<int, int, int, int>, std::pair<GemmShape, GemmShape>> g_gemm_shapes;   // (device, m, N, nt)
 
 // Picks the launch shape of each GEMM (persistent blocks or pairs, and with it
 // the stream-K split of its tiles x K-blocks) by timing every candidate, GEMM
@@ -343,15 +347,21 @@ tvcs_status tune_gemms(tvcs_ctx* h, int count)
 {
     tvcs_batch* b = h->batch;
     cudaStream_t s = h->stream;
-    GemmShape g1{h->num_sms, 0}, g2{h->num_sms, 0};
+    const int nt = gemm_nt(count);
+    const GemmShape dflt = nt == 1 ? GemmShape{h->num_sms, 0}
+                                   : GemmShape{2 * std::min(b->pair_clusters, h->num_sms / 2), 1};
+    GemmShape g1 = dflt, g2 = dflt;
     if (h->gemm_force[0] > 0) {
         g1 = {h->gemm_force[0], h->gemm_force[1]};
         g2 = {h->gemm_force[2], h->gemm_force[3]};
+        if (nt == 2 && (!g1.pair || !g2.pair))
+            return set_last_error(TVCS_ERR_INVALID_ARG,
+                                  "more than 256 images need the GEMMs on CTA pairs (tvcs_test_gemm_shape)");
     } else if (h->opt.autotune) {
         bool cached = false;
         {
             std::lock_guard<std::mutex> lk(g_gemm_tune_mutex);
-            auto it = g_gemm_shapes.find({h->dev, h->m, h->N});
+            auto it = g_gemm_shapes.find({h->dev, h->m, h->N, nt});
             if (it != g_gemm_shapes.end()) {
                 g1 = it->second.first;
                 g2 = it->second.second;
@@ -363,9 +373,9 @@ tvcs_status tune_gemms(tvcs_ctx* h, int count)
             for (int which = 0; which < 2; ++which) {
                 const int M = which == 0 ? h->m : h->N, K = which == 0 ? h->N : h->m;
                 float best = -1.f;
-                for (GemmShape g : gemm_shape_candidates(h->num_sms, b->pair_clusters)) {
+                for (GemmShape g : gemm_shape_candidates(h->num_sms, b->pair_clusters, nt)) {
                     GemmPlan p;
-                    gemm_plan(M, K, g.grid, &p, g.pair != 0);
+                    gemm_plan(M, K, g.grid, &p, g.pair != 0, nt);
                     int *tsb = nullptr, *ss = nullptr;
                     BCKS(upload_plan(p, &tsb, &ss, s));
                     float t[5];
@@ -374,13 +384,13 @@ tvcs_status tune_gemms(tvcs_ctx* h, int count)
                         if (which == 0) {
                             launch_gemm(&b->mAh, &b->mAl, &b->mUh, &b->mUl, p, b->ws, b->bctrl, 0,
                                         budget, s, count);
-                            launch_gemm_fixup(b->ws, tsb, ss, h->m, p.tiles_m, count, b->F, h->m,
+                            launch_gemm_fixup(b->ws, tsb, ss, h->m, p.tiles_m, p.nt * 256, count, b->F, h->m,
                                               b->R, h->m, b->Rh, b->Rl, b->mpad, b->r2part, b->bctrl,
                                               0, s);
                         } else {
                             launch_gemm(&b->mAth, &b->mAtl, &b->mRh, &b->mRl, p, b->ws, b->bctrl, 0,
                                         budget, s, count);
-                            launch_gemm_fixup(b->ws, tsb, ss, h->N, p.tiles_m, count, nullptr, 0,
+                            launch_gemm_fixup(b->ws, tsb, ss, h->N, p.tiles_m, p.nt * 256, count, nullptr, 0,
                                               b->G, h->N, nullptr, nullptr, 0, nullptr, b->bctrl, 0,
                                               s);
                         }
@@ -401,14 +411,14 @@ tvcs_status tune_gemms(tvcs_ctx* h, int count)
                 }
             }
             std::lock_guard<std::mutex> lk(g_gemm_tune_mutex);
-            g_gemm_shapes[{h->dev, h->m, h->N}] = {g1, g2};
+            g_gemm_shapes[{h->dev, h->m, h->N, nt}] = {g1, g2};
         }
     }
     GemmPlan q1, q2;
-    gemm_plan(h->m, h->N, g1.grid, &q1, g1.pair != 0);
-    gemm_plan(h->N, h->m, g2.grid, &q2, g2.pair != 0);
-    if (q1.grid != b->p1.grid || q1.pair != b->p1.pair || q2.grid != b->p2.grid ||
-        q2.pair != b->p2.pair) {
+    gemm_plan(h->m, h->N, g1.grid, &q1, g1.pair != 0, nt);
+    gemm_plan(h->N, h->m, g2.grid, &q2, g2.pair != 0, nt);
+    if (q1.grid != b->p1.grid || q1.pair != b->p1.pair || q1.nt != b->p1.nt ||
+        q2.grid != b->p2.grid || q2.pair != b->p2.pair || q2.nt != b->p2.nt) {
         cudaFree(b->tsb1);
         cudaFree(b->ss1);
         cudaFree(b->tsb2);
@@ -430,8 +440,8 @@ tvcs_status ensure_batch(tvcs_ctx* h, int count)
         return set_last_error(TVCS_ERR_UNSUPPORTED,
                               "the shared-A batched path needs A stored as bf16 hi+lo "
                               "(precision TVCS_PREC_BF16X2)");
-    if (count > BATCH_MAX)
-        return set_last_error(TVCS_ERR_INVALID_ARG, "at most %d images per batch", BATCH_MAX);
+    if (count > batch_max(h))
+        return set_last_error(TVCS_ERR_INVALID_ARG, "at most %d images per batch", batch_max(h));
     if (h->N % 128 != 0)
         return set_last_error(TVCS_ERR_UNSUPPORTED, "batched path needs n*n a multiple of 128");
     if (!h->batch) {
@@ -454,7 +464,7 @@ tvcs_status ensure_batch(tvcs_ctx* h, int count)
         // one contiguous 16 KB block in HBM)
         b->mpad = (int)((m + 7) / 8 * 8);
         BCK(gemm_configure());
-        b->pair_clusters = gemm_pair_max_clusters(h->num_sms);
+        b->pair_clusters = std::min(batch_pair_clusters(h), h->num_sms / 2);
         b->tiles1 = (int)((m + 127) / 128);
         b->kb1 = (int)((N + 63) / 64);
         b->tiles2 = (int)((N + 127) / 128);
@@ -482,16 +492,18 @@ tvcs_status ensure_batch(tvcs_ctx* h, int count)
         BCKS(upload_plan(b->p2, &b->tsb2, &b->ss2, s));
         // the workspace holds the partial tiles of every candidate shape the tuner may pick
         size_t wsf = 0;
-        std::vector<GemmShape> shapes = gemm_shape_candidates(h->num_sms, b->pair_clusters);
-        if (h->gemm_force[0] > 0) {
-            shapes.push_back({h->gemm_force[0], h->gemm_force[1]});
-            shapes.push_back({h->gemm_force[2], h->gemm_force[3]});
-        }
-        for (GemmShape g : shapes) {
-            GemmPlan q1, q2;
-            gemm_plan(h->m, h->N, g.grid, &q1, g.pair != 0);
-            gemm_plan(h->N, h->m, g.grid, &q2, g.pair != 0);
-            wsf = std::max(wsf, std::max(q1.ws_floats, q2.ws_floats));
+        for (int nt = 1; nt <= gemm_nt(count); ++nt) {
+            std::vector<GemmShape> shapes = gemm_shape_candidates(h->num_sms, b->pair_clusters, nt);
+            if (h->gemm_force[0] > 0) {
+                shapes.push_back({h->gemm_force[0], h->gemm_force[1]});
+                shapes.push_back({h->gemm_force[2], h->gemm_force[3]});
+            }
+            for (GemmShape g : shapes) {
+                GemmPlan q1, q2;
+                gemm_plan(h->m, h->N, g.grid, &q1, g.pair != 0, nt);
+                gemm_plan(h->N, h->m, g.grid, &q2, g.pair != 0, nt);
+                wsf = std::max(wsf, std::max(q1.ws_floats, q2.ws_floats));
+            }
         }
         BCKS(balloc((void**)&b->ws, sizeof(float) * wsf));
         BCKS(balloc((void**)&b->U, sizeof(float) * B * N));
@@ -529,6 +541,7 @@ tvcs_status ensure_batch(tvcs_ctx* h, int count)
     }
     b->last_count = count;
     BCKS(make_maps(h, count));
+    if (b->p1.nt != gemm_nt(count)) b->tuned = false;   // 256 or 512 columns per X tile
     if (!b->tuned) {
         BCKS(tune_gemms(h, count));
         b->tuned = true;
@@ -550,12 +563,12 @@ void batch_products(tvcs_ctx* h, int count, bool subtract_f, cudaStream_t s, boo
     const int chk = in_loop ? 1 : 0;
     launch_gemm(&b->mAh, &b->mAl, &b->mUh, &b->mUl, b->p1, b->ws, b->bctrl, chk, budget, s, count,
                 nact);
-    launch_gemm_fixup(b->ws, b->tsb1, b->ss1, h->m, b->p1.tiles_m, count,
+    launch_gemm_fixup(b->ws, b->tsb1, b->ss1, h->m, b->p1.tiles_m, b->p1.nt * 256, count,
                       subtract_f ? b->F : nullptr, h->m, b->R, h->m, b->Rh, b->Rl, b->mpad,
                       b->r2part, b->bctrl, chk, s, slot, nact);
     launch_gemm(&b->mAth, &b->mAtl, &b->mRh, &b->mRl, b->p2, b->ws, b->bctrl, chk, budget, s, count,
                 nact);
-    launch_gemm_fixup(b->ws, b->tsb2, b->ss2, h->N, b->p2.tiles_m, count, nullptr, 0, b->G, h->N,
+    launch_gemm_fixup(b->ws, b->tsb2, b->ss2, h->N, b->p2.tiles_m, b->p2.nt * 256, count, nullptr, 0, b->G, h->N,
                       nullptr, nullptr, 0, nullptr, b->bctrl, chk, s, slot, nact);
 }
 
@@ -637,6 +650,15 @@ tvcs_status build_batch_graph(tvcs_ctx* h, int count)
 
 }  // namespace
 
+int batch_pair_clusters(tvcs_ctx* h)
+{
+    if (h->pair_clusters < 0)
+        h->pair_clusters = gemm_configure() == cudaSuccess ? gemm_pair_max_clusters(h->num_sms) : 0;
+    return h->pair_clusters;
+}
+
+int batch_max(tvcs_ctx* h) { return batch_pair_clusters(h) > 0 ? BATCH_MAX : 256; }
+
 void free_batch(tvcs_ctx* h)
 {
     if (!h || !h->batch) return;
@@ -666,9 +688,9 @@ tvcs_status time_batch_stage(tvcs_ctx* h, int stage, int reps, double* ms)
             launch_gemm(&b->mAh, &b->mAl, &b->mUh, &b->mUl, b->p1, b->ws, b->bctrl, 0, budget, s, count);
             launch_gemm(&b->mAth, &b->mAtl, &b->mRh, &b->mRl, b->p2, b->ws, b->bctrl, 0, budget, s, count);
         } else if (stage == 4) {
-            launch_gemm_fixup(b->ws, b->tsb1, b->ss1, h->m, b->p1.tiles_m, count, b->F, h->m, b->R,
+            launch_gemm_fixup(b->ws, b->tsb1, b->ss1, h->m, b->p1.tiles_m, b->p1.nt * 256, count, b->F, h->m, b->R,
                               h->m, b->Rh, b->Rl, b->mpad, b->r2part, b->bctrl, 0, s);
-            launch_gemm_fixup(b->ws, b->tsb2, b->ss2, h->N, b->p2.tiles_m, count, nullptr, 0, b->G,
+            launch_gemm_fixup(b->ws, b->tsb2, b->ss2, h->N, b->p2.tiles_m, b->p2.nt * 256, count, nullptr, 0, b->G,
                               h->N, nullptr, nullptr, 0, nullptr, b->bctrl, 0, s);
         } else {
             batch_usolve(h, a, s);
@@ -745,7 +767,7 @@ tvcs_status solve_batch(tvcs_ctx* h, int count, const float* const* f, float* co
         launch_split_rows(b->F, count, h->m, h->m, b->Rh, b->Rl, b->mpad, s);
         const long long budget = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : (1LL << 31);
         launch_gemm(&b->mAth, &b->mAtl, &b->mRh, &b->mRl, b->p2, b->ws, b->bctrl, 0, budget, s, count);
-        launch_gemm_fixup(b->ws, b->tsb2, b->ss2, h->N, b->p2.tiles_m, count, nullptr, 0, b->U,
+        launch_gemm_fixup(b->ws, b->tsb2, b->ss2, h->N, b->p2.tiles_m, b->p2.nt * 256, count, nullptr, 0, b->U,
                           h->N, nullptr, nullptr, 0, nullptr, b->bctrl, 0, s);
     }
     launch_split_rows(b->U, count, h->N, h->N, b->Uh, b->Ul, h->N, s);

@@ -97,12 +97,18 @@ struct tvcs_ctx {
     tvcs_uneven* uneven = nullptr; // uneven batch whose first handle is this one
     int bar_extra = 0;             // timeout test hook (tvcs_test_hold_grid_barrier), else 0
     int gemm_force[4] = {0, 0, 0, 0};   // tvcs_test_gemm_shape: grid, pair of each batched GEMM (0: tuner)
+    int pair_clusters = -1;        // clusters of two GEMM blocks that fit (-1: not asked yet)
 };
 
 namespace tvcs {
 // Images one shared-A batch holds (one thread per image in the batch condition
-// kernel's slot tables); larger calls run in groups.
-constexpr int BATCH_MAX = 256;
+// kernel's slot tables); larger calls run in groups.  Above 256 images the GEMMs
+// need the CTA-pair kernel (two N tiles per X tile), so a device on which that
+// kernel cannot run holds 256 (batch_max).
+constexpr int BATCH_MAX = 512;
+int batch_max(tvcs_ctx* h);
+// Clusters of two GEMM blocks that fit on the handle's device (0: none).
+int batch_pair_clusters(tvcs_ctx* h);
 tvcs_status set_last_error(tvcs_status s, const char* fmt, ...);
 void free_batch(tvcs_ctx* h);
 // Many images with the handle's A (all handles of a tvcs_solve_batched call equal).

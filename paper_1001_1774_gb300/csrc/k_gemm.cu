@@ -46,7 +46,7 @@ constexpr int GM_BN = 256;
 constexpr int GM_NST = 2;
 constexpr uint32_t GM_A_BYTES = GM_BM * GM_BK * 2;            // 16 KB
 constexpr uint32_t GM_B_BYTES = GM_BN * GM_BK * 2;            // 32 KB
-constexpr uint32_t GM_YBOX_BYTES = GEMM_Y_BOX * GM_BK * 2;    // one 64-row box of a Y tile
+constexpr uint32_t GM_YBOX_BYTES = GEMM_Y_BOX * GM_BK * 2;    // one 32-row box of a Y tile (4 KB)
 constexpr uint32_t GM_STAGE = 2 * GM_A_BYTES + 2 * GM_B_BYTES; // 96 KB
 constexpr uint32_t GM_TMEM_COLS = 2 * GM_BN;                  // two accumulators
 constexpr size_t GM_SMEM = 1024 + GM_NST * GM_STAGE + 256;
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(192, 1)
                 const int xrow = (t * kblocks + kb) * GM_BM;   // tile-contiguous X (k_tile_planes)
                 tma_load_2d(st, &tXh, 0, xrow, &full[s], pol_x);
                 tma_load_2d(st + GM_A_BYTES, &tXl, 0, xrow, &full[s], pol_x);
-                for (int j = 0; j < ybox; ++j) {   // 64-row boxes, 1024-byte aligned
+                for (int j = 0; j < ybox; ++j) {   // 32-row boxes, 1024-byte aligned
                     tma_load_2d(st + 2 * GM_A_BYTES + j * GM_YBOX_BYTES, &tYh, kb * GM_BK,
                                 j * GEMM_Y_BOX, &full[s], pol_y);
                     tma_load_2d(st + 2 * GM_A_BYTES + GM_B_BYTES + j * GM_YBOX_BYTES, &tYl,
@@ -328,10 +328,19 @@ __global__ void __launch_bounds__(192, 1)
 // block c of the grid writes its partial tiles to ws + (c smax + j) BN 128, the
 // 128-row half tile 2 t + rank of the pair's tile t.
 // ---------------------------------------------------------------------------
-constexpr int GP_NST = 3;
-constexpr uint32_t GP_YH_BYTES = (GM_BN / 2) * GM_BK * 2;           // 16 KB: half a Y tile
-constexpr uint32_t GP_STAGE = 2 * GM_A_BYTES + 2 * GP_YH_BYTES;     // 64 KB
-constexpr size_t GP_SMEM = 1024 + GP_NST * GP_STAGE + 256;
+// NT: N tiles of 256 columns (images) per X tile, 1 or 2.  With two, TMEM holds
+// one accumulator per N tile (512 columns) and A is streamed once for up to 512
+// images.  A stage holds the X tile and this block's half of each N tile's
+// running columns in 32-row boxes, so its size follows the running images (64 KB
+// for 256, 72 KB for 300, 96 KB for 512), and the ring takes as many stages of
+// that size as 225 KB hold (at most six).
+constexpr uint32_t GP_RING_BYTES = 225 * 1024;
+constexpr int GP_NST_MAX = 6;
+constexpr size_t GP_SMEM = 1024 + GP_RING_BYTES + 256;
+template <int NT>
+struct PairCfg {
+    static constexpr int NSETS = 2 / NT;                              // accumulator sets in TMEM
+};
 
 __device__ __forceinline__ void tc_mma_pair(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
                                             uint32_t idesc, uint32_t accumulate)
@@ -410,6 +419,7 @@ __host__ __device__ constexpr uint32_t gemm_idesc_pair(int nb)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(nb >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
 }
 
+template <int NT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     k_gemm_bf16x3_pair(const __grid_constant__ CUtensorMap tXh, const __grid_constant__ CUtensorMap tXl,
                        const __grid_constant__ CUtensorMap tYh, const __grid_constant__ CUtensorMap tYl,
@@ -420,20 +430,32 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + GP_NST * GP_STAGE);
-    uint64_t* empty = full + GP_NST;
-    uint64_t* tfull = empty + GP_NST;    // [2] accumulator ready
-    uint64_t* tempty = tfull + 2;        // [2] accumulator drained (both blocks; used on the even one)
+    constexpr int NSETS = PairCfg<NT>::NSETS;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + GP_RING_BYTES);
+    uint64_t* empty = full + GP_NST_MAX;
+    uint64_t* tfull = empty + GP_NST_MAX;   // [NSETS] accumulator set ready
+    uint64_t* tempty = tfull + 2;        // [NSETS] accumulator set drained (both blocks; used on the even one)
     uint64_t* mdrain = tempty + 2;       // the issuer's MMAs have finished (after a timeout)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mdrain + 1);
 
     if (check_skip && ctrl->skip) return;   // the same for every block of the grid
-    int nb = min(ncols, GM_BN);
-    if (nact) nb = min(nb, *nact);
-    nb = min(GM_BN, max(32, (nb + 31) & ~31));
-    const int nbh = nb / 2;                                 // Y rows held by each block
-    const int ybox = (nbh + GEMM_Y_BOX - 1) / GEMM_Y_BOX;
-    const uint32_t stage_bytes = 2 * GM_A_BYTES + 2 * (uint32_t)ybox * GM_YBOX_BYTES;
+    int ntot = min(ncols, NT * GM_BN);      // running columns
+    if (nact) ntot = min(ntot, *nact);
+    // per N tile: MMA columns, Y rows per block, 32-row boxes, offset in a stage
+    int nbj[NT], nbh[NT], ybox[NT];
+    uint32_t yoff[NT];
+    uint32_t stage_bytes = 2 * GM_A_BYTES;   // a multiple of 4 KB: stages stay 1024-byte aligned
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+        const int rem = ntot - j * GM_BN;
+        nbj[j] = j == 0 ? min(GM_BN, max(32, (rem + 31) & ~31))
+                        : (rem > 0 ? min(GM_BN, (rem + 31) & ~31) : 0);
+        nbh[j] = nbj[j] / 2;
+        ybox[j] = (nbh[j] + GEMM_Y_BOX - 1) / GEMM_Y_BOX;
+        yoff[j] = stage_bytes;   // hi plane, then lo plane
+        stage_bytes += 2 * (uint32_t)ybox[j] * GM_YBOX_BYTES;
+    }
+    const int GP_NST = min(GP_NST_MAX, (int)(GP_RING_BYTES / stage_bytes));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t rank = gemm_cluster_rank();
     const bool lead = rank == 0;
@@ -442,11 +464,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     const long long w0 = W * pair / P, w1 = W * (pair + 1) / P;
 
     if (tid == 0) {
-        for (int s = 0; s < GP_NST; ++s) {
+        for (int s = 0; s < GP_NST_MAX; ++s) {
             mbar_init(&full[s], lead ? 2 : 1);   // own copies (+ the odd block's arrival)
             mbar_init(&empty[s], 1);
         }
-        for (int a = 0; a < 2; ++a) {
+        for (int a = 0; a < NSETS; ++a) {
             mbar_init(&tfull[a], 1);
             mbar_init(&tempty[a], 8);
         }
@@ -481,18 +503,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
                     break;
                 }
                 const int t = (int)(w / kblocks), kb = (int)(w % kblocks);
-                unsigned char* st = smem + (size_t)s * GP_STAGE;
+                unsigned char* st = smem + (size_t)s * stage_bytes;
                 mbar_arrive_expect_tx(&full[s], stage_bytes);
                 // 128-row tile 2 t + rank of the tile-contiguous X (past the last one: zeros)
                 const int xrow = ((2 * t + (int)rank) * kblocks + kb) * GM_BM;
                 tma_load_2d(st, &tXh, 0, xrow, &full[s], pol_x);
                 tma_load_2d(st + GM_A_BYTES, &tXl, 0, xrow, &full[s], pol_x);
-                for (int j = 0; j < ybox; ++j) {   // 64-row boxes, 1024-byte aligned
-                    const int yrow = (int)rank * nbh + j * GEMM_Y_BOX;
-                    tma_load_2d(st + 2 * GM_A_BYTES + j * GM_YBOX_BYTES, &tYh, kb * GM_BK, yrow,
-                                &full[s], pol_y);
-                    tma_load_2d(st + 2 * GM_A_BYTES + GP_YH_BYTES + j * GM_YBOX_BYTES, &tYl,
-                                kb * GM_BK, yrow, &full[s], pol_y);
+#pragma unroll
+                for (int n = 0; n < NT; ++n) {       // this block's half of each N tile
+                    unsigned char* yst = st + yoff[n];
+                    for (int j = 0; j < ybox[n]; ++j) {   // 32-row boxes, 1024-byte aligned
+                        const int yrow = n * GM_BN + (int)rank * nbh[n] + j * GEMM_Y_BOX;
+                        tma_load_2d(yst + j * GM_YBOX_BYTES, &tYh, kb * GM_BK, yrow, &full[s], pol_y);
+                        tma_load_2d(yst + (ybox[n] + j) * GM_YBOX_BYTES, &tYl, kb * GM_BK, yrow,
+                                    &full[s], pol_y);
+                    }
                 }
             }
             // leave no copy in flight; on the even block a stage's phase also
@@ -509,7 +534,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     } else if (warp == 1) {
         if (lane == 0 && lead) {
             // ---------------- MMA issuer (even block) ----------------
-            const uint32_t idesc = gemm_idesc_pair(nb);
+            uint32_t idesc[NT];
+#pragma unroll
+            for (int n = 0; n < NT; ++n) idesc[n] = gemm_idesc_pair(nbj[n] > 0 ? nbj[n] : 32);
             bool ok = true;
             long long it = 0;
             int seg = 0;
@@ -517,15 +544,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
             while (w < w1 && ok) {
                 const int t = (int)(w / kblocks);
                 const long long wend = min(w1, (long long)(t + 1) * kblocks);
-                const int acc = seg & 1;
-                if (seg >= 2 &&
-                    !mbar_wait_cluster(&tempty[acc], (uint32_t)((seg >> 1) - 1) & 1u, budget)) {
+                const int acc = seg % NSETS;
+                if (seg >= NSETS &&
+                    !mbar_wait_cluster(&tempty[acc], (uint32_t)((seg / NSETS) - 1) & 1u, budget)) {
                     set_error(ctrl, ERR_TIMEOUT);
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t dt = tmem + (uint32_t)(acc * GM_BN);
+                const uint32_t dt = tmem + (uint32_t)(acc * NT * GM_BN);   // N tile n at + n BN
                 bool first = true;
                 for (; w < wend; ++w, ++it) {
                     const int s = (int)(it % GP_NST);
@@ -535,16 +562,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t base = smem_u32(smem + (size_t)s * GP_STAGE);
+                    const uint32_t base = smem_u32(smem + (size_t)s * stage_bytes);
                     const uint32_t xh = base, xl = base + GM_A_BYTES;
-                    const uint32_t yh = base + 2 * GM_A_BYTES, yl = yh + GP_YH_BYTES;
 #pragma unroll
                     for (int k = 0; k < GM_BK / 16; ++k) {
                         const uint32_t off = k * 32;   // 16 bf16 along K
-                        tc_mma_pair(dt, sw128_desc(xh + off), sw128_desc(yh + off), idesc, first ? 0u : 1u);
+#pragma unroll
+                        for (int n = 0; n < NT; ++n) {
+                            if (nbj[n] == 0) continue;
+                            const uint32_t yh = base + yoff[n], yl = yh + (uint32_t)ybox[n] * GM_YBOX_BYTES;
+                            const uint32_t d = dt + (uint32_t)(n * GM_BN);
+                            tc_mma_pair(d, sw128_desc(xh + off), sw128_desc(yh + off), idesc[n], first ? 0u : 1u);
+                            tc_mma_pair(d, sw128_desc(xh + off), sw128_desc(yl + off), idesc[n], 1u);
+                            tc_mma_pair(d, sw128_desc(xl + off), sw128_desc(yh + off), idesc[n], 1u);
+                        }
                         first = false;
-                        tc_mma_pair(dt, sw128_desc(xh + off), sw128_desc(yl + off), idesc, 1u);
-                        tc_mma_pair(dt, sw128_desc(xl + off), sw128_desc(yh + off), idesc, 1u);
                     }
                     tc_commit_pair(&empty[s], 3);   // frees the stage in both blocks
                 }
@@ -578,18 +610,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
         while (w < w1) {
             const int t = (int)(w / kblocks);
             const long long wend = min(w1, (long long)(t + 1) * kblocks);
-            const int acc = seg & 1;
-            if (!mbar_wait_cluster(&tfull[acc], (uint32_t)(seg >> 1) & 1u, budget)) {
+            const int acc = seg % NSETS;
+            if (!mbar_wait_cluster(&tfull[acc], (uint32_t)(seg / NSETS) & 1u, budget)) {
                 set_error(ctrl, ERR_TIMEOUT);
                 break;
             }
             tc_fence_after();
-            float* dst = ws + ((size_t)blockIdx.x * smax + seg) * (size_t)GM_BN * GM_BM;
-            for (int c0 = 0; c0 < nb; c0 += 32) {
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * GM_BN + c0), v);
+            float* dst = ws + ((size_t)blockIdx.x * smax + seg) * (size_t)(NT * GM_BN) * GM_BM;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) dst[(size_t)(c0 + j) * GM_BM + q * 32 + lane] = v[j];
+            for (int n = 0; n < NT; ++n) {
+                for (int c0 = 0; c0 < nbj[n]; c0 += 32) {
+                    float v[32];
+                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((acc * NT + n) * GM_BN + c0), v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        dst[(size_t)(n * GM_BN + c0 + j) * GM_BM + q * 32 + lane] = v[j];
+                }
             }
             tc_fence_before();
             __syncwarp();
@@ -626,7 +662,7 @@ constexpr int FX_SEG = 6;   // segments a tile usually has at most (more are add
 
 __global__ void __launch_bounds__(128) k_gemm_fixup(
     const float* __restrict__ ws, const int* __restrict__ tile_seg_begin,
-    const int* __restrict__ seg_slot, int M, int count, const float* __restrict__ F, int ldf,
+    const int* __restrict__ seg_slot, int M, int ws_cols, int count, const float* __restrict__ F, int ldf,
     float* __restrict__ out, int ldo, __nv_bfloat16* __restrict__ out_hi,
     __nv_bfloat16* __restrict__ out_lo, int ldh, float2* __restrict__ r2part, int tiles_m,
     const Ctrl* __restrict__ ctrl, int check_skip, const int* __restrict__ slot_img,
@@ -650,7 +686,7 @@ __global__ void __launch_bounds__(128) k_gemm_fixup(
 #pragma unroll
         for (int q = 0; q < FX_SEG; ++q)
             v[k][q] = (q < ns && b0 + k < count)
-                          ? ws[((size_t)slot[q] * GM_BN + b0 + k) * GM_BM + threadIdx.x]
+                          ? ws[((size_t)slot[q] * ws_cols + b0 + k) * GM_BM + threadIdx.x]
                           : 0.f;
     // the columns' images and their F entries, loaded with the partials
     int img[FX_B];
@@ -672,7 +708,7 @@ __global__ void __launch_bounds__(128) k_gemm_fixup(
 #pragma unroll
         for (int q = 0; q < FX_SEG; ++q) d += v[k][q];
         for (int s = s0 + FX_SEG; s < s1; ++s)
-            d += ws[((size_t)seg_slot[s] * GM_BN + c) * GM_BM + threadIdx.x];
+            d += ws[((size_t)seg_slot[s] * ws_cols + c) * GM_BM + threadIdx.x];
         if (row < M) {
             d -= fv[k];
             out[(size_t)b * ldo + row] = d;
@@ -793,9 +829,10 @@ bool make_bf16_map(CUtensorMap* map, const void* base, int inner, int rows, int 
            CUDA_SUCCESS;
 }
 
-void gemm_plan(int M, int K, int grid, GemmPlan* p, bool pair)
+void gemm_plan(int M, int K, int grid, GemmPlan* p, bool pair, int nt)
 {
     p->pair = pair ? 1 : 0;
+    p->nt = pair && nt == 2 ? 2 : 1;
     p->tiles_m = (M + GM_BM - 1) / GM_BM;
     p->tiles = pair ? (M + 2 * GM_BM - 1) / (2 * GM_BM) : p->tiles_m;
     p->kblocks = (K + GM_BK - 1) / GM_BK;
@@ -833,7 +870,7 @@ void gemm_plan(int M, int K, int grid, GemmPlan* p, bool pair)
             p->seg_slot.push_back((int)((code / 1000000) * smax + code % 1000000));
     }
     p->tile_seg_begin[p->tiles_m] = (int)p->seg_slot.size();
-    p->ws_floats = (size_t)p->grid * smax * GM_BN * GM_BM;
+    p->ws_floats = (size_t)p->grid * smax * (p->nt * GM_BN) * GM_BM;
 }
 
 cudaError_t gemm_configure()
@@ -841,7 +878,10 @@ cudaError_t gemm_configure()
     cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)GM_SMEM);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_gemm_bf16x3_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_gemm_bf16x3_pair<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)GP_SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_gemm_bf16x3_pair<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)GP_SMEM);
 }
 
@@ -852,7 +892,7 @@ int gemm_pair_max_clusters(int num_sms)
     cfg.blockDim = dim3(192, 1, 1);
     cfg.dynamicSmemBytes = GP_SMEM;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, (const void*)k_gemm_bf16x3_pair, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, (const void*)k_gemm_bf16x3_pair<1>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -863,21 +903,24 @@ void launch_gemm(const CUtensorMap* xh, const CUtensorMap* xl, const CUtensorMap
                  const CUtensorMap* yl, const GemmPlan& p, float* ws, Ctrl* ctrl, int check_skip,
                  long long budget, cudaStream_t s, int ncols, const int* nact)
 {
-    if (p.pair)
-        k_gemm_bf16x3_pair<<<p.grid, 192, GP_SMEM, s>>>(*xh, *xl, *yh, *yl, p.tiles, p.kblocks, ws,
-                                                        p.smax, ctrl, check_skip, budget, ncols, nact);
+    if (p.pair && p.nt == 2)
+        k_gemm_bf16x3_pair<2><<<p.grid, 192, GP_SMEM, s>>>(
+            *xh, *xl, *yh, *yl, p.tiles, p.kblocks, ws, p.smax, ctrl, check_skip, budget, ncols, nact);
+    else if (p.pair)
+        k_gemm_bf16x3_pair<1><<<p.grid, 192, GP_SMEM, s>>>(
+            *xh, *xl, *yh, *yl, p.tiles, p.kblocks, ws, p.smax, ctrl, check_skip, budget, ncols, nact);
     else
         k_gemm_bf16x3<<<p.grid, 192, GM_SMEM, s>>>(*xh, *xl, *yh, *yl, p.tiles, p.kblocks, ws,
                                                    p.smax, ctrl, check_skip, budget, ncols, nact);
 }
 
 void launch_gemm_fixup(const float* ws, const int* tile_seg_begin, const int* seg_slot, int M,
-                       int tiles_m, int count, const float* F, int ldf, float* out, int ldo,
-                       void* out_hi, void* out_lo, int ldh, float2* r2part, const Ctrl* ctrl,
+                       int tiles_m, int ws_cols, int count, const float* F, int ldf, float* out,
+                       int ldo, void* out_hi, void* out_lo, int ldh, float2* r2part, const Ctrl* ctrl,
                        int check_skip, cudaStream_t s, const int* slot_img, const int* nact)
 {
     dim3 grid(tiles_m, (count + FX_B - 1) / FX_B);
-    k_gemm_fixup<<<grid, 128, 0, s>>>(ws, tile_seg_begin, seg_slot, M, count, F, ldf, out, ldo,
+    k_gemm_fixup<<<grid, 128, 0, s>>>(ws, tile_seg_begin, seg_slot, M, ws_cols, count, F, ldf, out, ldo,
                                       reinterpret_cast<__nv_bfloat16*>(out_hi),
                                       reinterpret_cast<__nv_bfloat16*>(out_lo), ldh, r2part,
                                       tiles_m, ctrl, check_skip, slot_img, nact);

@@ -115,6 +115,7 @@ void launch_quant_fp8(const float* A, int m, int N, void* q, void* c, float* sca
 struct GemmPlan {
     int tiles_m = 0, kblocks = 0, grid = 0, smax = 1;   // tiles_m: 128-row tiles of the fix-up
     int pair = 0;    // 1: CTA pairs (k_gemm_bf16x3_pair) on 256-row tiles
+    int nt = 1;      // N tiles of 256 columns per X tile (2: up to 512 images, pairs only)
     int tiles = 0;   // the kernel's tiles (128 or 256 rows)
     std::vector<int> tile_seg_begin;   // tiles_m + 1 offsets into seg_slot
     std::vector<int> seg_slot;         // workspace slot of each segment, per tile in K order
@@ -122,7 +123,7 @@ struct GemmPlan {
 };
 // grid: blocks of the launch (pair: rounded down to whole pairs); every plan
 // covers W = tiles x kblocks with at most W units (blocks or pairs).
-void gemm_plan(int M, int K, int grid, GemmPlan* p, bool pair = false);
+void gemm_plan(int M, int K, int grid, GemmPlan* p, bool pair = false, int nt = 1);
 cudaError_t gemm_configure();
 // Clusters of two GEMM blocks that fit on the device at once (0: the pair
 // kernel cannot run).
@@ -131,15 +132,16 @@ bool make_bf16_map(CUtensorMap* map, const void* base, int inner, int rows, int 
 // The Y operand's tensor maps use boxes of GEMM_Y_BOX rows.  ncols: columns
 // (images) of Y; nact (nullable): the number of leading columns that take part,
 // read on the device.  The MMAs run with N = min(ncols, nact) rounded up to 32.
-constexpr int GEMM_Y_BOX = 64;
+constexpr int GEMM_Y_BOX = 32;
 void launch_gemm(const CUtensorMap* xh, const CUtensorMap* xl, const CUtensorMap* yh,
                  const CUtensorMap* yl, const GemmPlan& p, float* ws, Ctrl* ctrl, int check_skip,
                  long long budget, cudaStream_t s, int ncols, const int* nact = nullptr);
 // Column j of the GEMM is image slot_img[j] (identity when slot_img is null) for
 // F, out and r2part; the bf16 planes out_hi/out_lo stay in column order.  With
 // nact set, only the first *nact columns are processed.
+// ws_cols: columns of a partial tile in the workspace (256 x the plan's nt).
 void launch_gemm_fixup(const float* ws, const int* tile_seg_begin, const int* seg_slot, int M,
-                       int tiles_m, int count, const float* F, int ldf, float* out, int ldo,
+                       int tiles_m, int ws_cols, int count, const float* F, int ldf, float* out, int ldo,
                        void* out_hi, void* out_lo, int ldh, float2* r2part, const Ctrl* ctrl,
                        int check_skip, cudaStream_t s, const int* slot_img = nullptr,
                        const int* nact = nullptr);

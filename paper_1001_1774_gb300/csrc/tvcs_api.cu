@@ -816,12 +816,13 @@ tvcs_status tvcs_solve_batched(const tvcs_handle* hs, int count, const float* co
     for (int i = 1; i < count && shared; ++i) shared = hs[i] == hs[0];
     if (shared) {
         CKS(check_handle(hs[0]));
-        if (count <= BATCH_MAX) return solve_batch(hs[0], count, f, u, mu, res);
+        if (count <= tvcs::batch_max(hs[0])) return solve_batch(hs[0], count, f, u, mu, res);
         // More images than one batch holds: groups of nearly equal size (the larger
         // ones first, so that the loop graph is rebuilt at most once), each through
         // the same tensor-core path.  A group whose images report a per-image
         // failure does not stop the later groups.
-        const int groups = (count + BATCH_MAX - 1) / BATCH_MAX;
+        const int gmax = tvcs::batch_max(hs[0]);
+        const int groups = (count + gmax - 1) / gmax;
         const int base = count / groups, extra = count % groups;
         tvcs_status worst = TVCS_OK, err = TVCS_OK;
         for (int gi = 0, off = 0; gi < groups; ++gi) {
@@ -969,8 +970,9 @@ tvcs_status tvcs_apply_batched(tvcs_handle h, int count, const float* X, const f
     CKS(check_handle(h));
     if (count < 1) return fail(TVCS_ERR_INVALID_ARG, "count must be >= 1");
     if (!X || !R || !G) return fail(TVCS_ERR_INVALID_ARG, "X, R and G must be non-NULL");
-    // groups of at most BATCH_MAX images (nearly equal sizes, the larger first)
-    const int groups = (count + BATCH_MAX - 1) / BATCH_MAX;
+    // groups of at most batch_max images (nearly equal sizes, the larger first)
+    const int gmax = tvcs::batch_max(h);
+    const int groups = (count + gmax - 1) / gmax;
     const int base = count / groups, extra = count % groups;
     const size_t N = (size_t)h->N, m = (size_t)h->m;
     for (int gi = 0, off = 0; gi < groups; ++gi) {
@@ -1000,8 +1002,7 @@ tvcs_status tvcs_test_gemm_shape(tvcs_handle h, int grid1, int pair1, int grid2,
     if (grid1 < 0 || grid2 < 0 || (grid1 == 0) != (grid2 == 0))
         return fail(TVCS_ERR_INVALID_ARG, "grids must both be > 0, or both 0 (the tuner decides)");
     if (grid1 > 0) {
-        CK(tvcs::gemm_configure());
-        const int pc = std::min(tvcs::gemm_pair_max_clusters(h->num_sms), h->num_sms / 2);
+        const int pc = std::min(tvcs::batch_pair_clusters(h), h->num_sms / 2);
         const int grid[2] = {grid1, grid2}, pair[2] = {pair1, pair2};
         for (int i = 0; i < 2; ++i) {
             if (pair[i] != 0 && pair[i] != 1) return fail(TVCS_ERR_INVALID_ARG, "pair must be 0 or 1");

@@ -130,14 +130,17 @@ def set_pair_shape(tv, h, pairs):
 # so both accumulators are reused; n = 128 is the full-size operand.
 @pytest.mark.parametrize("n,m,count,pairs", [(32, 307, 7, (76, 72, 64)), (32, 307, 7, (1,)),
                                              (64, 1229, 40, (76, 72, 64)), (64, 1229, 200, (3,)),
-                                             (128, 4915, 256, (76, 72, 64))])
+                                             (128, 4915, 256, (76, 72, 64)), (32, 307, 300, (76, 72, 64)),
+                                             (32, 307, 290, (1,)), (64, 1229, 512, (76, 72, 64))])
 def test_gemm_on_cta_pairs(tv, n, m, count, pairs):
     # The GEMMs on clusters of two blocks that share each 256-row tile
     # (tcgen05 cta_group::2): the same checks as the single-block kernel against
     # the split products in binary64 (1e-5 of the absolute sums), and agreement with
     # the single-block shape within the same bound: a different stream-K split
     # regroups binary32 sums of up to K = m or n^2 terms (whole-K tiles against
-    # tiles split over several blocks), which is not bitwise.
+    # tiles split over several blocks), which is not bitwise.  Above 256 images the
+    # pair kernel runs two N tiles per X tile; the single-block shape then runs as
+    # two calls (the first 256 images, the rest).
     N = n * n
     A = synth.gaussian_matrix(90 + n, m, N)
     rng = np.random.default_rng(count + 3 * n)
@@ -153,7 +156,12 @@ def test_gemm_on_cta_pairs(tv, n, m, count, pairs):
             tv.tvcs_test_gemm_shape(h, 152 if n > 32 else 64, 0, 152 if n > 32 else 64, 0)
         R = np.empty((count, m), np.float32)
         G = np.empty((count, N), np.float32)
-        tv.tvcs_apply_batched(h, count, X, Y, R, G)
+        for lo, hi in ([(0, count)] if pair or count <= 256 else [(0, 256), (256, count)]):
+            Rp = np.empty((hi - lo, m), np.float32)
+            Gp = np.empty((hi - lo, N), np.float32)
+            tv.tvcs_apply_batched(h, hi - lo, np.ascontiguousarray(X[lo:hi]), np.ascontiguousarray(Y[lo:hi]),
+                                  Rp, Gp)
+            R[lo:hi], G[lo:hi] = Rp, Gp
         out.append((R, G))
         tv.tvcs_destroy(h)
     (R1, G1), (R0, G0) = out
@@ -361,36 +369,44 @@ def test_batched_workload_256_images_n128(tv):
     tv.tvcs_destroy(h)
 
 
-def test_batched_more_than_256_images_run_in_groups(tv):
-    # 300 images: two groups of 150 through the same tensor-core path.  An image's
-    # column is independent of the others, so every image equals its result in a
-    # call that holds only its own group; a sample matches the FP64 oracle.
-    A, ubars, F, mus, _ = synth.workload_shared_batch(count=300, n=32, ratio=0.3, seed=12, n_ellipses=6)
+def test_batched_more_than_512_images_run_in_groups(tv):
+    # 600 images: two groups of 300 through the same tensor-core path (two N tiles of
+    # 256 columns per X tile of A).  An image's column is independent of the other
+    # columns and of how many run, so with one GEMM shape for every call each image
+    # equals its result in a call that holds only its own group, and in a call of
+    # 150 images (one N tile); a sample matches the FP64 oracle.
+    count = 600
+    A, ubars, F, mus, _ = synth.workload_shared_batch(count=count, n=32, ratio=0.3, seed=12, n_ellipses=6)
     m, N = A.shape
     tau = oracle.default_tau(A)
     iters = 30
     h = bf16_handle(tv, A, m, 32, mu=1e3, tau=tau, max_iter=iters)
+    set_pair_shape(tv, h, (76, 72, 64))
     Fd = torch.from_numpy(F).cuda()
-    U = torch.empty((300, N), dtype=torch.float32, device="cuda")
-    res = tv.tvcs_solve_batched([h] * 300, [Fd[b] for b in range(300)], [U[b] for b in range(300)], mus)
+    U = torch.empty((count, N), dtype=torch.float32, device="cuda")
+    res = tv.tvcs_solve_batched([h] * count, [Fd[b] for b in range(count)], [U[b] for b in range(count)], mus)
     assert all(r.iters == iters for r in res)
-    U2 = torch.empty((150, N), dtype=torch.float32, device="cuda")
-    tv.tvcs_solve_batched([h] * 150, [Fd[150 + b] for b in range(150)], [U2[b] for b in range(150)],
-                          mus[150:])
-    Uh, U2h = U.cpu().numpy(), U2.cpu().numpy()
-    assert np.array_equal(Uh[150:], U2h)
-    for b in (0, 149, 150, 299):
+    U2 = torch.empty((300, N), dtype=torch.float32, device="cuda")
+    tv.tvcs_solve_batched([h] * 300, [Fd[300 + b] for b in range(300)], [U2[b] for b in range(300)],
+                          mus[300:])
+    U3 = torch.empty((150, N), dtype=torch.float32, device="cuda")
+    tv.tvcs_solve_batched([h] * 150, [Fd[450 + b] for b in range(150)], [U3[b] for b in range(150)],
+                          mus[450:])
+    Uh, U2h, U3h = U.cpu().numpy(), U2.cpu().numpy(), U3.cpu().numpy()
+    assert np.array_equal(Uh[300:], U2h)
+    assert np.array_equal(Uh[450:], U3h)
+    for b in (0, 299, 300, 599):
         ref = oracle.solve(A, F[b], 32, mus[b], 10.0, tau, max_iter=iters)
         assert rel(Uh[b], ref.u) <= 1e-4, b
     # the products entry point groups the same way
-    X = np.ascontiguousarray(Uh[:260])
-    R = np.empty((260, m), np.float32)
-    G = np.empty((260, N), np.float32)
-    tv.tvcs_apply_batched(h, 260, X, F[:260], R, G)
-    R1 = np.empty((130, m), np.float32)
-    G1 = np.empty((130, N), np.float32)
-    tv.tvcs_apply_batched(h, 130, np.ascontiguousarray(X[130:]), np.ascontiguousarray(F[130:260]), R1, G1)
-    assert np.array_equal(R[130:], R1) and np.array_equal(G[130:], G1)
+    X = np.ascontiguousarray(Uh[:520])
+    R = np.empty((520, m), np.float32)
+    G = np.empty((520, N), np.float32)
+    tv.tvcs_apply_batched(h, 520, X, F[:520], R, G)
+    R1 = np.empty((260, m), np.float32)
+    G1 = np.empty((260, N), np.float32)
+    tv.tvcs_apply_batched(h, 260, np.ascontiguousarray(X[260:]), np.ascontiguousarray(F[260:520]), R1, G1)
+    assert np.array_equal(R[260:], R1) and np.array_equal(G[260:], G1)
     tv.tvcs_destroy(h)
 
 
