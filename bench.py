@@ -62,6 +62,9 @@ def parse_args():
                          "on the device), --steps back-to-back launches (for profiler captures)")
     ap.add_argument("--images", type=int, default=256,
                     help="images of --workload batch256 (one group up to 512; more run in groups of at most 512)")
+    ap.add_argument("--gemm-shape", default=None,
+                    help="--workload batch256: pin both batched GEMMs to 'BLOCKS,PAIR' (e.g. 152,1 for "
+                         "76 CTA pairs) instead of the tuner's pick (profiling captures)")
     ap.add_argument("--n", type=int, default=256, help="image side of --workload products")
     ap.add_argument("--m", type=int, default=13107, help="measurements of --workload products")
     ap.add_argument("--algo", choices=["iadm", "ftvcs"], default="iadm",
@@ -498,7 +501,7 @@ def n256_segment(tv, precision, steps, stream):
                          "peak_source": peak_src}}
 
 
-def batch_segment(tv, steps, warmup, stream, want_parity=True, images=256):
+def batch_segment(tv, steps, warmup, stream, want_parity=True, images=256, gemm_shape=None):
     """`images` (256 by default) images of 128 x 128 sharing one 4915 x 16384 A (bf16
     hi/lo): `steps` batched iterations; the GEMM pair's time against the bf16 peak;
     image 0 against the FP64 oracle after the same iterations."""
@@ -519,6 +522,9 @@ def batch_segment(tv, steps, warmup, stream, want_parity=True, images=256):
     stream.synchronize()
     h = tv.tvcs_create(A_dev, 0, m, 128, 1e3, 10.0, 0.0, opt)
     del A_dev
+    if gemm_shape:
+        g, p = (int(v) for v in gemm_shape.split(","))
+        tv.tvcs_test_gemm_shape(h, g, p, g, p)
     tau = tv.tvcs_get_tau(h)
     fl = [F_dev[b] for b in range(B)]
     ul = [U_dev[b] for b in range(B)]
@@ -531,6 +537,8 @@ def batch_segment(tv, steps, warmup, stream, want_parity=True, images=256):
     stream.synchronize()
     h = tv.tvcs_create(A_dev, 0, m, 128, 1e3, 10.0, 0.0, opt)
     del A_dev
+    if gemm_shape:
+        tv.tvcs_test_gemm_shape(h, g, p, g, p)
     tv.tvcs_solve_batched([h] * B, fl, ul, mus)      # state and the loop graph of this count
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -603,7 +611,7 @@ def run_batched(args):
     stream = torch.cuda.Stream()
     b = batch_segment(tv, args.steps, args.warmup, stream,
                       want_parity=not args.no_cpu_baseline and args.steps <= ITERS_PER_RECON,
-                      images=args.images)
+                      images=args.images, gemm_shape=args.gemm_shape)
     A, F, mus = b.pop("_A"), b.pop("_F"), b.pop("_mus")
     m, N = A.shape
     out = {"metric": METRIC, "value": b["value"], "unit": "image-iter/s", "n_gpus": 1,
