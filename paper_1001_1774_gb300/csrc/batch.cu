@@ -29,10 +29,13 @@ namespace tvcs {
 // Continue while any image runs and the loop bound holds.  With slot tables
 // (count <= blockDim.x = BATCH_MAX): the running images, in image order, take slots
 // 0 .. nact-1 for the next iteration (a block-wide exclusive prefix sum of the
-// running flags); an image that stopped gets slot -1.
+// running flags); an image that stopped gets slot -1.  img_slot_prev (nullable)
+// keeps each image's slot of the iteration that just ended (its column in that
+// iteration's GEMMs).
 __global__ void k_batch_cond(const Ctrl* __restrict__ ctrls, int count, Ctrl* __restrict__ bctrl,
                              cudaGraphConditionalHandle cond, int set_cond,
-                             int* __restrict__ slot_img, int* __restrict__ img_slot)
+                             int* __restrict__ slot_img, int* __restrict__ img_slot,
+                             int* __restrict__ img_slot_prev)
 {
     __shared__ int any;
     __shared__ int wtot[BATCH_MAX / 32];
@@ -53,6 +56,7 @@ __global__ void k_batch_cond(const Ctrl* __restrict__ ctrls, int count, Ctrl* __
         }
         const int slot = base + __popc(m & ((1u << lane) - 1u));
         if (b < count) {
+            if (img_slot_prev) img_slot_prev[b] = img_slot[b];   // read and rewritten by thread b only
             img_slot[b] = run ? slot : -1;
             if (run) slot_img[slot] = b;
         }
@@ -69,10 +73,11 @@ __global__ void k_batch_cond(const Ctrl* __restrict__ ctrls, int count, Ctrl* __
 }
 
 void launch_batch_cond(const Ctrl* ctrls, int count, Ctrl* bctrl, unsigned long long cond,
-                       int set_cond, cudaStream_t s, int* slot_img, int* img_slot)
+                       int set_cond, cudaStream_t s, int* slot_img, int* img_slot,
+                       int* img_slot_prev)
 {
     k_batch_cond<<<1, BATCH_MAX, 0, s>>>(ctrls, count, bctrl, (cudaGraphConditionalHandle)cond,
-                                         set_cond, slot_img, img_slot);
+                                         set_cond, slot_img, img_slot, img_slot_prev);
 }
 
 // End-of-run residual of every image, r_b = A_eff u_b - f_b with A_eff = hi + lo
@@ -218,7 +223,7 @@ void free_buffers(tvcs_batch* b)
 {
     void* bufs[] = {b->U, b->W, b->L, b->G, b->R, b->F, b->mu, b->Uh, b->Ul, b->Rh, b->Rl,
                     b->ctrls, b->bctrl, b->r2part, b->part, b->ws, b->tsb1, b->ss1, b->tsb2, b->ss2,
-                    b->slot_img, b->img_slot};
+                    b->slot_img, b->img_slot, b->img_slot_prev};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (b->hctrls) cudaFreeHost(b->hctrls);
@@ -230,7 +235,7 @@ void free_buffers(tvcs_batch* b)
     b->ctrls = b->bctrl = b->hctrls = b->hbctrl = nullptr;
     b->r2part = nullptr;
     b->part = nullptr;
-    b->slot_img = b->img_slot = nullptr;
+    b->slot_img = b->img_slot = b->img_slot_prev = nullptr;
     b->ws = nullptr;
     b->tsb1 = b->ss1 = b->tsb2 = b->ss2 = nullptr;
     b->exec = nullptr;
@@ -456,6 +461,7 @@ tvcs_status ensure_batch(tvcs_ctx* h, int count)
         // 8-block clusters (they pack the SMs more densely than 16).
         b->uimg = usolve_img_configure(h->n);
         b->ureg = h->n == 128 && usolve_reg_configure();
+        b->gfused = b->ureg;   // 128 x 128 images: GEMM tile t of G = A^T R is image row t
         b->ucluster = usolve_cluster_fits(h->n, 8) ? 8 : h->ucluster;
         usolve_cluster_fits(h->n, b->ucluster);   // kernel attributes of the chosen size
     }
@@ -523,6 +529,7 @@ tvcs_status ensure_batch(tvcs_ctx* h, int count)
         BCKS(balloc((void**)&b->part, sizeof(double) * B * 2 * ((N + 255) / 256)));
         BCKS(balloc((void**)&b->slot_img, sizeof(int) * B));
         BCKS(balloc((void**)&b->img_slot, sizeof(int) * B));
+        BCKS(balloc((void**)&b->img_slot_prev, sizeof(int) * B));
         BCK(cudaMallocHost((void**)&b->hctrls, sizeof(Ctrl) * B));
         BCK(cudaMallocHost((void**)&b->hbctrl, sizeof(Ctrl)));
         BCK(cudaMemsetAsync(b->Rh, 0, sizeof(unsigned short) * B * b->mpad, s));
@@ -554,7 +561,7 @@ tvcs_status ensure_batch(tvcs_ctx* h, int count)
 // slot_img[j] (the U and R planes are stored in that column order).  in_loop:
 // the kernels return at once when bctrl->skip is set (every image has stopped).
 void batch_products(tvcs_ctx* h, int count, bool subtract_f, cudaStream_t s, bool compact = false,
-                    bool in_loop = false)
+                    bool in_loop = false, bool g_partials = false)
 {
     tvcs_batch* b = h->batch;
     const long long budget = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : (1LL << 31);
@@ -568,6 +575,7 @@ void batch_products(tvcs_ctx* h, int count, bool subtract_f, cudaStream_t s, boo
                       b->r2part, b->bctrl, chk, s, slot, nact);
     launch_gemm(&b->mAth, &b->mAtl, &b->mRh, &b->mRl, b->p2, b->ws, b->bctrl, chk, budget, s, count,
                 nact);
+    if (g_partials) return;   // the next u-solve adds G's partial tiles itself
     launch_gemm_fixup(b->ws, b->tsb2, b->ss2, h->N, b->p2.tiles_m, b->p2.nt * 256, count, nullptr, 0, b->G, h->N,
                       nullptr, nullptr, 0, nullptr, b->bctrl, chk, s, slot, nact);
 }
@@ -595,6 +603,13 @@ TvArgs batch_tv_args(tvcs_ctx* h, int count, int mode, bool compact = false)
     a.u_hi = b->Uh;
     a.u_lo = b->Ul;
     a.img_slot = compact ? b->img_slot : nullptr;
+    if (b->gfused) {   // g from the partial tiles of G = A^T R (k_usolve_reg128)
+        a.gws = b->ws;
+        a.gtsb = b->tsb2;
+        a.gss = b->ss2;
+        a.gws_cols = b->p2.nt * 256;
+        a.img_slot_prev = compact ? b->img_slot_prev : nullptr;
+    }
     return a;
 }
 
@@ -634,10 +649,11 @@ tvcs_status build_batch_graph(tvcs_ctx* h, int count)
     TvArgs a = batch_tv_args(h, count, MODE_ITER, compact);
     for (int k = 0; k < BATCH_ITERS_PER_BODY; ++k) {
         batch_usolve(h, a, cs);
-        batch_products(h, count, true, cs, compact, true);
+        batch_products(h, count, true, cs, compact, true, b->gfused);
         launch_batch_cond(b->ctrls, count, b->bctrl, (unsigned long long)ch,
                           k + 1 == BATCH_ITERS_PER_BODY ? 1 : 0, cs,
-                          compact ? b->slot_img : nullptr, compact ? b->img_slot : nullptr);
+                          compact ? b->slot_img : nullptr, compact ? b->img_slot : nullptr,
+                          compact && b->gfused ? b->img_slot_prev : nullptr);
     }
     cudaGraph_t captured = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &captured);
@@ -690,8 +706,9 @@ tvcs_status time_batch_stage(tvcs_ctx* h, int stage, int reps, double* ms)
         } else if (stage == 4) {
             launch_gemm_fixup(b->ws, b->tsb1, b->ss1, h->m, b->p1.tiles_m, b->p1.nt * 256, count, b->F, h->m, b->R,
                               h->m, b->Rh, b->Rl, b->mpad, b->r2part, b->bctrl, 0, s);
-            launch_gemm_fixup(b->ws, b->tsb2, b->ss2, h->N, b->p2.tiles_m, b->p2.nt * 256, count, nullptr, 0, b->G,
-                              h->N, nullptr, nullptr, 0, nullptr, b->bctrl, 0, s);
+            if (!b->gfused)   // else the u-solve adds G's partials: no second fix-up in the loop
+                launch_gemm_fixup(b->ws, b->tsb2, b->ss2, h->N, b->p2.tiles_m, b->p2.nt * 256, count, nullptr,
+                                  0, b->G, h->N, nullptr, nullptr, 0, nullptr, b->bctrl, 0, s);
         } else {
             batch_usolve(h, a, s);
         }
@@ -757,6 +774,7 @@ tvcs_status solve_batch(tvcs_ctx* h, int count, const float* const* f, float* co
         for (int i = 0; i < count; ++i) ident[i] = i;
         BCK(cudaMemcpyAsync(b->slot_img, ident.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s));
         BCK(cudaMemcpyAsync(b->img_slot, ident.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s));
+        BCK(cudaMemcpyAsync(b->img_slot_prev, ident.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s));
         BCK(cudaStreamSynchronize(s));   // the host vector goes out of scope
     }
     BCK(cudaMemcpyAsync(b->bctrl, b->hbctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
@@ -771,11 +789,21 @@ tvcs_status solve_batch(tvcs_ctx* h, int count, const float* const* f, float* co
                           h->N, nullptr, nullptr, 0, nullptr, b->bctrl, 0, s);
     }
     launch_split_rows(b->U, count, h->N, h->N, b->Uh, b->Ul, h->N, s);
-    batch_products(h, count, true, s);
+    batch_products(h, count, true, s, false, false, b->gfused);
     BCKS(build_batch_graph(h, count));
     BCK(cudaEventRecord(h->ev0, s));
     if (h->opt.max_iter > 0) BCK(cudaGraphLaunch(b->exec, s));
     BCK(cudaEventRecord(h->ev1, s));
+    if (b->gfused) {
+        // G = A^T R of every image at its final iterate (the loop left G in partial
+        // tiles, in the columns of each iteration): R's planes in image order, the
+        // second GEMM and its fix-up, the same values the loop's fix-ups wrote before
+        const long long budget = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : (1LL << 31);
+        launch_split_rows(b->R, count, h->m, h->m, b->Rh, b->Rl, b->mpad, s);
+        launch_gemm(&b->mAth, &b->mAtl, &b->mRh, &b->mRl, b->p2, b->ws, b->bctrl, 0, budget, s, count);
+        launch_gemm_fixup(b->ws, b->tsb2, b->ss2, h->N, b->p2.tiles_m, b->p2.nt * 256, count, nullptr, 0, b->G,
+                          h->N, nullptr, nullptr, 0, nullptr, b->bctrl, 0, s);
+    }
     // end of run, per image: ||r||^2 of the image's own residual recomputed on the CUDA
     // cores, final multiplier update, objective, residuals
     k_batch_resid<<<dim3((h->m + RS_BM - 1) / RS_BM, (count + RS_BB - 1) / RS_BB), 256, 0, s>>>(

@@ -31,6 +31,7 @@ struct tvcs_batch {
     tvcs::GemmPlan p1, p2;               // R = A U - F (M = m, K = N) and G = A^T R (M = N, K = m)
     int *tsb1 = nullptr, *ss1 = nullptr, *tsb2 = nullptr, *ss2 = nullptr;
     int *slot_img = nullptr, *img_slot = nullptr;   // compaction: column -> image, image -> column
+    int* img_slot_prev = nullptr;  // image -> column in the GEMMs of the iteration that just ended
     CUtensorMap mAh, mAl, mAth, mAtl, mUh, mUl, mRh, mRl;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -39,6 +40,7 @@ struct tvcs_batch {
     int ucluster = 0;              // cluster size of the batched u-solve
     bool uimg = false;             // the u-solve runs one block per image (k_usolve_img)
     bool ureg = false;             // n = 128: one block per image, transforms in registers (k_usolve_reg.cu)
+    bool gfused = false;           // the u-solve adds the partial tiles of G = A^T R (no second fix-up in the loop)
     bool tuned = false;            // the GEMM launch shapes have been picked for these buffers
     int pair_clusters = 0;         // clusters of two GEMM blocks resident at once (0: no pair kernel)
 };

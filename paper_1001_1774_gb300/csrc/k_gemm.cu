@@ -658,7 +658,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
 // mode 1: R = D - F, R planes (column order), ||r_b||^2 partial;  mode 2: G = D.
 // ---------------------------------------------------------------------------
 constexpr int FX_B = 4;     // images per fix-up block
-constexpr int FX_SEG = 6;   // segments a tile usually has at most (more are added in a second pass)
+constexpr int FX_SEG = GEMM_FX_SEG;   // segments a tile usually has at most (more are added in a second pass)
 
 __global__ void __launch_bounds__(128) k_gemm_fixup(
     const float* __restrict__ ws, const int* __restrict__ tile_seg_begin,

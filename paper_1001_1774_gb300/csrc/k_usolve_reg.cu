@@ -48,7 +48,10 @@ constexpr int RG_QS = RG_NN + 1;         // column stride (complex)
 constexpr int RG_WARPS = 8;
 constexpr int RG_T = RG_WARPS * 32;
 constexpr int RG_XS = RG_NN + RG_NN / 16;   // exchange row of a warp, one pad per 16 values
-constexpr size_t RG_SMEM = ((size_t)RG_Q * RG_QS * 8 + 15) / 16 * 16 + (size_t)RG_WARPS * RG_XS * 8 + 64 * 8;
+constexpr int RG_TWK = 8;                 // per-lane twiddles (3 in-lane, 5 lane stages)
+static_assert(RG_T == RG_TWK * 32, "one thread fills each entry of the lane twiddle table");
+constexpr size_t RG_SMEM = ((size_t)RG_Q * RG_QS * 8 + 15) / 16 * 16 + (size_t)RG_WARPS * RG_XS * 8 + 64 * 8 +
+                           (size_t)RG_TWK * 32 * 8;
 
 __device__ __forceinline__ int bitrev5(int l) { return (int)(__brev((unsigned)l) >> 27); }
 
@@ -61,31 +64,21 @@ __device__ __forceinline__ float2 shfl_xor2(float2 v, int m)
     return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
 }
 
-// Per-lane twiddles: the in-lane W128^(l k1) (k1 = 1..3) and, for each lane
-// stage s (half h = 16 >> s), W_{2h}^(l mod h) on the lanes that take the
-// difference (l & h).  Forward values (exp(-2 pi i t / n)); the inverse uses
-// their conjugates.
-struct LaneTw {
-    float2 w1[3];
-    float2 ws[5];
-};
-
-__device__ __forceinline__ LaneTw lane_twiddles(const float2* __restrict__ tw128, int l)
+// Per-lane twiddles, in a shared table twl[k][lane] (the same for every warp):
+// k = 0..2 the in-lane W128^(l (k+1)); k = 3 + s, for lane stage s (half h = 16 >> s),
+// W_{2h}^(l mod h) on the lanes that take the difference (l & h).  Forward values
+// (exp(-2 pi i t / n)); the inverse uses their conjugates.
+__device__ __forceinline__ float2 lane_twiddle(const float2* __restrict__ tw128, int k, int l)
 {
-    LaneTw t;
-#pragma unroll
-    for (int k1 = 1; k1 < 4; ++k1) {
-        const float2 c = tw128[(l * k1) & (RG_NN - 1)];   // (cos, sin)(2 pi t / 128)
-        t.w1[k1 - 1] = make_float2(c.x, -c.y);
+    int t;
+    if (k < 3) {
+        t = (l * (k + 1)) & (RG_NN - 1);
+    } else {
+        const int h = 16 >> (k - 3);
+        t = (4 * (l & (h - 1)) * (16 / h)) & (RG_NN - 1);   // exponent of W32, in W128 steps
     }
-#pragma unroll
-    for (int s = 0; s < 5; ++s) {
-        const int h = 16 >> s;
-        const int e = (l & (h - 1)) * (16 / h);            // exponent of W32
-        const float2 c = tw128[(4 * e) & (RG_NN - 1)];
-        t.ws[s] = make_float2(c.x, -c.y);
-    }
-    return t;
+    const float2 c = tw128[t];   // (cos, sin)(2 pi t / 128)
+    return make_float2(c.x, -c.y);
 }
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b)
@@ -98,7 +91,7 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b)   // a * conj(b)
 }
 
 // Forward: v[j] = x[l + 32 j] in, v[k1] = X[k1 + 4 bitrev5(l)] out.
-__device__ __forceinline__ void fft128_fwd(float2 v[4], const LaneTw& t, int l)
+__device__ __forceinline__ void fft128_fwd(float2 v[4], const float2* __restrict__ twl, int l)
 {
     {   // radix 4 over j, W4 = -i
         const float2 s02 = make_float2(v[0].x + v[2].x, v[0].y + v[2].y);
@@ -111,9 +104,10 @@ __device__ __forceinline__ void fft128_fwd(float2 v[4], const LaneTw& t, int l)
         v[3] = make_float2(d02.x - d13.x, d02.y - d13.y);
     }
 #pragma unroll
-    for (int k1 = 1; k1 < 4; ++k1) v[k1] = cmulf(v[k1], t.w1[k1 - 1]);
+    for (int k1 = 1; k1 < 4; ++k1) v[k1] = cmulf(v[k1], twl[(k1 - 1) * 32 + l]);
 #pragma unroll
     for (int s = 0; s < 5; ++s) {   // decimation in frequency across the lanes
+        const float2 ws = twl[(3 + s) * 32 + l];
         const int h = 16 >> s;
         const bool lower = (l & h) != 0;
 #pragma unroll
@@ -122,29 +116,30 @@ __device__ __forceinline__ void fft128_fwd(float2 v[4], const LaneTw& t, int l)
             if (!lower) {
                 v[k1] = make_float2(v[k1].x + p.x, v[k1].y + p.y);
             } else {
-                v[k1] = cmulf(make_float2(p.x - v[k1].x, p.y - v[k1].y), t.ws[s]);
+                v[k1] = cmulf(make_float2(p.x - v[k1].x, p.y - v[k1].y), ws);
             }
         }
     }
 }
 
 // Inverse (unnormalised): v[k1] = X[k1 + 4 bitrev5(l)] in, v[j] = x[l + 32 j] out.
-__device__ __forceinline__ void fft128_inv(float2 v[4], const LaneTw& t, int l)
+__device__ __forceinline__ void fft128_inv(float2 v[4], const float2* __restrict__ twl, int l)
 {
 #pragma unroll
     for (int s = 4; s >= 0; --s) {   // decimation in time across the lanes
+        const float2 ws = twl[(3 + s) * 32 + l];
         const int h = 16 >> s;
         const bool lower = (l & h) != 0;
 #pragma unroll
         for (int k1 = 0; k1 < 4; ++k1) {
-            const float2 own = lower ? cmulc(v[k1], t.ws[s]) : v[k1];
+            const float2 own = lower ? cmulc(v[k1], ws) : v[k1];
             const float2 p = shfl_xor2(own, h);
             v[k1] = lower ? make_float2(p.x - own.x, p.y - own.y)
                           : make_float2(own.x + p.x, own.y + p.y);
         }
     }
 #pragma unroll
-    for (int k1 = 1; k1 < 4; ++k1) v[k1] = cmulc(v[k1], t.w1[k1 - 1]);
+    for (int k1 = 1; k1 < 4; ++k1) v[k1] = cmulc(v[k1], twl[(k1 - 1) * 32 + l]);
     {   // inverse radix 4, W4^-1 = +i
         const float2 s02 = make_float2(v[0].x + v[2].x, v[0].y + v[2].y);
         const float2 d02 = make_float2(v[0].x - v[2].x, v[0].y - v[2].y);
@@ -217,12 +212,29 @@ __device__ __forceinline__ void shrink_row(const float (&uc)[4], const float (&u
 struct PairIn {
     float u[2][4];
     float l1[2][4], l2[2][4], w1[2][4], w2[2][4];
+};
+
+// The first two stream-K partials of g for the pair's rows (the second 0 past the
+// last segment), loaded with the pair's other inputs.
+struct PairG {
     float g[2][4];
+    float g1[2][4];
+    int s0[2], ns[2];   // each row's (tile's) first segment and segment count
+};
+
+// Where g comes from: the partial tiles of G = A^T R, whose 128-row tile t holds
+// row t of a 128 x 128 image: g at pixel (t, c) is the sum of
+// ws[(slot_s cols + col) 128 + c] over the tile's segments s.
+struct GSrc {
+    const float* ws;
+    const int* tsb;
+    const int* ss;
+    int cols, col;
 };
 
 __device__ __forceinline__ void load_pair(PairIn& in, const float* __restrict__ u,
                                           const float* __restrict__ lsrc, const float* __restrict__ wsrc,
-                                          const float* __restrict__ g, int r0, int l, int pending)
+                                          int r0, int l, int pending)
 {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -235,8 +247,46 @@ __device__ __forceinline__ void load_pair(PairIn& in, const float* __restrict__ 
             in.l2[h][j] = lsrc[RG_N + gi];
             in.w1[h][j] = pending ? wsrc[gi] : 0.0f;
             in.w2[h][j] = pending ? wsrc[RG_N + gi] : 0.0f;
-            in.g[h][j] = g[gi];
         }
+    }
+}
+
+__device__ __forceinline__ void load_g(PairG& in, const GSrc& gs, int r0, int l)
+{
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int s0 = gs.tsb[r0 + h], ns = gs.tsb[r0 + h + 1] - s0;
+        in.s0[h] = s0;
+        in.ns[h] = ns;
+        const float* p0 = gs.ws + ((size_t)gs.ss[s0] * gs.cols + gs.col) * RG_NN;
+        const float* p1 = ns > 1 ? gs.ws + ((size_t)gs.ss[s0 + 1] * gs.cols + gs.col) * RG_NN : nullptr;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = l + 32 * j;
+            in.g[h][j] = p0[c];
+            in.g1[h][j] = p1 ? p1[c] : 0.0f;
+        }
+    }
+}
+
+// g of row r0 + h at columns l + 32 j, bitwise the fix-up's sum: it adds from +0
+// the first GEMM_FX_SEG partials (zeros past the last segment), then the rest, in
+// K order.  A sum that starts at +0 is never -0 after its first addition, and x + 0
+// is x for every other x, so the padding zeros change nothing: the sum from +0 over
+// the tile's segments in order is the same value.
+__device__ __forceinline__ void g_row(const PairG& in, const GSrc& gs, int h, int l, float (&g)[4])
+{
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float d = 0.f;
+        d += in.g[h][j];
+        d += in.g1[h][j];   // 0 for a one-segment tile: the same value
+        g[j] = d;
+    }
+    for (int q = 2; q < in.ns[h]; ++q) {   // tiles of more than two segments
+        const float* p = gs.ws + ((size_t)gs.ss[in.s0[h] + q] * gs.cols + gs.col) * RG_NN;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) g[j] += p[l + 32 * j];
     }
 }
 
@@ -250,15 +300,17 @@ __global__ void __launch_bounds__(RG_T, 2) k_usolve_reg128(
     float beta, float mu_over_tau, float mu, Ctrl* __restrict__ ctrl, int mode,
     const float* __restrict__ mu_img, const float* __restrict__ tau_img, float tau,
     unsigned short* __restrict__ u_hi, unsigned short* __restrict__ u_lo,
-    const int* __restrict__ img_slot)
+    const int* __restrict__ img_slot, const float* __restrict__ gws, const int* __restrict__ gtsb,
+    const int* __restrict__ gss, int gws_cols, const int* __restrict__ img_slot_prev)
 {
     constexpr int NN = RG_NN, N = RG_N;
+    GSrc gs{gws, gtsb, gss, gws_cols, 0};
     {
         const int b = blockIdx.x;
         u += (size_t)b * N;
         wbuf += (size_t)b * 4 * N;
         lbuf += (size_t)b * 4 * N;
-        g += (size_t)b * N;
+        gs.col = img_slot_prev ? img_slot_prev[b] : b;
         ctrl += b;
         if (u_hi) {
             const int row = img_slot ? img_slot[b] : b;
@@ -278,6 +330,7 @@ __global__ void __launch_bounds__(RG_T, 2) k_usolve_reg128(
     float2* spec = reinterpret_cast<float2*>(smem);                     // spec[q QS + p]
     float2* xrow_all = reinterpret_cast<float2*>(smem + ((size_t)RG_Q * RG_QS * 8 + 15) / 16 * 16);
     float2* red = xrow_all + RG_WARPS * RG_XS;                          // [64]
+    float2* twl = red + 64;                                             // [RG_TWK][32]
     const int tid = threadIdx.x, l = tid & 31, warp = tid >> 5;
     float2* xrow = xrow_all + warp * RG_XS;
 
@@ -292,7 +345,8 @@ __global__ void __launch_bounds__(RG_T, 2) k_usolve_reg128(
     const float* lsrc = lbuf + (size_t)par * 2 * N;
     float* wdst = wbuf + (size_t)(par ^ 1) * 2 * N;
     float* ldst = lbuf + (size_t)(par ^ 1) * 2 * N;
-    const LaneTw tw = lane_twiddles(tw_g, l);
+    twl[tid] = lane_twiddle(tw_g, tid >> 5, l);   // RG_T = RG_TWK * 32 entries, one per thread
+    __syncthreads();
     const float inv_beta = 1.0f / beta;
 
     // ---------------- phase A: pairs of rows ----------------
@@ -321,7 +375,9 @@ __global__ void __launch_bounds__(RG_T, 2) k_usolve_reg128(
         shrink_row(ur, ucur, lr1, lr2, wr1, wr2, pending, beta, inv_beta, l, y1d, y2prev, w1d, w2d);
     }
     PairIn cur;
-    load_pair(cur, u, lsrc, wsrc, g, R0, l, pending);
+    PairG gp;   // g of the pair (or its partials), loaded with the pair's other inputs
+    load_pair(cur, u, lsrc, wsrc, R0, l, pending);
+    load_g(gp, gs, R0, l);
 #pragma unroll 1
     for (int k = 0; k < PPW; ++k) {
         const int r0 = R0 + 2 * k;
@@ -348,10 +404,13 @@ __global__ void __launch_bounds__(RG_T, 2) k_usolve_reg128(
         float ym[2][4];
         shift_left_cols(y1[0], ym[0], l);
         shift_left_cols(y1[1], ym[1], l);
+        float g0[4], g1[4];
+        g_row(gp, gs, 0, l, g0);
+        g_row(gp, gs, 1, l, g1);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const float rr0 = ym[0][j] - y1[0][j] + y2prev[j] - y2[0][j] - mu * cur.g[0][j];
-            const float rr1 = ym[1][j] - y1[1][j] + y2[0][j] - y2[1][j] - mu * cur.g[1][j];
+            const float rr0 = ym[0][j] - y1[0][j] + y2prev[j] - y2[0][j] - mu * g0[j];
+            const float rr1 = ym[1][j] - y1[1][j] + y2[0][j] - y2[1][j] - mu * g1[j];
             v[j] = make_float2(rr0, rr1);
         }
 #pragma unroll
@@ -359,8 +418,11 @@ __global__ void __launch_bounds__(RG_T, 2) k_usolve_reg128(
             ucur[j] = cur.u[1][j];
             y2prev[j] = y2[1][j];
         }
-        if (k + 1 < PPW) load_pair(cur, u, lsrc, wsrc, g, r0 + 2, l, pending);
-        fft128_fwd(v, tw, l);
+        if (k + 1 < PPW) {
+            load_pair(cur, u, lsrc, wsrc, r0 + 2, l, pending);
+            load_g(gp, gs, r0 + 2, l);
+        }
+        fft128_fwd(v, twl, l);
         // exchange row: Z[k] at its padded position, then the split of the pair
         const int br = bitrev5(l);
 #pragma unroll
@@ -388,7 +450,7 @@ __global__ void __launch_bounds__(RG_T, 2) k_usolve_reg128(
         float2 v[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) v[j] = col[l + 32 * j];
-        fft128_fwd(v, tw, l);
+        fft128_fwd(v, twl, l);
         const float s2q = s2_g[q];
 #pragma unroll
         for (int k1 = 0; k1 < 4; ++k1) {
@@ -396,7 +458,7 @@ __global__ void __launch_bounds__(RG_T, 2) k_usolve_reg128(
             v[k1].x *= rd;
             v[k1].y *= rd;
         }
-        fft128_inv(v, tw, l);
+        fft128_inv(v, twl, l);
 #pragma unroll
         for (int j = 0; j < 4; ++j) col[l + 32 * j] = v[j];
     }
@@ -432,7 +494,7 @@ __global__ void __launch_bounds__(RG_T, 2) k_usolve_reg128(
             }
             v[j] = make_float2(X.x - Y.y, -(X.y + Y.x));   // conj(X + i Y)
         }
-        fft128_fwd(v, tw, l);
+        fft128_fwd(v, twl, l);
         const int br = bitrev5(l);
         // conj of the result, through the exchange row into natural column order
 #pragma unroll
@@ -482,7 +544,7 @@ void launch_usolve_reg128(const TvArgs& a, cudaStream_t s)
 {
     k_usolve_reg128<<<a.nimg > 0 ? a.nimg : 1, RG_T, RG_SMEM, s>>>(
         a.u, a.w, a.lam, a.g, a.tw, a.s2, a.beta, a.mu_over_tau, a.mu, a.ctrl, a.mode, a.mu_img,
-        a.tau_img, a.tau, a.u_hi, a.u_lo, a.img_slot);
+        a.tau_img, a.tau, a.u_hi, a.u_lo, a.img_slot, a.gws, a.gtsb, a.gss, a.gws_cols, a.img_slot_prev);
 }
 
 }  // namespace tvcs

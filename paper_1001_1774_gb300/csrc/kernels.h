@@ -34,6 +34,14 @@ struct TvArgs {
     unsigned short* u_lo;
     const int* img_slot;        // nullable: row of image b's planes (compacted batch), else b
     int pdl;                    // launch with a programmatic dependency on the preceding grid
+    // k_usolve_reg128 only: g read as the sum of the stream-K partial tiles of the
+    // G = A^T R GEMM (tile t = image row t), in the order the fix-up adds them, when
+    // gws is set; the image's column in that GEMM is img_slot_prev[b] (else b)
+    const float* gws;
+    const int* gtsb;            // per tile: first segment (the GEMM plan's tile_seg_begin)
+    const int* gss;             // workspace slot of each segment (seg_slot)
+    int gws_cols;               // columns of a partial tile
+    const int* img_slot_prev;
 };
 
 bool tv_supported(int n);
@@ -133,6 +141,10 @@ bool make_bf16_map(CUtensorMap* map, const void* base, int inner, int rows, int 
 // (images) of Y; nact (nullable): the number of leading columns that take part,
 // read on the device.  The MMAs run with N = min(ncols, nact) rounded up to 32.
 constexpr int GEMM_Y_BOX = 32;
+// The fix-up adds a tile's first GEMM_FX_SEG partials (zeros past the last
+// segment) and then the rest, each from 0 in K order; readers of the partials
+// that stand in for the fix-up add them the same way.
+constexpr int GEMM_FX_SEG = 6;
 void launch_gemm(const CUtensorMap* xh, const CUtensorMap* xl, const CUtensorMap* yh,
                  const CUtensorMap* yl, const GemmPlan& p, float* ws, Ctrl* ctrl, int check_skip,
                  long long budget, cudaStream_t s, int ncols, const int* nact = nullptr);
@@ -221,12 +233,13 @@ void launch_dct_products(int n, const DctArgs& a, cudaStream_t s);
 
 // Loop condition of a batch: continue while any of ctrls[0..count) runs and
 // bctrl->loops stays below bctrl->loops_max (batch.cu).
-// With slot_img / img_slot set (count <= 256), also packs the running images
+// With slot_img / img_slot set (count <= 512), also packs the running images
 // into the leading slots in image order: slot_img[0 .. nact), img_slot[b] (-1 for
-// an image that stopped), bctrl->nact.
+// an image that stopped), bctrl->nact; img_slot_prev (nullable) receives the
+// slots of the iteration that just ended.
 void launch_batch_cond(const Ctrl* ctrls, int count, Ctrl* bctrl, unsigned long long cond,
                        int set_cond, cudaStream_t s, int* slot_img = nullptr,
-                       int* img_slot = nullptr);
+                       int* img_slot = nullptr, int* img_slot_prev = nullptr);
 
 // gather: out = scale * sum_p gpart[p], ctrl->vec2 = ||out||^2 (binary64)
 void launch_gather(const float* gpart, int P, int N, float scale, float* out, double* part,

@@ -329,6 +329,42 @@ def test_batched_compaction_is_exact(tv):
         check_converged(A, F[b], 32, mus[b], 20.0, tau, 1e-4, 3000, uc[b], rc[b])
 
 
+def test_batched_compaction_is_exact_n128(tv):
+    # 128 x 128 images: the u-solve adds the partial tiles of G = A^T R itself (no second
+    # fix-up inside the loop), each image reading its column of the iteration that just
+    # ended, and G is formed once at the end of the run.  Images stop at different
+    # iterations; the compacted run (columns move as images leave) equals the run that
+    # keeps every column bit for bit, and an image matches the oracle at convergence.
+    count = 24
+    A, ubars, F, mus, _ = synth.workload_shared_batch(count=count, n=128, ratio=0.3, seed=6, n_ellipses=6)
+    m, N = A.shape
+    tau = oracle.default_tau(A)
+    mus = [100.0 * 1.35 ** (b % 8) for b in range(count)]
+    out = {}
+    for compact in (1, 0):
+        opt = tv.tvcs_default_options()
+        opt.precision = tv.TVCS_PREC_BF16X2
+        opt.tau = tau
+        opt.max_iter = 4000
+        opt.batch_compact = compact
+        h = tv.tvcs_create(torch.from_numpy(A).cuda(), 0, m, 128, 1e3, 10.0, 1e-4, opt)
+        us = [np.empty(N, np.float32) for _ in range(count)]
+        res = tv.tvcs_solve_batched([h] * count, [F[b] for b in range(count)], us, mus)
+        out[compact] = (us, res)
+        tv.tvcs_destroy(h)
+    (uc, rc), (uf, rf) = out[1], out[0]
+    iters = [r.iters for r in rc]
+    print("stop iterations", sorted(set(iters)))
+    assert len(set(iters)) >= 4 and all(r.stopped_by_tol == 1 for r in rc)
+    assert iters == [r.iters for r in rf]
+    for b in range(count):
+        assert np.array_equal(uc[b], uf[b]), b
+        assert rc[b].objective == rf[b].objective
+        assert rc[b].kkt_dual == rf[b].kkt_dual   # the end-of-run G
+    b = int(np.argmin(iters))
+    check_converged(A, F[b], 128, mus[b], 10.0, tau, 1e-4, 4000, uc[b], rc[b])
+
+
 def test_batched_converges_with_the_shared_batch_parameters(tv):
     # The shared-A batch's parameters (mu cycling over 2e2, 5e2, 1e3, 2e3, beta = 10,
     # noise U[1e-3, 1e-2] RMS, tol 1e-4) at n = 32, m = 307 (ratio 0.3), where the FP64
