@@ -26,11 +26,13 @@
 //   B  per column q = 0..64: forward transform, divide by beta Lambda_pq + mu/tau,
 //      inverse transform, in registers;
 //   C  per pair of rows: the packed inverse row transform (through the same
-//      forward code on the conjugate), u += d, bf16 planes, double-single norms;
+//      forward code on the conjugate), u += d, bf16 planes, the norms (each
+//      lane's 8 squares of a pair in binary32, then double-single across pairs);
 // then the block's sums and eq. (stop).  Shared memory: the half spectrum
 // (65 columns of 129 complex values) and one 128-value exchange row per warp:
 // 75 KB; two images per SM (256 images in one wave), with the registers of
 // that occupancy holding the next pair's loads while a pair is transformed.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -469,6 +471,7 @@ __global__ void __launch_bounds__(RG_T, 2) k_usolve_reg128(
     float2 du2 = make_float2(0.f, 0.f), u2 = make_float2(0.f, 0.f);
     for (int pr = warp; pr < NN / 2; pr += RG_WARPS) {
         const int r0 = 2 * pr;
+        float du2p = 0.f, u2p = 0.f;   // this lane's 8 squares of the pair, in binary32
         float uo[2][4];   // u of the pair, loaded before the transform that hides the latency
 #pragma unroll
         for (int h = 0; h < 2; ++h)
@@ -509,21 +512,22 @@ __global__ void __launch_bounds__(RG_T, 2) k_usolve_reg128(
                 const int gi = (r0 + h) * NN + c;
                 const float d = (h == 0 ? z.x : z.y) * sc;
                 const float o = uo[h][j];
-                du2 = ds_add(du2, ds_sq(d));
-                u2 = ds_add(u2, ds_sq(o));
+                du2p = fmaf(d, d, du2p);
+                u2p = fmaf(o, o, u2p);
                 const float nw = o + d;
                 u[gi] = nw;
-                if (u_hi) {
-                    const unsigned int bits = __float_as_uint(nw);
-                    const unsigned int hb = (bits + 0x7fffu + ((bits >> 16) & 1u)) & 0xffff0000u;
-                    const float rem = nw - __uint_as_float(hb);
-                    const unsigned int rb = __float_as_uint(rem);
-                    const unsigned int lb = (rb + 0x7fffu + ((rb >> 16) & 1u)) & 0xffff0000u;
-                    u_hi[gi] = (unsigned short)(hb >> 16);
-                    u_lo[gi] = (unsigned short)(lb >> 16);
+                if (u_hi) {   // bf16 hi = RN(u), lo = RN(u - hi)
+                    const __nv_bfloat16 hb = __float2bfloat16_rn(nw);
+                    const __nv_bfloat16 lb = __float2bfloat16_rn(nw - __bfloat162float(hb));
+                    u_hi[gi] = __bfloat16_as_ushort(hb);
+                    u_lo[gi] = __bfloat16_as_ushort(lb);
                 }
             }
         }
+        // the pair's sums (relative error at most 8 x 2^-24) into the double-single
+        // totals of eq. (stop)
+        du2 = ds_add(du2, make_float2(du2p, 0.f));
+        u2 = ds_add(u2, make_float2(u2p, 0.f));
         __syncwarp();
     }
     block_sum_ds2(du2, u2, red);
