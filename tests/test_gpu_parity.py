@@ -498,3 +498,32 @@ def test_beta_continuation_matches_oracle_stages(tv, algo):
     assert np.array_equal(u1, u2)
     tv.tvcs_destroy(h)
     tv.tvcs_destroy(h2)
+
+
+# ----------------------------------------------------------------------------- reduction accuracy
+
+@pytest.mark.parametrize("n,m,precision", [(128, 4915, 0), (128, 4915, 1), (32, 307, 0)])
+def test_resid2_is_the_binary64_sum_of_the_stored_residual(tv, n, m, precision):
+    # ||r||^2 of eq. (stop) and of the objective is summed on the device in double-single
+    # binary32 pairs (exact squares, renormalised additions: about 44 bits), not in
+    # binary64.  Against the binary64 sum of the squares of the same stored binary32
+    # residual it agrees to 1e-9 of the sum (m <= 4915 additions of at most 2^-44
+    # each bound it by 3e-10); a plain binary32 sum misses by 1e-7 to 1e-5.
+    P = small_problem(n, m, seed=21)
+    opt = tv.tvcs_default_options()
+    opt.tau = oracle.default_tau(P.A)
+    opt.precision = precision
+    opt.max_iter = 30
+    h = tv.tvcs_create(torch.from_numpy(P.A).cuda(), 0, P.m, P.n, P.mu, P.beta, 0.0, opt)
+    u = np.empty(P.N, np.float32)
+    tv.tvcs_solve(h, P.f, u)
+    for k in (1, 7):
+        res = tv.tvcs_iterate(h, k)
+        r = np.empty(P.m, np.float32)
+        tv.tvcs_get_state(h, tv.TVCS_STATE_R, r)
+        exact = float(np.sum(r.astype(np.float64) ** 2))
+        naive = float(np.sum(r * r, dtype=np.float32))
+        print("n %d prec %d: resid2 rel err %.2e (binary32 sum %.2e)"
+              % (n, precision, abs(res.resid2 - exact) / exact, abs(naive - exact) / exact))
+        assert abs(res.resid2 - exact) <= 1e-9 * exact
+    tv.tvcs_destroy(h)
