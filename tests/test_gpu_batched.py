@@ -365,6 +365,43 @@ def test_batched_compaction_is_exact_n128(tv):
     check_converged(A, F[b], 128, mus[b], 10.0, tau, 1e-4, 4000, uc[b], rc[b])
 
 
+@pytest.mark.parametrize("n,count,mu0", [(32, 400, 20.0), (128, 300, 100.0)])
+def test_batched_compaction_above_256_images_is_exact(tv, n, count, mu0):
+    # More than 256 images in one group: the pair GEMMs run two N tiles per tile of A,
+    # and as images stop the running columns fall below 256, so the second N tile
+    # empties; at n = 128 the u-solve also reads G's partial tiles by each image's
+    # column of the iteration that just ended.  The compacted run equals the run that
+    # keeps every column, bit for bit.
+    A, ubars, F, mus, _ = synth.workload_shared_batch(count=count, n=n, ratio=0.3, seed=8, n_ellipses=6)
+    m, N = A.shape
+    tau = oracle.default_tau(A)
+    mus = [mu0 * 1.35 ** (b % 8) for b in range(count)]
+    beta = 20.0 if n == 32 else 10.0
+    out = {}
+    for compact in (1, 0):
+        opt = tv.tvcs_default_options()
+        opt.precision = tv.TVCS_PREC_BF16X2
+        opt.tau = tau
+        opt.max_iter = 4000
+        opt.batch_compact = compact
+        h = tv.tvcs_create(torch.from_numpy(A).cuda(), 0, m, n, 1e3, beta, 1e-4, opt)
+        Fd = torch.from_numpy(F).cuda()
+        U = torch.empty((count, N), dtype=torch.float32, device="cuda")
+        res = tv.tvcs_solve_batched([h] * count, [Fd[b] for b in range(count)], [U[b] for b in range(count)], mus)
+        out[compact] = (U.cpu().numpy(), res)
+        tv.tvcs_destroy(h)
+    (uc, rc), (uf, rf) = out[1], out[0]
+    iters = [r.iters for r in rc]
+    print("n %d, %d images: stop iterations %d .. %d (%d distinct)" % (n, count, min(iters), max(iters),
+                                                                        len(set(iters))))
+    # columns leave at many different iterations (a few images may reach the cap)
+    assert len(set(iters)) >= 4 and sum(r.stopped_by_tol for r in rc) >= count // 2
+    assert iters == [r.iters for r in rf]
+    assert np.array_equal(uc, uf)
+    for b in range(count):
+        assert rc[b].objective == rf[b].objective and rc[b].kkt_dual == rf[b].kkt_dual, b
+
+
 def test_batched_converges_with_the_shared_batch_parameters(tv):
     # The shared-A batch's parameters (mu cycling over 2e2, 5e2, 1e3, 2e3, beta = 10,
     # noise U[1e-3, 1e-2] RMS, tol 1e-4) at n = 32, m = 307 (ratio 0.3), where the FP64
