@@ -228,6 +228,19 @@ def batch_launch_iters(iters):
     return -(-iters // 4) * 4
 
 
+def batch_launches(iters, g_in_usolve=True):
+    """Kernels one shared-A batched solve launches: u^0 = A^T F (bf16 split of F, GEMM,
+    fix-up, split of u^0), the first products (GEMM, fix-up, GEMM and, unless the
+    u-solve adds G's partial tiles itself as it does for 128 x 128 images, G's
+    fix-up), per launched iteration the u-solve, two GEMMs, one or two fix-ups and
+    the condition kernel, then G formed after the loop when the loop left it in
+    partial tiles (split of R, GEMM, fix-up) and the end-of-run kernels (residual,
+    its norm, the two final kernels)."""
+    per_iter = 5 if g_in_usolve else 6
+    fixed = 4 + (3 if g_in_usolve else 4) + (3 if g_in_usolve else 0) + 4
+    return per_iter * batch_launch_iters(iters) + fixed
+
+
 def loop_launch_iters(iters, max_iter=None):
     """Iterations whose kernels a single-image run launches: the run's first
     16 * (max_iter // 16) iterations go through a WHILE graph of 16-iteration
@@ -578,14 +591,14 @@ def batch_segment(tv, steps, warmup, stream, want_parity=True, images=256, gemm_
            "unit": "image-iter/s", "steps": steps, "recons_per_s": value / ITERS_PER_RECON,
            "ms_per_step": ms / steps,
            "roofline": {"bound": "tensor", "achieved": tf, "peak": peak[0], "unit": "TFLOP/s",
-                        "frac": tf / peak[0], "kernel": "k_gemm_bf16x3 pair (R = A U, G = A^T R)",
+                        "frac": tf / peak[0], "kernel": "the two batched GEMMs, R = A U and G = A^T R (k_gemm_bf16x3_pair on CTA pairs or k_gemm_bf16x3, the shape the tuner picks)",
                         "flops_per_iteration": flops, "launch_pair_us": gemm_us,
                         "peak_source": peak[1]},
            "stage_us": {"gemm_pair": gemm_us, "fixups": fix_us, "usolve_batched": us_us,
                         "loop_per_iteration": loop_ms * 1e3 / steps},
            "e2e": {"value": B * steps / e2e_s, "unit": "image-iter/s",
                    "h2d_bytes_per_step": 4 * m * B / steps, "d2h_bytes_per_step": 4 * N * B / steps},
-           "gpu_launches": groups * (6 * batch_launch_iters(steps) + 8), "clocks": clocks, "tau": tau,
+           "gpu_launches": groups * batch_launches(steps), "clocks": clocks, "tau": tau,
            "groups": groups, "_A": A, "_F": F, "_mus": mus}
     if want_parity:
         import oracle
@@ -985,7 +998,7 @@ def run_batched_tol(args):
                         "kernel": "k_gemm_bf16x3 (columns = running images); see --workload batch256"},
            "e2e": {"value": B / e2e_s, "unit": "recons/s", "h2d_bytes_per_step": 4 * m * B / its_a.max(),
                    "d2h_bytes_per_step": 4 * N * B / its_a.max()},
-           "gpu_launches": 6 * batch_launch_iters(int(its_a.max())) + 8, "clocks": clocks, "tau": tau}
+           "gpu_launches": batch_launches(int(its_a.max())), "clocks": clocks, "tau": tau}
     print(json.dumps(out), flush=True)
 
 def bf16_peak():

@@ -88,3 +88,6 @@ def test_launch_counts_include_the_skipped_tail_of_a_loop_body():
     assert [bench.loop_launch_iters(k, 5000) for k in (1, 16, 17, 2403, 4995, 5000)] == \
         [24, 24, 40, 2424, 5000, 5000]
     assert [bench.batch_launch_iters(k) for k in (1, 4, 7, 300)] == [4, 4, 8, 300]
+    # a 128 x 128 batch (G's partial tiles added by the u-solve) against another side
+    assert bench.batch_launches(300) == 5 * 300 + 14
+    assert bench.batch_launches(7, g_in_usolve=False) == 6 * 8 + 12
