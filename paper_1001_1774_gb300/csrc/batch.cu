@@ -568,13 +568,16 @@ void batch_products(tvcs_ctx* h, int count, bool subtract_f, cudaStream_t s, boo
     const int* nact = compact ? &b->bctrl->nact : nullptr;
     const int* slot = compact ? b->slot_img : nullptr;
     const int chk = in_loop ? 1 : 0;
+    // in the loop both GEMMs overlap the tail of the preceding kernel (the u-solve, R's
+    // fix-up) with their first copies of A
+    const int pdl = in_loop && h->pdl ? 1 : 0;
     launch_gemm(&b->mAh, &b->mAl, &b->mUh, &b->mUl, b->p1, b->ws, b->bctrl, chk, budget, s, count,
-                nact);
+                nact, pdl);
     launch_gemm_fixup(b->ws, b->tsb1, b->ss1, h->m, b->p1.tiles_m, b->p1.nt * 256, count,
                       subtract_f ? b->F : nullptr, h->m, b->R, h->m, b->Rh, b->Rl, b->mpad,
                       b->r2part, b->bctrl, chk, s, slot, nact);
     launch_gemm(&b->mAth, &b->mAtl, &b->mRh, &b->mRl, b->p2, b->ws, b->bctrl, chk, budget, s, count,
-                nact);
+                nact, pdl);
     if (g_partials) return;   // the next u-solve adds G's partial tiles itself
     launch_gemm_fixup(b->ws, b->tsb2, b->ss2, h->N, b->p2.tiles_m, b->p2.nt * 256, count, nullptr, 0, b->G, h->N,
                       nullptr, nullptr, 0, nullptr, b->bctrl, chk, s, slot, nact);

@@ -190,27 +190,44 @@ __global__ void __launch_bounds__(192, 1)
         if (lane == 0) {
             // ---------------- TMA producer ----------------
             bool ok = true;
-            long long it = 0;
             const uint64_t pol_x = l2_policy_evict_first(), pol_y = l2_policy_evict_last();
-            for (long long w = w0; w < w1; ++w, ++it) {
-                const int s = (int)(it % GM_NST);
-                if (it >= GM_NST && !mbar_wait(&empty[s], (uint32_t)((it / GM_NST) - 1) & 1u, budget)) {
-                    set_error(ctrl, ERR_TIMEOUT);
-                    ok = false;
-                    break;
-                }
+            auto load_x = [&](long long it_, long long w) {   // X: tile-contiguous A or A^T
+                const int s = (int)(it_ % GM_NST);
                 const int t = (int)(w / kblocks), kb = (int)(w % kblocks);
                 unsigned char* st = smem + (size_t)s * GM_STAGE;
                 mbar_arrive_expect_tx(&full[s], stage_bytes);
-                const int xrow = (t * kblocks + kb) * GM_BM;   // tile-contiguous X (k_tile_planes)
+                const int xrow = (t * kblocks + kb) * GM_BM;
                 tma_load_2d(st, &tXh, 0, xrow, &full[s], pol_x);
                 tma_load_2d(st + GM_A_BYTES, &tXl, 0, xrow, &full[s], pol_x);
+            };
+            auto load_y = [&](long long it_, long long w) {   // Y: the images' planes
+                const int s = (int)(it_ % GM_NST);
+                const int kb = (int)(w % kblocks);
+                unsigned char* st = smem + (size_t)s * GM_STAGE;
                 for (int j = 0; j < ybox; ++j) {   // 32-row boxes, 1024-byte aligned
                     tma_load_2d(st + 2 * GM_A_BYTES + j * GM_YBOX_BYTES, &tYh, kb * GM_BK,
                                 j * GEMM_Y_BOX, &full[s], pol_y);
                     tma_load_2d(st + 2 * GM_A_BYTES + GM_B_BYTES + j * GM_YBOX_BYTES, &tYl,
                                 kb * GM_BK, j * GEMM_Y_BOX, &full[s], pol_y);
                 }
+            };
+            // The first stages' X halves do not depend on the preceding kernel: under a
+            // programmatic dependent launch they stream in before its end; Y (the
+            // images' planes it writes) only after the wait.
+            const long long npre = min((long long)GM_NST, w1 - w0);
+            for (long long j = 0; j < npre; ++j) load_x(j, w0 + j);
+            pdl_wait();
+            for (long long j = 0; j < npre; ++j) load_y(j, w0 + j);
+            long long it = npre;
+            for (long long w = w0 + npre; w < w1; ++w, ++it) {
+                const int s = (int)(it % GM_NST);
+                if (!mbar_wait(&empty[s], (uint32_t)((it / GM_NST) - 1) & 1u, budget)) {
+                    set_error(ctrl, ERR_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+                load_x(it, w);
+                load_y(it, w);
             }
             // leave no copy in flight
             const long long n_issued = it;
@@ -492,16 +509,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
         if (lane == 0) {
             // ---------------- TMA producer (both blocks) ----------------
             bool ok = true;
-            long long it = 0;
             const uint64_t pol_x = l2_policy_evict_first(), pol_y = l2_policy_evict_last();
-            for (long long w = w0; w < w1; ++w, ++it) {
-                const int s = (int)(it % GP_NST);
-                if (it >= GP_NST &&
-                    !mbar_wait_cluster(&empty[s], (uint32_t)((it / GP_NST) - 1) & 1u, budget)) {
-                    set_error(ctrl, ERR_TIMEOUT);
-                    ok = false;
-                    break;
-                }
+            auto load_x = [&](long long it_, long long w) {
+                const int s = (int)(it_ % GP_NST);
                 const int t = (int)(w / kblocks), kb = (int)(w % kblocks);
                 unsigned char* st = smem + (size_t)s * stage_bytes;
                 mbar_arrive_expect_tx(&full[s], stage_bytes);
@@ -509,6 +519,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
                 const int xrow = ((2 * t + (int)rank) * kblocks + kb) * GM_BM;
                 tma_load_2d(st, &tXh, 0, xrow, &full[s], pol_x);
                 tma_load_2d(st + GM_A_BYTES, &tXl, 0, xrow, &full[s], pol_x);
+            };
+            auto load_y = [&](long long it_, long long w) {
+                const int s = (int)(it_ % GP_NST);
+                const int kb = (int)(w % kblocks);
+                unsigned char* st = smem + (size_t)s * stage_bytes;
 #pragma unroll
                 for (int n = 0; n < NT; ++n) {       // this block's half of each N tile
                     unsigned char* yst = st + yoff[n];
@@ -519,6 +534,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
                                     &full[s], pol_y);
                     }
                 }
+            };
+            // the first stages' X halves before the wait on the preceding kernel, Y after it
+            const long long npre = min((long long)GP_NST, w1 - w0);
+            for (long long j = 0; j < npre; ++j) load_x(j, w0 + j);
+            pdl_wait();
+            for (long long j = 0; j < npre; ++j) load_y(j, w0 + j);
+            long long it = npre;
+            for (long long w = w0 + npre; w < w1; ++w, ++it) {
+                const int s = (int)(it % GP_NST);
+                if (!mbar_wait_cluster(&empty[s], (uint32_t)((it / GP_NST) - 1) & 1u, budget)) {
+                    set_error(ctrl, ERR_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+                load_x(it, w);
+                load_y(it, w);
             }
             // leave no copy in flight; on the even block a stage's phase also
             // needs the odd block's arrival, hence the drain bound
@@ -669,6 +700,7 @@ __global__ void __launch_bounds__(128) k_gemm_fixup(
     const int* __restrict__ nact)
 {
     __shared__ float2 red[4][FX_B];
+    pdl_release();   // the next GEMM may start its independent prologue (it waits before reading R)
     if (check_skip && ctrl->skip) return;
     const int t = blockIdx.x, b0 = blockIdx.y * FX_B;
     if (nact) count = min(count, *nact);
@@ -901,17 +933,27 @@ int gemm_pair_max_clusters(int num_sms)
 
 void launch_gemm(const CUtensorMap* xh, const CUtensorMap* xl, const CUtensorMap* yh,
                  const CUtensorMap* yl, const GemmPlan& p, float* ws, Ctrl* ctrl, int check_skip,
-                 long long budget, cudaStream_t s, int ncols, const int* nact)
+                 long long budget, cudaStream_t s, int ncols, const int* nact, int pdl)
 {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)p.grid, 1, 1);
+    cfg.blockDim = dim3(192, 1, 1);
+    cfg.dynamicSmemBytes = p.pair ? GP_SMEM : GM_SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
     if (p.pair && p.nt == 2)
-        k_gemm_bf16x3_pair<2><<<p.grid, 192, GP_SMEM, s>>>(
-            *xh, *xl, *yh, *yl, p.tiles, p.kblocks, ws, p.smax, ctrl, check_skip, budget, ncols, nact);
+        cudaLaunchKernelEx(&cfg, k_gemm_bf16x3_pair<2>, *xh, *xl, *yh, *yl, p.tiles, p.kblocks, ws,
+                           p.smax, ctrl, check_skip, budget, ncols, nact);
     else if (p.pair)
-        k_gemm_bf16x3_pair<1><<<p.grid, 192, GP_SMEM, s>>>(
-            *xh, *xl, *yh, *yl, p.tiles, p.kblocks, ws, p.smax, ctrl, check_skip, budget, ncols, nact);
+        cudaLaunchKernelEx(&cfg, k_gemm_bf16x3_pair<1>, *xh, *xl, *yh, *yl, p.tiles, p.kblocks, ws,
+                           p.smax, ctrl, check_skip, budget, ncols, nact);
     else
-        k_gemm_bf16x3<<<p.grid, 192, GM_SMEM, s>>>(*xh, *xl, *yh, *yl, p.tiles, p.kblocks, ws,
-                                                   p.smax, ctrl, check_skip, budget, ncols, nact);
+        cudaLaunchKernelEx(&cfg, k_gemm_bf16x3, *xh, *xl, *yh, *yl, p.tiles, p.kblocks, ws, p.smax,
+                           ctrl, check_skip, budget, ncols, nact);
 }
 
 void launch_gemm_fixup(const float* ws, const int* tile_seg_begin, const int* seg_slot, int M,

@@ -306,6 +306,7 @@ __global__ void __launch_bounds__(RG_T, 2) k_usolve_reg128(
     const int* __restrict__ gss, int gws_cols, const int* __restrict__ img_slot_prev)
 {
     constexpr int NN = RG_NN, N = RG_N;
+    pdl_release();   // the next GEMM may start its first copies of A (it waits before reading u)
     GSrc gs{gws, gtsb, gss, gws_cols, 0};
     {
         const int b = blockIdx.x;

@@ -147,10 +147,13 @@ constexpr int GEMM_Y_BOX = 32;
 constexpr int GEMM_FX_SEG = 6;
 void launch_gemm(const CUtensorMap* xh, const CUtensorMap* xl, const CUtensorMap* yh,
                  const CUtensorMap* yl, const GemmPlan& p, float* ws, Ctrl* ctrl, int check_skip,
-                 long long budget, cudaStream_t s, int ncols, const int* nact = nullptr);
+                 long long budget, cudaStream_t s, int ncols, const int* nact = nullptr,
+                 int pdl = 0);
 // Column j of the GEMM is image slot_img[j] (identity when slot_img is null) for
 // F, out and r2part; the bf16 planes out_hi/out_lo stay in column order.  With
 // nact set, only the first *nact columns are processed.
+// pdl: launch with a programmatic dependency on the preceding kernel (the GEMM issues
+// its first stages' copies of A before it waits for that kernel's output).
 // ws_cols: columns of a partial tile in the workspace (256 x the plan's nt).
 void launch_gemm_fixup(const float* ws, const int* tile_seg_begin, const int* seg_slot, int M,
                        int tiles_m, int ws_cols, int count, const float* F, int ldf, float* out, int ldo,
