@@ -68,8 +68,9 @@ __device__ __forceinline__ float2 shfl_xor2(float2 v, int m)
 
 // Per-lane twiddles, in a shared table twl[k][lane] (the same for every warp):
 // k = 0..2 the in-lane W128^(l (k+1)); k = 3 + s, for lane stage s (half h = 16 >> s),
-// W_{2h}^(l mod h) on the lanes that take the difference (l & h).  Forward values
-// (exp(-2 pi i t / n)); the inverse uses their conjugates.
+// W_{2h}^(l mod h) on the lanes that take the difference (l & h) and exactly 1 on
+// the others, so that every lane runs the same butterfly (a product by 1 is exact).
+// Forward values (exp(-2 pi i t / n)); the inverse uses their conjugates.
 __device__ __forceinline__ float2 lane_twiddle(const float2* __restrict__ tw128, int k, int l)
 {
     int t;
@@ -77,6 +78,7 @@ __device__ __forceinline__ float2 lane_twiddle(const float2* __restrict__ tw128,
         t = (l * (k + 1)) & (RG_NN - 1);
     } else {
         const int h = 16 >> (k - 3);
+        if ((l & h) == 0) return make_float2(1.f, 0.f);
         t = (4 * (l & (h - 1)) * (16 / h)) & (RG_NN - 1);   // exponent of W32, in W128 steps
     }
     const float2 c = tw128[t];   // (cos, sin)(2 pi t / 128)
@@ -109,17 +111,17 @@ __device__ __forceinline__ void fft128_fwd(float2 v[4], const float2* __restrict
     for (int k1 = 1; k1 < 4; ++k1) v[k1] = cmulf(v[k1], twl[(k1 - 1) * 32 + l]);
 #pragma unroll
     for (int s = 0; s < 5; ++s) {   // decimation in frequency across the lanes
-        const float2 ws = twl[(3 + s) * 32 + l];
+        // upper lanes (l & h) == 0 keep v + p, the others (p - v) W: one signed
+        // sum and a product by the lane's twiddle (1 on the upper lanes, and on
+        // every lane in the last stage, where it is left out)
         const int h = 16 >> s;
-        const bool lower = (l & h) != 0;
+        const float sg = (l & h) ? -1.f : 1.f;
+        const float2 ws = twl[(3 + (s < 4 ? s : 0)) * 32 + l];
 #pragma unroll
         for (int k1 = 0; k1 < 4; ++k1) {
             const float2 p = shfl_xor2(v[k1], h);
-            if (!lower) {
-                v[k1] = make_float2(v[k1].x + p.x, v[k1].y + p.y);
-            } else {
-                v[k1] = cmulf(make_float2(p.x - v[k1].x, p.y - v[k1].y), ws);
-            }
+            v[k1] = make_float2(fmaf(sg, v[k1].x, p.x), fmaf(sg, v[k1].y, p.y));
+            if (s < 4) v[k1] = cmulf(v[k1], ws);
         }
     }
 }
@@ -129,15 +131,16 @@ __device__ __forceinline__ void fft128_inv(float2 v[4], const float2* __restrict
 {
 #pragma unroll
     for (int s = 4; s >= 0; --s) {   // decimation in time across the lanes
-        const float2 ws = twl[(3 + s) * 32 + l];
+        // lanes (l & h) != 0 send v conj(W) and keep p - own, the others send v and
+        // keep own + p (twiddle 1 on the upper lanes and in the first stage)
         const int h = 16 >> s;
-        const bool lower = (l & h) != 0;
+        const float sg = (l & h) ? -1.f : 1.f;
+        const float2 ws = twl[(3 + (s < 4 ? s : 0)) * 32 + l];
 #pragma unroll
         for (int k1 = 0; k1 < 4; ++k1) {
-            const float2 own = lower ? cmulc(v[k1], ws) : v[k1];
+            const float2 own = s < 4 ? cmulc(v[k1], ws) : v[k1];
             const float2 p = shfl_xor2(own, h);
-            v[k1] = lower ? make_float2(p.x - own.x, p.y - own.y)
-                          : make_float2(own.x + p.x, own.y + p.y);
+            v[k1] = make_float2(fmaf(sg, own.x, p.x), fmaf(sg, own.y, p.y));
         }
     }
 #pragma unroll
