@@ -14,7 +14,13 @@
 // across the lanes (five radix-2 butterfly stages through shuffles, decimation
 // in frequency: lane l ends with k2 = bitrev5(l)).  The inverse runs the mirror
 // image (decimation in time from that order, twiddle, inverse radix-4), so a
-// forward transform followed by its inverse needs no reordering.
+// forward transform followed by its inverse needs no reordering.  Rows of the
+// image are read with lane l holding the contiguous columns c = 4 l + j (one
+// 16-byte access per lane and plane, a column shift in one shuffle); their
+// forward transform takes the other factor order, k = k1 + 32 k2 (k1 = 0..31):
+//     X[k1 + 32 k2] = sum_j W4^(j k2) * [ W128^(j k1) * sum_l x[4 l + j] W32^(l k1) ],
+// the same 32-point lane stages first (lane l ends with k1 = bitrev5(l)), then a
+// twiddle and the radix-4 DFT in registers.
 //
 // Phases (8 warps):
 //   A  per pair of rows (r0, r0+1), each warp down a stripe of 16 rows: the
@@ -50,8 +56,7 @@ constexpr int RG_QS = RG_NN + 1;         // column stride (complex)
 constexpr int RG_WARPS = 8;
 constexpr int RG_T = RG_WARPS * 32;
 constexpr int RG_XS = RG_NN + RG_NN / 16;   // exchange row of a warp, one pad per 16 values
-constexpr int RG_TWK = 8;                 // per-lane twiddles (3 in-lane, 5 lane stages)
-static_assert(RG_T == RG_TWK * 32, "one thread fills each entry of the lane twiddle table");
+constexpr int RG_TWK = 11;   // per-lane twiddles (3 in-lane, 5 lane stages, 3 for the contiguous rows)
 constexpr size_t RG_SMEM = ((size_t)RG_Q * RG_QS * 8 + 15) / 16 * 16 + (size_t)RG_WARPS * RG_XS * 8 + 64 * 8 +
                            (size_t)RG_TWK * 32 * 8;
 
@@ -69,13 +74,16 @@ __device__ __forceinline__ float2 shfl_xor2(float2 v, int m)
 // Per-lane twiddles, in a shared table twl[k][lane] (the same for every warp):
 // k = 0..2 the in-lane W128^(l (k+1)); k = 3 + s, for lane stage s (half h = 16 >> s),
 // W_{2h}^(l mod h) on the lanes that take the difference (l & h) and exactly 1 on
-// the others, so that every lane runs the same butterfly (a product by 1 is exact).
+// the others, so that every lane runs the same butterfly (a product by 1 is exact);
+// k = 8..10 the W128^(bitrev5(l) (k-7)) of the contiguous-row transform.
 // Forward values (exp(-2 pi i t / n)); the inverse uses their conjugates.
 __device__ __forceinline__ float2 lane_twiddle(const float2* __restrict__ tw128, int k, int l)
 {
     int t;
     if (k < 3) {
         t = (l * (k + 1)) & (RG_NN - 1);
+    } else if (k >= 8) {
+        t = (bitrev5(l) * (k - 7)) & (RG_NN - 1);
     } else {
         const int h = 16 >> (k - 3);
         if ((l & h) == 0) return make_float2(1.f, 0.f);
@@ -94,21 +102,23 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b)   // a * conj(b)
     return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 
-// Forward: v[j] = x[l + 32 j] in, v[k1] = X[k1 + 4 bitrev5(l)] out.
-__device__ __forceinline__ void fft128_fwd(float2 v[4], const float2* __restrict__ twl, int l)
+// Forward radix-4 DFT of the four values of a lane, W4 = -i.
+__device__ __forceinline__ void radix4_fwd(float2 v[4])
 {
-    {   // radix 4 over j, W4 = -i
-        const float2 s02 = make_float2(v[0].x + v[2].x, v[0].y + v[2].y);
-        const float2 d02 = make_float2(v[0].x - v[2].x, v[0].y - v[2].y);
-        const float2 s13 = make_float2(v[1].x + v[3].x, v[1].y + v[3].y);
-        const float2 d13 = make_float2(v[1].y - v[3].y, v[3].x - v[1].x);   // -i (v1 - v3)
-        v[0] = make_float2(s02.x + s13.x, s02.y + s13.y);
-        v[2] = make_float2(s02.x - s13.x, s02.y - s13.y);
-        v[1] = make_float2(d02.x + d13.x, d02.y + d13.y);
-        v[3] = make_float2(d02.x - d13.x, d02.y - d13.y);
-    }
-#pragma unroll
-    for (int k1 = 1; k1 < 4; ++k1) v[k1] = cmulf(v[k1], twl[(k1 - 1) * 32 + l]);
+    const float2 s02 = make_float2(v[0].x + v[2].x, v[0].y + v[2].y);
+    const float2 d02 = make_float2(v[0].x - v[2].x, v[0].y - v[2].y);
+    const float2 s13 = make_float2(v[1].x + v[3].x, v[1].y + v[3].y);
+    const float2 d13 = make_float2(v[1].y - v[3].y, v[3].x - v[1].x);   // -i (v1 - v3)
+    v[0] = make_float2(s02.x + s13.x, s02.y + s13.y);
+    v[2] = make_float2(s02.x - s13.x, s02.y - s13.y);
+    v[1] = make_float2(d02.x + d13.x, d02.y + d13.y);
+    v[3] = make_float2(d02.x - d13.x, d02.y - d13.y);
+}
+
+// For each of the four values of a lane, the forward 32-point DFT across the
+// lanes (lane l holds element l in, coefficient bitrev5(l) out).
+__device__ __forceinline__ void lanes_fwd(float2 v[4], const float2* __restrict__ twl, int l)
+{
 #pragma unroll
     for (int s = 0; s < 5; ++s) {   // decimation in frequency across the lanes
         // upper lanes (l & h) == 0 keep v + p, the others (p - v) W: one signed
@@ -124,6 +134,24 @@ __device__ __forceinline__ void fft128_fwd(float2 v[4], const float2* __restrict
             if (s < 4) v[k1] = cmulf(v[k1], ws);
         }
     }
+}
+
+// Forward: v[j] = x[l + 32 j] in, v[k1] = X[k1 + 4 bitrev5(l)] out.
+__device__ __forceinline__ void fft128_fwd(float2 v[4], const float2* __restrict__ twl, int l)
+{
+    radix4_fwd(v);
+#pragma unroll
+    for (int k1 = 1; k1 < 4; ++k1) v[k1] = cmulf(v[k1], twl[(k1 - 1) * 32 + l]);
+    lanes_fwd(v, twl, l);
+}
+
+// Forward on contiguous columns: v[j] = x[4 l + j] in, v[k2] = X[bitrev5(l) + 32 k2] out.
+__device__ __forceinline__ void fft128_fwd_c(float2 v[4], const float2* __restrict__ twl, int l)
+{
+    lanes_fwd(v, twl, l);
+#pragma unroll
+    for (int j = 1; j < 4; ++j) v[j] = cmulf(v[j], twl[(7 + j) * 32 + l]);
+    radix4_fwd(v);
 }
 
 // Inverse (unnormalised): v[k1] = X[k1 + 4 bitrev5(l)] in, v[j] = x[l + 32 j] out.
@@ -157,29 +185,43 @@ __device__ __forceinline__ void fft128_inv(float2 v[4], const float2* __restrict
     }
 }
 
-// The value of lane l-1 (lane 0: lane 31's value of the previous j; column c-1).
+// Rows with lane l holding columns 4 l + j: the value at column c - 1 (periodic;
+// column 4 l - 1 is lane l - 1's last value, lane 0 takes lane 31's).
 __device__ __forceinline__ void shift_left_cols(const float v[4], float out[4], int l)
 {
-    float s[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) s[j] = __shfl_sync(0xffffffffu, v[j], (l + 31) & 31);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) out[j] = (l == 0) ? s[(j + 3) & 3] : s[j];
+    out[0] = __shfl_sync(0xffffffffu, v[3], (l + 31) & 31);
+    out[1] = v[0];
+    out[2] = v[1];
+    out[3] = v[2];
 }
 
-// The value of lane l+1 (lane 31: lane 0's value of the next j; column c+1).
+// The value at column c + 1 (column 4 l + 4 is lane l + 1's first value, lane 31
+// takes lane 0's).
 __device__ __forceinline__ void shift_right_cols(const float v[4], float out[4], int l)
 {
-    float s[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) s[j] = __shfl_sync(0xffffffffu, v[j], (l + 1) & 31);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) out[j] = (l == 31) ? s[(j + 1) & 3] : s[j];
+    out[0] = v[1];
+    out[1] = v[2];
+    out[2] = v[3];
+    out[3] = __shfl_sync(0xffffffffu, v[0], (l + 1) & 31);
+}
+
+__device__ __forceinline__ void ld4(const float* __restrict__ p, float (&v)[4])
+{
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+}
+
+__device__ __forceinline__ void st4(float* __restrict__ p, const float (&v)[4])
+{
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
 // Multiplier update of eq. (udlamb) (when an iteration is pending), shrink of
 // eq. (shrink) and y = beta (w - Du) - lambda for one row held as columns
-// l + 32 j: uc is the row, ud the row below it (periodic), l1/l2 the
+// 4 l + j: uc is the row, ud the row below it (periodic), l1/l2 the
 // multipliers (updated in place), wo1/wo2 the previous w (read when pending).
 __device__ __forceinline__ void shrink_row(const float (&uc)[4], const float (&ud)[4], float (&l1)[4],
                                            float (&l2)[4], const float (&wo1)[4], const float (&wo2)[4],
@@ -243,15 +285,16 @@ __device__ __forceinline__ void load_pair(PairIn& in, const float* __restrict__ 
 {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
+        const int gi = (r0 + h) * RG_NN + 4 * l;
+        ld4(u + ((r0 + 1 + h) & (RG_NN - 1)) * RG_NN + 4 * l, in.u[h]);
+        ld4(lsrc + gi, in.l1[h]);
+        ld4(lsrc + RG_N + gi, in.l2[h]);
+        if (pending) {
+            ld4(wsrc + gi, in.w1[h]);
+            ld4(wsrc + RG_N + gi, in.w2[h]);
+        } else {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int c = l + 32 * j;
-            const int gi = (r0 + h) * RG_NN + c;
-            in.u[h][j] = u[((r0 + 1 + h) & (RG_NN - 1)) * RG_NN + c];
-            in.l1[h][j] = lsrc[gi];
-            in.l2[h][j] = lsrc[RG_N + gi];
-            in.w1[h][j] = pending ? wsrc[gi] : 0.0f;
-            in.w2[h][j] = pending ? wsrc[RG_N + gi] : 0.0f;
+            for (int j = 0; j < 4; ++j) in.w1[h][j] = in.w2[h][j] = 0.0f;
         }
     }
 }
@@ -265,16 +308,17 @@ __device__ __forceinline__ void load_g(PairG& in, const GSrc& gs, int r0, int l)
         in.ns[h] = ns;
         const float* p0 = gs.ws + ((size_t)gs.ss[s0] * gs.cols + gs.col) * RG_NN;
         const float* p1 = ns > 1 ? gs.ws + ((size_t)gs.ss[s0 + 1] * gs.cols + gs.col) * RG_NN : nullptr;
+        ld4(p0 + 4 * l, in.g[h]);
+        if (p1) {
+            ld4(p1 + 4 * l, in.g1[h]);
+        } else {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int c = l + 32 * j;
-            in.g[h][j] = p0[c];
-            in.g1[h][j] = p1 ? p1[c] : 0.0f;
+            for (int j = 0; j < 4; ++j) in.g1[h][j] = 0.0f;
         }
     }
 }
 
-// g of row r0 + h at columns l + 32 j, bitwise the fix-up's sum: it adds from +0
+// g of row r0 + h at columns 4 l + j, bitwise the fix-up's sum: it adds from +0
 // the first GEMM_FX_SEG partials (zeros past the last segment), then the rest, in
 // K order.  A sum that starts at +0 is never -0 after its first addition, and x + 0
 // is x for every other x, so the padding zeros change nothing: the sum from +0 over
@@ -290,8 +334,10 @@ __device__ __forceinline__ void g_row(const PairG& in, const GSrc& gs, int h, in
     }
     for (int q = 2; q < in.ns[h]; ++q) {   // tiles of more than two segments
         const float* p = gs.ws + ((size_t)gs.ss[in.s0[h] + q] * gs.cols + gs.col) * RG_NN;
+        float t[4];
+        ld4(p + 4 * l, t);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) g[j] += p[l + 32 * j];
+        for (int j = 0; j < 4; ++j) g[j] += t[j];
     }
 }
 
@@ -351,7 +397,7 @@ __global__ void __launch_bounds__(RG_T, 2) k_usolve_reg128(
     const float* lsrc = lbuf + (size_t)par * 2 * N;
     float* wdst = wbuf + (size_t)(par ^ 1) * 2 * N;
     float* ldst = lbuf + (size_t)(par ^ 1) * 2 * N;
-    twl[tid] = lane_twiddle(tw_g, tid >> 5, l);   // RG_T = RG_TWK * 32 entries, one per thread
+    for (int e = tid; e < RG_TWK * 32; e += RG_T) twl[e] = lane_twiddle(tw_g, e >> 5, e & 31);
     __syncthreads();
     const float inv_beta = 1.0f / beta;
 
@@ -366,16 +412,15 @@ __global__ void __launch_bounds__(RG_T, 2) k_usolve_reg128(
     float ucur[4], y2prev[4];   // u row r0 and y2 of row r0 - 1
     {
         const int rp = (R0 - 1 + NN) & (NN - 1);
-        float ur[4], lr1[4], lr2[4], wr1[4], wr2[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int gi = rp * NN + l + 32 * j;
-            ur[j] = u[gi];
-            ucur[j] = u[R0 * NN + l + 32 * j];
-            lr1[j] = lsrc[gi];
-            lr2[j] = lsrc[N + gi];
-            wr1[j] = pending ? wsrc[gi] : 0.0f;
-            wr2[j] = pending ? wsrc[N + gi] : 0.0f;
+        const int gi = rp * NN + 4 * l;
+        float ur[4], lr1[4], lr2[4], wr1[4] = {0.f, 0.f, 0.f, 0.f}, wr2[4] = {0.f, 0.f, 0.f, 0.f};
+        ld4(u + gi, ur);
+        ld4(u + R0 * NN + 4 * l, ucur);
+        ld4(lsrc + gi, lr1);
+        ld4(lsrc + N + gi, lr2);
+        if (pending) {
+            ld4(wsrc + gi, wr1);
+            ld4(wsrc + N + gi, wr2);
         }
         float y1d[4], w1d[4], w2d[4];
         shrink_row(ur, ucur, lr1, lr2, wr1, wr2, pending, beta, inv_beta, l, y1d, y2prev, w1d, w2d);
@@ -396,14 +441,11 @@ __global__ void __launch_bounds__(RG_T, 2) k_usolve_reg128(
             else
                 shrink_row(cur.u[0], cur.u[1], cur.l1[1], cur.l2[1], cur.w1[1], cur.w2[1], pending, beta,
                            inv_beta, l, y1[1], y2[1], w1, w2);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int gi = (r0 + h) * NN + l + 32 * j;
-                wdst[gi] = w1[j];
-                wdst[N + gi] = w2[j];
-                ldst[gi] = cur.l1[h][j];
-                ldst[N + gi] = cur.l2[h][j];
-            }
+            const int gi = (r0 + h) * NN + 4 * l;
+            st4(wdst + gi, w1);
+            st4(wdst + N + gi, w2);
+            st4(ldst + gi, cur.l1[h]);
+            st4(ldst + N + gi, cur.l2[h]);
         }
         // right-hand side of rows r0, r0+1 packed: z = rhs[r0] + i rhs[r0+1]
         float2 v[4];
@@ -428,11 +470,11 @@ __global__ void __launch_bounds__(RG_T, 2) k_usolve_reg128(
             load_pair(cur, u, lsrc, wsrc, r0 + 2, l, pending);
             load_g(gp, gs, r0 + 2, l);
         }
-        fft128_fwd(v, twl, l);
+        fft128_fwd_c(v, twl, l);
         // exchange row: Z[k] at its padded position, then the split of the pair
         const int br = bitrev5(l);
 #pragma unroll
-        for (int k1 = 0; k1 < 4; ++k1) xrow[xpos(k1 + 4 * br)] = v[k1];
+        for (int k2 = 0; k2 < 4; ++k2) xrow[xpos(br + 32 * k2)] = v[k2];
         __syncwarp();
         for (int q = l; q < RG_Q; q += 32) {
             const float2 a = xrow[xpos(q)];
@@ -476,11 +518,9 @@ __global__ void __launch_bounds__(RG_T, 2) k_usolve_reg128(
     for (int pr = warp; pr < NN / 2; pr += RG_WARPS) {
         const int r0 = 2 * pr;
         float du2p = 0.f, u2p = 0.f;   // this lane's 8 squares of the pair, in binary32
-        float uo[2][4];   // u of the pair, loaded before the transform that hides the latency
+        float uo[2][4];   // u of the pair at columns 4 l + j, loaded before the transform that hides the latency
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) uo[h][j] = u[(r0 + h) * NN + l + 32 * j];
+        for (int h = 0; h < 2; ++h) ld4(u + (r0 + h) * NN + 4 * l, uo[h]);
         // packed inverse input Z[q] = X[q] + i Y[q] (q >= 65 by conjugate symmetry);
         // transformed with the forward code on conj(Z): x = conj(F(conj Z))
         float2 v[4];
@@ -507,25 +547,32 @@ __global__ void __launch_bounds__(RG_T, 2) k_usolve_reg128(
 #pragma unroll
         for (int k1 = 0; k1 < 4; ++k1) xrow[xpos(k1 + 4 * br)] = make_float2(v[k1].x, -v[k1].y);
         __syncwarp();
+        float2 z[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int c = l + 32 * j;
-            const float2 z = xrow[xpos(c)];
+        for (int j = 0; j < 4; ++j) z[j] = xrow[xpos(4 * l + j)];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int gi = (r0 + h) * NN + c;
-                const float d = (h == 0 ? z.x : z.y) * sc;
+        for (int h = 0; h < 2; ++h) {
+            const int gi = (r0 + h) * NN + 4 * l;
+            float nw[4];
+            unsigned short hi[4], lo[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float d = (h == 0 ? z[j].x : z[j].y) * sc;
                 const float o = uo[h][j];
                 du2p = fmaf(d, d, du2p);
                 u2p = fmaf(o, o, u2p);
-                const float nw = o + d;
-                u[gi] = nw;
-                if (u_hi) {   // bf16 hi = RN(u), lo = RN(u - hi)
-                    const __nv_bfloat16 hb = __float2bfloat16_rn(nw);
-                    const __nv_bfloat16 lb = __float2bfloat16_rn(nw - __bfloat162float(hb));
-                    u_hi[gi] = __bfloat16_as_ushort(hb);
-                    u_lo[gi] = __bfloat16_as_ushort(lb);
-                }
+                nw[j] = o + d;
+                // bf16 hi = RN(u), lo = RN(u - hi)
+                const __nv_bfloat16 hb = __float2bfloat16_rn(nw[j]);
+                hi[j] = __bfloat16_as_ushort(hb);
+                lo[j] = __bfloat16_as_ushort(__float2bfloat16_rn(nw[j] - __bfloat162float(hb)));
+            }
+            st4(u + gi, nw);
+            if (u_hi) {   // four bf16 values in one 8-byte store per plane
+                *reinterpret_cast<uint2*>(u_hi + gi) =
+                    make_uint2(hi[0] | ((unsigned)hi[1] << 16), hi[2] | ((unsigned)hi[3] << 16));
+                *reinterpret_cast<uint2*>(u_lo + gi) =
+                    make_uint2(lo[0] | ((unsigned)lo[1] << 16), lo[2] | ((unsigned)lo[3] << 16));
             }
         }
         // the pair's sums (relative error at most 8 x 2^-24) into the double-single
