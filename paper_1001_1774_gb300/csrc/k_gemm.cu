@@ -395,6 +395,19 @@ __device__ __forceinline__ uint32_t gemm_map_peer(const void* local, uint32_t ra
     return r;
 }
 
+// Tensor copy into this block's shared memory that completes on the barrier at
+// shared::cluster address `bar` in either block of the CTA pair (cta_group::2):
+// both blocks' copies of a stage complete on the even block's barrier.
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map, int x, int y,
+                                                 uint32_t bar, uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2"
+        ".L2::cache_hint [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "l"(policy)
+        : "memory");
+}
+
 __device__ __forceinline__ void gemm_arrive_remote(uint32_t addr)
 {
     asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr)
@@ -482,7 +495,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
 
     if (tid == 0) {
         for (int s = 0; s < GP_NST_MAX; ++s) {
-            mbar_init(&full[s], lead ? 2 : 1);   // own copies (+ the odd block's arrival)
+            mbar_init(&full[s], 1);   // even block: its producer's arrival, both blocks' bytes
             mbar_init(&empty[s], 1);
         }
         for (int a = 0; a < NSETS; ++a) {
@@ -510,28 +523,33 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
             // ---------------- TMA producer (both blocks) ----------------
             bool ok = true;
             const uint64_t pol_x = l2_policy_evict_first(), pol_y = l2_policy_evict_last();
+            // every copy of a stage, in either block, completes on the even block's
+            // full barrier, which its producer arms with both blocks' bytes
+            const uint32_t full_lead = gemm_map_peer(full, 0);
             auto load_x = [&](long long it_, long long w) {
                 const int s = (int)(it_ % GP_NST);
                 const int t = (int)(w / kblocks), kb = (int)(w % kblocks);
                 unsigned char* st = smem + (size_t)s * stage_bytes;
-                mbar_arrive_expect_tx(&full[s], stage_bytes);
+                if (lead) mbar_arrive_expect_tx(&full[s], 2 * stage_bytes);
                 // 128-row tile 2 t + rank of the tile-contiguous X (past the last one: zeros)
                 const int xrow = ((2 * t + (int)rank) * kblocks + kb) * GM_BM;
-                tma_load_2d(st, &tXh, 0, xrow, &full[s], pol_x);
-                tma_load_2d(st + GM_A_BYTES, &tXl, 0, xrow, &full[s], pol_x);
+                const uint32_t fb = full_lead + (uint32_t)(s * 8);
+                tma_load_2d_pair(st, &tXh, 0, xrow, fb, pol_x);
+                tma_load_2d_pair(st + GM_A_BYTES, &tXl, 0, xrow, fb, pol_x);
             };
             auto load_y = [&](long long it_, long long w) {
                 const int s = (int)(it_ % GP_NST);
                 const int kb = (int)(w % kblocks);
                 unsigned char* st = smem + (size_t)s * stage_bytes;
+                const uint32_t fb = full_lead + (uint32_t)(s * 8);
 #pragma unroll
                 for (int n = 0; n < NT; ++n) {       // this block's half of each N tile
                     unsigned char* yst = st + yoff[n];
                     for (int j = 0; j < ybox[n]; ++j) {   // 32-row boxes, 1024-byte aligned
                         const int yrow = n * GM_BN + (int)rank * nbh[n] + j * GEMM_Y_BOX;
-                        tma_load_2d(yst + j * GM_YBOX_BYTES, &tYh, kb * GM_BK, yrow, &full[s], pol_y);
-                        tma_load_2d(yst + (ybox[n] + j) * GM_YBOX_BYTES, &tYl, kb * GM_BK, yrow,
-                                    &full[s], pol_y);
+                        tma_load_2d_pair(yst + j * GM_YBOX_BYTES, &tYh, kb * GM_BK, yrow, fb, pol_y);
+                        tma_load_2d_pair(yst + (ybox[n] + j) * GM_YBOX_BYTES, &tYl, kb * GM_BK, yrow, fb,
+                                         pol_y);
                     }
                 }
             };
@@ -551,14 +569,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
                 load_x(it, w);
                 load_y(it, w);
             }
-            // leave no copy in flight; on the even block a stage's phase also
-            // needs the odd block's arrival, hence the drain bound
+            // leave no copy in flight: the even block's full barriers count both
+            // blocks' bytes; the odd block's copies of a stage have landed once the
+            // even block has consumed it (its commit arrives on this block's empty)
             const long long n_issued = it;
-            for (long long j = (n_issued > GP_NST ? n_issued - GP_NST : 0); j < n_issued; ++j)
-                mbar_wait_cluster(&full[j % GP_NST], (uint32_t)(j / GP_NST) & 1u, drain_budget(budget));
+            const long long j0 = n_issued > GP_NST ? n_issued - GP_NST : 0;
+            if (lead)
+                for (long long j = j0; j < n_issued; ++j)
+                    mbar_wait_cluster(&full[j % GP_NST], (uint32_t)(j / GP_NST) & 1u, drain_budget(budget));
             // and no MMA-commit arrival still on its way to this block's barriers
-            if (ok)
-                for (long long j = (n_issued > GP_NST ? n_issued - GP_NST : 0); j < n_issued; ++j)
+            if (ok || !lead)
+                for (long long j = j0; j < n_issued; ++j)
                     mbar_wait_cluster(&empty[j % GP_NST], (uint32_t)(j / GP_NST) & 1u,
                                       drain_budget(budget));
         }
@@ -618,18 +639,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
             if (!ok) {   // a wait gave up: the MMAs already issued finish before TMEM is freed
                 tc_commit_pair(mdrain, 1);
                 mbar_wait(mdrain, 0u, drain_budget(budget));
-            }
-        } else if (lane == 0) {
-            // ------- odd block: tell the even block when each stage has landed -------
-            const uint32_t lead_full = gemm_map_peer(full, 0);
-            long long it = 0;
-            for (long long w = w0; w < w1; ++w, ++it) {
-                const int s = (int)(it % GP_NST);
-                if (!mbar_wait_cluster(&full[s], (uint32_t)(it / GP_NST) & 1u, budget)) {
-                    set_error(ctrl, ERR_TIMEOUT);
-                    break;
-                }
-                gemm_arrive_remote(lead_full + (uint32_t)(s * 8));
             }
         }
     } else {
