@@ -335,9 +335,11 @@ __global__ void __launch_bounds__(192, 1)
 // stages) and the MMAs read 96 KB of shared memory instead of 144 KB, the Y
 // operand is fetched once per pair, and the two blocks' epilogues drain their
 // own halves.
-//   Barriers: the odd block's producer fills its own stage and, once its
-// copies have landed, its warp 1 arrives on the even block's "full" barrier
-// (remote arrival), so the even block's MMAs start when both halves are in.
+//   Barriers: both blocks' producers fill their own stages with tensor copies
+// that complete on the even block's "full" barrier (cta_group::2 copies may
+// signal a barrier in either block of the pair), which the even block's
+// producer arms with both blocks' bytes, so the even block's MMAs start when
+// both halves are in and no thread hands a stage from one block to the other.
 // The MMA commits arrive on the "empty" and "accumulator ready" barriers of
 // both blocks (multicast); the odd block's epilogue warps arrive on the even
 // block's "accumulator drained" barrier.  Stream-K over pairs: pair p owns
