@@ -83,14 +83,14 @@ __device__ __forceinline__ uint32_t map_remote(uint32_t local_smem, uint32_t ran
     return r;
 }
 
-__device__ __forceinline__ void st_remote_f32(uint32_t addr, float v)
+// Store v at shared::cluster address `addr` (any block of the cluster) and count
+// its 4 bytes on the barrier at `bar` in that block (complete_tx): the value is
+// visible to the threads that observe the barrier's phase, with no release fence
+// (a cluster-scope release per row stalled this block's bulk copies of A).
+__device__ __forceinline__ void st_async_f32(uint32_t addr, float v, uint32_t bar)
 {
-    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_remote(uint32_t addr)
-{
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr)
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f32 [%0], %1, [%2];" ::"r"(addr),
+                 "f"(v), "r"(bar)
                  : "memory");
 }
 
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(CONS + 64, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], WARPS);
         }
-        for (int b = 0; b < 4; ++b) mbar_init(&xbar[b], CS);
+        for (int b = 0; b < 4; ++b) mbar_init(&xbar[b], 1);   // the exchange warp's arrival (+ CS parts' bytes)
         for (int b = 0; b < 2; ++b) mbar_init(&partbar[b], WARPS);
         fence_mbar_init();
     }
@@ -174,11 +174,16 @@ __global__ void __launch_bounds__(CONS + 64, 1)
     if (tid >= CONS + 32) {
         // ---------------- exchange warp: the block's part of every row to the cluster ----
         // The warps' parts of row s (red[s & 1], complete when partbar[s & 1] completes)
-        // are read by lanes 0 .. WARPS-1 and added by a fixed shuffle tree; lane k < CS
-        // then stores the sum into block k's slot s mod 4 and arrives on its barrier.  All
-        // reads of red[] for row s precede every send of row s, so the consumers, which
-        // reuse red[s & 1] for row s+2 only after this block's own part of row s reached
-        // them, never overwrite a part that is still to be read.
+        // are read by lanes 0 .. WARPS-1 and added by a fixed shuffle tree; lane 0 arms
+        // this block's slot s mod 4 for the CS parts (one arrival, CS x 4 bytes) and lane
+        // k < CS stores the sum into block k's slot with an asynchronous store that
+        // counts its bytes on block k's barrier.  Slot s mod 4 is armed for row s only
+        // once this block's warps have passed row s-2, hence row s-4: its previous phase
+        // is complete (a peer's bytes may land before the arming, which the barrier's
+        // transaction count allows).  All reads of red[] for row s precede every send of
+        // row s, so the consumers, which reuse red[s & 1] for row s+2 only after this
+        // block's own part of row s reached them, never overwrite a part that is still
+        // to be read.
         const int lane = tid & 31;
         const uint32_t xr = CS > 1 ? map_remote(smem_u32(xred), (uint32_t)(lane % CS)) : 0u;
         const uint32_t xb = CS > 1 ? map_remote(smem_u32(xbar), (uint32_t)(lane % CS)) : 0u;
@@ -191,14 +196,12 @@ __global__ void __launch_bounds__(CONS + 64, 1)
             float part = lane < WARPS ? red[(s & 1) * WARPS + lane] : 0.f;
             part = warp_sum(part);
             const int b = s & 3;
-            if (lane < CS) {
-                if constexpr (CS > 1) {
-                    st_remote_f32(xr + (uint32_t)((b * CS + rank) * 4), part);
-                    mbar_arrive_remote(xb + (uint32_t)(b * 8));
-                } else {
-                    xred[b] = part;
-                    mbar_arrive(&xbar[b]);
-                }
+            if constexpr (CS > 1) {
+                if (lane == 0) mbar_arrive_expect_tx(&xbar[b], (uint32_t)CS * 4u);
+                if (lane < CS) st_async_f32(xr + (uint32_t)((b * CS + rank) * 4), part, xb + (uint32_t)(b * 8));
+            } else if (lane == 0) {
+                xred[b] = part;
+                mbar_arrive(&xbar[b]);
             }
             __syncwarp();
         }
