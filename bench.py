@@ -34,6 +34,7 @@ METRIC = "ADM iter/s and recons/s at <=1e-4 rel err vs FP64 oracle; % of HBM/ten
 ITERS_PER_RECON = 300
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_products_n128_m4915.json")
 PRODUCTS_SRC = os.path.join(ROOT, "paper_1001_1774_gb300", "csrc", "k_products.cu")
+GEMM_SUMMARY = os.path.join(ROOT, "profiles", "k_gemm_bf16x3_pair_batch256_n128_m4915.json")
 
 
 def parse_args():
@@ -208,17 +209,17 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- traffic summary
 
-def traffic_from_profile():
-    """dram bytes per launch of the product kernel from the committed ncu summary,
-    or None when the kernel source changed since it was taken."""
+def traffic_from_profile(summary=PROFILE_SUMMARY, key="dram_bytes_per_launch"):
+    """dram bytes per launch (or launch pair) of a kernel from its committed ncu
+    summary, or None when the kernel's source changed since it was taken."""
     try:
-        with open(PROFILE_SUMMARY) as fh:
+        with open(summary) as fh:
             d = json.load(fh)
-        with open(PRODUCTS_SRC, "rb") as fh:
+        with open(os.path.join(ROOT, d["source"]), "rb") as fh:
             sha = hashlib.sha256(fh.read()).hexdigest()
         if d.get("source_sha256") != sha:
             return None
-        return float(d["dram_bytes_per_launch"])
+        return float(d[key])
     except Exception:
         return None
 
@@ -593,7 +594,11 @@ def batch_segment(tv, steps, warmup, stream, want_parity=True, images=256, gemm_
            "roofline": {"bound": "tensor", "achieved": tf, "peak": peak[0], "unit": "TFLOP/s",
                         "frac": tf / peak[0], "kernel": "the two batched GEMMs, R = A U and G = A^T R (k_gemm_bf16x3_pair on CTA pairs or k_gemm_bf16x3, the shape the tuner picks)",
                         "flops_per_iteration": flops, "launch_pair_us": gemm_us,
-                        "peak_source": peak[1]},
+                        "peak_source": peak[1],
+                        # dram bytes of one launch pair (both GEMMs), from the committed capture
+                        # at 256 images
+                        "traffic": (traffic_from_profile(GEMM_SUMMARY, "dram_bytes_per_launch_pair")
+                                    if B == 256 else None)},
            "stage_us": {"gemm_pair": gemm_us, "fixups": fix_us, "usolve_batched": us_us,
                         "loop_per_iteration": loop_ms * 1e3 / steps},
            "e2e": {"value": B * steps / e2e_s, "unit": "image-iter/s",
@@ -638,7 +643,6 @@ def run_batched(args):
     for k in ("roofline", "stage_us", "e2e", "gpu_launches", "clocks", "tau", "parity_vs_oracle"):
         if k in b:
             out[k] = b[k]
-    out["roofline"]["traffic"] = None
     if not args.no_cpu_baseline:
         P = synth.Problem("batch_img0", 128, m, 1, mus[0], 10.0, 0.0, args.steps, 0.0, None, A,
                           F[0])
