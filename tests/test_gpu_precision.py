@@ -65,6 +65,35 @@ def test_precision_products(tv, prec, n, m):
     tv.tvcs_destroy(h)
 
 
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_cluster_products_repeat_bitwise(tv, prec):
+    """The 256 x 256 products (rows split over a 4-block cluster) sum each row's
+    block parts in a fixed order after an exchange whose stores complete on the
+    receiving block's barrier: a part read before it landed would change r (and g)
+    from one launch to the next.  Five launches on the same inputs, 2000 rows (55-56
+    per cluster, each exchange slot reused 14 times), must agree bit for bit."""
+    n, m = 256, 2000
+    N = n * n
+    opt = tv.tvcs_default_options()
+    opt.precision = prec
+    opt.tau = 0.1
+    h = tv.tvcs_create(None, 11 + prec, m, n, 1.0, 1.0, 0.0, opt)
+    rng = np.random.default_rng(5 + prec)
+    x = torch.from_numpy(rng.standard_normal(N).astype(np.float32)).cuda()
+    y = torch.from_numpy(rng.standard_normal(m).astype(np.float32)).cuda()
+    runs = []
+    for _ in range(5):
+        r = torch.empty(m, device="cuda")
+        g = torch.empty(N, device="cuda")
+        tv.tvcs_apply(h, x, y, r, g)
+        runs.append((r.cpu().numpy(), g.cpu().numpy()))
+    tv.tvcs_destroy(h)
+    r0, g0 = runs[0]
+    assert np.all(np.isfinite(r0)) and np.all(np.isfinite(g0)) and np.any(r0 != 0)
+    for r1, g1 in runs[1:]:
+        assert np.array_equal(r0, r1) and np.array_equal(g0, g1)
+
+
 @pytest.mark.parametrize("prec", [1, 2])
 def test_precision_fixed_50_iterations(tv, prec):
     P = synth.make_problem(64, 0.3, 9, 6, 1e3, 10.0, noise_c=1e-3)
