@@ -272,6 +272,7 @@ __global__ void __launch_bounds__(CONS + 64, 1)
     named_barrier(1, CONS);
     float2 r2 = make_float2(0.f, 0.f);   // double-single ||r||^2 (block 0, thread 0)
     bool ok = true;
+    int s_nowait = -1;   // first row whose parts this thread did not wait for (a wait gave up)
     auto row_scale = [&](int s) -> float {
         if constexpr (PREC == 2) return s_in_smem ? ss[s] : rscale[i0 + s];
         return 1.0f;
@@ -285,6 +286,7 @@ __global__ void __launch_bounds__(CONS + 64, 1)
         if (ok && !mbar_wait(&full[slot], (s / NST) & 1, budget)) {
             set_error(ctrl, ERR_TIMEOUT);
             ok = false;
+            s_nowait = s > 0 ? s - 1 : 0;   // the exchange of row s-1 is not awaited either
         }
         const unsigned char* sb = smem + (size_t)slot * S::STAGE_BYTES;
         float d0 = 0.f, d1 = 0.f;
@@ -360,6 +362,7 @@ __global__ void __launch_bounds__(CONS + 64, 1)
                     if (clock64() - t0 > budget) {
                         set_error(ctrl, ERR_TIMEOUT);
                         ok = false;
+                        s_nowait = s;
                         break;
                     }
                 }
@@ -445,7 +448,16 @@ __global__ void __launch_bounds__(CONS + 64, 1)
         }
     }
     __syncwarp();
-    if constexpr (CS > 1) cluster_sync_all();
+    if constexpr (CS > 1) {
+        cluster_sync_all();
+        // After a wait gave up, parts of the rows no longer awaited may still be on their
+        // way into this block's shared memory (stores that complete on its barriers).
+        // Every block has issued all of its parts by the cluster barrier above, so thread
+        // 0 waits for them (bounded) before the block retires.
+        if (tid == 0 && s_nowait >= 0)
+            for (int s = s_nowait; s < nrows; ++s)
+                mbar_wait(&xbar[s & 3], (uint32_t)((s >> 2) & 1), drain_budget(budget));
+    }
 }
 
 // ---------------------------------------------------------------------------
