@@ -133,7 +133,7 @@ void chunking(int m, int N, int* rpc, int* chunks)
 std::vector<RegenPlan> candidates(int maxN, int P)
 {
     std::vector<RegenPlan> out;
-    const int variants[5][2] = {{2, 2}, {3, 2}, {3, 1}, {4, 2}, {4, 1}};   // (blocks/SM, tile buffers)
+    const int variants[6][2] = {{2, 2}, {2, 1}, {3, 2}, {3, 1}, {4, 2}, {4, 1}};   // (blocks/SM, tile buffers)
     for (const auto& v : variants)
         for (int cs : {4, 8, 16})
             for (int rt : {1, 2, 4, 8}) {
